@@ -1,0 +1,223 @@
+/*
+ * pp.h -- C ABI of the B300 photon propagator.
+ *
+ * Monte Carlo propagation of photons from light sources ("photon emitting
+ * steps", paper Sec. 4) through ice described in 10 m depth layers with
+ * per-layer scattering and absorption coefficients, until each photon reaches
+ * a detector module (DOM), is absorbed, or leaves the simulated volume
+ * (paper Sec. 2: distance to the next scatter drawn by Monte Carlo, a new
+ * angle from the scattering physics, repeated until the photon meets a DOM or
+ * is absorbed; photons are independent, "embarrassingly parallel").
+ *
+ * Conventions for every entry point:
+ *   - Return 0 (PP_OK) or a negative PP_E* code; pp_last_error() gives a
+ *     message for the context.  No C++ exception crosses this ABI.
+ *   - Host pointers are caller-owned, read (or written) only during the call.
+ *   - Device pointers ("d_" prefix) are caller-owned device memory on the
+ *     context's device; *_async entry points enqueue work on the given CUDA
+ *     stream (NULL: the context's stream) and return without synchronising;
+ *     the caller keeps the buffers alive until that work completes.
+ *   - Memory the library needs beyond inputs and outputs (geometry tables,
+ *     prefix sums, work counters, staging copies of host inputs) is owned by
+ *     the context, allocated with cudaMalloc, grown on demand and freed by
+ *     pp_destroy().
+ *   - Results depend only on (seed, event id, the event's sources, geometry,
+ *     ice, settings): never on batching, launch shape or timing.  Random
+ *     numbers are Philox4x32-10 keyed by (seed, event id) with counter
+ *     (photon id, step), and tallies are integer atomics, so hits + absorbed
+ *     + escaped equals the number of emitted photons exactly.
+ *   - Calls on one context are serialised by the library (a mutex).
+ *
+ * Coordinates: metres, right-handed, z up; depth = depth_of_z0_m - z.
+ */
+#ifndef PP_H_
+#define PP_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PP_OK 0
+#define PP_EINVAL (-1)      /* bad argument (null pointer, size, non-finite value) */
+#define PP_ENOTLOADED (-2)  /* geometry or ice not loaded yet */
+#define PP_EBUDGET (-3)     /* request larger than the configured budget */
+#define PP_ETIMEDOUT (-4)   /* a bounded wait ran out */
+#define PP_ECUDA (-5)       /* a CUDA runtime call failed (message in pp_last_error) */
+#define PP_EDEVICE (-6)     /* a kernel raised its error flag (bad input seen on device) */
+#define PP_ENOMEM (-7)      /* device allocation failed */
+#define PP_ENODEV (-8)      /* no usable CUDA device */
+
+/* Source types.  ISO_POINT and CASCADE emit isotropically from a point on the
+ * segment; CHERENKOV emits on a 41 degree cone about the segment direction. */
+#define PP_SRC_ISO_POINT 0u
+#define PP_SRC_CHERENKOV 1u
+#define PP_SRC_CASCADE 2u
+
+/* Photon outcome codes of pp_debug_trace (a value >= 0 is the DOM index). */
+#define PP_OUT_ABSORBED (-1)
+#define PP_OUT_ESCAPED (-2)
+#define PP_OUT_TRUNCATED (-3)
+
+typedef struct pp_ctx pp_ctx; /* opaque, library-owned */
+
+typedef struct pp_config {
+  int32_t device;                     /* CUDA device ordinal */
+  uint32_t max_steps;                 /* step cap per photon; reaching it counts as absorbed
+                                         and as truncated (default 100000) */
+  uint64_t seed;                      /* Philox key word 0 (low 32 bits used) */
+  uint64_t photon_budget_bytes;       /* admission budget for queued requests (0: none) */
+  float world_margin_m;               /* world cylinder = DOM extent + margin (default 100) */
+  float depth_of_z0_m;                /* depth of the z = 0 plane (default 1950) */
+  int32_t scatter_coeff_is_effective; /* 1 (default): b_e is the effective coefficient and the
+                                         geometric one is b_e / (1 - g); 0: b_e is used as is */
+  int32_t reserved;
+  void* stream;                       /* cudaStream_t for the context's work; NULL: a stream
+                                         the context creates */
+} pp_config;
+
+/* One light source, 40 bytes: photons are born uniformly along the segment
+ * [x, x + length * d] (a point when length is 0). */
+typedef struct pp_source {
+  float x, y, z;    /* start point (m) */
+  float dx, dy, dz; /* direction of the emitting segment (normalised on use) */
+  float length;     /* segment length (m), >= 0 */
+  uint32_t type;    /* PP_SRC_* */
+  uint64_t n_photons;
+} pp_source;
+
+/* Fills *cfg with the defaults listed above.  Returns PP_EINVAL on NULL. */
+int pp_config_default(pp_config* cfg);
+
+/* Creates a context on cfg->device.  *out receives the context.
+ * Errors: PP_EINVAL, PP_ENODEV, PP_ECUDA. */
+int pp_create(const pp_config* cfg, pp_ctx** out);
+
+/* Frees the context and all device memory it owns.  NULL is accepted. */
+int pp_destroy(pp_ctx* ctx);
+
+/* Message for the last error raised on this context (never NULL). */
+const char* pp_last_error(const pp_ctx* ctx);
+
+/* Text for a PP_E* code (never NULL). */
+const char* pp_strerror(int code);
+
+/* Loads the detector (paper Sec. 1: DOMs on vertical strings between 1450 m
+ * and 2450 m depth).
+ *   xyz        [n_dom][3] float32 DOM centres (m), host memory
+ *   string_id  [n_dom] int32 string of each DOM (DOMs of one string should sit
+ *              near one vertical line; any grouping gives the same results,
+ *              this one is fast)
+ *   n_dom      0 <= n_dom <= 65535
+ *   dom_radius sphere radius (m), > 0
+ * Builds the per-string tables, the 2-D cell grid used by the hit test, and
+ * the world cylinder (radius = max DOM distance from the z axis + margin,
+ * z range = DOM z range +- margin).  Errors: PP_EINVAL, PP_ENOMEM, PP_ECUDA. */
+int pp_load_geometry(pp_ctx* ctx, const float* xyz, const int32_t* string_id, int32_t n_dom,
+                     float dom_radius);
+
+/* Loads the ice model (paper Sec. 2: vertical layers of 10 m, each with its
+ * own scattering and absorption coefficient).
+ *   b_e, a      [n_layers] float32, >= 0: effective scattering and absorption
+ *               coefficients (1/m); layer i spans depth
+ *               [depth_top_m + i dz_m, depth_top_m + (i + 1) dz_m); depths
+ *               outside the table take the nearest edge layer's values
+ *   n_layers    1 <= n_layers <= 4096
+ *   dz_m        > 0
+ *   g           Henyey-Greenstein mean cosine, -1 < g < 1
+ * Errors: PP_EINVAL, PP_ENOMEM, PP_ECUDA. */
+int pp_load_ice(pp_ctx* ctx, const float* b_e, const float* a, int32_t n_layers,
+                float depth_top_m, float dz_m, float g);
+
+/* One event, plain path: one GPU thread per photon, launched for this event
+ * alone.  Host buffers.
+ *   src[n_src]   sources of the event; photon j of source s has photon id
+ *                (sum of n_photons of the sources before s) + j
+ *   hits[n_dom]  out: photons that ended on each DOM
+ *   counts[4]    out: absorbed (truncated included), escaped, truncated, steps
+ * Errors: PP_EINVAL, PP_ENOTLOADED, PP_ECUDA, PP_EDEVICE. */
+int pp_propagate(pp_ctx* ctx, uint64_t event_id, const pp_source* src, int64_t n_src,
+                 uint64_t* hits, uint64_t* counts);
+
+/* Many events in one persistent launch (cross-event batching, paper Sec. 4:
+ * the photon server aggregates steps from many events and clients).  Host
+ * buffers.
+ *   event_ids[n_events]       event ids (the Philox key's second word, low 32 bits)
+ *   src_begin[n_events + 1]   event e owns src[src_begin[e] .. src_begin[e+1]),
+ *                             non-decreasing, src_begin[0] = 0
+ *   src[src_begin[n_events]]  all sources
+ *   hits[n_events][n_dom], counts[n_events][4]  out, as for pp_propagate
+ * Errors: PP_EINVAL, PP_ENOTLOADED, PP_ECUDA, PP_EDEVICE. */
+int pp_propagate_batch(pp_ctx* ctx, int32_t n_events, const uint64_t* event_ids,
+                       const int64_t* src_begin, const pp_source* src, uint64_t* hits,
+                       uint64_t* counts);
+
+/* pp_propagate_batch on device-resident inputs and outputs, enqueued on
+ * `stream` (NULL: the context's stream); returns once enqueued.
+ *   d_event_ids[n_events], d_src_begin[n_events + 1], d_src[n_src] device inputs
+ *   n_src                     = src_begin[n_events] (host value)
+ *   d_hits[n_events][n_dom], d_counts[n_events][4] device outputs (overwritten)
+ * Device errors are latched in the context and returned by pp_sync(). */
+int pp_propagate_batch_async(pp_ctx* ctx, int32_t n_events, const uint64_t* d_event_ids,
+                             const int64_t* d_src_begin, const pp_source* d_src, int64_t n_src,
+                             uint64_t* d_hits, uint64_t* d_counts, void* stream);
+
+/* The plain per-event path on device-resident data: for each event, its own
+ * launches with one thread per photon.  Event sizes must be known on the host:
+ *   h_event_ids[n_events], h_src_begin[n_events + 1], h_event_photons[n_events]
+ *   host arrays; d_src, d_hits, d_counts device buffers as above. */
+int pp_propagate_plain_async(pp_ctx* ctx, int32_t n_events, const uint64_t* h_event_ids,
+                             const int64_t* h_src_begin, const uint64_t* h_event_photons,
+                             const pp_source* d_src, uint64_t* d_hits, uint64_t* d_counts,
+                             void* stream);
+
+/* Waits for `stream` (NULL: the context's stream) and reports a device error
+ * flag raised since the last pp_sync.  Errors: PP_ECUDA, PP_EDEVICE. */
+int pp_sync(pp_ctx* ctx, void* stream);
+
+/* Launch settings of the persistent kernel (the autotuner's knobs).
+ *   block_threads     128, 256, 512 or 1024 (0: keep)
+ *   blocks_per_sm     >= 1 (0: as many as fit)
+ *   refill_threshold  1..32: a warp claims new photons once at least this
+ *                     many of its lanes are idle (0: keep) */
+int pp_set_launch(pp_ctx* ctx, int32_t block_threads, int32_t blocks_per_sm,
+                  int32_t refill_threshold);
+
+/* Reads back the launch settings in use (any pointer may be NULL). */
+int pp_get_launch(const pp_ctx* ctx, int32_t* block_threads, int32_t* blocks_per_sm,
+                  int32_t* refill_threshold, int32_t* grid_blocks);
+
+/* World cylinder in use: out3 = {radius, z_min, z_max}. */
+int pp_get_world(const pp_ctx* ctx, float* out3);
+
+/* ---- debug and parity entry points (host buffers) ------------------------ */
+
+/* Philox4x32-10 blocks computed on the device: out[i] = Philox(ctr[i], key[i]).
+ *   ctr[n][4], key[n][2], out[n][4] uint32 */
+int pp_debug_philox(pp_ctx* ctx, const uint32_t* ctr, const uint32_t* key, uint32_t* out,
+                    int64_t n);
+
+/* Follows chosen photons of one event with the production step code and
+ * records them.  photon_ids[n] are per-event photon ids.
+ *   outcome[n]   out: DOM index, or PP_OUT_ABSORBED / _ESCAPED / _TRUNCATED
+ *   n_steps[n]   out: steps taken (Philox blocks drawn after birth)
+ *   birth[n][6]  out: birth point and direction (may be NULL)
+ *   trace[n][n_trace][3] out: the first n_trace scatter points, NaN after the
+ *                photon's last scatter (may be NULL when n_trace = 0) */
+int pp_debug_trace(pp_ctx* ctx, uint64_t event_id, const pp_source* src, int64_t n_src,
+                   const uint64_t* photon_ids, int64_t n, int32_t n_trace, int32_t* outcome,
+                   int64_t* n_steps, float* birth, float* trace);
+
+/* The device hit test on given segments: first DOM met on [p, p + S d].
+ *   seg[n][7]   p (3), d (3, unit), S
+ *   mode        0: string / cell-grid search (production), 1: every DOM
+ *   dom[n]      out: DOM index or -1;  t[n] out: distance (inf when none) */
+int pp_debug_first_hit(pp_ctx* ctx, const float* seg, int64_t n, int32_t mode, int32_t* dom,
+                       float* t);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PP_H_ */

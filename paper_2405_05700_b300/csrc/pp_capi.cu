@@ -1,0 +1,763 @@
+// C ABI of the photon propagator (declared in include/pp.h): context,
+// geometry and ice loading (with the host-side preprocessing of the hit-test
+// tables), argument checking, staging of host buffers, launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "pp.h"
+#include "pp_internal.h"
+
+using namespace ppk;
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+}  // namespace
+
+struct pp_ctx {
+  pp_config cfg{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int sm_count = 0;
+  std::mutex mu;
+  std::string last_error = "no error";
+
+  bool geom_loaded = false, ice_loaded = false;
+  GeomDev geom{};
+  IceDev ice{};
+  // device tables
+  DevBuf dom, str, str_range, sdom_z, sdom_idx, clear, cell_off, cell_list, layers;
+  // scratch
+  DevBuf off, chunk, src_event, bsum, meta, work, err;
+  // staging for host entry points
+  DevBuf s_src, s_begin, s_ids, s_hits, s_counts, s_misc1, s_misc2, s_misc3, s_misc4;
+  size_t smem_limit_set = 0;
+
+  int block_threads = 256;
+  int blocks_per_sm = 0;  // 0: occupancy maximum
+  int refill = 8;
+};
+
+namespace {
+
+int fail(pp_ctx* c, int code, const std::string& msg) {
+  if (c) c->last_error = msg;
+  return code;
+}
+
+int cuda_fail(pp_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, PP_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define PP_CUDA(expr)                                   \
+  do {                                                  \
+    cudaError_t _e = (expr);                            \
+    if (_e != cudaSuccess) return cuda_fail(ctx, _e, #expr); \
+  } while (0)
+
+int ensure(pp_ctx* ctx, DevBuf& b, size_t bytes) {
+  if (bytes <= b.cap && b.p) return PP_OK;
+  // the old buffer may still be read by queued work on the context's stream
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+  size_t nb = std::max<size_t>(bytes, 256);
+  nb = (nb + 255) & ~(size_t)255;
+  e = cudaMalloc(&b.p, nb);
+  if (e != cudaSuccess) {
+    b.p = nullptr;
+    (void)cudaGetLastError();
+    return fail(ctx, PP_ENOMEM, std::string("cudaMalloc of ") + std::to_string(nb) +
+                                     " bytes failed: " + cudaGetErrorString(e));
+  }
+  b.cap = nb;
+  return PP_OK;
+}
+
+void release(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+}
+
+template <class T>
+int upload(pp_ctx* ctx, DevBuf& b, const std::vector<T>& v) {
+  int rc = ensure(ctx, b, v.size() * sizeof(T));
+  if (rc) return rc;
+  if (!v.empty()) PP_CUDA(cudaMemcpy(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return PP_OK;
+}
+
+cudaStream_t pick_stream(pp_ctx* ctx, void* s) {
+  return s ? static_cast<cudaStream_t>(s) : ctx->stream;
+}
+
+bool source_ok(const pp_source& s) {
+  return std::isfinite(s.x) && std::isfinite(s.y) && std::isfinite(s.z) && std::isfinite(s.dx) &&
+         std::isfinite(s.dy) && std::isfinite(s.dz) && std::isfinite(s.length) && s.length >= 0.f &&
+         (s.dx != 0.f || s.dy != 0.f || s.dz != 0.f) && s.type <= PP_SRC_CASCADE;
+}
+
+int check_sources(pp_ctx* ctx, const pp_source* src, int64_t n) {
+  for (int64_t i = 0; i < n; ++i)
+    if (!source_ok(src[i]))
+      return fail(ctx, PP_EINVAL, "source " + std::to_string(i) +
+                                      " has a non-finite field, a zero direction, a negative "
+                                      "length or an unknown type");
+  return PP_OK;
+}
+
+int check_loaded(pp_ctx* ctx) {
+  if (!ctx->geom_loaded || !ctx->ice_loaded)
+    return fail(ctx, PP_ENOTLOADED, "load geometry and ice before propagating");
+  return PP_OK;
+}
+
+int prepare_smem(pp_ctx* ctx, size_t* smem) {
+  *smem = tables_smem_bytes(ctx->ice, ctx->geom);
+  if (*smem > ctx->smem_limit_set || ctx->smem_limit_set == 0) {
+    cudaError_t e = set_propagate_smem_limit(std::max<size_t>(*smem, 48 * 1024));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute");
+    ctx->smem_limit_set = std::max<size_t>(*smem, 48 * 1024);
+  }
+  return PP_OK;
+}
+
+int grid_blocks(pp_ctx* ctx, size_t smem, int* out) {
+  int occ = 0;
+  cudaError_t e = propagate_occupancy(ctx->block_threads, smem, &occ);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  if (occ < 1) return fail(ctx, PP_EINVAL, "propagation kernel does not fit on an SM");
+  const int bps = ctx->blocks_per_sm > 0 ? std::min(ctx->blocks_per_sm, occ) : occ;
+  *out = bps * ctx->sm_count;
+  return PP_OK;
+}
+
+RunDev run_params(const pp_ctx* ctx) {
+  RunDev r;
+  r.seed_lo = (uint32_t)ctx->cfg.seed;
+  r.max_steps = ctx->cfg.max_steps;
+  r.cos_cherenkov = (float)std::cos(41.0 * 3.14159265358979323846 / 180.0);
+  r.refill = ctx->refill;
+  return r;
+}
+
+int ensure_scratch(pp_ctx* ctx, int64_t n_src, bool with_events) {
+  int rc;
+  if ((rc = ensure(ctx, ctx->off, sizeof(uint64_t) * (size_t)(n_src + 1)))) return rc;
+  if ((rc = ensure(ctx, ctx->chunk, sizeof(uint32_t) * (size_t)(n_src + 2)))) return rc;
+  if (with_events && (rc = ensure(ctx, ctx->src_event, sizeof(uint32_t) * (size_t)std::max<int64_t>(n_src, 1))))
+    return rc;
+  const int64_t nb = (n_src + kScanTile - 1) / kScanTile;
+  if ((rc = ensure(ctx, ctx->bsum, sizeof(uint64_t) * (size_t)std::max<int64_t>(nb, 1)))) return rc;
+  if ((rc = ensure(ctx, ctx->meta, sizeof(uint64_t) * 2))) return rc;
+  if ((rc = ensure(ctx, ctx->work, sizeof(uint64_t)))) return rc;
+  return PP_OK;
+}
+
+ExpandBufs expand_bufs(pp_ctx* ctx, bool with_events) {
+  ExpandBufs b;
+  b.off = static_cast<uint64_t*>(ctx->off.p);
+  b.chunk_src = static_cast<uint32_t*>(ctx->chunk.p);
+  b.src_event = with_events ? static_cast<uint32_t*>(ctx->src_event.p) : nullptr;
+  b.bsum = static_cast<uint64_t*>(ctx->bsum.p);
+  b.meta = static_cast<uint64_t*>(ctx->meta.p);
+  return b;
+}
+
+WorkDev work_desc(pp_ctx* ctx, const pp_source* d_src, int64_t n_src, bool with_events,
+                  const int64_t* d_begin, const uint64_t* d_ids, uint64_t* d_hits,
+                  uint64_t* d_counts, uint32_t single_ev_lo) {
+  WorkDev w;
+  w.src = d_src;
+  w.off = static_cast<const uint64_t*>(ctx->off.p);
+  w.chunk_src = static_cast<const uint32_t*>(ctx->chunk.p);
+  w.src_event = with_events ? static_cast<const uint32_t*>(ctx->src_event.p) : nullptr;
+  w.src_begin = d_begin;
+  w.event_ids = d_ids;
+  w.meta = static_cast<const uint64_t*>(ctx->meta.p);
+  w.work = static_cast<unsigned long long*>(ctx->work.p);
+  w.hits = reinterpret_cast<unsigned long long*>(d_hits);
+  w.counts = reinterpret_cast<unsigned long long*>(d_counts);
+  w.err = static_cast<int*>(ctx->err.p);
+  w.n_src = (int)n_src;
+  w.single_event_lo = single_ev_lo;
+  return w;
+}
+
+// Batched persistent path on device data (the lock is held by the caller).
+int batch_async(pp_ctx* ctx, int32_t n_events, const uint64_t* d_ids, const int64_t* d_begin,
+                const pp_source* d_src, int64_t n_src, uint64_t* d_hits, uint64_t* d_counts,
+                cudaStream_t st) {
+  int rc;
+  if ((rc = check_loaded(ctx))) return rc;
+  if (n_events < 0 || n_src < 0 || n_src > kMaxSources)
+    return fail(ctx, PP_EINVAL, "n_events/n_src out of range (n_src <= 33554432 per call)");
+  if (n_events == 0) return PP_OK;
+  if (!d_ids || !d_begin || !d_hits || !d_counts || (n_src > 0 && !d_src))
+    return fail(ctx, PP_EINVAL, "null device pointer");
+  const size_t hb = sizeof(uint64_t) * (size_t)n_events * ctx->geom.n_dom;
+  if (hb) PP_CUDA(cudaMemsetAsync(d_hits, 0, hb, st));
+  PP_CUDA(cudaMemsetAsync(d_counts, 0, sizeof(uint64_t) * 4 * (size_t)n_events, st));
+  if (n_src == 0) return PP_OK;
+  if ((rc = ensure_scratch(ctx, n_src, true))) return rc;
+  size_t smem;
+  if ((rc = prepare_smem(ctx, &smem))) return rc;
+  int grid;
+  if ((rc = grid_blocks(ctx, smem, &grid))) return rc;
+  PP_CUDA(cudaMemsetAsync(ctx->work.p, 0, sizeof(uint64_t), st));
+  PP_CUDA(launch_expand(d_src, n_src, d_begin, n_events, expand_bufs(ctx, true), st));
+  const WorkDev w = work_desc(ctx, d_src, n_src, true, d_begin, d_ids, d_hits, d_counts, 0);
+  PP_CUDA(launch_propagate(true, ctx->ice, ctx->geom, w, run_params(ctx), ctx->block_threads,
+                           grid, 0, smem, st));
+  return PP_OK;
+}
+
+// Plain path: per event, expansion and one thread per photon.
+int plain_async(pp_ctx* ctx, int32_t n_events, const uint64_t* h_ids, const int64_t* h_begin,
+                const uint64_t* h_photons, const pp_source* d_src, uint64_t* d_hits,
+                uint64_t* d_counts, cudaStream_t st) {
+  int rc;
+  if ((rc = check_loaded(ctx))) return rc;
+  if (n_events < 0) return fail(ctx, PP_EINVAL, "n_events < 0");
+  if (n_events == 0) return PP_OK;
+  if (!h_ids || !h_begin || !h_photons || !d_hits || !d_counts)
+    return fail(ctx, PP_EINVAL, "null pointer");
+  int64_t max_src = 0;
+  for (int32_t e = 0; e < n_events; ++e) {
+    const int64_t n = h_begin[e + 1] - h_begin[e];
+    if (n < 0 || h_begin[0] != 0) return fail(ctx, PP_EINVAL, "src_begin must start at 0 and not decrease");
+    max_src = std::max(max_src, n);
+  }
+  if (max_src > kMaxSources) return fail(ctx, PP_EINVAL, "too many sources in one event");
+  if (max_src > 0 && !d_src) return fail(ctx, PP_EINVAL, "null source pointer");
+  const int n_dom = ctx->geom.n_dom;
+  if (n_dom) PP_CUDA(cudaMemsetAsync(d_hits, 0, sizeof(uint64_t) * (size_t)n_events * n_dom, st));
+  PP_CUDA(cudaMemsetAsync(d_counts, 0, sizeof(uint64_t) * 4 * (size_t)n_events, st));
+  if ((rc = ensure_scratch(ctx, std::max<int64_t>(max_src, 1), false))) return rc;
+  size_t smem;
+  if ((rc = prepare_smem(ctx, &smem))) return rc;
+  const RunDev run = run_params(ctx);
+  for (int32_t e = 0; e < n_events; ++e) {
+    const int64_t n = h_begin[e + 1] - h_begin[e];
+    if (n == 0 || h_photons[e] == 0) continue;
+    const pp_source* s = d_src + h_begin[e];
+    PP_CUDA(launch_expand(s, n, nullptr, 1, expand_bufs(ctx, false), st));
+    const WorkDev w = work_desc(ctx, s, n, false, nullptr, nullptr, d_hits + (size_t)e * n_dom,
+                                d_counts + 4 * (size_t)e, (uint32_t)h_ids[e]);
+    PP_CUDA(launch_propagate(false, ctx->ice, ctx->geom, w, run, ctx->block_threads, 0,
+                             h_photons[e], smem, st));
+  }
+  return PP_OK;
+}
+
+int sync_and_check(pp_ctx* ctx, cudaStream_t st) {
+  PP_CUDA(cudaStreamSynchronize(st));
+  int flag = 0;
+  PP_CUDA(cudaMemcpy(&flag, ctx->err.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) {
+    PP_CUDA(cudaMemset(ctx->err.p, 0, sizeof(int)));
+    return fail(ctx, PP_EDEVICE, "device error flag " + std::to_string(flag) +
+                                     " (malformed source seen by a kernel)");
+  }
+  return PP_OK;
+}
+
+// Host batch: stage inputs, run the given path, copy results back.
+int batch_host(pp_ctx* ctx, bool plain, int32_t n_events, const uint64_t* ids,
+               const int64_t* begin, const pp_source* src, uint64_t* hits, uint64_t* counts) {
+  int rc;
+  if ((rc = check_loaded(ctx))) return rc;
+  if (n_events < 0 || (n_events > 0 && (!ids || !begin || !hits || !counts)))
+    return fail(ctx, PP_EINVAL, "null pointer or negative n_events");
+  if (n_events == 0) return PP_OK;
+  if (begin[0] != 0) return fail(ctx, PP_EINVAL, "src_begin[0] must be 0");
+  for (int32_t e = 0; e < n_events; ++e)
+    if (begin[e + 1] < begin[e]) return fail(ctx, PP_EINVAL, "src_begin decreases");
+  const int64_t n_src = begin[n_events];
+  if (n_src > 0 && !src) return fail(ctx, PP_EINVAL, "null source pointer");
+  if ((rc = check_sources(ctx, src, n_src))) return rc;
+  const int n_dom = ctx->geom.n_dom;
+  cudaStream_t st = ctx->stream;
+  if ((rc = ensure(ctx, ctx->s_src, sizeof(pp_source) * (size_t)std::max<int64_t>(n_src, 1)))) return rc;
+  if ((rc = ensure(ctx, ctx->s_begin, sizeof(int64_t) * (size_t)(n_events + 1)))) return rc;
+  if ((rc = ensure(ctx, ctx->s_ids, sizeof(uint64_t) * (size_t)n_events))) return rc;
+  if ((rc = ensure(ctx, ctx->s_hits, sizeof(uint64_t) * (size_t)n_events * std::max(n_dom, 1)))) return rc;
+  if ((rc = ensure(ctx, ctx->s_counts, sizeof(uint64_t) * 4 * (size_t)n_events))) return rc;
+  if (n_src)
+    PP_CUDA(cudaMemcpyAsync(ctx->s_src.p, src, sizeof(pp_source) * n_src, cudaMemcpyHostToDevice, st));
+  PP_CUDA(cudaMemcpyAsync(ctx->s_begin.p, begin, sizeof(int64_t) * (n_events + 1), cudaMemcpyHostToDevice, st));
+  PP_CUDA(cudaMemcpyAsync(ctx->s_ids.p, ids, sizeof(uint64_t) * n_events, cudaMemcpyHostToDevice, st));
+  uint64_t* d_hits = static_cast<uint64_t*>(ctx->s_hits.p);
+  uint64_t* d_counts = static_cast<uint64_t*>(ctx->s_counts.p);
+  const pp_source* d_src = static_cast<const pp_source*>(ctx->s_src.p);
+  if (plain) {
+    std::vector<uint64_t> ph(n_events, 0);
+    for (int32_t e = 0; e < n_events; ++e)
+      for (int64_t s = begin[e]; s < begin[e + 1]; ++s) ph[e] += src[s].n_photons;
+    rc = plain_async(ctx, n_events, ids, begin, ph.data(), d_src, d_hits, d_counts, st);
+  } else {
+    rc = batch_async(ctx, n_events, static_cast<const uint64_t*>(ctx->s_ids.p),
+                     static_cast<const int64_t*>(ctx->s_begin.p), d_src, n_src, d_hits, d_counts, st);
+  }
+  if (rc) return rc;
+  if (n_dom)
+    PP_CUDA(cudaMemcpyAsync(hits, d_hits, sizeof(uint64_t) * (size_t)n_events * n_dom, cudaMemcpyDeviceToHost, st));
+  PP_CUDA(cudaMemcpyAsync(counts, d_counts, sizeof(uint64_t) * 4 * (size_t)n_events, cudaMemcpyDeviceToHost, st));
+  return sync_and_check(ctx, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pp_strerror(int code) {
+  switch (code) {
+    case PP_OK: return "ok";
+    case PP_EINVAL: return "invalid argument";
+    case PP_ENOTLOADED: return "geometry or ice not loaded";
+    case PP_EBUDGET: return "request exceeds the budget";
+    case PP_ETIMEDOUT: return "timed out";
+    case PP_ECUDA: return "CUDA runtime error";
+    case PP_EDEVICE: return "device error flag raised";
+    case PP_ENOMEM: return "device allocation failed";
+    case PP_ENODEV: return "no usable CUDA device";
+    default: return "unknown error";
+  }
+}
+
+const char* pp_last_error(const pp_ctx* ctx) {
+  return ctx ? ctx->last_error.c_str() : "null context";
+}
+
+int pp_config_default(pp_config* cfg) {
+  if (!cfg) return PP_EINVAL;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->device = 0;
+  cfg->max_steps = 100000;
+  cfg->seed = 0;
+  cfg->photon_budget_bytes = 0;
+  cfg->world_margin_m = 100.0f;
+  cfg->depth_of_z0_m = 1950.0f;
+  cfg->scatter_coeff_is_effective = 1;
+  cfg->stream = nullptr;
+  return PP_OK;
+}
+
+int pp_create(const pp_config* cfg, pp_ctx** out) {
+  if (!cfg || !out) return PP_EINVAL;
+  *out = nullptr;
+  if (cfg->max_steps == 0 || !(cfg->world_margin_m >= 0.f) || !std::isfinite(cfg->depth_of_z0_m))
+    return PP_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    (void)cudaGetLastError();
+    return PP_ENODEV;
+  }
+  if (cfg->device < 0 || cfg->device >= ndev) return PP_ENODEV;
+  pp_ctx* ctx = new pp_ctx();
+  ctx->cfg = *cfg;
+  cudaError_t e = cudaSetDevice(cfg->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, cfg->device);
+  if (e == cudaSuccess) {
+    if (cfg->stream) {
+      ctx->stream = static_cast<cudaStream_t>(cfg->stream);
+    } else {
+      e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+      ctx->own_stream = (e == cudaSuccess);
+    }
+  }
+  if (e == cudaSuccess && ensure(ctx, ctx->err, sizeof(int)) == PP_OK)
+    e = cudaMemset(ctx->err.p, 0, sizeof(int));
+  if (e != cudaSuccess || !ctx->err.p) {
+    (void)cudaGetLastError();
+    pp_destroy(ctx);
+    return PP_ECUDA;
+  }
+  *out = ctx;
+  return PP_OK;
+}
+
+int pp_destroy(pp_ctx* ctx) {
+  if (!ctx) return PP_OK;
+  cudaSetDevice(ctx->cfg.device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  DevBuf* bufs[] = {&ctx->dom, &ctx->str, &ctx->str_range, &ctx->sdom_z, &ctx->sdom_idx,
+                    &ctx->clear, &ctx->cell_off, &ctx->cell_list, &ctx->layers, &ctx->off,
+                    &ctx->chunk, &ctx->src_event, &ctx->bsum, &ctx->meta, &ctx->work, &ctx->err,
+                    &ctx->s_src, &ctx->s_begin, &ctx->s_ids, &ctx->s_hits, &ctx->s_counts,
+                    &ctx->s_misc1, &ctx->s_misc2, &ctx->s_misc3, &ctx->s_misc4};
+  for (DevBuf* b : bufs) release(*b);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return PP_OK;
+}
+
+int pp_load_geometry(pp_ctx* ctx, const float* xyz, const int32_t* string_id, int32_t n_dom,
+                     float dom_radius) {
+  if (!ctx) return PP_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (n_dom < 0 || n_dom > 65535 || (n_dom > 0 && !xyz) || !(dom_radius > 0.f) ||
+      !std::isfinite(dom_radius))
+    return fail(ctx, PP_EINVAL, "need 0 <= n_dom <= 65535, xyz, dom_radius > 0");
+  for (int64_t i = 0; i < 3 * (int64_t)n_dom; ++i)
+    if (!std::isfinite(xyz[i])) return fail(ctx, PP_EINVAL, "non-finite DOM coordinate");
+  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  const double r = dom_radius;
+  const double M = ctx->cfg.world_margin_m;
+  const double eps = 2e-3;  // slack for FP32 rounding in the culling tests
+
+  // strings: group by id, DOMs by ascending z
+  std::map<int32_t, std::vector<int>> groups;
+  for (int k = 0; k < n_dom; ++k) groups[string_id ? string_id[k] : 0].push_back(k);
+  if ((int)groups.size() > kMaxStrings) return fail(ctx, PP_EINVAL, "more than 4096 strings");
+  std::vector<float4> dom(n_dom), str;
+  std::vector<int2> rng;
+  std::vector<float> sz;
+  std::vector<int> sidx;
+  std::vector<double> scx, scy, srad;
+  double rmax = 0, zmin = 0, zmax = 0;
+  for (int k = 0; k < n_dom; ++k) {
+    dom[k] = make_float4(xyz[3 * k], xyz[3 * k + 1], xyz[3 * k + 2], 0.f);
+    rmax = std::max(rmax, std::hypot((double)xyz[3 * k], (double)xyz[3 * k + 1]));
+    if (k == 0 || xyz[3 * k + 2] < zmin) zmin = xyz[3 * k + 2];
+    if (k == 0 || xyz[3 * k + 2] > zmax) zmax = xyz[3 * k + 2];
+  }
+  for (auto& kv : groups) {
+    std::vector<int>& ks = kv.second;
+    std::sort(ks.begin(), ks.end(), [&](int p, int q) {
+      return xyz[3 * p + 2] < xyz[3 * q + 2] || (xyz[3 * p + 2] == xyz[3 * q + 2] && p < q);
+    });
+    double cx = 0, cy = 0;
+    for (int k : ks) {
+      cx += xyz[3 * k];
+      cy += xyz[3 * k + 1];
+    }
+    cx /= ks.size();
+    cy /= ks.size();
+    double rad = 0;
+    for (int k : ks) rad = std::max(rad, std::hypot(xyz[3 * k] - cx, xyz[3 * k + 1] - cy));
+    rad += r + eps;
+    rng.push_back(make_int2((int)sz.size(), (int)ks.size()));
+    for (int k : ks) {
+      sz.push_back(xyz[3 * k + 2]);
+      sidx.push_back(k);
+    }
+    str.push_back(make_float4((float)cx, (float)cy, (float)rad, 0.f));
+    scx.push_back(cx);
+    scy.push_back(cy);
+    srad.push_back(rad);
+  }
+  const int n_str = (int)str.size();
+  // world cylinder
+  const double R = rmax + M, zlo = (n_dom ? zmin : 0.0) - M, zhi = (n_dom ? zmax : 0.0) + M;
+  // cell grid over [-R, R]^2: clearance (u8, units of 0.25 m) and string lists
+  const int nside = 181;  // nside^2 <= kMaxCells
+  const double cell = std::max(2.0 * R / nside, 1.0);
+  const int nx = std::max(1, (int)std::ceil(2.0 * R / cell));
+  const int ny = nx;
+  const double unit = 0.25, halo = cell;
+  std::vector<uint8_t> clear((size_t)nx * ny);
+  std::vector<uint32_t> coff((size_t)nx * ny + 1, 0);
+  std::vector<uint16_t> clist;
+  for (int iy = 0; iy < ny; ++iy) {
+    for (int ix = 0; ix < nx; ++ix) {
+      const double x0 = -R + ix * cell, x1 = x0 + cell, y0 = -R + iy * cell, y1 = y0 + cell;
+      double cl = 1e30;
+      const size_t c = (size_t)iy * nx + ix;
+      coff[c] = (uint32_t)clist.size();
+      for (int s = 0; s < n_str; ++s) {
+        const double ddx = std::max({x0 - scx[s], 0.0, scx[s] - x1});
+        const double ddy = std::max({y0 - scy[s], 0.0, scy[s] - y1});
+        const double d = std::hypot(ddx, ddy);
+        cl = std::min(cl, d - srad[s]);
+        if (d <= srad[s] + halo + eps) clist.push_back((uint16_t)s);
+      }
+      const double q = std::floor((cl - 0.01) / unit);
+      clear[c] = (uint8_t)std::max(0.0, std::min(255.0, q));
+    }
+  }
+  coff[(size_t)nx * ny] = (uint32_t)clist.size();
+  if (clist.empty()) clist.push_back(0);
+  if (sz.empty()) {
+    sz.push_back(0.f);
+    sidx.push_back(0);
+  }
+  if (str.empty()) {
+    str.push_back(make_float4(0, 0, 0, 0));
+    rng.push_back(make_int2(0, 0));
+  }
+  if (dom.empty()) dom.push_back(make_float4(0, 0, 0, 0));
+  int rc;
+  if ((rc = upload(ctx, ctx->dom, dom))) return rc;
+  if ((rc = upload(ctx, ctx->str, str))) return rc;
+  if ((rc = upload(ctx, ctx->str_range, rng))) return rc;
+  if ((rc = upload(ctx, ctx->sdom_z, sz))) return rc;
+  if ((rc = upload(ctx, ctx->sdom_idx, sidx))) return rc;
+  std::vector<uint8_t> clear_pad(clear);
+  clear_pad.resize((clear.size() + 15) & ~(size_t)15, 0);
+  if ((rc = upload(ctx, ctx->clear, clear_pad))) return rc;
+  if ((rc = upload(ctx, ctx->cell_off, coff))) return rc;
+  if ((rc = upload(ctx, ctx->cell_list, clist))) return rc;
+  GeomDev& G = ctx->geom;
+  G.dom = static_cast<const float4*>(ctx->dom.p);
+  G.str = static_cast<const float4*>(ctx->str.p);
+  G.str_range = static_cast<const int2*>(ctx->str_range.p);
+  G.sdom_z = static_cast<const float*>(ctx->sdom_z.p);
+  G.sdom_idx = static_cast<const int*>(ctx->sdom_idx.p);
+  G.clear = static_cast<const uint8_t*>(ctx->clear.p);
+  G.cell_off = static_cast<const uint32_t*>(ctx->cell_off.p);
+  G.cell_list = static_cast<const uint16_t*>(ctx->cell_list.p);
+  G.n_dom = n_dom;
+  G.n_str = n_dom ? n_str : 0;
+  G.nx = nx;
+  G.ny = ny;
+  G.r = (float)r;
+  G.r2 = (float)(r * r);
+  G.zpad = (float)(r + eps);
+  G.gx0 = (float)(-R);
+  G.gy0 = (float)(-R);
+  G.inv_cell = (float)(1.0 / cell);
+  G.halo = (float)halo;
+  G.clear_unit = (float)unit;
+  G.R = (float)R;
+  G.R2 = (float)(R * R);
+  G.zlo = (float)zlo;
+  G.zhi = (float)zhi;
+  ctx->geom_loaded = true;
+  return PP_OK;
+}
+
+int pp_load_ice(pp_ctx* ctx, const float* b_e, const float* a, int32_t n_layers,
+                float depth_top_m, float dz_m, float g) {
+  if (!ctx) return PP_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (!b_e || !a || n_layers < 1 || n_layers > kMaxLayers || !(dz_m > 0.f) ||
+      !std::isfinite(dz_m) || !std::isfinite(depth_top_m) || !(g > -1.f && g < 1.f))
+    return fail(ctx, PP_EINVAL, "need 1 <= n_layers <= 4096, dz > 0, -1 < g < 1");
+  for (int i = 0; i < n_layers; ++i)
+    if (!(b_e[i] >= 0.f) || !(a[i] >= 0.f) || !std::isfinite(b_e[i]) || !std::isfinite(a[i]))
+      return fail(ctx, PP_EINVAL, "coefficients must be finite and >= 0");
+  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  const double gd = g;
+  std::vector<float4> lay(n_layers);
+  const float inf = INFINITY;
+  for (int i = 0; i < n_layers; ++i) {
+    const double b = ctx->cfg.scatter_coeff_is_effective ? (double)b_e[i] / (1.0 - gd) : (double)b_e[i];
+    const float bf = (float)b, af = a[i];
+    lay[i] = make_float4(bf, af, bf > 0.f ? (float)(1.0 / b) : inf, af > 0.f ? (float)(1.0 / (double)af) : inf);
+  }
+  int rc;
+  if ((rc = upload(ctx, ctx->layers, lay))) return rc;
+  IceDev& I = ctx->ice;
+  I.layer = static_cast<const float4*>(ctx->layers.p);
+  I.L = n_layers;
+  I.z_top = (float)((double)ctx->cfg.depth_of_z0_m - (double)depth_top_m);
+  I.dz = dz_m;
+  I.g = g;
+  I.c1 = (float)(1.0 - gd * gd);
+  I.c2 = (float)(1.0 - gd);
+  I.c3 = (float)(2.0 * gd);
+  I.c4 = (float)(1.0 + gd * gd);
+  I.c5 = gd != 0.0 ? (float)(1.0 / (2.0 * gd)) : 0.f;
+  ctx->ice_loaded = true;
+  return PP_OK;
+}
+
+int pp_propagate(pp_ctx* ctx, uint64_t event_id, const pp_source* src, int64_t n_src,
+                 uint64_t* hits, uint64_t* counts) {
+  if (!ctx) return PP_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (n_src < 0) return fail(ctx, PP_EINVAL, "n_src < 0");
+  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  const int64_t begin[2] = {0, n_src};
+  return batch_host(ctx, true, 1, &event_id, begin, src, hits, counts);
+}
+
+int pp_propagate_batch(pp_ctx* ctx, int32_t n_events, const uint64_t* event_ids,
+                       const int64_t* src_begin, const pp_source* src, uint64_t* hits,
+                       uint64_t* counts) {
+  if (!ctx) return PP_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  return batch_host(ctx, false, n_events, event_ids, src_begin, src, hits, counts);
+}
+
+int pp_propagate_batch_async(pp_ctx* ctx, int32_t n_events, const uint64_t* d_event_ids,
+                             const int64_t* d_src_begin, const pp_source* d_src, int64_t n_src,
+                             uint64_t* d_hits, uint64_t* d_counts, void* stream) {
+  if (!ctx) return PP_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  return batch_async(ctx, n_events, d_event_ids, d_src_begin, d_src, n_src, d_hits, d_counts,
+                     pick_stream(ctx, stream));
+}
+
+int pp_propagate_plain_async(pp_ctx* ctx, int32_t n_events, const uint64_t* h_event_ids,
+                             const int64_t* h_src_begin, const uint64_t* h_event_photons,
+                             const pp_source* d_src, uint64_t* d_hits, uint64_t* d_counts,
+                             void* stream) {
+  if (!ctx) return PP_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  return plain_async(ctx, n_events, h_event_ids, h_src_begin, h_event_photons, d_src, d_hits,
+                     d_counts, pick_stream(ctx, stream));
+}
+
+int pp_sync(pp_ctx* ctx, void* stream) {
+  if (!ctx) return PP_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  return sync_and_check(ctx, pick_stream(ctx, stream));
+}
+
+int pp_set_launch(pp_ctx* ctx, int32_t block_threads, int32_t blocks_per_sm,
+                  int32_t refill_threshold) {
+  if (!ctx) return PP_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (block_threads != 0 && block_threads != 128 && block_threads != 256 && block_threads != 512 &&
+      block_threads != 1024)
+    return fail(ctx, PP_EINVAL, "block_threads must be 128, 256, 512 or 1024");
+  if (blocks_per_sm < 0 || refill_threshold < 0 || refill_threshold > 32)
+    return fail(ctx, PP_EINVAL, "blocks_per_sm >= 0 and 0 <= refill_threshold <= 32");
+  if (block_threads) ctx->block_threads = block_threads;
+  ctx->blocks_per_sm = blocks_per_sm;
+  if (refill_threshold) ctx->refill = refill_threshold;
+  return PP_OK;
+}
+
+int pp_get_launch(const pp_ctx* ctx_c, int32_t* block_threads, int32_t* blocks_per_sm,
+                  int32_t* refill_threshold, int32_t* grid) {
+  pp_ctx* ctx = const_cast<pp_ctx*>(ctx_c);
+  if (!ctx) return PP_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (block_threads) *block_threads = ctx->block_threads;
+  if (blocks_per_sm) *blocks_per_sm = ctx->blocks_per_sm;
+  if (refill_threshold) *refill_threshold = ctx->refill;
+  if (grid) {
+    *grid = 0;
+    if (ctx->geom_loaded && ctx->ice_loaded) {
+      PP_CUDA(cudaSetDevice(ctx->cfg.device));
+      size_t smem;
+      int rc = prepare_smem(ctx, &smem);
+      if (!rc) rc = grid_blocks(ctx, smem, grid);
+      if (rc) return rc;
+    }
+  }
+  return PP_OK;
+}
+
+int pp_get_world(const pp_ctx* ctx, float* out3) {
+  if (!ctx || !out3) return PP_EINVAL;
+  if (!ctx->geom_loaded) return PP_ENOTLOADED;
+  out3[0] = ctx->geom.R;
+  out3[1] = ctx->geom.zlo;
+  out3[2] = ctx->geom.zhi;
+  return PP_OK;
+}
+
+int pp_debug_philox(pp_ctx* ctx, const uint32_t* ctr, const uint32_t* key, uint32_t* out,
+                    int64_t n) {
+  if (!ctx) return PP_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (n < 0 || (n > 0 && (!ctr || !key || !out))) return fail(ctx, PP_EINVAL, "bad arguments");
+  if (n == 0) return PP_OK;
+  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  int rc;
+  if ((rc = ensure(ctx, ctx->s_misc1, 16 * (size_t)n))) return rc;
+  if ((rc = ensure(ctx, ctx->s_misc2, 8 * (size_t)n))) return rc;
+  if ((rc = ensure(ctx, ctx->s_misc3, 16 * (size_t)n))) return rc;
+  cudaStream_t st = ctx->stream;
+  PP_CUDA(cudaMemcpyAsync(ctx->s_misc1.p, ctr, 16 * n, cudaMemcpyHostToDevice, st));
+  PP_CUDA(cudaMemcpyAsync(ctx->s_misc2.p, key, 8 * n, cudaMemcpyHostToDevice, st));
+  PP_CUDA(launch_philox(static_cast<uint32_t*>(ctx->s_misc1.p), static_cast<uint32_t*>(ctx->s_misc2.p),
+                        static_cast<uint32_t*>(ctx->s_misc3.p), n, st));
+  PP_CUDA(cudaMemcpyAsync(out, ctx->s_misc3.p, 16 * n, cudaMemcpyDeviceToHost, st));
+  PP_CUDA(cudaStreamSynchronize(st));
+  return PP_OK;
+}
+
+int pp_debug_trace(pp_ctx* ctx, uint64_t event_id, const pp_source* src, int64_t n_src,
+                   const uint64_t* photon_ids, int64_t n, int32_t n_trace, int32_t* outcome,
+                   int64_t* n_steps, float* birth, float* trace) {
+  if (!ctx) return PP_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  int rc;
+  if ((rc = check_loaded(ctx))) return rc;
+  if (n_src < 1 || n < 0 || n_trace < 0 || !src || (n > 0 && (!photon_ids || !outcome || !n_steps)) ||
+      (n_trace > 0 && !trace) || n_src > kMaxSources)
+    return fail(ctx, PP_EINVAL, "bad arguments");
+  if ((rc = check_sources(ctx, src, n_src))) return rc;
+  if (n == 0) return PP_OK;
+  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  cudaStream_t st = ctx->stream;
+  if ((rc = ensure(ctx, ctx->s_src, sizeof(pp_source) * n_src))) return rc;
+  if ((rc = ensure(ctx, ctx->s_misc1, 8 * (size_t)n))) return rc;
+  if ((rc = ensure(ctx, ctx->s_misc2, 4 * (size_t)n + 8 * (size_t)n))) return rc;
+  if ((rc = ensure(ctx, ctx->s_misc3, 24 * (size_t)n))) return rc;
+  if ((rc = ensure(ctx, ctx->s_misc4, 12 * (size_t)n * std::max(n_trace, 1)))) return rc;
+  if ((rc = ensure_scratch(ctx, n_src, false))) return rc;
+  size_t smem;
+  if ((rc = prepare_smem(ctx, &smem))) return rc;
+  PP_CUDA(cudaMemcpyAsync(ctx->s_src.p, src, sizeof(pp_source) * n_src, cudaMemcpyHostToDevice, st));
+  PP_CUDA(cudaMemcpyAsync(ctx->s_misc1.p, photon_ids, 8 * n, cudaMemcpyHostToDevice, st));
+  const pp_source* d_src = static_cast<const pp_source*>(ctx->s_src.p);
+  PP_CUDA(launch_expand(d_src, n_src, nullptr, 1, expand_bufs(ctx, false), st));
+  const WorkDev w = work_desc(ctx, d_src, n_src, false, nullptr, nullptr, nullptr, nullptr,
+                              (uint32_t)event_id);
+  int* d_out = static_cast<int*>(ctx->s_misc2.p);
+  int64_t* d_ns = reinterpret_cast<int64_t*>(static_cast<char*>(ctx->s_misc2.p) + ((4 * n + 7) & ~7));
+  float* d_birth = static_cast<float*>(ctx->s_misc3.p);
+  float* d_tr = n_trace > 0 ? static_cast<float*>(ctx->s_misc4.p) : nullptr;
+  PP_CUDA(launch_trace(ctx->ice, ctx->geom, w, run_params(ctx), static_cast<uint64_t*>(ctx->s_misc1.p),
+                       n, n_trace, d_out, d_ns, d_birth, d_tr, smem, st));
+  PP_CUDA(cudaMemcpyAsync(outcome, d_out, 4 * n, cudaMemcpyDeviceToHost, st));
+  PP_CUDA(cudaMemcpyAsync(n_steps, d_ns, 8 * n, cudaMemcpyDeviceToHost, st));
+  if (birth) PP_CUDA(cudaMemcpyAsync(birth, d_birth, 24 * n, cudaMemcpyDeviceToHost, st));
+  if (n_trace > 0)
+    PP_CUDA(cudaMemcpyAsync(trace, d_tr, 12 * (size_t)n * n_trace, cudaMemcpyDeviceToHost, st));
+  PP_CUDA(cudaStreamSynchronize(st));
+  return PP_OK;
+}
+
+int pp_debug_first_hit(pp_ctx* ctx, const float* seg, int64_t n, int32_t mode, int32_t* dom,
+                       float* t) {
+  if (!ctx) return PP_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  int rc;
+  if ((rc = check_loaded(ctx))) return rc;
+  if (n < 0 || (n > 0 && (!seg || !dom || !t)) || (mode != 0 && mode != 1))
+    return fail(ctx, PP_EINVAL, "bad arguments");
+  if (n == 0) return PP_OK;
+  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  cudaStream_t st = ctx->stream;
+  if ((rc = ensure(ctx, ctx->s_misc1, 28 * (size_t)n))) return rc;
+  if ((rc = ensure(ctx, ctx->s_misc2, 4 * (size_t)n))) return rc;
+  if ((rc = ensure(ctx, ctx->s_misc3, 4 * (size_t)n))) return rc;
+  size_t smem;
+  if ((rc = prepare_smem(ctx, &smem))) return rc;
+  PP_CUDA(cudaMemcpyAsync(ctx->s_misc1.p, seg, 28 * n, cudaMemcpyHostToDevice, st));
+  PP_CUDA(launch_first_hit(ctx->geom, ctx->ice, static_cast<float*>(ctx->s_misc1.p), n, mode,
+                           static_cast<int*>(ctx->s_misc2.p), static_cast<float*>(ctx->s_misc3.p),
+                           smem, st));
+  PP_CUDA(cudaMemcpyAsync(dom, ctx->s_misc2.p, 4 * n, cudaMemcpyDeviceToHost, st));
+  PP_CUDA(cudaMemcpyAsync(t, ctx->s_misc3.p, 4 * n, cudaMemcpyDeviceToHost, st));
+  PP_CUDA(cudaStreamSynchronize(st));
+  return PP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,414 @@
+// Device code of one photon's life: birth, steps through layered ice, DOM hit
+// test, world escape, scattering.  Everything here runs in FP32 (random words
+// in uint32) and is shared by every kernel that moves photons, so that the
+// plain, persistent and trace kernels follow identical trajectories.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pp_internal.h"
+
+namespace ppk {
+
+#define PP_INF (__int_as_float(0x7f800000))
+
+// ---------------------------------------------------------------- Philox --
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 products
+// on counter words 0 and 2, the high halves xor-ed into the other words with
+// the key, the key bumped by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k.x += 0x9E3779B9u;
+      k.y += 0xBB67AE85u;
+    }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+// uint32 -> (0, 1): top 24 bits with the lowest forced to 1, times 2^-24
+// (exact in FP32).
+__device__ __forceinline__ float u01f(uint32_t x) {
+  return __uint2float_rn((x >> 8) | 1u) * 5.9604644775390625e-08f;
+}
+
+// --------------------------------------------------------- shared tables --
+struct Tables {
+  const float4* layer;   // [L]
+  const float4* str;     // [n_str]
+  const int2* range;     // [n_str]
+  const uint8_t* clear;  // [nx*ny]
+};
+
+__device__ __forceinline__ Tables stage_tables(unsigned char* smem, const IceDev& I,
+                                               const GeomDev& G) {
+  float4* lay = reinterpret_cast<float4*>(smem);
+  float4* str = lay + I.L;
+  int2* rng = reinterpret_cast<int2*>(str + G.n_str);
+  uint8_t* clr = reinterpret_cast<uint8_t*>(rng + G.n_str);
+  for (int i = threadIdx.x; i < I.L; i += blockDim.x) lay[i] = I.layer[i];
+  for (int i = threadIdx.x; i < G.n_str; i += blockDim.x) {
+    str[i] = G.str[i];
+    rng[i] = G.str_range[i];
+  }
+  const int ncell = G.nx * G.ny;
+  const int nvec = ncell >> 4;
+  const uint4* csrc = reinterpret_cast<const uint4*>(G.clear);
+  uint4* cdst = reinterpret_cast<uint4*>(clr);
+  if ((reinterpret_cast<uintptr_t>(clr) & 15) == 0) {
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x) cdst[i] = csrc[i];
+    for (int i = (nvec << 4) + threadIdx.x; i < ncell; i += blockDim.x) clr[i] = G.clear[i];
+  } else {
+    for (int i = threadIdx.x; i < ncell; i += blockDim.x) clr[i] = G.clear[i];
+  }
+  return Tables{lay, str, rng, clr};
+}
+
+// ------------------------------------------------------------ geometry --
+// Layer of a point at height z moving with vertical component w (same rule as
+// the ice description: a point on a boundary belongs to the layer it moves
+// into; depths outside the table take the edge layer).
+__device__ __forceinline__ int layer_at(const IceDev& I, float z, float w) {
+  const float f = (I.z_top - z) / I.dz;
+  if (!(f >= 0.0f)) return 0;
+  if (f >= (float)I.L) return I.L - 1;
+  const float fl = floorf(f);
+  int i = (int)fl;
+  if (w > 0.0f && f == fl) i -= 1;
+  return max(0, min(I.L - 1, i));
+}
+
+// Paper Sec. 2: ice in layers of given scattering and absorption; the
+// distance to the next scatter is a Monte Carlo draw.  The step consumes tau_s
+// with the local scattering coefficient and the photon's remaining tau_a with
+// the local absorption coefficient, crossing layer boundaries as it goes; it
+// ends at the scatter point or the absorption point (tie: absorption).
+__device__ __forceinline__ float walk(const float4* __restrict__ lay, const IceDev& I, float z,
+                                      float w, int& layer, float tau_s, float& tau_a,
+                                      bool& absorb) {
+  const float inv_w = 1.0f / w;
+  float zc = z;
+  float S = 0.0f;
+  for (;;) {
+    const float4 L = lay[layer];
+    float ell = PP_INF;
+    if (w < 0.0f) {
+      if (layer < I.L - 1) ell = (fmaf(-(float)(layer + 1), I.dz, I.z_top) - zc) * inv_w;
+    } else if (w > 0.0f) {
+      if (layer > 0) ell = (fmaf(-(float)layer, I.dz, I.z_top) - zc) * inv_w;
+    }
+    ell = fmaxf(ell, 0.0f);
+    const float ds = (L.x > 0.0f) ? tau_s * L.z : PP_INF;
+    const float da = (L.y > 0.0f) ? tau_a * L.w : PP_INF;
+    if (da <= ds && da <= ell) {
+      absorb = true;
+      tau_a = 0.0f;
+      return S + da;
+    }
+    if (ds <= ell) {
+      absorb = false;
+      tau_a = fmaxf(0.0f, fmaf(-L.y, ds, tau_a));
+      return S + ds;
+    }
+    S += ell;
+    tau_s = fmaxf(0.0f, fmaf(-L.x, ell, tau_s));
+    tau_a = fmaxf(0.0f, fmaf(-L.y, ell, tau_a));
+    if (w < 0.0f) {
+      zc = fmaf(-(float)(layer + 1), I.dz, I.z_top);
+      layer += 1;
+    } else {
+      zc = fmaf(-(float)layer, I.dz, I.z_top);
+      layer -= 1;
+    }
+  }
+}
+
+// Distance to the exit of the world cylinder along d; 0 when already outside.
+__device__ __forceinline__ float world_exit(const GeomDev& G, float px, float py, float pz,
+                                            float dx, float dy, float dz) {
+  const float c = fmaf(px, px, fmaf(py, py, -G.R2));
+  if (c > 0.0f || pz < G.zlo || pz > G.zhi) return 0.0f;
+  float tz = PP_INF;
+  if (dz > 0.0f) tz = (G.zhi - pz) / dz;
+  else if (dz < 0.0f) tz = (G.zlo - pz) / dz;
+  float tr = PP_INF;
+  const float a = fmaf(dx, dx, dy * dy);
+  if (a > 0.0f) {
+    const float b = fmaf(px, dx, py * dy);
+    const float sq = sqrtf(fmaxf(0.0f, fmaf(b, b, -a * c)));
+    tr = (b > 0.0f) ? (-c) / (b + sq) : (sq - b) / a;
+  }
+  return fminf(tz, tr);
+}
+
+// Sphere of radius r about c met on [p, p + S d]: entry distance, 0 when the
+// start is inside.  Uses r^2 - |m - (m.d) d|^2 for the discriminant (the
+// same quantity as (m.d)^2 - |m|^2 + r^2, with less cancellation).
+__device__ __forceinline__ bool sphere_hit(float4 c, float r2, float px, float py, float pz,
+                                           float dx, float dy, float dz, float S, float& t) {
+  const float mx = px - c.x, my = py - c.y, mz = pz - c.z;
+  const float beta = fmaf(mx, dx, fmaf(my, dy, mz * dz));
+  const float gamma = fmaf(mx, mx, fmaf(my, my, fmaf(mz, mz, -r2)));
+  if (gamma <= 0.0f) {
+    t = 0.0f;
+    return true;
+  }
+  if (beta >= 0.0f) return false;
+  const float hx = fmaf(-beta, dx, mx), hy = fmaf(-beta, dy, my), hz = fmaf(-beta, dz, mz);
+  const float disc = r2 - fmaf(hx, hx, fmaf(hy, hy, hz * hz));
+  if (disc < 0.0f) return false;
+  const float tt = -beta - sqrtf(disc);
+  if (tt < 0.0f || tt > S) return false;
+  t = tt;
+  return true;
+}
+
+__device__ __forceinline__ void consider_dom(const GeomDev& G, int k, float px, float py,
+                                             float pz, float dx, float dy, float dz, float S,
+                                             int& best, float& bt) {
+  float t;
+  if (sphere_hit(__ldg(G.dom + k), G.r2, px, py, pz, dx, dy, dz, S, t)) {
+    if (t < bt || (t == bt && k < best)) {
+      bt = t;
+      best = k;
+    }
+  }
+}
+
+// Candidate DOMs of one string: the part of the segment inside the string's
+// bounding cylinder gives a z window; the string's DOMs in that window (by
+// binary search on their sorted z) get the exact sphere test.
+__device__ __forceinline__ void test_string(const GeomDev& G, const Tables& T, int s, float px,
+                                            float py, float pz, float dx, float dy, float dz,
+                                            float S, float dxy2, int& best, float& bt) {
+  const float4 st = T.str[s];
+  const float ox = px - st.x, oy = py - st.y;
+  float t0 = 0.0f, t1 = S;
+  const float c2 = fmaf(ox, ox, fmaf(oy, oy, -st.z * st.z));
+  if (dxy2 > 1e-12f) {
+    const float b2 = fmaf(ox, dx, oy * dy);
+    const float disc = fmaf(b2, b2, -dxy2 * c2);
+    if (disc < 0.0f) return;
+    const float sq = sqrtf(disc);
+    const float inv = 1.0f / dxy2;
+    t0 = fmaxf(0.0f, (-b2 - sq) * inv);
+    t1 = fminf(S, (-b2 + sq) * inv);
+    if (t0 > t1) return;
+  } else if (c2 > 0.0f) {
+    return;
+  }
+  const float za = fmaf(t0, dz, pz), zb = fmaf(t1, dz, pz);
+  const float zl = fminf(za, zb) - G.zpad, zh = fmaxf(za, zb) + G.zpad;
+  const int2 rg = T.range[s];
+  int lo = rg.x, hi = rg.x + rg.y;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(G.sdom_z + mid) < zl) lo = mid + 1;
+    else hi = mid;
+  }
+  const int end = rg.x + rg.y;
+  for (int q = lo; q < end; ++q) {
+    if (__ldg(G.sdom_z + q) > zh) break;
+    consider_dom(G, __ldg(G.sdom_idx + q), px, py, pz, dx, dy, dz, S, best, bt);
+  }
+}
+
+// First DOM met on [p, p + S d] (smallest t, ties to the lowest index).
+// Fast path: a step shorter (horizontally) than its cell's clearance cannot
+// reach any string.  Otherwise the cell's string list (steps up to `halo`
+// long) or every string is searched.
+__device__ __forceinline__ int first_hit_grid(const GeomDev& G, const Tables& T, float px,
+                                              float py, float pz, float dx, float dy, float dz,
+                                              float S, float& t_out) {
+  t_out = PP_INF;
+  if (G.n_dom == 0) return -1;
+  const float dxy2 = fmaf(dx, dx, dy * dy);
+  const float Lxy = S * sqrtf(dxy2);
+  const int ix = min(max(__float2int_rd((px - G.gx0) * G.inv_cell), 0), G.nx - 1);
+  const int iy = min(max(__float2int_rd((py - G.gy0) * G.inv_cell), 0), G.ny - 1);
+  const int cell = iy * G.nx + ix;
+  if (Lxy < (float)T.clear[cell] * G.clear_unit) return -1;
+  int best = -1;
+  float bt = PP_INF;
+  if (Lxy <= G.halo) {
+    const uint32_t b = __ldg(G.cell_off + cell), e = __ldg(G.cell_off + cell + 1);
+    for (uint32_t j = b; j < e; ++j)
+      test_string(G, T, (int)__ldg(G.cell_list + j), px, py, pz, dx, dy, dz, S, dxy2, best, bt);
+  } else {
+    for (int s = 0; s < G.n_str; ++s)
+      test_string(G, T, s, px, py, pz, dx, dy, dz, S, dxy2, best, bt);
+  }
+  t_out = bt;
+  return best;
+}
+
+__device__ __forceinline__ int first_hit_brute(const GeomDev& G, float px, float py, float pz,
+                                               float dx, float dy, float dz, float S,
+                                               float& t_out) {
+  int best = -1;
+  float bt = PP_INF;
+  for (int k = 0; k < G.n_dom; ++k) consider_dom(G, k, px, py, pz, dx, dy, dz, S, best, bt);
+  t_out = bt;
+  return best;
+}
+
+// ---------------------------------------------------------- scattering --
+// Henyey-Greenstein cosine by inversion of its cumulative distribution.
+__device__ __forceinline__ float hg_mu(const IceDev& I, float u) {
+  if (I.g == 0.0f) return fmaf(2.0f, u, -1.0f);
+  const float t = I.c1 / fmaf(I.c3, u, I.c2);
+  const float mu = fmaf(-t, t, I.c4) * I.c5;
+  return fminf(1.0f, fmaxf(-1.0f, mu));
+}
+
+// New direction at polar cosine mu, azimuth 2 pi u_phi about (dx, dy, dz):
+// the MCML rotation (Wang, Jacques & Zheng 1995), lab frame near the poles,
+// renormalised.
+__device__ __forceinline__ void rotate(float& dx, float& dy, float& dz, float mu, float u_phi) {
+  const float st = sqrtf(fmaxf(0.0f, (1.0f - mu) * (1.0f + mu)));
+  float sp, cp;
+  sincospif(2.0f * u_phi, &sp, &cp);
+  float ox, oy, oz;
+  if (fabsf(dz) > 0.99999f) {
+    ox = st * cp;
+    oy = st * sp;
+    oz = (dz >= 0.0f) ? mu : -mu;
+  } else {
+    const float tmp = sqrtf((1.0f - dz) * (1.0f + dz));
+    const float it = 1.0f / tmp;
+    ox = fmaf(st * fmaf(dx * dz, cp, -dy * sp), it, dx * mu);
+    oy = fmaf(st * fmaf(dy * dz, cp, dx * sp), it, dy * mu);
+    oz = fmaf(-st * cp, tmp, dz * mu);
+  }
+  const float inv = rsqrtf(fmaf(ox, ox, fmaf(oy, oy, oz * oz)));
+  dx = ox * inv;
+  dy = oy * inv;
+  dz = oz * inv;
+}
+
+// ------------------------------------------------------------- photon --
+struct Photon {
+  float px, py, pz, dx, dy, dz, tau_a;
+  int layer;
+  uint32_t n;          // steps taken
+  uint32_t pid_lo, pid_hi, ev_lo;
+  int ev;              // event slot for the tallies
+};
+
+// a2: birth from Philox block 0 -- point on the emitting segment, direction
+// (isotropic, or on the Cherenkov cone about the segment), and the absorption
+// optical depth the photon carries.  Returns false for a malformed source.
+__device__ __forceinline__ bool birth(Photon& ph, const pp_source& s, const IceDev& I,
+                                      const RunDev& R) {
+  const uint4 x = philox4x32_10(make_uint4(ph.pid_lo, ph.pid_hi, 0u, 0u),
+                                make_uint2(R.seed_lo, ph.ev_lo));
+  float sdx = s.dx, sdy = s.dy, sdz = s.dz;
+  const float nn = fmaf(sdx, sdx, fmaf(sdy, sdy, sdz * sdz));
+  if (nn > 0.0f) {
+    const float inv = rsqrtf(nn);
+    sdx *= inv;
+    sdy *= inv;
+    sdz *= inv;
+  }
+  const float t0 = u01f(x.x) * s.length;
+  ph.px = fmaf(t0, sdx, s.x);
+  ph.py = fmaf(t0, sdy, s.y);
+  ph.pz = fmaf(t0, sdz, s.z);
+  if (s.type == PP_SRC_CHERENKOV) {
+    ph.dx = sdx;
+    ph.dy = sdy;
+    ph.dz = sdz;
+    rotate(ph.dx, ph.dy, ph.dz, R.cos_cherenkov, u01f(x.z));
+  } else {
+    const float mu = fmaf(2.0f, u01f(x.y), -1.0f);
+    const float st = sqrtf(fmaxf(0.0f, (1.0f - mu) * (1.0f + mu)));
+    float sp, cp;
+    sincospif(2.0f * u01f(x.z), &sp, &cp);
+    ph.dx = st * cp;
+    ph.dy = st * sp;
+    ph.dz = mu;
+  }
+  ph.tau_a = -logf(u01f(x.w));
+  ph.n = 0;
+  const bool ok = s.type <= PP_SRC_CASCADE && isfinite(ph.px) && isfinite(ph.py) &&
+                  isfinite(ph.pz) && nn > 0.0f && s.length >= 0.0f;
+  ph.layer = ok ? layer_at(I, ph.pz, ph.dz) : 0;
+  return ok;
+}
+
+// a3..a7: one step.  Returns kContinue after a scatter, else the outcome.
+__device__ __forceinline__ int photon_step(Photon& ph, const IceDev& I, const GeomDev& G,
+                                           const Tables& T, const RunDev& R) {
+  ph.n += 1;
+  const uint4 x = philox4x32_10(make_uint4(ph.pid_lo, ph.pid_hi, ph.n, 0u),
+                                make_uint2(R.seed_lo, ph.ev_lo));
+  const float tau_s = -logf(u01f(x.x));
+  int layer = ph.layer;
+  float tau_a = ph.tau_a;
+  bool absorb;
+  const float S = walk(T.layer, I, ph.pz, ph.dz, layer, tau_s, tau_a, absorb);
+  const float tw = world_exit(G, ph.px, ph.py, ph.pz, ph.dx, ph.dy, ph.dz);
+  const float St = fminf(S, tw);
+  float th;
+  const int k = first_hit_grid(G, T, ph.px, ph.py, ph.pz, ph.dx, ph.dy, ph.dz, St, th);
+  if (k >= 0 && th < tw) return k;
+  if (tw <= S) return kEscaped;
+  if (absorb) return kAbsorbed;
+  ph.px = fmaf(S, ph.dx, ph.px);
+  ph.py = fmaf(S, ph.dy, ph.py);
+  ph.pz = fmaf(S, ph.dz, ph.pz);
+  rotate(ph.dx, ph.dy, ph.dz, hg_mu(I, u01f(x.y)), u01f(x.z));
+  ph.layer = layer;
+  ph.tau_a = tau_a;
+  if (ph.n >= R.max_steps) return kTruncated;
+  return kContinue;
+}
+
+// Finds the source and event of batch photon index g and fills the photon's
+// identity.  Returns the source index.
+__device__ __forceinline__ int locate(const WorkDev& W, uint32_t chunk_log2, uint64_t g,
+                                      Photon& ph) {
+  const uint64_t c = g >> chunk_log2;
+  int lo = (int)__ldg(W.chunk_src + c), hi = (int)__ldg(W.chunk_src + c + 1);
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(W.off + mid) <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  uint64_t pid = g;
+  if (W.src_event) {
+    const int e = (int)__ldg(W.src_event + lo);
+    pid = g - __ldg(W.off + __ldg(W.src_begin + e));
+    ph.ev = e;
+    ph.ev_lo = (uint32_t)__ldg(W.event_ids + e);
+  } else {
+    ph.ev = 0;
+    ph.ev_lo = W.single_event_lo;
+  }
+  ph.pid_lo = (uint32_t)pid;
+  ph.pid_hi = (uint32_t)(pid >> 32);
+  return lo;
+}
+
+// a6: integer tallies.
+__device__ __forceinline__ void tally(const WorkDev& W, int n_dom, const Photon& ph, int out) {
+  unsigned long long* cnt = W.counts + (size_t)ph.ev * 4;
+  if (out >= 0) {
+    atomicAdd(W.hits + (size_t)ph.ev * n_dom + out, 1ull);
+  } else if (out == kEscaped) {
+    atomicAdd(cnt + 1, 1ull);
+  } else {
+    atomicAdd(cnt + 0, 1ull);
+    if (out == kTruncated) atomicAdd(cnt + 2, 1ull);
+  }
+  atomicAdd(cnt + 3, (unsigned long long)ph.n);
+}
+
+}  // namespace ppk

@@ -1,0 +1,130 @@
+// Internal interface between the C ABI (pp_capi.cu) and the kernels
+// (pp_kernels.cu).  Not installed, not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pp.h"
+
+namespace ppk {
+
+constexpr int kMaxLayers = 4096;
+constexpr int kMaxStrings = 4096;
+constexpr int kMaxCells = 32768;         // u8 clearance grid staged in shared memory
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;            // sources per scan thread
+constexpr int kScanTile = kScanThreads * kScanItems;
+constexpr int kTopThreads = 1024;
+constexpr int kTopItems = 16;
+constexpr int64_t kMaxSources = (int64_t)kScanTile * kTopThreads * kTopItems;  // 33.5 M
+constexpr int kSmallThreads = 1024;      // fused single-block expansion
+constexpr int kSmallItems = 8;
+constexpr int64_t kSmallMax = (int64_t)kSmallThreads * kSmallItems;
+
+// Per-step outcome of a photon (>= 0: the DOM it hit).
+constexpr int kContinue = -100;
+constexpr int kAbsorbed = PP_OUT_ABSORBED;
+constexpr int kEscaped = PP_OUT_ESCAPED;
+constexpr int kTruncated = PP_OUT_TRUNCATED;
+
+// Error flag bits (latched in device memory, read by pp_sync).
+constexpr int kErrBadSource = 1;
+constexpr int kErrBadIndex = 2;
+
+// Ice table as the kernels read it: per layer (b, a, 1/b, 1/a) with b the
+// geometric scattering coefficient; 1/x is +inf where x is 0.
+struct IceDev {
+  const float4* layer;
+  int L;
+  float z_top;   // z of the top of layer 0
+  float dz;
+  float g;
+  float c1, c2, c3, c4, c5;   // HG: 1-g^2, 1-g, 2g, 1+g^2, 1/(2g)
+};
+
+// Detector tables.  DOMs are grouped by string; each string is bounded by a
+// vertical cylinder (cx, cy, radius incl. DOM radius and a margin); the DOMs
+// of a string are listed by ascending z.  A 2-D cell grid holds for each cell
+// a lower bound of the horizontal distance from any point of the cell to any
+// string cylinder ("clearance", in units of clear_unit) and the strings
+// within `halo` of the cell.
+struct GeomDev {
+  const float4* dom;        // [n_dom] (x, y, z, 0)
+  const float4* str;        // [n_str] (cx, cy, radius, 0)
+  const int2* str_range;    // [n_str] (first, count) into sdom_*
+  const float* sdom_z;      // [n_dom] z, per string ascending
+  const int* sdom_idx;      // [n_dom] DOM index, same order
+  const uint8_t* clear;     // [ny][nx]
+  const uint32_t* cell_off; // [nx*ny + 1] into cell_list
+  const uint16_t* cell_list;
+  int n_dom, n_str, nx, ny;
+  float r, r2, zpad;        // DOM radius, r^2, z window padding
+  float gx0, gy0, inv_cell, halo, clear_unit;
+  float R, R2, zlo, zhi;    // world cylinder
+};
+
+// One propagation launch's work description.
+struct WorkDev {
+  const pp_source* src;       // batch sources
+  const uint64_t* off;        // [n_src + 1] photon prefix over the batch
+  const uint32_t* chunk_src;  // [n_src + 2] first source of each photon chunk
+  const uint32_t* src_event;  // [n_src] event slot of each source (NULL: single event)
+  const int64_t* src_begin;   // [n_events + 1] (batch mode)
+  const uint64_t* event_ids;  // [n_events]     (batch mode)
+  const uint64_t* meta;       // [0] total photons, [1] chunk log2
+  unsigned long long* work;   // persistent work counter (zeroed before launch)
+  unsigned long long* hits;   // [n_events][n_dom]
+  unsigned long long* counts; // [n_events][4]
+  int* err;
+  int n_src;
+  uint32_t single_event_lo;   // event id (low word) in single-event mode
+};
+
+struct RunDev {
+  uint32_t seed_lo;
+  uint32_t max_steps;
+  float cos_cherenkov;
+  int refill;                 // persistent: refill once this many lanes are idle
+};
+
+// Shared-memory footprint of the tables the propagation kernels stage.
+size_t tables_smem_bytes(const IceDev& ice, const GeomDev& geom);
+
+// Scratch needed by the expansion for n_src sources.
+struct ExpandBufs {
+  uint64_t* off;          // n_src + 1
+  uint32_t* chunk_src;    // n_src + 2
+  uint32_t* src_event;    // n_src (NULL in single-event mode)
+  uint64_t* bsum;         // ceil(n_src / kScanTile)
+  uint64_t* meta;         // 2
+};
+
+// a1: exclusive prefix of n_photons over the sources, photon-chunk table and
+// source -> event map.  src_begin/n_events may be NULL/0 (single event).
+cudaError_t launch_expand(const pp_source* src, int64_t n_src, const int64_t* src_begin,
+                          int n_events, const ExpandBufs& b, cudaStream_t st);
+
+// a2..a8 for the photons of the work description.
+//   persistent = false: one thread per photon, `n_photons_host` photons
+//   persistent = true : grid_blocks persistent blocks with warp refill
+cudaError_t launch_propagate(bool persistent, const IceDev& ice, const GeomDev& geom,
+                             const WorkDev& work, const RunDev& run, int block_threads,
+                             int grid_blocks, uint64_t n_photons_host, size_t smem,
+                             cudaStream_t st);
+
+cudaError_t set_propagate_smem_limit(size_t smem);
+cudaError_t propagate_occupancy(int block_threads, size_t smem, int* blocks_per_sm);
+
+cudaError_t launch_trace(const IceDev& ice, const GeomDev& geom, const WorkDev& work,
+                         const RunDev& run, const uint64_t* ids, int64_t n, int n_trace,
+                         int* outcome, int64_t* n_steps, float* birth, float* trace,
+                         size_t smem, cudaStream_t st);
+
+cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n,
+                          cudaStream_t st);
+
+cudaError_t launch_first_hit(const GeomDev& geom, const IceDev& ice, const float* seg, int64_t n,
+                             int mode, int* dom, float* t, size_t smem, cudaStream_t st);
+
+}  // namespace ppk

@@ -1,0 +1,316 @@
+"""Python binding of the C ABI in ``include/pp.h`` (ctypes, marshalling only).
+
+Every ``pp_*`` function here has the name and argument order of the C entry
+point it calls; numpy arrays are passed as host pointers and torch CUDA
+tensors (or raw integers) as device pointers.  All arithmetic runs in the
+CUDA library ``libpp.so``; if that library is missing this module raises on
+import -- there is no CPU fallback.
+
+``Propagator`` wraps a context with the same calls on numpy / torch inputs.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import workloads
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpp.so")
+
+PP_OK, PP_EINVAL, PP_ENOTLOADED, PP_EBUDGET = 0, -1, -2, -3
+PP_ETIMEDOUT, PP_ECUDA, PP_EDEVICE, PP_ENOMEM, PP_ENODEV = -4, -5, -6, -7, -8
+PP_OUT_ABSORBED, PP_OUT_ESCAPED, PP_OUT_TRUNCATED = -1, -2, -3
+
+
+class pp_config(C.Structure):
+    _fields_ = [
+        ("device", C.c_int32), ("max_steps", C.c_uint32), ("seed", C.c_uint64),
+        ("photon_budget_bytes", C.c_uint64), ("world_margin_m", C.c_float),
+        ("depth_of_z0_m", C.c_float), ("scatter_coeff_is_effective", C.c_int32),
+        ("reserved", C.c_int32), ("stream", C.c_void_p),
+    ]
+
+
+class pp_source(C.Structure):
+    _fields_ = [
+        ("x", C.c_float), ("y", C.c_float), ("z", C.c_float),
+        ("dx", C.c_float), ("dy", C.c_float), ("dz", C.c_float),
+        ("length", C.c_float), ("type", C.c_uint32), ("n_photons", C.c_uint64),
+    ]
+
+
+assert C.sizeof(pp_source) == workloads.SOURCE_DTYPE.itemsize == 40
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with "
+                      "`python -m paper_2405_05700_b300.build` (needs nvcc)")
+
+_lib = C.CDLL(LIB_PATH)
+
+_vp, _i32, _i64, _u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
+_SIGS = {
+    "pp_config_default": [_vp],
+    "pp_create": [_vp, _vp],
+    "pp_destroy": [_vp],
+    "pp_load_geometry": [_vp, _vp, _vp, _i32, C.c_float],
+    "pp_load_ice": [_vp, _vp, _vp, _i32, C.c_float, C.c_float, C.c_float],
+    "pp_propagate": [_vp, _u64, _vp, _i64, _vp, _vp],
+    "pp_propagate_batch": [_vp, _i32, _vp, _vp, _vp, _vp, _vp],
+    "pp_propagate_batch_async": [_vp, _i32, _vp, _vp, _vp, _i64, _vp, _vp, _vp],
+    "pp_propagate_plain_async": [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "pp_sync": [_vp, _vp],
+    "pp_set_launch": [_vp, _i32, _i32, _i32],
+    "pp_get_launch": [_vp, _vp, _vp, _vp, _vp],
+    "pp_get_world": [_vp, _vp],
+    "pp_debug_philox": [_vp, _vp, _vp, _vp, _i64],
+    "pp_debug_trace": [_vp, _u64, _vp, _i64, _vp, _i64, _i32, _vp, _vp, _vp, _vp],
+    "pp_debug_first_hit": [_vp, _vp, _i64, _i32, _vp, _vp],
+}
+EXPORTS = tuple(_SIGS) + ("pp_last_error", "pp_strerror")
+
+for _name, _args in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = C.c_int
+_lib.pp_last_error.argtypes = [_vp]
+_lib.pp_last_error.restype = C.c_char_p
+_lib.pp_strerror.argtypes = [C.c_int]
+_lib.pp_strerror.restype = C.c_char_p
+
+
+class PPError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+def _ptr(x):
+    """Host numpy array -> pointer; torch tensor -> its data pointer;
+    int -> itself; None -> NULL."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+# ---- the C entry points, same names --------------------------------------
+
+def pp_strerror(code: int) -> str:
+    return _lib.pp_strerror(code).decode()
+
+
+def pp_last_error(ctx) -> str:
+    return _lib.pp_last_error(ctx).decode()
+
+
+def _call(name, ctx, *args):
+    rc = getattr(_lib, name)(ctx, *args)
+    if rc != PP_OK:
+        msg = pp_last_error(ctx) if ctx else pp_strerror(rc)
+        raise PPError(rc, f"{name}: {msg}")
+    return rc
+
+
+def pp_config_default() -> pp_config:
+    cfg = pp_config()
+    rc = _lib.pp_config_default(C.byref(cfg))
+    if rc:
+        raise PPError(rc, "pp_config_default")
+    return cfg
+
+
+def pp_create(cfg: pp_config):
+    h = C.c_void_p()
+    rc = _lib.pp_create(C.byref(cfg), C.byref(h))
+    if rc:
+        raise PPError(rc, f"pp_create: {pp_strerror(rc)}")
+    return h.value
+
+
+def pp_destroy(ctx):
+    return _lib.pp_destroy(ctx)
+
+
+def pp_load_geometry(ctx, xyz, string_id, n_dom, dom_radius):
+    return _call("pp_load_geometry", ctx, _ptr(xyz), _ptr(string_id), n_dom, dom_radius)
+
+
+def pp_load_ice(ctx, b_e, a, n_layers, depth_top_m, dz_m, g):
+    return _call("pp_load_ice", ctx, _ptr(b_e), _ptr(a), n_layers, depth_top_m, dz_m, g)
+
+
+def pp_propagate(ctx, event_id, src, n_src, hits, counts):
+    return _call("pp_propagate", ctx, event_id, _ptr(src), n_src, _ptr(hits), _ptr(counts))
+
+
+def pp_propagate_batch(ctx, n_events, event_ids, src_begin, src, hits, counts):
+    return _call("pp_propagate_batch", ctx, n_events, _ptr(event_ids), _ptr(src_begin),
+                 _ptr(src), _ptr(hits), _ptr(counts))
+
+
+def pp_propagate_batch_async(ctx, n_events, d_event_ids, d_src_begin, d_src, n_src, d_hits,
+                             d_counts, stream=None):
+    return _call("pp_propagate_batch_async", ctx, n_events, _ptr(d_event_ids),
+                 _ptr(d_src_begin), _ptr(d_src), n_src, _ptr(d_hits), _ptr(d_counts),
+                 _ptr(stream))
+
+
+def pp_propagate_plain_async(ctx, n_events, h_event_ids, h_src_begin, h_event_photons, d_src,
+                             d_hits, d_counts, stream=None):
+    return _call("pp_propagate_plain_async", ctx, n_events, _ptr(h_event_ids),
+                 _ptr(h_src_begin), _ptr(h_event_photons), _ptr(d_src), _ptr(d_hits),
+                 _ptr(d_counts), _ptr(stream))
+
+
+def pp_sync(ctx, stream=None):
+    return _call("pp_sync", ctx, _ptr(stream))
+
+
+def pp_set_launch(ctx, block_threads=0, blocks_per_sm=0, refill_threshold=0):
+    return _call("pp_set_launch", ctx, block_threads, blocks_per_sm, refill_threshold)
+
+
+def pp_get_launch(ctx):
+    v = [C.c_int32() for _ in range(4)]
+    _call("pp_get_launch", ctx, *[C.addressof(x) for x in v])
+    return tuple(x.value for x in v)
+
+
+def pp_get_world(ctx):
+    out = np.zeros(3, np.float32)
+    _call("pp_get_world", ctx, _ptr(out))
+    return tuple(float(v) for v in out)
+
+
+def pp_debug_philox(ctx, ctr, key, out, n):
+    return _call("pp_debug_philox", ctx, _ptr(ctr), _ptr(key), _ptr(out), n)
+
+
+def pp_debug_trace(ctx, event_id, src, n_src, photon_ids, n, n_trace, outcome, n_steps, birth,
+                   trace):
+    return _call("pp_debug_trace", ctx, event_id, _ptr(src), n_src, _ptr(photon_ids), n,
+                 n_trace, _ptr(outcome), _ptr(n_steps), _ptr(birth), _ptr(trace))
+
+
+def pp_debug_first_hit(ctx, seg, n, mode, dom, t):
+    return _call("pp_debug_first_hit", ctx, _ptr(seg), n, mode, _ptr(dom), _ptr(t))
+
+
+# ---- convenience wrapper ---------------------------------------------------
+
+class Propagator:
+    """One library context with geometry and ice loaded."""
+
+    def __init__(self, geom, ice, seed=0, device=0, max_steps=100_000, world_margin=100.0,
+                 depth_of_z0=1950.0, scatter_coeff_is_effective=True, stream=None):
+        cfg = pp_config_default()
+        cfg.device = device
+        cfg.seed = seed
+        cfg.max_steps = max_steps
+        cfg.world_margin_m = world_margin
+        cfg.depth_of_z0_m = depth_of_z0
+        cfg.scatter_coeff_is_effective = 1 if scatter_coeff_is_effective else 0
+        cfg.stream = _ptr(stream)
+        self.ctx = pp_create(cfg)
+        self.n_dom = geom.n_dom
+        xyz = np.ascontiguousarray(geom.xyz, np.float32).reshape(-1, 3)
+        sid = np.ascontiguousarray(geom.string_id, np.int32)
+        pp_load_geometry(self.ctx, xyz if xyz.size else None, sid if sid.size else None,
+                         geom.n_dom, float(geom.dom_radius))
+        b_e = np.ascontiguousarray(ice.b_e, np.float32)
+        a = np.ascontiguousarray(ice.a, np.float32)
+        pp_load_ice(self.ctx, b_e, a, ice.n_layers, float(ice.depth_top), float(ice.dz),
+                    float(ice.g))
+
+    def close(self):
+        if self.ctx:
+            pp_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @staticmethod
+    def _src(sources):
+        s = np.ascontiguousarray(sources)
+        if s.dtype != workloads.SOURCE_DTYPE:
+            raise TypeError("sources must use workloads.SOURCE_DTYPE")
+        return s
+
+    def propagate(self, event_id, sources):
+        """Plain path for one event: (hits [n_dom], counts [4])."""
+        s = self._src(sources)
+        hits = np.zeros(self.n_dom, np.uint64)
+        counts = np.zeros(4, np.uint64)
+        pp_propagate(self.ctx, int(event_id), s if s.size else None, s.shape[0], hits, counts)
+        return hits, counts
+
+    def propagate_batch(self, batch):
+        """Persistent batched path: (hits [E, n_dom], counts [E, 4])."""
+        s = self._src(batch.sources)
+        ids = np.ascontiguousarray(batch.event_ids, np.uint64)
+        beg = np.ascontiguousarray(batch.src_begin, np.int64)
+        E = ids.shape[0]
+        hits = np.zeros((E, self.n_dom), np.uint64)
+        counts = np.zeros((E, 4), np.uint64)
+        pp_propagate_batch(self.ctx, E, ids, beg, s if s.size else None, hits, counts)
+        return hits, counts
+
+    def set_launch(self, block_threads=0, blocks_per_sm=0, refill_threshold=0):
+        pp_set_launch(self.ctx, block_threads, blocks_per_sm, refill_threshold)
+
+    def get_launch(self):
+        return pp_get_launch(self.ctx)
+
+    def world(self):
+        return pp_get_world(self.ctx)
+
+    def philox(self, ctr, key):
+        ctr = np.ascontiguousarray(ctr, np.uint32).reshape(-1, 4)
+        key = np.ascontiguousarray(np.broadcast_to(np.asarray(key, np.uint32).reshape(-1, 2),
+                                                   (ctr.shape[0], 2)))
+        out = np.zeros_like(ctr)
+        pp_debug_philox(self.ctx, ctr, key, out, ctr.shape[0])
+        return out
+
+    def trace(self, event_id, sources, photon_ids, n_trace=10):
+        s = self._src(sources)
+        ids = np.ascontiguousarray(photon_ids, np.uint64).ravel()
+        n = ids.shape[0]
+        outc = np.zeros(n, np.int32)
+        ns = np.zeros(n, np.int64)
+        birth = np.zeros((n, 6), np.float32)
+        tr = np.zeros((n, max(n_trace, 0), 3), np.float32)
+        pp_debug_trace(self.ctx, int(event_id), s, s.shape[0], ids, n, n_trace, outc, ns, birth,
+                       tr if n_trace > 0 else None)
+        return outc, ns, birth, tr
+
+    def first_hit(self, p, d, S, mode=0):
+        p = np.asarray(p, np.float32).reshape(-1, 3)
+        S = np.broadcast_to(np.asarray(S, np.float32), (p.shape[0],)).reshape(-1, 1)
+        seg = np.ascontiguousarray(np.concatenate(
+            [p, np.asarray(d, np.float32).reshape(-1, 3), S], axis=1), np.float32)
+        n = seg.shape[0]
+        dom = np.zeros(n, np.int32)
+        t = np.zeros(n, np.float32)
+        pp_debug_first_hit(self.ctx, seg, n, mode, dom, t)
+        return dom, t
