@@ -1,0 +1,390 @@
+#!/usr/bin/env python
+"""Benchmark of the photon-propagation hot path on one B300 (or N replicas).
+
+Workload: the full detector (86 strings x 60 DOMs = 5160 DOMs), 171 ice layers
+of 10 m with smooth seeded profiles and one dust layer, and 1000 downgoing
+muon-bundle events (E^-2.7 on 1e3..1e7 GeV, cos zenith U[0.3, 1],
+multiplicity Poisson(3) >= 1, 41 degree Cherenkov light from 1 m segments,
+10 photons/GeV): 2.4e7 photons from 2.8e6 sources per step.  Inputs are
+synthetic (seeded generators), resident in HBM before the timed region.
+
+A step is one pass of the whole path over the batch: source expansion, then
+the persistent propagation kernel over all events' photons (birth, layer walk,
+DOM hit test, escape, scattering, tallies).  `value` is photons/s of that
+batched path; the plain per-event launch path is timed beside it, the
+end-to-end number goes through the host-buffer C entry point, and the CPU
+oracle is timed on a bounded sample of the same workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2405_05700_b300 import workloads as W  # noqa: E402
+
+METRIC = "photons/s on 1 B300, batched vs plain MC; surrogate speedup at χ²/ndf≤1.2"
+UNIT = "photons/s"
+WORKLOAD = ("batched MC, full grid: 86x60 = 5160 DOMs, 171 ice layers (smooth + dust), "
+            "1000 power-law muon-bundle events, Cherenkov 41 deg from 1 m segments")
+
+# Algorithmic ALU work per unit (FP32 + INT32 lane operations of the method as
+# stated in the oracle, an FMA counted once; derivation in the design notes):
+OPS_PER_STEP = 190        # Philox block (98), uniforms, -ln u, first layer visit,
+                          # world exit, cell test, resolve, HG, sincos, rotation
+OPS_PER_CROSSING = 12     # one more layer visited inside a step
+OPS_PER_BIRTH = 185       # Philox block, source lookup, direction, -ln u, layer
+LANES_PER_SM = 128        # 4 schedulers x 32 lanes issue one instruction per clock
+
+# DRAM bytes per launch of the persistent kernel from the committed ncu
+# summary of this workload (profiles/propagate_persistent_full.md); None until
+# a capture of the current kernel exists.
+NCU_TRAFFIC_BYTES = None
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--plain-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-photons", type=int, default=400_000)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def replica_batch(rank: int) -> W.Batch:
+    """The workload of one replica: the same 1000 events, event ids offset by
+    rank so every replica draws its own photons."""
+    b = W.events_full()
+    b.event_ids = (b.event_ids + np.uint64(rank * b.n_events)).astype(np.uint64)
+    return b
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    """Samples SM clocks, power and throttle reasons with nvidia-smi while the
+    timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in self.rows if num(r[1])]
+        mx = [num(r[2]) for r in self.rows if num(r[2])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------- CPU baseline --
+
+def cpu_sample(batch: W.Batch, photons: int) -> W.Batch:
+    """Leading events of the batch up to about `photons` photons."""
+    ppe = batch.photons_per_event()
+    n = int(np.searchsorted(np.cumsum(ppe), photons)) + 1
+    return batch.select(range(min(n, batch.n_events)))
+
+
+def run_oracle_sample(sample: W.Batch):
+    import oracle
+    m = oracle.Model(W.geometry_full(), W.ice_full(), seed=0)
+    t0 = time.perf_counter()
+    hits, counts, _ = oracle.propagate(m, sample)
+    dt = time.perf_counter() - t0
+    return dt, hits, counts
+
+
+def cpu_baseline(batch: W.Batch, photons: int):
+    sample = cpu_sample(batch, photons)
+    dt, _, _ = run_oracle_sample(sample)
+    n = sample.total_photons()
+    return {"value": n / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"first {sample.n_events} of the 1000 events ({n} photons), "
+                      f"double precision, {os.cpu_count()} threads, {dt:.1f} s"}
+
+
+# ---------------------------------------------------------- reference arm --
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    batch = replica_batch(0)
+    sample = cpu_sample(batch, args.cpu_sample_photons // 2)
+    n = sample.total_photons()
+    for _ in range(args.warmup):
+        run_oracle_sample(sample)
+    times = [run_oracle_sample(sample)[0] for _ in range(args.steps)]
+    total = sum(times)
+    value = n * args.steps / total
+    cores = os.cpu_count()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "events": batch.n_events,
+                       "photons_per_step": batch.total_photons(), "parallelism": "replicas"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"each step: first {sample.n_events} events "
+                                       f"({n} photons), {cores} threads"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm --
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2405_05700_b300 import build
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2405_05700_b300 import pp
+
+    batch = replica_batch(rank)
+    geom, ice = W.geometry_full(), W.ice_full()
+    # one explicit stream for the library, torch's copies/flush and the events
+    stream = torch.cuda.Stream(device=local)
+    torch.cuda.set_stream(stream)
+    prop = pp.Propagator(geom, ice, seed=0, device=local, stream=stream.cuda_stream)
+    ctx = prop.ctx
+    E, n_dom = batch.n_events, geom.n_dom
+    n_src = len(batch.sources)
+    photons = batch.total_photons()
+    dev = torch.device("cuda", local)
+    src_np = np.ascontiguousarray(batch.sources)
+    d_src = torch.from_numpy(src_np.view(np.uint8).copy()).to(dev)
+    d_ids = torch.from_numpy(batch.event_ids.astype(np.int64)).to(dev)
+    d_begin = torch.from_numpy(batch.src_begin.astype(np.int64)).to(dev)
+    d_hits = torch.zeros((E, n_dom), dtype=torch.int64, device=dev)
+    d_counts = torch.zeros((E, 4), dtype=torch.int64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 126 MB L2
+
+    def step():
+        pp.pp_propagate_batch_async(ctx, E, d_ids, d_begin, d_src, n_src, d_hits, d_counts,
+                                    stream.cuda_stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    pp.pp_sync(ctx, stream.cuda_stream)
+    pp.pp_get_kernel_time(ctx)
+    pp.pp_get_path_stats(ctx)
+
+    # ---- timed region: K steps, L2 flushed between steps outside the events
+    pp.pp_set_kernel_timing(ctx, True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks.stop()
+    pp.pp_sync(ctx, stream.cuda_stream)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    kern_ms, n_timed, n_kernels = pp.pp_get_kernel_time(ctx)
+    pp.pp_set_kernel_timing(ctx, False)
+    steps_n, cross_n, births_n = pp.pp_get_path_stats(ctx)
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    # validity: exact conservation on the last step
+    hits = d_hits.cpu().numpy().astype(np.int64)
+    counts = d_counts.cpu().numpy().astype(np.int64)
+    emitted = batch.photons_per_event().astype(np.int64)
+    conserved = bool(np.array_equal(hits.sum(1) + counts[:, 0] + counts[:, 1], emitted))
+    steps_per_launch = steps_n / max(1, n_timed)
+    cross_per_launch = cross_n / max(1, n_timed)
+    births_per_launch = births_n / max(1, n_timed)
+
+    # ---- plain per-event launches, same data
+    ev_photons = batch.photons_per_event().astype(np.uint64)
+    h_ids = np.ascontiguousarray(batch.event_ids, np.uint64)
+    h_begin = np.ascontiguousarray(batch.src_begin, np.int64)
+    plain_ms = []
+    for i in range(1 + args.plain_steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pp.pp_propagate_plain_async(ctx, E, h_ids, h_begin, ev_photons, d_src, d_hits, d_counts,
+                                    stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i > 0:
+            plain_ms.append(e0.elapsed_time(e1))
+    pp.pp_sync(ctx, stream.cuda_stream)
+    pp.pp_get_kernel_time(ctx)
+    plain_hits = d_hits.cpu().numpy().astype(np.int64)
+    plain_same = bool(np.array_equal(plain_hits, hits))
+
+    # ---- end to end through the host-buffer entry point (pinned host memory)
+    pin_src = torch.from_numpy(src_np.view(np.uint8).copy()).pin_memory()
+    pin_ids = torch.from_numpy(h_ids.view(np.int64).copy()).pin_memory()
+    pin_begin = torch.from_numpy(h_begin.copy()).pin_memory()
+    pin_hits = torch.zeros((E, n_dom), dtype=torch.int64).pin_memory()
+    pin_counts = torch.zeros((E, 4), dtype=torch.int64).pin_memory()
+
+    def e2e_step():
+        pp.pp_propagate_batch(ctx, E, pin_ids.data_ptr(), pin_begin.data_ptr(),
+                              pin_src.data_ptr(), pin_hits.data_ptr(), pin_counts.data_ptr())
+
+    e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        e2e_step()
+    e2e_s = time.perf_counter() - t0
+    h2d = src_np.nbytes + h_ids.nbytes + h_begin.nbytes
+    d2h = pin_hits.numel() * 8 + pin_counts.numel() * 8
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(batch, args.cpu_sample_photons)
+
+    if rank != 0:
+        return
+    import json as _json
+    peaks = {}
+    try:
+        peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    props = torch.cuda.get_device_properties(dev)
+    ck = clocks.summary()
+    sm_max = ck["sm_max_mhz"] or peaks.get("sm_max_mhz") or 2032.0
+    peak_gops = props.multi_processor_count * LANES_PER_SM * sm_max * 1e6 / 1e9
+    ops = (OPS_PER_STEP * steps_per_launch + OPS_PER_CROSSING * cross_per_launch
+           + OPS_PER_BIRTH * births_per_launch)
+    kern_avg_ms = kern_ms / max(1, n_timed)
+    achieved = ops / (kern_avg_ms * 1e-3) / 1e9
+    value = world * photons * args.steps / (total_ms * 1e-3)
+    plain_value = photons / (statistics.mean(plain_ms) * 1e-3) if plain_ms else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "events": E, "sources_per_step": n_src,
+                   "photons_per_step": photons, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed (256 MB write) between steps, outside the timed events",
+                   "launch": dict(zip(("block_threads", "blocks_per_sm", "refill_threshold",
+                                       "grid_blocks"), prop.get_launch()))},
+        "plain": {"value": plain_value, "unit": UNIT,
+                  "ms_per_step": statistics.mean(plain_ms) if plain_ms else None,
+                  "same_hits_as_batched": plain_same},
+        "batched_over_plain": value / world / plain_value if plain_value else None,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
+                     "frac": achieved / peak_gops, "traffic": NCU_TRAFFIC_BYTES,
+                     "peak_basis": f"{props.multi_processor_count} SMs x {LANES_PER_SM} lanes x "
+                                   f"{sm_max:.0f} MHz (issue peak; derived, not measured)",
+                     "kernel": "k_propagate<persistent>", "kernel_ms": kern_avg_ms,
+                     "steps_per_launch": steps_per_launch,
+                     "crossings_per_launch": cross_per_launch},
+        "steps_per_s": steps_per_launch / (kern_avg_ms * 1e-3),
+        "e2e": {"value": photons * args.e2e_steps / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(n_kernels),
+        "clocks": ck,
+        "conserved": conserved,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    prop.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

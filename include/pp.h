@@ -188,6 +188,19 @@ int pp_set_launch(pp_ctx* ctx, int32_t block_threads, int32_t blocks_per_sm,
 int pp_get_launch(const pp_ctx* ctx, int32_t* block_threads, int32_t* blocks_per_sm,
                   int32_t* refill_threshold, int32_t* grid_blocks);
 
+/* Kernel timing for benchmarks.  While enabled, the library records a pair of
+ * CUDA events on the launching stream around every propagation kernel launch.
+ * pp_get_kernel_time waits for those events and returns the summed kernel
+ * milliseconds and the number of timed launches, plus the number of this
+ * library's kernels launched (expansion and propagation, timed or not), all
+ * since the previous pp_get_kernel_time; then it resets them. */
+int pp_set_kernel_timing(pp_ctx* ctx, int32_t enable);
+int pp_get_kernel_time(pp_ctx* ctx, double* total_ms, uint64_t* n_timed, uint64_t* n_kernels);
+
+/* Totals counted by the persistent kernel since the previous call (waits for
+ * the device, then resets them): out4 = {steps, layer crossings, photons born, 0}. */
+int pp_get_path_stats(pp_ctx* ctx, uint64_t* out4);
+
 /* World cylinder in use: out3 = {radius, z_min, z_max}. */
 int pp_get_world(const pp_ctx* ctx, float* out3);
 

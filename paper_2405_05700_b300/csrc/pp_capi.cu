@@ -40,7 +40,7 @@ struct pp_ctx {
   // device tables
   DevBuf dom, str, str_range, sdom_z, sdom_idx, clear, cell_off, cell_list, layers;
   // scratch
-  DevBuf off, chunk, src_event, bsum, meta, work, err;
+  DevBuf off, chunk, src_event, bsum, meta, work, err, stats;
   // staging for host entry points
   DevBuf s_src, s_begin, s_ids, s_hits, s_counts, s_misc1, s_misc2, s_misc3, s_misc4;
   size_t smem_limit_set = 0;
@@ -48,6 +48,12 @@ struct pp_ctx {
   int block_threads = 256;
   int blocks_per_sm = 0;  // 0: occupancy maximum
   int refill = 8;
+
+  // benchmark timing of propagation launches
+  bool timing = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+  std::vector<cudaEvent_t> event_pool;
+  uint64_t kernels_launched = 0;
 };
 
 namespace {
@@ -194,9 +200,46 @@ WorkDev work_desc(pp_ctx* ctx, const pp_source* d_src, int64_t n_src, bool with_
   w.hits = reinterpret_cast<unsigned long long*>(d_hits);
   w.counts = reinterpret_cast<unsigned long long*>(d_counts);
   w.err = static_cast<int*>(ctx->err.p);
+  w.stats = static_cast<unsigned long long*>(ctx->stats.p);
   w.n_src = (int)n_src;
   w.single_event_lo = single_ev_lo;
   return w;
+}
+
+int take_event(pp_ctx* ctx, cudaEvent_t* ev) {
+  if (!ctx->event_pool.empty()) {
+    *ev = ctx->event_pool.back();
+    ctx->event_pool.pop_back();
+    return PP_OK;
+  }
+  PP_CUDA(cudaEventCreate(ev));
+  return PP_OK;
+}
+
+// Launches the propagation kernel, bracketed by timing events when enabled.
+int timed_propagate(pp_ctx* ctx, bool persistent, const WorkDev& w, const RunDev& run, int grid,
+                    uint64_t n_photons, size_t smem, cudaStream_t st) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc;
+  if (ctx->timing) {
+    if ((rc = take_event(ctx, &e0)) || (rc = take_event(ctx, &e1))) return rc;
+    PP_CUDA(cudaEventRecord(e0, st));
+  }
+  PP_CUDA(launch_propagate(persistent, ctx->ice, ctx->geom, w, run, ctx->block_threads, grid,
+                           n_photons, smem, st));
+  ctx->kernels_launched += 1;
+  if (ctx->timing) {
+    PP_CUDA(cudaEventRecord(e1, st));
+    ctx->pending.emplace_back(e0, e1);
+  }
+  return PP_OK;
+}
+
+int expand(pp_ctx* ctx, const pp_source* d_src, int64_t n_src, const int64_t* d_begin,
+           int n_events, bool with_events, cudaStream_t st) {
+  PP_CUDA(launch_expand(d_src, n_src, d_begin, n_events, expand_bufs(ctx, with_events), st));
+  ctx->kernels_launched += (n_src <= kSmallMax) ? 1 : 4;
+  return PP_OK;
 }
 
 // Batched persistent path on device data (the lock is held by the caller).
@@ -220,11 +263,9 @@ int batch_async(pp_ctx* ctx, int32_t n_events, const uint64_t* d_ids, const int6
   int grid;
   if ((rc = grid_blocks(ctx, smem, &grid))) return rc;
   PP_CUDA(cudaMemsetAsync(ctx->work.p, 0, sizeof(uint64_t), st));
-  PP_CUDA(launch_expand(d_src, n_src, d_begin, n_events, expand_bufs(ctx, true), st));
+  if ((rc = expand(ctx, d_src, n_src, d_begin, n_events, true, st))) return rc;
   const WorkDev w = work_desc(ctx, d_src, n_src, true, d_begin, d_ids, d_hits, d_counts, 0);
-  PP_CUDA(launch_propagate(true, ctx->ice, ctx->geom, w, run_params(ctx), ctx->block_threads,
-                           grid, 0, smem, st));
-  return PP_OK;
+  return timed_propagate(ctx, true, w, run_params(ctx), grid, 0, smem, st);
 }
 
 // Plain path: per event, expansion and one thread per photon.
@@ -256,11 +297,10 @@ int plain_async(pp_ctx* ctx, int32_t n_events, const uint64_t* h_ids, const int6
     const int64_t n = h_begin[e + 1] - h_begin[e];
     if (n == 0 || h_photons[e] == 0) continue;
     const pp_source* s = d_src + h_begin[e];
-    PP_CUDA(launch_expand(s, n, nullptr, 1, expand_bufs(ctx, false), st));
+    if ((rc = expand(ctx, s, n, nullptr, 1, false, st))) return rc;
     const WorkDev w = work_desc(ctx, s, n, false, nullptr, nullptr, d_hits + (size_t)e * n_dom,
                                 d_counts + 4 * (size_t)e, (uint32_t)h_ids[e]);
-    PP_CUDA(launch_propagate(false, ctx->ice, ctx->geom, w, run, ctx->block_threads, 0,
-                             h_photons[e], smem, st));
+    if ((rc = timed_propagate(ctx, false, w, run, 0, h_photons[e], smem, st))) return rc;
   }
   return PP_OK;
 }
@@ -381,9 +421,12 @@ int pp_create(const pp_config* cfg, pp_ctx** out) {
       ctx->own_stream = (e == cudaSuccess);
     }
   }
-  if (e == cudaSuccess && ensure(ctx, ctx->err, sizeof(int)) == PP_OK)
+  if (e == cudaSuccess && ensure(ctx, ctx->err, sizeof(int)) == PP_OK &&
+      ensure(ctx, ctx->stats, 4 * sizeof(uint64_t)) == PP_OK) {
     e = cudaMemset(ctx->err.p, 0, sizeof(int));
-  if (e != cudaSuccess || !ctx->err.p) {
+    if (e == cudaSuccess) e = cudaMemset(ctx->stats.p, 0, 4 * sizeof(uint64_t));
+  }
+  if (e != cudaSuccess || !ctx->err.p || !ctx->stats.p) {
     (void)cudaGetLastError();
     pp_destroy(ctx);
     return PP_ECUDA;
@@ -399,9 +442,15 @@ int pp_destroy(pp_ctx* ctx) {
   DevBuf* bufs[] = {&ctx->dom, &ctx->str, &ctx->str_range, &ctx->sdom_z, &ctx->sdom_idx,
                     &ctx->clear, &ctx->cell_off, &ctx->cell_list, &ctx->layers, &ctx->off,
                     &ctx->chunk, &ctx->src_event, &ctx->bsum, &ctx->meta, &ctx->work, &ctx->err,
+                    &ctx->stats,
                     &ctx->s_src, &ctx->s_begin, &ctx->s_ids, &ctx->s_hits, &ctx->s_counts,
                     &ctx->s_misc1, &ctx->s_misc2, &ctx->s_misc3, &ctx->s_misc4};
   for (DevBuf* b : bufs) release(*b);
+  for (auto& pr : ctx->pending) {
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+  for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return PP_OK;
@@ -658,6 +707,46 @@ int pp_get_launch(const pp_ctx* ctx_c, int32_t* block_threads, int32_t* blocks_p
       if (rc) return rc;
     }
   }
+  return PP_OK;
+}
+
+int pp_set_kernel_timing(pp_ctx* ctx, int32_t enable) {
+  if (!ctx) return PP_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->timing = enable != 0;
+  return PP_OK;
+}
+
+int pp_get_kernel_time(pp_ctx* ctx, double* total_ms, uint64_t* n_timed, uint64_t* n_kernels) {
+  if (!ctx) return PP_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  double sum = 0.0;
+  const uint64_t n = ctx->pending.size();
+  for (auto& pr : ctx->pending) {
+    PP_CUDA(cudaEventSynchronize(pr.second));
+    float ms = 0.f;
+    PP_CUDA(cudaEventElapsedTime(&ms, pr.first, pr.second));
+    sum += ms;
+    ctx->event_pool.push_back(pr.first);
+    ctx->event_pool.push_back(pr.second);
+  }
+  ctx->pending.clear();
+  if (total_ms) *total_ms = sum;
+  if (n_timed) *n_timed = n;
+  if (n_kernels) *n_kernels = ctx->kernels_launched;
+  ctx->kernels_launched = 0;
+  return PP_OK;
+}
+
+int pp_get_path_stats(pp_ctx* ctx, uint64_t* out4) {
+  if (!ctx || !out4) return PP_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  PP_CUDA(cudaStreamSynchronize(ctx->stream));
+  PP_CUDA(cudaDeviceSynchronize());
+  PP_CUDA(cudaMemcpy(out4, ctx->stats.p, 4 * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+  PP_CUDA(cudaMemset(ctx->stats.p, 0, 4 * sizeof(uint64_t)));
   return PP_OK;
 }
 

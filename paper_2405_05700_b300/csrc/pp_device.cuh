@@ -92,7 +92,7 @@ __device__ __forceinline__ int layer_at(const IceDev& I, float z, float w) {
 // ends at the scatter point or the absorption point (tie: absorption).
 __device__ __forceinline__ float walk(const float4* __restrict__ lay, const IceDev& I, float z,
                                       float w, int& layer, float tau_s, float& tau_a,
-                                      bool& absorb) {
+                                      bool& absorb, uint32_t& crossings) {
   const float inv_w = 1.0f / w;
   float zc = z;
   float S = 0.0f;
@@ -118,6 +118,7 @@ __device__ __forceinline__ float walk(const float4* __restrict__ lay, const IceD
       return S + ds;
     }
     S += ell;
+    crossings += 1;
     tau_s = fmaxf(0.0f, fmaf(-L.x, ell, tau_s));
     tau_a = fmaxf(0.0f, fmaf(-L.y, ell, tau_a));
     if (w < 0.0f) {
@@ -345,7 +346,8 @@ __device__ __forceinline__ bool birth(Photon& ph, const pp_source& s, const IceD
 
 // a3..a7: one step.  Returns kContinue after a scatter, else the outcome.
 __device__ __forceinline__ int photon_step(Photon& ph, const IceDev& I, const GeomDev& G,
-                                           const Tables& T, const RunDev& R) {
+                                           const Tables& T, const RunDev& R,
+                                           uint32_t& crossings) {
   ph.n += 1;
   const uint4 x = philox4x32_10(make_uint4(ph.pid_lo, ph.pid_hi, ph.n, 0u),
                                 make_uint2(R.seed_lo, ph.ev_lo));
@@ -353,7 +355,7 @@ __device__ __forceinline__ int photon_step(Photon& ph, const IceDev& I, const Ge
   int layer = ph.layer;
   float tau_a = ph.tau_a;
   bool absorb;
-  const float S = walk(T.layer, I, ph.pz, ph.dz, layer, tau_s, tau_a, absorb);
+  const float S = walk(T.layer, I, ph.pz, ph.dz, layer, tau_s, tau_a, absorb, crossings);
   const float tw = world_exit(G, ph.px, ph.py, ph.pz, ph.dx, ph.dy, ph.dz);
   const float St = fminf(S, tw);
   float th;

@@ -77,6 +77,7 @@ struct WorkDev {
   unsigned long long* hits;   // [n_events][n_dom]
   unsigned long long* counts; // [n_events][4]
   int* err;
+  unsigned long long* stats;  // [4] steps, layer crossings, births, 0 (persistent kernel)
   int n_src;
   uint32_t single_event_lo;   // event id (low word) in single-event mode
 };

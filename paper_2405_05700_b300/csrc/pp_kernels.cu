@@ -211,8 +211,9 @@ k_propagate(IceDev I, GeomDev G, WorkDev W, RunDev R, uint64_t n_plain) {
       atomicOr(W.err, kErrBadSource);
       return;
     }
+    uint32_t crossings = 0;
     for (;;) {
-      const int out = photon_step(ph, I, G, T, R);
+      const int out = photon_step(ph, I, G, T, R, crossings);
       if (out != kContinue) {
         tally(W, G.n_dom, ph, out);
         return;
@@ -224,6 +225,8 @@ k_propagate(IceDev I, GeomDev G, WorkDev W, RunDev R, uint64_t n_plain) {
     const unsigned lane = threadIdx.x & 31;
     bool alive = false;
     bool exhausted = false;
+    uint32_t crossings = 0, births = 0;
+    uint64_t steps = 0;
     for (;;) {
       const unsigned idle = __ballot_sync(kFull, !alive);
       const int n_idle = __popc(idle);
@@ -238,6 +241,7 @@ k_propagate(IceDev I, GeomDev G, WorkDev W, RunDev R, uint64_t n_plain) {
             const int s = locate(W, k, g, ph);
             const pp_source src = W.src[s];
             alive = birth(ph, src, I, R);
+            births += 1;
             if (!alive) atomicOr(W.err, kErrBadSource);
           }
         }
@@ -247,11 +251,26 @@ k_propagate(IceDev I, GeomDev G, WorkDev W, RunDev R, uint64_t n_plain) {
         continue;
       }
       if (alive) {
-        const int out = photon_step(ph, I, G, T, R);
+        const int out = photon_step(ph, I, G, T, R, crossings);
         if (out != kContinue) {
           tally(W, G.n_dom, ph, out);
+          steps += ph.n;
           alive = false;
         }
+      }
+    }
+    if (W.stats) {
+      unsigned long long v0 = steps, v1 = crossings, v2 = births;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        v0 += __shfl_down_sync(kFull, v0, o);
+        v1 += __shfl_down_sync(kFull, v1, o);
+        v2 += __shfl_down_sync(kFull, v2, o);
+      }
+      if (lane == 0) {
+        atomicAdd(W.stats + 0, v0);
+        atomicAdd(W.stats + 1, v1);
+        atomicAdd(W.stats + 2, v2);
       }
     }
   }
@@ -288,8 +307,9 @@ __global__ void k_trace(IceDev I, GeomDev G, WorkDev W, RunDev R, const uint64_t
     b[0] = ph.px; b[1] = ph.py; b[2] = ph.pz;
     b[3] = ph.dx; b[4] = ph.dy; b[5] = ph.dz;
   }
+  uint32_t crossings = 0;
   for (;;) {
-    const int out = photon_step(ph, I, G, T, R);
+    const int out = photon_step(ph, I, G, T, R, crossings);
     if ((out == kContinue || out == kTruncated) && tr && (int)ph.n <= n_trace) {
       tr[3 * (ph.n - 1) + 0] = ph.px;
       tr[3 * (ph.n - 1) + 1] = ph.py;

@@ -65,6 +65,9 @@ _SIGS = {
     "pp_set_launch": [_vp, _i32, _i32, _i32],
     "pp_get_launch": [_vp, _vp, _vp, _vp, _vp],
     "pp_get_world": [_vp, _vp],
+    "pp_set_kernel_timing": [_vp, _i32],
+    "pp_get_path_stats": [_vp, _vp],
+    "pp_get_kernel_time": [_vp, _vp, _vp, _vp],
     "pp_debug_philox": [_vp, _vp, _vp, _vp, _i64],
     "pp_debug_trace": [_vp, _u64, _vp, _i64, _vp, _i64, _i32, _vp, _vp, _vp, _vp],
     "pp_debug_first_hit": [_vp, _vp, _i64, _i32, _vp, _vp],
@@ -190,6 +193,25 @@ def pp_get_world(ctx):
     out = np.zeros(3, np.float32)
     _call("pp_get_world", ctx, _ptr(out))
     return tuple(float(v) for v in out)
+
+
+def pp_set_kernel_timing(ctx, enable):
+    return _call("pp_set_kernel_timing", ctx, 1 if enable else 0)
+
+
+def pp_get_kernel_time(ctx):
+    """-> (total_ms, n_timed_launches, n_kernels_launched) since the last call."""
+    ms, nt, nk = C.c_double(), C.c_uint64(), C.c_uint64()
+    _call("pp_get_kernel_time", ctx, C.addressof(ms), C.addressof(nt), C.addressof(nk))
+    return ms.value, nt.value, nk.value
+
+
+def pp_get_path_stats(ctx):
+    """-> (steps, layer crossings, photons born) counted by the persistent
+    kernel since the last call."""
+    out = np.zeros(4, np.uint64)
+    _call("pp_get_path_stats", ctx, _ptr(out))
+    return int(out[0]), int(out[1]), int(out[2])
 
 
 def pp_debug_philox(ctx, ctr, key, out, n):

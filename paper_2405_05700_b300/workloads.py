@@ -349,3 +349,19 @@ def event_large(total_photons: int = 10_000_000_000, seed: int = 5,
     rng = np.random.default_rng(seed)
     src = muon_bundle(rng, geom, 1e7, 20, 0.8, 1.0, total_photons=total_photons)
     return single_event(src, 0)
+
+
+def sources_gate(photons_per_dom: int = 1000, offset: float = 3.0,
+                 geom: Geometry | None = None) -> Batch:
+    """One isotropic point source ``offset`` metres from every DOM (along +x),
+    so that nearly every DOM of the tiny detector is lit: the input of the
+    per-DOM statistical comparison between two independent propagators."""
+    geom = geometry_tiny() if geom is None else geom
+    s = make_sources(geom.n_dom)
+    s["x"] = geom.xyz[:, 0] + offset
+    s["y"] = geom.xyz[:, 1]
+    s["z"] = geom.xyz[:, 2]
+    s["dz"] = 1.0
+    s["type"] = SRC_ISO_POINT
+    s["n_photons"] = photons_per_dom
+    return single_event(s, 7)

@@ -1,0 +1,355 @@
+"""GPU parity: the CUDA path through the C ABI against the oracle.
+
+* Philox blocks: bit-exact.
+* DOM hit test: the production (cell-grid) search equals the all-DOM loop on
+  the device exactly, and equals the oracle except on grazing segments.
+* Trajectories: births and the first 10 scatter points per photon agree with
+  the oracle (same random streams) to 1e-4 * max(|p|, 1 m).
+* Tallies: exact conservation, plain == batched bit for bit, a result alone ==
+  the same result inside a mix, and the debug tracer (same step code) sums to
+  the production kernel's tallies.
+* Statistics: per-DOM hit maps of 20 independent GPU seeds against 20 oracle
+  seeds (stored maps): every per-DOM pull |z| < 4, pooled chi2/ndf in 1 +- 0.1.
+* Closed forms on the GPU path and the edge cases of the interface.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2405_05700_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def pp():
+    from paper_2405_05700_b300 import build
+    build.build()
+    from paper_2405_05700_b300 import pp as mod
+    return mod
+
+
+@pytest.fixture(scope="module")
+def tiny(pp):
+    prop = pp.Propagator(W.geometry_tiny(), W.ice_tiny(), seed=0)
+    yield prop
+    prop.close()
+
+
+@pytest.fixture(scope="module")
+def full(pp):
+    prop = pp.Propagator(W.geometry_full(), W.ice_full(), seed=0)
+    yield prop
+    prop.close()
+
+
+# ------------------------------------------------------------------ Philox --
+
+def test_philox_bit_exact(tiny, orc):
+    rng = np.random.default_rng(77)
+    n = 1_000_000
+    ctr = rng.integers(0, 2 ** 32, (n, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2 ** 32, (n, 2), dtype=np.uint64).astype(np.uint32)
+    ctr[:1000, 1:] = 0  # photon-style counters
+    assert np.array_equal(tiny.philox(ctr, key), orc.philox(ctr, key))
+
+
+# -------------------------------------------------------------- DOM test --
+
+def _segments(rng, geom, n):
+    k = rng.integers(0, geom.n_dom, n)
+    c = geom.xyz[k].astype(np.float64)
+    p = c + rng.uniform(-6.0, 6.0, (n, 3))
+    d = rng.normal(size=(n, 3))
+    aim = slice(n // 10, n // 2)
+    d[aim] = c[aim] - p[aim] + rng.normal(0.0, 0.12, (n // 2 - n // 10, 3))
+    d[: n // 10, :2] *= 1e-3
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    S = rng.exponential(3.0, n)
+    S[: n // 20] = rng.uniform(10, 300, n // 20)
+    # a share of steps anywhere in the world, long and short
+    m = n // 5
+    R = float(np.max(np.hypot(geom.xyz[:, 0], geom.xyz[:, 1]))) + 100
+    p[-m:, 0] = rng.uniform(-R, R, m) * 0.7
+    p[-m:, 1] = rng.uniform(-R, R, m) * 0.7
+    p[-m:, 2] = rng.uniform(-550, 550, m)
+    S[-m:] = rng.exponential(30.0, m)
+    return p.astype(np.float32), d.astype(np.float32), S.astype(np.float32)
+
+
+@pytest.mark.parametrize("which", ["tiny", "full"])
+def test_grid_search_equals_all_dom_loop(which, tiny, full):
+    prop = tiny if which == "tiny" else full
+    geom = W.geometry_tiny() if which == "tiny" else W.geometry_full()
+    rng = np.random.default_rng(5 if which == "tiny" else 6)
+    p, d, S = _segments(rng, geom, 1_000_000)
+    dom_g, t_g = prop.first_hit(p, d, S, mode=0)
+    dom_b, t_b = prop.first_hit(p, d, S, mode=1)
+    assert np.array_equal(dom_g, dom_b)
+    assert np.array_equal(t_g[dom_b >= 0], t_b[dom_b >= 0])
+    assert (dom_b >= 0).mean() > 0.05
+
+
+def test_grid_search_matches_oracle_except_grazing(full, orc):
+    geom = W.geometry_full()
+    rng = np.random.default_rng(8)
+    p, d, S = _segments(rng, geom, 200_000)
+    dom_g, t_g = full.first_hit(p, d, S, mode=0)
+    m = orc.Model(geom, W.ice_full())
+    dom_o, t_o = orc.first_hit(m, p.astype(np.float64), d.astype(np.float64), S.astype(np.float64))
+    bad = np.nonzero(dom_g != dom_o)[0]
+    assert len(bad) <= 1e-4 * len(dom_g)
+    c = geom.xyz.astype(np.float64)
+    for i in bad:   # each disagreement sits on a decision boundary
+        q0, dd, s = p[i].astype(np.float64), d[i].astype(np.float64), float(S[i])
+        near = False
+        for k in {int(dom_g[i]), int(dom_o[i])} - {-1}:
+            v = c[k] - q0
+            tt = np.clip(v @ dd, 0, s)
+            dist = np.linalg.norm(q0 + tt * dd - c[k])
+            near |= abs(dist - geom.dom_radius) < 1e-3 or abs(tt - s) < 1e-3
+        assert near, i
+    both = dom_g >= 0
+    assert np.allclose(t_g[both], t_o[both], atol=2e-4, rtol=1e-5)
+
+
+# ---------------------------------------------------------- trajectories --
+
+def _trace_both(prop, orc, geom, ice, batch_sources, ids, seed=0, event_id=0):
+    out_g, ns_g, birth_g, tr_g = prop.trace(event_id, batch_sources, ids, n_trace=10)
+    m = orc.Model(geom, ice, seed=seed)
+    out_o, ns_o, birth_o, tr_o = orc.trace(m, event_id, batch_sources, ids, n_trace=10)
+    return (out_g, ns_g, birth_g.astype(np.float64), tr_g.astype(np.float64)), \
+           (out_o, ns_o, birth_o, tr_o)
+
+
+def _check_trajectories(g, o, max_flip_frac):
+    out_g, ns_g, birth_g, tr_g = g
+    out_o, ns_o, birth_o, tr_o = o
+    n = len(out_g)
+    scale = np.maximum(np.linalg.norm(birth_o[:, :3], axis=1), 1.0)
+    assert np.all(np.linalg.norm(birth_g[:, :3] - birth_o[:, :3], axis=1) <= 1e-4 * scale)
+    assert np.all(np.linalg.norm(birth_g[:, 3:] - birth_o[:, 3:], axis=1) <= 1e-5)
+    fin_g, fin_o = np.isfinite(tr_g[:, :, 0]), np.isfinite(tr_o[:, :, 0])
+    same_hist = np.all(fin_g == fin_o, axis=1)
+    both = fin_g & fin_o
+    sc = np.maximum(np.linalg.norm(tr_o, axis=2), 1.0)
+    err = np.where(both, np.linalg.norm(tr_g - tr_o, axis=2) / sc, 0.0)
+    close = np.all(err <= 1e-4, axis=1)
+    off = ~(same_hist & close)
+    assert off.sum() <= max(1, max_flip_frac * n), (off.sum(), n)
+    # whole-life discrete outcomes (hit DOM / absorbed / escaped, step count)
+    diff = (out_g != out_o) | (ns_g != ns_o)
+    assert diff.sum() <= max(2, 1e-3 * n), (diff.sum(), n)
+    return int(off.sum()), int(diff.sum())
+
+
+def test_trajectories_tiny_point_source(tiny, orc):
+    b = W.sources_tiny()
+    ids = np.arange(20000, dtype=np.uint64)
+    g, o = _trace_both(tiny, orc, W.geometry_tiny(), W.ice_tiny(), b.sources, ids)
+    _check_trajectories(g, o, 1e-4)
+
+
+def test_trajectories_cherenkov_bundle(full, orc):
+    b = W.events_full(n_events=3, seed=11)
+    e = int(np.argmax(b.photons_per_event()))
+    src = b.event(e)
+    n_ph = int(src["n_photons"].sum())
+    ids = np.random.default_rng(1).choice(n_ph, size=min(n_ph, 20000), replace=False).astype(np.uint64)
+    g, o = _trace_both(full, orc, W.geometry_full(), W.ice_full(), src, ids,
+                       event_id=int(b.event_ids[e]))
+    _check_trajectories(g, o, 1e-4)
+
+
+def test_photon_ids_beyond_32_bits(tiny, orc):
+    src = W.point_source(0.0, 0.0, 0.0, 6_000_000_000)
+    ids = np.array([0, 2 ** 32 - 2, 2 ** 32 - 1, 2 ** 32, 2 ** 32 + 1, 5_999_999_999], np.uint64)
+    g, o = _trace_both(tiny, orc, W.geometry_tiny(), W.ice_tiny(), src, ids, event_id=9)
+    assert np.allclose(g[2], o[2], atol=1e-4)
+    assert np.array_equal(g[0], o[0])
+
+
+# --------------------------------------------------------------- tallies --
+
+def _conserved(batch, hits, counts):
+    emitted = batch.photons_per_event().astype(np.int64)
+    got = hits.sum(1).astype(np.int64) + counts[:, 0].astype(np.int64) + counts[:, 1].astype(np.int64)
+    return np.array_equal(got, emitted)
+
+
+def test_conservation_tiny_plain_and_batched(tiny):
+    b = W.sources_tiny()
+    h, c = tiny.propagate(0, b.sources)
+    assert int(h.sum() + c[0] + c[1]) == 200_000 and int(c[2]) == 0
+    hb, cb = tiny.propagate_batch(b)
+    assert np.array_equal(hb[0], h) and np.array_equal(cb[0], c)
+
+
+def test_plain_equals_batched_and_mix_invariance(full):
+    b = W.events_full(n_events=40, seed=21)
+    hb, cb = full.propagate_batch(b)
+    assert _conserved(b, hb, cb)
+    for e in range(0, 40, 7):
+        h, c = full.propagate(int(b.event_ids[e]), b.event(e))
+        assert np.array_equal(h, hb[e]) and np.array_equal(c, cb[e])
+    # the same events in another order, with others mixed in, and alone
+    order = list(range(39, -1, -3))
+    mix = b.select(order)
+    hm, cm = full.propagate_batch(mix)
+    for j, e in enumerate(order):
+        assert np.array_equal(hm[j], hb[e]) and np.array_equal(cm[j], cb[e])
+    alone = b.select([5])
+    ha, ca = full.propagate_batch(alone)
+    assert np.array_equal(ha[0], hb[5]) and np.array_equal(ca[0], cb[5])
+
+
+def test_launch_shape_does_not_change_results(full):
+    b = W.events_full(n_events=15, seed=23)
+    ref = full.propagate_batch(b)
+    try:
+        for bt, bps, refill in [(128, 1, 1), (512, 2, 32), (1024, 0, 16), (256, 3, 4)]:
+            full.set_launch(bt, bps, refill)
+            h, c = full.propagate_batch(b)
+            assert np.array_equal(h, ref[0]) and np.array_equal(c, ref[1])
+    finally:
+        full.set_launch(256, 0, 8)
+
+
+def test_tracer_sums_to_production_tallies(tiny):
+    b = W.sources_tiny(50_000)
+    h, c = tiny.propagate(0, b.sources)
+    out, ns, _, _ = tiny.trace(0, b.sources, np.arange(50_000, dtype=np.uint64), n_trace=0)
+    assert np.array_equal(np.bincount(out[out >= 0], minlength=420).astype(np.uint64), h)
+    assert int((out == -1).sum() + (out == -3).sum()) == int(c[0])
+    assert int((out == -2).sum()) == int(c[1])
+    assert int(ns.sum()) == int(c[3])
+
+
+# ------------------------------------------------------------ statistics --
+
+def test_statistical_hit_map_gate(pp):
+    ref = np.load(os.path.join(HERE, "golden", "gate_tiny_oracle.npz"))
+    geom, ice = W.geometry_tiny(), W.ice_tiny()
+    batch = W.sources_gate(int(ref["photons_per_dom"]))
+    gpu = []
+    for seed in range(1, 21):
+        with pp.Propagator(geom, ice, seed=seed) as prop:
+            h, c = prop.propagate_batch(batch)
+            assert _conserved(batch, h, c)
+            gpu.append(h[0].astype(np.int64))
+    gpu = np.array(gpu)
+    cpu = ref["hits"].astype(np.int64)
+    chi2 = ndf = 0.0
+    for a, b_ in zip(gpu, cpu):
+        k = a + b_
+        lit = k > 0
+        chi2 += float((((a - b_) ** 2)[lit] / k[lit]).sum())
+        ndf += float(lit.sum())
+    assert ndf > 3200
+    assert 0.9 <= chi2 / ndf <= 1.1, (chi2, ndf)
+    G, Cc = gpu.sum(0), cpu.sum(0)
+    lit = (G + Cc) > 0
+    z = (G - Cc)[lit] / np.sqrt((G + Cc)[lit])
+    assert np.all(np.abs(z) < 4), float(np.abs(z).max())
+
+
+# ---------------------------------------------------------- closed forms --
+
+def test_gpu_no_scatter_single_dom_closed_form(pp):
+    from scipy import integrate
+    d, r, a = 10.0, 1.0, 0.01
+    geom = W.Geometry(np.array([[0.0, 0.0, -d]], np.float32), np.zeros(1, np.int32), r)
+    ice = W.ice_homogeneous(0.0, a, n_layers=1, depth_top=0.0)
+    N = 50_000_000
+    with pp.Propagator(geom, ice, seed=3, world_margin=1000.0) as prop:
+        h, c = prop.propagate(0, W.point_source(0, 0, 0, N))
+    mu0 = math.sqrt(1 - r * r / (d * d))
+    a32 = float(np.float32(a))
+    P = 0.5 * integrate.quad(lambda mu: math.exp(-a32 * (d * mu - math.sqrt(max(0.0, r * r - d * d * (1 - mu * mu))))),
+                             mu0, 1.0, epsabs=1e-14, epsrel=1e-12)[0]
+    k = int(h[0])
+    assert abs(k - N * P) / math.sqrt(N * P * (1 - P)) < 4
+    assert int(h.sum() + c[0] + c[1]) == N
+
+
+def test_gpu_infinite_medium_moments(pp):
+    geom = W.Geometry(np.zeros((0, 3), np.float32), np.zeros(0, np.int32), 0.1651)
+    be, a, g = 0.05, 0.01, 0.9
+    ice = W.ice_homogeneous(be, a, g=g, n_layers=3, depth_top=1900.0)
+    N = 2_000_000
+    with pp.Propagator(geom, ice, seed=2, world_margin=1e5) as prop:
+        h, c = prop.propagate_batch(W.single_event(W.point_source(0, 0, 0, N), 4))
+    assert int(c[0, 0]) == N and int(c[0, 1]) == 0 and int(c[0, 2]) == 0
+    m_sc = (float(np.float32(be)) / (1 - g)) / float(np.float32(a))
+    mean_steps = int(c[0, 3]) / N          # scatters + the final step
+    assert abs(mean_steps - (m_sc + 1)) < 4 * math.sqrt(m_sc * (1 + m_sc) / N)
+
+
+# ----------------------------------------------------------- edge cases --
+
+def test_edge_cases(tiny, pp):
+    # empty batch, event with no sources, zero-photon sources, one photon
+    empty = W.Batch(np.zeros(0, np.uint64), np.zeros(1, np.int64), W.make_sources(0))
+    h, c = tiny.propagate_batch(empty)
+    assert h.shape == (0, 420)
+    s = np.concatenate([W.point_source(0, 0, 0, 0), W.point_source(1, 0, 0, 1),
+                        W.point_source(0, 2, 0, 0), W.point_source(0, 0, 5, 3)])
+    b = W.Batch(np.array([4, 5, 6], np.uint64), np.array([0, 0, 4, 4], np.int64), s)
+    h, c = tiny.propagate_batch(b)
+    assert h[0].sum() == 0 and c[0].sum() == 0 and c[2].sum() == 0
+    assert int(h[1].sum() + c[1, 0] + c[1, 1]) == 4
+    h1, c1 = tiny.propagate(5, s)
+    assert np.array_equal(h1, h[1]) and np.array_equal(c1, c[1])
+    h0, c0 = tiny.propagate(5, W.make_sources(0))
+    assert h0.sum() == 0 and c0.sum() == 0
+    # malformed input is refused on the host
+    bad = W.point_source(np.nan, 0, 0, 10)
+    with pytest.raises(pp.PPError) as ei:
+        tiny.propagate(0, bad)
+    assert ei.value.code == pp.PP_EINVAL
+    bad = W.point_source(0, 0, 0, 10)
+    bad["type"] = 7
+    with pytest.raises(pp.PPError):
+        tiny.propagate(0, bad)
+
+
+def test_step_cap_truncates_and_conserves(pp, orc):
+    geom, ice = W.geometry_tiny(), W.ice_tiny()
+    b = W.sources_tiny(100_000)
+    with pp.Propagator(geom, ice, seed=0, max_steps=5) as prop:
+        h, c = prop.propagate(0, b.sources)
+        hb, cb = prop.propagate_batch(b)
+        out, ns, _, _ = prop.trace(0, b.sources, np.arange(2000, dtype=np.uint64), n_trace=0)
+    assert np.array_equal(h, hb[0]) and np.array_equal(c, cb[0])
+    assert int(h.sum() + c[0] + c[1]) == 100_000
+    assert 0 < int(c[2]) <= int(c[0])
+    assert int(ns.max()) == 5
+    m = orc.Model(geom, ice, seed=0, max_steps=5)
+    out_o, ns_o, _, _ = orc.trace(m, 0, b.sources, np.arange(2000, dtype=np.uint64), n_trace=0)
+    assert (out != out_o).sum() <= 2 and (ns != ns_o).sum() <= 2
+
+
+# --------------------------------------------- full size, bench launch shape --
+
+@pytest.mark.slow
+def test_full_workload_conservation_and_sampled_photons(full, orc):
+    b = W.events_full()          # the benchmark's 1000 power-law muon-bundle events
+    h, c = full.propagate_batch(b)
+    assert _conserved(b, h, c)
+    assert int(c[:, 2].sum()) == 0
+    rng = np.random.default_rng(99)
+    m = orc.Model(W.geometry_full(), W.ice_full(), seed=0)
+    n_diff = n_tot = 0
+    for e in rng.choice(b.n_events, 6, replace=False):
+        src = b.event(int(e))
+        n_ph = int(src["n_photons"].sum())
+        ids = rng.choice(n_ph, size=min(n_ph, 1500), replace=False).astype(np.uint64)
+        out_g, ns_g, _, _ = full.trace(int(b.event_ids[e]), src, ids, n_trace=0)
+        out_o, ns_o, _, _ = orc.trace(m, int(b.event_ids[e]), src, ids, n_trace=0)
+        n_diff += int(((out_g != out_o) | (ns_g != ns_o)).sum())
+        n_tot += len(ids)
+    assert n_diff <= max(2, 1e-3 * n_tot), (n_diff, n_tot)
