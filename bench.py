@@ -42,10 +42,12 @@ WORKLOAD = ("batched MC, full grid: 86x60 = 5160 DOMs, 171 ice layers (smooth + 
 
 # Algorithmic ALU work per unit (FP32 + INT32 lane operations of the method as
 # stated in the oracle, an FMA counted once; derivation in the design notes):
-OPS_PER_STEP = 190        # Philox block (98), uniforms, -ln u, first layer visit,
-                          # world exit, cell test, resolve, HG, sincos, rotation
-OPS_PER_CROSSING = 12     # one more layer visited inside a step
-OPS_PER_BIRTH = 185       # Philox block, source lookup, direction, -ln u, layer
+OPS_PER_STEP = 210        # Philox block (98), 3 uniforms (12), -ln u (2), first layer
+                          # visit (14), world exit (17), cell test (19), resolve (4),
+                          # move (3), HG (6), sin theta (5), sincos (3), rotation (28)
+OPS_PER_CROSSING = 14     # one more layer visited inside a step
+OPS_PER_BIRTH = 180       # Philox block, 4 uniforms, source lookup, point, direction,
+                          # -ln u, starting layer
 LANES_PER_SM = 128        # 4 schedulers x 32 lanes issue one instruction per clock
 
 # DRAM bytes per launch of the persistent kernel from the committed ncu
@@ -63,7 +65,10 @@ def parse():
     ap.add_argument("--plain-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-photons", type=int, default=400_000)
+    ap.add_argument("--cpu-sample-photons", type=int, default=10_000_000)
+    ap.add_argument("--ref-sample-photons", type=int, default=500_000)
+    ap.add_argument("--events", type=int, default=1000,
+                    help="leading events of the workload (profiling runs use fewer)")
     return ap.parse_args()
 
 
@@ -74,11 +79,13 @@ def dist_env():
     return rank, world, local
 
 
-def replica_batch(rank: int) -> W.Batch:
-    """The workload of one replica: the same 1000 events, event ids offset by
-    rank so every replica draws its own photons."""
+def replica_batch(rank: int, n_events: int = 1000) -> W.Batch:
+    """The workload of one replica: the same events, event ids offset by rank
+    so every replica draws its own photons."""
     b = W.events_full()
-    b.event_ids = (b.event_ids + np.uint64(rank * b.n_events)).astype(np.uint64)
+    if n_events < b.n_events:
+        b = b.select(range(n_events))
+    b.event_ids = (b.event_ids + np.uint64(rank * 1000)).astype(np.uint64)
     return b
 
 
@@ -101,7 +108,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -113,7 +120,10 @@ class ClockSampler:
         for line in self.proc.stdout:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) >= 9:
-                self.rows.append(parts)
+                self.rows.append([time.time()] + parts)
+
+    def mark(self, which):
+        setattr(self, which, time.time())
 
     def stop(self):
         if self.proc:
@@ -131,14 +141,19 @@ class ClockSampler:
                 return float(x)
             except ValueError:
                 return None
-        sm = [num(r[1]) for r in self.rows if num(r[1])]
-        mx = [num(r[2]) for r in self.rows if num(r[2])]
+        t0, t1 = getattr(self, "t_start", 0.0), getattr(self, "t_end", 1e30)
+        # samples taken while the timed steps ran (nvidia-smi reports with a
+        # lag of up to one period, so allow one period on each side)
+        rows = [r[1:] for r in self.rows if t0 - 0.1 <= r[0] <= t1 + 0.1] or \
+               [r[1:] for r in self.rows]
+        sm = [num(r[1]) for r in rows if num(r[1])]
+        mx = [num(r[2]) for r in rows if num(r[2])]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in self.rows for i in range(4)
+        reasons = sorted({names[i] for r in rows for i in range(4)
                           if r[5 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(self.rows)}
+                "samples": len(rows)}
 
 
 # ------------------------------------------------------------- CPU baseline --
@@ -174,8 +189,8 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    batch = replica_batch(0)
-    sample = cpu_sample(batch, args.cpu_sample_photons // 2)
+    batch = replica_batch(0, args.events)
+    sample = cpu_sample(batch, args.ref_sample_photons)
     n = sample.total_photons()
     for _ in range(args.warmup):
         run_oracle_sample(sample)
@@ -213,7 +228,7 @@ def run_ours(args):
         torch.distributed.barrier()
     from paper_2405_05700_b300 import pp
 
-    batch = replica_batch(rank)
+    batch = replica_batch(rank, args.events)
     geom, ice = W.geometry_full(), W.ice_full()
     # one explicit stream for the library, torch's copies/flush and the events
     stream = torch.cuda.Stream(device=local)
@@ -250,6 +265,7 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    clocks.mark("t_start")
     evs = []
     for _ in range(args.steps):
         flush.zero_()
@@ -259,8 +275,10 @@ def run_ours(args):
         e1.record(stream)
         evs.append((e0, e1))
     torch.cuda.synchronize()
+    clocks.mark("t_end")
     if world > 1:
         torch.distributed.barrier()
+    time.sleep(0.15)
     clocks.stop()
     pp.pp_sync(ctx, stream.cuda_stream)
     step_ms = [a.elapsed_time(b) for a, b in evs]
@@ -313,12 +331,14 @@ def run_ours(args):
         pp.pp_propagate_batch(ctx, E, pin_ids.data_ptr(), pin_begin.data_ptr(),
                               pin_src.data_ptr(), pin_hits.data_ptr(), pin_counts.data_ptr())
 
-    e2e_step()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
+    e2e_s = None
+    if args.e2e_steps > 0:
         e2e_step()
-    e2e_s = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        e2e_s = time.perf_counter() - t0
     h2d = src_np.nbytes + h_ids.nbytes + h_begin.nbytes
     d2h = pin_hits.numel() * 8 + pin_counts.numel() * 8
 
@@ -365,7 +385,7 @@ def run_ours(args):
                      "steps_per_launch": steps_per_launch,
                      "crossings_per_launch": cross_per_launch},
         "steps_per_s": steps_per_launch / (kern_avg_ms * 1e-3),
-        "e2e": {"value": photons * args.e2e_steps / e2e_s, "unit": UNIT,
+        "e2e": {"value": photons * args.e2e_steps / e2e_s if e2e_s else None, "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(n_kernels),
         "clocks": ck,
