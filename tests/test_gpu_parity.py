@@ -112,8 +112,18 @@ def test_grid_search_matches_oracle_except_grazing(full, orc):
             dist = np.linalg.norm(q0 + tt * dd - c[k])
             near |= abs(dist - geom.dom_radius) < 1e-3 or abs(tt - s) < 1e-3
         assert near, i
-    both = dom_g >= 0
-    assert np.allclose(t_g[both], t_o[both], atol=2e-4, rtol=1e-5)
+    # entry distances: FP32 vs FP64 with float32 (not exactly unit) directions;
+    # the error grows like t^2 |1 - |d|^2| / sqrt(disc), so it is bounded
+    # relatively except on near-grazing rays
+    both = np.nonzero((dom_g >= 0) & (dom_g == dom_o))[0]
+    dt = np.abs(t_g[both].astype(np.float64) - t_o[both])
+    loose = both[dt > 1e-4 * np.maximum(1.0, t_o[both])]
+    assert len(loose) <= 1e-3 * len(both), (len(loose), len(both))
+    for i in loose:
+        k = int(dom_o[i])
+        q0, dd = p[i].astype(np.float64), d[i].astype(np.float64)
+        tt = np.clip((c[k] - q0) @ dd, 0, float(S[i]))
+        assert abs(np.linalg.norm(q0 + tt * dd - c[k]) - geom.dom_radius) < 2e-2, i
 
 
 # ---------------------------------------------------------- trajectories --
