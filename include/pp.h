@@ -222,6 +222,12 @@ int pp_debug_trace(pp_ctx* ctx, uint64_t event_id, const pp_source* src, int64_t
                    const uint64_t* photon_ids, int64_t n, int32_t n_trace, int32_t* outcome,
                    int64_t* n_steps, float* birth, float* trace);
 
+/* The device scattering step on given directions: the HG polar angle from
+ * word x_mu (mapped to u in (0,1) as in the propagation), the azimuth from
+ * word x_phi, applied to dir with the context's g.
+ *   dir[n][3] unit directions, words[n][2] (x_mu, x_phi), out[n][3] new directions */
+int pp_debug_scatter(pp_ctx* ctx, const float* dir, const uint32_t* words, float* out, int64_t n);
+
 /* The device hit test on given segments: first DOM met on [p, p + S d].
  *   seg[n][7]   p (3), d (3, unit), S
  *   mode        0: string / cell-grid search (production), 1: every DOM

@@ -65,7 +65,7 @@ def lib():
             "orc_world": ([P, vp], None),
             "orc_first_hit": ([P, vp, vp, vp, vp, vp, i64], None),
             "orc_propagate": ([P, i32, vp, vp, vp, vp, vp, vp, vp, vp], C.c_int),
-            "orc_trace": ([P, C.c_uint64, i64, vp, vp, vp, vp, i64, i32, vp, vp, vp, vp], C.c_int),
+            "orc_trace": ([P, C.c_uint64, i64, vp, vp, vp, vp, i64, i32, vp, vp, vp, vp, vp], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(_lib, name)
@@ -223,9 +223,11 @@ def propagate(model: Model, batch):
                           "cos_sum": stats[3]}
 
 
-def trace(model: Model, event_id: int, sources, photon_ids, n_trace: int = 10):
+def trace(model: Model, event_id: int, sources, photon_ids, n_trace: int = 10,
+          margins: bool = False):
     """Follows chosen photons of one event.  Returns (outcome [n] i32,
-    n_steps [n] i64, birth [n, 6], trace [n, n_trace, 3])."""
+    n_steps [n] i64, birth [n, 6], trace [n, n_trace, 3]) and, with
+    margins=True, also the per-step decision margins [n, n_trace] (metres)."""
     f, typ, nph = _source_arrays(sources)
     ids = np.ascontiguousarray(photon_ids, dtype=np.uint64).ravel()
     n = ids.shape[0]
@@ -233,8 +235,12 @@ def trace(model: Model, event_id: int, sources, photon_ids, n_trace: int = 10):
     ns = np.zeros(n, np.int64)
     birth = np.zeros((n, 6))
     tr = np.zeros((n, n_trace, 3))
+    mg = np.zeros((n, n_trace)) if margins else None
     rc = lib().orc_trace(model.pref(), int(event_id), f.shape[0], _ptr(f), _ptr(typ), _ptr(nph),
-                         _ptr(ids), n, n_trace, _ptr(outc), _ptr(ns), _ptr(birth), _ptr(tr))
+                         _ptr(ids), n, n_trace, _ptr(outc), _ptr(ns), _ptr(birth), _ptr(tr),
+                         _ptr(mg) if margins else None)
     if rc != 0:
         raise RuntimeError(f"orc_trace failed: {rc}")
+    if margins:
+        return outc, ns, birth, tr, mg
     return outc, ns, birth, tr

@@ -249,10 +249,12 @@ struct WalkResult {
   int layer;         // layer at the end of the step
   double tau_a;      // absorption optical depth left
   int64_t crossings;
+  double race;       // |da - ds| in the last layer (m): how close scatter and
+                     // absorption came (a diagnostic, not used by the method)
 };
 
 WalkResult walk(const Ice& ice, double z, double w, int layer, double tau_s, double tau_a) {
-  WalkResult r{0.0, false, layer, tau_a, 0};
+  WalkResult r{0.0, false, layer, tau_a, 0, kInf};
   double zc = z;
   for (;;) {
     const int i = r.layer;
@@ -263,6 +265,7 @@ WalkResult walk(const Ice& ice, double z, double w, int layer, double tau_s, dou
     if (ell < 0.0) ell = 0.0;
     const double ds = bi > 0.0 ? tau_s / bi : kInf;
     const double da = ai > 0.0 ? r.tau_a / ai : kInf;
+    if (da <= ell || ds <= ell) r.race = std::fabs(da - ds);
     if (da <= ds && da <= ell) {
       r.S += da;
       r.tau_a = 0.0;
@@ -425,8 +428,24 @@ struct PhotonStats {
 // One photon from birth to its end.  Returns the DOM index it hits, or
 // OUT_ABSORBED / OUT_ESCAPED / OUT_TRUNCATED.  trace (optional) receives the
 // birth point and direction and the first n_trace scatter points.
+// Distance (m) from the decision boundaries of the DOM test on [p, p + S d]:
+// for every sphere, | closest approach of the segment to its centre - r |.
+double dom_margin(const Geom& G, const double p[3], const double d[3], double S) {
+  double m = kInf;
+  for (int k = 0; k < G.n; ++k) {
+    const double v[3] = {G.x[k] - p[0], G.y[k] - p[1], G.z[k] - p[2]};
+    double t = v[0] * d[0] + v[1] * d[1] + v[2] * d[2];
+    t = std::max(0.0, std::min(S, t));
+    const double q[3] = {p[0] + t * d[0] - G.x[k], p[1] + t * d[1] - G.y[k],
+                         p[2] + t * d[2] - G.z[k]};
+    m = std::min(m, std::fabs(std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]) - G.r));
+  }
+  return m;
+}
+
 int simulate_photon(const Model& M, uint32_t event_lo, uint64_t pid, const Source& src,
-                    PhotonStats* st, double* birth6, double* trace, int n_trace) {
+                    PhotonStats* st, double* birth6, double* trace, int n_trace,
+                    double* margin = nullptr) {
   const uint32_t key[2] = {(uint32_t)M.seed, event_lo};
   uint32_t ctr[4] = {(uint32_t)pid, (uint32_t)(pid >> 32), 0u, 0u};
   uint32_t x[4];
@@ -465,6 +484,13 @@ int simulate_photon(const Model& M, uint32_t event_lo, uint64_t pid, const Sourc
     const double S_test = std::min(w.S, tw);
     double th = kInf;
     const int k = first_hit(M.geom, M.brute, pos, dir, S_test, &th);
+    if (margin && (int)n <= n_trace) {
+      // diagnostic: how close this step's discrete decisions came to flipping
+      double mg = std::min(w.race, dom_margin(M.geom, pos, dir, S_test));
+      if (std::isfinite(tw) && std::isfinite(w.S)) mg = std::min(mg, std::fabs(tw - w.S));
+      if (std::fabs(std::fabs(dir[2]) - 0.99999) < 1e-6) mg = 0.0;  // rotation frame choice
+      margin[n - 1] = mg;
+    }
     if (k >= 0 && th < tw) {
       st->path += th;
       return k;
@@ -658,10 +684,13 @@ int orc_propagate(const orc_params* P, int32_t n_events, const uint64_t* event_i
 // Outputs: outcome[n] (DOM index, -1 absorbed, -2 escaped, -3 truncated),
 // n_steps[n], birth[n][6] (point, direction), trace[n][n_trace][3] scatter
 // points (NaN past the photon's last scatter).
+// margins[n][n_trace] (optional): for each of the first n_trace steps, the
+// distance in metres of that step's decisions from a flip (scatter/absorb race,
+// sphere grazing, world exit); NaN past the photon's end.
 int orc_trace(const orc_params* P, uint64_t event_id, int64_t n_src, const float* src_f,
               const uint32_t* src_type, const uint64_t* src_n, const uint64_t* photon_ids,
               int64_t n, int32_t n_trace, int32_t* outcome, int64_t* n_steps, double* birth,
-              double* trace) {
+              double* trace, double* margins) {
   if (!P || n < 0 || n_trace < 0) return -1;
   Model M;
   build_model(P, &M);
@@ -678,6 +707,8 @@ int orc_trace(const orc_params* P, uint64_t event_id, int64_t n_src, const float
       const int64_t s = (int64_t)(std::upper_bound(off.begin(), off.end() - 1, pid) - off.begin()) - 1;
       double* tr = trace + (size_t)i * n_trace * 3;
       for (int q = 0; q < 3 * n_trace; ++q) tr[q] = std::nan("");
+      double* mg = margins ? margins + (size_t)i * n_trace : nullptr;
+      for (int q = 0; mg && q < n_trace; ++q) mg[q] = std::nan("");
       if (s < 0 || pid >= off[n_src]) {
         outcome[i] = -4;
         n_steps[i] = 0;
@@ -686,7 +717,8 @@ int orc_trace(const orc_params* P, uint64_t event_id, int64_t n_src, const float
       }
       PhotonStats ps;
       const Source src = read_source(src_f, src_type, s);
-      outcome[i] = simulate_photon(M, (uint32_t)event_id, pid, src, &ps, birth + 6 * i, tr, n_trace);
+      outcome[i] = simulate_photon(M, (uint32_t)event_id, pid, src, &ps, birth + 6 * i, tr, n_trace,
+                                   mg);
       n_steps[i] = ps.steps;
     }
   };

@@ -158,6 +158,7 @@ RunDev run_params(const pp_ctx* ctx) {
   r.seed_lo = (uint32_t)ctx->cfg.seed;
   r.max_steps = ctx->cfg.max_steps;
   r.cos_cherenkov = (float)std::cos(41.0 * 3.14159265358979323846 / 180.0);
+  r.sin_cherenkov = (float)std::sin(41.0 * 3.14159265358979323846 / 180.0);
   r.refill = ctx->refill;
   return r;
 }
@@ -819,6 +820,28 @@ int pp_debug_trace(pp_ctx* ctx, uint64_t event_id, const pp_source* src, int64_t
   if (birth) PP_CUDA(cudaMemcpyAsync(birth, d_birth, 24 * n, cudaMemcpyDeviceToHost, st));
   if (n_trace > 0)
     PP_CUDA(cudaMemcpyAsync(trace, d_tr, 12 * (size_t)n * n_trace, cudaMemcpyDeviceToHost, st));
+  PP_CUDA(cudaStreamSynchronize(st));
+  return PP_OK;
+}
+
+int pp_debug_scatter(pp_ctx* ctx, const float* dir, const uint32_t* words, float* out, int64_t n) {
+  if (!ctx) return PP_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (!ctx->ice_loaded) return fail(ctx, PP_ENOTLOADED, "load ice first");
+  if (n < 0 || (n > 0 && (!dir || !words || !out))) return fail(ctx, PP_EINVAL, "bad arguments");
+  if (n == 0) return PP_OK;
+  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  cudaStream_t st = ctx->stream;
+  int rc;
+  if ((rc = ensure(ctx, ctx->s_misc1, 12 * (size_t)n))) return rc;
+  if ((rc = ensure(ctx, ctx->s_misc2, 8 * (size_t)n))) return rc;
+  if ((rc = ensure(ctx, ctx->s_misc3, 12 * (size_t)n))) return rc;
+  PP_CUDA(cudaMemcpyAsync(ctx->s_misc1.p, dir, 12 * n, cudaMemcpyHostToDevice, st));
+  PP_CUDA(cudaMemcpyAsync(ctx->s_misc2.p, words, 8 * n, cudaMemcpyHostToDevice, st));
+  PP_CUDA(launch_scatter(ctx->ice, static_cast<float*>(ctx->s_misc1.p),
+                         static_cast<uint32_t*>(ctx->s_misc2.p), static_cast<float*>(ctx->s_misc3.p),
+                         n, st));
+  PP_CUDA(cudaMemcpyAsync(out, ctx->s_misc3.p, 12 * n, cudaMemcpyDeviceToHost, st));
   PP_CUDA(cudaStreamSynchronize(st));
   return PP_OK;
 }

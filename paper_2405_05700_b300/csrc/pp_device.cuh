@@ -39,6 +39,27 @@ __device__ __forceinline__ float u01f(uint32_t x) {
   return __uint2float_rn((x >> 8) | 1u) * 5.9604644775390625e-08f;
 }
 
+// Hot-path arithmetic: hardware approximations (PTX sqrt.approx / MUFU
+// instructions behind the CUDA intrinsics), accurate to a few ulp -- far
+// inside the 1e-4 position tolerance against the FP64 oracle.
+__device__ __forceinline__ float fast_sqrt(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// -ln u for u in (0, 1)
+__device__ __forceinline__ float neg_log(float u) { return -__logf(u); }
+
+// (sin, cos) of 2 pi u for u in (0, 1): evaluated at pi (2u - 1), which lies
+// in (-pi, pi) where the hardware sine/cosine are accurate, and negated
+// (sin(x + pi) = -sin x, cos(x + pi) = -cos x).
+__device__ __forceinline__ void sincos_2pi(float u, float& s, float& c) {
+  __sincosf(3.14159265358979f * fmaf(2.0f, u, -1.0f), &s, &c);
+  s = -s;
+  c = -c;
+}
+
 // --------------------------------------------------------- shared tables --
 struct Tables {
   const float4* layer;   // [L]
@@ -93,7 +114,7 @@ __device__ __forceinline__ int layer_at(const IceDev& I, float z, float w) {
 __device__ __forceinline__ float walk(const float4* __restrict__ lay, const IceDev& I, float z,
                                       float w, int& layer, float tau_s, float& tau_a,
                                       bool& absorb, uint32_t& crossings) {
-  const float inv_w = 1.0f / w;
+  const float inv_w = __fdividef(1.0f, w);
   float zc = z;
   float S = 0.0f;
   for (;;) {
@@ -137,16 +158,30 @@ __device__ __forceinline__ float world_exit(const GeomDev& G, float px, float py
   const float c = fmaf(px, px, fmaf(py, py, -G.R2));
   if (c > 0.0f || pz < G.zlo || pz > G.zhi) return 0.0f;
   float tz = PP_INF;
-  if (dz > 0.0f) tz = (G.zhi - pz) / dz;
-  else if (dz < 0.0f) tz = (G.zlo - pz) / dz;
+  if (dz > 0.0f) tz = __fdividef(G.zhi - pz, dz);
+  else if (dz < 0.0f) tz = __fdividef(G.zlo - pz, dz);
   float tr = PP_INF;
   const float a = fmaf(dx, dx, dy * dy);
   if (a > 0.0f) {
     const float b = fmaf(px, dx, py * dy);
-    const float sq = sqrtf(fmaxf(0.0f, fmaf(b, b, -a * c)));
-    tr = (b > 0.0f) ? (-c) / (b + sq) : (sq - b) / a;
+    const float sq = fast_sqrt(fmaxf(0.0f, fmaf(b, b, -a * c)));
+    tr = (b > 0.0f) ? __fdividef(-c, b + sq) : __fdividef(sq - b, a);
   }
   return fminf(tz, tr);
+}
+
+// Exit distance when the step [0, S] may reach the world boundary, +inf when
+// it provably stays inside (then only "t_exit > S" matters and every decision
+// is the same as with the exact distance).  The 1 cm margin exceeds the FP32
+// error of both tests.
+__device__ __forceinline__ float world_exit_within(const GeomDev& G, float px, float py,
+                                                   float pz, float dx, float dy, float dz,
+                                                   float S) {
+  const float m = S + 0.01f;
+  const float rin = G.R - m;
+  const bool inside = rin > 0.0f && fmaf(px, px, py * py) < rin * rin && pz - m > G.zlo &&
+                      pz + m < G.zhi;
+  return inside ? PP_INF : world_exit(G, px, py, pz, dx, dy, dz);
 }
 
 // Sphere of radius r about c met on [p, p + S d]: entry distance, 0 when the
@@ -227,15 +262,18 @@ __device__ __forceinline__ void test_string(const GeomDev& G, const Tables& T, i
 // long) or every string is searched.
 __device__ __forceinline__ int first_hit_grid(const GeomDev& G, const Tables& T, float px,
                                               float py, float pz, float dx, float dy, float dz,
-                                              float S, float& t_out) {
+                                              float S, float& t_out, uint32_t& slow) {
   t_out = PP_INF;
   if (G.n_dom == 0) return -1;
   const float dxy2 = fmaf(dx, dx, dy * dy);
-  const float Lxy = S * sqrtf(dxy2);
+  const float L2 = S * S * dxy2;  // squared horizontal length of the step
   const int ix = min(max(__float2int_rd((px - G.gx0) * G.inv_cell), 0), G.nx - 1);
   const int iy = min(max(__float2int_rd((py - G.gy0) * G.inv_cell), 0), G.ny - 1);
   const int cell = iy * G.nx + ix;
-  if (Lxy < (float)T.clear[cell] * G.clear_unit) return -1;
+  const float clr = (float)T.clear[cell] * G.clear_unit;
+  if (L2 < clr * clr) return -1;
+  slow += 1;
+  const float Lxy = fast_sqrt(L2);
   int best = -1;
   float bt = PP_INF;
   if (Lxy <= G.halo) {
@@ -261,29 +299,49 @@ __device__ __forceinline__ int first_hit_brute(const GeomDev& G, float px, float
 }
 
 // ---------------------------------------------------------- scattering --
-// Henyey-Greenstein cosine by inversion of its cumulative distribution.
-__device__ __forceinline__ float hg_mu(const IceDev& I, float u) {
-  if (I.g == 0.0f) return fmaf(2.0f, u, -1.0f);
-  const float t = I.c1 / fmaf(I.c3, u, I.c2);
-  const float mu = fmaf(-t, t, I.c4) * I.c5;
-  return fminf(1.0f, fmaxf(-1.0f, mu));
+// Henyey-Greenstein scattering angle by inversion of its cumulative
+// distribution: mu = (1 + g^2 - t^2) / (2g), t = (1 - g^2) / (1 - g + 2gu).
+// Strong forward scattering puts mu within 1e-5 of 1 for a percent of the
+// draws, where FP32 loses 1 - mu to rounding; so 1 - mu and 1 + mu come from
+// the algebraically equal, cancellation-free forms
+//   1 - mu = (1-g)(1-u)(t + 1 - g) / (1 - g + 2gu)
+//   1 + mu = (1+g) u (1 + g + t) / (1 - g + 2gu)
+// (1 - u is exact in FP32), and sin(theta) = sqrt((1 - mu)(1 + mu)).
+__device__ __forceinline__ void hg_angle(const IceDev& I, float u, float& mu, float& st) {
+  if (I.g == 0.0f) {
+    mu = fmaf(2.0f, u, -1.0f);
+    st = 2.0f * fast_sqrt(u * (1.0f - u));
+    return;
+  }
+  const float den = fmaf(I.c3, u, I.c2);        // 1 - g + 2gu
+  const float inv = __fdividef(1.0f, den);
+  const float t = I.c1 * inv;
+  const float omm = I.c2 * (1.0f - u) * (t + I.c2) * inv;        // 1 - mu
+  const float opm = (2.0f - I.c2) * u * ((2.0f - I.c2) + t) * inv;  // 1 + mu
+  mu = (omm < opm) ? 1.0f - omm : opm - 1.0f;
+  mu = fminf(1.0f, fmaxf(-1.0f, mu));
+  st = fast_sqrt(fmaxf(0.0f, omm * opm));
 }
 
-// New direction at polar cosine mu, azimuth 2 pi u_phi about (dx, dy, dz):
-// the MCML rotation (Wang, Jacques & Zheng 1995), lab frame near the poles,
-// renormalised.
-__device__ __forceinline__ void rotate(float& dx, float& dy, float& dz, float mu, float u_phi) {
-  const float st = sqrtf(fmaxf(0.0f, (1.0f - mu) * (1.0f + mu)));
+// New direction at polar cosine mu (sine st), azimuth 2 pi u_phi about
+// (dx, dy, dz): the MCML rotation (Wang, Jacques & Zheng 1995), lab frame near
+// the poles, renormalised.
+__device__ __forceinline__ void rotate(float& dx, float& dy, float& dz, float mu, float st,
+                                       float u_phi) {
   float sp, cp;
-  sincospif(2.0f * u_phi, &sp, &cp);
+  sincos_2pi(u_phi, sp, cp);
   float ox, oy, oz;
   if (fabsf(dz) > 0.99999f) {
     ox = st * cp;
     oy = st * sp;
     oz = (dz >= 0.0f) ? mu : -mu;
   } else {
-    const float tmp = sqrtf((1.0f - dz) * (1.0f + dz));
-    const float it = 1.0f / tmp;
+    // 1 - dz^2 of a unit vector, taken as dx^2 + dy^2: an FP32 direction is
+    // unit only to ~1e-7, and near the poles 1 - dz^2 would carry that error
+    // into a frame of size ~1e-4
+    const float q = fmaf(dx, dx, dy * dy);
+    const float it = rsqrtf(q);
+    const float tmp = q * it;
     ox = fmaf(st * fmaf(dx * dz, cp, -dy * sp), it, dx * mu);
     oy = fmaf(st * fmaf(dy * dz, cp, dx * sp), it, dy * mu);
     oz = fmaf(-st * cp, tmp, dz * mu);
@@ -326,17 +384,19 @@ __device__ __forceinline__ bool birth(Photon& ph, const pp_source& s, const IceD
     ph.dx = sdx;
     ph.dy = sdy;
     ph.dz = sdz;
-    rotate(ph.dx, ph.dy, ph.dz, R.cos_cherenkov, u01f(x.z));
+    rotate(ph.dx, ph.dy, ph.dz, R.cos_cherenkov, R.sin_cherenkov, u01f(x.z));
   } else {
-    const float mu = fmaf(2.0f, u01f(x.y), -1.0f);
-    const float st = sqrtf(fmaxf(0.0f, (1.0f - mu) * (1.0f + mu)));
+    // mu = 2u - 1, so (1 - mu)(1 + mu) = 4u(1 - u) without cancellation
+    const float u = u01f(x.y);
+    const float mu = fmaf(2.0f, u, -1.0f);
+    const float st = 2.0f * fast_sqrt(u * (1.0f - u));
     float sp, cp;
-    sincospif(2.0f * u01f(x.z), &sp, &cp);
+    sincos_2pi(u01f(x.z), sp, cp);
     ph.dx = st * cp;
     ph.dy = st * sp;
     ph.dz = mu;
   }
-  ph.tau_a = -logf(u01f(x.w));
+  ph.tau_a = neg_log(u01f(x.w));
   ph.n = 0;
   const bool ok = s.type <= PP_SRC_CASCADE && isfinite(ph.px) && isfinite(ph.py) &&
                   isfinite(ph.pz) && nn > 0.0f && s.length >= 0.0f;
@@ -347,26 +407,28 @@ __device__ __forceinline__ bool birth(Photon& ph, const pp_source& s, const IceD
 // a3..a7: one step.  Returns kContinue after a scatter, else the outcome.
 __device__ __forceinline__ int photon_step(Photon& ph, const IceDev& I, const GeomDev& G,
                                            const Tables& T, const RunDev& R,
-                                           uint32_t& crossings) {
+                                           uint32_t& crossings, uint32_t& slow) {
   ph.n += 1;
   const uint4 x = philox4x32_10(make_uint4(ph.pid_lo, ph.pid_hi, ph.n, 0u),
                                 make_uint2(R.seed_lo, ph.ev_lo));
-  const float tau_s = -logf(u01f(x.x));
+  const float tau_s = neg_log(u01f(x.x));
   int layer = ph.layer;
   float tau_a = ph.tau_a;
   bool absorb;
   const float S = walk(T.layer, I, ph.pz, ph.dz, layer, tau_s, tau_a, absorb, crossings);
-  const float tw = world_exit(G, ph.px, ph.py, ph.pz, ph.dx, ph.dy, ph.dz);
+  const float tw = world_exit_within(G, ph.px, ph.py, ph.pz, ph.dx, ph.dy, ph.dz, S);
   const float St = fminf(S, tw);
   float th;
-  const int k = first_hit_grid(G, T, ph.px, ph.py, ph.pz, ph.dx, ph.dy, ph.dz, St, th);
+  const int k = first_hit_grid(G, T, ph.px, ph.py, ph.pz, ph.dx, ph.dy, ph.dz, St, th, slow);
   if (k >= 0 && th < tw) return k;
   if (tw <= S) return kEscaped;
   if (absorb) return kAbsorbed;
   ph.px = fmaf(S, ph.dx, ph.px);
   ph.py = fmaf(S, ph.dy, ph.py);
   ph.pz = fmaf(S, ph.dz, ph.pz);
-  rotate(ph.dx, ph.dy, ph.dz, hg_mu(I, u01f(x.y)), u01f(x.z));
+  float mu, st;
+  hg_angle(I, u01f(x.y), mu, st);
+  rotate(ph.dx, ph.dy, ph.dz, mu, st, u01f(x.z));
   ph.layer = layer;
   ph.tau_a = tau_a;
   if (ph.n >= R.max_steps) return kTruncated;

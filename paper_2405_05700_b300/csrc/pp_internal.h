@@ -85,7 +85,7 @@ struct WorkDev {
 struct RunDev {
   uint32_t seed_lo;
   uint32_t max_steps;
-  float cos_cherenkov;
+  float cos_cherenkov, sin_cherenkov;
   int refill;                 // persistent: refill once this many lanes are idle
 };
 
@@ -124,6 +124,9 @@ cudaError_t launch_trace(const IceDev& ice, const GeomDev& geom, const WorkDev& 
 
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n,
                           cudaStream_t st);
+
+cudaError_t launch_scatter(const IceDev& ice, const float* dir, const uint32_t* words, float* out,
+                           int64_t n, cudaStream_t st);
 
 cudaError_t launch_first_hit(const GeomDev& geom, const IceDev& ice, const float* seg, int64_t n,
                              int mode, int* dom, float* t, size_t smem, cudaStream_t st);

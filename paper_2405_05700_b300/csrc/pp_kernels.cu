@@ -211,9 +211,9 @@ k_propagate(IceDev I, GeomDev G, WorkDev W, RunDev R, uint64_t n_plain) {
       atomicOr(W.err, kErrBadSource);
       return;
     }
-    uint32_t crossings = 0;
+    uint32_t crossings = 0, slow = 0;
     for (;;) {
-      const int out = photon_step(ph, I, G, T, R, crossings);
+      const int out = photon_step(ph, I, G, T, R, crossings, slow);
       if (out != kContinue) {
         tally(W, G.n_dom, ph, out);
         return;
@@ -225,7 +225,7 @@ k_propagate(IceDev I, GeomDev G, WorkDev W, RunDev R, uint64_t n_plain) {
     const unsigned lane = threadIdx.x & 31;
     bool alive = false;
     bool exhausted = false;
-    uint32_t crossings = 0, births = 0;
+    uint32_t crossings = 0, births = 0, slow = 0;
     uint64_t steps = 0;
     for (;;) {
       const unsigned idle = __ballot_sync(kFull, !alive);
@@ -251,7 +251,7 @@ k_propagate(IceDev I, GeomDev G, WorkDev W, RunDev R, uint64_t n_plain) {
         continue;
       }
       if (alive) {
-        const int out = photon_step(ph, I, G, T, R, crossings);
+        const int out = photon_step(ph, I, G, T, R, crossings, slow);
         if (out != kContinue) {
           tally(W, G.n_dom, ph, out);
           steps += ph.n;
@@ -260,17 +260,19 @@ k_propagate(IceDev I, GeomDev G, WorkDev W, RunDev R, uint64_t n_plain) {
       }
     }
     if (W.stats) {
-      unsigned long long v0 = steps, v1 = crossings, v2 = births;
+      unsigned long long v0 = steps, v1 = crossings, v2 = births, v3 = slow;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         v0 += __shfl_down_sync(kFull, v0, o);
         v1 += __shfl_down_sync(kFull, v1, o);
         v2 += __shfl_down_sync(kFull, v2, o);
+        v3 += __shfl_down_sync(kFull, v3, o);
       }
       if (lane == 0) {
         atomicAdd(W.stats + 0, v0);
         atomicAdd(W.stats + 1, v1);
         atomicAdd(W.stats + 2, v2);
+        atomicAdd(W.stats + 3, v3);
       }
     }
   }
@@ -307,9 +309,9 @@ __global__ void k_trace(IceDev I, GeomDev G, WorkDev W, RunDev R, const uint64_t
     b[0] = ph.px; b[1] = ph.py; b[2] = ph.pz;
     b[3] = ph.dx; b[4] = ph.dy; b[5] = ph.dz;
   }
-  uint32_t crossings = 0;
+  uint32_t crossings = 0, slow = 0;
   for (;;) {
-    const int out = photon_step(ph, I, G, T, R, crossings);
+    const int out = photon_step(ph, I, G, T, R, crossings, slow);
     if ((out == kContinue || out == kTruncated) && tr && (int)ph.n <= n_trace) {
       tr[3 * (ph.n - 1) + 0] = ph.px;
       tr[3 * (ph.n - 1) + 1] = ph.py;
@@ -328,6 +330,19 @@ __global__ void k_philox(const uint4* ctr, const uint2* key, uint4* out, int64_t
   if (i < n) out[i] = philox4x32_10(ctr[i], key[i]);
 }
 
+__global__ void k_scatter(IceDev I, const float* dir, const uint32_t* words, float* out,
+                          int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float dx = dir[3 * i], dy = dir[3 * i + 1], dz = dir[3 * i + 2];
+  float mu, st;
+  hg_angle(I, u01f(words[2 * i]), mu, st);
+  rotate(dx, dy, dz, mu, st, u01f(words[2 * i + 1]));
+  out[3 * i] = dx;
+  out[3 * i + 1] = dy;
+  out[3 * i + 2] = dz;
+}
+
 __global__ void k_first_hit(GeomDev G, IceDev I, const float* seg, int64_t n, int mode, int* dom,
                             float* t) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -337,7 +352,8 @@ __global__ void k_first_hit(GeomDev G, IceDev I, const float* seg, int64_t n, in
   if (i >= n) return;
   const float* q = seg + 7 * i;
   float th;
-  const int k = mode == 0 ? first_hit_grid(G, T, q[0], q[1], q[2], q[3], q[4], q[5], q[6], th)
+  uint32_t slow = 0;
+  const int k = mode == 0 ? first_hit_grid(G, T, q[0], q[1], q[2], q[3], q[4], q[5], q[6], th, slow)
                           : first_hit_brute(G, q[0], q[1], q[2], q[3], q[4], q[5], q[6], th);
   dom[i] = k;
   t[i] = th;
@@ -414,6 +430,13 @@ cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* ou
   k_philox<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
       reinterpret_cast<const uint4*>(ctr), reinterpret_cast<const uint2*>(key),
       reinterpret_cast<uint4*>(out), n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const IceDev& ice, const float* dir, const uint32_t* words, float* out,
+                           int64_t n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_scatter<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ice, dir, words, out, n);
   return cudaGetLastError();
 }
 

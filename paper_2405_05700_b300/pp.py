@@ -71,6 +71,7 @@ _SIGS = {
     "pp_debug_philox": [_vp, _vp, _vp, _vp, _i64],
     "pp_debug_trace": [_vp, _u64, _vp, _i64, _vp, _i64, _i32, _vp, _vp, _vp, _vp],
     "pp_debug_first_hit": [_vp, _vp, _i64, _i32, _vp, _vp],
+    "pp_debug_scatter": [_vp, _vp, _vp, _vp, _i64],
 }
 EXPORTS = tuple(_SIGS) + ("pp_last_error", "pp_strerror")
 
@@ -224,6 +225,10 @@ def pp_debug_trace(ctx, event_id, src, n_src, photon_ids, n, n_trace, outcome, n
                  n_trace, _ptr(outcome), _ptr(n_steps), _ptr(birth), _ptr(trace))
 
 
+def pp_debug_scatter(ctx, dir, words, out, n):
+    return _call("pp_debug_scatter", ctx, _ptr(dir), _ptr(words), _ptr(out), n)
+
+
 def pp_debug_first_hit(ctx, seg, n, mode, dom, t):
     return _call("pp_debug_first_hit", ctx, _ptr(seg), n, mode, _ptr(dom), _ptr(t))
 
@@ -325,6 +330,13 @@ class Propagator:
         pp_debug_trace(self.ctx, int(event_id), s, s.shape[0], ids, n, n_trace, outc, ns, birth,
                        tr if n_trace > 0 else None)
         return outc, ns, birth, tr
+
+    def scatter(self, d, words):
+        d = np.ascontiguousarray(d, np.float32).reshape(-1, 3)
+        words = np.ascontiguousarray(words, np.uint32).reshape(-1, 2)
+        out = np.zeros_like(d)
+        pp_debug_scatter(self.ctx, d, words, out, d.shape[0])
+        return out
 
     def first_hit(self, p, d, S, mode=0):
         p = np.asarray(p, np.float32).reshape(-1, 3)
