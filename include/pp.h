@@ -172,6 +172,30 @@ int pp_propagate_plain_async(pp_ctx* ctx, int32_t n_events, const uint64_t* h_ev
                              const pp_source* d_src, uint64_t* d_hits, uint64_t* d_counts,
                              void* stream);
 
+/* One event on device-resident data with no device allocation during the
+ * call.  The paper has no counterpart: this serves callers that may not
+ * allocate device memory while they run -- for example a host that hands the
+ * library fixed, pre-sized buffers and forbids allocator calls (and the
+ * synchronisation cudaMalloc/cudaFree imply) on its hot loop.  The caller
+ * passes inputs and outputs as for pp_propagate_batch_async; the kernels'
+ * scratch (photon prefix sums, chunk table, work counter) comes from one
+ * static device array inside the library, sized for PP_NOALLOC_MAX_SOURCES
+ * sources (about 97 KiB, held by every GPU that loads the library until the
+ * process exits).
+ *   d_src[n_src]  device sources of the event, 0 <= n_src <= PP_NOALLOC_MAX_SOURCES
+ *                 (more: PP_EINVAL with a message, nothing enqueued)
+ *   d_hits[n_dom], d_counts[4]  device outputs, overwritten (as pp_propagate)
+ *   stream        CUDA stream (NULL: the context's stream); returns once enqueued,
+ *                 device errors are reported by pp_sync
+ * The first call on a device looks up the array's device address (set-up, once
+ * per device), so make that first call before any stream capture.  Every call
+ * shares the one array and the work counter in it is cleared by each call:
+ * calls whose GPU work overlaps in time (different streams, or several
+ * contexts on one device) race and must be serialised by the caller. */
+#define PP_NOALLOC_MAX_SOURCES 8192
+int pp_propagate_noalloc(pp_ctx* ctx, uint64_t event_id, const pp_source* d_src, int64_t n_src,
+                         uint64_t* d_hits, uint64_t* d_counts, void* stream);
+
 /* Waits for `stream` (NULL: the context's stream) and reports a device error
  * flag raised since the last pp_sync.  Errors: PP_ECUDA, PP_EDEVICE. */
 int pp_sync(pp_ctx* ctx, void* stream);

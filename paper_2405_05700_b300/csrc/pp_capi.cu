@@ -67,6 +67,9 @@ int cuda_fail(pp_ctx* c, cudaError_t e, const char* where) {
   return fail(c, PP_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+int fail_ctx(pp_ctx* c, int code, const char* msg) { return fail(c, code, msg); }
+int cuda_fail_ctx(pp_ctx* c, cudaError_t e, const char* where) { return cuda_fail(c, e, where); }
+
 #define PP_CUDA(expr)                                   \
   do {                                                  \
     cudaError_t _e = (expr);                            \
@@ -363,6 +366,36 @@ int batch_host(pp_ctx* ctx, bool plain, int32_t n_events, const uint64_t* ids,
 }
 
 }  // namespace
+
+namespace ppk {
+
+int LaunchView::fail(int code, const char* msg) const { return fail_ctx(ctx, code, msg); }
+
+int LaunchView::cuda_fail(cudaError_t e, const char* where) const {
+  return cuda_fail_ctx(ctx, e, where);
+}
+
+int with_launch_view(pp_ctx* ctx, const std::function<int(const LaunchView&)>& fn) {
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  int rc;
+  if ((rc = check_loaded(ctx))) return rc;
+  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  LaunchView v;
+  v.ctx = ctx;
+  v.device = ctx->cfg.device;
+  v.stream = ctx->stream;
+  v.ice = ctx->ice;
+  v.geom = ctx->geom;
+  v.run = run_params(ctx);
+  v.block_threads = ctx->block_threads;
+  if ((rc = prepare_smem(ctx, &v.smem))) return rc;
+  if ((rc = grid_blocks(ctx, v.smem, &v.grid_blocks))) return rc;
+  v.err = static_cast<int*>(ctx->err.p);
+  v.stats = static_cast<unsigned long long*>(ctx->stats.p);
+  return fn(v);
+}
+
+}  // namespace ppk
 
 extern "C" {
 

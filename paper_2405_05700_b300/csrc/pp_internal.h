@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
+
 #include "pp.h"
 
 namespace ppk {
@@ -130,5 +132,27 @@ cudaError_t launch_scatter(const IceDev& ice, const float* dir, const uint32_t* 
 
 cudaError_t launch_first_hit(const GeomDev& geom, const IceDev& ice, const float* seg, int64_t n,
                              int mode, int* dom, float* t, size_t smem, cudaStream_t st);
+
+// What a launch needs from a context, for entry points defined outside
+// pp_capi.cu.  with_launch_view locks the context, checks that geometry and
+// ice are loaded, prepares the kernels' shared-memory limit and the persistent
+// grid, and calls fn with the view (fn's return value is returned).
+struct LaunchView {
+  pp_ctx* ctx;
+  int device;
+  cudaStream_t stream;
+  IceDev ice;
+  GeomDev geom;
+  RunDev run;
+  int block_threads;
+  int grid_blocks;
+  size_t smem;
+  int* err;
+  unsigned long long* stats;
+  int fail(int code, const char* msg) const;
+  int cuda_fail(cudaError_t e, const char* where) const;
+};
+
+int with_launch_view(pp_ctx* ctx, const std::function<int(const LaunchView&)>& fn);
 
 }  // namespace ppk

@@ -61,6 +61,7 @@ _SIGS = {
     "pp_propagate_batch": [_vp, _i32, _vp, _vp, _vp, _vp, _vp],
     "pp_propagate_batch_async": [_vp, _i32, _vp, _vp, _vp, _i64, _vp, _vp, _vp],
     "pp_propagate_plain_async": [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "pp_propagate_noalloc": [_vp, _u64, _vp, _i64, _vp, _vp, _vp],
     "pp_sync": [_vp, _vp],
     "pp_set_launch": [_vp, _i32, _i32, _i32],
     "pp_get_launch": [_vp, _vp, _vp, _vp, _vp],
@@ -173,6 +174,16 @@ def pp_propagate_plain_async(ctx, n_events, h_event_ids, h_src_begin, h_event_ph
                              d_hits, d_counts, stream=None):
     return _call("pp_propagate_plain_async", ctx, n_events, _ptr(h_event_ids),
                  _ptr(h_src_begin), _ptr(h_event_photons), _ptr(d_src), _ptr(d_hits),
+                 _ptr(d_counts), _ptr(stream))
+
+
+PP_NOALLOC_MAX_SOURCES = 8192
+
+
+def pp_propagate_noalloc(ctx, event_id, d_src, n_src, d_hits, d_counts, stream=None):
+    """One event on device data; the library allocates nothing during the call
+    (its scratch is a fixed static device array, at most 8192 sources)."""
+    return _call("pp_propagate_noalloc", ctx, event_id, _ptr(d_src), n_src, _ptr(d_hits),
                  _ptr(d_counts), _ptr(stream))
 
 
