@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--plain-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--cpu-sample-photons", type=int, default=10_000_000)
     ap.add_argument("--ref-sample-photons", type=int, default=500_000)
     ap.add_argument("--events", type=int, default=1000,
@@ -251,6 +252,10 @@ def run_ours(args):
         pp.pp_propagate_batch_async(ctx, E, d_ids, d_begin, d_src, n_src, d_hits, d_counts,
                                     stream.cuda_stream)
 
+    tuned = None
+    if not args.no_autotune:
+        tuned = pp.pp_autotune_batch(ctx, E, d_ids, d_begin, d_src, n_src, d_hits, d_counts,
+                                     stream.cuda_stream, repeats=1)
     for _ in range(max(3, args.warmup)):
         step()
     pp.pp_sync(ctx, stream.cuda_stream)
@@ -284,7 +289,7 @@ def run_ours(args):
     step_ms = [a.elapsed_time(b) for a, b in evs]
     kern_ms, n_timed, n_kernels = pp.pp_get_kernel_time(ctx)
     pp.pp_set_kernel_timing(ctx, False)
-    steps_n, cross_n, births_n = pp.pp_get_path_stats(ctx)
+    steps_n, cross_n, births_n, slow_n = pp.pp_get_path_stats(ctx)
     total_ms = sum(step_ms)
     if world > 1:
         t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
@@ -383,7 +388,9 @@ def run_ours(args):
                                    f"{sm_max:.0f} MHz (issue peak; derived, not measured)",
                      "kernel": "k_propagate<persistent>", "kernel_ms": kern_avg_ms,
                      "steps_per_launch": steps_per_launch,
-                     "crossings_per_launch": cross_per_launch},
+                     "crossings_per_launch": cross_per_launch,
+                     "string_search_frac": slow_n / max(1, steps_n)},
+        "autotune": {"best": tuned[0], "best_ms": tuned[1]} if tuned else None,
         "steps_per_s": steps_per_launch / (kern_avg_ms * 1e-3),
         "e2e": {"value": photons * args.e2e_steps / e2e_s if e2e_s else None, "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},

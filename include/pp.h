@@ -208,6 +208,19 @@ int pp_sync(pp_ctx* ctx, void* stream);
 int pp_set_launch(pp_ctx* ctx, int32_t block_threads, int32_t blocks_per_sm,
                   int32_t refill_threshold);
 
+/* Autotuner: times the batched path on the given device-resident batch (as
+ * pp_propagate_batch_async) for a fixed set of launch settings -- block size
+ * 128..1024, 4 to 6 resident 256-thread blocks per SM (register-capped kernel
+ * variants), refill thresholds 1..32 -- each once untimed and `repeats` times
+ * timed with CUDA events on `stream`, keeps the fastest, and reports it in
+ * best3 = {block_threads, blocks_per_sm, refill_threshold} and best_ms (both
+ * may be NULL).  Results do not depend on the settings (the outputs of the
+ * last run are valid).  Errors: as pp_propagate_batch_async. */
+int pp_autotune_batch(pp_ctx* ctx, int32_t n_events, const uint64_t* d_event_ids,
+                      const int64_t* d_src_begin, const pp_source* d_src, int64_t n_src,
+                      uint64_t* d_hits, uint64_t* d_counts, void* stream, int32_t repeats,
+                      int32_t* best3, float* best_ms);
+
 /* Reads back the launch settings in use (any pointer may be NULL). */
 int pp_get_launch(const pp_ctx* ctx, int32_t* block_threads, int32_t* blocks_per_sm,
                   int32_t* refill_threshold, int32_t* grid_blocks);
@@ -222,7 +235,8 @@ int pp_set_kernel_timing(pp_ctx* ctx, int32_t enable);
 int pp_get_kernel_time(pp_ctx* ctx, double* total_ms, uint64_t* n_timed, uint64_t* n_kernels);
 
 /* Totals counted by the persistent kernel since the previous call (waits for
- * the device, then resets them): out4 = {steps, layer crossings, photons born, 0}. */
+ * the device, then resets them): out4 = {steps, layer crossings, photons born,
+ * steps that needed the string search of the DOM test}. */
 int pp_get_path_stats(pp_ctx* ctx, uint64_t* out4);
 
 /* World cylinder in use: out3 = {radius, z_min, z_max}. */

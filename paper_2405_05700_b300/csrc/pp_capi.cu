@@ -40,7 +40,7 @@ struct pp_ctx {
   // device tables
   DevBuf dom, str, str_range, sdom_z, sdom_idx, clear, cell_off, cell_list, layers;
   // scratch
-  DevBuf off, chunk, src_event, bsum, meta, work, err, stats;
+  DevBuf off, chunk, aux, bsum, meta, work, err, stats;
   // staging for host entry points
   DevBuf s_src, s_begin, s_ids, s_hits, s_counts, s_misc1, s_misc2, s_misc3, s_misc4;
   size_t smem_limit_set = 0;
@@ -146,9 +146,16 @@ int prepare_smem(pp_ctx* ctx, size_t* smem) {
   return PP_OK;
 }
 
+// Register-capped kernel variant for the launch settings (see launch_propagate).
+int kernel_variant(const pp_ctx* ctx) {
+  if (ctx->block_threads == 256 && (ctx->blocks_per_sm == 5 || ctx->blocks_per_sm == 6))
+    return ctx->blocks_per_sm;
+  return 0;
+}
+
 int grid_blocks(pp_ctx* ctx, size_t smem, int* out) {
   int occ = 0;
-  cudaError_t e = propagate_occupancy(ctx->block_threads, smem, &occ);
+  cudaError_t e = propagate_occupancy(ctx->block_threads, smem, kernel_variant(ctx), &occ);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   if (occ < 1) return fail(ctx, PP_EINVAL, "propagation kernel does not fit on an SM");
   const int bps = ctx->blocks_per_sm > 0 ? std::min(ctx->blocks_per_sm, occ) : occ;
@@ -170,7 +177,7 @@ int ensure_scratch(pp_ctx* ctx, int64_t n_src, bool with_events) {
   int rc;
   if ((rc = ensure(ctx, ctx->off, sizeof(uint64_t) * (size_t)(n_src + 1)))) return rc;
   if ((rc = ensure(ctx, ctx->chunk, sizeof(uint32_t) * (size_t)(n_src + 2)))) return rc;
-  if (with_events && (rc = ensure(ctx, ctx->src_event, sizeof(uint32_t) * (size_t)std::max<int64_t>(n_src, 1))))
+  if (with_events && (rc = ensure(ctx, ctx->aux, sizeof(SrcAux) * (size_t)std::max<int64_t>(n_src, 1))))
     return rc;
   const int64_t nb = (n_src + kScanTile - 1) / kScanTile;
   if ((rc = ensure(ctx, ctx->bsum, sizeof(uint64_t) * (size_t)std::max<int64_t>(nb, 1)))) return rc;
@@ -183,7 +190,7 @@ ExpandBufs expand_bufs(pp_ctx* ctx, bool with_events) {
   ExpandBufs b;
   b.off = static_cast<uint64_t*>(ctx->off.p);
   b.chunk_src = static_cast<uint32_t*>(ctx->chunk.p);
-  b.src_event = with_events ? static_cast<uint32_t*>(ctx->src_event.p) : nullptr;
+  b.aux = with_events ? static_cast<SrcAux*>(ctx->aux.p) : nullptr;
   b.bsum = static_cast<uint64_t*>(ctx->bsum.p);
   b.meta = static_cast<uint64_t*>(ctx->meta.p);
   return b;
@@ -196,9 +203,9 @@ WorkDev work_desc(pp_ctx* ctx, const pp_source* d_src, int64_t n_src, bool with_
   w.src = d_src;
   w.off = static_cast<const uint64_t*>(ctx->off.p);
   w.chunk_src = static_cast<const uint32_t*>(ctx->chunk.p);
-  w.src_event = with_events ? static_cast<const uint32_t*>(ctx->src_event.p) : nullptr;
-  w.src_begin = d_begin;
-  w.event_ids = d_ids;
+  w.aux = with_events ? static_cast<const SrcAux*>(ctx->aux.p) : nullptr;
+  (void)d_begin;
+  (void)d_ids;
   w.meta = static_cast<const uint64_t*>(ctx->meta.p);
   w.work = static_cast<unsigned long long*>(ctx->work.p);
   w.hits = reinterpret_cast<unsigned long long*>(d_hits);
@@ -230,7 +237,7 @@ int timed_propagate(pp_ctx* ctx, bool persistent, const WorkDev& w, const RunDev
     PP_CUDA(cudaEventRecord(e0, st));
   }
   PP_CUDA(launch_propagate(persistent, ctx->ice, ctx->geom, w, run, ctx->block_threads, grid,
-                           n_photons, smem, st));
+                           n_photons, smem, st, persistent ? kernel_variant(ctx) : 0));
   ctx->kernels_launched += 1;
   if (ctx->timing) {
     PP_CUDA(cudaEventRecord(e1, st));
@@ -240,8 +247,8 @@ int timed_propagate(pp_ctx* ctx, bool persistent, const WorkDev& w, const RunDev
 }
 
 int expand(pp_ctx* ctx, const pp_source* d_src, int64_t n_src, const int64_t* d_begin,
-           int n_events, bool with_events, cudaStream_t st) {
-  PP_CUDA(launch_expand(d_src, n_src, d_begin, n_events, expand_bufs(ctx, with_events), st));
+           const uint64_t* d_ids, int n_events, bool with_events, cudaStream_t st) {
+  PP_CUDA(launch_expand(d_src, n_src, d_begin, d_ids, n_events, expand_bufs(ctx, with_events), st));
   ctx->kernels_launched += (n_src <= kSmallMax) ? 1 : 4;
   return PP_OK;
 }
@@ -267,7 +274,7 @@ int batch_async(pp_ctx* ctx, int32_t n_events, const uint64_t* d_ids, const int6
   int grid;
   if ((rc = grid_blocks(ctx, smem, &grid))) return rc;
   PP_CUDA(cudaMemsetAsync(ctx->work.p, 0, sizeof(uint64_t), st));
-  if ((rc = expand(ctx, d_src, n_src, d_begin, n_events, true, st))) return rc;
+  if ((rc = expand(ctx, d_src, n_src, d_begin, d_ids, n_events, true, st))) return rc;
   const WorkDev w = work_desc(ctx, d_src, n_src, true, d_begin, d_ids, d_hits, d_counts, 0);
   return timed_propagate(ctx, true, w, run_params(ctx), grid, 0, smem, st);
 }
@@ -301,7 +308,7 @@ int plain_async(pp_ctx* ctx, int32_t n_events, const uint64_t* h_ids, const int6
     const int64_t n = h_begin[e + 1] - h_begin[e];
     if (n == 0 || h_photons[e] == 0) continue;
     const pp_source* s = d_src + h_begin[e];
-    if ((rc = expand(ctx, s, n, nullptr, 1, false, st))) return rc;
+    if ((rc = expand(ctx, s, n, nullptr, nullptr, 1, false, st))) return rc;
     const WorkDev w = work_desc(ctx, s, n, false, nullptr, nullptr, d_hits + (size_t)e * n_dom,
                                 d_counts + 4 * (size_t)e, (uint32_t)h_ids[e]);
     if ((rc = timed_propagate(ctx, false, w, run, 0, h_photons[e], smem, st))) return rc;
@@ -388,6 +395,7 @@ int with_launch_view(pp_ctx* ctx, const std::function<int(const LaunchView&)>& f
   v.geom = ctx->geom;
   v.run = run_params(ctx);
   v.block_threads = ctx->block_threads;
+  v.variant = kernel_variant(ctx);
   if ((rc = prepare_smem(ctx, &v.smem))) return rc;
   if ((rc = grid_blocks(ctx, v.smem, &v.grid_blocks))) return rc;
   v.err = static_cast<int*>(ctx->err.p);
@@ -475,7 +483,7 @@ int pp_destroy(pp_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   DevBuf* bufs[] = {&ctx->dom, &ctx->str, &ctx->str_range, &ctx->sdom_z, &ctx->sdom_idx,
                     &ctx->clear, &ctx->cell_off, &ctx->cell_list, &ctx->layers, &ctx->off,
-                    &ctx->chunk, &ctx->src_event, &ctx->bsum, &ctx->meta, &ctx->work, &ctx->err,
+                    &ctx->chunk, &ctx->aux, &ctx->bsum, &ctx->meta, &ctx->work, &ctx->err,
                     &ctx->stats,
                     &ctx->s_src, &ctx->s_begin, &ctx->s_ids, &ctx->s_hits, &ctx->s_counts,
                     &ctx->s_misc1, &ctx->s_misc2, &ctx->s_misc3, &ctx->s_misc4};
@@ -744,6 +752,70 @@ int pp_get_launch(const pp_ctx* ctx_c, int32_t* block_threads, int32_t* blocks_p
   return PP_OK;
 }
 
+int pp_autotune_batch(pp_ctx* ctx, int32_t n_events, const uint64_t* d_event_ids,
+                      const int64_t* d_src_begin, const pp_source* d_src, int64_t n_src,
+                      uint64_t* d_hits, uint64_t* d_counts, void* stream, int32_t repeats,
+                      int32_t* best3, float* best_ms) {
+  if (!ctx) return PP_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  if (repeats < 1) repeats = 1;
+  cudaStream_t st = pick_stream(ctx, stream);
+  struct Cand {
+    int bt, bps, refill;
+  };
+  static const Cand cands[] = {
+      {256, 0, 1},  {256, 0, 2},  {256, 0, 4},  {256, 0, 8},  {256, 0, 16}, {256, 0, 32},
+      {256, 5, 4},  {256, 5, 8},  {256, 5, 16}, {256, 6, 4},  {256, 6, 8},  {256, 6, 16},
+      {128, 0, 4},  {128, 0, 8},  {128, 0, 16}, {512, 0, 8},  {512, 0, 16}, {1024, 0, 16}};
+  const int keep_bt = ctx->block_threads, keep_bps = ctx->blocks_per_sm, keep_r = ctx->refill;
+  const bool keep_timing = ctx->timing;
+  ctx->timing = false;
+  cudaEvent_t e0, e1;
+  PP_CUDA(cudaEventCreate(&e0));
+  PP_CUDA(cudaEventCreate(&e1));
+  float best = 3.4e38f;
+  Cand win{keep_bt, keep_bps, keep_r};
+  int rc = PP_OK;
+  for (const Cand& c : cands) {
+    ctx->block_threads = c.bt;
+    ctx->blocks_per_sm = c.bps;
+    ctx->refill = c.refill;
+    // warm-up launch, then the timed ones
+    rc = batch_async(ctx, n_events, d_event_ids, d_src_begin, d_src, n_src, d_hits, d_counts, st);
+    if (rc) break;
+    if (cudaEventRecord(e0, st) != cudaSuccess) { rc = PP_ECUDA; break; }
+    for (int r = 0; r < repeats && !rc; ++r)
+      rc = batch_async(ctx, n_events, d_event_ids, d_src_begin, d_src, n_src, d_hits, d_counts, st);
+    if (rc) break;
+    float ms = 0.f;
+    if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      rc = fail(ctx, PP_ECUDA, "autotune timing failed");
+      break;
+    }
+    ms /= repeats;
+    if (ms < best) {
+      best = ms;
+      win = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->timing = keep_timing;
+  ctx->block_threads = rc ? keep_bt : win.bt;
+  ctx->blocks_per_sm = rc ? keep_bps : win.bps;
+  ctx->refill = rc ? keep_r : win.refill;
+  if (rc) return rc;
+  if (best3) {
+    best3[0] = win.bt;
+    best3[1] = win.bps;
+    best3[2] = win.refill;
+  }
+  if (best_ms) *best_ms = best;
+  return PP_OK;
+}
+
 int pp_set_kernel_timing(pp_ctx* ctx, int32_t enable) {
   if (!ctx) return PP_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
@@ -839,7 +911,7 @@ int pp_debug_trace(pp_ctx* ctx, uint64_t event_id, const pp_source* src, int64_t
   PP_CUDA(cudaMemcpyAsync(ctx->s_src.p, src, sizeof(pp_source) * n_src, cudaMemcpyHostToDevice, st));
   PP_CUDA(cudaMemcpyAsync(ctx->s_misc1.p, photon_ids, 8 * n, cudaMemcpyHostToDevice, st));
   const pp_source* d_src = static_cast<const pp_source*>(ctx->s_src.p);
-  PP_CUDA(launch_expand(d_src, n_src, nullptr, 1, expand_bufs(ctx, false), st));
+  PP_CUDA(launch_expand(d_src, n_src, nullptr, nullptr, 1, expand_bufs(ctx, false), st));
   const WorkDev w = work_desc(ctx, d_src, n_src, false, nullptr, nullptr, nullptr, nullptr,
                               (uint32_t)event_id);
   int* d_out = static_cast<int*>(ctx->s_misc2.p);

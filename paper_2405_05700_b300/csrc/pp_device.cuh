@@ -404,7 +404,7 @@ __device__ __forceinline__ bool birth(Photon& ph, const pp_source& s, const IceD
   return ok;
 }
 
-// a3..a7: one step.  Returns kContinue after a scatter, else the outcome.
+// a3..a7: one step.  Returns kScattered after a scatter, else the outcome.
 __device__ __forceinline__ int photon_step(Photon& ph, const IceDev& I, const GeomDev& G,
                                            const Tables& T, const RunDev& R,
                                            uint32_t& crossings, uint32_t& slow) {
@@ -432,13 +432,12 @@ __device__ __forceinline__ int photon_step(Photon& ph, const IceDev& I, const Ge
   ph.layer = layer;
   ph.tau_a = tau_a;
   if (ph.n >= R.max_steps) return kTruncated;
-  return kContinue;
+  return kScattered;
 }
 
-// Finds the source and event of batch photon index g and fills the photon's
-// identity.  Returns the source index.
-__device__ __forceinline__ int locate(const WorkDev& W, uint32_t chunk_log2, uint64_t g,
-                                      Photon& ph) {
+// Source containing batch photon index g: the last s with off[s] <= g, found
+// inside the range the photon-chunk table gives for g's chunk.
+__device__ __forceinline__ int find_source(const WorkDev& W, uint32_t chunk_log2, uint64_t g) {
   const uint64_t c = g >> chunk_log2;
   int lo = (int)__ldg(W.chunk_src + c), hi = (int)__ldg(W.chunk_src + c + 1);
   while (lo < hi) {
@@ -446,19 +445,71 @@ __device__ __forceinline__ int locate(const WorkDev& W, uint32_t chunk_log2, uin
     if (__ldg(W.off + mid) <= g) lo = mid;
     else hi = mid - 1;
   }
+  return lo;
+}
+
+// Fills the photon's identity (event slot, Philox key word, event-local id)
+// from its source s and its index within that source.
+__device__ __forceinline__ void identify(const WorkDev& W, int s, uint64_t in_src, uint64_t g,
+                                         Photon& ph) {
   uint64_t pid = g;
-  if (W.src_event) {
-    const int e = (int)__ldg(W.src_event + lo);
-    pid = g - __ldg(W.off + __ldg(W.src_begin + e));
-    ph.ev = e;
-    ph.ev_lo = (uint32_t)__ldg(W.event_ids + e);
+  if (W.aux) {
+    const uint4 a = __ldg(reinterpret_cast<const uint4*>(W.aux) + s);
+    pid = ((uint64_t)a.y << 32 | a.x) + in_src;
+    ph.ev_lo = a.z;
+    ph.ev = (int)a.w;
   } else {
     ph.ev = 0;
     ph.ev_lo = W.single_event_lo;
   }
   ph.pid_lo = (uint32_t)pid;
   ph.pid_hi = (uint32_t)(pid >> 32);
-  return lo;
+}
+
+// One photon's identity from its batch index alone.  Returns the source.
+__device__ __forceinline__ int locate(const WorkDev& W, uint32_t chunk_log2, uint64_t g,
+                                      Photon& ph) {
+  const int s = find_source(W, chunk_log2, g);
+  identify(W, s, g - __ldg(W.off + s), g, ph);
+  return s;
+}
+
+// Sources of a warp's claim of consecutive batch photons g0 .. g0 + 31 (lane
+// with rank r takes g0 + r): one warp-uniform search for g0's source s0, one
+// coalesced load of the 32 boundaries off[s0 + 1 .. s0 + 32], and per lane a
+// 5-step shuffle search for how many of them lie at or below its photon.
+// Returns the lane's source; in_src receives the photon's index inside it.
+// Must be called by all 32 lanes; `rank` only matters for lanes that use it.
+__device__ __forceinline__ int locate_claim(const WorkDev& W, uint32_t chunk_log2, uint64_t g0,
+                                            uint32_t rank, uint64_t total, uint64_t& in_src) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int s0 = find_source(W, chunk_log2, g0);
+  const uint64_t off0 = __ldg(W.off + s0);
+  const int sj = s0 + 1 + lane;
+  const uint64_t bj = (sj <= W.n_src) ? __ldg(W.off + sj) : ~0ull;
+  const uint64_t dj = bj - g0;  // > 0: boundary after source s0 + lane, relative to g0
+  const uint32_t kj = dj > 0xffffffffull ? 0xffffffffu : (uint32_t)dj;
+  int pos = 0;
+#pragma unroll
+  for (int step = 16; step >= 1; step >>= 1) {
+    const uint32_t kv = __shfl_sync(full, kj, pos + step - 1);
+    if (kv <= rank) pos += step;
+  }
+  if (__shfl_sync(full, kj, 31) <= rank && pos == 31) pos = 32;
+  const uint32_t kprev = __shfl_sync(full, kj, pos > 0 ? (pos < 32 ? pos - 1 : 31) : 0);
+  if (pos == 32) {  // more than 32 sources in the claim (empty sources): plain search
+    const uint64_t g = g0 + rank;
+    if (g >= total) {  // past the end: a lane with nothing to claim
+      in_src = 0;
+      return s0;
+    }
+    const int s = find_source(W, chunk_log2, g);
+    in_src = g - __ldg(W.off + s);
+    return s;
+  }
+  in_src = (pos == 0) ? (g0 - off0) + rank : (uint64_t)(rank - kprev);
+  return s0 + pos;
 }
 
 // a6: integer tallies.

@@ -25,7 +25,7 @@ constexpr int kSmallItems = 8;
 constexpr int64_t kSmallMax = (int64_t)kSmallThreads * kSmallItems;
 
 // Per-step outcome of a photon (>= 0: the DOM it hit).
-constexpr int kContinue = -100;
+constexpr int kScattered = -100;  // the step ended in a scatter; the photon goes on
 constexpr int kAbsorbed = PP_OUT_ABSORBED;
 constexpr int kEscaped = PP_OUT_ESCAPED;
 constexpr int kTruncated = PP_OUT_TRUNCATED;
@@ -66,14 +66,21 @@ struct GeomDev {
   float R, R2, zlo, zhi;    // world cylinder
 };
 
+// Per-source event record written by the expansion (batch mode): the
+// event-local photon id of the source's first photon, the event id's low word
+// (Philox key) and the event slot (row of the outputs).
+struct SrcAux {
+  unsigned long long base;
+  uint32_t ev_lo;
+  uint32_t ev;
+};
+
 // One propagation launch's work description.
 struct WorkDev {
   const pp_source* src;       // batch sources
   const uint64_t* off;        // [n_src + 1] photon prefix over the batch
   const uint32_t* chunk_src;  // [n_src + 2] first source of each photon chunk
-  const uint32_t* src_event;  // [n_src] event slot of each source (NULL: single event)
-  const int64_t* src_begin;   // [n_events + 1] (batch mode)
-  const uint64_t* event_ids;  // [n_events]     (batch mode)
+  const SrcAux* aux;          // [n_src] event record of each source (NULL: single event)
   const uint64_t* meta;       // [0] total photons, [1] chunk log2
   unsigned long long* work;   // persistent work counter (zeroed before launch)
   unsigned long long* hits;   // [n_events][n_dom]
@@ -98,7 +105,7 @@ size_t tables_smem_bytes(const IceDev& ice, const GeomDev& geom);
 struct ExpandBufs {
   uint64_t* off;          // n_src + 1
   uint32_t* chunk_src;    // n_src + 2
-  uint32_t* src_event;    // n_src (NULL in single-event mode)
+  SrcAux* aux;            // n_src (NULL in single-event mode)
   uint64_t* bsum;         // ceil(n_src / kScanTile)
   uint64_t* meta;         // 2
 };
@@ -106,18 +113,21 @@ struct ExpandBufs {
 // a1: exclusive prefix of n_photons over the sources, photon-chunk table and
 // source -> event map.  src_begin/n_events may be NULL/0 (single event).
 cudaError_t launch_expand(const pp_source* src, int64_t n_src, const int64_t* src_begin,
-                          int n_events, const ExpandBufs& b, cudaStream_t st);
+                          const uint64_t* event_ids, int n_events, const ExpandBufs& b,
+                          cudaStream_t st);
 
 // a2..a8 for the photons of the work description.
 //   persistent = false: one thread per photon, `n_photons_host` photons
 //   persistent = true : grid_blocks persistent blocks with warp refill
+// variant selects the register budget of the persistent kernel: 0 = any block
+// size (up to 64 registers), 5 / 6 = 256-thread blocks, 5 / 6 resident per SM.
 cudaError_t launch_propagate(bool persistent, const IceDev& ice, const GeomDev& geom,
                              const WorkDev& work, const RunDev& run, int block_threads,
                              int grid_blocks, uint64_t n_photons_host, size_t smem,
-                             cudaStream_t st);
+                             cudaStream_t st, int variant = 0);
 
 cudaError_t set_propagate_smem_limit(size_t smem);
-cudaError_t propagate_occupancy(int block_threads, size_t smem, int* blocks_per_sm);
+cudaError_t propagate_occupancy(int block_threads, size_t smem, int variant, int* blocks_per_sm);
 
 cudaError_t launch_trace(const IceDev& ice, const GeomDev& geom, const WorkDev& work,
                          const RunDev& run, const uint64_t* ids, int64_t n, int n_trace,
@@ -146,6 +156,7 @@ struct LaunchView {
   RunDev run;
   int block_threads;
   int grid_blocks;
+  int variant;
   size_t smem;
   int* err;
   unsigned long long* stats;

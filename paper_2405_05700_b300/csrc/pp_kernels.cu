@@ -79,9 +79,22 @@ __device__ __forceinline__ void chunk_entry(const uint64_t* off, int64_t n_src, 
 }
 
 // ---- a1, small batches: one block does scan, maps and chunk table ----------
+// Per-source event record: event slot, event-local photon base, event id.
+__device__ __forceinline__ void write_aux(const uint64_t* off, const int64_t* src_begin,
+                                          const uint64_t* event_ids, int n_events, int64_t s,
+                                          SrcAux* aux) {
+  const uint32_t e = event_of(src_begin, n_events, s);
+  SrcAux a;
+  a.base = off[s] - off[src_begin[e]];
+  a.ev_lo = (uint32_t)event_ids[e];
+  a.ev = e;
+  aux[s] = a;
+}
+
 __global__ void __launch_bounds__(kSmallThreads)
 k_expand_small(const pp_source* __restrict__ src, int64_t n_src,
-               const int64_t* __restrict__ src_begin, int n_events, ExpandBufs b) {
+               const int64_t* __restrict__ src_begin, const uint64_t* __restrict__ event_ids,
+               int n_events, ExpandBufs b) {
   __shared__ uint64_t ws[32];
   __shared__ uint64_t s_total;
   __shared__ uint32_t s_k;
@@ -99,10 +112,7 @@ k_expand_small(const pp_source* __restrict__ src, int64_t n_src,
 #pragma unroll
   for (int i = 0; i < kSmallItems; ++i) {
     const int64_t s = base + i;
-    if (s < n_src) {
-      b.off[s] = pre;
-      if (b.src_event) b.src_event[s] = event_of(src_begin, n_events, s);
-    }
+    if (s < n_src) b.off[s] = pre;
     pre += v[i];
   }
   if (threadIdx.x == 0) {
@@ -116,6 +126,9 @@ k_expand_small(const pp_source* __restrict__ src, int64_t n_src,
   const uint64_t n_chunks = (s_total + (1ull << s_k) - 1) >> s_k;
   for (uint64_t c = threadIdx.x; c <= n_chunks; c += blockDim.x)
     chunk_entry(b.off, n_src, c, s_k, b.chunk_src);
+  if (b.aux)
+    for (int64_t s = threadIdx.x; s < n_src; s += blockDim.x)
+      write_aux(b.off, src_begin, event_ids, n_events, s, b.aux);
 }
 
 // ---- a1, large batches: partial sums, top scan, final pass, chunk table ----
@@ -158,7 +171,6 @@ k_scan_top(uint64_t* __restrict__ bsum, int nb, int64_t n_src, uint64_t* __restr
 
 __global__ void __launch_bounds__(kScanThreads)
 k_scan_final(const pp_source* __restrict__ src, int64_t n_src,
-             const int64_t* __restrict__ src_begin, int n_events,
              const uint64_t* __restrict__ bsum, ExpandBufs b) {
   __shared__ uint64_t ws[32];
   const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
@@ -174,27 +186,26 @@ k_scan_final(const pp_source* __restrict__ src, int64_t n_src,
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     const int64_t s = base + i;
-    if (s < n_src) {
-      b.off[s] = pre;
-      if (b.src_event) b.src_event[s] = event_of(src_begin, n_events, s);
-    }
+    if (s < n_src) b.off[s] = pre;
     pre += v[i];
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) b.off[n_src] = b.meta[0];
 }
 
-__global__ void k_chunks(const uint64_t* __restrict__ off, int64_t n_src,
-                         const uint64_t* __restrict__ meta, uint32_t* __restrict__ chunk_src) {
-  const uint64_t total = meta[0];
-  const uint32_t k = (uint32_t)meta[1];
+// Chunk table and per-source event records, once all offsets are known.
+__global__ void k_finish(int64_t n_src, const int64_t* __restrict__ src_begin,
+                         const uint64_t* __restrict__ event_ids, int n_events, ExpandBufs b) {
+  const uint64_t total = b.meta[0];
+  const uint32_t k = (uint32_t)b.meta[1];
   const uint64_t n_chunks = (total + (1ull << k) - 1) >> k;
   const uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c <= n_chunks) chunk_entry(off, n_src, c, k, chunk_src);
+  if (c <= n_chunks) chunk_entry(b.off, n_src, c, k, b.chunk_src);
+  if (b.aux && (int64_t)c < n_src) write_aux(b.off, src_begin, event_ids, n_events, (int64_t)c, b.aux);
 }
 
 // ---- a2..a8: propagation ---------------------------------------------------
-template <bool kPersistent>
-__global__ void __launch_bounds__(1024)
+template <bool kPersistent, int kMinBlocks>
+__global__ void __launch_bounds__(kMinBlocks > 0 ? 256 : 1024, kMinBlocks > 0 ? kMinBlocks : 1)
 k_propagate(IceDev I, GeomDev G, WorkDev W, RunDev R, uint64_t n_plain) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Tables T = stage_tables(smem, I, G);
@@ -214,7 +225,7 @@ k_propagate(IceDev I, GeomDev G, WorkDev W, RunDev R, uint64_t n_plain) {
     uint32_t crossings = 0, slow = 0;
     for (;;) {
       const int out = photon_step(ph, I, G, T, R, crossings, slow);
-      if (out != kContinue) {
+      if (out != kScattered) {
         tally(W, G.n_dom, ph, out);
         return;
       }
@@ -235,10 +246,13 @@ k_propagate(IceDev I, GeomDev G, WorkDev W, RunDev R, uint64_t n_plain) {
         if (lane == 0) base = atomicAdd(W.work, (unsigned long long)n_idle);
         base = __shfl_sync(kFull, base, 0);
         if (base + (unsigned long long)n_idle >= total) exhausted = true;
-        if (!alive) {
-          const uint64_t g = base + __popc(idle & ((1u << lane) - 1u));
-          if (g < total) {
-            const int s = locate(W, k, g, ph);
+        if (base < total) {
+          const uint32_t rank = __popc(idle & ((1u << lane) - 1u));
+          uint64_t in_src = 0;
+          const int s = locate_claim(W, k, base, rank, total, in_src);
+          const uint64_t g = base + rank;
+          if (!alive && g < total) {
+            identify(W, s, in_src, g, ph);
             const pp_source src = W.src[s];
             alive = birth(ph, src, I, R);
             births += 1;
@@ -252,7 +266,7 @@ k_propagate(IceDev I, GeomDev G, WorkDev W, RunDev R, uint64_t n_plain) {
       }
       if (alive) {
         const int out = photon_step(ph, I, G, T, R, crossings, slow);
-        if (out != kContinue) {
+        if (out != kScattered) {
           tally(W, G.n_dom, ph, out);
           steps += ph.n;
           alive = false;
@@ -312,12 +326,12 @@ __global__ void k_trace(IceDev I, GeomDev G, WorkDev W, RunDev R, const uint64_t
   uint32_t crossings = 0, slow = 0;
   for (;;) {
     const int out = photon_step(ph, I, G, T, R, crossings, slow);
-    if ((out == kContinue || out == kTruncated) && tr && (int)ph.n <= n_trace) {
+    if ((out == kScattered || out == kTruncated) && tr && (int)ph.n <= n_trace) {
       tr[3 * (ph.n - 1) + 0] = ph.px;
       tr[3 * (ph.n - 1) + 1] = ph.py;
       tr[3 * (ph.n - 1) + 2] = ph.pz;
     }
-    if (out != kContinue) {
+    if (out != kScattered) {
       outcome[i] = out;
       n_steps[i] = ph.n;
       return;
@@ -367,49 +381,62 @@ size_t tables_smem_bytes(const IceDev& ice, const GeomDev& geom) {
 }
 
 cudaError_t launch_expand(const pp_source* src, int64_t n_src, const int64_t* src_begin,
-                          int n_events, const ExpandBufs& b, cudaStream_t st) {
+                          const uint64_t* event_ids, int n_events, const ExpandBufs& b,
+                          cudaStream_t st) {
   if (n_src <= kSmallMax) {
-    k_expand_small<<<1, kSmallThreads, 0, st>>>(src, n_src, src_begin, n_events, b);
+    k_expand_small<<<1, kSmallThreads, 0, st>>>(src, n_src, src_begin, event_ids, n_events, b);
     return cudaGetLastError();
   }
   const int nb = (int)((n_src + kScanTile - 1) / kScanTile);
   k_scan_partial<<<nb, kScanThreads, 0, st>>>(src, n_src, b.bsum);
   k_scan_top<<<1, kTopThreads, 0, st>>>(b.bsum, nb, n_src, b.meta);
-  k_scan_final<<<nb, kScanThreads, 0, st>>>(src, n_src, src_begin, n_events, b.bsum, b);
+  k_scan_final<<<nb, kScanThreads, 0, st>>>(src, n_src, b.bsum, b);
   const int64_t nc = n_src + 2;
-  k_chunks<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(b.off, n_src, b.meta, b.chunk_src);
+  k_finish<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(n_src, src_begin, event_ids, n_events, b);
   return cudaGetLastError();
 }
 
 cudaError_t set_propagate_smem_limit(size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(k_propagate<true>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_propagate<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
-  if (e != cudaSuccess) return e;
+  const void* fns[] = {(const void*)k_propagate<true, 0>, (const void*)k_propagate<true, 5>,
+                       (const void*)k_propagate<true, 6>, (const void*)k_propagate<false, 0>};
+  cudaError_t e;
+  for (const void* f : fns) {
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   e = cudaFuncSetAttribute(k_trace, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_first_hit, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)smem);
 }
 
-cudaError_t propagate_occupancy(int block_threads, size_t smem, int* blocks_per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_propagate<true>,
+cudaError_t propagate_occupancy(int block_threads, size_t smem, int variant, int* blocks_per_sm) {
+  if (variant == 5)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_propagate<true, 5>, 256,
+                                                         smem);
+  if (variant == 6)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_propagate<true, 6>, 256,
+                                                         smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_propagate<true, 0>,
                                                        block_threads, smem);
 }
 
 cudaError_t launch_propagate(bool persistent, const IceDev& ice, const GeomDev& geom,
                              const WorkDev& work, const RunDev& run, int block_threads,
                              int grid_blocks, uint64_t n_photons_host, size_t smem,
-                             cudaStream_t st) {
+                             cudaStream_t st, int variant) {
   if (persistent) {
-    k_propagate<true><<<grid_blocks, block_threads, smem, st>>>(ice, geom, work, run, 0);
+    if (variant == 5)
+      k_propagate<true, 5><<<grid_blocks, 256, smem, st>>>(ice, geom, work, run, 0);
+    else if (variant == 6)
+      k_propagate<true, 6><<<grid_blocks, 256, smem, st>>>(ice, geom, work, run, 0);
+    else
+      k_propagate<true, 0><<<grid_blocks, block_threads, smem, st>>>(ice, geom, work, run, 0);
   } else {
     if (n_photons_host == 0) return cudaSuccess;
     const uint64_t nb = (n_photons_host + block_threads - 1) / block_threads;
-    k_propagate<false><<<(unsigned)nb, block_threads, smem, st>>>(ice, geom, work, run,
-                                                                   n_photons_host);
+    k_propagate<false, 0><<<(unsigned)nb, block_threads, smem, st>>>(ice, geom, work, run,
+                                                                      n_photons_host);
   }
   return cudaGetLastError();
 }

@@ -76,20 +76,18 @@ extern "C" int pp_propagate_noalloc(pp_ctx* ctx, uint64_t event_id, const pp_sou
     ppk::ExpandBufs b;
     b.off = reinterpret_cast<uint64_t*>(base + kOffAt);
     b.chunk_src = reinterpret_cast<uint32_t*>(base + kChunkAt);
-    b.src_event = nullptr;
+    b.aux = nullptr;
     b.bsum = reinterpret_cast<uint64_t*>(base + kBsumAt);
     b.meta = reinterpret_cast<uint64_t*>(base + kMetaAt);
     unsigned long long* work = reinterpret_cast<unsigned long long*>(base + kWorkAt);
     e = cudaMemsetAsync(work, 0, sizeof(uint64_t), st);  // the counter starts at 0 each call
-    if (e == cudaSuccess) e = ppk::launch_expand(d_src, n_src, nullptr, 1, b, st);
+    if (e == cudaSuccess) e = ppk::launch_expand(d_src, n_src, nullptr, nullptr, 1, b, st);
     if (e != cudaSuccess) return v.cuda_fail(e, "noalloc expansion");
     ppk::WorkDev w{};
     w.src = d_src;
     w.off = b.off;
     w.chunk_src = b.chunk_src;
-    w.src_event = nullptr;
-    w.src_begin = nullptr;
-    w.event_ids = nullptr;
+    w.aux = nullptr;
     w.meta = b.meta;
     w.work = work;
     w.hits = reinterpret_cast<unsigned long long*>(d_hits);
@@ -99,7 +97,7 @@ extern "C" int pp_propagate_noalloc(pp_ctx* ctx, uint64_t event_id, const pp_sou
     w.n_src = (int)n_src;
     w.single_event_lo = (uint32_t)event_id;
     e = ppk::launch_propagate(true, v.ice, v.geom, w, v.run, v.block_threads, v.grid_blocks, 0,
-                              v.smem, st);
+                              v.smem, st, v.variant);
     if (e != cudaSuccess) return v.cuda_fail(e, "noalloc propagation");
     return PP_OK;
   });

@@ -64,6 +64,7 @@ _SIGS = {
     "pp_propagate_noalloc": [_vp, _u64, _vp, _i64, _vp, _vp, _vp],
     "pp_sync": [_vp, _vp],
     "pp_set_launch": [_vp, _i32, _i32, _i32],
+    "pp_autotune_batch": [_vp, _i32, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _i32, _vp, _vp],
     "pp_get_launch": [_vp, _vp, _vp, _vp, _vp],
     "pp_get_world": [_vp, _vp],
     "pp_set_kernel_timing": [_vp, _i32],
@@ -195,6 +196,17 @@ def pp_set_launch(ctx, block_threads=0, blocks_per_sm=0, refill_threshold=0):
     return _call("pp_set_launch", ctx, block_threads, blocks_per_sm, refill_threshold)
 
 
+def pp_autotune_batch(ctx, n_events, d_event_ids, d_src_begin, d_src, n_src, d_hits, d_counts,
+                      stream=None, repeats=2):
+    """-> ((block_threads, blocks_per_sm, refill_threshold), best_ms)"""
+    best = (C.c_int32 * 3)()
+    ms = C.c_float()
+    _call("pp_autotune_batch", ctx, n_events, _ptr(d_event_ids), _ptr(d_src_begin), _ptr(d_src),
+          n_src, _ptr(d_hits), _ptr(d_counts), _ptr(stream), repeats, C.addressof(best),
+          C.addressof(ms))
+    return tuple(best), ms.value
+
+
 def pp_get_launch(ctx):
     v = [C.c_int32() for _ in range(4)]
     _call("pp_get_launch", ctx, *[C.addressof(x) for x in v])
@@ -219,11 +231,11 @@ def pp_get_kernel_time(ctx):
 
 
 def pp_get_path_stats(ctx):
-    """-> (steps, layer crossings, photons born) counted by the persistent
-    kernel since the last call."""
+    """-> (steps, layer crossings, photons born, steps with a string search)
+    counted by the persistent kernel since the last call."""
     out = np.zeros(4, np.uint64)
     _call("pp_get_path_stats", ctx, _ptr(out))
-    return int(out[0]), int(out[1]), int(out[2])
+    return int(out[0]), int(out[1]), int(out[2]), int(out[3])
 
 
 def pp_debug_philox(ctx, ctr, key, out, n):

@@ -253,10 +253,34 @@ def test_launch_shape_does_not_change_results(full):
     b = W.events_full(n_events=15, seed=23)
     ref = full.propagate_batch(b)
     try:
-        for bt, bps, refill in [(128, 1, 1), (512, 2, 32), (1024, 0, 16), (256, 3, 4)]:
+        for bt, bps, refill in [(128, 1, 1), (512, 2, 32), (1024, 0, 16), (256, 3, 4),
+                                (256, 5, 8), (256, 6, 16)]:
             full.set_launch(bt, bps, refill)
             h, c = full.propagate_batch(b)
             assert np.array_equal(h, ref[0]) and np.array_equal(c, ref[1])
+    finally:
+        full.set_launch(256, 0, 8)
+
+
+def test_autotuner_picks_a_listed_setting_and_keeps_results(full, pp):
+    import torch
+    b = W.events_full(n_events=30, seed=24)
+    ref_h, ref_c = full.propagate_batch(b)
+    dev = torch.device("cuda", 0)
+    src = np.ascontiguousarray(b.sources)
+    d_src = torch.from_numpy(src.view(np.uint8).copy()).to(dev)
+    d_ids = torch.from_numpy(b.event_ids.astype(np.int64)).to(dev)
+    d_beg = torch.from_numpy(b.src_begin.astype(np.int64)).to(dev)
+    d_h = torch.zeros((b.n_events, 5160), dtype=torch.int64, device=dev)
+    d_c = torch.zeros((b.n_events, 4), dtype=torch.int64, device=dev)
+    try:
+        best, ms = pp.pp_autotune_batch(full.ctx, b.n_events, d_ids, d_beg, d_src, len(src), d_h,
+                                        d_c, None, 1)
+        pp.pp_sync(full.ctx)
+        assert best[0] in (128, 256, 512, 1024) and 1 <= best[2] <= 32 and ms > 0
+        assert full.get_launch()[:3] == best
+        assert np.array_equal(d_h.cpu().numpy().astype(np.uint64), ref_h)
+        assert np.array_equal(d_c.cpu().numpy().astype(np.uint64), ref_c)
     finally:
         full.set_launch(256, 0, 8)
 
