@@ -10,10 +10,12 @@ synthetic (seeded generators), resident in HBM before the timed region.
 
 A step is one pass of the whole path over the batch: source expansion, then
 the persistent propagation kernel over all events' photons (birth, layer walk,
-DOM hit test, escape, scattering, tallies).  `value` is photons/s of that
-batched path; the plain per-event launch path is timed beside it, the
-end-to-end number goes through the host-buffer C entry point, and the CPU
-oracle is timed on a bounded sample of the same workload.
+DOM hit test, escape, scattering, tallies), replayed as a CUDA graph after the
+autotuner picked the launch settings.  `value` is photons/s of that batched
+path; the plain per-event launch path is timed beside it, the end-to-end
+number goes through the host-buffer C entry point, one 1e10-photon event runs
+in 1e9-photon chunks, and the CPU oracle is timed on a bounded sample of the
+same workload.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -66,6 +68,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--large-photons", type=int, default=10_000_000_000)
+    ap.add_argument("--large-chunk", type=int, default=1_000_000_000)
     ap.add_argument("--cpu-sample-photons", type=int, default=10_000_000)
     ap.add_argument("--ref-sample-photons", type=int, default=500_000)
     ap.add_argument("--events", type=int, default=1000,
@@ -252,6 +256,7 @@ def run_ours(args):
         pp.pp_propagate_batch_async(ctx, E, d_ids, d_begin, d_src, n_src, d_hits, d_counts,
                                     stream.cuda_stream)
 
+    pp.pp_set_graphs(ctx, True)
     tuned = None
     if not args.no_autotune:
         tuned = pp.pp_autotune_batch(ctx, E, d_ids, d_begin, d_src, n_src, d_hits, d_counts,
@@ -262,8 +267,8 @@ def run_ours(args):
     pp.pp_get_kernel_time(ctx)
     pp.pp_get_path_stats(ctx)
 
-    # ---- timed region: K steps, L2 flushed between steps outside the events
-    pp.pp_set_kernel_timing(ctx, True)
+    # ---- timed region: K steps (CUDA-graph replays of the captured step), L2
+    # flushed between steps outside the timed events
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
@@ -287,7 +292,18 @@ def run_ours(args):
     clocks.stop()
     pp.pp_sync(ctx, stream.cuda_stream)
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    kern_ms, n_timed, n_kernels = pp.pp_get_kernel_time(ctx)
+    _, _, n_kernels = pp.pp_get_kernel_time(ctx)       # kernels the replays launched
+    pp.pp_get_path_stats(ctx)
+
+    # ---- the same K steps launched directly, with CUDA events around the
+    # propagation kernel on its stream: the roofline's kernel time and units
+    pp.pp_set_graphs(ctx, False)
+    pp.pp_set_kernel_timing(ctx, True)
+    for _ in range(args.steps):
+        flush.zero_()
+        step()
+    pp.pp_sync(ctx, stream.cuda_stream)
+    kern_ms, n_timed, _ = pp.pp_get_kernel_time(ctx)
     pp.pp_set_kernel_timing(ctx, False)
     steps_n, cross_n, births_n, slow_n = pp.pp_get_path_stats(ctx)
     total_ms = sum(step_ms)
@@ -347,6 +363,37 @@ def run_ours(args):
     h2d = src_np.nbytes + h_ids.nbytes + h_begin.nbytes
     d2h = pin_hits.numel() * 8 + pin_counts.numel() * 8
 
+    # ---- one huge event (1e7 GeV bundle of 20 muons, 1e10 photons) in fixed
+    # photon chunks accumulated into one result
+    large = None
+    pp.pp_get_path_stats(ctx)
+    if args.large_photons > 0:
+        lb = W.event_large(total_photons=args.large_photons)
+        lsrc = np.ascontiguousarray(lb.sources)
+        d_lsrc = torch.from_numpy(lsrc.view(np.uint8).copy()).to(dev)
+        d_lh = torch.zeros(n_dom, dtype=torch.int64, device=dev)
+        d_lc = torch.zeros(4, dtype=torch.int64, device=dev)
+        ltot = lb.total_photons()
+        cuts = list(range(0, ltot, args.large_chunk)) + [ltot]
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for j in range(len(cuts) - 1):
+            pp.pp_propagate_range_async(ctx, 0, d_lsrc, len(lsrc), cuts[j], cuts[j + 1], j > 0,
+                                        d_lh, d_lc, stream.cuda_stream)
+        e1.record(stream)
+        pp.pp_sync(ctx, stream.cuda_stream)
+        lms = e0.elapsed_time(e1)
+        lsteps = pp.pp_get_path_stats(ctx)[0]
+        lh = d_lh.cpu().numpy()
+        lc = d_lc.cpu().numpy()
+        large = {"photons": ltot, "sources": len(lsrc), "chunks": len(cuts) - 1,
+                 "chunk_photons": args.large_chunk, "seconds": lms * 1e-3,
+                 "value": ltot / (lms * 1e-3), "unit": UNIT,
+                 "steps_per_photon": lsteps / ltot, "steps_per_s": lsteps / (lms * 1e-3),
+                 "conserved": bool(int(lh.sum() + lc[0] + lc[1]) == ltot)}
+        pp.pp_get_kernel_time(ctx)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(batch, args.cpu_sample_photons)
@@ -376,6 +423,7 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "events": E, "sources_per_step": n_src,
                    "photons_per_step": photons, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed (256 MB write) between steps, outside the timed events",
+                   "timed_launch": "CUDA-graph replay of the captured step",
                    "launch": dict(zip(("block_threads", "blocks_per_sm", "refill_threshold",
                                        "grid_blocks"), prop.get_launch()))},
         "plain": {"value": plain_value, "unit": UNIT,
@@ -392,6 +440,7 @@ def run_ours(args):
                      "string_search_frac": slow_n / max(1, steps_n)},
         "autotune": {"best": tuned[0], "best_ms": tuned[1]} if tuned else None,
         "steps_per_s": steps_per_launch / (kern_avg_ms * 1e-3),
+        "large_event": large,
         "e2e": {"value": photons * args.e2e_steps / e2e_s if e2e_s else None, "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(n_kernels),

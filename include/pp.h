@@ -196,6 +196,21 @@ int pp_propagate_plain_async(pp_ctx* ctx, int32_t n_events, const uint64_t* h_ev
 int pp_propagate_noalloc(pp_ctx* ctx, uint64_t event_id, const pp_source* d_src, int64_t n_src,
                          uint64_t* d_hits, uint64_t* d_counts, void* stream);
 
+/* Photons [photon_begin, photon_end) of one event (per-event photon ids, see
+ * pp_propagate) through the persistent kernel, on device-resident data.  With
+ * accumulate = 0 the outputs are overwritten first, otherwise the tallies are
+ * added to them.  Because every photon's random numbers depend only on (seed,
+ * event id, photon id), an event split into ranges -- in any order, over any
+ * number of calls -- gives exactly the result of one pass: this is how a huge
+ * event (paper Sec. 3: power-law energies make single events arbitrarily
+ * large) is processed in fixed-size chunks with bounded launch times, and how
+ * an interrupted event resumes at its next chunk.
+ *   d_src[n_src], d_hits[n_dom], d_counts[4] device buffers; stream as above */
+int pp_propagate_range_async(pp_ctx* ctx, uint64_t event_id, const pp_source* d_src,
+                             int64_t n_src, uint64_t photon_begin, uint64_t photon_end,
+                             int32_t accumulate, uint64_t* d_hits, uint64_t* d_counts,
+                             void* stream);
+
 /* Waits for `stream` (NULL: the context's stream) and reports a device error
  * flag raised since the last pp_sync.  Errors: PP_ECUDA, PP_EDEVICE. */
 int pp_sync(pp_ctx* ctx, void* stream);
@@ -224,6 +239,16 @@ int pp_autotune_batch(pp_ctx* ctx, int32_t n_events, const uint64_t* d_event_ids
 /* Reads back the launch settings in use (any pointer may be NULL). */
 int pp_get_launch(const pp_ctx* ctx, int32_t* block_threads, int32_t* blocks_per_sm,
                   int32_t* refill_threshold, int32_t* grid_blocks);
+
+/* CUDA graphs for pp_propagate_batch_async.  While enabled, the first call with
+ * a given shape (event and source counts, device pointers, stream, launch
+ * settings) is captured into a CUDA graph -- output clearing, source expansion
+ * and the persistent propagation launch -- and later calls with the same shape
+ * replay it with one cudaGraphLaunch.  Up to 8 graphs are kept; loading
+ * geometry or ice, growing the context's scratch, or disabling graphs drops
+ * them.  Calls on the legacy default stream, or with kernel timing enabled,
+ * are launched directly. */
+int pp_set_graphs(pp_ctx* ctx, int32_t enable);
 
 /* Kernel timing for benchmarks.  While enabled, the library records a pair of
  * CUDA events on the launching stream around every propagation kernel launch.

@@ -49,6 +49,16 @@ struct pp_ctx {
   int blocks_per_sm = 0;  // 0: occupancy maximum
   int refill = 8;
 
+  // CUDA graphs of the batched path, keyed by everything a capture bakes in
+  struct GraphEntry {
+    uint64_t key[12];
+    cudaGraphExec_t exec;
+    int kernels;
+  };
+  bool graphs = false;
+  uint64_t epoch = 0;  // bumped when a device buffer or table the kernels read moves
+  std::vector<GraphEntry> graph_cache;
+
   // benchmark timing of propagation launches
   bool timing = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
@@ -78,6 +88,7 @@ int cuda_fail_ctx(pp_ctx* c, cudaError_t e, const char* where) { return cuda_fai
 
 int ensure(pp_ctx* ctx, DevBuf& b, size_t bytes) {
   if (bytes <= b.cap && b.p) return PP_OK;
+  ctx->epoch += 1;  // captured graphs hold the old address
   // the old buffer may still be read by queued work on the context's stream
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
@@ -214,6 +225,8 @@ WorkDev work_desc(pp_ctx* ctx, const pp_source* d_src, int64_t n_src, bool with_
   w.stats = static_cast<unsigned long long*>(ctx->stats.p);
   w.n_src = (int)n_src;
   w.single_event_lo = single_ev_lo;
+  w.g_begin = 0;
+  w.g_end = ~0ull;
   return w;
 }
 
@@ -265,17 +278,87 @@ int batch_async(pp_ctx* ctx, int32_t n_events, const uint64_t* d_ids, const int6
   if (!d_ids || !d_begin || !d_hits || !d_counts || (n_src > 0 && !d_src))
     return fail(ctx, PP_EINVAL, "null device pointer");
   const size_t hb = sizeof(uint64_t) * (size_t)n_events * ctx->geom.n_dom;
-  if (hb) PP_CUDA(cudaMemsetAsync(d_hits, 0, hb, st));
-  PP_CUDA(cudaMemsetAsync(d_counts, 0, sizeof(uint64_t) * 4 * (size_t)n_events, st));
-  if (n_src == 0) return PP_OK;
-  if ((rc = ensure_scratch(ctx, n_src, true))) return rc;
+  size_t smem = 0;
+  int grid = 0;
+  if (n_src > 0) {
+    if ((rc = ensure_scratch(ctx, n_src, true))) return rc;
+    if ((rc = prepare_smem(ctx, &smem))) return rc;
+    if ((rc = grid_blocks(ctx, smem, &grid))) return rc;
+  }
+  auto enqueue = [&]() -> int {
+    if (hb) PP_CUDA(cudaMemsetAsync(d_hits, 0, hb, st));
+    PP_CUDA(cudaMemsetAsync(d_counts, 0, sizeof(uint64_t) * 4 * (size_t)n_events, st));
+    if (n_src == 0) return PP_OK;
+    PP_CUDA(cudaMemsetAsync(ctx->work.p, 0, sizeof(uint64_t), st));
+    int r;
+    if ((r = expand(ctx, d_src, n_src, d_begin, d_ids, n_events, true, st))) return r;
+    const WorkDev w = work_desc(ctx, d_src, n_src, true, d_begin, d_ids, d_hits, d_counts, 0);
+    return timed_propagate(ctx, true, w, run_params(ctx), grid, 0, smem, st);
+  };
+  if (!ctx->graphs || ctx->timing || st == nullptr) return enqueue();
+  // CUDA graph: capture this exact launch sequence once, replay it afterwards
+  const uint64_t key[12] = {(uint64_t)n_events, (uint64_t)n_src, (uint64_t)d_ids, (uint64_t)d_begin,
+                            (uint64_t)d_src, (uint64_t)d_hits, (uint64_t)d_counts, (uint64_t)st,
+                            ctx->epoch, (uint64_t)ctx->block_threads,
+                            (uint64_t)ctx->blocks_per_sm, (uint64_t)ctx->refill};
+  for (const auto& g : ctx->graph_cache) {
+    if (std::memcmp(g.key, key, sizeof(key)) == 0) {
+      PP_CUDA(cudaGraphLaunch(g.exec, st));
+      ctx->kernels_launched += g.kernels;
+      return PP_OK;
+    }
+  }
+  PP_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  const uint64_t k0 = ctx->kernels_launched;
+  rc = enqueue();
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(st, &graph);
+  if (rc || ec != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc ? rc : cuda_fail(ctx, ec, "cudaStreamEndCapture");
+  }
+  pp_ctx::GraphEntry g;
+  std::memcpy(g.key, key, sizeof(key));
+  g.kernels = (int)(ctx->kernels_launched - k0);
+  const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) return cuda_fail(ctx, ei, "cudaGraphInstantiate");
+  if (ctx->graph_cache.size() >= 8) {
+    cudaGraphExecDestroy(ctx->graph_cache.front().exec);
+    ctx->graph_cache.erase(ctx->graph_cache.begin());
+  }
+  ctx->graph_cache.push_back(g);
+  PP_CUDA(cudaGraphLaunch(g.exec, st));  // the capture only recorded the work
+  return PP_OK;
+}
+
+// Photons [g0, g1) of one event through the persistent kernel, optionally
+// adding to the outputs (the lock is held by the caller).
+int range_async(pp_ctx* ctx, uint64_t event_id, const pp_source* d_src, int64_t n_src,
+                uint64_t g0, uint64_t g1, bool accumulate, uint64_t* d_hits, uint64_t* d_counts,
+                cudaStream_t st) {
+  int rc;
+  if ((rc = check_loaded(ctx))) return rc;
+  if (n_src < 0 || n_src > kMaxSources || g1 < g0)
+    return fail(ctx, PP_EINVAL, "need 0 <= n_src <= 33554432 and photon_begin <= photon_end");
+  if (!d_hits || !d_counts || (n_src > 0 && !d_src)) return fail(ctx, PP_EINVAL, "null pointer");
+  if (!accumulate) {
+    if (ctx->geom.n_dom)
+      PP_CUDA(cudaMemsetAsync(d_hits, 0, sizeof(uint64_t) * (size_t)ctx->geom.n_dom, st));
+    PP_CUDA(cudaMemsetAsync(d_counts, 0, sizeof(uint64_t) * 4, st));
+  }
+  if (n_src == 0 || g1 == g0) return PP_OK;
+  if ((rc = ensure_scratch(ctx, n_src, false))) return rc;
   size_t smem;
   if ((rc = prepare_smem(ctx, &smem))) return rc;
   int grid;
   if ((rc = grid_blocks(ctx, smem, &grid))) return rc;
   PP_CUDA(cudaMemsetAsync(ctx->work.p, 0, sizeof(uint64_t), st));
-  if ((rc = expand(ctx, d_src, n_src, d_begin, d_ids, n_events, true, st))) return rc;
-  const WorkDev w = work_desc(ctx, d_src, n_src, true, d_begin, d_ids, d_hits, d_counts, 0);
+  if ((rc = expand(ctx, d_src, n_src, nullptr, nullptr, 1, false, st))) return rc;
+  WorkDev w = work_desc(ctx, d_src, n_src, false, nullptr, nullptr, d_hits, d_counts,
+                        (uint32_t)event_id);
+  w.g_begin = g0;
+  w.g_end = g1;
   return timed_propagate(ctx, true, w, run_params(ctx), grid, 0, smem, st);
 }
 
@@ -314,6 +397,12 @@ int plain_async(pp_ctx* ctx, int32_t n_events, const uint64_t* h_ids, const int6
     if ((rc = timed_propagate(ctx, false, w, run, 0, h_photons[e], smem, st))) return rc;
   }
   return PP_OK;
+}
+
+void drop_graphs(pp_ctx* ctx) {
+  for (auto& g : ctx->graph_cache) cudaGraphExecDestroy(g.exec);
+  ctx->graph_cache.clear();
+  ctx->epoch += 1;
 }
 
 int sync_and_check(pp_ctx* ctx, cudaStream_t st) {
@@ -487,6 +576,7 @@ int pp_destroy(pp_ctx* ctx) {
                     &ctx->stats,
                     &ctx->s_src, &ctx->s_begin, &ctx->s_ids, &ctx->s_hits, &ctx->s_counts,
                     &ctx->s_misc1, &ctx->s_misc2, &ctx->s_misc3, &ctx->s_misc4};
+  drop_graphs(ctx);
   for (DevBuf* b : bufs) release(*b);
   for (auto& pr : ctx->pending) {
     cudaEventDestroy(pr.first);
@@ -630,6 +720,7 @@ int pp_load_geometry(pp_ctx* ctx, const float* xyz, const int32_t* string_id, in
   G.zlo = (float)zlo;
   G.zhi = (float)zhi;
   ctx->geom_loaded = true;
+  drop_graphs(ctx);
   return PP_OK;
 }
 
@@ -666,6 +757,7 @@ int pp_load_ice(pp_ctx* ctx, const float* b_e, const float* a, int32_t n_layers,
   I.c4 = (float)(1.0 + gd * gd);
   I.c5 = gd != 0.0 ? (float)(1.0 / (2.0 * gd)) : 0.f;
   ctx->ice_loaded = true;
+  drop_graphs(ctx);
   return PP_OK;
 }
 
@@ -707,6 +799,17 @@ int pp_propagate_plain_async(pp_ctx* ctx, int32_t n_events, const uint64_t* h_ev
   PP_CUDA(cudaSetDevice(ctx->cfg.device));
   return plain_async(ctx, n_events, h_event_ids, h_src_begin, h_event_photons, d_src, d_hits,
                      d_counts, pick_stream(ctx, stream));
+}
+
+int pp_propagate_range_async(pp_ctx* ctx, uint64_t event_id, const pp_source* d_src,
+                             int64_t n_src, uint64_t photon_begin, uint64_t photon_end,
+                             int32_t accumulate, uint64_t* d_hits, uint64_t* d_counts,
+                             void* stream) {
+  if (!ctx) return PP_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  return range_async(ctx, event_id, d_src, n_src, photon_begin, photon_end, accumulate != 0,
+                     d_hits, d_counts, pick_stream(ctx, stream));
 }
 
 int pp_sync(pp_ctx* ctx, void* stream) {
@@ -769,8 +872,9 @@ int pp_autotune_batch(pp_ctx* ctx, int32_t n_events, const uint64_t* d_event_ids
       {256, 5, 4},  {256, 5, 8},  {256, 5, 16}, {256, 6, 4},  {256, 6, 8},  {256, 6, 16},
       {128, 0, 4},  {128, 0, 8},  {128, 0, 16}, {512, 0, 8},  {512, 0, 16}, {1024, 0, 16}};
   const int keep_bt = ctx->block_threads, keep_bps = ctx->blocks_per_sm, keep_r = ctx->refill;
-  const bool keep_timing = ctx->timing;
+  const bool keep_timing = ctx->timing, keep_graphs = ctx->graphs;
   ctx->timing = false;
+  ctx->graphs = false;
   cudaEvent_t e0, e1;
   PP_CUDA(cudaEventCreate(&e0));
   PP_CUDA(cudaEventCreate(&e1));
@@ -803,6 +907,7 @@ int pp_autotune_batch(pp_ctx* ctx, int32_t n_events, const uint64_t* d_event_ids
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   ctx->timing = keep_timing;
+  ctx->graphs = keep_graphs;
   ctx->block_threads = rc ? keep_bt : win.bt;
   ctx->blocks_per_sm = rc ? keep_bps : win.bps;
   ctx->refill = rc ? keep_r : win.refill;
@@ -813,6 +918,15 @@ int pp_autotune_batch(pp_ctx* ctx, int32_t n_events, const uint64_t* d_event_ids
     best3[2] = win.refill;
   }
   if (best_ms) *best_ms = best;
+  return PP_OK;
+}
+
+int pp_set_graphs(pp_ctx* ctx, int32_t enable) {
+  if (!ctx) return PP_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  ctx->graphs = enable != 0;
+  if (!ctx->graphs) drop_graphs(ctx);
   return PP_OK;
 }
 

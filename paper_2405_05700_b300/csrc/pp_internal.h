@@ -89,6 +89,7 @@ struct WorkDev {
   unsigned long long* stats;  // [4] steps, layer crossings, births, 0 (persistent kernel)
   int n_src;
   uint32_t single_event_lo;   // event id (low word) in single-event mode
+  uint64_t g_begin, g_end;    // persistent kernel: batch photon range to run
 };
 
 struct RunDev {

@@ -238,20 +238,22 @@ k_propagate(IceDev I, GeomDev G, WorkDev W, RunDev R, uint64_t n_plain) {
     bool exhausted = false;
     uint32_t crossings = 0, births = 0, slow = 0;
     uint64_t steps = 0;
+    // photons [g_begin, end) of the batch: claims count from g_begin
+    const uint64_t end = total < W.g_end ? total : W.g_end;
     for (;;) {
       const unsigned idle = __ballot_sync(kFull, !alive);
       const int n_idle = __popc(idle);
       if (!exhausted && n_idle >= R.refill) {
         unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(W.work, (unsigned long long)n_idle);
+        if (lane == 0) base = W.g_begin + atomicAdd(W.work, (unsigned long long)n_idle);
         base = __shfl_sync(kFull, base, 0);
-        if (base + (unsigned long long)n_idle >= total) exhausted = true;
-        if (base < total) {
+        if (base + (unsigned long long)n_idle >= end) exhausted = true;
+        if (base < end) {
           const uint32_t rank = __popc(idle & ((1u << lane) - 1u));
           uint64_t in_src = 0;
-          const int s = locate_claim(W, k, base, rank, total, in_src);
+          const int s = locate_claim(W, k, base, rank, end, in_src);
           const uint64_t g = base + rank;
-          if (!alive && g < total) {
+          if (!alive && g < end) {
             identify(W, s, in_src, g, ph);
             const pp_source src = W.src[s];
             alive = birth(ph, src, I, R);

@@ -96,6 +96,8 @@ extern "C" int pp_propagate_noalloc(pp_ctx* ctx, uint64_t event_id, const pp_sou
     w.stats = v.stats;
     w.n_src = (int)n_src;
     w.single_event_lo = (uint32_t)event_id;
+    w.g_begin = 0;
+    w.g_end = ~0ull;
     e = ppk::launch_propagate(true, v.ice, v.geom, w, v.run, v.block_threads, v.grid_blocks, 0,
                               v.smem, st, v.variant);
     if (e != cudaSuccess) return v.cuda_fail(e, "noalloc propagation");

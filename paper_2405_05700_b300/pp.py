@@ -62,12 +62,14 @@ _SIGS = {
     "pp_propagate_batch_async": [_vp, _i32, _vp, _vp, _vp, _i64, _vp, _vp, _vp],
     "pp_propagate_plain_async": [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "pp_propagate_noalloc": [_vp, _u64, _vp, _i64, _vp, _vp, _vp],
+    "pp_propagate_range_async": [_vp, _u64, _vp, _i64, _u64, _u64, _i32, _vp, _vp, _vp],
     "pp_sync": [_vp, _vp],
     "pp_set_launch": [_vp, _i32, _i32, _i32],
     "pp_autotune_batch": [_vp, _i32, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _i32, _vp, _vp],
     "pp_get_launch": [_vp, _vp, _vp, _vp, _vp],
     "pp_get_world": [_vp, _vp],
     "pp_set_kernel_timing": [_vp, _i32],
+    "pp_set_graphs": [_vp, _i32],
     "pp_get_path_stats": [_vp, _vp],
     "pp_get_kernel_time": [_vp, _vp, _vp, _vp],
     "pp_debug_philox": [_vp, _vp, _vp, _vp, _i64],
@@ -178,6 +180,12 @@ def pp_propagate_plain_async(ctx, n_events, h_event_ids, h_src_begin, h_event_ph
                  _ptr(d_counts), _ptr(stream))
 
 
+def pp_propagate_range_async(ctx, event_id, d_src, n_src, photon_begin, photon_end, accumulate,
+                             d_hits, d_counts, stream=None):
+    return _call("pp_propagate_range_async", ctx, event_id, _ptr(d_src), n_src, photon_begin,
+                 photon_end, 1 if accumulate else 0, _ptr(d_hits), _ptr(d_counts), _ptr(stream))
+
+
 PP_NOALLOC_MAX_SOURCES = 8192
 
 
@@ -217,6 +225,10 @@ def pp_get_world(ctx):
     out = np.zeros(3, np.float32)
     _call("pp_get_world", ctx, _ptr(out))
     return tuple(float(v) for v in out)
+
+
+def pp_set_graphs(ctx, enable):
+    return _call("pp_set_graphs", ctx, 1 if enable else 0)
 
 
 def pp_set_kernel_timing(ctx, enable):

@@ -285,6 +285,64 @@ def test_autotuner_picks_a_listed_setting_and_keeps_results(full, pp):
         full.set_launch(256, 0, 8)
 
 
+def _device_batch(b):
+    import torch
+    dev = torch.device("cuda", 0)
+    src = np.ascontiguousarray(b.sources)
+    return (torch.from_numpy(src.view(np.uint8).copy()).to(dev),
+            torch.from_numpy(b.event_ids.astype(np.int64)).to(dev),
+            torch.from_numpy(b.src_begin.astype(np.int64)).to(dev),
+            torch.zeros((b.n_events, 5160), dtype=torch.int64, device=dev),
+            torch.zeros((b.n_events, 4), dtype=torch.int64, device=dev))
+
+
+def test_cuda_graph_replay_equals_direct_launch(full, pp):
+    import torch
+    b = W.events_full(n_events=25, seed=26)
+    ref_h, ref_c = full.propagate_batch(b)
+    d_src, d_ids, d_beg, d_h, d_c = _device_batch(b)
+    s = torch.cuda.Stream()
+    try:
+        pp.pp_set_graphs(full.ctx, True)
+        for rep in range(3):            # capture, then two replays
+            d_h.fill_(-1)
+            d_c.fill_(-1)
+            torch.cuda.synchronize()
+            pp.pp_propagate_batch_async(full.ctx, b.n_events, d_ids, d_beg, d_src, len(b.sources),
+                                        d_h, d_c, s.cuda_stream)
+            pp.pp_sync(full.ctx, s.cuda_stream)
+            assert np.array_equal(d_h.cpu().numpy().astype(np.uint64), ref_h), rep
+            assert np.array_equal(d_c.cpu().numpy().astype(np.uint64), ref_c), rep
+        _, _, nk = pp.pp_get_kernel_time(full.ctx)
+        assert nk > 0
+    finally:
+        pp.pp_set_graphs(full.ctx, False)
+
+
+def test_event_in_photon_ranges_equals_one_pass(full, pp):
+    import torch
+    b = W.event_large(total_photons=3_000_000, seed=7)
+    src = np.ascontiguousarray(b.sources)
+    total = int(src["n_photons"].sum())
+    h1, c1 = full.propagate(0, src)
+    dev = torch.device("cuda", 0)
+    d_src = torch.from_numpy(src.view(np.uint8).copy()).to(dev)
+    d_h = torch.zeros(5160, dtype=torch.int64, device=dev)
+    d_c = torch.zeros(4, dtype=torch.int64, device=dev)
+    cuts = [0, 1, 777_777, 1_500_000, 2_999_999, total]
+    order = [3, 0, 4, 2, 1]                      # any order, accumulated
+    for j, i in enumerate(order):
+        pp.pp_propagate_range_async(full.ctx, 0, d_src, len(src), cuts[i], cuts[i + 1], j > 0,
+                                    d_h, d_c)
+    pp.pp_sync(full.ctx)
+    assert np.array_equal(d_h.cpu().numpy().astype(np.uint64), h1)
+    assert np.array_equal(d_c.cpu().numpy().astype(np.uint64), c1)
+    # an empty range leaves accumulated outputs untouched
+    pp.pp_propagate_range_async(full.ctx, 0, d_src, len(src), 5, 5, True, d_h, d_c)
+    pp.pp_sync(full.ctx)
+    assert np.array_equal(d_h.cpu().numpy().astype(np.uint64), h1)
+
+
 def test_tracer_sums_to_production_tallies(tiny):
     b = W.sources_tiny(50_000)
     h, c = tiny.propagate(0, b.sources)
