@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--serve-clients", type=int, default=16)
+    ap.add_argument("--serve-bunches", type=int, default=30)
     ap.add_argument("--large-photons", type=int, default=10_000_000_000)
     ap.add_argument("--large-chunk", type=int, default=1_000_000_000)
     ap.add_argument("--cpu-sample-photons", type=int, default=10_000_000)
@@ -394,6 +396,57 @@ def run_ours(args):
                  "conserved": bool(int(lh.sum() + lc[0] + lc[1]) == ltot)}
         pp.pp_get_kernel_time(ctx)
 
+    # ---- serving loop: 16 host client threads stream photon bunches (tracks
+    # with stochastic losses, 1e4..1e7 photons each) into one server
+    serving = None
+    if args.serve_clients > 0:
+        import threading
+        server = pp.Server(prop, slots=3)
+        errs = []
+
+        start = threading.Barrier(args.serve_clients + 1)
+        gen_s = []
+
+        def client(c):
+            try:
+                # each client generates its tracks and bunches, then streams them
+                g0 = time.perf_counter()
+                rng = np.random.default_rng(5000 + 100 * rank + c)
+                mine = [W.serving_bunch(rng) for _ in range(args.serve_bunches)]
+                gen_s.append(time.perf_counter() - g0)
+                start.wait()
+                inflight = []
+                for k, src in enumerate(mine):
+                    inflight.append(server.submit((rank << 40) | (c << 20) | k, src))
+                    if len(inflight) >= 4:
+                        if server.collect(inflight.pop(0), timeout_ms=600_000)[0] != pp.PP_OK:
+                            errs.append("collect failed")
+                for t in inflight:
+                    if server.collect(t, timeout_ms=600_000)[0] != pp.PP_OK:
+                        errs.append("collect failed")
+            except Exception as exc:
+                errs.append(repr(exc))
+
+        threads = [threading.Thread(target=client, args=(c,)) for c in range(args.serve_clients)]
+        for t in threads:
+            t.start()
+        start.wait()
+        t0 = time.perf_counter()
+        for t in threads:
+            t.join()
+        wall = time.perf_counter() - t0
+        st = server.stats()
+        server.close()
+        serving = {"clients": args.serve_clients, "bunches": int(st["bunches"]),
+                   "photons": int(st["photons"]), "value": st["photons_per_s"], "unit": UNIT,
+                   "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                   "bunches_per_batch": st["bunches_per_batch"], "batches": int(st["batches"]),
+                   "budget_bytes": 8 << 30, "peak_admitted_bytes": int(st["peak_admitted_bytes"]),
+                   "wall_s": wall, "errors": errs[:3],
+                   "client_generation_s": max(gen_s) if gen_s else None,
+                   "note": "bunches generated by each client thread before a start barrier, "
+                           "then streamed with up to 4 in flight per client"}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(batch, args.cpu_sample_photons)
@@ -441,6 +494,7 @@ def run_ours(args):
         "autotune": {"best": tuned[0], "best_ms": tuned[1]} if tuned else None,
         "steps_per_s": steps_per_launch / (kern_avg_ms * 1e-3),
         "large_event": large,
+        "serving": serving,
         "e2e": {"value": photons * args.e2e_steps / e2e_s if e2e_s else None, "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(n_kernels),

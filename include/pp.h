@@ -267,6 +267,64 @@ int pp_get_path_stats(pp_ctx* ctx, uint64_t* out4);
 /* World cylinder in use: out3 = {radius, z_min, z_max}. */
 int pp_get_world(const pp_ctx* ctx, float* out3);
 
+/* ---- serving loop ------------------------------------------------------- */
+/* Paper Sec. 4: propagation clients queue photon-emitting steps and send them
+ * in blocks to one photon server, which aggregates steps from many events and
+ * clients to keep the GPU busy; several client instances share one memory
+ * budget.  A pp_server runs that server on a context: any number of host
+ * threads submit bunches (pp_submit) and collect their results (pp_collect);
+ * one scheduler thread admits bunches in arrival order under a fixed budget and
+ * runs them in batches as soon as one of `slots` batch slots is free
+ * (continuous batching: bunches that arrive while others run join the next
+ * batch, and the slots' kernels overlap on the device).  A bunch's result is
+ * the same alone and in any mix. */
+typedef struct pp_server pp_server; /* opaque */
+
+typedef struct pp_server_config {
+  uint64_t budget_bytes;        /* admission budget (default 8 GiB): a bunch is charged
+                                   photon_state_bytes per photon + 68 B per source +
+                                   8 B per DOM + 64 B while admitted and not finished */
+  uint64_t photon_state_bytes;  /* bytes charged per photon (default 32) */
+  int32_t slots;                /* batches in flight at once, 1..16 (default 3) */
+  int32_t max_batch_requests;   /* bunches per batch (default 512) */
+  int64_t max_batch_sources;    /* sources per batch, also per bunch (default 1 << 20) */
+} pp_server_config;
+
+/* Fills *cfg with the defaults above. */
+int pp_server_config_default(pp_server_config* cfg);
+
+/* Starts a server on ctx (geometry and ice loaded; while the server exists the
+ * context refuses new geometry or ice).  Allocates `slots` sets of device
+ * buffers and pinned staging sized by the batch limits.
+ * Errors: PP_EINVAL, PP_ENOTLOADED, PP_ENOMEM. */
+int pp_server_create(pp_ctx* ctx, const pp_server_config* cfg, pp_server** out);
+
+/* Runs every submitted bunch to completion, stops the scheduler and frees the
+ * server; results not yet collected are discarded. */
+int pp_server_destroy(pp_server* server);
+
+/* Thread-safe.  Copies n_src host sources of one bunch (event id as for
+ * pp_propagate) and queues it; *ticket_out identifies it.
+ * Errors: PP_EINVAL (bad source, too many sources), PP_EBUDGET (the bunch alone
+ * costs more than the whole budget). */
+int pp_submit(pp_server* server, uint64_t event_id, const pp_source* src, int64_t n_src,
+              uint64_t* ticket_out);
+
+/* Thread-safe.  Waits up to timeout_ms (< 0: no limit) for the bunch's result
+ * and copies it to hits[n_dom] and counts[4] (either may be NULL); the ticket
+ * is then released.  Errors: PP_EINVAL (unknown ticket), PP_ETIMEDOUT (not done
+ * yet; the ticket stays valid), PP_EDEVICE / PP_ECUDA (the batch failed). */
+int pp_collect(pp_server* server, uint64_t ticket, uint64_t* hits, uint64_t* counts,
+               int32_t timeout_ms);
+
+/* out8 = {bunches done, photons done, p50 latency ms, p99 latency ms,
+ * photons/s from first submit to last completion, mean bunches per batch,
+ * batches, peak admitted bytes}; latency = submit to result ready. */
+int pp_server_stats(pp_server* server, double* out8);
+
+/* Message for the last scheduler error (never NULL). */
+const char* pp_server_last_error(const pp_server* server);
+
 /* ---- debug and parity entry points (host buffers) ------------------------ */
 
 /* Philox4x32-10 blocks computed on the device: out[i] = Philox(ctr[i], key[i]).

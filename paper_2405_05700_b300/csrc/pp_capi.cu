@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <string>
@@ -56,7 +57,8 @@ struct pp_ctx {
     int kernels;
   };
   bool graphs = false;
-  uint64_t epoch = 0;  // bumped when a device buffer or table the kernels read moves
+  uint64_t epoch = 0;
+  std::atomic<int> servers{0};  // attached serving loops  // bumped when a device buffer or table the kernels read moves
   std::vector<GraphEntry> graph_cache;
 
   // benchmark timing of propagation launches
@@ -471,6 +473,8 @@ int LaunchView::cuda_fail(cudaError_t e, const char* where) const {
   return cuda_fail_ctx(ctx, e, where);
 }
 
+void attach_server(pp_ctx* ctx, int delta) { ctx->servers += delta; }
+
 int with_launch_view(pp_ctx* ctx, const std::function<int(const LaunchView&)>& fn) {
   std::lock_guard<std::mutex> lk(ctx->mu);
   int rc;
@@ -592,6 +596,7 @@ int pp_load_geometry(pp_ctx* ctx, const float* xyz, const int32_t* string_id, in
                      float dom_radius) {
   if (!ctx) return PP_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
+  if (ctx->servers > 0) return fail(ctx, PP_EINVAL, "a serving loop is attached to this context");
   if (n_dom < 0 || n_dom > 65535 || (n_dom > 0 && !xyz) || !(dom_radius > 0.f) ||
       !std::isfinite(dom_radius))
     return fail(ctx, PP_EINVAL, "need 0 <= n_dom <= 65535, xyz, dom_radius > 0");
@@ -728,6 +733,7 @@ int pp_load_ice(pp_ctx* ctx, const float* b_e, const float* a, int32_t n_layers,
                 float depth_top_m, float dz_m, float g) {
   if (!ctx) return PP_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
+  if (ctx->servers > 0) return fail(ctx, PP_EINVAL, "a serving loop is attached to this context");
   if (!b_e || !a || n_layers < 1 || n_layers > kMaxLayers || !(dz_m > 0.f) ||
       !std::isfinite(dz_m) || !std::isfinite(depth_top_m) || !(g > -1.f && g < 1.f))
     return fail(ctx, PP_EINVAL, "need 1 <= n_layers <= 4096, dz > 0, -1 < g < 1");

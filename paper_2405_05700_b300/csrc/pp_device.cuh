@@ -526,4 +526,44 @@ __device__ __forceinline__ void tally(const WorkDev& W, int n_dom, const Photon&
   atomicAdd(cnt + 3, (unsigned long long)ph.n);
 }
 
+// Per-lane tallies of the lane's current event: the absorbed / escaped /
+// truncated / step counts of successive photons of one event are summed in
+// registers and added to the event's counters only when the lane moves to
+// another event (and at exit).  A batch of one huge event would otherwise send
+// every photon's atomics to the same three addresses.
+struct LaneTally {
+  int ev = -1;
+  uint32_t absorbed = 0, escaped = 0, truncated = 0;
+  unsigned long long steps = 0;
+};
+
+__device__ __forceinline__ void flush(const WorkDev& W, LaneTally& t) {
+  if (t.ev >= 0) {
+    unsigned long long* cnt = W.counts + (size_t)t.ev * 4;
+    if (t.absorbed) atomicAdd(cnt + 0, (unsigned long long)t.absorbed);
+    if (t.escaped) atomicAdd(cnt + 1, (unsigned long long)t.escaped);
+    if (t.truncated) atomicAdd(cnt + 2, (unsigned long long)t.truncated);
+    if (t.steps) atomicAdd(cnt + 3, t.steps);
+  }
+  t.absorbed = t.escaped = t.truncated = 0;
+  t.steps = 0;
+}
+
+__device__ __forceinline__ void tally(const WorkDev& W, int n_dom, const Photon& ph, int out,
+                                      LaneTally& t) {
+  if (ph.ev != t.ev) {
+    flush(W, t);
+    t.ev = ph.ev;
+  }
+  if (out >= 0) {
+    atomicAdd(W.hits + (size_t)ph.ev * n_dom + out, 1ull);
+  } else if (out == kEscaped) {
+    t.escaped += 1;
+  } else {
+    t.absorbed += 1;
+    if (out == kTruncated) t.truncated += 1;
+  }
+  t.steps += ph.n;
+}
+
 }  // namespace ppk

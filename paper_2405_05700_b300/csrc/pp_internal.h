@@ -167,4 +167,8 @@ struct LaunchView {
 
 int with_launch_view(pp_ctx* ctx, const std::function<int(const LaunchView&)>& fn);
 
+// Servers that hold a LaunchView of the context (its table pointers): while
+// any is attached the context refuses to load new geometry or ice.
+void attach_server(pp_ctx* ctx, int delta);
+
 }  // namespace ppk

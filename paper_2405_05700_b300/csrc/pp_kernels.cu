@@ -238,6 +238,7 @@ k_propagate(IceDev I, GeomDev G, WorkDev W, RunDev R, uint64_t n_plain) {
     bool exhausted = false;
     uint32_t crossings = 0, births = 0, slow = 0;
     uint64_t steps = 0;
+    LaneTally lt;
     // photons [g_begin, end) of the batch: claims count from g_begin
     const uint64_t end = total < W.g_end ? total : W.g_end;
     for (;;) {
@@ -269,12 +270,13 @@ k_propagate(IceDev I, GeomDev G, WorkDev W, RunDev R, uint64_t n_plain) {
       if (alive) {
         const int out = photon_step(ph, I, G, T, R, crossings, slow);
         if (out != kScattered) {
-          tally(W, G.n_dom, ph, out);
+          tally(W, G.n_dom, ph, out, lt);
           steps += ph.n;
           alive = false;
         }
       }
     }
+    flush(W, lt);
     if (W.stats) {
       unsigned long long v0 = steps, v1 = crossings, v2 = births, v3 = slow;
 #pragma unroll

@@ -72,12 +72,18 @@ _SIGS = {
     "pp_set_graphs": [_vp, _i32],
     "pp_get_path_stats": [_vp, _vp],
     "pp_get_kernel_time": [_vp, _vp, _vp, _vp],
+    "pp_server_config_default": [_vp],
+    "pp_server_create": [_vp, _vp, _vp],
+    "pp_server_destroy": [_vp],
+    "pp_submit": [_vp, _u64, _vp, _i64, _vp],
+    "pp_collect": [_vp, _u64, _vp, _vp, _i32],
+    "pp_server_stats": [_vp, _vp],
     "pp_debug_philox": [_vp, _vp, _vp, _vp, _i64],
     "pp_debug_trace": [_vp, _u64, _vp, _i64, _vp, _i64, _i32, _vp, _vp, _vp, _vp],
     "pp_debug_first_hit": [_vp, _vp, _i64, _i32, _vp, _vp],
     "pp_debug_scatter": [_vp, _vp, _vp, _vp, _i64],
 }
-EXPORTS = tuple(_SIGS) + ("pp_last_error", "pp_strerror")
+EXPORTS = tuple(_SIGS) + ("pp_last_error", "pp_strerror", "pp_server_last_error")
 
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -87,6 +93,8 @@ _lib.pp_last_error.argtypes = [_vp]
 _lib.pp_last_error.restype = C.c_char_p
 _lib.pp_strerror.argtypes = [C.c_int]
 _lib.pp_strerror.restype = C.c_char_p
+_lib.pp_server_last_error.argtypes = [_vp]
+_lib.pp_server_last_error.restype = C.c_char_p
 
 
 class PPError(RuntimeError):
@@ -266,6 +274,104 @@ def pp_debug_scatter(ctx, dir, words, out, n):
 
 def pp_debug_first_hit(ctx, seg, n, mode, dom, t):
     return _call("pp_debug_first_hit", ctx, _ptr(seg), n, mode, _ptr(dom), _ptr(t))
+
+
+# ---- serving loop ------------------------------------------------------------
+
+class pp_server_config(C.Structure):
+    _fields_ = [("budget_bytes", C.c_uint64), ("photon_state_bytes", C.c_uint64),
+                ("slots", C.c_int32), ("max_batch_requests", C.c_int32),
+                ("max_batch_sources", C.c_int64)]
+
+
+def pp_server_config_default() -> pp_server_config:
+    cfg = pp_server_config()
+    rc = _lib.pp_server_config_default(C.byref(cfg))
+    if rc:
+        raise PPError(rc, "pp_server_config_default")
+    return cfg
+
+
+def pp_server_create(ctx, cfg: pp_server_config):
+    h = C.c_void_p()
+    rc = _lib.pp_server_create(ctx, C.byref(cfg), C.byref(h))
+    if rc:
+        raise PPError(rc, f"pp_server_create: {pp_last_error(ctx)}")
+    return h.value
+
+
+def pp_server_destroy(server):
+    return _lib.pp_server_destroy(server)
+
+
+def pp_server_last_error(server) -> str:
+    return _lib.pp_server_last_error(server).decode()
+
+
+def pp_submit(server, event_id, src, n_src):
+    """-> ticket"""
+    t = C.c_uint64()
+    rc = _lib.pp_submit(server, event_id, _ptr(src), n_src, C.byref(t))
+    if rc:
+        raise PPError(rc, f"pp_submit: {pp_strerror(rc)}")
+    return t.value
+
+
+def pp_collect(server, ticket, hits, counts, timeout_ms=-1):
+    """Returns the status code (PP_OK, PP_ETIMEDOUT, ...) without raising."""
+    return _lib.pp_collect(server, ticket, _ptr(hits), _ptr(counts), timeout_ms)
+
+
+def pp_server_stats(server):
+    out = np.zeros(8)
+    rc = _lib.pp_server_stats(server, _ptr(out))
+    if rc:
+        raise PPError(rc, "pp_server_stats")
+    keys = ("bunches", "photons", "p50_ms", "p99_ms", "photons_per_s", "bunches_per_batch",
+            "batches", "peak_admitted_bytes")
+    return dict(zip(keys, out.tolist()))
+
+
+class Server:
+    """A serving loop on a Propagator's context (same calls, numpy inputs)."""
+
+    def __init__(self, prop, budget_bytes=None, slots=None, max_batch_requests=None,
+                 max_batch_sources=None, photon_state_bytes=None):
+        cfg = pp_server_config_default()
+        for k, v in (("budget_bytes", budget_bytes), ("slots", slots),
+                     ("max_batch_requests", max_batch_requests),
+                     ("max_batch_sources", max_batch_sources),
+                     ("photon_state_bytes", photon_state_bytes)):
+            if v is not None:
+                setattr(cfg, k, v)
+        self.prop = prop
+        self.n_dom = prop.n_dom
+        self.handle = pp_server_create(prop.ctx, cfg)
+
+    def submit(self, event_id, sources):
+        s = np.ascontiguousarray(sources)
+        return pp_submit(self.handle, int(event_id), s if s.size else None, s.shape[0])
+
+    def collect(self, ticket, timeout_ms=-1):
+        """-> (status, hits [n_dom], counts [4])"""
+        hits = np.zeros(self.n_dom, np.uint64)
+        counts = np.zeros(4, np.uint64)
+        rc = pp_collect(self.handle, ticket, hits, counts, timeout_ms)
+        return rc, hits, counts
+
+    def stats(self):
+        return pp_server_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            pp_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 # ---- convenience wrapper ---------------------------------------------------

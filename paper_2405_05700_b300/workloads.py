@@ -365,3 +365,52 @@ def sources_gate(photons_per_dom: int = 1000, offset: float = 3.0,
     s["type"] = SRC_ISO_POINT
     s["n_photons"] = photons_per_dom
     return single_event(s, 7)
+
+
+def serving_bunch(rng, geom: Geometry | None = None, photons_min: float = 1e4,
+                  photons_max: float = 1e7) -> np.ndarray:
+    """Sources of one photon bunch of the serving workload: a downgoing muon
+    track (cos zenith ~ U[0.3, 1]) through the world cylinder with stochastic
+    energy losses -- cascades every U[5, 50] m with energies log-uniform in
+    [1, 1e4] GeV.  The bunch carries a log-uniform number of photons in
+    [photons_min, photons_max], split over the track's 1 m Cherenkov segments
+    and its cascades (isotropic points) in proportion to segment length and
+    cascade energy, 1 GeV of cascade energy weighing as 1 m of track."""
+    geom = geometry_full() if geom is None else geom
+    R, zlo, zhi = world_cylinder(geom)
+    cz = rng.uniform(0.3, 1.0)
+    az = rng.uniform(0.0, 2.0 * math.pi)
+    st = math.sqrt(1.0 - cz * cz)
+    d = -np.array([st * math.cos(az), st * math.sin(az), cz])
+    e1, e2 = _perp_basis(d)
+    rgen = math.hypot(R, 0.5 * (zhi - zlo))
+    centre = np.array([0.0, 0.0, 0.5 * (zlo + zhi)])
+    iv = None
+    for _ in range(1000):
+        rr = rgen * math.sqrt(rng.uniform())
+        ph = rng.uniform(0.0, 2.0 * math.pi)
+        p0 = centre + rr * (math.cos(ph) * e1 + math.sin(ph) * e2)
+        iv = _clip_line_to_cylinder(p0, d, R, zlo, zhi)
+        if iv is not None:
+            break
+    t0, t1 = iv
+    track = _muon_segments(p0, d, R, zlo, zhi, 0)
+    pos = t0 + rng.uniform(5.0, 50.0)
+    cascades = []
+    while pos < t1:
+        cascades.append((pos, math.exp(rng.uniform(0.0, math.log(1e4)))))
+        pos += rng.uniform(5.0, 50.0)
+    cas = make_sources(len(cascades))
+    for i, (t, _) in enumerate(cascades):
+        q = p0 + t * d
+        cas["x"][i], cas["y"][i], cas["z"][i] = q
+    cas["dx"], cas["dy"], cas["dz"] = d[0], d[1], d[2]
+    cas["type"] = SRC_CASCADE
+    src = np.concatenate([track, cas])
+    w = np.concatenate([track["length"].astype(np.float64),
+                        np.array([e for _, e in cascades], np.float64)])
+    n_total = int(round(math.exp(rng.uniform(math.log(photons_min), math.log(photons_max)))))
+    share = np.floor(n_total * w / w.sum()).astype(np.int64)
+    share[: n_total - int(share.sum())] += 1
+    src["n_photons"] = share.astype(np.uint64)
+    return src
