@@ -325,6 +325,71 @@ int pp_server_stats(pp_server* server, double* out8);
 /* Message for the last scheduler error (never NULL). */
 const char* pp_server_last_error(const pp_server* server);
 
+/* ---- learned surrogate -------------------------------------------------- */
+/* No counterpart in the paper's propagation step: an MLP that predicts the
+ * expected number of photons a DOM receives from a light source, trained on
+ * this library's own Monte Carlo hit counts, so that MC can be replaced where
+ * the surrogate is accurate enough and kept as the fallback and judge
+ * elsewhere.  Network: 16 inputs per (source, DOM) pair -- the ten named
+ * (source position, source direction polar/azimuth angles, DOM position
+ * relative to the source, effective scattering and absorption at the source's
+ * layer) and six derived from them (unit direction, distance, log distance,
+ * cosine between direction and the line to the DOM) -- four hidden layers of
+ * 256 SiLU units, output lambda = n_photons * softplus(z).  BF16 weights and
+ * activations, FP32 accumulation on the tensor cores (hand-written tcgen05
+ * GEMMs), FP32 master weights and Adam.  Training minimises the Poisson
+ * negative log-likelihood mean(lambda - n ln lambda).
+ * Parameters are a flat FP32 array of PP_MLP_N_PARAMS values: W1 [256][16],
+ * b1 [256], W2 [256][256], b2, W3, b3, W4, b4, w5 [256], b5 [1] (W[out][in]).
+ * An MLP keeps the context's tables in place (like a server); one host thread
+ * at a time per MLP; work is enqueued on the context's stream unless a stream
+ * is given. */
+#define PP_MLP_N_PARAMS 201985
+#define PP_MLP_INPUTS 16
+typedef struct pp_mlp pp_mlp;
+
+/* max_batch: largest training batch (multiple of 16); max_rows: pairs per
+ * inference chunk (buffers of ~1 KiB per row are allocated). */
+int pp_mlp_create(pp_ctx* ctx, int32_t max_batch, int64_t max_rows, pp_mlp** out);
+int pp_mlp_destroy(pp_mlp* mlp);
+const char* pp_mlp_last_error(const pp_mlp* mlp);
+
+/* Host FP32 parameters in / out (n = PP_MLP_N_PARAMS); set also resets Adam. */
+int pp_mlp_set_params(pp_mlp* mlp, const float* params, int64_t n);
+int pp_mlp_get_params(pp_mlp* mlp, float* params, int64_t n);
+
+/* Device features of n pairs (source index, DOM index) into d_feat[n][16]
+ * (BF16 bit patterns); sources as in pp_propagate (the point is the segment's
+ * midpoint). */
+int pp_mlp_features(pp_mlp* mlp, const pp_source* d_src, const int32_t* d_pair_src,
+                    const int32_t* d_pair_dom, int64_t n, uint16_t* d_feat, void* stream);
+
+/* d_lambda[i] = predicted photons on pair i given d_nph[i] photons emitted. */
+int pp_mlp_forward(pp_mlp* mlp, const uint16_t* d_feat, const float* d_nph, int64_t n,
+                   float* d_lambda, void* stream);
+
+/* Forward and backward on one batch (n multiple of 16, <= max_batch) without
+ * updating: h_grads[PP_MLP_N_PARAMS] receives d(loss)/d(params) and *h_loss
+ * the mean loss.  Synchronous. */
+int pp_mlp_gradients(pp_mlp* mlp, const uint16_t* d_feat, const float* d_nph,
+                     const float* d_count, int64_t n, float* h_grads, double* h_loss);
+
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) on a batch of pairs with counts. */
+int pp_mlp_train_step(pp_mlp* mlp, const uint16_t* d_feat, const float* d_nph,
+                      const float* d_count, int64_t n, float lr, void* stream);
+
+/* Sum of the mean losses of the train steps since the last call (waits). */
+int pp_mlp_loss(pp_mlp* mlp, double* loss);
+
+/* Dense inference over n_src sources x all DOMs: d_dom_sums[n_dom] (zeroed
+ * here) receives sum over sources of lambda, and d_lambda[n_src][n_dom] (if not
+ * NULL) every pair's lambda; d_nph_src[n_src] photons per source. */
+int pp_mlp_dom_sums(pp_mlp* mlp, const pp_source* d_src, int64_t n_src, const float* d_nph_src,
+                    double* d_dom_sums, float* d_lambda, void* stream);
+
+/* Waits for the MLP's work and reports a device error flag. */
+int pp_mlp_sync(pp_mlp* mlp);
+
 /* ---- debug and parity entry points (host buffers) ------------------------ */
 
 /* Philox4x32-10 blocks computed on the device: out[i] = Philox(ctr[i], key[i]).
@@ -348,6 +413,13 @@ int pp_debug_trace(pp_ctx* ctx, uint64_t event_id, const pp_source* src, int64_t
  * word x_phi, applied to dir with the context's g.
  *   dir[n][3] unit directions, words[n][2] (x_mu, x_phi), out[n][3] new directions */
 int pp_debug_scatter(pp_ctx* ctx, const float* dir, const uint32_t* words, float* out, int64_t n);
+
+/* The tensor-core GEMM of the surrogate on host data: C[M][N] = A[M][K] . B[N][K]^T
+ * with A, B BF16 (raw 16-bit patterns, row-major) and C FP32.  16 <= N <= 256,
+ * N and K multiples of 16.  swap_lbo_sbo = 1 exchanges the two strides of the
+ * shared-memory operand descriptors (a layout probe; results are then wrong). */
+int pp_debug_gemm(pp_ctx* ctx, const uint16_t* A, const uint16_t* B, int32_t M, int32_t N,
+                  int32_t K, int32_t swap_lbo_sbo, float* C);
 
 /* The device hit test on given segments: first DOM met on [p, p + S d].
  *   seg[n][7]   p (3), d (3, unit), S

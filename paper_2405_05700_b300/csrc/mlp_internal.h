@@ -1,0 +1,86 @@
+// Internal interface of the surrogate MLP kernels (mlp_kernels.cu) and its C
+// ABI (pp_mlp.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pp.h"
+
+namespace mlp {
+
+// Epilogues of the tensor-core GEMM C = A . B^T (FP32 accumulators):
+enum {
+  kEpiStoreF32 = 0,      // Cf = acc
+  kEpiAddF32 = 1,        // Cf += acc
+  kEpiBiasSiluBf16 = 2,  // z = acc + bias; Zb = bf16(z) (if set); Cb = bf16(silu(z))
+  kEpiDsiluBf16 = 3,     // Cb = bf16(acc * silu'(Zin))
+  kEpiAtomicF32 = 4,     // Cf += acc with atomics (split-K partial sums)
+};
+
+struct GemmArgs {
+  const __nv_bfloat16* A;  // [M][lda], K contiguous
+  const __nv_bfloat16* B;  // [N][ldb], K contiguous
+  int M, N, K, lda, ldb, ldc;
+  int bn;                  // N tile: multiple of 16, <= 256
+  int k_split;             // K ranges run by separate CTAs (grid z); needs kEpiAtomicF32 if > 1
+  int swap_lbo_sbo;        // layout probe: exchange the descriptor strides
+  float* Cf;
+  __nv_bfloat16* Cb;
+  __nv_bfloat16* Zb;
+  const __nv_bfloat16* Zin;
+  const float* bias;
+  int* err;
+};
+
+size_t gemm_smem_bytes(int bn);
+cudaError_t launch_gemm(const GemmArgs& g, int epi, cudaStream_t st);
+
+constexpr int kIn = 16;      // input features (10 named + 6 derived), the first MMA's K
+constexpr int kHid = 256;    // hidden width
+constexpr int kLayers = 4;   // hidden layers (Linear + SiLU)
+
+// Geometry and ice the feature kernels read (device pointers).
+struct FeatGeom {
+  const float4* dom;         // [n_dom] (x, y, z, 0)
+  const float4* layer;       // [L] (b, a, 1/b, 1/a), b geometric
+  int n_dom, L;
+  float z_top, dz, be_over_b;  // effective b_e = b * be_over_b
+};
+
+// Features of pairs (source s, DOM d) as BF16 [n][16].
+cudaError_t launch_features(const FeatGeom& fg, const pp_source* src, const int32_t* pair_src,
+                            const int32_t* pair_dom, int64_t n, __nv_bfloat16* feat,
+                            cudaStream_t st);
+// Features of all pairs of sources [s0, s0 + ns) x DOMs [0, n_dom), row = s * n_dom + d.
+cudaError_t launch_features_dense(const FeatGeom& fg, const pp_source* src, int64_t s0,
+                                  int64_t ns, __nv_bfloat16* feat, cudaStream_t st);
+
+// Head z = h . w5 + b5, lambda = nph * softplus(z).
+cudaError_t launch_head(const __nv_bfloat16* h, const float* w5, const float* b5,
+                        const float* nph, int64_t n, float* lambda, cudaStream_t st);
+// Head with loss and gradients: Poisson NLL sum(lambda - n ln lambda) / n_total;
+// dZ4 = dL/dz * w5 * silu'(z4) (BF16), dw5 += sum dL/dz * h, db5 += sum dL/dz,
+// loss (double) += the batch's loss sum / n_total.
+cudaError_t launch_head_backward(const __nv_bfloat16* h, const __nv_bfloat16* z4, const float* w5,
+                                 const float* b5, const float* nph, const float* cnt, int64_t n,
+                                 float inv_n, __nv_bfloat16* dz4, float* dw5, float* db5,
+                                 double* loss, cudaStream_t st);
+// Head over dense pairs, summed per DOM: dom_sum[d] += lambda(s, d).
+cudaError_t launch_head_dom_sums(const __nv_bfloat16* h, const float* w5, const float* b5,
+                                 const float* nph_src, int64_t s0, int64_t ns, int n_dom,
+                                 double* dom_sum, float* lambda_out, cudaStream_t st);
+
+cudaError_t launch_transpose(const __nv_bfloat16* in, int rows, int cols, __nv_bfloat16* out,
+                             cudaStream_t st);
+// out[c] = sum_r in[r][c] (FP32) for a BF16 matrix
+cudaError_t launch_colsum(const __nv_bfloat16* in, int rows, int cols, float* out,
+                          cudaStream_t st);
+// Adam on n parameters; writes the BF16 copy of the weights it updates.
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr,
+                        float b1, float b2, float eps, float bc1, float bc2, __nv_bfloat16* pb,
+                        cudaStream_t st);
+cudaError_t launch_to_bf16(const float* in, int64_t n, __nv_bfloat16* out, cudaStream_t st);
+
+}  // namespace mlp

@@ -1,0 +1,433 @@
+// Kernels of the learned surrogate: a tensor-core GEMM with fused epilogues
+// (tcgen05, BF16 in, FP32 accumulate in TMEM) and the small element-wise and
+// reduction kernels of training and inference.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mlp_internal.h"
+#include "tc_gemm.cuh"
+
+namespace mlp {
+
+namespace {
+
+constexpr int kBM = 128;      // rows of A / C per CTA (the MMA's M)
+constexpr int kBK = 64;       // K staged per round
+constexpr uint32_t kWaitTries = 1u << 22;
+
+__device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
+
+__device__ __forceinline__ float silu_grad(float z) {
+  const float s = 1.0f / (1.0f + __expf(-z));
+  return s * (1.0f + z * (1.0f - s));
+}
+
+__device__ __forceinline__ uint32_t pow2_cols(int n) {
+  return n > 128 ? 256u : (n > 64 ? 128u : (n > 32 ? 64u : 32u));
+}
+
+// Copies rows [r0, r0 + rows) x K columns [k0, k0 + kBK) of a row-major BF16
+// matrix (leading dimension ld) into a K-major no-swizzle smem tile; rows or
+// columns outside (n_rows, K) are zero.
+__device__ __forceinline__ void stage_tile(unsigned char* tile, const __nv_bfloat16* X, int ld,
+                                           int n_rows, int K, int r0, int rows, int k0) {
+  const int chunks = rows * (kBK / 8);
+  for (int i = threadIdx.x; i < chunks; i += blockDim.x) {
+    const int r = i >> 3, c = i & 7;
+    const int gr = r0 + r, gk = k0 + c * 8;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (gr < n_rows && gk < K) v = *reinterpret_cast<const uint4*>(X + (size_t)gr * ld + gk);
+    *reinterpret_cast<uint4*>(tile + tc::tile_off(r, c * 8, kBK)) = v;
+  }
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ uint32_t tslot;
+  __shared__ __align__(8) uint64_t bar;
+  unsigned char* sA = smem;                         // 128 x 64 BF16 = 16 KB
+  unsigned char* sB = smem + kBM * kBK * 2;         // BN x 64 BF16
+  const int BN = g.bn;
+  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+  // split K: this CTA runs K range [kb, ke)
+  const int kc = g.k_split > 1 ? ((g.K + g.k_split * kBK - 1) / (g.k_split * kBK)) * kBK : g.K;
+  const int kb = blockIdx.z * kc;
+  const int ke = (kb + kc < g.K) ? kb + kc : g.K;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t ncols = pow2_cols(BN);
+  if (warp == 0) tc::tmem_alloc(&tslot, ncols);
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = tslot;
+  const uint32_t idesc = tc::idesc_bf16(kBM, BN);
+  // descriptor strides: K-direction core matrices 128 B apart, 8-row groups
+  // kBK * 16 B apart (exchanged when probing the layout)
+  const uint32_t lbo = g.swap_lbo_sbo ? kBK * 16 : 128;
+  const uint32_t sbo = g.swap_lbo_sbo ? 128 : kBK * 16;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int k0 = kb; k0 < ke && ok; k0 += kBK) {
+    stage_tile(sA, g.A, g.lda, g.M, ke, m0, kBM, k0);
+    stage_tile(sB, g.B, g.ldb, g.N, ke, n0, BN, k0);
+    tc::fence_smem_async();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tc::fence_after_sync();
+      const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
+#pragma unroll
+      for (int s = 0; s < kBK / 16; ++s) {
+        if (k0 + 16 * s >= ke) break;
+        tc::mma_bf16(taddr, tc::smem_desc(a0 + 256 * s, lbo, sbo),
+                     tc::smem_desc(b0 + 256 * s, lbo, sbo), idesc, (k0 > kb || s > 0) ? 1u : 0u);
+      }
+      tc::mma_commit(&bar);
+    }
+    const bool done = tc::mbar_wait(&bar, phase, kWaitTries);
+    phase ^= 1u;
+    ok = __syncthreads_and(done);
+    tc::fence_after_sync();
+  }
+  if (!ok) {
+    if (threadIdx.x == 0) atomicOr(g.err, 1);
+  } else if (kb < ke) {
+    // epilogue: warp w owns rows m0 + 32 w + lane; 32 columns per TMEM load
+    const int row = m0 + warp * 32 + lane;
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+      float v[32];
+      tc::tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      if (row >= g.M) continue;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int col = n0 + c0 + j;
+        if (col >= g.N || c0 + j >= BN) continue;
+        const size_t o = (size_t)row * g.ldc + col;
+        if (EPI == kEpiStoreF32) {
+          g.Cf[o] = v[j];
+        } else if (EPI == kEpiAddF32) {
+          g.Cf[o] += v[j];
+        } else if (EPI == kEpiBiasSiluBf16) {
+          const float z = v[j] + g.bias[col];
+          if (g.Zb) g.Zb[o] = __float2bfloat16_rn(z);
+          g.Cb[o] = __float2bfloat16_rn(silu(z));
+        } else if (EPI == kEpiDsiluBf16) {
+          g.Cb[o] = __float2bfloat16_rn(v[j] * silu_grad(__bfloat162float(g.Zin[o])));
+        } else if (EPI == kEpiAtomicF32) {
+          atomicAdd(g.Cf + o, v[j]);
+        }
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(taddr, ncols);
+}
+
+}  // namespace
+
+size_t gemm_smem_bytes(int bn) { return (size_t)(kBM + bn) * kBK * 2 + 1024; }
+
+cudaError_t launch_gemm(const GemmArgs& g, int epi, cudaStream_t st) {
+  if (g.M <= 0 || g.N <= 0 || g.K <= 0) return cudaSuccess;
+  const dim3 grid((g.M + kBM - 1) / kBM, (g.N + g.bn - 1) / g.bn, g.k_split > 1 ? g.k_split : 1);
+  const size_t smem = gemm_smem_bytes(g.bn);
+  // at least 80 KB per CTA: at most two CTAs (2 x 256 TMEM columns) per SM
+  const size_t smem_req = smem < 80 * 1024 ? 80 * 1024 : smem;
+  cudaError_t e = cudaSuccess;
+#define PP_GEMM_CASE(E)                                                                          \
+  case E:                                                                                        \
+    e = cudaFuncSetAttribute(k_gemm<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_req); \
+    if (e == cudaSuccess) k_gemm<E><<<grid, 128, smem_req, st>>>(g);                             \
+    break;
+  switch (epi) {
+    PP_GEMM_CASE(kEpiStoreF32)
+    PP_GEMM_CASE(kEpiAddF32)
+    PP_GEMM_CASE(kEpiBiasSiluBf16)
+    PP_GEMM_CASE(kEpiDsiluBf16)
+    PP_GEMM_CASE(kEpiAtomicF32)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef PP_GEMM_CASE
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- features --
+namespace {
+
+// Surrogate inputs of a (source, DOM) pair.  The ten named inputs: source
+// position (/500 m), direction polar and azimuth angles (/pi), DOM position
+// relative to the source (/100 m), effective scattering and absorption at the
+// source's layer (x10, x50); six derived: the unit direction, the distance
+// (/100 m), the cosine between the direction and the line to the DOM, and
+// ln(1 + distance / 1 m) / 5.  The source point is the segment's midpoint.
+__device__ __forceinline__ void pair_features(const FeatGeom& fg, const pp_source& s, float4 c,
+                                              __nv_bfloat16* out) {
+  float dx = s.dx, dy = s.dy, dz = s.dz;
+  const float nn = sqrtf(dx * dx + dy * dy + dz * dz);
+  if (nn > 0.0f) {
+    dx /= nn;
+    dy /= nn;
+    dz /= nn;
+  }
+  const float h = 0.5f * s.length;
+  const float px = s.x + h * dx, py = s.y + h * dy, pz = s.z + h * dz;
+  const float ex = c.x - px, ey = c.y - py, ez = c.z - pz;
+  const float r = sqrtf(ex * ex + ey * ey + ez * ez);
+  int li = (int)floorf((fg.z_top - pz) / fg.dz);
+  li = li < 0 ? 0 : (li > fg.L - 1 ? fg.L - 1 : li);
+  const float4 L = fg.layer[li];
+  float f[kIn];
+  f[0] = px / 500.0f;
+  f[1] = py / 500.0f;
+  f[2] = pz / 500.0f;
+  f[3] = acosf(fminf(1.0f, fmaxf(-1.0f, dz))) / 3.14159265358979f;
+  f[4] = atan2f(dy, dx) / 3.14159265358979f;
+  f[5] = ex / 100.0f;
+  f[6] = ey / 100.0f;
+  f[7] = ez / 100.0f;
+  f[8] = L.x * fg.be_over_b * 10.0f;
+  f[9] = L.y * 50.0f;
+  f[10] = dx;
+  f[11] = dy;
+  f[12] = dz;
+  f[13] = r / 100.0f;
+  f[14] = (dx * ex + dy * ey + dz * ez) / fmaxf(r, 1e-3f);
+  f[15] = log1pf(r) / 5.0f;
+#pragma unroll
+  for (int i = 0; i < kIn; ++i) out[i] = __float2bfloat16_rn(f[i]);
+}
+
+__global__ void k_features(FeatGeom fg, const pp_source* src, const int32_t* ps, const int32_t* pd,
+                           int64_t n, __nv_bfloat16* feat) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  pair_features(fg, src[ps[i]], fg.dom[pd[i]], feat + i * kIn);
+}
+
+__global__ void k_features_dense(FeatGeom fg, const pp_source* src, int64_t s0, int64_t ns,
+                                 __nv_bfloat16* feat) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ns * fg.n_dom) return;
+  const int64_t s = s0 + i / fg.n_dom;
+  const int d = (int)(i % fg.n_dom);
+  pair_features(fg, src[s], fg.dom[d], feat + i * kIn);
+}
+
+// ------------------------------------------------------------------ head --
+__device__ __forceinline__ float softplus(float z) { return z > 20.0f ? z : log1pf(__expf(z)); }
+
+// z of pair p by one warp: 256 BF16 activations . w5
+__device__ __forceinline__ float head_z(const __nv_bfloat16* hp, const float* w5, float b5) {
+  const int lane = threadIdx.x & 31;
+  const uint4 raw = *reinterpret_cast<const uint4*>(hp + lane * 8);
+  const __nv_bfloat16* hv = reinterpret_cast<const __nv_bfloat16*>(&raw);
+  float acc = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) acc = fmaf(__bfloat162float(hv[j]), w5[lane * 8 + j], acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  return acc + b5;
+}
+
+__global__ void k_head(const __nv_bfloat16* h, const float* w5, const float* b5, const float* nph,
+                       int64_t n, float* lambda) {
+  const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (p >= n) return;
+  const float z = head_z(h + p * kHid, w5, *b5);
+  if ((threadIdx.x & 31) == 0) lambda[p] = nph[p] * softplus(z);
+}
+
+__global__ void k_head_dom(const __nv_bfloat16* h, const float* w5, const float* b5,
+                           const float* nph_src, int64_t s0, int64_t ns, int n_dom,
+                           double* dom_sum, float* lambda_out) {
+  const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (p >= ns * n_dom) return;
+  const float z = head_z(h + p * kHid, w5, *b5);
+  if ((threadIdx.x & 31) == 0) {
+    const int64_t s = s0 + p / n_dom;
+    const float lam = nph_src[s] * softplus(z);
+    if (dom_sum) atomicAdd(dom_sum + (p % n_dom), (double)lam);
+    if (lambda_out) lambda_out[p] = lam;
+  }
+}
+
+constexpr int kHeadPairs = 64;  // pairs per block of the head backward
+
+__global__ void __launch_bounds__(256) k_head_bwd(const __nv_bfloat16* h, const __nv_bfloat16* z4,
+                                                  const float* w5, const float* b5,
+                                                  const float* nph, const float* cnt, int64_t n,
+                                                  float inv_n, __nv_bfloat16* dz4, float* dw5,
+                                                  float* db5, double* loss) {
+  __shared__ float s_g[kHeadPairs];
+  __shared__ float s_w5[kHid];
+  const int64_t p0 = (int64_t)blockIdx.x * kHeadPairs;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  s_w5[threadIdx.x] = w5[threadIdx.x];
+  __syncthreads();
+  double lsum = 0.0;
+  float gsum = 0.0f;
+  for (int q = warp; q < kHeadPairs; q += 8) {
+    const int64_t p = p0 + q;
+    float g = 0.0f;
+    if (p < n) {
+      const float z = head_z(h + p * kHid, s_w5, *b5);
+      const float sp = fmaxf(softplus(z), 1e-30f);
+      const float lam = nph[p] * sp;
+      const float k = cnt[p];
+      const float sig = 1.0f / (1.0f + __expf(-z));
+      g = nph[p] * sig * (1.0f - k / lam) * inv_n;
+      if (lane == 0) lsum += (double)(lam - (k > 0.0f ? k * logf(lam) : 0.0f)) * inv_n;
+    }
+    if (lane == 0) {
+      s_g[q] = g;
+      gsum += g;
+    }
+  }
+  __syncthreads();
+  const int j = threadIdx.x;
+  float acc = 0.0f;
+  for (int q = 0; q < kHeadPairs; ++q) {
+    const int64_t p = p0 + q;
+    if (p >= n) break;
+    const float g = s_g[q];
+    const size_t o = (size_t)p * kHid + j;
+    acc = fmaf(g, __bfloat162float(h[o]), acc);
+    const float zz = __bfloat162float(z4[o]);
+    const float sg = 1.0f / (1.0f + __expf(-zz));
+    dz4[o] = __float2bfloat16_rn(g * s_w5[j] * sg * (1.0f + zz * (1.0f - sg)));
+  }
+  atomicAdd(dw5 + j, acc);
+  if (lane == 0) {
+    if (gsum != 0.0f) atomicAdd(db5, gsum);
+    if (lsum != 0.0) atomicAdd(loss, lsum);
+  }
+}
+
+// ----------------------------------------------------------- utilities --
+__global__ void k_transpose(const __nv_bfloat16* in, int rows, int cols, __nv_bfloat16* out) {
+  __shared__ __nv_bfloat16 t[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) t[i][threadIdx.x] = in[(size_t)r * cols + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) out[(size_t)c * rows + r] = t[threadIdx.x][i];
+  }
+}
+
+__global__ void k_colsum(const __nv_bfloat16* in, int rows, int cols, float* out) {
+  const int c = blockIdx.y * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  const int per = (rows + gridDim.x - 1) / gridDim.x;
+  const int rb = blockIdx.x * per, re = min(rows, rb + per);
+  float acc = 0.0f;
+  for (int r = rb; r < re; ++r) acc += __bfloat162float(in[(size_t)r * cols + c]);
+  atomicAdd(out + c, acc);
+}
+
+__global__ void k_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1,
+                       float b2, float eps, float bc1, float bc2, __nv_bfloat16* pb) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.0f - b1) * gi;
+  const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  const float pi = p[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+  p[i] = pi;
+  if (pb) pb[i] = __float2bfloat16_rn(pi);
+}
+
+__global__ void k_to_bf16(const float* in, int64_t n, __nv_bfloat16* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = __float2bfloat16_rn(in[i]);
+}
+
+unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t launch_features(const FeatGeom& fg, const pp_source* src, const int32_t* pair_src,
+                            const int32_t* pair_dom, int64_t n, __nv_bfloat16* feat,
+                            cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_features<<<blocks_for(n, 256), 256, 0, st>>>(fg, src, pair_src, pair_dom, n, feat);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_features_dense(const FeatGeom& fg, const pp_source* src, int64_t s0,
+                                  int64_t ns, __nv_bfloat16* feat, cudaStream_t st) {
+  const int64_t n = ns * fg.n_dom;
+  if (n <= 0) return cudaSuccess;
+  k_features_dense<<<blocks_for(n, 256), 256, 0, st>>>(fg, src, s0, ns, feat);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_head(const __nv_bfloat16* h, const float* w5, const float* b5,
+                        const float* nph, int64_t n, float* lambda, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_head<<<blocks_for(n * 32, 256), 256, 0, st>>>(h, w5, b5, nph, n, lambda);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_head_backward(const __nv_bfloat16* h, const __nv_bfloat16* z4, const float* w5,
+                                 const float* b5, const float* nph, const float* cnt, int64_t n,
+                                 float inv_n, __nv_bfloat16* dz4, float* dw5, float* db5,
+                                 double* loss, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_head_bwd<<<blocks_for(n, kHeadPairs), 256, 0, st>>>(h, z4, w5, b5, nph, cnt, n, inv_n, dz4,
+                                                        dw5, db5, loss);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_head_dom_sums(const __nv_bfloat16* h, const float* w5, const float* b5,
+                                 const float* nph_src, int64_t s0, int64_t ns, int n_dom,
+                                 double* dom_sum, float* lambda_out, cudaStream_t st) {
+  const int64_t n = ns * n_dom;
+  if (n <= 0) return cudaSuccess;
+  k_head_dom<<<blocks_for(n * 32, 256), 256, 0, st>>>(h, w5, b5, nph_src, s0, ns, n_dom, dom_sum,
+                                                      lambda_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transpose(const __nv_bfloat16* in, int rows, int cols, __nv_bfloat16* out,
+                             cudaStream_t st) {
+  const dim3 grid(blocks_for(cols, 32), blocks_for(rows, 32));
+  k_transpose<<<grid, dim3(32, 8), 0, st>>>(in, rows, cols, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_colsum(const __nv_bfloat16* in, int rows, int cols, float* out,
+                          cudaStream_t st) {
+  const int parts = rows >= 4096 ? 128 : 1;
+  k_colsum<<<dim3(parts, blocks_for(cols, 256)), 256, 0, st>>>(in, rows, cols, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr,
+                        float b1, float b2, float eps, float bc1, float bc2, __nv_bfloat16* pb,
+                        cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_adam<<<blocks_for(n, 256), 256, 0, st>>>(p, g, m, v, n, lr, b1, b2, eps, bc1, bc2, pb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_bf16(const float* in, int64_t n, __nv_bfloat16* out, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_to_bf16<<<blocks_for(n, 256), 256, 0, st>>>(in, n, out);
+  return cudaGetLastError();
+}
+
+}  // namespace mlp

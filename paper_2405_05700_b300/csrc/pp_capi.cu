@@ -15,6 +15,7 @@
 
 #include "pp.h"
 #include "pp_internal.h"
+#include "mlp_internal.h"
 
 using namespace ppk;
 
@@ -489,6 +490,7 @@ int with_launch_view(pp_ctx* ctx, const std::function<int(const LaunchView&)>& f
   v.run = run_params(ctx);
   v.block_threads = ctx->block_threads;
   v.variant = kernel_variant(ctx);
+  v.scatter_effective = ctx->cfg.scatter_coeff_is_effective;
   if ((rc = prepare_smem(ctx, &v.smem))) return rc;
   if ((rc = grid_blocks(ctx, v.smem, &v.grid_blocks))) return rc;
   v.err = static_cast<int*>(ctx->err.p);
@@ -1069,6 +1071,39 @@ int pp_debug_scatter(pp_ctx* ctx, const float* dir, const uint32_t* words, float
   PP_CUDA(cudaMemcpyAsync(out, ctx->s_misc3.p, 12 * n, cudaMemcpyDeviceToHost, st));
   PP_CUDA(cudaStreamSynchronize(st));
   return PP_OK;
+}
+
+int pp_debug_gemm(pp_ctx* ctx, const uint16_t* A, const uint16_t* B, int32_t M, int32_t N,
+                  int32_t K, int32_t swap_lbo_sbo, float* C) {
+  if (!ctx) return PP_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (!A || !B || !C || M < 1 || N < 16 || N > 256 || N % 16 || K < 16 || K % 16)
+    return fail(ctx, PP_EINVAL, "need M >= 1, 16 <= N <= 256 (multiple of 16), K multiple of 16");
+  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  cudaStream_t st = ctx->stream;
+  int rc;
+  const size_t a = 2 * (size_t)M * K, b = 2 * (size_t)N * K, c = 4 * (size_t)M * N;
+  if ((rc = ensure(ctx, ctx->s_misc1, a)) || (rc = ensure(ctx, ctx->s_misc2, b)) ||
+      (rc = ensure(ctx, ctx->s_misc3, c)))
+    return rc;
+  PP_CUDA(cudaMemcpyAsync(ctx->s_misc1.p, A, a, cudaMemcpyHostToDevice, st));
+  PP_CUDA(cudaMemcpyAsync(ctx->s_misc2.p, B, b, cudaMemcpyHostToDevice, st));
+  mlp::GemmArgs g{};
+  g.A = static_cast<const __nv_bfloat16*>(ctx->s_misc1.p);
+  g.B = static_cast<const __nv_bfloat16*>(ctx->s_misc2.p);
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.lda = K;
+  g.ldb = K;
+  g.ldc = N;
+  g.bn = N;
+  g.swap_lbo_sbo = swap_lbo_sbo;
+  g.Cf = static_cast<float*>(ctx->s_misc3.p);
+  g.err = static_cast<int*>(ctx->err.p);
+  PP_CUDA(mlp::launch_gemm(g, mlp::kEpiStoreF32, st));
+  PP_CUDA(cudaMemcpyAsync(C, ctx->s_misc3.p, c, cudaMemcpyDeviceToHost, st));
+  return sync_and_check(ctx, st);
 }
 
 int pp_debug_first_hit(pp_ctx* ctx, const float* seg, int64_t n, int32_t mode, int32_t* dom,

@@ -158,6 +158,7 @@ struct LaunchView {
   int block_threads;
   int grid_blocks;
   int variant;
+  int scatter_effective;  // the context's scatter_coeff_is_effective
   size_t smem;
   int* err;
   unsigned long long* stats;

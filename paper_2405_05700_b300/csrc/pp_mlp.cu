@@ -1,0 +1,396 @@
+// The learned surrogate behind the C ABI: an MLP from (source, DOM) pair
+// features to the expected number of photons the DOM receives, trained on the
+// propagator's own hit counts.  BF16 weights and activations, FP32
+// accumulation on the tensor cores (tcgen05 GEMMs of mlp_kernels.cu), FP32
+// master weights and Adam state.
+//
+//   h1 = silu(W1 x + b1), h2..h4 = silu(Wi h + bi), z = w5 . h4 + b5,
+//   lambda = n_photons * softplus(z),  loss = mean(lambda - n ln lambda)
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "mlp_internal.h"
+#include "pp.h"
+#include "pp_internal.h"
+
+using namespace mlp;
+
+namespace {
+
+// Flat parameter layout (FP32): W1 [256][16], b1, W2 [256][256], b2, W3, b3,
+// W4, b4, w5 [256], b5.
+constexpr int64_t kOffW1 = 0;
+constexpr int64_t kOffB1 = kOffW1 + kHid * kIn;
+constexpr int64_t kOffW2 = kOffB1 + kHid;
+constexpr int64_t kHidBlock = (int64_t)kHid * kHid + kHid;  // one hidden layer's W and b
+constexpr int64_t kOffW5 = kOffW2 + 3 * kHidBlock;
+constexpr int64_t kOffB5 = kOffW5 + kHid;
+constexpr int64_t kNParams = kOffB5 + 1;
+static_assert(kNParams == PP_MLP_N_PARAMS, "parameter count");
+
+int64_t off_w(int layer) { return layer == 0 ? kOffW1 : kOffW2 + (layer - 1) * kHidBlock; }
+int64_t off_b(int layer) { return layer == 0 ? kOffB1 : off_w(layer) + (int64_t)kHid * kHid; }
+
+template <class T>
+cudaError_t dalloc(T** p, size_t n) {
+  return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (n ? n : 1));
+}
+
+}  // namespace
+
+struct pp_mlp {
+  pp_ctx* ctx = nullptr;
+  ppk::LaunchView view{};
+  FeatGeom fg{};
+  int max_batch = 0;
+  int64_t max_rows = 0;
+  std::string last_error = "no error";
+  // parameters
+  float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
+  __nv_bfloat16* wb[kLayers] = {};   // BF16 weights of the 4 GEMM layers
+  __nv_bfloat16* wtb[kLayers] = {};  // their transposes (layers 1..3 used)
+  int64_t step = 0;
+  // training activations [max_batch][256]
+  __nv_bfloat16* z[kLayers] = {};
+  __nv_bfloat16* h[kLayers] = {};
+  __nv_bfloat16 *dza = nullptr, *dzb = nullptr, *t1 = nullptr, *t2 = nullptr;
+  double* loss = nullptr;
+  int* err = nullptr;
+  // inference buffers [max_rows]
+  __nv_bfloat16 *x0 = nullptr, *ha = nullptr, *hb = nullptr;
+};
+
+namespace {
+
+int mfail(pp_mlp* m, int code, const std::string& msg) {
+  m->last_error = msg;
+  return code;
+}
+
+#define PP_MLP_CUDA(expr)                                                              \
+  do {                                                                                 \
+    cudaError_t _e = (expr);                                                           \
+    if (_e != cudaSuccess) return mfail(m, PP_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
+
+GemmArgs gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, int M, int N, int K, int* err) {
+  GemmArgs a{};
+  a.A = A;
+  a.B = B;
+  a.M = M;
+  a.N = N;
+  a.K = K;
+  a.lda = K;
+  a.ldb = K;
+  a.ldc = N;
+  a.bn = N;
+  a.k_split = 1;
+  a.err = err;
+  return a;
+}
+
+// BF16 copies and transposes of the weights from the FP32 masters.
+int refresh_bf16(pp_mlp* m, cudaStream_t st) {
+  PP_MLP_CUDA(launch_to_bf16(m->p + kOffW1, (int64_t)kHid * kIn, m->wb[0], st));
+  for (int l = 1; l < kLayers; ++l) {
+    PP_MLP_CUDA(launch_to_bf16(m->p + off_w(l), (int64_t)kHid * kHid, m->wb[l], st));
+    PP_MLP_CUDA(launch_transpose(m->wb[l], kHid, kHid, m->wtb[l], st));
+  }
+  return PP_OK;
+}
+
+// Hidden layers on n rows of features x0: h (and, when training, z) buffers.
+int forward_layers(pp_mlp* m, const __nv_bfloat16* x0, int n, __nv_bfloat16* const* h,
+                   __nv_bfloat16* const* z, cudaStream_t st) {
+  const __nv_bfloat16* in = x0;
+  for (int l = 0; l < kLayers; ++l) {
+    GemmArgs a = gemm(in, m->wb[l], n, kHid, l == 0 ? kIn : kHid, m->err);
+    a.bias = m->p + off_b(l);
+    a.Cb = h[l];
+    a.Zb = z ? z[l] : nullptr;
+    PP_MLP_CUDA(launch_gemm(a, kEpiBiasSiluBf16, st));
+    in = h[l];
+  }
+  return PP_OK;
+}
+
+// Forward + backward of one batch: gradients into m->g (zeroed), loss added.
+int forward_backward(pp_mlp* m, const __nv_bfloat16* x0, const float* nph, const float* cnt,
+                     int n, cudaStream_t st) {
+  int rc;
+  PP_MLP_CUDA(cudaMemsetAsync(m->g, 0, sizeof(float) * kNParams, st));
+  if ((rc = forward_layers(m, x0, n, m->h, m->z, st))) return rc;
+  PP_MLP_CUDA(launch_head_backward(m->h[3], m->z[3], m->p + kOffW5, m->p + kOffB5, nph, cnt, n,
+                                   1.0f / (float)n, m->dza, m->g + kOffW5, m->g + kOffB5, m->loss,
+                                   st));
+  __nv_bfloat16* dz = m->dza;     // dL/dz of the current layer (pre-activation)
+  __nv_bfloat16* dzn = m->dzb;
+  const int ks = n >= 8192 ? 32 : (n >= 1024 ? 8 : 1);
+  for (int l = kLayers - 1; l >= 0; --l) {
+    const int in_w = l == 0 ? kIn : kHid;
+    const __nv_bfloat16* x = l == 0 ? x0 : m->h[l - 1];
+    // dW_l = dz^T . x  (split over the batch, summed with atomics)
+    PP_MLP_CUDA(launch_transpose(dz, n, kHid, m->t1, st));
+    PP_MLP_CUDA(launch_transpose(x, n, in_w, m->t2, st));
+    GemmArgs a = gemm(m->t1, m->t2, kHid, in_w, n, m->err);
+    a.k_split = ks;
+    a.Cf = m->g + off_w(l);
+    PP_MLP_CUDA(launch_gemm(a, kEpiAtomicF32, st));
+    PP_MLP_CUDA(launch_colsum(dz, n, kHid, m->g + off_b(l), st));
+    if (l == 0) break;
+    // dz_{l-1} = (dz . W_l) * silu'(z_{l-1})
+    GemmArgs b = gemm(dz, m->wtb[l], n, kHid, kHid, m->err);
+    b.Zin = m->z[l - 1];
+    b.Cb = dzn;
+    PP_MLP_CUDA(launch_gemm(b, kEpiDsiluBf16, st));
+    __nv_bfloat16* t = dz;
+    dz = dzn;
+    dzn = t;
+  }
+  return PP_OK;
+}
+
+int check_batch(pp_mlp* m, int64_t n) {
+  if (n < 16 || n > m->max_batch || n % 16)
+    return mfail(m, PP_EINVAL, "training batch must be a multiple of 16 in [16, max_batch]");
+  return PP_OK;
+}
+
+int mlp_sync(pp_mlp* m, cudaStream_t st) {
+  PP_MLP_CUDA(cudaStreamSynchronize(st));
+  int flag = 0;
+  PP_MLP_CUDA(cudaMemcpy(&flag, m->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) {
+    PP_MLP_CUDA(cudaMemset(m->err, 0, sizeof(int)));
+    return mfail(m, PP_EDEVICE, "a tensor-core wait ran out (device error flag)");
+  }
+  return PP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pp_mlp_create(pp_ctx* ctx, int32_t max_batch, int64_t max_rows, pp_mlp** out) {
+  if (!ctx || !out || max_batch < 16 || max_batch % 16 || max_rows < 1) return PP_EINVAL;
+  *out = nullptr;
+  pp_mlp* m = new pp_mlp();
+  m->ctx = ctx;
+  m->max_batch = max_batch;
+  m->max_rows = max_rows;
+  const int rc = ppk::with_launch_view(ctx, [&](const ppk::LaunchView& v) {
+    m->view = v;
+    ppk::attach_server(ctx, +1);  // keeps the context's tables in place
+    return PP_OK;
+  });
+  if (rc) {
+    delete m;
+    return rc;
+  }
+  const float g = m->view.ice.g;
+  m->fg.dom = m->view.geom.dom;
+  m->fg.layer = m->view.ice.layer;
+  m->fg.n_dom = m->view.geom.n_dom;
+  m->fg.L = m->view.ice.L;
+  m->fg.z_top = m->view.ice.z_top;
+  m->fg.dz = m->view.ice.dz;
+  m->fg.be_over_b = m->view.scatter_effective ? 1.0f - g : 1.0f;
+  cudaError_t e = cudaSetDevice(m->view.device);
+  const size_t B = (size_t)max_batch, H = (size_t)kHid;
+#define PP_A(x) \
+  if (e == cudaSuccess) e = (x)
+  PP_A(dalloc(&m->p, kNParams));
+  PP_A(dalloc(&m->g, kNParams));
+  PP_A(dalloc(&m->m, kNParams));
+  PP_A(dalloc(&m->v, kNParams));
+  PP_A(dalloc(&m->wb[0], H * kIn));
+  for (int l = 1; l < kLayers; ++l) {
+    PP_A(dalloc(&m->wb[l], H * H));
+    PP_A(dalloc(&m->wtb[l], H * H));
+  }
+  for (int l = 0; l < kLayers; ++l) {
+    PP_A(dalloc(&m->z[l], B * H));
+    PP_A(dalloc(&m->h[l], B * H));
+  }
+  PP_A(dalloc(&m->dza, B * H));
+  PP_A(dalloc(&m->dzb, B * H));
+  PP_A(dalloc(&m->t1, B * H));
+  PP_A(dalloc(&m->t2, B * H));
+  PP_A(dalloc(&m->loss, 1));
+  PP_A(dalloc(&m->err, 64));
+  PP_A(dalloc(&m->x0, (size_t)max_rows * kIn));
+  PP_A(dalloc(&m->ha, (size_t)max_rows * H));
+  PP_A(dalloc(&m->hb, (size_t)max_rows * H));
+  PP_A(cudaMemset(m->loss, 0, sizeof(double)));
+  PP_A(cudaMemset(m->err, 0, 64 * sizeof(int)));
+  PP_A(cudaMemset(m->p, 0, sizeof(float) * kNParams));
+#undef PP_A
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    pp_mlp_destroy(m);
+    return PP_ENOMEM;
+  }
+  *out = m;
+  return PP_OK;
+}
+
+int pp_mlp_destroy(pp_mlp* m) {
+  if (!m) return PP_OK;
+  cudaSetDevice(m->view.device);
+  cudaDeviceSynchronize();
+  void* bufs[] = {m->p, m->g, m->m, m->v, m->dza, m->dzb, m->t1, m->t2, m->loss, m->err, m->x0,
+                  m->ha, m->hb};
+  for (void* b : bufs) cudaFree(b);
+  for (int l = 0; l < kLayers; ++l) {
+    cudaFree(m->wb[l]);
+    cudaFree(m->wtb[l]);
+    cudaFree(m->z[l]);
+    cudaFree(m->h[l]);
+  }
+  if (m->ctx) ppk::attach_server(m->ctx, -1);
+  delete m;
+  return PP_OK;
+}
+
+const char* pp_mlp_last_error(const pp_mlp* m) { return m ? m->last_error.c_str() : "null"; }
+
+int pp_mlp_set_params(pp_mlp* m, const float* params, int64_t n) {
+  if (!m || !params || n != kNParams) return PP_EINVAL;
+  cudaStream_t st = m->view.stream;
+  PP_MLP_CUDA(cudaSetDevice(m->view.device));
+  PP_MLP_CUDA(cudaMemcpyAsync(m->p, params, sizeof(float) * kNParams, cudaMemcpyHostToDevice, st));
+  PP_MLP_CUDA(cudaMemsetAsync(m->m, 0, sizeof(float) * kNParams, st));
+  PP_MLP_CUDA(cudaMemsetAsync(m->v, 0, sizeof(float) * kNParams, st));
+  m->step = 0;
+  int rc = refresh_bf16(m, st);
+  if (rc) return rc;
+  return mlp_sync(m, st);
+}
+
+int pp_mlp_get_params(pp_mlp* m, float* params, int64_t n) {
+  if (!m || !params || n != kNParams) return PP_EINVAL;
+  PP_MLP_CUDA(cudaSetDevice(m->view.device));
+  PP_MLP_CUDA(cudaStreamSynchronize(m->view.stream));
+  PP_MLP_CUDA(cudaMemcpy(params, m->p, sizeof(float) * kNParams, cudaMemcpyDeviceToHost));
+  return PP_OK;
+}
+
+int pp_mlp_features(pp_mlp* m, const pp_source* d_src, const int32_t* d_pair_src,
+                    const int32_t* d_pair_dom, int64_t n, uint16_t* d_feat, void* stream) {
+  if (!m || n < 0 || (n > 0 && (!d_src || !d_pair_src || !d_pair_dom || !d_feat))) return PP_EINVAL;
+  PP_MLP_CUDA(cudaSetDevice(m->view.device));
+  cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : m->view.stream;
+  PP_MLP_CUDA(launch_features(m->fg, d_src, d_pair_src, d_pair_dom, n,
+                              reinterpret_cast<__nv_bfloat16*>(d_feat), st));
+  return PP_OK;
+}
+
+int pp_mlp_forward(pp_mlp* m, const uint16_t* d_feat, const float* d_nph, int64_t n,
+                   float* d_lambda, void* stream) {
+  if (!m || n < 0 || (n > 0 && (!d_feat || !d_nph || !d_lambda))) return PP_EINVAL;
+  PP_MLP_CUDA(cudaSetDevice(m->view.device));
+  cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : m->view.stream;
+  const __nv_bfloat16* f = reinterpret_cast<const __nv_bfloat16*>(d_feat);
+  for (int64_t r0 = 0; r0 < n; r0 += m->max_rows) {
+    const int rows = (int)((n - r0) < m->max_rows ? (n - r0) : m->max_rows);
+    __nv_bfloat16* hs[kLayers] = {m->ha, m->hb, m->ha, m->hb};
+    int rc;
+    if ((rc = forward_layers(m, f + r0 * kIn, rows, hs, nullptr, st))) return rc;
+    PP_MLP_CUDA(launch_head(hs[3], m->p + kOffW5, m->p + kOffB5, d_nph + r0, rows, d_lambda + r0, st));
+  }
+  return PP_OK;
+}
+
+int pp_mlp_gradients(pp_mlp* m, const uint16_t* d_feat, const float* d_nph, const float* d_count,
+                     int64_t n, float* h_grads, double* h_loss) {
+  if (!m || !d_feat || !d_nph || !d_count || !h_grads) return PP_EINVAL;
+  int rc;
+  if ((rc = check_batch(m, n))) return rc;
+  PP_MLP_CUDA(cudaSetDevice(m->view.device));
+  cudaStream_t st = m->view.stream;
+  PP_MLP_CUDA(cudaMemsetAsync(m->loss, 0, sizeof(double), st));
+  if ((rc = forward_backward(m, reinterpret_cast<const __nv_bfloat16*>(d_feat), d_nph, d_count,
+                             (int)n, st)))
+    return rc;
+  if ((rc = mlp_sync(m, st))) return rc;
+  PP_MLP_CUDA(cudaMemcpy(h_grads, m->g, sizeof(float) * kNParams, cudaMemcpyDeviceToHost));
+  if (h_loss) PP_MLP_CUDA(cudaMemcpy(h_loss, m->loss, sizeof(double), cudaMemcpyDeviceToHost));
+  return PP_OK;
+}
+
+int pp_mlp_train_step(pp_mlp* m, const uint16_t* d_feat, const float* d_nph, const float* d_count,
+                      int64_t n, float lr, void* stream) {
+  if (!m || !d_feat || !d_nph || !d_count || !(lr > 0.0f)) return PP_EINVAL;
+  int rc;
+  if ((rc = check_batch(m, n))) return rc;
+  PP_MLP_CUDA(cudaSetDevice(m->view.device));
+  cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : m->view.stream;
+  if ((rc = forward_backward(m, reinterpret_cast<const __nv_bfloat16*>(d_feat), d_nph, d_count,
+                             (int)n, st)))
+    return rc;
+  m->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float bc1 = 1.0f - (float)std::pow(0.9, (double)m->step);
+  const float bc2 = 1.0f - (float)std::pow(0.999, (double)m->step);
+  // Adam on each weight block (writing its BF16 copy) and on the rest
+  PP_MLP_CUDA(launch_adam(m->p + kOffW1, m->g + kOffW1, m->m + kOffW1, m->v + kOffW1,
+                          (int64_t)kHid * kIn, lr, b1, b2, 1e-8f, bc1, bc2, m->wb[0], st));
+  PP_MLP_CUDA(launch_adam(m->p + kOffB1, m->g + kOffB1, m->m + kOffB1, m->v + kOffB1, kHid, lr,
+                          b1, b2, 1e-8f, bc1, bc2, nullptr, st));
+  for (int l = 1; l < kLayers; ++l) {
+    const int64_t o = off_w(l);
+    PP_MLP_CUDA(launch_adam(m->p + o, m->g + o, m->m + o, m->v + o, (int64_t)kHid * kHid, lr, b1,
+                            b2, 1e-8f, bc1, bc2, m->wb[l], st));
+    const int64_t ob = off_b(l);
+    PP_MLP_CUDA(launch_adam(m->p + ob, m->g + ob, m->m + ob, m->v + ob, kHid, lr, b1, b2, 1e-8f,
+                            bc1, bc2, nullptr, st));
+    PP_MLP_CUDA(launch_transpose(m->wb[l], kHid, kHid, m->wtb[l], st));
+  }
+  PP_MLP_CUDA(launch_adam(m->p + kOffW5, m->g + kOffW5, m->m + kOffW5, m->v + kOffW5, kHid + 1,
+                          lr, b1, b2, 1e-8f, bc1, bc2, nullptr, st));
+  return PP_OK;
+}
+
+int pp_mlp_loss(pp_mlp* m, double* loss) {
+  if (!m || !loss) return PP_EINVAL;
+  int rc;
+  if ((rc = mlp_sync(m, m->view.stream))) return rc;
+  PP_MLP_CUDA(cudaMemcpy(loss, m->loss, sizeof(double), cudaMemcpyDeviceToHost));
+  PP_MLP_CUDA(cudaMemset(m->loss, 0, sizeof(double)));
+  return PP_OK;
+}
+
+int pp_mlp_dom_sums(pp_mlp* m, const pp_source* d_src, int64_t n_src, const float* d_nph_src,
+                    double* d_dom_sums, float* d_lambda, void* stream) {
+  if (!m || n_src < 0 || (n_src > 0 && (!d_src || !d_nph_src)) || (!d_dom_sums && !d_lambda))
+    return PP_EINVAL;
+  PP_MLP_CUDA(cudaSetDevice(m->view.device));
+  cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : m->view.stream;
+  const int n_dom = m->fg.n_dom;
+  if (d_dom_sums) PP_MLP_CUDA(cudaMemsetAsync(d_dom_sums, 0, sizeof(double) * n_dom, st));
+  if (n_dom == 0 || n_src == 0) return PP_OK;
+  const int64_t per = m->max_rows / n_dom;
+  if (per < 1) return mfail(m, PP_EINVAL, "max_rows is smaller than one source's DOM count");
+  for (int64_t s0 = 0; s0 < n_src; s0 += per) {
+    const int64_t ns = (n_src - s0) < per ? (n_src - s0) : per;
+    const int rows = (int)(ns * n_dom);
+    PP_MLP_CUDA(launch_features_dense(m->fg, d_src, s0, ns, m->x0, st));
+    __nv_bfloat16* hs[kLayers] = {m->ha, m->hb, m->ha, m->hb};
+    int rc;
+    if ((rc = forward_layers(m, m->x0, rows, hs, nullptr, st))) return rc;
+    PP_MLP_CUDA(launch_head_dom_sums(hs[3], m->p + kOffW5, m->p + kOffB5, d_nph_src, s0, ns, n_dom,
+                                     d_dom_sums, d_lambda ? d_lambda + s0 * n_dom : nullptr, st));
+  }
+  return PP_OK;
+}
+
+int pp_mlp_sync(pp_mlp* m) {
+  if (!m) return PP_EINVAL;
+  return mlp_sync(m, m->view.stream);
+}
+
+}  // extern "C"

@@ -78,12 +78,25 @@ _SIGS = {
     "pp_submit": [_vp, _u64, _vp, _i64, _vp],
     "pp_collect": [_vp, _u64, _vp, _vp, _i32],
     "pp_server_stats": [_vp, _vp],
+    "pp_mlp_create": [_vp, _i32, _i64, _vp],
+    "pp_mlp_destroy": [_vp],
+    "pp_mlp_set_params": [_vp, _vp, _i64],
+    "pp_mlp_get_params": [_vp, _vp, _i64],
+    "pp_mlp_features": [_vp, _vp, _vp, _vp, _i64, _vp, _vp],
+    "pp_mlp_forward": [_vp, _vp, _vp, _i64, _vp, _vp],
+    "pp_mlp_gradients": [_vp, _vp, _vp, _vp, _i64, _vp, _vp],
+    "pp_mlp_train_step": [_vp, _vp, _vp, _vp, _i64, C.c_float, _vp],
+    "pp_mlp_loss": [_vp, _vp],
+    "pp_mlp_dom_sums": [_vp, _vp, _i64, _vp, _vp, _vp, _vp],
+    "pp_mlp_sync": [_vp],
     "pp_debug_philox": [_vp, _vp, _vp, _vp, _i64],
     "pp_debug_trace": [_vp, _u64, _vp, _i64, _vp, _i64, _i32, _vp, _vp, _vp, _vp],
     "pp_debug_first_hit": [_vp, _vp, _i64, _i32, _vp, _vp],
+    "pp_debug_gemm": [_vp, _vp, _vp, _i32, _i32, _i32, _i32, _vp],
     "pp_debug_scatter": [_vp, _vp, _vp, _vp, _i64],
 }
-EXPORTS = tuple(_SIGS) + ("pp_last_error", "pp_strerror", "pp_server_last_error")
+EXPORTS = tuple(_SIGS) + ("pp_last_error", "pp_strerror", "pp_server_last_error",
+                          "pp_mlp_last_error")
 
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -95,6 +108,8 @@ _lib.pp_strerror.argtypes = [C.c_int]
 _lib.pp_strerror.restype = C.c_char_p
 _lib.pp_server_last_error.argtypes = [_vp]
 _lib.pp_server_last_error.restype = C.c_char_p
+_lib.pp_mlp_last_error.argtypes = [_vp]
+_lib.pp_mlp_last_error.restype = C.c_char_p
 
 
 class PPError(RuntimeError):
@@ -272,6 +287,22 @@ def pp_debug_scatter(ctx, dir, words, out, n):
     return _call("pp_debug_scatter", ctx, _ptr(dir), _ptr(words), _ptr(out), n)
 
 
+def pp_debug_gemm(ctx, A, B, M, N, K, swap_lbo_sbo, C):
+    return _call("pp_debug_gemm", ctx, _ptr(A), _ptr(B), M, N, K, swap_lbo_sbo, _ptr(C))
+
+
+def bf16_bits(x) -> np.ndarray:
+    """float array -> BF16 bit patterns (round to nearest even), uint16."""
+    f = np.ascontiguousarray(x, np.float32).view(np.uint32)
+    r = ((f >> 16) & 1) + 0x7FFF
+    return ((f + r) >> 16).astype(np.uint16)
+
+
+def bf16_value(bits) -> np.ndarray:
+    """BF16 bit patterns -> float32 values."""
+    return (np.asarray(bits, np.uint16).astype(np.uint32) << 16).view(np.float32)
+
+
 def pp_debug_first_hit(ctx, seg, n, mode, dom, t):
     return _call("pp_debug_first_hit", ctx, _ptr(seg), n, mode, _ptr(dom), _ptr(t))
 
@@ -374,6 +405,119 @@ class Server:
         self.close()
 
 
+# ---- learned surrogate ---------------------------------------------------------
+
+PP_MLP_N_PARAMS = 201985
+PP_MLP_INPUTS = 16
+
+
+def _mcall(name, m, *args):
+    rc = getattr(_lib, name)(m, *args)
+    if rc != PP_OK:
+        raise PPError(rc, f"{name}: {_lib.pp_mlp_last_error(m).decode() if m else pp_strerror(rc)}")
+    return rc
+
+
+def pp_mlp_create(ctx, max_batch, max_rows):
+    h = C.c_void_p()
+    rc = _lib.pp_mlp_create(ctx, max_batch, max_rows, C.byref(h))
+    if rc:
+        raise PPError(rc, f"pp_mlp_create: {pp_last_error(ctx)}")
+    return h.value
+
+
+def pp_mlp_last_error(m) -> str:
+    return _lib.pp_mlp_last_error(m).decode()
+
+
+def pp_mlp_destroy(m):
+    return _lib.pp_mlp_destroy(m)
+
+
+def pp_mlp_set_params(m, params, n):
+    return _mcall("pp_mlp_set_params", m, _ptr(params), n)
+
+
+def pp_mlp_get_params(m, params, n):
+    return _mcall("pp_mlp_get_params", m, _ptr(params), n)
+
+
+def pp_mlp_features(m, d_src, d_pair_src, d_pair_dom, n, d_feat, stream=None):
+    return _mcall("pp_mlp_features", m, _ptr(d_src), _ptr(d_pair_src), _ptr(d_pair_dom), n,
+                  _ptr(d_feat), _ptr(stream))
+
+
+def pp_mlp_forward(m, d_feat, d_nph, n, d_lambda, stream=None):
+    return _mcall("pp_mlp_forward", m, _ptr(d_feat), _ptr(d_nph), n, _ptr(d_lambda), _ptr(stream))
+
+
+def pp_mlp_gradients(m, d_feat, d_nph, d_count, n, h_grads, h_loss):
+    return _mcall("pp_mlp_gradients", m, _ptr(d_feat), _ptr(d_nph), _ptr(d_count), n,
+                  _ptr(h_grads), _ptr(h_loss))
+
+
+def pp_mlp_train_step(m, d_feat, d_nph, d_count, n, lr, stream=None):
+    return _mcall("pp_mlp_train_step", m, _ptr(d_feat), _ptr(d_nph), _ptr(d_count), n, lr,
+                  _ptr(stream))
+
+
+def pp_mlp_loss(m):
+    v = C.c_double()
+    _mcall("pp_mlp_loss", m, C.addressof(v))
+    return v.value
+
+
+def pp_mlp_dom_sums(m, d_src, n_src, d_nph_src, d_dom_sums, d_lambda=None, stream=None):
+    return _mcall("pp_mlp_dom_sums", m, _ptr(d_src), n_src, _ptr(d_nph_src), _ptr(d_dom_sums),
+                  _ptr(d_lambda), _ptr(stream))
+
+
+def pp_mlp_sync(m):
+    return _mcall("pp_mlp_sync", m)
+
+
+def mlp_init_params(seed: int = 0) -> np.ndarray:
+    """Initial parameters: weights N(0, 1/fan_in) (He-like for SiLU), zero
+    biases, b5 chosen so that softplus(b5) is a small hit probability."""
+    rng = np.random.default_rng(seed)
+    parts = [rng.normal(0.0, np.sqrt(1.0 / 16), (256, 16)), np.zeros(256)]
+    for _ in range(3):
+        parts += [rng.normal(0.0, np.sqrt(2.0 / 256), (256, 256)), np.zeros(256)]
+    parts += [rng.normal(0.0, np.sqrt(1.0 / 256), 256), np.array([-9.0])]
+    p = np.concatenate([x.ravel() for x in parts]).astype(np.float32)
+    assert p.size == PP_MLP_N_PARAMS
+    return p
+
+
+class Mlp:
+    """The surrogate on a Propagator's context (device buffers are torch tensors)."""
+
+    def __init__(self, prop, max_batch=16384, max_rows=1 << 18):
+        self.prop = prop
+        self.n_dom = prop.n_dom
+        self.handle = pp_mlp_create(prop.ctx, max_batch, max_rows)
+
+    def close(self):
+        if self.handle:
+            pp_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        pp_mlp_set_params(self.handle, p, p.size)
+
+    def get_params(self):
+        p = np.zeros(PP_MLP_N_PARAMS, np.float32)
+        pp_mlp_get_params(self.handle, p, p.size)
+        return p
+
+
 # ---- convenience wrapper ---------------------------------------------------
 
 class Propagator:
@@ -392,6 +536,7 @@ class Propagator:
         self.ctx = pp_create(cfg)
         self.n_dom = geom.n_dom
         xyz = np.ascontiguousarray(geom.xyz, np.float32).reshape(-1, 3)
+        self.geom_xyz = xyz.astype(np.float64)
         sid = np.ascontiguousarray(geom.string_id, np.int32)
         pp_load_geometry(self.ctx, xyz if xyz.size else None, sid if sid.size else None,
                          geom.n_dom, float(geom.dom_radius))

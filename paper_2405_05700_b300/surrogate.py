@@ -1,0 +1,176 @@
+"""Training and evaluation of the learned surrogate through the C ABI.
+
+Host orchestration only: sources and pair lists are prepared with numpy and
+torch (device buffers, index gathers); Monte Carlo runs in the propagation
+kernels, features, forward, backward and Adam in the surrogate's kernels.
+
+* make_training_set: sources propagated by Monte Carlo, one event per source;
+  every (source, DOM) pair within r_max becomes a training pair with its hit
+  count (pairs farther out carry no light worth learning: see DESIGN notes).
+* train: Adam steps over shuffled batches, cosine learning-rate decay.
+* evaluate: per-DOM expected hits of fresh sources from the surrogate against
+  Monte Carlo hit counts (Pearson chi2 over DOMs expecting >= 5 hits), the
+  time of each, and the hybrid that sends sources closer than r_fallback to a
+  DOM to Monte Carlo.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+import time
+
+import numpy as np
+
+from . import pp, workloads as W
+
+
+@dataclasses.dataclass
+class TrainingSet:
+    sources: np.ndarray
+    feat: object         # torch int16 [P][16] (BF16 bits), on the device
+    counts: object       # torch float32 [P]
+    nph: object          # torch float32 [P]
+    n_pairs: int
+    mc_seconds: float
+
+
+def _device_sources(src):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(src).view(np.uint8).copy()).cuda()
+
+
+def _midpoints(src):
+    d = np.stack([src["dx"], src["dy"], src["dz"]], 1).astype(np.float64)
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return np.stack([src["x"], src["y"], src["z"]], 1) + 0.5 * src["length"][:, None] * d
+
+
+def mc_hits(prop, src, event_base, chunk=2000):
+    """Monte Carlo hits [n_src][n_dom] with one event per source; returns
+    (hits, seconds of device time)."""
+    import torch
+    n, n_dom = len(src), prop.n_dom
+    out = np.zeros((n, n_dom), np.int64)
+    secs = 0.0
+    for c0 in range(0, n, chunk):
+        part = np.ascontiguousarray(src[c0:c0 + chunk])
+        m = len(part)
+        d_src = _device_sources(part)
+        ids = torch.arange(event_base + c0, event_base + c0 + m, dtype=torch.int64, device="cuda")
+        beg = torch.arange(0, m + 1, dtype=torch.int64, device="cuda")
+        hits = torch.zeros((m, n_dom), dtype=torch.int64, device="cuda")
+        cnt = torch.zeros((m, 4), dtype=torch.int64, device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream = torch.cuda.current_stream()
+        e0.record(stream)
+        pp.pp_propagate_batch_async(prop.ctx, m, ids, beg, d_src, m, hits, cnt,
+                                    stream.cuda_stream)
+        e1.record(stream)
+        pp.pp_sync(prop.ctx, stream.cuda_stream)
+        secs += e0.elapsed_time(e1) * 1e-3
+        out[c0:c0 + m] = hits.cpu().numpy()
+    return out, secs
+
+
+def make_training_set(prop, mlp, n_sources, photons, r_max=250.0, seed=0, event_base=0):
+    import torch
+    geom_xyz = _dom_xyz(prop)
+    src = W.surrogate_sources(np.random.default_rng(seed), n_sources, photons)
+    hits, secs = mc_hits(prop, src, event_base)
+    mid = _midpoints(src)
+    ps_l, pd_l, cn_l = [], [], []
+    for s0 in range(0, n_sources, 4096):
+        m = mid[s0:s0 + 4096]
+        dist = np.linalg.norm(m[:, None, :] - geom_xyz[None, :, :], axis=2)
+        s_idx, d_idx = np.nonzero(dist <= r_max)
+        ps_l.append((s_idx + s0).astype(np.int32))
+        pd_l.append(d_idx.astype(np.int32))
+        cn_l.append(hits[s_idx + s0, d_idx].astype(np.float32))
+    ps, pd, cn = np.concatenate(ps_l), np.concatenate(pd_l), np.concatenate(cn_l)
+    n_pairs = len(ps)
+    feat = torch.zeros((n_pairs, 16), dtype=torch.int16, device="cuda")
+    pp.pp_mlp_features(mlp.handle, _device_sources(src), torch.from_numpy(ps).cuda(),
+                       torch.from_numpy(pd).cuda(), n_pairs, feat)
+    pp.pp_mlp_sync(mlp.handle)
+    nph = torch.full((n_pairs,), float(photons), dtype=torch.float32, device="cuda")
+    return TrainingSet(src, feat, torch.from_numpy(cn).cuda(), nph, n_pairs, secs)
+
+
+def _dom_xyz(prop):
+    return prop.geom_xyz
+
+
+def train(mlp, data, epochs, batch=16384, lr=1e-3, lr_final_frac=0.03, seed=0, max_steps=None):
+    """Adam over shuffled batches; returns the mean loss of each epoch."""
+    import torch
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    steps_per_epoch = data.n_pairs // batch
+    total = steps_per_epoch * epochs if max_steps is None else min(max_steps, steps_per_epoch * epochs)
+    losses, k = [], 0
+    for _ in range(epochs):
+        perm = torch.randperm(data.n_pairs, device="cuda", generator=g)
+        pp.pp_mlp_loss(mlp.handle)
+        done = 0
+        for i in range(steps_per_epoch):
+            if k >= total:
+                break
+            idx = perm[i * batch:(i + 1) * batch]
+            rate = lr * (lr_final_frac + (1 - lr_final_frac) * 0.5 * (1 + math.cos(math.pi * k / max(1, total))))
+            pp.pp_mlp_train_step(mlp.handle, data.feat[idx].contiguous(), data.nph[idx].contiguous(),
+                                 data.counts[idx].contiguous(), batch, rate)
+            k += 1
+            done += 1
+        losses.append(pp.pp_mlp_loss(mlp.handle) / max(1, done))
+        if k >= total:
+            break
+    return losses
+
+
+def evaluate(prop, mlp, n_sources, photons, seed=123, event_base=10_000_000, r_fallback=None,
+             min_expected=5.0):
+    """Surrogate vs Monte Carlo on fresh sources: per-DOM sums over sources."""
+    import torch
+    src = W.surrogate_sources(np.random.default_rng(seed), n_sources, photons)
+    hits, mc_secs = mc_hits(prop, src, event_base)
+    mc_dom = hits.sum(0).astype(np.float64)
+    d_src = _device_sources(src)
+    nph = torch.full((n_sources,), float(photons), dtype=torch.float32, device="cuda")
+    sums = torch.zeros(prop.n_dom, dtype=torch.float64, device="cuda")
+    lam = torch.zeros((n_sources, prop.n_dom), dtype=torch.float32, device="cuda")
+    pp.pp_mlp_dom_sums(mlp.handle, d_src, n_sources, nph, sums, lam)   # warm
+    pp.pp_mlp_sync(mlp.handle)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    pp.pp_mlp_dom_sums(mlp.handle, d_src, n_sources, nph, sums, None)
+    e1.record()
+    pp.pp_mlp_sync(mlp.handle)
+    sur_secs = e0.elapsed_time(e1) * 1e-3
+    sur_dom = sums.cpu().numpy()
+
+    def chi2(resid2, var):
+        use = var >= min_expected
+        return float((resid2[use] / var[use]).sum()) / max(1, int(use.sum())), int(use.sum())
+
+    res = {"sources": n_sources, "photons_per_source": photons,
+           "mc_seconds": mc_secs, "surrogate_seconds": sur_secs,
+           "speedup": mc_secs / sur_secs if sur_secs > 0 else None}
+    # surrogate expectation against Monte Carlo counts (Poisson variance = expectation)
+    res["chi2_ndf"], res["ndf"] = chi2((mc_dom - sur_dom) ** 2, sur_dom)
+    if r_fallback is not None:
+        # hybrid: sources closer than r_fallback to a DOM go to Monte Carlo,
+        # the rest to the surrogate; judged against an independent Monte Carlo
+        # of all sources (variance: surrogate part's Poisson + 2 x fallback counts)
+        mid = _midpoints(src)
+        dist = np.linalg.norm(mid[:, None, :] - prop.geom_xyz[None, :, :], axis=2).min(1)
+        fb = dist < r_fallback
+        lam_h = lam.cpu().numpy().astype(np.float64)
+        hyb = lam_h[~fb].sum(0) + hits[fb].sum(0)
+        hits2, _ = mc_hits(prop, src, event_base + 5_000_000)
+        ref = hits2.sum(0).astype(np.float64)
+        var = lam_h[~fb].sum(0) + 2.0 * hits[fb].sum(0)
+        res["fallback_fraction"] = float(fb.mean())
+        res["hybrid_chi2_ndf"], res["hybrid_ndf"] = chi2((hyb - ref) ** 2, var)
+        res["hybrid_seconds"] = sur_secs * float((~fb).mean()) + mc_secs * float(fb.mean())
+        res["hybrid_speedup"] = mc_secs / res["hybrid_seconds"]
+    return res

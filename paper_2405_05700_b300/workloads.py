@@ -414,3 +414,21 @@ def serving_bunch(rng, geom: Geometry | None = None, photons_min: float = 1e4,
     share[: n_total - int(share.sum())] += 1
     src["n_photons"] = share.astype(np.uint64)
     return src
+
+
+def surrogate_sources(rng, n: int, photons: int, half_width: float = 450.0,
+                      z_range: tuple = (-500.0, 500.0)) -> np.ndarray:
+    """Light sources for the surrogate: 1 m Cherenkov segments at uniform
+    positions in the instrumented volume, isotropic directions, `photons`
+    photons each."""
+    src = make_sources(n)
+    src["x"] = rng.uniform(-half_width, half_width, n)
+    src["y"] = rng.uniform(-half_width, half_width, n)
+    src["z"] = rng.uniform(z_range[0], z_range[1], n)
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    src["dx"], src["dy"], src["dz"] = d[:, 0], d[:, 1], d[:, 2]
+    src["length"] = 1.0
+    src["type"] = SRC_CHERENKOV
+    src["n_photons"] = photons
+    return src

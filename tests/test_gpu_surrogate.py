@@ -1,0 +1,153 @@
+"""GPU parity of the learned surrogate (tensor-core MLP) against its oracle.
+
+* The tcgen05 GEMM (BF16 in, FP32 accumulate) against float64 products of the
+  same BF16 values, over the shapes the network uses.
+* Pair features against the oracle's, within one BF16 rounding step.
+* Forward lambda and every parameter's gradient against the oracle network,
+  which rounds to BF16 where the device does; the oracle's features are fed
+  to both, so the comparison isolates the network.
+* Training on the propagator's own hit counts lowers the Poisson loss.
+"""
+import numpy as np
+import pytest
+
+from paper_2405_05700_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pp():
+    from paper_2405_05700_b300 import build
+    build.build()
+    from paper_2405_05700_b300 import pp as mod
+    return mod
+
+
+@pytest.fixture(scope="module")
+def prop(pp):
+    p = pp.Propagator(W.geometry_full(), W.ice_full(), seed=11)
+    yield p
+    p.close()
+
+
+@pytest.fixture(scope="module")
+def mlp(pp, prop):
+    m = pp.Mlp(prop, max_batch=4096, max_rows=1 << 16)
+    yield m
+    m.close()
+
+
+def _dev(x, dtype=None):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(x))
+    return t.to("cuda") if dtype is None else t.to(dtype).to("cuda")
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 256, 16), (4096, 256, 256), (256, 256, 4096),
+                                   (256, 16, 4096), (300, 48, 80)])
+def test_tensor_core_gemm(pp, prop, M, N, K):
+    rng = np.random.default_rng(M + N + K)
+    A = pp.bf16_bits(rng.normal(size=(M, K)))
+    B = pp.bf16_bits(rng.normal(size=(N, K)))
+    C = np.zeros((M, N), np.float32)
+    pp.pp_debug_gemm(prop.ctx, A, B, M, N, K, 0, C)
+    ref = pp.bf16_value(A).astype(np.float64) @ pp.bf16_value(B).astype(np.float64).T
+    assert np.max(np.abs(C - ref)) <= 2e-6 * np.sqrt(K) * np.abs(ref).max() + 1e-6
+
+
+def _training_like_pairs(rng, n_src, geom):
+    src = W.make_sources(n_src)
+    src["x"] = rng.uniform(-400, 400, n_src)
+    src["y"] = rng.uniform(-400, 400, n_src)
+    src["z"] = rng.uniform(-480, 480, n_src)
+    d = rng.normal(size=(n_src, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    src["dx"], src["dy"], src["dz"] = d[:, 0], d[:, 1], d[:, 2]
+    src["length"] = 1.0
+    src["type"] = W.SRC_CHERENKOV
+    src["n_photons"] = 1000
+    ps = rng.integers(0, n_src, 4096).astype(np.int32)
+    pd = rng.integers(0, geom.n_dom, 4096).astype(np.int32)
+    return src, ps, pd
+
+
+def test_features_match_oracle(pp, prop, mlp):
+    import torch
+    from oracle import mlp as M
+    geom, ice = W.geometry_full(), W.ice_full()
+    rng = np.random.default_rng(2)
+    src, ps, pd = _training_like_pairs(rng, 300, geom)
+    feat = torch.zeros((len(ps), 16), dtype=torch.int16, device="cuda")
+    pp.pp_mlp_features(mlp.handle, _dev(src.view(np.uint8)), _dev(ps), _dev(pd), len(ps), feat)
+    pp.pp_mlp_sync(mlp.handle)
+    got = pp.bf16_value(feat.cpu().numpy().view(np.uint16)).astype(np.float64)
+    ref = M.bf16(M.features(src, ps, pd, geom.xyz, ice.b_e, ice.a, ice.depth_top, ice.dz))
+    # equal, or one BF16 step apart where FP32 and FP64 round differently
+    step = np.abs(ref) * 2.0 ** -7 + 1e-30
+    assert np.all(np.abs(got - ref) <= step * 1.01)
+    assert np.mean(got == ref) > 0.99
+
+
+def _batch(rng, n):
+    from oracle import mlp as M
+    geom, ice = W.geometry_full(), W.ice_full()
+    src, ps, pd = _training_like_pairs(rng, 500, geom)
+    x = M.bf16(M.features(src, ps[:n], pd[:n], geom.xyz, ice.b_e, ice.a, ice.depth_top, ice.dz))
+    nph = rng.uniform(1e3, 1e5, n)
+    counts = rng.poisson(2.0, n).astype(np.float64)
+    return x, nph, counts
+
+
+def test_forward_matches_oracle(pp, mlp):
+    import torch
+    from oracle import mlp as M
+    rng = np.random.default_rng(5)
+    x, nph, _ = _batch(rng, 2048)
+    p = pp.mlp_init_params(7).astype(np.float64)
+    p[-1] = -6.0
+    mlp.set_params(p.astype(np.float32))
+    p32 = p.astype(np.float32).astype(np.float64)
+    lam_ref, _ = M.forward(p32, x, nph, rounding=True)
+    feat = _dev(pp.bf16_bits(x).view(np.int16))
+    lam = torch.zeros(len(x), dtype=torch.float32, device="cuda")
+    pp.pp_mlp_forward(mlp.handle, feat, _dev(nph.astype(np.float32)), len(x), lam)
+    pp.pp_mlp_sync(mlp.handle)
+    rel = np.abs(lam.cpu().numpy() - lam_ref) / lam_ref
+    assert np.median(rel) < 2e-3 and rel.max() < 3e-2, (np.median(rel), rel.max())
+
+
+def test_gradients_match_oracle(pp, mlp):
+    from oracle import mlp as M
+    rng = np.random.default_rng(6)
+    n = 4096
+    x, nph, counts = _batch(rng, n)
+    p = pp.mlp_init_params(9).astype(np.float64)
+    p[-1] = -6.0
+    mlp.set_params(p.astype(np.float32))
+    p32 = p.astype(np.float32).astype(np.float64)
+    loss_ref, g_ref = M.loss_and_grads(p32, x, nph, counts, rounding=True)
+    g = np.zeros(pp.PP_MLP_N_PARAMS, np.float32)
+    loss = np.zeros(1)
+    pp.pp_mlp_gradients(mlp.handle, _dev(pp.bf16_bits(x).view(np.int16)),
+                        _dev(nph.astype(np.float32)), _dev(counts.astype(np.float32)), n, g, loss)
+    assert abs(loss[0] - loss_ref) <= 1e-3 * abs(loss_ref)
+    blocks = M.unpack(np.arange(M.N_PARAMS))
+    for name, idx in blocks.items():
+        idx = np.asarray(idx).ravel().astype(np.int64)
+        a, b = g[idx].astype(np.float64), g_ref[idx]
+        err = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+        assert err < 2e-2, (name, err)
+
+
+def test_training_on_propagator_counts_lowers_loss(pp, prop, mlp):
+    import torch
+    from paper_2405_05700_b300 import surrogate
+    data = surrogate.make_training_set(prop, mlp, n_sources=300, photons=20_000, r_max=200.0,
+                                       seed=1)
+    assert data.n_pairs > 16_384
+    mlp.set_params(pp.mlp_init_params(3))
+    first = surrogate.train(mlp, data, epochs=1, batch=4096, lr=2e-3, max_steps=5)
+    later = surrogate.train(mlp, data, epochs=3, batch=4096, lr=2e-3)
+    assert later[-1] < 0.8 * first[0], (first, later)
+    torch.cuda.synchronize()

@@ -1,0 +1,74 @@
+"""Pins of the surrogate's oracle (CPU only): its analytic gradients against
+central finite differences of its own loss (plain float64 network), the BF16
+rounding against the binary32/BF16 bit layout, and the features against
+hand-computed pairs."""
+import math
+
+import numpy as np
+
+from oracle import mlp as M
+from paper_2405_05700_b300 import workloads as W
+
+
+def _params(seed, scale=1.0):
+    rng = np.random.default_rng(seed)
+    p = rng.normal(0.0, 0.08 * scale, M.N_PARAMS)
+    d = M.unpack(p)
+    d["b5"] = -3.0
+    return M.pack(d)
+
+
+def test_gradients_match_finite_differences():
+    rng = np.random.default_rng(3)
+    n = 48
+    x = rng.normal(0, 1, (n, M.IN))
+    nph = rng.uniform(50, 500, n)
+    counts = rng.poisson(3.0, n).astype(np.float64)
+    p = _params(4)
+    loss, g = M.loss_and_grads(p, x, nph, counts, rounding=False)
+    idx = np.concatenate([rng.choice(M.N_PARAMS - 1, 60, replace=False), [M.N_PARAMS - 1]])
+    h = 1e-6
+    for i in idx:
+        e = np.zeros(M.N_PARAMS)
+        e[i] = h
+        lp, _ = M.loss_and_grads(p + e, x, nph, counts, rounding=False)
+        lm, _ = M.loss_and_grads(p - e, x, nph, counts, rounding=False)
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)) + 1e-7, (i, fd, g[i])
+
+
+def test_bf16_rounding_definition():
+    x = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 2 ** -7, 1.0 + 3 * 2 ** -8, -2.5, 0.0, 1e-40])
+    r = M.bf16(x)
+    assert r[0] == 1.0 and r[1] == 1.0               # tie to even (down)
+    assert r[2] == 1.0 + 2 ** -7                     # exactly representable
+    assert r[3] == 1.0 + 2 ** -6                     # tie to even (up)
+    assert r[4] == -2.5 and r[5] == 0.0
+    # every value has at most 8 significant bits
+    y = M.bf16(np.random.default_rng(0).normal(size=1000))
+    m, _ = np.frexp(y)
+    assert np.all(m * 2 ** 8 == np.round(m * 2 ** 8))
+
+
+def test_features_hand_computed():
+    src = W.make_sources(2)
+    src["x"], src["y"], src["z"] = [10.0, 0.0], [20.0, 0.0], [30.0, 0.0]
+    src["dx"], src["dy"], src["dz"] = [0.0, 1.0], [0.0, 0.0], [1.0, 0.0]
+    src["length"] = [2.0, 0.0]
+    src["type"] = W.SRC_CHERENKOV
+    doms = np.array([[10.0, 20.0, 61.0], [0.0, 5.0, 0.0]])
+    b_e = np.array([0.01, 0.02, 0.03], np.float32)
+    a = np.array([0.1, 0.2, 0.3], np.float32)
+    f = M.features(src, [0, 1], [0, 1], doms, b_e, a, depth_top=1900.0, dz=10.0)
+    # pair 0: midpoint (10, 20, 31), DOM 30 m straight above along the direction
+    assert np.allclose(f[0, 0:3], [10 / 500, 20 / 500, 31 / 500])
+    assert f[0, 3] == 0.0                                # polar angle 0
+    assert np.allclose(f[0, 5:8], [0, 0, 0.3]) and np.isclose(f[0, 13], 0.3)
+    assert np.isclose(f[0, 14], 1.0) and np.isclose(f[0, 15], math.log(31) / 5)
+    # depth 1950 - 31 = 1919 -> layer 1 of the table starting at 1900 m
+    assert np.isclose(f[0, 8], 0.2) and np.isclose(f[0, 9], 10.0)
+    # pair 1: direction +x, DOM 5 m along +y: perpendicular
+    assert np.isclose(f[1, 3], 0.5) and np.isclose(f[1, 4], 0.0)
+    assert np.isclose(f[1, 14], 0.0) and np.allclose(f[1, 10:13], [1, 0, 0])
+    # depth 1950 -> layer 5, clamped to the last row
+    assert np.isclose(f[1, 8], 0.3)
