@@ -383,9 +383,11 @@ int pp_mlp_loss(pp_mlp* mlp, double* loss);
 
 /* Dense inference over n_src sources x all DOMs: d_dom_sums[n_dom] (zeroed
  * here) receives sum over sources of lambda, and d_lambda[n_src][n_dom] (if not
- * NULL) every pair's lambda; d_nph_src[n_src] photons per source. */
+ * NULL) every pair's lambda; d_nph_src[n_src] photons per source.  Pairs
+ * farther apart than r_max (the distance range the network was trained on)
+ * count zero. */
 int pp_mlp_dom_sums(pp_mlp* mlp, const pp_source* d_src, int64_t n_src, const float* d_nph_src,
-                    double* d_dom_sums, float* d_lambda, void* stream);
+                    float r_max, double* d_dom_sums, float* d_lambda, void* stream);
 
 /* Waits for the MLP's work and reports a device error flag. */
 int pp_mlp_sync(pp_mlp* mlp);

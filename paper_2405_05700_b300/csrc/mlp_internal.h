@@ -67,10 +67,12 @@ cudaError_t launch_head_backward(const __nv_bfloat16* h, const __nv_bfloat16* z4
                                  const float* b5, const float* nph, const float* cnt, int64_t n,
                                  float inv_n, __nv_bfloat16* dz4, float* dw5, float* db5,
                                  double* loss, cudaStream_t st);
-// Head over dense pairs, summed per DOM: dom_sum[d] += lambda(s, d).
+// Head over dense pairs, summed per DOM: dom_sum[d] += lambda(s, d), zero for
+// pairs farther apart than r_max (read from the features).
 cudaError_t launch_head_dom_sums(const __nv_bfloat16* h, const float* w5, const float* b5,
                                  const float* nph_src, int64_t s0, int64_t ns, int n_dom,
-                                 double* dom_sum, float* lambda_out, cudaStream_t st);
+                                 const __nv_bfloat16* feat, float r_max, double* dom_sum,
+                                 float* lambda_out, cudaStream_t st);
 
 cudaError_t launch_transpose(const __nv_bfloat16* in, int rows, int cols, __nv_bfloat16* out,
                              cudaStream_t st);

@@ -247,13 +247,17 @@ __global__ void k_head(const __nv_bfloat16* h, const float* w5, const float* b5,
 
 __global__ void k_head_dom(const __nv_bfloat16* h, const float* w5, const float* b5,
                            const float* nph_src, int64_t s0, int64_t ns, int n_dom,
-                           double* dom_sum, float* lambda_out) {
+                           const __nv_bfloat16* feat, float r_max, double* dom_sum,
+                           float* lambda_out) {
   const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (p >= ns * n_dom) return;
   const float z = head_z(h + p * kHid, w5, *b5);
   if ((threadIdx.x & 31) == 0) {
     const int64_t s = s0 + p / n_dom;
-    const float lam = nph_src[s] * softplus(z);
+    // pairs farther apart than r_max lie outside the trained domain and
+    // receive no light worth counting: zero
+    const float r = 100.0f * __bfloat162float(feat[p * kIn + 13]);
+    const float lam = r > r_max ? 0.0f : nph_src[s] * softplus(z);
     if (dom_sum) atomicAdd(dom_sum + (p % n_dom), (double)lam);
     if (lambda_out) lambda_out[p] = lam;
   }
@@ -394,11 +398,12 @@ cudaError_t launch_head_backward(const __nv_bfloat16* h, const __nv_bfloat16* z4
 
 cudaError_t launch_head_dom_sums(const __nv_bfloat16* h, const float* w5, const float* b5,
                                  const float* nph_src, int64_t s0, int64_t ns, int n_dom,
-                                 double* dom_sum, float* lambda_out, cudaStream_t st) {
+                                 const __nv_bfloat16* feat, float r_max, double* dom_sum,
+                                 float* lambda_out, cudaStream_t st) {
   const int64_t n = ns * n_dom;
   if (n <= 0) return cudaSuccess;
-  k_head_dom<<<blocks_for(n * 32, 256), 256, 0, st>>>(h, w5, b5, nph_src, s0, ns, n_dom, dom_sum,
-                                                      lambda_out);
+  k_head_dom<<<blocks_for(n * 32, 256), 256, 0, st>>>(h, w5, b5, nph_src, s0, ns, n_dom, feat,
+                                                      r_max, dom_sum, lambda_out);
   return cudaGetLastError();
 }
 

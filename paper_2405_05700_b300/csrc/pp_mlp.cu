@@ -365,7 +365,7 @@ int pp_mlp_loss(pp_mlp* m, double* loss) {
 }
 
 int pp_mlp_dom_sums(pp_mlp* m, const pp_source* d_src, int64_t n_src, const float* d_nph_src,
-                    double* d_dom_sums, float* d_lambda, void* stream) {
+                    float r_max, double* d_dom_sums, float* d_lambda, void* stream) {
   if (!m || n_src < 0 || (n_src > 0 && (!d_src || !d_nph_src)) || (!d_dom_sums && !d_lambda))
     return PP_EINVAL;
   PP_MLP_CUDA(cudaSetDevice(m->view.device));
@@ -383,7 +383,8 @@ int pp_mlp_dom_sums(pp_mlp* m, const pp_source* d_src, int64_t n_src, const floa
     int rc;
     if ((rc = forward_layers(m, m->x0, rows, hs, nullptr, st))) return rc;
     PP_MLP_CUDA(launch_head_dom_sums(hs[3], m->p + kOffW5, m->p + kOffB5, d_nph_src, s0, ns, n_dom,
-                                     d_dom_sums, d_lambda ? d_lambda + s0 * n_dom : nullptr, st));
+                                     m->x0, r_max, d_dom_sums,
+                                     d_lambda ? d_lambda + s0 * n_dom : nullptr, st));
   }
   return PP_OK;
 }

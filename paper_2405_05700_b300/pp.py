@@ -87,7 +87,7 @@ _SIGS = {
     "pp_mlp_gradients": [_vp, _vp, _vp, _vp, _i64, _vp, _vp],
     "pp_mlp_train_step": [_vp, _vp, _vp, _vp, _i64, C.c_float, _vp],
     "pp_mlp_loss": [_vp, _vp],
-    "pp_mlp_dom_sums": [_vp, _vp, _i64, _vp, _vp, _vp, _vp],
+    "pp_mlp_dom_sums": [_vp, _vp, _i64, _vp, C.c_float, _vp, _vp, _vp],
     "pp_mlp_sync": [_vp],
     "pp_debug_philox": [_vp, _vp, _vp, _vp, _i64],
     "pp_debug_trace": [_vp, _u64, _vp, _i64, _vp, _i64, _i32, _vp, _vp, _vp, _vp],
@@ -467,9 +467,9 @@ def pp_mlp_loss(m):
     return v.value
 
 
-def pp_mlp_dom_sums(m, d_src, n_src, d_nph_src, d_dom_sums, d_lambda=None, stream=None):
-    return _mcall("pp_mlp_dom_sums", m, _ptr(d_src), n_src, _ptr(d_nph_src), _ptr(d_dom_sums),
-                  _ptr(d_lambda), _ptr(stream))
+def pp_mlp_dom_sums(m, d_src, n_src, d_nph_src, r_max, d_dom_sums, d_lambda=None, stream=None):
+    return _mcall("pp_mlp_dom_sums", m, _ptr(d_src), n_src, _ptr(d_nph_src), r_max,
+                  _ptr(d_dom_sums), _ptr(d_lambda), _ptr(stream))
 
 
 def pp_mlp_sync(m):
@@ -533,6 +533,7 @@ class Propagator:
         cfg.depth_of_z0_m = depth_of_z0
         cfg.scatter_coeff_is_effective = 1 if scatter_coeff_is_effective else 0
         cfg.stream = _ptr(stream)
+        self.stream = cfg.stream    # the context's stream handle (None: its own)
         self.ctx = pp_create(cfg)
         self.n_dom = geom.n_dom
         xyz = np.ascontiguousarray(geom.xyz, np.float32).reshape(-1, 3)

@@ -49,6 +49,13 @@ def mc_hits(prop, src, event_base, chunk=2000):
     """Monte Carlo hits [n_src][n_dom] with one event per source; returns
     (hits, seconds of device time)."""
     import torch
+    stream = _stream(prop)
+    with torch.cuda.stream(stream):
+        return _mc_hits(prop, src, event_base, chunk, stream)
+
+
+def _mc_hits(prop, src, event_base, chunk, stream):
+    import torch
     n, n_dom = len(src), prop.n_dom
     out = np.zeros((n, n_dom), np.int64)
     secs = 0.0
@@ -61,7 +68,6 @@ def mc_hits(prop, src, event_base, chunk=2000):
         hits = torch.zeros((m, n_dom), dtype=torch.int64, device="cuda")
         cnt = torch.zeros((m, 4), dtype=torch.int64, device="cuda")
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        stream = torch.cuda.current_stream()
         e0.record(stream)
         pp.pp_propagate_batch_async(prop.ctx, m, ids, beg, d_src, m, hits, cnt,
                                     stream.cuda_stream)
@@ -72,7 +78,23 @@ def mc_hits(prop, src, event_base, chunk=2000):
     return out, secs
 
 
+def _stream(prop):
+    """The torch view of the context's CUDA stream: torch ops of this module
+    run on it, so they are ordered with the library's work (the Propagator
+    must have been created with an explicit stream)."""
+    import torch
+    if not prop.stream:
+        raise ValueError("create the Propagator with stream=<a CUDA stream handle>")
+    return torch.cuda.ExternalStream(prop.stream)
+
+
 def make_training_set(prop, mlp, n_sources, photons, r_max=250.0, seed=0, event_base=0):
+    import torch
+    with torch.cuda.stream(_stream(prop)):
+        return _make_training_set(prop, mlp, n_sources, photons, r_max, seed, event_base)
+
+
+def _make_training_set(prop, mlp, n_sources, photons, r_max, seed, event_base):
     import torch
     geom_xyz = _dom_xyz(prop)
     src = W.surrogate_sources(np.random.default_rng(seed), n_sources, photons)
@@ -103,6 +125,12 @@ def _dom_xyz(prop):
 def train(mlp, data, epochs, batch=16384, lr=1e-3, lr_final_frac=0.03, seed=0, max_steps=None):
     """Adam over shuffled batches; returns the mean loss of each epoch."""
     import torch
+    with torch.cuda.stream(_stream(mlp.prop)):
+        return _train(mlp, data, epochs, batch, lr, lr_final_frac, seed, max_steps)
+
+
+def _train(mlp, data, epochs, batch, lr, lr_final_frac, seed, max_steps):
+    import torch
     g = torch.Generator(device="cuda")
     g.manual_seed(seed)
     steps_per_epoch = data.n_pairs // batch
@@ -128,8 +156,15 @@ def train(mlp, data, epochs, batch=16384, lr=1e-3, lr_final_frac=0.03, seed=0, m
 
 
 def evaluate(prop, mlp, n_sources, photons, seed=123, event_base=10_000_000, r_fallback=None,
-             min_expected=5.0):
+             min_expected=5.0, r_max=250.0):
     """Surrogate vs Monte Carlo on fresh sources: per-DOM sums over sources."""
+    import torch
+    with torch.cuda.stream(_stream(prop)):
+        return _evaluate(prop, mlp, n_sources, photons, seed, event_base, r_fallback,
+                         min_expected, r_max)
+
+
+def _evaluate(prop, mlp, n_sources, photons, seed, event_base, r_fallback, min_expected, r_max):
     import torch
     src = W.surrogate_sources(np.random.default_rng(seed), n_sources, photons)
     hits, mc_secs = mc_hits(prop, src, event_base)
@@ -138,12 +173,15 @@ def evaluate(prop, mlp, n_sources, photons, seed=123, event_base=10_000_000, r_f
     nph = torch.full((n_sources,), float(photons), dtype=torch.float32, device="cuda")
     sums = torch.zeros(prop.n_dom, dtype=torch.float64, device="cuda")
     lam = torch.zeros((n_sources, prop.n_dom), dtype=torch.float32, device="cuda")
-    pp.pp_mlp_dom_sums(mlp.handle, d_src, n_sources, nph, sums, lam)   # warm
-    pp.pp_mlp_sync(mlp.handle)
+    st = _stream(prop)
+    torch.cuda.synchronize()
+    pp.pp_mlp_dom_sums(mlp.handle, d_src, n_sources, nph, r_max, sums, lam, st.cuda_stream)  # warm
+    st.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    pp.pp_mlp_dom_sums(mlp.handle, d_src, n_sources, nph, sums, None)
-    e1.record()
+    e0.record(st)
+    pp.pp_mlp_dom_sums(mlp.handle, d_src, n_sources, nph, r_max, sums, None, st.cuda_stream)
+    e1.record(st)
+    st.synchronize()
     pp.pp_mlp_sync(mlp.handle)
     sur_secs = e0.elapsed_time(e1) * 1e-3
     sur_dom = sums.cpu().numpy()

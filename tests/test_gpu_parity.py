@@ -273,6 +273,7 @@ def test_autotuner_picks_a_listed_setting_and_keeps_results(full, pp):
     d_beg = torch.from_numpy(b.src_begin.astype(np.int64)).to(dev)
     d_h = torch.zeros((b.n_events, 5160), dtype=torch.int64, device=dev)
     d_c = torch.zeros((b.n_events, 4), dtype=torch.int64, device=dev)
+    torch.cuda.synchronize()   # torch's work is on its stream, the library's on the context's
     try:
         best, ms = pp.pp_autotune_batch(full.ctx, b.n_events, d_ids, d_beg, d_src, len(src), d_h,
                                         d_c, None, 1)
@@ -329,6 +330,7 @@ def test_event_in_photon_ranges_equals_one_pass(full, pp):
     d_src = torch.from_numpy(src.view(np.uint8).copy()).to(dev)
     d_h = torch.zeros(5160, dtype=torch.int64, device=dev)
     d_c = torch.zeros(4, dtype=torch.int64, device=dev)
+    torch.cuda.synchronize()
     cuts = [0, 1, 777_777, 1_500_000, 2_999_999, total]
     order = [3, 0, 4, 2, 1]                      # any order, accumulated
     for j, i in enumerate(order):

@@ -26,9 +26,16 @@ def pp():
 
 @pytest.fixture(scope="module")
 def prop(pp):
-    p = pp.Propagator(W.geometry_full(), W.ice_full(), seed=11)
+    # one stream for the library and for torch, so their work is ordered
+    import torch
+    st = torch.cuda.Stream()
+    prev = torch.cuda.current_stream()
+    torch.cuda.set_stream(st)
+    p = pp.Propagator(W.geometry_full(), W.ice_full(), seed=11, stream=st.cuda_stream)
     yield p
     p.close()
+    torch.cuda.synchronize()
+    torch.cuda.set_stream(prev)
 
 
 @pytest.fixture(scope="module")

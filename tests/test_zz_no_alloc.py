@@ -36,6 +36,7 @@ def test_noalloc_matches_allocating_entry_point_twice_in_a_row():
             d_src = torch.from_numpy(src.view(np.uint8).copy()).to(dev)
             d_hits = torch.full((geom.n_dom,), -1, dtype=torch.int64, device=dev)
             d_counts = torch.full((4,), -1, dtype=torch.int64, device=dev)
+            torch.cuda.synchronize()   # torch's fills are on its stream, the call on the context's
             pp.pp_propagate_noalloc(prop.ctx, ev_id, d_src, len(src), d_hits, d_counts)
             pp.pp_sync(prop.ctx)
             got_h = d_hits.cpu().numpy().astype(np.uint64)
