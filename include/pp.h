@@ -389,6 +389,13 @@ int pp_mlp_loss(pp_mlp* mlp, double* loss);
 int pp_mlp_dom_sums(pp_mlp* mlp, const pp_source* d_src, int64_t n_src, const float* d_nph_src,
                     float r_max, double* d_dom_sums, float* d_lambda, void* stream);
 
+/* The (source, DOM) pairs closer than r_max (segment midpoint to DOM centre),
+ * in unspecified order: the first max_out go to d_pair_src / d_pair_dom, and
+ * *h_count receives how many there are (may exceed max_out).  Synchronous. */
+int pp_mlp_near_pairs(pp_mlp* mlp, const pp_source* d_src, int64_t n_src, float r_max,
+                      int64_t max_out, int32_t* d_pair_src, int32_t* d_pair_dom,
+                      uint64_t* h_count);
+
 /* Waits for the MLP's work and reports a device error flag. */
 int pp_mlp_sync(pp_mlp* mlp);
 

@@ -53,9 +53,6 @@ struct FeatGeom {
 cudaError_t launch_features(const FeatGeom& fg, const pp_source* src, const int32_t* pair_src,
                             const int32_t* pair_dom, int64_t n, __nv_bfloat16* feat,
                             cudaStream_t st);
-// Features of all pairs of sources [s0, s0 + ns) x DOMs [0, n_dom), row = s * n_dom + d.
-cudaError_t launch_features_dense(const FeatGeom& fg, const pp_source* src, int64_t s0,
-                                  int64_t ns, __nv_bfloat16* feat, cudaStream_t st);
 
 // Head z = h . w5 + b5, lambda = nph * softplus(z).
 cudaError_t launch_head(const __nv_bfloat16* h, const float* w5, const float* b5,
@@ -67,12 +64,16 @@ cudaError_t launch_head_backward(const __nv_bfloat16* h, const __nv_bfloat16* z4
                                  const float* b5, const float* nph, const float* cnt, int64_t n,
                                  float inv_n, __nv_bfloat16* dz4, float* dw5, float* db5,
                                  double* loss, cudaStream_t st);
-// Head over dense pairs, summed per DOM: dom_sum[d] += lambda(s, d), zero for
-// pairs farther apart than r_max (read from the features).
-cudaError_t launch_head_dom_sums(const __nv_bfloat16* h, const float* w5, const float* b5,
-                                 const float* nph_src, int64_t s0, int64_t ns, int n_dom,
-                                 const __nv_bfloat16* feat, float r_max, double* dom_sum,
-                                 float* lambda_out, cudaStream_t st);
+
+// Pairs of sources [s0, s0+ns) x DOMs within r_max into (ps, pd); *count += all of them
+// (only the first max_out are written).
+cudaError_t launch_near_pairs(const FeatGeom& fg, const pp_source* src, int64_t s0, int64_t ns,
+                              float r_max, int64_t max_out, int32_t* ps, int32_t* pd,
+                              unsigned long long* count, cudaStream_t st);
+// Head over listed pairs: dom_sum[pd] += lambda, lambda_out[ps][pd] = lambda.
+cudaError_t launch_head_pairs(const __nv_bfloat16* h, const float* w5, const float* b5,
+                              const float* nph_src, const int32_t* ps, const int32_t* pd, int64_t n,
+                              int n_dom, double* dom_sum, float* lambda_out, cudaStream_t st);
 
 cudaError_t launch_transpose(const __nv_bfloat16* in, int rows, int cols, __nv_bfloat16* out,
                              cudaStream_t st);

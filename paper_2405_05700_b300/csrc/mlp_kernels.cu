@@ -29,27 +29,41 @@ __device__ __forceinline__ uint32_t pow2_cols(int n) {
 
 // Copies rows [r0, r0 + rows) x K columns [k0, k0 + kBK) of a row-major BF16
 // matrix (leading dimension ld) into a K-major no-swizzle smem tile; rows or
-// columns outside (n_rows, K) are zero.
+// columns outside (n_rows, K) are zero.  Four 16-byte loads are in flight per
+// thread before their stores.
 __device__ __forceinline__ void stage_tile(unsigned char* tile, const __nv_bfloat16* X, int ld,
                                            int n_rows, int K, int r0, int rows, int k0) {
   const int chunks = rows * (kBK / 8);
-  for (int i = threadIdx.x; i < chunks; i += blockDim.x) {
-    const int r = i >> 3, c = i & 7;
-    const int gr = r0 + r, gk = k0 + c * 8;
-    uint4 v = make_uint4(0, 0, 0, 0);
-    if (gr < n_rows && gk < K) v = *reinterpret_cast<const uint4*>(X + (size_t)gr * ld + gk);
-    *reinterpret_cast<uint4*>(tile + tc::tile_off(r, c * 8, kBK)) = v;
+  const int step = blockDim.x;
+  for (int base = threadIdx.x; base < chunks; base += 4 * step) {
+    uint4 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = base + u * step;
+      const int r = i >> 3, c = i & 7;
+      const int gr = r0 + r, gk = k0 + c * 8;
+      v[u] = make_uint4(0, 0, 0, 0);
+      if (i < chunks && gr < n_rows && gk < K)
+        v[u] = *reinterpret_cast<const uint4*>(X + (size_t)gr * ld + gk);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = base + u * step;
+      if (i < chunks)
+        *reinterpret_cast<uint4*>(tile + tc::tile_off(i >> 3, (i & 7) * 8, kBK)) = v[u];
+    }
   }
 }
 
+// Two operand stages: while the tensor core works on one, the threads stage
+// the next K slice into the other.
 template <int EPI>
 __global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ uint32_t tslot;
-  __shared__ __align__(8) uint64_t bar;
-  unsigned char* sA = smem;                         // 128 x 64 BF16 = 16 KB
-  unsigned char* sB = smem + kBM * kBK * 2;         // BN x 64 BF16
+  __shared__ __align__(8) uint64_t bar[2];
   const int BN = g.bn;
+  const int stage = (kBM + BN) * kBK * 2;
   const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
   // split K: this CTA runs K range [kb, ke)
   const int kc = g.k_split > 1 ? ((g.K + g.k_split * kBK - 1) / (g.k_split * kBK)) * kBK : g.K;
@@ -59,7 +73,8 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
   const uint32_t ncols = pow2_cols(BN);
   if (warp == 0) tc::tmem_alloc(&tslot, ncols);
   if (threadIdx.x == 0) {
-    tc::mbar_init(&bar, 1);
+    tc::mbar_init(&bar[0], 1);
+    tc::mbar_init(&bar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc::fence_before_sync();
@@ -71,9 +86,21 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
   // kBK * 16 B apart (exchanged when probing the layout)
   const uint32_t lbo = g.swap_lbo_sbo ? kBK * 16 : 128;
   const uint32_t sbo = g.swap_lbo_sbo ? 128 : kBK * 16;
-  uint32_t phase = 0;
+  uint32_t phase[2] = {0u, 0u};
+  bool pending[2] = {false, false};
   bool ok = true;
-  for (int k0 = kb; k0 < ke && ok; k0 += kBK) {
+  int it = 0;
+  for (int k0 = kb; k0 < ke; k0 += kBK, ++it) {
+    const int b = it & 1;
+    if (pending[b]) {  // the MMAs that read this stage two rounds ago must be done
+      const bool done = tc::mbar_wait(&bar[b], phase[b], kWaitTries);
+      phase[b] ^= 1u;
+      pending[b] = false;
+      ok = __syncthreads_and(done);
+      if (!ok) break;
+    }
+    unsigned char* sA = smem + b * stage;
+    unsigned char* sB = sA + kBM * kBK * 2;
     stage_tile(sA, g.A, g.lda, g.M, ke, m0, kBM, k0);
     stage_tile(sB, g.B, g.ldb, g.N, ke, n0, BN, k0);
     tc::fence_smem_async();
@@ -87,13 +114,18 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
         tc::mma_bf16(taddr, tc::smem_desc(a0 + 256 * s, lbo, sbo),
                      tc::smem_desc(b0 + 256 * s, lbo, sbo), idesc, (k0 > kb || s > 0) ? 1u : 0u);
       }
-      tc::mma_commit(&bar);
+      tc::mma_commit(&bar[b]);
     }
-    const bool done = tc::mbar_wait(&bar, phase, kWaitTries);
-    phase ^= 1u;
-    ok = __syncthreads_and(done);
-    tc::fence_after_sync();
+    pending[b] = true;
   }
+  // drain the stages still in flight (MMAs complete in issue order)
+  for (int b = 0; b < 2; ++b) {
+    if (!pending[b]) continue;
+    const bool done = tc::mbar_wait(&bar[b], phase[b], kWaitTries);
+    phase[b] ^= 1u;
+    ok = __syncthreads_and(done && ok);
+  }
+  tc::fence_after_sync();
   if (!ok) {
     if (threadIdx.x == 0) atomicOr(g.err, 1);
   } else if (kb < ke) {
@@ -131,7 +163,7 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
 
 }  // namespace
 
-size_t gemm_smem_bytes(int bn) { return (size_t)(kBM + bn) * kBK * 2 + 1024; }
+size_t gemm_smem_bytes(int bn) { return 2 * (size_t)(kBM + bn) * kBK * 2 + 1024; }
 
 cudaError_t launch_gemm(const GemmArgs& g, int epi, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0 || g.K <= 0) return cudaSuccess;
@@ -212,15 +244,6 @@ __global__ void k_features(FeatGeom fg, const pp_source* src, const int32_t* ps,
   pair_features(fg, src[ps[i]], fg.dom[pd[i]], feat + i * kIn);
 }
 
-__global__ void k_features_dense(FeatGeom fg, const pp_source* src, int64_t s0, int64_t ns,
-                                 __nv_bfloat16* feat) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= ns * fg.n_dom) return;
-  const int64_t s = s0 + i / fg.n_dom;
-  const int d = (int)(i % fg.n_dom);
-  pair_features(fg, src[s], fg.dom[d], feat + i * kIn);
-}
-
 // ------------------------------------------------------------------ head --
 __device__ __forceinline__ float softplus(float z) { return z > 20.0f ? z : log1pf(__expf(z)); }
 
@@ -243,24 +266,6 @@ __global__ void k_head(const __nv_bfloat16* h, const float* w5, const float* b5,
   if (p >= n) return;
   const float z = head_z(h + p * kHid, w5, *b5);
   if ((threadIdx.x & 31) == 0) lambda[p] = nph[p] * softplus(z);
-}
-
-__global__ void k_head_dom(const __nv_bfloat16* h, const float* w5, const float* b5,
-                           const float* nph_src, int64_t s0, int64_t ns, int n_dom,
-                           const __nv_bfloat16* feat, float r_max, double* dom_sum,
-                           float* lambda_out) {
-  const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (p >= ns * n_dom) return;
-  const float z = head_z(h + p * kHid, w5, *b5);
-  if ((threadIdx.x & 31) == 0) {
-    const int64_t s = s0 + p / n_dom;
-    // pairs farther apart than r_max lie outside the trained domain and
-    // receive no light worth counting: zero
-    const float r = 100.0f * __bfloat162float(feat[p * kIn + 13]);
-    const float lam = r > r_max ? 0.0f : nph_src[s] * softplus(z);
-    if (dom_sum) atomicAdd(dom_sum + (p % n_dom), (double)lam);
-    if (lambda_out) lambda_out[p] = lam;
-  }
 }
 
 constexpr int kHeadPairs = 64;  // pairs per block of the head backward
@@ -312,6 +317,62 @@ __global__ void __launch_bounds__(256) k_head_bwd(const __nv_bfloat16* h, const 
   if (lane == 0) {
     if (gsum != 0.0f) atomicAdd(db5, gsum);
     if (lsum != 0.0) atomicAdd(loss, lsum);
+  }
+}
+
+// Pairs of sources [s0, s0 + ns) x all DOMs whose distance (segment midpoint
+// to DOM centre, as in the features) is at most r_max, appended in any order
+// (one atomic per warp); at most max_out are written, *count counts them all.
+__global__ void k_near_pairs(FeatGeom fg, const pp_source* src, int64_t s0, int64_t ns,
+                             float r_max, int64_t max_out, int32_t* ps, int32_t* pd,
+                             unsigned long long* count) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool near = false;
+  int64_t s = 0;
+  int d = 0;
+  if (i < ns * fg.n_dom) {
+    s = s0 + i / fg.n_dom;
+    d = (int)(i % fg.n_dom);
+    const pp_source q = src[s];
+    float dx = q.dx, dy = q.dy, dz = q.dz;
+    const float nn = sqrtf(dx * dx + dy * dy + dz * dz);
+    if (nn > 0.0f) {
+      dx /= nn;
+      dy /= nn;
+      dz /= nn;
+    }
+    const float h = 0.5f * q.length;
+    const float4 c = fg.dom[d];
+    const float ex = c.x - (q.x + h * dx), ey = c.y - (q.y + h * dy), ez = c.z - (q.z + h * dz);
+    near = sqrtf(ex * ex + ey * ey + ez * ez) <= r_max;
+  }
+  const unsigned mask = __ballot_sync(0xffffffffu, near);
+  if (!mask) return;
+  const int lane = threadIdx.x & 31;
+  unsigned long long base = 0;
+  if (lane == __ffs(mask) - 1) base = atomicAdd(count, (unsigned long long)__popc(mask));
+  base = __shfl_sync(0xffffffffu, base, __ffs(mask) - 1);
+  if (near) {
+    const unsigned long long o = base + __popc(mask & ((1u << lane) - 1u));
+    if ((int64_t)o < max_out) {
+      ps[o] = (int32_t)s;
+      pd[o] = d;
+    }
+  }
+}
+
+// Head over listed pairs: dom_sum[d] += lambda, lambda_out[s][d] = lambda.
+__global__ void k_head_pairs(const __nv_bfloat16* h, const float* w5, const float* b5,
+                             const float* nph_src, const int32_t* ps, const int32_t* pd,
+                             int64_t n, int n_dom, double* dom_sum, float* lambda_out) {
+  const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (p >= n) return;
+  const float z = head_z(h + p * kHid, w5, *b5);
+  if ((threadIdx.x & 31) == 0) {
+    const int s = ps[p], d = pd[p];
+    const float lam = nph_src[s] * softplus(z);
+    if (dom_sum) atomicAdd(dom_sum + d, (double)lam);
+    if (lambda_out) lambda_out[(size_t)s * n_dom + d] = lam;
   }
 }
 
@@ -371,14 +432,6 @@ cudaError_t launch_features(const FeatGeom& fg, const pp_source* src, const int3
   return cudaGetLastError();
 }
 
-cudaError_t launch_features_dense(const FeatGeom& fg, const pp_source* src, int64_t s0,
-                                  int64_t ns, __nv_bfloat16* feat, cudaStream_t st) {
-  const int64_t n = ns * fg.n_dom;
-  if (n <= 0) return cudaSuccess;
-  k_features_dense<<<blocks_for(n, 256), 256, 0, st>>>(fg, src, s0, ns, feat);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_head(const __nv_bfloat16* h, const float* w5, const float* b5,
                         const float* nph, int64_t n, float* lambda, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
@@ -396,14 +449,21 @@ cudaError_t launch_head_backward(const __nv_bfloat16* h, const __nv_bfloat16* z4
   return cudaGetLastError();
 }
 
-cudaError_t launch_head_dom_sums(const __nv_bfloat16* h, const float* w5, const float* b5,
-                                 const float* nph_src, int64_t s0, int64_t ns, int n_dom,
-                                 const __nv_bfloat16* feat, float r_max, double* dom_sum,
-                                 float* lambda_out, cudaStream_t st) {
-  const int64_t n = ns * n_dom;
+cudaError_t launch_near_pairs(const FeatGeom& fg, const pp_source* src, int64_t s0, int64_t ns,
+                              float r_max, int64_t max_out, int32_t* ps, int32_t* pd,
+                              unsigned long long* count, cudaStream_t st) {
+  const int64_t n = ns * fg.n_dom;
   if (n <= 0) return cudaSuccess;
-  k_head_dom<<<blocks_for(n * 32, 256), 256, 0, st>>>(h, w5, b5, nph_src, s0, ns, n_dom, feat,
-                                                      r_max, dom_sum, lambda_out);
+  k_near_pairs<<<blocks_for(n, 256), 256, 0, st>>>(fg, src, s0, ns, r_max, max_out, ps, pd, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_head_pairs(const __nv_bfloat16* h, const float* w5, const float* b5,
+                              const float* nph_src, const int32_t* ps, const int32_t* pd, int64_t n,
+                              int n_dom, double* dom_sum, float* lambda_out, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_head_pairs<<<blocks_for(n * 32, 256), 256, 0, st>>>(h, w5, b5, nph_src, ps, pd, n, n_dom,
+                                                        dom_sum, lambda_out);
   return cudaGetLastError();
 }
 

@@ -62,6 +62,8 @@ struct pp_mlp {
   int* err = nullptr;
   // inference buffers [max_rows]
   __nv_bfloat16 *x0 = nullptr, *ha = nullptr, *hb = nullptr;
+  int32_t *ps = nullptr, *pd = nullptr;
+  unsigned long long* count = nullptr;
 };
 
 namespace {
@@ -225,6 +227,9 @@ int pp_mlp_create(pp_ctx* ctx, int32_t max_batch, int64_t max_rows, pp_mlp** out
   PP_A(dalloc(&m->x0, (size_t)max_rows * kIn));
   PP_A(dalloc(&m->ha, (size_t)max_rows * H));
   PP_A(dalloc(&m->hb, (size_t)max_rows * H));
+  PP_A(dalloc(&m->ps, (size_t)max_rows));
+  PP_A(dalloc(&m->pd, (size_t)max_rows));
+  PP_A(dalloc(&m->count, 1));
   PP_A(cudaMemset(m->loss, 0, sizeof(double)));
   PP_A(cudaMemset(m->err, 0, 64 * sizeof(int)));
   PP_A(cudaMemset(m->p, 0, sizeof(float) * kNParams));
@@ -243,7 +248,7 @@ int pp_mlp_destroy(pp_mlp* m) {
   cudaSetDevice(m->view.device);
   cudaDeviceSynchronize();
   void* bufs[] = {m->p, m->g, m->m, m->v, m->dza, m->dzb, m->t1, m->t2, m->loss, m->err, m->x0,
-                  m->ha, m->hb};
+                  m->ha, m->hb, m->ps, m->pd, m->count};
   for (void* b : bufs) cudaFree(b);
   for (int l = 0; l < kLayers; ++l) {
     cudaFree(m->wb[l]);
@@ -366,26 +371,62 @@ int pp_mlp_loss(pp_mlp* m, double* loss) {
 
 int pp_mlp_dom_sums(pp_mlp* m, const pp_source* d_src, int64_t n_src, const float* d_nph_src,
                     float r_max, double* d_dom_sums, float* d_lambda, void* stream) {
-  if (!m || n_src < 0 || (n_src > 0 && (!d_src || !d_nph_src)) || (!d_dom_sums && !d_lambda))
+  if (!m || n_src < 0 || (n_src > 0 && (!d_src || !d_nph_src)) || (!d_dom_sums && !d_lambda) ||
+      !(r_max > 0.0f))
     return PP_EINVAL;
   PP_MLP_CUDA(cudaSetDevice(m->view.device));
   cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : m->view.stream;
   const int n_dom = m->fg.n_dom;
   if (d_dom_sums) PP_MLP_CUDA(cudaMemsetAsync(d_dom_sums, 0, sizeof(double) * n_dom, st));
+  if (d_lambda)
+    PP_MLP_CUDA(cudaMemsetAsync(d_lambda, 0, sizeof(float) * (size_t)n_src * n_dom, st));
   if (n_dom == 0 || n_src == 0) return PP_OK;
-  const int64_t per = m->max_rows / n_dom;
-  if (per < 1) return mfail(m, PP_EINVAL, "max_rows is smaller than one source's DOM count");
-  for (int64_t s0 = 0; s0 < n_src; s0 += per) {
-    const int64_t ns = (n_src - s0) < per ? (n_src - s0) : per;
-    const int rows = (int)(ns * n_dom);
-    PP_MLP_CUDA(launch_features_dense(m->fg, d_src, s0, ns, m->x0, st));
-    __nv_bfloat16* hs[kLayers] = {m->ha, m->hb, m->ha, m->hb};
-    int rc;
-    if ((rc = forward_layers(m, m->x0, rows, hs, nullptr, st))) return rc;
-    PP_MLP_CUDA(launch_head_dom_sums(hs[3], m->p + kOffW5, m->p + kOffB5, d_nph_src, s0, ns, n_dom,
-                                     m->x0, r_max, d_dom_sums,
-                                     d_lambda ? d_lambda + s0 * n_dom : nullptr, st));
+  // pairs within r_max only: the network is evaluated on a compacted list
+  int64_t per = 8 * (m->max_rows / n_dom);
+  if (per < 1) per = 1;
+  for (int64_t s0 = 0; s0 < n_src;) {
+    int64_t ns = (n_src - s0) < per ? (n_src - s0) : per;
+    unsigned long long cnt = 0;
+    for (;;) {
+      PP_MLP_CUDA(cudaMemsetAsync(m->count, 0, sizeof(unsigned long long), st));
+      PP_MLP_CUDA(launch_near_pairs(m->fg, d_src, s0, ns, r_max, m->max_rows, m->ps, m->pd,
+                                    m->count, st));
+      PP_MLP_CUDA(cudaMemcpyAsync(&cnt, m->count, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+      PP_MLP_CUDA(cudaStreamSynchronize(st));
+      if ((int64_t)cnt <= m->max_rows || ns == 1) break;
+      ns = (ns + 1) / 2;  // too many close pairs for the buffers: fewer sources
+    }
+    if ((int64_t)cnt > m->max_rows)
+      return mfail(m, PP_EINVAL, "one source has more pairs within r_max than max_rows");
+    const int rows = (int)cnt;
+    if (rows > 0) {
+      PP_MLP_CUDA(launch_features(m->fg, d_src, m->ps, m->pd, rows, m->x0, st));
+      __nv_bfloat16* hs[kLayers] = {m->ha, m->hb, m->ha, m->hb};
+      int rc;
+      if ((rc = forward_layers(m, m->x0, rows, hs, nullptr, st))) return rc;
+      PP_MLP_CUDA(launch_head_pairs(hs[3], m->p + kOffW5, m->p + kOffB5, d_nph_src, m->ps, m->pd,
+                                    rows, n_dom, d_dom_sums, d_lambda, st));
+    }
+    s0 += ns;
   }
+  return PP_OK;
+}
+
+int pp_mlp_near_pairs(pp_mlp* m, const pp_source* d_src, int64_t n_src, float r_max,
+                      int64_t max_out, int32_t* d_pair_src, int32_t* d_pair_dom,
+                      uint64_t* h_count) {
+  if (!m || n_src < 0 || (n_src > 0 && !d_src) || !h_count || max_out < 0 || !(r_max > 0.0f) ||
+      (max_out > 0 && (!d_pair_src || !d_pair_dom)))
+    return PP_EINVAL;
+  PP_MLP_CUDA(cudaSetDevice(m->view.device));
+  cudaStream_t st = m->view.stream;
+  PP_MLP_CUDA(cudaMemsetAsync(m->count, 0, sizeof(unsigned long long), st));
+  PP_MLP_CUDA(launch_near_pairs(m->fg, d_src, 0, n_src, r_max, max_out, d_pair_src, d_pair_dom,
+                                m->count, st));
+  unsigned long long c = 0;
+  PP_MLP_CUDA(cudaMemcpyAsync(&c, m->count, sizeof(c), cudaMemcpyDeviceToHost, st));
+  PP_MLP_CUDA(cudaStreamSynchronize(st));
+  *h_count = c;
   return PP_OK;
 }
 

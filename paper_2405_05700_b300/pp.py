@@ -89,6 +89,7 @@ _SIGS = {
     "pp_mlp_loss": [_vp, _vp],
     "pp_mlp_dom_sums": [_vp, _vp, _i64, _vp, C.c_float, _vp, _vp, _vp],
     "pp_mlp_sync": [_vp],
+    "pp_mlp_near_pairs": [_vp, _vp, _i64, C.c_float, _i64, _vp, _vp, _vp],
     "pp_debug_philox": [_vp, _vp, _vp, _vp, _i64],
     "pp_debug_trace": [_vp, _u64, _vp, _i64, _vp, _i64, _i32, _vp, _vp, _vp, _vp],
     "pp_debug_first_hit": [_vp, _vp, _i64, _i32, _vp, _vp],
@@ -470,6 +471,14 @@ def pp_mlp_loss(m):
 def pp_mlp_dom_sums(m, d_src, n_src, d_nph_src, r_max, d_dom_sums, d_lambda=None, stream=None):
     return _mcall("pp_mlp_dom_sums", m, _ptr(d_src), n_src, _ptr(d_nph_src), r_max,
                   _ptr(d_dom_sums), _ptr(d_lambda), _ptr(stream))
+
+
+def pp_mlp_near_pairs(m, d_src, n_src, r_max, max_out, d_pair_src, d_pair_dom):
+    """-> number of pairs within r_max (the first max_out are written)"""
+    c = C.c_uint64()
+    _mcall("pp_mlp_near_pairs", m, _ptr(d_src), n_src, r_max, max_out, _ptr(d_pair_src),
+           _ptr(d_pair_dom), C.addressof(c))
+    return c.value
 
 
 def pp_mlp_sync(m):

@@ -1,8 +1,9 @@
 """Training and evaluation of the learned surrogate through the C ABI.
 
-Host orchestration only: sources and pair lists are prepared with numpy and
-torch (device buffers, index gathers); Monte Carlo runs in the propagation
-kernels, features, forward, backward and Adam in the surrogate's kernels.
+Host orchestration only: sources are drawn with numpy and moved with torch
+(device buffers, index gathers); Monte Carlo runs in the propagation kernels,
+the pair search, features, forward, backward and Adam in the surrogate's
+kernels.
 
 * make_training_set: sources propagated by Monte Carlo, one event per source;
   every (source, DOM) pair within r_max becomes a training pair with its hit
@@ -37,12 +38,6 @@ class TrainingSet:
 def _device_sources(src):
     import torch
     return torch.from_numpy(np.ascontiguousarray(src).view(np.uint8).copy()).cuda()
-
-
-def _midpoints(src):
-    d = np.stack([src["dx"], src["dy"], src["dz"]], 1).astype(np.float64)
-    d /= np.linalg.norm(d, axis=1, keepdims=True)
-    return np.stack([src["x"], src["y"], src["z"]], 1) + 0.5 * src["length"][:, None] * d
 
 
 def mc_hits(prop, src, event_base, chunk=2000):
@@ -94,32 +89,51 @@ def make_training_set(prop, mlp, n_sources, photons, r_max=250.0, seed=0, event_
         return _make_training_set(prop, mlp, n_sources, photons, r_max, seed, event_base)
 
 
-def _make_training_set(prop, mlp, n_sources, photons, r_max, seed, event_base):
+def _near_pairs(mlp, d_src, n_src, r_max):
+    """Device lists (pair_src, pair_dom) of the pairs closer than r_max."""
     import torch
-    geom_xyz = _dom_xyz(prop)
+    n = pp.pp_mlp_near_pairs(mlp.handle, d_src, n_src, r_max, 0, None, None)
+    ps = torch.zeros(max(n, 1), dtype=torch.int32, device="cuda")
+    pd = torch.zeros(max(n, 1), dtype=torch.int32, device="cuda")
+    got = pp.pp_mlp_near_pairs(mlp.handle, d_src, n_src, r_max, n, ps, pd)
+    assert got == n
+    return ps[:n], pd[:n]
+
+
+def _make_training_set(prop, mlp, n_sources, photons, r_max, seed, event_base, chunk=2000):
+    import torch
     src = W.surrogate_sources(np.random.default_rng(seed), n_sources, photons)
-    hits, secs = mc_hits(prop, src, event_base)
-    mid = _midpoints(src)
-    ps_l, pd_l, cn_l = [], [], []
-    for s0 in range(0, n_sources, 4096):
-        m = mid[s0:s0 + 4096]
-        dist = np.linalg.norm(m[:, None, :] - geom_xyz[None, :, :], axis=2)
-        s_idx, d_idx = np.nonzero(dist <= r_max)
-        ps_l.append((s_idx + s0).astype(np.int32))
-        pd_l.append(d_idx.astype(np.int32))
-        cn_l.append(hits[s_idx + s0, d_idx].astype(np.float32))
-    ps, pd, cn = np.concatenate(ps_l), np.concatenate(pd_l), np.concatenate(cn_l)
-    n_pairs = len(ps)
+    d_src = _device_sources(src)
+    stream = _stream(prop)
+    all_ps, all_pd, all_cn = [], [], []
+    secs = 0.0
+    rec = src.dtype.itemsize
+    for c0 in range(0, n_sources, chunk):
+        m = min(chunk, n_sources - c0)
+        part = d_src[c0 * rec:(c0 + m) * rec]
+        # Monte Carlo counts of the chunk, one event per source, kept on the device
+        ids = torch.arange(event_base + c0, event_base + c0 + m, dtype=torch.int64, device="cuda")
+        beg = torch.arange(0, m + 1, dtype=torch.int64, device="cuda")
+        hits = torch.zeros((m, prop.n_dom), dtype=torch.int64, device="cuda")
+        cnt = torch.zeros((m, 4), dtype=torch.int64, device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pp.pp_propagate_batch_async(prop.ctx, m, ids, beg, part, m, hits, cnt, stream.cuda_stream)
+        e1.record(stream)
+        pp.pp_sync(prop.ctx, stream.cuda_stream)
+        secs += e0.elapsed_time(e1) * 1e-3
+        # the chunk's pairs within r_max and their counts
+        ps, pd = _near_pairs(mlp, part, m, r_max)
+        all_cn.append(hits[ps.long(), pd.long()].to(torch.float32))
+        all_ps.append(ps + c0)
+        all_pd.append(pd)
+    ps, pd, cn = torch.cat(all_ps), torch.cat(all_pd), torch.cat(all_cn)
+    n_pairs = int(ps.numel())
     feat = torch.zeros((n_pairs, 16), dtype=torch.int16, device="cuda")
-    pp.pp_mlp_features(mlp.handle, _device_sources(src), torch.from_numpy(ps).cuda(),
-                       torch.from_numpy(pd).cuda(), n_pairs, feat)
+    pp.pp_mlp_features(mlp.handle, d_src, ps, pd, n_pairs, feat)
     pp.pp_mlp_sync(mlp.handle)
     nph = torch.full((n_pairs,), float(photons), dtype=torch.float32, device="cuda")
-    return TrainingSet(src, feat, torch.from_numpy(cn).cuda(), nph, n_pairs, secs)
-
-
-def _dom_xyz(prop):
-    return prop.geom_xyz
+    return TrainingSet(src, feat, cn, nph, n_pairs, secs)
 
 
 def train(mlp, data, epochs, batch=16384, lr=1e-3, lr_final_frac=0.03, seed=0, max_steps=None):
@@ -199,9 +213,9 @@ def _evaluate(prop, mlp, n_sources, photons, seed, event_base, r_fallback, min_e
         # hybrid: sources closer than r_fallback to a DOM go to Monte Carlo,
         # the rest to the surrogate; judged against an independent Monte Carlo
         # of all sources (variance: surrogate part's Poisson + 2 x fallback counts)
-        mid = _midpoints(src)
-        dist = np.linalg.norm(mid[:, None, :] - prop.geom_xyz[None, :, :], axis=2).min(1)
-        fb = dist < r_fallback
+        fb = np.zeros(n_sources, bool)
+        near_src, _ = _near_pairs(mlp, d_src, n_sources, r_fallback)
+        fb[near_src.cpu().numpy()] = True
         lam_h = lam.cpu().numpy().astype(np.float64)
         hyb = lam_h[~fb].sum(0) + hits[fb].sum(0)
         hits2, _ = mc_hits(prop, src, event_base + 5_000_000)

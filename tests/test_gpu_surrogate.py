@@ -158,3 +158,28 @@ def test_training_on_propagator_counts_lowers_loss(pp, prop, mlp):
     later = surrogate.train(mlp, data, epochs=3, batch=4096, lr=2e-3)
     assert later[-1] < 0.8 * first[0], (first, later)
     torch.cuda.synchronize()
+
+
+def test_near_pairs_match_brute_force(pp, prop, mlp):
+    import torch
+    geom = W.geometry_full()
+    rng = np.random.default_rng(8)
+    src, _, _ = _training_like_pairs(rng, 700, geom)
+    src["length"] = rng.uniform(0.0, 20.0, len(src))
+    r_max = 180.0
+    d_src = _dev(src.view(np.uint8))
+    n = pp.pp_mlp_near_pairs(mlp.handle, d_src, len(src), r_max, 0, None, None)
+    ps = torch.zeros(n, dtype=torch.int32, device="cuda")
+    pd = torch.zeros(n, dtype=torch.int32, device="cuda")
+    assert pp.pp_mlp_near_pairs(mlp.handle, d_src, len(src), r_max, n, ps, pd) == n
+    got = set(zip(ps.cpu().numpy().tolist(), pd.cpu().numpy().tolist()))
+    assert len(got) == n                      # no pair twice
+    d = np.stack([src["dx"], src["dy"], src["dz"]], 1).astype(np.float64)
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    mid = np.stack([src["x"], src["y"], src["z"]], 1) + 0.5 * src["length"][:, None] * d
+    r = np.linalg.norm(mid[:, None, :] - geom.xyz[None, :, :], axis=2)
+    inside = set(zip(*np.nonzero(r <= r_max - 1e-3)))
+    border = set(zip(*np.nonzero(np.abs(r - r_max) < 1e-3)))
+    assert inside <= got and got <= inside | border
+    # a short output buffer receives a prefix, the count stays the total
+    assert pp.pp_mlp_near_pairs(mlp.handle, d_src, len(src), r_max, 10, ps, pd) == n
