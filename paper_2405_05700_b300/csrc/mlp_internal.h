@@ -54,9 +54,6 @@ cudaError_t launch_features(const FeatGeom& fg, const pp_source* src, const int3
                             const int32_t* pair_dom, int64_t n, __nv_bfloat16* feat,
                             cudaStream_t st);
 
-// Head z = h . w5 + b5, lambda = nph * softplus(z).
-cudaError_t launch_head(const __nv_bfloat16* h, const float* w5, const float* b5,
-                        const float* nph, int64_t n, float* lambda, cudaStream_t st);
 // Head with loss and gradients: Poisson NLL sum(lambda - n ln lambda) / n_total;
 // dZ4 = dL/dz * w5 * silu'(z4) (BF16), dw5 += sum dL/dz * h, db5 += sum dL/dz,
 // loss (double) += the batch's loss sum / n_total.
@@ -70,10 +67,35 @@ cudaError_t launch_head_backward(const __nv_bfloat16* h, const __nv_bfloat16* z4
 cudaError_t launch_near_pairs(const FeatGeom& fg, const pp_source* src, int64_t s0, int64_t ns,
                               float r_max, int64_t max_out, int32_t* ps, int32_t* pd,
                               unsigned long long* count, cudaStream_t st);
-// Head over listed pairs: dom_sum[pd] += lambda, lambda_out[ps][pd] = lambda.
-cudaError_t launch_head_pairs(const __nv_bfloat16* h, const float* w5, const float* b5,
-                              const float* nph_src, const int32_t* ps, const int32_t* pd, int64_t n,
-                              int n_dom, double* dom_sum, float* lambda_out, cudaStream_t st);
+// Fused inference (mlp_fused.cu): rows are either pairs (features computed
+// in the kernel; lambda summed per DOM and/or stored as [source][DOM]) or
+// precomputed BF16 feature rows (lambda per row).  All feature and pair
+// pointers 16-byte aligned.
+struct FusedArgs {
+  FeatGeom fg;
+  const pp_source* src;          // pairs mode
+  const int32_t* ps;
+  const int32_t* pd;
+  const __nv_bfloat16* feat;     // rows mode: [n][16]
+  int64_t n;
+  const __nv_bfloat16* w1;       // [256][16]
+  const unsigned char* wpack;    // hidden weights in the ring's chunk layout
+  const float* bias[kLayers];
+  const float* w5;
+  const float* b5;
+  const float* nph;              // per source (pairs) or per row
+  double* dom_sum;               // pairs mode, may be null
+  float* lambda_out;             // pairs mode [n_src][n_dom], may be null
+  int n_dom;
+  float* lambda;                 // rows mode
+  int* err;
+};
+
+size_t packed_hidden_bytes();
+cudaError_t launch_pack_hidden(const __nv_bfloat16* w2, const __nv_bfloat16* w3,
+                               const __nv_bfloat16* w4, unsigned char* out, cudaStream_t st);
+// grid: the CTA count cap (one CTA per SM runs at a time)
+cudaError_t launch_mlp_fused(const FusedArgs& a, bool from_pairs, int grid, cudaStream_t st);
 
 cudaError_t launch_transpose(const __nv_bfloat16* in, int rows, int cols, __nv_bfloat16* out,
                              cudaStream_t st);

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "mlp_internal.h"
+#include "mlp_features.cuh"
 #include "tc_gemm.cuh"
 
 namespace mlp {
@@ -194,49 +195,6 @@ cudaError_t launch_gemm(const GemmArgs& g, int epi, cudaStream_t st) {
 // ------------------------------------------------------------- features --
 namespace {
 
-// Surrogate inputs of a (source, DOM) pair.  The ten named inputs: source
-// position (/500 m), direction polar and azimuth angles (/pi), DOM position
-// relative to the source (/100 m), effective scattering and absorption at the
-// source's layer (x10, x50); six derived: the unit direction, the distance
-// (/100 m), the cosine between the direction and the line to the DOM, and
-// ln(1 + distance / 1 m) / 5.  The source point is the segment's midpoint.
-__device__ __forceinline__ void pair_features(const FeatGeom& fg, const pp_source& s, float4 c,
-                                              __nv_bfloat16* out) {
-  float dx = s.dx, dy = s.dy, dz = s.dz;
-  const float nn = sqrtf(dx * dx + dy * dy + dz * dz);
-  if (nn > 0.0f) {
-    dx /= nn;
-    dy /= nn;
-    dz /= nn;
-  }
-  const float h = 0.5f * s.length;
-  const float px = s.x + h * dx, py = s.y + h * dy, pz = s.z + h * dz;
-  const float ex = c.x - px, ey = c.y - py, ez = c.z - pz;
-  const float r = sqrtf(ex * ex + ey * ey + ez * ez);
-  int li = (int)floorf((fg.z_top - pz) / fg.dz);
-  li = li < 0 ? 0 : (li > fg.L - 1 ? fg.L - 1 : li);
-  const float4 L = fg.layer[li];
-  float f[kIn];
-  f[0] = px / 500.0f;
-  f[1] = py / 500.0f;
-  f[2] = pz / 500.0f;
-  f[3] = acosf(fminf(1.0f, fmaxf(-1.0f, dz))) / 3.14159265358979f;
-  f[4] = atan2f(dy, dx) / 3.14159265358979f;
-  f[5] = ex / 100.0f;
-  f[6] = ey / 100.0f;
-  f[7] = ez / 100.0f;
-  f[8] = L.x * fg.be_over_b * 10.0f;
-  f[9] = L.y * 50.0f;
-  f[10] = dx;
-  f[11] = dy;
-  f[12] = dz;
-  f[13] = r / 100.0f;
-  f[14] = (dx * ex + dy * ey + dz * ez) / fmaxf(r, 1e-3f);
-  f[15] = log1pf(r) / 5.0f;
-#pragma unroll
-  for (int i = 0; i < kIn; ++i) out[i] = __float2bfloat16_rn(f[i]);
-}
-
 __global__ void k_features(FeatGeom fg, const pp_source* src, const int32_t* ps, const int32_t* pd,
                            int64_t n, __nv_bfloat16* feat) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -258,14 +216,6 @@ __device__ __forceinline__ float head_z(const __nv_bfloat16* hp, const float* w5
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   return acc + b5;
-}
-
-__global__ void k_head(const __nv_bfloat16* h, const float* w5, const float* b5, const float* nph,
-                       int64_t n, float* lambda) {
-  const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (p >= n) return;
-  const float z = head_z(h + p * kHid, w5, *b5);
-  if ((threadIdx.x & 31) == 0) lambda[p] = nph[p] * softplus(z);
 }
 
 constexpr int kHeadPairs = 64;  // pairs per block of the head backward
@@ -361,21 +311,6 @@ __global__ void k_near_pairs(FeatGeom fg, const pp_source* src, int64_t s0, int6
   }
 }
 
-// Head over listed pairs: dom_sum[d] += lambda, lambda_out[s][d] = lambda.
-__global__ void k_head_pairs(const __nv_bfloat16* h, const float* w5, const float* b5,
-                             const float* nph_src, const int32_t* ps, const int32_t* pd,
-                             int64_t n, int n_dom, double* dom_sum, float* lambda_out) {
-  const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (p >= n) return;
-  const float z = head_z(h + p * kHid, w5, *b5);
-  if ((threadIdx.x & 31) == 0) {
-    const int s = ps[p], d = pd[p];
-    const float lam = nph_src[s] * softplus(z);
-    if (dom_sum) atomicAdd(dom_sum + d, (double)lam);
-    if (lambda_out) lambda_out[(size_t)s * n_dom + d] = lam;
-  }
-}
-
 // ----------------------------------------------------------- utilities --
 __global__ void k_transpose(const __nv_bfloat16* in, int rows, int cols, __nv_bfloat16* out) {
   __shared__ __nv_bfloat16 t[32][33];
@@ -432,13 +367,6 @@ cudaError_t launch_features(const FeatGeom& fg, const pp_source* src, const int3
   return cudaGetLastError();
 }
 
-cudaError_t launch_head(const __nv_bfloat16* h, const float* w5, const float* b5,
-                        const float* nph, int64_t n, float* lambda, cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
-  k_head<<<blocks_for(n * 32, 256), 256, 0, st>>>(h, w5, b5, nph, n, lambda);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_head_backward(const __nv_bfloat16* h, const __nv_bfloat16* z4, const float* w5,
                                  const float* b5, const float* nph, const float* cnt, int64_t n,
                                  float inv_n, __nv_bfloat16* dz4, float* dw5, float* db5,
@@ -455,15 +383,6 @@ cudaError_t launch_near_pairs(const FeatGeom& fg, const pp_source* src, int64_t 
   const int64_t n = ns * fg.n_dom;
   if (n <= 0) return cudaSuccess;
   k_near_pairs<<<blocks_for(n, 256), 256, 0, st>>>(fg, src, s0, ns, r_max, max_out, ps, pd, count);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_head_pairs(const __nv_bfloat16* h, const float* w5, const float* b5,
-                              const float* nph_src, const int32_t* ps, const int32_t* pd, int64_t n,
-                              int n_dom, double* dom_sum, float* lambda_out, cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
-  k_head_pairs<<<blocks_for(n * 32, 256), 256, 0, st>>>(h, w5, b5, nph_src, ps, pd, n, n_dom,
-                                                        dom_sum, lambda_out);
   return cudaGetLastError();
 }
 

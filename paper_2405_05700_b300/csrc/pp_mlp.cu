@@ -60,8 +60,11 @@ struct pp_mlp {
   __nv_bfloat16 *dza = nullptr, *dzb = nullptr, *t1 = nullptr, *t2 = nullptr;
   double* loss = nullptr;
   int* err = nullptr;
-  // inference buffers [max_rows]
-  __nv_bfloat16 *x0 = nullptr, *ha = nullptr, *hb = nullptr;
+  // inference: hidden weights in the fused kernel's chunk layout (repacked
+  // when the weights change), the pair list [max_rows]
+  unsigned char* wpack = nullptr;
+  int64_t weights_version = 0, packed_version = -1;
+  int sms = 0;
   int32_t *ps = nullptr, *pd = nullptr;
   unsigned long long* count = nullptr;
 };
@@ -156,6 +159,28 @@ int forward_backward(pp_mlp* m, const __nv_bfloat16* x0, const float* nph, const
   return PP_OK;
 }
 
+int ensure_packed(pp_mlp* m, cudaStream_t st) {
+  if (m->packed_version == m->weights_version) return PP_OK;
+  PP_MLP_CUDA(launch_pack_hidden(m->wb[1], m->wb[2], m->wb[3], m->wpack, st));
+  m->packed_version = m->weights_version;
+  return PP_OK;
+}
+
+FusedArgs fused_args(pp_mlp* m) {
+  FusedArgs a{};
+  a.fg = m->fg;
+  a.w1 = m->wb[0];
+  a.wpack = m->wpack;
+  for (int l = 0; l < kLayers; ++l) a.bias[l] = m->p + off_b(l);
+  a.w5 = m->p + kOffW5;
+  a.b5 = m->p + kOffB5;
+  a.n_dom = m->fg.n_dom;
+  a.err = m->err;
+  return a;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
 int check_batch(pp_mlp* m, int64_t n) {
   if (n < 16 || n > m->max_batch || n % 16)
     return mfail(m, PP_EINVAL, "training batch must be a multiple of 16 in [16, max_batch]");
@@ -224,9 +249,8 @@ int pp_mlp_create(pp_ctx* ctx, int32_t max_batch, int64_t max_rows, pp_mlp** out
   PP_A(dalloc(&m->t2, B * H));
   PP_A(dalloc(&m->loss, 1));
   PP_A(dalloc(&m->err, 64));
-  PP_A(dalloc(&m->x0, (size_t)max_rows * kIn));
-  PP_A(dalloc(&m->ha, (size_t)max_rows * H));
-  PP_A(dalloc(&m->hb, (size_t)max_rows * H));
+  PP_A(dalloc(&m->wpack, packed_hidden_bytes()));
+  PP_A(cudaDeviceGetAttribute(&m->sms, cudaDevAttrMultiProcessorCount, m->view.device));
   PP_A(dalloc(&m->ps, (size_t)max_rows));
   PP_A(dalloc(&m->pd, (size_t)max_rows));
   PP_A(dalloc(&m->count, 1));
@@ -247,8 +271,8 @@ int pp_mlp_destroy(pp_mlp* m) {
   if (!m) return PP_OK;
   cudaSetDevice(m->view.device);
   cudaDeviceSynchronize();
-  void* bufs[] = {m->p, m->g, m->m, m->v, m->dza, m->dzb, m->t1, m->t2, m->loss, m->err, m->x0,
-                  m->ha, m->hb, m->ps, m->pd, m->count};
+  void* bufs[] = {m->p,    m->g,   m->m,    m->v,  m->dza,   m->dzb, m->t1,
+                  m->t2,   m->loss, m->err, m->wpack, m->ps, m->pd,  m->count};
   for (void* b : bufs) cudaFree(b);
   for (int l = 0; l < kLayers; ++l) {
     cudaFree(m->wb[l]);
@@ -271,6 +295,7 @@ int pp_mlp_set_params(pp_mlp* m, const float* params, int64_t n) {
   PP_MLP_CUDA(cudaMemsetAsync(m->m, 0, sizeof(float) * kNParams, st));
   PP_MLP_CUDA(cudaMemsetAsync(m->v, 0, sizeof(float) * kNParams, st));
   m->step = 0;
+  m->weights_version += 1;
   int rc = refresh_bf16(m, st);
   if (rc) return rc;
   return mlp_sync(m, st);
@@ -297,16 +322,17 @@ int pp_mlp_features(pp_mlp* m, const pp_source* d_src, const int32_t* d_pair_src
 int pp_mlp_forward(pp_mlp* m, const uint16_t* d_feat, const float* d_nph, int64_t n,
                    float* d_lambda, void* stream) {
   if (!m || n < 0 || (n > 0 && (!d_feat || !d_nph || !d_lambda))) return PP_EINVAL;
+  if (n > 0 && !aligned16(d_feat)) return mfail(m, PP_EINVAL, "features must be 16-byte aligned");
   PP_MLP_CUDA(cudaSetDevice(m->view.device));
   cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : m->view.stream;
-  const __nv_bfloat16* f = reinterpret_cast<const __nv_bfloat16*>(d_feat);
-  for (int64_t r0 = 0; r0 < n; r0 += m->max_rows) {
-    const int rows = (int)((n - r0) < m->max_rows ? (n - r0) : m->max_rows);
-    __nv_bfloat16* hs[kLayers] = {m->ha, m->hb, m->ha, m->hb};
-    int rc;
-    if ((rc = forward_layers(m, f + r0 * kIn, rows, hs, nullptr, st))) return rc;
-    PP_MLP_CUDA(launch_head(hs[3], m->p + kOffW5, m->p + kOffB5, d_nph + r0, rows, d_lambda + r0, st));
-  }
+  int rc;
+  if ((rc = ensure_packed(m, st))) return rc;
+  FusedArgs a = fused_args(m);
+  a.feat = reinterpret_cast<const __nv_bfloat16*>(d_feat);
+  a.n = n;
+  a.nph = d_nph;
+  a.lambda = d_lambda;
+  PP_MLP_CUDA(launch_mlp_fused(a, false, m->sms, st));
   return PP_OK;
 }
 
@@ -338,6 +364,7 @@ int pp_mlp_train_step(pp_mlp* m, const uint16_t* d_feat, const float* d_nph, con
                              (int)n, st)))
     return rc;
   m->step += 1;
+  m->weights_version += 1;
   const float b1 = 0.9f, b2 = 0.999f;
   const float bc1 = 1.0f - (float)std::pow(0.9, (double)m->step);
   const float bc2 = 1.0f - (float)std::pow(0.999, (double)m->step);
@@ -381,6 +408,8 @@ int pp_mlp_dom_sums(pp_mlp* m, const pp_source* d_src, int64_t n_src, const floa
   if (d_lambda)
     PP_MLP_CUDA(cudaMemsetAsync(d_lambda, 0, sizeof(float) * (size_t)n_src * n_dom, st));
   if (n_dom == 0 || n_src == 0) return PP_OK;
+  int rc;
+  if ((rc = ensure_packed(m, st))) return rc;
   // pairs within r_max only: the network is evaluated on a compacted list
   int64_t per = 8 * (m->max_rows / n_dom);
   if (per < 1) per = 1;
@@ -398,14 +427,16 @@ int pp_mlp_dom_sums(pp_mlp* m, const pp_source* d_src, int64_t n_src, const floa
     }
     if ((int64_t)cnt > m->max_rows)
       return mfail(m, PP_EINVAL, "one source has more pairs within r_max than max_rows");
-    const int rows = (int)cnt;
-    if (rows > 0) {
-      PP_MLP_CUDA(launch_features(m->fg, d_src, m->ps, m->pd, rows, m->x0, st));
-      __nv_bfloat16* hs[kLayers] = {m->ha, m->hb, m->ha, m->hb};
-      int rc;
-      if ((rc = forward_layers(m, m->x0, rows, hs, nullptr, st))) return rc;
-      PP_MLP_CUDA(launch_head_pairs(hs[3], m->p + kOffW5, m->p + kOffB5, d_nph_src, m->ps, m->pd,
-                                    rows, n_dom, d_dom_sums, d_lambda, st));
+    if (cnt > 0) {
+      FusedArgs a = fused_args(m);
+      a.src = d_src;
+      a.ps = m->ps;
+      a.pd = m->pd;
+      a.n = (int64_t)cnt;
+      a.nph = d_nph_src;
+      a.dom_sum = d_dom_sums;
+      a.lambda_out = d_lambda;
+      PP_MLP_CUDA(launch_mlp_fused(a, true, m->sms, st));
     }
     s0 += ns;
   }

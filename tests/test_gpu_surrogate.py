@@ -63,7 +63,7 @@ def test_tensor_core_gemm(pp, prop, M, N, K):
     assert np.max(np.abs(C - ref)) <= 2e-6 * np.sqrt(K) * np.abs(ref).max() + 1e-6
 
 
-def _training_like_pairs(rng, n_src, geom):
+def _training_like_pairs(rng, n_src, geom, n_pairs=4096):
     src = W.make_sources(n_src)
     src["x"] = rng.uniform(-400, 400, n_src)
     src["y"] = rng.uniform(-400, 400, n_src)
@@ -74,8 +74,8 @@ def _training_like_pairs(rng, n_src, geom):
     src["length"] = 1.0
     src["type"] = W.SRC_CHERENKOV
     src["n_photons"] = 1000
-    ps = rng.integers(0, n_src, 4096).astype(np.int32)
-    pd = rng.integers(0, geom.n_dom, 4096).astype(np.int32)
+    ps = rng.integers(0, n_src, n_pairs).astype(np.int32)
+    pd = rng.integers(0, geom.n_dom, n_pairs).astype(np.int32)
     return src, ps, pd
 
 
@@ -99,18 +99,21 @@ def test_features_match_oracle(pp, prop, mlp):
 def _batch(rng, n):
     from oracle import mlp as M
     geom, ice = W.geometry_full(), W.ice_full()
-    src, ps, pd = _training_like_pairs(rng, 500, geom)
+    src, ps, pd = _training_like_pairs(rng, 500, geom, max(n, 4096))
     x = M.bf16(M.features(src, ps[:n], pd[:n], geom.xyz, ice.b_e, ice.a, ice.depth_top, ice.dz))
     nph = rng.uniform(1e3, 1e5, n)
     counts = rng.poisson(2.0, n).astype(np.float64)
     return x, nph, counts
 
 
-def test_forward_matches_oracle(pp, mlp):
+@pytest.mark.parametrize("n", [2048, 77, 80_077])
+def test_forward_matches_oracle(pp, mlp, n):
+    """The fused inference kernel (rows mode) against the oracle network: one
+    tile, a ragged single tile, and several tiles per CTA with a ragged end."""
     import torch
     from oracle import mlp as M
-    rng = np.random.default_rng(5)
-    x, nph, _ = _batch(rng, 2048)
+    rng = np.random.default_rng(5 + n)
+    x, nph, _ = _batch(rng, n)
     p = pp.mlp_init_params(7).astype(np.float64)
     p[-1] = -6.0
     mlp.set_params(p.astype(np.float32))
@@ -183,3 +186,43 @@ def test_near_pairs_match_brute_force(pp, prop, mlp):
     assert inside <= got and got <= inside | border
     # a short output buffer receives a prefix, the count stays the total
     assert pp.pp_mlp_near_pairs(mlp.handle, d_src, len(src), r_max, 10, ps, pd) == n
+
+
+def test_dom_sums_match_oracle(pp, prop, mlp):
+    """Pairs mode of the fused kernel: lambda of every pair within r_max against
+    the oracle network on the oracle's features (sampled), zero beyond r_max,
+    and the per-DOM sums equal to the sums of the per-pair values."""
+    import torch
+    from oracle import mlp as M
+    geom, ice = W.geometry_full(), W.ice_full()
+    rng = np.random.default_rng(12)
+    src, _, _ = _training_like_pairs(rng, 700, geom)
+    p = pp.mlp_init_params(4).astype(np.float64)
+    p[-1] = -6.0
+    mlp.set_params(p.astype(np.float32))
+    p32 = p.astype(np.float32).astype(np.float64)
+    nph = rng.uniform(1e3, 1e5, len(src)).astype(np.float32)
+    r_max = 250.0
+    sums = torch.zeros(geom.n_dom, dtype=torch.float64, device="cuda")
+    lam = torch.zeros((len(src), geom.n_dom), dtype=torch.float32, device="cuda")
+    pp.pp_mlp_dom_sums(mlp.handle, _dev(src.view(np.uint8)), len(src), _dev(nph), r_max, sums, lam,
+                       None)
+    pp.pp_mlp_sync(mlp.handle)
+    lam = lam.cpu().numpy().astype(np.float64)
+    sums = sums.cpu().numpy()
+    d = np.stack([src["dx"], src["dy"], src["dz"]], 1).astype(np.float64)
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    mid = np.stack([src["x"], src["y"], src["z"]], 1) + 0.5 * src["length"][:, None] * d
+    r = np.linalg.norm(mid[:, None, :] - geom.xyz[None, :, :], axis=2)
+    inside, outside = r <= r_max - 1e-3, r > r_max + 1e-3
+    assert inside.sum() > 100_000            # several tiles per CTA
+    assert np.all(lam[outside] == 0.0) and np.all(lam[inside] > 0.0)
+    assert np.allclose(sums, lam.sum(0), rtol=1e-5, atol=1e-9)
+    s_i, d_i = np.nonzero(inside)
+    pick = rng.choice(len(s_i), 6000, replace=False)
+    ps, pd = s_i[pick], d_i[pick]
+    x = M.bf16(M.features(src, ps, pd, geom.xyz, ice.b_e, ice.a, ice.depth_top, ice.dz))
+    ref, _ = M.forward(p32, x, nph[ps].astype(np.float64), rounding=True)
+    rel = np.abs(lam[ps, pd] - ref) / ref
+    # device features may sit one BF16 step from the oracle's (FP32 vs FP64)
+    assert np.median(rel) < 3e-3 and np.quantile(rel, 0.99) < 3e-2, (np.median(rel), rel.max())
