@@ -330,26 +330,28 @@ const char* pp_server_last_error(const pp_server* server);
  * expected number of photons a DOM receives from a light source, trained on
  * this library's own Monte Carlo hit counts, so that MC can be replaced where
  * the surrogate is accurate enough and kept as the fallback and judge
- * elsewhere.  Network: 16 inputs per (source, DOM) pair -- the ten named
+ * elsewhere.  Network: 32 inputs per (source, DOM) pair -- the ten named
  * (source position, source direction polar/azimuth angles, DOM position
  * relative to the source, effective scattering and absorption at the source's
- * layer) and six derived from them (unit direction, distance, log distance,
- * cosine between direction and the line to the DOM) -- four hidden layers of
- * 256 SiLU units, output lambda = n_photons * softplus(z).  BF16 weights and
- * activations, FP32 accumulation on the tensor cores (hand-written tcgen05
- * GEMMs), FP32 master weights and Adam.  Training minimises the Poisson
- * negative log-likelihood mean(lambda - n ln lambda).
- * Parameters are a flat FP32 array of PP_MLP_N_PARAMS values: W1 [256][16],
+ * layer) and 22 derived from them and the ice table (unit direction,
+ * distance and functions of it, cosine to the DOM, angle and distance from
+ * the Cherenkov cone, the ice at the DOM, the mean ice and optical depths
+ * along the line to the DOM, DOM height, distance from the track axis) --
+ * four hidden layers of 256 SiLU units, output lambda = n_photons *
+ * softplus(z).  BF16 weights and activations, FP32 accumulation on the tensor
+ * cores (hand-written tcgen05 kernels), FP32 master weights and Adam.
+ * Training minimises the Poisson negative log-likelihood mean(lambda - n ln
+ * lambda).  Parameters are a flat FP32 array of PP_MLP_N_PARAMS values: W1 [256][32],
  * b1 [256], W2 [256][256], b2, W3, b3, W4, b4, w5 [256], b5 [1] (W[out][in]).
  * An MLP keeps the context's tables in place (like a server); one host thread
  * at a time per MLP; work is enqueued on the context's stream unless a stream
  * is given. */
-#define PP_MLP_N_PARAMS 201985
-#define PP_MLP_INPUTS 16
+#define PP_MLP_N_PARAMS 206081
+#define PP_MLP_INPUTS 32
 typedef struct pp_mlp pp_mlp;
 
-/* max_batch: largest training batch (multiple of 16); max_rows: pairs per
- * inference chunk (buffers of ~1 KiB per row are allocated). */
+/* max_batch: largest training batch (multiple of 16); max_rows: capacity of
+ * the inference pair list (8 bytes per row). */
 int pp_mlp_create(pp_ctx* ctx, int32_t max_batch, int64_t max_rows, pp_mlp** out);
 int pp_mlp_destroy(pp_mlp* mlp);
 const char* pp_mlp_last_error(const pp_mlp* mlp);
@@ -358,13 +360,14 @@ const char* pp_mlp_last_error(const pp_mlp* mlp);
 int pp_mlp_set_params(pp_mlp* mlp, const float* params, int64_t n);
 int pp_mlp_get_params(pp_mlp* mlp, float* params, int64_t n);
 
-/* Device features of n pairs (source index, DOM index) into d_feat[n][16]
+/* Device features of n pairs (source index, DOM index) into d_feat[n][32]
  * (BF16 bit patterns); sources as in pp_propagate (the point is the segment's
  * midpoint). */
 int pp_mlp_features(pp_mlp* mlp, const pp_source* d_src, const int32_t* d_pair_src,
                     const int32_t* d_pair_dom, int64_t n, uint16_t* d_feat, void* stream);
 
-/* d_lambda[i] = predicted photons on pair i given d_nph[i] photons emitted. */
+/* d_lambda[i] = predicted photons on pair i given d_nph[i] photons emitted
+ * (fused inference kernel; d_feat 16-byte aligned). */
 int pp_mlp_forward(pp_mlp* mlp, const uint16_t* d_feat, const float* d_nph, int64_t n,
                    float* d_lambda, void* stream);
 
@@ -395,6 +398,10 @@ int pp_mlp_dom_sums(pp_mlp* mlp, const pp_source* d_src, int64_t n_src, const fl
 int pp_mlp_near_pairs(pp_mlp* mlp, const pp_source* d_src, int64_t n_src, float r_max,
                       int64_t max_out, int32_t* d_pair_src, int32_t* d_pair_dom,
                       uint64_t* h_count);
+
+/* SiLU of the inference kernel: 0 (default) one tanh.approx per unit, 1
+ * z / (1 + exp(-z)) as in training. */
+int pp_mlp_set_exact_silu(pp_mlp* mlp, int exact);
 
 /* Waits for the MLP's work and reports a device error flag. */
 int pp_mlp_sync(pp_mlp* mlp);

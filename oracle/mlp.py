@@ -21,7 +21,7 @@ import math
 
 import numpy as np
 
-HID, IN = 256, 16
+HID, IN = 256, 32
 N_PARAMS = HID * IN + HID + 3 * (HID * HID + HID) + HID + 1
 
 
@@ -56,34 +56,93 @@ def pack(d):
     return np.concatenate(parts)
 
 
-def features(sources, pair_src, pair_dom, dom_xyz, b_e, a, depth_top, dz, depth_of_z0=1950.0):
-    """The 16 inputs of each (source, DOM) pair, float64, unrounded:
-    source point (segment midpoint) / 500 m, direction polar and azimuth angle
-    / pi, DOM position relative to the point / 100 m, effective scattering x 10
-    and absorption x 50 at the point's layer (depth rows clamped to the
-    table), the unit direction, distance / 100 m, cosine between direction and
-    the line to the DOM, ln(1 + distance / 1 m) / 5."""
+def _layer_index(u, L):
+    return np.clip(np.floor(u).astype(np.int64), 0, L - 1)
+
+
+def path_mean(v, u1, u2):
+    """Mean of the piecewise-constant profile v (one value per layer, the
+    edge layers extended outward) over the layer coordinate interval
+    [u1, u2] (either order): the exact integral divided by the length, the
+    layer's own value when both ends fall in one layer."""
+    v = np.asarray(v, np.float64)
+    L = len(v)
+    cum = np.concatenate([[0.0], np.cumsum(v)])[:L]          # sum of the layers before i
+    i1, i2 = _layer_index(u1, L), _layer_index(u2, L)
+    F1 = cum[i1] + (u1 - i1) * v[i1]
+    F2 = cum[i2] + (u2 - i2) * v[i2]
+    same = i1 == i2
+    du = np.where(same, 1.0, u2 - u1)
+    return np.where(same, v[i1], ((cum[i2] - cum[i1]) + (u2 - i2) * v[i2] - (u1 - i1) * v[i1]) / du)
+
+
+def features(sources, pair_src, pair_dom, dom_xyz, b_e, a, depth_top, dz, depth_of_z0=1950.0,
+             theta_c=math.radians(41.0)):
+    """The IN = 32 inputs of each (source, DOM) pair, float64, unrounded.
+
+    p = segment midpoint, d = unit direction, e = DOM - p, r = |e|,
+    c = d.e / max(r, 1 mm), delta = acos(c) - theta_c (angle from the
+    Cherenkov cone), rho = r sin(delta) (distance from the cone's surface),
+    u = (z_top - z) / dz the continuous layer coordinate of a height z:
+      0-2  p / 500 m          3  polar angle / pi     4  azimuth / pi
+      5-7  e / 100 m          8  b_e(p) x 10          9  a(p) x 50
+      10-12 d                 13 r / 100 m            14 c
+      15 ln(1 + r / 1 m) / 5  16 2 delta              17 rho / 10 m
+      18 exp(-|rho| / 2 m)    19 b_e(DOM) x 10        20 a(DOM) x 50
+      21 mean b_e on the line x 10                    22 mean a on the line x 50
+      23 r x mean a           24 r x mean b_e / 10
+      25-27 exp(-r / 10, 30, 100 m)                   28 DOM z / 500 m
+      29 e_z / max(r, 1 mm)   30 1 / (1 + r / 5 m)    31 r sin(acos c) / 100 m
+    Point values use the layer containing the point (index clamped to the
+    table); line means are path_mean over the heights of p and the DOM."""
     s = sources[np.asarray(pair_src)]
-    c = np.asarray(dom_xyz, np.float64)[np.asarray(pair_dom)]
+    cpos = np.asarray(dom_xyz, np.float64)[np.asarray(pair_dom)]
     d = np.stack([s["dx"], s["dy"], s["dz"]], 1).astype(np.float64)
     d /= np.linalg.norm(d, axis=1, keepdims=True)
     p = np.stack([s["x"], s["y"], s["z"]], 1).astype(np.float64) + \
         0.5 * s["length"].astype(np.float64)[:, None] * d
-    e = c - p
+    e = cpos - p
     r = np.linalg.norm(e, axis=1)
+    rr = np.maximum(r, 1e-3)
+    c = (d * e).sum(1) / rr
+    th = np.arccos(np.clip(c, -1.0, 1.0))
+    delta = th - theta_c
+    rho = r * np.sin(delta)
+    b_e = np.asarray(b_e, np.float64)
+    a = np.asarray(a, np.float64)
+    L = len(b_e)
     z_top = depth_of_z0 - depth_top
-    li = np.clip(np.floor((z_top - p[:, 2]) / dz).astype(np.int64), 0, len(b_e) - 1)
+    us = (z_top - p[:, 2]) / dz
+    ud = (z_top - cpos[:, 2]) / dz
+    i_s, i_d = _layer_index(us, L), _layer_index(ud, L)
+    mb, ma = path_mean(b_e, us, ud), path_mean(a, us, ud)
     f = np.zeros((len(s), IN))
     f[:, 0:3] = p / 500.0
     f[:, 3] = np.arccos(np.clip(d[:, 2], -1, 1)) / math.pi
     f[:, 4] = np.arctan2(d[:, 1], d[:, 0]) / math.pi
     f[:, 5:8] = e / 100.0
-    f[:, 8] = np.asarray(b_e, np.float64)[li] * 10.0
-    f[:, 9] = np.asarray(a, np.float64)[li] * 50.0
+    f[:, 8] = b_e[i_s] * 10.0
+    f[:, 9] = a[i_s] * 50.0
     f[:, 10:13] = d
     f[:, 13] = r / 100.0
-    f[:, 14] = (d * e).sum(1) / np.maximum(r, 1e-3)
+    f[:, 14] = c
     f[:, 15] = np.log1p(r) / 5.0
+    f[:, 16] = 2.0 * delta
+    f[:, 17] = rho / 10.0
+    f[:, 18] = np.exp(-np.abs(rho) / 2.0)
+    f[:, 19] = b_e[i_d] * 10.0
+    f[:, 20] = a[i_d] * 50.0
+    f[:, 21] = mb * 10.0
+    f[:, 22] = ma * 50.0
+    f[:, 23] = r * ma
+    f[:, 24] = r * mb / 10.0
+    f[:, 25] = np.exp(-r / 10.0)
+    f[:, 26] = np.exp(-r / 30.0)
+    f[:, 27] = np.exp(-r / 100.0)
+    f[:, 28] = cpos[:, 2] / 500.0
+    f[:, 29] = e[:, 2] / rr
+    f[:, 30] = 1.0 / (1.0 + r / 5.0)
+    f[:, 31] = r * np.sqrt(np.maximum(0.0, 1.0 - c * c)) / 100.0
     return f
 
 

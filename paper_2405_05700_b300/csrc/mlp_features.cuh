@@ -8,12 +8,24 @@
 
 namespace mlp {
 
-// Surrogate inputs of a (source, DOM) pair.  The ten named inputs: source
-// position (/500 m), direction polar and azimuth angles (/pi), DOM position
-// relative to the source (/100 m), effective scattering and absorption at the
-// source's layer (x10, x50); six derived: the unit direction, the distance
-// (/100 m), the cosine between the direction and the line to the DOM, and
-// ln(1 + distance / 1 m) / 5.  The source point is the segment's midpoint.
+// Continuous layer coordinate of height z and its (clamped) layer index.
+__device__ __forceinline__ int feat_layer(const FeatGeom& fg, float u) {
+  int i = (int)floorf(u);
+  return i < 0 ? 0 : (i > fg.L - 1 ? fg.L - 1 : i);
+}
+
+// Surrogate inputs of a (source, DOM) pair.  p = segment midpoint, d = unit
+// direction, e = DOM - p, r = |e|, c = d.e / max(r, 1 mm), delta = acos(c) -
+// theta_c (angle from the Cherenkov cone), rho = r sin(delta) (distance from
+// the cone's surface), u = (z_top - z) / dz (layer coordinate):
+//   0-2 p / 500 m, 3 polar angle / pi, 4 azimuth / pi, 5-7 e / 100 m,
+//   8 b_e(p) x 10, 9 a(p) x 50, 10-12 d, 13 r / 100 m, 14 c,
+//   15 ln(1 + r / 1 m) / 5, 16 2 delta, 17 rho / 10 m, 18 exp(-|rho| / 2 m),
+//   19 b_e(DOM) x 10, 20 a(DOM) x 50, 21-22 the means of b_e and a along the
+//   line (the integral of the layer profile, edge layers extended) x 10, x 50,
+//   23 r x mean a, 24 r x mean b_e / 10, 25-27 exp(-r / 10, 30, 100 m),
+//   28 DOM z / 500 m, 29 e_z / max(r, 1 mm), 30 1 / (1 + r / 5 m),
+//   31 r sin(acos c) / 100 m.
 __device__ __forceinline__ void pair_features(const FeatGeom& fg, const pp_source& s, float4 c,
                                               __nv_bfloat16* out) {
   float dx = s.dx, dy = s.dy, dz = s.dz;
@@ -27,26 +39,59 @@ __device__ __forceinline__ void pair_features(const FeatGeom& fg, const pp_sourc
   const float px = s.x + h * dx, py = s.y + h * dy, pz = s.z + h * dz;
   const float ex = c.x - px, ey = c.y - py, ez = c.z - pz;
   const float r = sqrtf(ex * ex + ey * ey + ez * ez);
-  int li = (int)floorf((fg.z_top - pz) / fg.dz);
-  li = li < 0 ? 0 : (li > fg.L - 1 ? fg.L - 1 : li);
-  const float4 L = fg.layer[li];
+  const float rr = fmaxf(r, 1e-3f);
+  const float cs = (dx * ex + dy * ey + dz * ez) / rr;
+  const float th = acosf(fminf(1.0f, fmaxf(-1.0f, cs)));
+  const float delta = th - fg.theta_c;
+  const float rho = r * sinf(delta);
+  // point values and line means of the layer profile
+  const float us = (fg.z_top - pz) / fg.dz, ud = (fg.z_top - c.z) / fg.dz;
+  const int is = feat_layer(fg, us), id = feat_layer(fg, ud);
+  const float4 Ls = fg.layer[is], Ld = fg.layer[id];
+  const float bs = Ls.x * fg.be_over_b, as = Ls.y;
+  const float bd = Ld.x * fg.be_over_b, ad = Ld.y;
+  float mb = bs, ma = as;
+  if (is != id) {
+    const float2 cs_ = fg.cum[is], cd = fg.cum[id];
+    const float fs = us - (float)is, fd = ud - (float)id;
+    const float du = ud - us;
+    mb = ((cd.x - cs_.x) + fd * bd - fs * bs) / du;
+    ma = ((cd.y - cs_.y) + fd * ad - fs * as) / du;
+  }
+  const float pi = 3.14159265358979f;
   float f[kIn];
   f[0] = px / 500.0f;
   f[1] = py / 500.0f;
   f[2] = pz / 500.0f;
-  f[3] = acosf(fminf(1.0f, fmaxf(-1.0f, dz))) / 3.14159265358979f;
-  f[4] = atan2f(dy, dx) / 3.14159265358979f;
+  f[3] = acosf(fminf(1.0f, fmaxf(-1.0f, dz))) / pi;
+  f[4] = atan2f(dy, dx) / pi;
   f[5] = ex / 100.0f;
   f[6] = ey / 100.0f;
   f[7] = ez / 100.0f;
-  f[8] = L.x * fg.be_over_b * 10.0f;
-  f[9] = L.y * 50.0f;
+  f[8] = bs * 10.0f;
+  f[9] = as * 50.0f;
   f[10] = dx;
   f[11] = dy;
   f[12] = dz;
   f[13] = r / 100.0f;
-  f[14] = (dx * ex + dy * ey + dz * ez) / fmaxf(r, 1e-3f);
+  f[14] = cs;
   f[15] = log1pf(r) / 5.0f;
+  f[16] = 2.0f * delta;
+  f[17] = rho / 10.0f;
+  f[18] = expf(-fabsf(rho) / 2.0f);
+  f[19] = bd * 10.0f;
+  f[20] = ad * 50.0f;
+  f[21] = mb * 10.0f;
+  f[22] = ma * 50.0f;
+  f[23] = r * ma;
+  f[24] = r * mb / 10.0f;
+  f[25] = expf(-r / 10.0f);
+  f[26] = expf(-r / 30.0f);
+  f[27] = expf(-r / 100.0f);
+  f[28] = c.z / 500.0f;
+  f[29] = ez / rr;
+  f[30] = 1.0f / (1.0f + r / 5.0f);
+  f[31] = r * sqrtf(fmaxf(0.0f, 1.0f - cs * cs)) / 100.0f;
 #pragma unroll
   for (int i = 0; i < kIn; ++i) out[i] = __float2bfloat16_rn(f[i]);
 }

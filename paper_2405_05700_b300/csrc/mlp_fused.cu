@@ -5,9 +5,9 @@
 // Per CTA (one per SM): two row halves of 128 pairs, each an M = 128 tcgen05
 // MMA with its FP32 accumulator (256 columns) in TMEM, so one weight chunk
 // feeds both halves.  The layer's input (features, then BF16 activations)
-// sits in shared memory as the MMA's A operand; the hidden layers' weights
-// stream from global memory (L2-resident, shared by every CTA) through a ring
-// of 16 KB chunks filled by bulk copies.
+// sits in shared memory as the MMA's A operand; the weights (W1 as one chunk,
+// then 8 chunks per hidden layer) stream from global memory (L2-resident,
+// shared by every CTA) through a ring of 16 KB chunks filled by bulk copies.
 //
 //   warps 0-7 : epilogue (warp w: half w / 4, TMEM lanes 32 (w % 4) ..): features,
 //               bias + SiLU to BF16 back into shared memory, head
@@ -34,8 +34,9 @@ constexpr int kChunkK = 32;                // K per weight chunk
 constexpr int kChunksPerLayer = kHid / kChunkK;
 constexpr int kChunkBytes = kHid * kChunkK * 2;
 constexpr int kStages = 5;
-constexpr int kHiddenGemms = kLayers - 1;  // layers 2..4 stream their weights
-constexpr int kChunksPerTile = kHiddenGemms * kChunksPerLayer;
+constexpr int kHiddenGemms = kLayers - 1;  // layers 2..4
+constexpr int kChunksPerTile = 1 + kHiddenGemms * kChunksPerLayer;
+static_assert(kIn == kChunkK, "W1 is one ring chunk");
 constexpr int kEpiThreads = 256;
 constexpr int kThreads = kEpiThreads + 64;
 constexpr uint32_t kWaitTries = 1u << 22;
@@ -43,10 +44,10 @@ constexpr uint32_t kWaitTries = 1u << 22;
 // dynamic shared memory
 constexpr uint32_t kOffH = 0;                                  // 2 x [128][256] BF16 (features alias)
 constexpr uint32_t kHalfBytes = kHalf * kHid * 2;
-constexpr uint32_t kOffW1 = kOffH + 2 * kHalfBytes;             // [256][16] BF16
-constexpr uint32_t kOffRing = kOffW1 + kHid * kIn * 2;
+constexpr uint32_t kOffRing = kOffH + 2 * kHalfBytes;
 constexpr uint32_t kOffPar = kOffRing + kStages * kChunkBytes;  // biases [4][256], w5 [256] (FP32)
 constexpr uint32_t kSmemBytes = kOffPar + (kLayers + 1) * kHid * 4;
+static_assert(kSmemBytes + 1024 <= 232448, "shared memory per CTA");
 
 __device__ __forceinline__ float tanh_approx(float x) {
   float y;
@@ -67,7 +68,9 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-template <bool kFromPairs>
+__device__ __forceinline__ float silu_exact(float z) { return z / (1.0f + __expf(-z)); }
+
+template <bool kFromPairs, bool kExactSilu>
 __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kStages], empty[kStages], acc_full, in_ready, done;
@@ -94,14 +97,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
     for (int i = threadIdx.x; i < kLayers * kHid; i += blockDim.x)
       par[i] = a.bias[i / kHid][i % kHid];
     for (int i = threadIdx.x; i < kHid; i += blockDim.x) par[kLayers * kHid + i] = a.w5[i];
-    // W1 as the first MMA's B operand: K-major, 16 columns
-    for (int i = threadIdx.x; i < kHid * 2; i += blockDim.x) {
-      const int n = i >> 1, k8 = (i & 1) * 8;
-      *reinterpret_cast<uint4*>(smem + kOffW1 + tc::tile_off(n, k8, kIn)) =
-          *reinterpret_cast<const uint4*>(a.w1 + n * kIn + k8);
-    }
   }
-  tc::fence_smem_async();
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -143,7 +139,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
     if (lane == 0) {
       const uint32_t idesc = tc::idesc_bf16(kHalf, kHid);
       const uint32_t sh = tc::smem_u32(smem + kOffH);
-      const uint32_t sw1 = tc::smem_u32(smem + kOffW1);
       const uint32_t ring = tc::smem_u32(smem + kOffRing);
       uint32_t it = 0, in_phase = 0;
       bool ok = true;
@@ -156,31 +151,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
           }
           ++in_phase;
           tc::fence_after_sync();
-          if (layer == 0) {
-            for (int h = 0; h < 2; ++h)
-              tc::mma_bf16(tmem + h * kHid, tc::smem_desc(sh + h * kHalfBytes, 128, kIn * 16),
-                           tc::smem_desc(sw1, 128, kIn * 16), idesc, 0u);
-          } else {
-            for (int c = 0; c < kChunksPerLayer; ++c, ++it) {
-              const uint32_t s = it % kStages;
-              if (!tc::mbar_wait(&full[s], (it / kStages) & 1, kWaitTries)) {
-                ok = false;
-                break;
-              }
-              tc::fence_after_sync();
-              const uint32_t b0 = ring + s * kChunkBytes;
-#pragma unroll
-              for (int h = 0; h < 2; ++h)
-#pragma unroll
-                for (int kk = 0; kk < kChunkK / 16; ++kk) {
-                  const uint32_t k0 = c * kChunkK + kk * 16;
-                  tc::mma_bf16(tmem + h * kHid,
-                               tc::smem_desc(sh + h * kHalfBytes + k0 * 16, 128, kHid * 16),
-                               tc::smem_desc(b0 + kk * 256, 128, kChunkK * 16), idesc,
-                               (c > 0 || kk > 0) ? 1u : 0u);
-                }
-              tc::mma_commit(&empty[s]);
+          // layer 0: features (32 columns) x W1 (one chunk); then 8 chunks per layer
+          const int chunks = layer == 0 ? 1 : kChunksPerLayer;
+          const uint32_t sbo_a = (layer == 0 ? kIn : kHid) * 16;
+          for (int c = 0; c < chunks; ++c, ++it) {
+            const uint32_t s = it % kStages;
+            if (!tc::mbar_wait(&full[s], (it / kStages) & 1, kWaitTries)) {
+              ok = false;
+              break;
             }
+            tc::fence_after_sync();
+            const uint32_t b0 = ring + s * kChunkBytes;
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+              for (int kk = 0; kk < kChunkK / 16; ++kk) {
+                const uint32_t k0 = c * kChunkK + kk * 16;
+                tc::mma_bf16(tmem + h * kHid,
+                             tc::smem_desc(sh + h * kHalfBytes + k0 * 16, 128, sbo_a),
+                             tc::smem_desc(b0 + kk * 256, 128, kChunkK * 16), idesc,
+                             (c > 0 || kk > 0) ? 1u : 0u);
+              }
+            tc::mma_commit(&empty[s]);
           }
           tc::mma_commit(&acc_full);
         }
@@ -207,20 +199,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
       const bool valid = row < a.n;
       // features of this row as the first MMA's A operand (aliasing the activations)
       {
-        uint4 f0 = make_uint4(0, 0, 0, 0), f1 = f0;
+        uint4 fv[kIn / 8];
+#pragma unroll
+        for (int i = 0; i < kIn / 8; ++i) fv[i] = make_uint4(0, 0, 0, 0);
         if (valid) {
           if (kFromPairs) {
             __align__(16) __nv_bfloat16 fb[kIn];
             pair_features(a.fg, a.src[a.ps[row]], a.fg.dom[a.pd[row]], fb);
-            f0 = *reinterpret_cast<const uint4*>(fb);
-            f1 = *reinterpret_cast<const uint4*>(fb + 8);
+#pragma unroll
+            for (int i = 0; i < kIn / 8; ++i) fv[i] = *reinterpret_cast<const uint4*>(fb + 8 * i);
           } else {
-            f0 = *reinterpret_cast<const uint4*>(a.feat + row * kIn);
-            f1 = *reinterpret_cast<const uint4*>(a.feat + row * kIn + 8);
+#pragma unroll
+            for (int i = 0; i < kIn / 8; ++i)
+              fv[i] = *reinterpret_cast<const uint4*>(a.feat + row * kIn + 8 * i);
           }
         }
-        *reinterpret_cast<uint4*>(sH + tc::tile_off(r, 0, kIn)) = f0;
-        *reinterpret_cast<uint4*>(sH + tc::tile_off(r, 8, kIn)) = f1;
+#pragma unroll
+        for (int i = 0; i < kIn / 8; ++i)
+          *reinterpret_cast<uint4*>(sH + tc::tile_off(r, 8 * i, kIn)) = fv[i];
       }
       tc::fence_smem_async();
       tc::fence_before_sync();
@@ -246,8 +242,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
           uint32_t packed[16];
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
-            const float y0 = silu_fast(__uint_as_float(raw[2 * j]) + bias[c0 + 2 * j]);
-            const float y1 = silu_fast(__uint_as_float(raw[2 * j + 1]) + bias[c0 + 2 * j + 1]);
+            const float z0 = __uint_as_float(raw[2 * j]) + bias[c0 + 2 * j];
+            const float z1 = __uint_as_float(raw[2 * j + 1]) + bias[c0 + 2 * j + 1];
+            const float y0 = kExactSilu ? silu_exact(z0) : silu_fast(z0);
+            const float y1 = kExactSilu ? silu_exact(z1) : silu_fast(z1);
             packed[j] = pack_bf16(y0, y1);
           }
           if (layer < kLayers - 1) {
@@ -296,31 +294,49 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
   if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
-// Hidden-layer weights (BF16 [256 out][256 in] each) into the ring's chunk
-// layout: layer l, chunk c (inputs 32c .. 32c + 31) is one K-major 16 KB
-// block, so that one bulk copy stages it.
-__global__ void k_pack_hidden(const __nv_bfloat16* w2, const __nv_bfloat16* w3,
-                              const __nv_bfloat16* w4, unsigned char* out) {
+// The weights in the ring's chunk layout: chunk 0 is W1 ([256][32]), then
+// each hidden layer (BF16 [256 out][256 in]) as 8 chunks of 32 inputs; every
+// chunk is one K-major 16 KB block, staged by one bulk copy.
+__global__ void k_pack_weights(const __nv_bfloat16* w1, const __nv_bfloat16* w2,
+                               const __nv_bfloat16* w3, const __nv_bfloat16* w4,
+                               unsigned char* out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;  // one 8-element group
-  if (i >= kHiddenGemms * kHid * kHid / 8) return;
-  const int l = i / (kHid * kHid / 8);
-  const int rem = i % (kHid * kHid / 8);
+  constexpr int kG1 = kHid * kIn / 8, kGh = kHid * kHid / 8;
+  if (i >= kG1 + kHiddenGemms * kGh) return;
+  if (i < kG1) {
+    const int n = i / (kIn / 8), k = (i % (kIn / 8)) * 8;
+    *reinterpret_cast<uint4*>(out + tc::tile_off(n, k, kChunkK)) =
+        *reinterpret_cast<const uint4*>(w1 + n * kIn + k);
+    return;
+  }
+  const int l = (i - kG1) / kGh;
+  const int rem = (i - kG1) % kGh;
   const int n = rem / (kHid / 8), k = (rem % (kHid / 8)) * 8;
   const __nv_bfloat16* w = l == 0 ? w2 : (l == 1 ? w3 : w4);
   const int c = k / kChunkK;
-  unsigned char* dst = out + (size_t)(l * kChunksPerLayer + c) * kChunkBytes +
+  unsigned char* dst = out + (size_t)(1 + l * kChunksPerLayer + c) * kChunkBytes +
                        tc::tile_off(n, k - c * kChunkK, kChunkK);
   *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(w + n * kHid + k);
 }
 
 }  // namespace
 
-size_t packed_hidden_bytes() { return (size_t)kHiddenGemms * kChunksPerLayer * kChunkBytes; }
+size_t packed_weight_bytes() { return (size_t)kChunksPerTile * kChunkBytes; }
 
-cudaError_t launch_pack_hidden(const __nv_bfloat16* w2, const __nv_bfloat16* w3,
-                               const __nv_bfloat16* w4, unsigned char* out, cudaStream_t st) {
-  const int groups = kHiddenGemms * kHid * kHid / 8;
-  k_pack_hidden<<<(groups + 255) / 256, 256, 0, st>>>(w2, w3, w4, out);
+cudaError_t launch_pack_weights(const __nv_bfloat16* const* w, unsigned char* out,
+                                cudaStream_t st) {
+  const int groups = kHid * kIn / 8 + kHiddenGemms * kHid * kHid / 8;
+  k_pack_weights<<<(groups + 255) / 256, 256, 0, st>>>(w[0], w[1], w[2], w[3], out);
+  return cudaGetLastError();
+}
+
+template <bool P, bool E>
+cudaError_t launch_variant(const FusedArgs& a, int g, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_fused<P, E>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kSmemBytes);
+  if (e != cudaSuccess) return e;
+  k_mlp_fused<P, E><<<g, kThreads, kSmemBytes, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -328,18 +344,9 @@ cudaError_t launch_mlp_fused(const FusedArgs& a, bool from_pairs, int grid, cuda
   if (a.n <= 0) return cudaSuccess;
   const int64_t tiles = (a.n + kRows - 1) / kRows;
   const int g = (int)(tiles < grid ? tiles : grid);
-  cudaError_t e;
-  if (from_pairs) {
-    e = cudaFuncSetAttribute(k_mlp_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kSmemBytes);
-    if (e == cudaSuccess) k_mlp_fused<true><<<g, kThreads, kSmemBytes, st>>>(a);
-  } else {
-    e = cudaFuncSetAttribute(k_mlp_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kSmemBytes);
-    if (e == cudaSuccess) k_mlp_fused<false><<<g, kThreads, kSmemBytes, st>>>(a);
-  }
-  if (e != cudaSuccess) return e;
-  return cudaGetLastError();
+  if (from_pairs)
+    return a.exact_silu ? launch_variant<true, true>(a, g, st) : launch_variant<true, false>(a, g, st);
+  return a.exact_silu ? launch_variant<false, true>(a, g, st) : launch_variant<false, false>(a, g, st);
 }
 
 }  // namespace mlp

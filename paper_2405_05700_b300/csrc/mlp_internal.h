@@ -37,7 +37,7 @@ struct GemmArgs {
 size_t gemm_smem_bytes(int bn);
 cudaError_t launch_gemm(const GemmArgs& g, int epi, cudaStream_t st);
 
-constexpr int kIn = 16;      // input features (10 named + 6 derived), the first MMA's K
+constexpr int kIn = 32;      // input features (10 named + 22 derived), the first MMA's K
 constexpr int kHid = 256;    // hidden width
 constexpr int kLayers = 4;   // hidden layers (Linear + SiLU)
 
@@ -45,9 +45,14 @@ constexpr int kLayers = 4;   // hidden layers (Linear + SiLU)
 struct FeatGeom {
   const float4* dom;         // [n_dom] (x, y, z, 0)
   const float4* layer;       // [L] (b, a, 1/b, 1/a), b geometric
+  const float2* cum;         // [L] sums of (b_e, a) over the layers before each
   int n_dom, L;
   float z_top, dz, be_over_b;  // effective b_e = b * be_over_b
+  float theta_c;             // Cherenkov angle (rad)
 };
+
+// fg.cum from fg.layer (one thread; L is small).
+cudaError_t launch_ice_cum(const FeatGeom& fg, float2* cum, cudaStream_t st);
 
 // Features of pairs (source s, DOM d) as BF16 [n][16].
 cudaError_t launch_features(const FeatGeom& fg, const pp_source* src, const int32_t* pair_src,
@@ -76,10 +81,10 @@ struct FusedArgs {
   const pp_source* src;          // pairs mode
   const int32_t* ps;
   const int32_t* pd;
-  const __nv_bfloat16* feat;     // rows mode: [n][16]
+  const __nv_bfloat16* feat;     // rows mode: [n][kIn]
   int64_t n;
-  const __nv_bfloat16* w1;       // [256][16]
-  const unsigned char* wpack;    // hidden weights in the ring's chunk layout
+  const unsigned char* wpack;    // W1..W4 in the ring's chunk layout
+  int exact_silu;                // 1: z / (1 + exp(-z)); 0: one tanh.approx
   const float* bias[kLayers];
   const float* w5;
   const float* b5;
@@ -91,9 +96,9 @@ struct FusedArgs {
   int* err;
 };
 
-size_t packed_hidden_bytes();
-cudaError_t launch_pack_hidden(const __nv_bfloat16* w2, const __nv_bfloat16* w3,
-                               const __nv_bfloat16* w4, unsigned char* out, cudaStream_t st);
+size_t packed_weight_bytes();
+cudaError_t launch_pack_weights(const __nv_bfloat16* const* w, unsigned char* out,
+                                cudaStream_t st);
 // grid: the CTA count cap (one CTA per SM runs at a time)
 cudaError_t launch_mlp_fused(const FusedArgs& a, bool from_pairs, int grid, cudaStream_t st);
 

@@ -195,6 +195,16 @@ cudaError_t launch_gemm(const GemmArgs& g, int epi, cudaStream_t st) {
 // ------------------------------------------------------------- features --
 namespace {
 
+__global__ void k_ice_cum(FeatGeom fg, float2* cum) {
+  double sb = 0.0, sa = 0.0;
+  for (int i = 0; i < fg.L; ++i) {
+    cum[i] = make_float2((float)sb, (float)sa);
+    const float4 l = fg.layer[i];
+    sb += (double)(l.x * fg.be_over_b);
+    sa += (double)l.y;
+  }
+}
+
 __global__ void k_features(FeatGeom fg, const pp_source* src, const int32_t* ps, const int32_t* pd,
                            int64_t n, __nv_bfloat16* feat) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -358,6 +368,11 @@ __global__ void k_to_bf16(const float* in, int64_t n, __nv_bfloat16* out) {
 unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
+
+cudaError_t launch_ice_cum(const FeatGeom& fg, float2* cum, cudaStream_t st) {
+  k_ice_cum<<<1, 1, 0, st>>>(fg, cum);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_features(const FeatGeom& fg, const pp_source* src, const int32_t* pair_src,
                             const int32_t* pair_dom, int64_t n, __nv_bfloat16* feat,

@@ -21,7 +21,7 @@ using namespace mlp;
 
 namespace {
 
-// Flat parameter layout (FP32): W1 [256][16], b1, W2 [256][256], b2, W3, b3,
+// Flat parameter layout (FP32): W1 [256][32], b1, W2 [256][256], b2, W3, b3,
 // W4, b4, w5 [256], b5.
 constexpr int64_t kOffW1 = 0;
 constexpr int64_t kOffB1 = kOffW1 + kHid * kIn;
@@ -64,6 +64,8 @@ struct pp_mlp {
   // when the weights change), the pair list [max_rows]
   unsigned char* wpack = nullptr;
   int64_t weights_version = 0, packed_version = -1;
+  int exact_silu = 0;
+  float2* ice_cum = nullptr;
   int sms = 0;
   int32_t *ps = nullptr, *pd = nullptr;
   unsigned long long* count = nullptr;
@@ -161,7 +163,7 @@ int forward_backward(pp_mlp* m, const __nv_bfloat16* x0, const float* nph, const
 
 int ensure_packed(pp_mlp* m, cudaStream_t st) {
   if (m->packed_version == m->weights_version) return PP_OK;
-  PP_MLP_CUDA(launch_pack_hidden(m->wb[1], m->wb[2], m->wb[3], m->wpack, st));
+  PP_MLP_CUDA(launch_pack_weights(m->wb, m->wpack, st));
   m->packed_version = m->weights_version;
   return PP_OK;
 }
@@ -169,8 +171,8 @@ int ensure_packed(pp_mlp* m, cudaStream_t st) {
 FusedArgs fused_args(pp_mlp* m) {
   FusedArgs a{};
   a.fg = m->fg;
-  a.w1 = m->wb[0];
   a.wpack = m->wpack;
+  a.exact_silu = m->exact_silu;
   for (int l = 0; l < kLayers; ++l) a.bias[l] = m->p + off_b(l);
   a.w5 = m->p + kOffW5;
   a.b5 = m->p + kOffB5;
@@ -226,6 +228,7 @@ int pp_mlp_create(pp_ctx* ctx, int32_t max_batch, int64_t max_rows, pp_mlp** out
   m->fg.z_top = m->view.ice.z_top;
   m->fg.dz = m->view.ice.dz;
   m->fg.be_over_b = m->view.scatter_effective ? 1.0f - g : 1.0f;
+  m->fg.theta_c = std::acos(m->view.run.cos_cherenkov);
   cudaError_t e = cudaSetDevice(m->view.device);
   const size_t B = (size_t)max_batch, H = (size_t)kHid;
 #define PP_A(x) \
@@ -249,7 +252,11 @@ int pp_mlp_create(pp_ctx* ctx, int32_t max_batch, int64_t max_rows, pp_mlp** out
   PP_A(dalloc(&m->t2, B * H));
   PP_A(dalloc(&m->loss, 1));
   PP_A(dalloc(&m->err, 64));
-  PP_A(dalloc(&m->wpack, packed_hidden_bytes()));
+  PP_A(dalloc(&m->wpack, packed_weight_bytes()));
+  PP_A(dalloc(&m->ice_cum, (size_t)m->fg.L));
+  m->fg.cum = m->ice_cum;
+  PP_A(launch_ice_cum(m->fg, m->ice_cum, 0));
+  PP_A(cudaDeviceSynchronize());
   PP_A(cudaDeviceGetAttribute(&m->sms, cudaDevAttrMultiProcessorCount, m->view.device));
   PP_A(dalloc(&m->ps, (size_t)max_rows));
   PP_A(dalloc(&m->pd, (size_t)max_rows));
@@ -272,7 +279,7 @@ int pp_mlp_destroy(pp_mlp* m) {
   cudaSetDevice(m->view.device);
   cudaDeviceSynchronize();
   void* bufs[] = {m->p,    m->g,   m->m,    m->v,  m->dza,   m->dzb, m->t1,
-                  m->t2,   m->loss, m->err, m->wpack, m->ps, m->pd,  m->count};
+                  m->t2,   m->loss, m->err, m->wpack, m->ps, m->pd,  m->count, m->ice_cum};
   for (void* b : bufs) cudaFree(b);
   for (int l = 0; l < kLayers; ++l) {
     cudaFree(m->wb[l]);
@@ -458,6 +465,12 @@ int pp_mlp_near_pairs(pp_mlp* m, const pp_source* d_src, int64_t n_src, float r_
   PP_MLP_CUDA(cudaMemcpyAsync(&c, m->count, sizeof(c), cudaMemcpyDeviceToHost, st));
   PP_MLP_CUDA(cudaStreamSynchronize(st));
   *h_count = c;
+  return PP_OK;
+}
+
+int pp_mlp_set_exact_silu(pp_mlp* m, int exact) {
+  if (!m) return PP_EINVAL;
+  m->exact_silu = exact ? 1 : 0;
   return PP_OK;
 }
 

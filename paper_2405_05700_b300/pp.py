@@ -89,6 +89,7 @@ _SIGS = {
     "pp_mlp_loss": [_vp, _vp],
     "pp_mlp_dom_sums": [_vp, _vp, _i64, _vp, C.c_float, _vp, _vp, _vp],
     "pp_mlp_sync": [_vp],
+    "pp_mlp_set_exact_silu": [_vp, _i32],
     "pp_mlp_near_pairs": [_vp, _vp, _i64, C.c_float, _i64, _vp, _vp, _vp],
     "pp_debug_philox": [_vp, _vp, _vp, _vp, _i64],
     "pp_debug_trace": [_vp, _u64, _vp, _i64, _vp, _i64, _i32, _vp, _vp, _vp, _vp],
@@ -408,8 +409,8 @@ class Server:
 
 # ---- learned surrogate ---------------------------------------------------------
 
-PP_MLP_N_PARAMS = 201985
-PP_MLP_INPUTS = 16
+PP_MLP_N_PARAMS = 206081
+PP_MLP_INPUTS = 32
 
 
 def _mcall(name, m, *args):
@@ -485,11 +486,15 @@ def pp_mlp_sync(m):
     return _mcall("pp_mlp_sync", m)
 
 
+def pp_mlp_set_exact_silu(m, exact):
+    return _mcall("pp_mlp_set_exact_silu", m, 1 if exact else 0)
+
+
 def mlp_init_params(seed: int = 0) -> np.ndarray:
     """Initial parameters: weights N(0, 1/fan_in) (He-like for SiLU), zero
     biases, b5 chosen so that softplus(b5) is a small hit probability."""
     rng = np.random.default_rng(seed)
-    parts = [rng.normal(0.0, np.sqrt(1.0 / 16), (256, 16)), np.zeros(256)]
+    parts = [rng.normal(0.0, np.sqrt(1.0 / PP_MLP_INPUTS), (256, PP_MLP_INPUTS)), np.zeros(256)]
     for _ in range(3):
         parts += [rng.normal(0.0, np.sqrt(2.0 / 256), (256, 256)), np.zeros(256)]
     parts += [rng.normal(0.0, np.sqrt(1.0 / 256), 256), np.array([-9.0])]

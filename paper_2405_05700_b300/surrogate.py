@@ -28,7 +28,7 @@ from . import pp, workloads as W
 @dataclasses.dataclass
 class TrainingSet:
     sources: np.ndarray
-    feat: object         # torch int16 [P][16] (BF16 bits), on the device
+    feat: object         # torch int16 [P][32] (BF16 bits), on the device
     counts: object       # torch float32 [P]
     nph: object          # torch float32 [P]
     n_pairs: int
@@ -40,16 +40,18 @@ def _device_sources(src):
     return torch.from_numpy(np.ascontiguousarray(src).view(np.uint8).copy()).cuda()
 
 
-def mc_hits(prop, src, event_base, chunk=2000):
-    """Monte Carlo hits [n_src][n_dom] with one event per source; returns
-    (hits, seconds of device time)."""
+def mc_hits(prop, src, event_base, chunk=2000, event_ids=None):
+    """Monte Carlo hits [n_src][n_dom] with one event per source (event ids
+    event_base + i, or the given ones); returns (hits, seconds of device time)."""
     import torch
     stream = _stream(prop)
+    ids = np.arange(event_base, event_base + len(src), dtype=np.int64) if event_ids is None \
+        else np.asarray(event_ids, np.int64)
     with torch.cuda.stream(stream):
-        return _mc_hits(prop, src, event_base, chunk, stream)
+        return _mc_hits(prop, src, ids, chunk, stream)
 
 
-def _mc_hits(prop, src, event_base, chunk, stream):
+def _mc_hits(prop, src, event_ids, chunk, stream):
     import torch
     n, n_dom = len(src), prop.n_dom
     out = np.zeros((n, n_dom), np.int64)
@@ -58,7 +60,7 @@ def _mc_hits(prop, src, event_base, chunk, stream):
         part = np.ascontiguousarray(src[c0:c0 + chunk])
         m = len(part)
         d_src = _device_sources(part)
-        ids = torch.arange(event_base + c0, event_base + c0 + m, dtype=torch.int64, device="cuda")
+        ids = torch.from_numpy(event_ids[c0:c0 + m].copy()).cuda()
         beg = torch.arange(0, m + 1, dtype=torch.int64, device="cuda")
         hits = torch.zeros((m, n_dom), dtype=torch.int64, device="cuda")
         cnt = torch.zeros((m, 4), dtype=torch.int64, device="cuda")
@@ -83,10 +85,15 @@ def _stream(prop):
     return torch.cuda.ExternalStream(prop.stream)
 
 
-def make_training_set(prop, mlp, n_sources, photons, r_max=250.0, seed=0, event_base=0):
+def make_training_set(prop, mlp, n_sources, photons, r_max=250.0, seed=0, event_base=0,
+                      near_fraction=0.0, r_near=25.0):
+    """Training pairs from n_sources Monte Carlo sources: a fraction
+    near_fraction of them placed within r_near of a DOM, the rest uniform in
+    the instrumented volume."""
     import torch
     with torch.cuda.stream(_stream(prop)):
-        return _make_training_set(prop, mlp, n_sources, photons, r_max, seed, event_base)
+        return _make_training_set(prop, mlp, n_sources, photons, r_max, seed, event_base,
+                                  near_fraction, r_near)
 
 
 def _near_pairs(mlp, d_src, n_src, r_max):
@@ -100,9 +107,15 @@ def _near_pairs(mlp, d_src, n_src, r_max):
     return ps[:n], pd[:n]
 
 
-def _make_training_set(prop, mlp, n_sources, photons, r_max, seed, event_base, chunk=2000):
+def _make_training_set(prop, mlp, n_sources, photons, r_max, seed, event_base, near_fraction,
+                       r_near, chunk=2000):
     import torch
-    src = W.surrogate_sources(np.random.default_rng(seed), n_sources, photons)
+    rng = np.random.default_rng(seed)
+    n_near = int(round(near_fraction * n_sources))
+    parts = [W.surrogate_sources(rng, n_sources - n_near, photons)]
+    if n_near:
+        parts.append(W.surrogate_sources_near(rng, n_near, photons, prop.geom_xyz, r_near))
+    src = np.concatenate(parts)
     d_src = _device_sources(src)
     stream = _stream(prop)
     all_ps, all_pd, all_cn = [], [], []
@@ -129,7 +142,7 @@ def _make_training_set(prop, mlp, n_sources, photons, r_max, seed, event_base, c
         all_pd.append(pd)
     ps, pd, cn = torch.cat(all_ps), torch.cat(all_pd), torch.cat(all_cn)
     n_pairs = int(ps.numel())
-    feat = torch.zeros((n_pairs, 16), dtype=torch.int16, device="cuda")
+    feat = torch.zeros((n_pairs, pp.PP_MLP_INPUTS), dtype=torch.int16, device="cuda")
     pp.pp_mlp_features(mlp.handle, d_src, ps, pd, n_pairs, feat)
     pp.pp_mlp_sync(mlp.handle)
     nph = torch.full((n_pairs,), float(photons), dtype=torch.float32, device="cuda")
@@ -169,60 +182,76 @@ def _train(mlp, data, epochs, batch, lr, lr_final_frac, seed, max_steps):
     return losses
 
 
-def evaluate(prop, mlp, n_sources, photons, seed=123, event_base=10_000_000, r_fallback=None,
-             min_expected=5.0, r_max=250.0):
-    """Surrogate vs Monte Carlo on fresh sources: per-DOM sums over sources."""
+def evaluate(prop, mlp, n_sources, photons, seed=123, event_base=10_000_000,
+             r_fallbacks=(0.0, 3.0, 5.0, 10.0), min_expected=5.0, r_max=250.0):
+    """Surrogate vs Monte Carlo on fresh sources, per-DOM sums over sources.
+
+    Surrogate alone: its per-DOM expectation against one MC run (Pearson
+    chi2 / ndf over DOMs expecting >= min_expected hits).  Hybrid, for each
+    fallback radius: sources closer than the radius to a DOM go to MC (the
+    same events, hence the same counts), the rest to the surrogate, each part
+    timed on its own; judged against an independent MC run of all sources
+    (variance: the surrogate part's expectation + twice the MC part's
+    counts).  Speedup = full MC time / surrogate (+ fallback MC) time."""
     import torch
     with torch.cuda.stream(_stream(prop)):
-        return _evaluate(prop, mlp, n_sources, photons, seed, event_base, r_fallback,
+        return _evaluate(prop, mlp, n_sources, photons, seed, event_base, r_fallbacks,
                          min_expected, r_max)
 
 
-def _evaluate(prop, mlp, n_sources, photons, seed, event_base, r_fallback, min_expected, r_max):
+def _sur_time(prop, mlp, src, photons, r_max, lam_out=None):
+    """(per-DOM sums, device seconds) of the surrogate over the sources."""
     import torch
-    src = W.surrogate_sources(np.random.default_rng(seed), n_sources, photons)
-    hits, mc_secs = mc_hits(prop, src, event_base)
-    mc_dom = hits.sum(0).astype(np.float64)
-    d_src = _device_sources(src)
-    nph = torch.full((n_sources,), float(photons), dtype=torch.float32, device="cuda")
-    sums = torch.zeros(prop.n_dom, dtype=torch.float64, device="cuda")
-    lam = torch.zeros((n_sources, prop.n_dom), dtype=torch.float32, device="cuda")
     st = _stream(prop)
-    torch.cuda.synchronize()
-    pp.pp_mlp_dom_sums(mlp.handle, d_src, n_sources, nph, r_max, sums, lam, st.cuda_stream)  # warm
+    n = len(src)
+    sums = torch.zeros(prop.n_dom, dtype=torch.float64, device="cuda")
+    if n == 0:
+        return sums.cpu().numpy(), 0.0
+    d_src = _device_sources(src)
+    nph = torch.full((n,), float(photons), dtype=torch.float32, device="cuda")
+    pp.pp_mlp_dom_sums(mlp.handle, d_src, n, nph, r_max, sums, lam_out, st.cuda_stream)  # warm
     st.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
-    pp.pp_mlp_dom_sums(mlp.handle, d_src, n_sources, nph, r_max, sums, None, st.cuda_stream)
+    pp.pp_mlp_dom_sums(mlp.handle, d_src, n, nph, r_max, sums, None, st.cuda_stream)
     e1.record(st)
     st.synchronize()
     pp.pp_mlp_sync(mlp.handle)
-    sur_secs = e0.elapsed_time(e1) * 1e-3
-    sur_dom = sums.cpu().numpy()
+    return sums.cpu().numpy(), e0.elapsed_time(e1) * 1e-3
+
+
+def _evaluate(prop, mlp, n_sources, photons, seed, event_base, r_fallbacks, min_expected, r_max):
+    import torch
+    src = W.surrogate_sources(np.random.default_rng(seed), n_sources, photons)
+    ids = np.arange(event_base, event_base + n_sources, dtype=np.int64)
+    hits, mc_secs = mc_hits(prop, src, 0, event_ids=ids)
+    hits2, _ = mc_hits(prop, src, 0, event_ids=ids + 5_000_000)   # the judge
+    ref = hits2.sum(0).astype(np.float64)
+    lam = torch.zeros((n_sources, prop.n_dom), dtype=torch.float32, device="cuda")
+    sur_dom, sur_secs = _sur_time(prop, mlp, src, photons, r_max, lam)
+    lam = lam.cpu().numpy().astype(np.float64)
 
     def chi2(resid2, var):
         use = var >= min_expected
         return float((resid2[use] / var[use]).sum()) / max(1, int(use.sum())), int(use.sum())
 
-    res = {"sources": n_sources, "photons_per_source": photons,
-           "mc_seconds": mc_secs, "surrogate_seconds": sur_secs,
-           "speedup": mc_secs / sur_secs if sur_secs > 0 else None}
-    # surrogate expectation against Monte Carlo counts (Poisson variance = expectation)
-    res["chi2_ndf"], res["ndf"] = chi2((mc_dom - sur_dom) ** 2, sur_dom)
-    if r_fallback is not None:
-        # hybrid: sources closer than r_fallback to a DOM go to Monte Carlo,
-        # the rest to the surrogate; judged against an independent Monte Carlo
-        # of all sources (variance: surrogate part's Poisson + 2 x fallback counts)
+    res = {"sources": n_sources, "photons_per_source": photons, "mc_seconds": mc_secs,
+           "surrogate_seconds": sur_secs, "speedup": mc_secs / sur_secs if sur_secs > 0 else None}
+    res["chi2_ndf"], res["ndf"] = chi2((hits.sum(0) - sur_dom) ** 2, sur_dom)
+    d_src = _device_sources(src)
+    res["hybrid"] = []
+    for r_fb in r_fallbacks:
         fb = np.zeros(n_sources, bool)
-        near_src, _ = _near_pairs(mlp, d_src, n_sources, r_fallback)
-        fb[near_src.cpu().numpy()] = True
-        lam_h = lam.cpu().numpy().astype(np.float64)
-        hyb = lam_h[~fb].sum(0) + hits[fb].sum(0)
-        hits2, _ = mc_hits(prop, src, event_base + 5_000_000)
-        ref = hits2.sum(0).astype(np.float64)
-        var = lam_h[~fb].sum(0) + 2.0 * hits[fb].sum(0)
-        res["fallback_fraction"] = float(fb.mean())
-        res["hybrid_chi2_ndf"], res["hybrid_ndf"] = chi2((hyb - ref) ** 2, var)
-        res["hybrid_seconds"] = sur_secs * float((~fb).mean()) + mc_secs * float(fb.mean())
-        res["hybrid_speedup"] = mc_secs / res["hybrid_seconds"]
+        if r_fb > 0:
+            near_src, _ = _near_pairs(mlp, d_src, n_sources, r_fb)
+            fb[near_src.cpu().numpy()] = True
+        pred = lam[~fb].sum(0) + hits[fb].sum(0)
+        var = lam[~fb].sum(0) + 2.0 * hits[fb].sum(0)
+        c2, ndf = chi2((pred - ref) ** 2, var)
+        _, t_sur = _sur_time(prop, mlp, src[~fb], photons, r_max)
+        t_mc = mc_hits(prop, src[fb], 0, event_ids=ids[fb])[1] if fb.any() else 0.0
+        t = t_sur + t_mc
+        res["hybrid"].append({"r_fallback": r_fb, "fallback_fraction": float(fb.mean()),
+                              "chi2_ndf": c2, "ndf": ndf, "seconds": t,
+                              "speedup": mc_secs / t if t > 0 else None})
     return res

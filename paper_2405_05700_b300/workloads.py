@@ -432,3 +432,25 @@ def surrogate_sources(rng, n: int, photons: int, half_width: float = 450.0,
     src["type"] = SRC_CHERENKOV
     src["n_photons"] = photons
     return src
+
+
+def surrogate_sources_near(rng, n: int, photons: int, dom_xyz: np.ndarray,
+                           r_near: float = 25.0, r_min: float = 0.5) -> np.ndarray:
+    """Surrogate training sources close to DOMs, where direct light is bright
+    and uniform placement rarely lands: each at a random DOM plus an offset
+    uniform in the shell r_min <= |offset| <= r_near (segment midpoint),
+    isotropic directions, 1 m Cherenkov segments."""
+    src = make_sources(n)
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    o = rng.normal(size=(n, 3))
+    o /= np.linalg.norm(o, axis=1, keepdims=True)
+    rad = np.cbrt(rng.uniform(r_min ** 3, r_near ** 3, n))
+    centre = np.asarray(dom_xyz, np.float64)[rng.integers(0, len(dom_xyz), n)]
+    start = centre + o * rad[:, None] - 0.5 * d     # the midpoint sits at the offset
+    src["x"], src["y"], src["z"] = start[:, 0], start[:, 1], start[:, 2]
+    src["dx"], src["dy"], src["dz"] = d[:, 0], d[:, 1], d[:, 2]
+    src["length"] = 1.0
+    src["type"] = SRC_CHERENKOV
+    src["n_photons"] = photons
+    return src

@@ -85,7 +85,7 @@ def test_features_match_oracle(pp, prop, mlp):
     geom, ice = W.geometry_full(), W.ice_full()
     rng = np.random.default_rng(2)
     src, ps, pd = _training_like_pairs(rng, 300, geom)
-    feat = torch.zeros((len(ps), 16), dtype=torch.int16, device="cuda")
+    feat = torch.zeros((len(ps), pp.PP_MLP_INPUTS), dtype=torch.int16, device="cuda")
     pp.pp_mlp_features(mlp.handle, _dev(src.view(np.uint8)), _dev(ps), _dev(pd), len(ps), feat)
     pp.pp_mlp_sync(mlp.handle)
     got = pp.bf16_value(feat.cpu().numpy().view(np.uint16)).astype(np.float64)
@@ -106,14 +106,21 @@ def _batch(rng, n):
     return x, nph, counts
 
 
-@pytest.mark.parametrize("n", [2048, 77, 80_077])
-def test_forward_matches_oracle(pp, mlp, n):
+@pytest.mark.parametrize("n,exact", [(2048, 0), (77, 0), (80_077, 0), (80_077, 1)])
+def test_forward_matches_oracle(pp, mlp, n, exact):
     """The fused inference kernel (rows mode) against the oracle network: one
-    tile, a ragged single tile, and several tiles per CTA with a ragged end."""
+    tile, a ragged single tile, and several tiles per CTA with a ragged end,
+    with the one-SFU SiLU (default) and the exact one.
+
+    Both sides round to BF16 at the same points, so almost every row agrees
+    to FP32 accumulation error; where the device's SiLU lands on the other
+    side of a BF16 rounding boundary, that one-ulp step (2^-8 relative)
+    propagates through the later layers: rare, up to a few per cent."""
     import torch
     from oracle import mlp as M
     rng = np.random.default_rng(5 + n)
     x, nph, _ = _batch(rng, n)
+    pp.pp_mlp_set_exact_silu(mlp.handle, exact)
     p = pp.mlp_init_params(7).astype(np.float64)
     p[-1] = -6.0
     mlp.set_params(p.astype(np.float32))
@@ -123,8 +130,10 @@ def test_forward_matches_oracle(pp, mlp, n):
     lam = torch.zeros(len(x), dtype=torch.float32, device="cuda")
     pp.pp_mlp_forward(mlp.handle, feat, _dev(nph.astype(np.float32)), len(x), lam)
     pp.pp_mlp_sync(mlp.handle)
+    pp.pp_mlp_set_exact_silu(mlp.handle, 0)
     rel = np.abs(lam.cpu().numpy() - lam_ref) / lam_ref
-    assert np.median(rel) < 2e-3 and rel.max() < 3e-2, (np.median(rel), rel.max())
+    assert np.median(rel) < 1e-4, np.median(rel)
+    assert np.quantile(rel, 0.99) < 2e-2 and rel.max() < 0.1, (np.quantile(rel, 0.99), rel.max())
 
 
 def test_gradients_match_oracle(pp, mlp):

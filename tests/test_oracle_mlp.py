@@ -57,18 +57,51 @@ def test_features_hand_computed():
     src["length"] = [2.0, 0.0]
     src["type"] = W.SRC_CHERENKOV
     doms = np.array([[10.0, 20.0, 61.0], [0.0, 5.0, 0.0]])
-    b_e = np.array([0.01, 0.02, 0.03], np.float32)
-    a = np.array([0.1, 0.2, 0.3], np.float32)
+    b_e = np.array([0.01, 0.02, 0.03], np.float32).astype(np.float64)
+    a = np.array([0.1, 0.2, 0.3], np.float32).astype(np.float64)
     f = M.features(src, [0, 1], [0, 1], doms, b_e, a, depth_top=1900.0, dz=10.0)
+    tc = math.radians(41.0)
     # pair 0: midpoint (10, 20, 31), DOM 30 m straight above along the direction
     assert np.allclose(f[0, 0:3], [10 / 500, 20 / 500, 31 / 500])
     assert f[0, 3] == 0.0                                # polar angle 0
     assert np.allclose(f[0, 5:8], [0, 0, 0.3]) and np.isclose(f[0, 13], 0.3)
     assert np.isclose(f[0, 14], 1.0) and np.isclose(f[0, 15], math.log(31) / 5)
     # depth 1950 - 31 = 1919 -> layer 1 of the table starting at 1900 m
-    assert np.isclose(f[0, 8], 0.2) and np.isclose(f[0, 9], 10.0)
+    assert np.isclose(f[0, 8], b_e[1] * 10) and np.isclose(f[0, 9], a[1] * 50)
+    # on the axis: 41 degrees inside the cone, 30 sin(41 deg) m from its surface
+    assert np.isclose(f[0, 16], -2 * tc) and np.isclose(f[0, 17], -3 * math.sin(tc))
+    assert np.isclose(f[0, 18], math.exp(-15 * math.sin(tc)))
+    # the DOM at height 61 m (depth 1889 m) lies above the table: layer 0
+    assert np.isclose(f[0, 19], b_e[0] * 10) and np.isclose(f[0, 20], a[0] * 50)
+    # the line spans layer coordinates -1.1 .. 1.9: 2.1 layers of row 0, 0.9 of row 1
+    ma, mb = (2.1 * a[0] + 0.9 * a[1]) / 3.0, (2.1 * b_e[0] + 0.9 * b_e[1]) / 3.0
+    assert np.isclose(f[0, 21], mb * 10) and np.isclose(f[0, 22], ma * 50)
+    assert np.isclose(f[0, 23], 30 * ma) and np.isclose(f[0, 24], 3 * mb)
+    assert np.allclose(f[0, 25:28], np.exp(-30 / np.array([10, 30, 100])))
+    assert np.isclose(f[0, 28], 61 / 500) and np.isclose(f[0, 29], 1.0)
+    assert np.isclose(f[0, 30], 1 / 7) and abs(f[0, 31]) < 1e-12
     # pair 1: direction +x, DOM 5 m along +y: perpendicular
     assert np.isclose(f[1, 3], 0.5) and np.isclose(f[1, 4], 0.0)
     assert np.isclose(f[1, 14], 0.0) and np.allclose(f[1, 10:13], [1, 0, 0])
-    # depth 1950 -> layer 5, clamped to the last row
-    assert np.isclose(f[1, 8], 0.3)
+    assert np.isclose(f[1, 16], 2 * (math.pi / 2 - tc))
+    assert np.isclose(f[1, 17], 0.5 * math.sin(math.pi / 2 - tc))
+    # depth 1950 -> layer 5, clamped to the last row, for the point, the DOM and the line
+    assert np.isclose(f[1, 8], b_e[2] * 10) and np.isclose(f[1, 19], b_e[2] * 10)
+    assert np.isclose(f[1, 21], b_e[2] * 10) and np.isclose(f[1, 22], a[2] * 50)
+    assert np.isclose(f[1, 31], 0.05) and np.isclose(f[1, 30], 0.5)
+
+
+def test_path_mean_against_numerical_integration():
+    rng = np.random.default_rng(9)
+    v = rng.uniform(0.01, 0.3, 12)
+    u1 = rng.uniform(-3, 15, 200)
+    u2 = rng.uniform(-3, 15, 200)
+    got = M.path_mean(v, u1, u2)
+    for a, b, g in zip(u1, u2, got):
+        lo, hi = min(a, b), max(a, b)
+        t = lo + (np.arange(200_000) + 0.5) * (hi - lo) / 200_000     # midpoint rule
+        ref = v[np.clip(np.floor(t).astype(int), 0, len(v) - 1)].mean()
+        assert abs(g - ref) <= 2e-4 * ref, (a, b, g, ref)
+    # inside one layer: that layer's value; a homogeneous profile: its value
+    assert np.allclose(M.path_mean(v, np.array([3.2]), np.array([3.9])), v[3])
+    assert np.allclose(M.path_mean(np.full(5, 0.07), u1, u2), 0.07)
