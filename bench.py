@@ -55,7 +55,11 @@ LANES_PER_SM = 128        # 4 schedulers x 32 lanes issue one instruction per cl
 # DRAM bytes per launch of the persistent kernel from the committed ncu
 # summary of this workload (profiles/propagate_persistent_full.md); None until
 # a capture of the current kernel exists.
-NCU_TRAFFIC_BYTES = None
+# DRAM bytes per launch from ncu captures of the current kernels: the propagation
+# launch of the 1000-event step (captured on its first 200 events, scaled by sources),
+# and one 4 194 304-row launch of the fused surrogate kernel.
+NCU_TRAFFIC_BYTES = 186e6
+SUR_NCU_TRAFFIC_BYTES = 301.6e6
 
 
 def parse():
@@ -307,7 +311,8 @@ def surrogate_leg(args, prop, stream, dev):
         peak = peaks.get("bf16_tflops") or 1800.0
         achieved = rows * SUR_FLOP_PER_PAIR / (k_ms * 1e-3) / 1e12
         out["roofline"] = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                           "frac": achieved / peak, "traffic": None,
+                           "frac": achieved / peak,
+                           "traffic": SUR_NCU_TRAFFIC_BYTES if rows == 1 << 22 else None,
                            "peak_basis": "measured bf16 burst" if "bf16_tflops" in peaks
                            else "fallback 1.8 PFLOP/s",
                            "kernel": "k_mlp_fused (rows mode)", "rows": rows, "kernel_ms": k_ms,
@@ -584,7 +589,8 @@ def run_ours(args):
                   "same_hits_as_batched": plain_same},
         "batched_over_plain": value / world / plain_value if plain_value else None,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
-                     "frac": achieved / peak_gops, "traffic": NCU_TRAFFIC_BYTES,
+                     "frac": achieved / peak_gops,
+                     "traffic": NCU_TRAFFIC_BYTES if E == 1000 else None,
                      "peak_basis": f"{props.multi_processor_count} SMs x {LANES_PER_SM} lanes x "
                                    f"{sm_max:.0f} MHz (issue peak; derived, not measured)",
                      "kernel": "k_propagate<persistent>", "kernel_ms": kern_avg_ms,
