@@ -468,6 +468,37 @@ def run_ours(args):
 
     # ---- one huge event (1e7 GeV bundle of 20 muons, 1e10 photons) in fixed
     # photon chunks accumulated into one result
+    # the same step with compact hit records (one 16-byte record per hit)
+    records = None
+    if rank == 0:
+        step()
+        stream.synchronize()
+        ref_hits = d_hits.clone()
+        cap = 1 << 24
+        d_rec = torch.empty((cap, 4), dtype=torch.int32, device=dev)
+        d_nrec = torch.zeros(1, dtype=torch.int64, device=dev)
+        for _ in range(2):
+            pp.pp_propagate_records_async(ctx, E, d_ids, d_begin, d_src, n_src, d_hits, d_counts,
+                                          1.35, d_rec, cap, d_nrec, stream.cuda_stream)
+        pp.pp_sync(ctx, stream.cuda_stream)
+        r_ms = []
+        for _ in range(3):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pp.pp_propagate_records_async(ctx, E, d_ids, d_begin, d_src, n_src, d_hits, d_counts,
+                                          1.35, d_rec, cap, d_nrec, stream.cuda_stream)
+            e1.record(stream)
+            pp.pp_sync(ctx, stream.cuda_stream)
+            r_ms.append(e0.elapsed_time(e1))
+        n_rec = int(d_nrec.item())
+        records = {"value": photons / (statistics.mean(r_ms) * 1e-3), "unit": UNIT,
+                   "ms_per_step": statistics.mean(r_ms), "records_per_step": n_rec,
+                   "record_bytes_per_step": 16 * min(n_rec, cap),
+                   "same_hits_as_batched": bool(torch.equal(d_hits, ref_hits)),
+                   "records_equal_hits": int(d_hits.sum().item()) == n_rec}
+        del d_rec, ref_hits
+
     large = None
     pp.pp_get_path_stats(ctx)
     if args.large_photons > 0:
@@ -599,6 +630,7 @@ def run_ours(args):
                      "string_search_frac": slow_n / max(1, steps_n)},
         "autotune": {"best": tuned[0], "best_ms": tuned[1]} if tuned else None,
         "steps_per_s": steps_per_launch / (kern_avg_ms * 1e-3),
+        "records": records,
         "large_event": large,
         "serving": serving,
         "e2e": {"value": photons * args.e2e_steps / e2e_s if e2e_s else None, "unit": UNIT,

@@ -211,6 +211,36 @@ int pp_propagate_range_async(pp_ctx* ctx, uint64_t event_id, const pp_source* d_
                              int32_t accumulate, uint64_t* d_hits, uint64_t* d_counts,
                              void* stream);
 
+/* ---- compact hit records ------------------------------------------------ */
+/* Paper Sec. 4: the hit store keeps only the ID of the particle that
+ * produced a hit, the time of the hit and its weight (the diagnostic fields of
+ * the older store are dropped).  One record per photon that ends on a DOM:
+ *   dom      DOM index (as in hits[])
+ *   source   index of the emitting source in the call's d_src array
+ *   time_ns  emission offset along the segment at the speed of light plus
+ *            the photon's path length at the group velocity c / group_index,
+ *            from the segment's start point (sources carry no start time)
+ *   weight   1: every geometric hit counts once (no acceptance model is given) */
+typedef struct pp_hit {
+  uint32_t dom;
+  uint32_t source;
+  float time_ns;
+  float weight;
+} pp_hit;
+
+/* pp_propagate_batch_async that also writes the hit records: the same hits
+ * and counts, plus up to max_records records in d_records[max_records]
+ * (device, in no particular order); *d_n_records (device u64, zeroed by the
+ * call) receives the number of hits, which may exceed max_records (the excess
+ * is counted, not written).  group_index <= 0 selects 1.35; otherwise it must
+ * lie in [1, 10).  n_src < 2^32.  Launched directly (never through a cached
+ * graph).  Errors: as pp_propagate_batch_async. */
+int pp_propagate_records_async(pp_ctx* ctx, int32_t n_events, const uint64_t* d_event_ids,
+                               const int64_t* d_src_begin, const pp_source* d_src, int64_t n_src,
+                               uint64_t* d_hits, uint64_t* d_counts, float group_index,
+                               pp_hit* d_records, uint64_t max_records, uint64_t* d_n_records,
+                               void* stream);
+
 /* Waits for `stream` (NULL: the context's stream) and reports a device error
  * flag raised since the last pp_sync.  Errors: PP_ECUDA, PP_EDEVICE. */
 int pp_sync(pp_ctx* ctx, void* stream);

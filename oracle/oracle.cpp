@@ -445,7 +445,7 @@ double dom_margin(const Geom& G, const double p[3], const double d[3], double S)
 
 int simulate_photon(const Model& M, uint32_t event_lo, uint64_t pid, const Source& src,
                     PhotonStats* st, double* birth6, double* trace, int n_trace,
-                    double* margin = nullptr) {
+                    double* margin = nullptr, double* emit_offset = nullptr) {
   const uint32_t key[2] = {(uint32_t)M.seed, event_lo};
   uint32_t ctr[4] = {(uint32_t)pid, (uint32_t)(pid >> 32), 0u, 0u};
   uint32_t x[4];
@@ -454,6 +454,7 @@ int simulate_photon(const Model& M, uint32_t event_lo, uint64_t pid, const Sourc
   philox4x32_10(ctr, key, x);
   double pos[3], dir[3];
   const double t0 = u01(x[0]) * src.len;
+  if (emit_offset) *emit_offset = t0;
   for (int q = 0; q < 3; ++q) pos[q] = src.p[q] + t0 * src.d[q];
   if (src.type == 1) {
     rotate(src.d, kCherenkovCos, 2.0 * kPi * u01(x[2]), dir);
@@ -677,6 +678,44 @@ int orc_propagate(const orc_params* P, int32_t n_events, const uint64_t* event_i
     stats[2] += ps.path;
     stats[3] += ps.cos_sum;
   }
+  return 0;
+}
+
+// Compact hit records of one event (paper Sec. 4: the producing particle's
+// ID, the hit time and the weight), one per photon that ends on a DOM, in
+// photon order: DOM, source index, time = (emission offset along the segment
+// + group_index x path length) / c in ns, and the photon's id.  At most
+// max_records are written; *n_records receives the number of hits.
+int orc_hit_records(const orc_params* P, uint64_t event_id, int64_t n_src, const float* src_f,
+                    const uint32_t* src_type, const uint64_t* src_n, double group_index,
+                    int64_t max_records, uint32_t* dom, uint32_t* source, double* time_ns,
+                    uint64_t* photon, int64_t* n_records) {
+  if (!P || n_src < 0 || max_records < 0 || !(group_index >= 1.0)) return -1;
+  Model M;
+  build_model(P, &M);
+  const double c = 0.299792458;  // m / ns
+  const std::vector<uint64_t> off = photon_offsets(src_n, 0, n_src);
+  int64_t n = 0;
+  PhotonStats ps;
+  for (int64_t s = 0; s < n_src; ++s) {
+    const Source src = read_source(src_f, src_type, s);
+    for (uint64_t j = 0; j < src_n[s]; ++j) {
+      const double path0 = ps.path;
+      double t_emit = 0.0;
+      const uint64_t pid = off[s] + j;
+      const int out = simulate_photon(M, (uint32_t)event_id, pid, src, &ps, nullptr, nullptr, 0,
+                                      nullptr, &t_emit);
+      if (out < 0) continue;
+      if (n < max_records) {
+        dom[n] = (uint32_t)out;
+        source[n] = (uint32_t)s;
+        time_ns[n] = (t_emit + group_index * (ps.path - path0)) / c;
+        photon[n] = pid;
+      }
+      ++n;
+    }
+  }
+  *n_records = n;
   return 0;
 }
 

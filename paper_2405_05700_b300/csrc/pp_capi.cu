@@ -167,9 +167,10 @@ int kernel_variant(const pp_ctx* ctx) {
   return 0;
 }
 
-int grid_blocks(pp_ctx* ctx, size_t smem, int* out) {
+int grid_blocks(pp_ctx* ctx, size_t smem, int* out, int variant = -1) {
   int occ = 0;
-  cudaError_t e = propagate_occupancy(ctx->block_threads, smem, kernel_variant(ctx), &occ);
+  cudaError_t e = propagate_occupancy(ctx->block_threads, smem,
+                                      variant < 0 ? kernel_variant(ctx) : variant, &occ);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   if (occ < 1) return fail(ctx, PP_EINVAL, "propagation kernel does not fit on an SM");
   const int bps = ctx->blocks_per_sm > 0 ? std::min(ctx->blocks_per_sm, occ) : occ;
@@ -184,6 +185,8 @@ RunDev run_params(const pp_ctx* ctx) {
   r.cos_cherenkov = (float)std::cos(41.0 * 3.14159265358979323846 / 180.0);
   r.sin_cherenkov = (float)std::sin(41.0 * 3.14159265358979323846 / 180.0);
   r.refill = ctx->refill;
+  r.ns_per_m_emit = (float)(1.0 / kLightSpeedMperNs);
+  r.ns_per_m_path = (float)(kGroupIndexDefault / kLightSpeedMperNs);
   return r;
 }
 
@@ -230,6 +233,9 @@ WorkDev work_desc(pp_ctx* ctx, const pp_source* d_src, int64_t n_src, bool with_
   w.single_event_lo = single_ev_lo;
   w.g_begin = 0;
   w.g_end = ~0ull;
+  w.records = nullptr;
+  w.n_records = nullptr;
+  w.max_records = 0;
   return w;
 }
 
@@ -245,15 +251,16 @@ int take_event(pp_ctx* ctx, cudaEvent_t* ev) {
 
 // Launches the propagation kernel, bracketed by timing events when enabled.
 int timed_propagate(pp_ctx* ctx, bool persistent, const WorkDev& w, const RunDev& run, int grid,
-                    uint64_t n_photons, size_t smem, cudaStream_t st) {
+                    uint64_t n_photons, size_t smem, cudaStream_t st, int variant = -1) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int rc;
   if (ctx->timing) {
     if ((rc = take_event(ctx, &e0)) || (rc = take_event(ctx, &e1))) return rc;
     PP_CUDA(cudaEventRecord(e0, st));
   }
+  if (variant < 0) variant = persistent ? kernel_variant(ctx) : 0;
   PP_CUDA(launch_propagate(persistent, ctx->ice, ctx->geom, w, run, ctx->block_threads, grid,
-                           n_photons, smem, st, persistent ? kernel_variant(ctx) : 0));
+                           n_photons, smem, st, variant));
   ctx->kernels_launched += 1;
   if (ctx->timing) {
     PP_CUDA(cudaEventRecord(e1, st));
@@ -269,10 +276,18 @@ int expand(pp_ctx* ctx, const pp_source* d_src, int64_t n_src, const int64_t* d_
   return PP_OK;
 }
 
+// Compact hit records requested from the batched path.
+struct RecordsOut {
+  pp_hit* records;
+  uint64_t capacity;
+  uint64_t* count;     // device: total hits (zeroed by the call)
+  float group_index;
+};
+
 // Batched persistent path on device data (the lock is held by the caller).
 int batch_async(pp_ctx* ctx, int32_t n_events, const uint64_t* d_ids, const int64_t* d_begin,
                 const pp_source* d_src, int64_t n_src, uint64_t* d_hits, uint64_t* d_counts,
-                cudaStream_t st) {
+                cudaStream_t st, const RecordsOut* rec = nullptr) {
   int rc;
   if ((rc = check_loaded(ctx))) return rc;
   if (n_events < 0 || n_src < 0 || n_src > kMaxSources)
@@ -280,25 +295,38 @@ int batch_async(pp_ctx* ctx, int32_t n_events, const uint64_t* d_ids, const int6
   if (n_events == 0) return PP_OK;
   if (!d_ids || !d_begin || !d_hits || !d_counts || (n_src > 0 && !d_src))
     return fail(ctx, PP_EINVAL, "null device pointer");
+  if (rec && (!rec->count || (rec->capacity > 0 && !rec->records) || n_src > 0xffffffffll ||
+              !(rec->group_index >= 1.0f && rec->group_index < 10.0f)))
+    return fail(ctx, PP_EINVAL, "hit records: need a count pointer, a buffer for capacity > 0 "
+                                "and 1 <= group_index < 10");
   const size_t hb = sizeof(uint64_t) * (size_t)n_events * ctx->geom.n_dom;
+  const int variant = rec ? kVariantRecords : kernel_variant(ctx);
   size_t smem = 0;
   int grid = 0;
   if (n_src > 0) {
     if ((rc = ensure_scratch(ctx, n_src, true))) return rc;
     if ((rc = prepare_smem(ctx, &smem))) return rc;
-    if ((rc = grid_blocks(ctx, smem, &grid))) return rc;
+    if ((rc = grid_blocks(ctx, smem, &grid, variant))) return rc;
   }
   auto enqueue = [&]() -> int {
     if (hb) PP_CUDA(cudaMemsetAsync(d_hits, 0, hb, st));
     PP_CUDA(cudaMemsetAsync(d_counts, 0, sizeof(uint64_t) * 4 * (size_t)n_events, st));
+    if (rec) PP_CUDA(cudaMemsetAsync(rec->count, 0, sizeof(uint64_t), st));
     if (n_src == 0) return PP_OK;
     PP_CUDA(cudaMemsetAsync(ctx->work.p, 0, sizeof(uint64_t), st));
     int r;
     if ((r = expand(ctx, d_src, n_src, d_begin, d_ids, n_events, true, st))) return r;
-    const WorkDev w = work_desc(ctx, d_src, n_src, true, d_begin, d_ids, d_hits, d_counts, 0);
-    return timed_propagate(ctx, true, w, run_params(ctx), grid, 0, smem, st);
+    WorkDev w = work_desc(ctx, d_src, n_src, true, d_begin, d_ids, d_hits, d_counts, 0);
+    RunDev run = run_params(ctx);
+    if (rec) {
+      w.records = rec->records;
+      w.n_records = reinterpret_cast<unsigned long long*>(rec->count);
+      w.max_records = rec->capacity;
+      run.ns_per_m_path = (float)(rec->group_index / kLightSpeedMperNs);
+    }
+    return timed_propagate(ctx, true, w, run, grid, 0, smem, st, variant);
   };
-  if (!ctx->graphs || ctx->timing || st == nullptr) return enqueue();
+  if (!ctx->graphs || ctx->timing || st == nullptr || rec) return enqueue();
   // CUDA graph: capture this exact launch sequence once, replay it afterwards
   const uint64_t key[12] = {(uint64_t)n_events, (uint64_t)n_src, (uint64_t)d_ids, (uint64_t)d_begin,
                             (uint64_t)d_src, (uint64_t)d_hits, (uint64_t)d_counts, (uint64_t)st,
@@ -796,6 +824,20 @@ int pp_propagate_batch_async(pp_ctx* ctx, int32_t n_events, const uint64_t* d_ev
   PP_CUDA(cudaSetDevice(ctx->cfg.device));
   return batch_async(ctx, n_events, d_event_ids, d_src_begin, d_src, n_src, d_hits, d_counts,
                      pick_stream(ctx, stream));
+}
+
+int pp_propagate_records_async(pp_ctx* ctx, int32_t n_events, const uint64_t* d_event_ids,
+                               const int64_t* d_src_begin, const pp_source* d_src, int64_t n_src,
+                               uint64_t* d_hits, uint64_t* d_counts, float group_index,
+                               pp_hit* d_records, uint64_t max_records, uint64_t* d_n_records,
+                               void* stream) {
+  if (!ctx) return PP_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  const RecordsOut rec{d_records, max_records, d_n_records,
+                       group_index > 0.0f ? group_index : (float)kGroupIndexDefault};
+  return batch_async(ctx, n_events, d_event_ids, d_src_begin, d_src, n_src, d_hits, d_counts,
+                     pick_stream(ctx, stream), &rec);
 }
 
 int pp_propagate_plain_async(pp_ctx* ctx, int32_t n_events, const uint64_t* h_event_ids,

@@ -359,6 +359,10 @@ struct Photon {
   uint32_t n;          // steps taken
   uint32_t pid_lo, pid_hi, ev_lo;
   int ev;              // event slot for the tallies
+  // hit records only (dead code elsewhere): emission offset along the
+  // segment, path length so far, emitting source
+  float t_emit, path;
+  int src;
 };
 
 // a2: birth from Philox block 0 -- point on the emitting segment, direction
@@ -377,6 +381,8 @@ __device__ __forceinline__ bool birth(Photon& ph, const pp_source& s, const IceD
     sdz *= inv;
   }
   const float t0 = u01f(x.x) * s.length;
+  ph.t_emit = t0;
+  ph.path = 0.0f;
   ph.px = fmaf(t0, sdx, s.x);
   ph.py = fmaf(t0, sdy, s.y);
   ph.pz = fmaf(t0, sdz, s.z);
@@ -420,9 +426,13 @@ __device__ __forceinline__ int photon_step(Photon& ph, const IceDev& I, const Ge
   const float St = fminf(S, tw);
   float th;
   const int k = first_hit_grid(G, T, ph.px, ph.py, ph.pz, ph.dx, ph.dy, ph.dz, St, th, slow);
-  if (k >= 0 && th < tw) return k;
+  if (k >= 0 && th < tw) {
+    ph.path += th;
+    return k;
+  }
   if (tw <= S) return kEscaped;
   if (absorb) return kAbsorbed;
+  ph.path += S;
   ph.px = fmaf(S, ph.dx, ph.px);
   ph.py = fmaf(S, ph.dy, ph.py);
   ph.pz = fmaf(S, ph.dz, ph.pz);
@@ -524,6 +534,22 @@ __device__ __forceinline__ void tally(const WorkDev& W, int n_dom, const Photon&
     if (out == kTruncated) atomicAdd(cnt + 2, 1ull);
   }
   atomicAdd(cnt + 3, (unsigned long long)ph.n);
+}
+
+// Compact hit record (paper Sec. 4: the producing particle's ID, the hit time
+// and the weight): appended at an atomic cursor; past the capacity only the
+// count grows.
+__device__ __forceinline__ void record_hit(const WorkDev& W, const RunDev& R, const Photon& ph,
+                                           int dom) {
+  const unsigned long long i = atomicAdd(W.n_records, 1ull);
+  if (i < W.max_records) {
+    pp_hit h;
+    h.dom = (uint32_t)dom;
+    h.source = (uint32_t)ph.src;
+    h.time_ns = fmaf(ph.path, R.ns_per_m_path, ph.t_emit * R.ns_per_m_emit);
+    h.weight = 1.0f;
+    W.records[i] = h;
+  }
 }
 
 // Per-lane tallies of the lane's current event: the absorbed / escaped /

@@ -90,6 +90,11 @@ struct WorkDev {
   int n_src;
   uint32_t single_event_lo;   // event id (low word) in single-event mode
   uint64_t g_begin, g_end;    // persistent kernel: batch photon range to run
+  // compact hit records (records kernel variant only): one pp_hit per hit,
+  // appended at an atomic cursor; records past max_records are counted, not written
+  pp_hit* records;
+  unsigned long long* n_records;
+  uint64_t max_records;
 };
 
 struct RunDev {
@@ -97,6 +102,8 @@ struct RunDev {
   uint32_t max_steps;
   float cos_cherenkov, sin_cherenkov;
   int refill;                 // persistent: refill once this many lanes are idle
+  float ns_per_m_emit;        // hit time: emission offset along the segment at c (ns / m)
+  float ns_per_m_path;        // hit time: photon path at the group velocity (ns / m)
 };
 
 // Shared-memory footprint of the tables the propagation kernels stage.
@@ -121,7 +128,15 @@ cudaError_t launch_expand(const pp_source* src, int64_t n_src, const int64_t* sr
 //   persistent = false: one thread per photon, `n_photons_host` photons
 //   persistent = true : grid_blocks persistent blocks with warp refill
 // variant selects the register budget of the persistent kernel: 0 = any block
-// size (up to 64 registers), 5 / 6 = 256-thread blocks, 5 / 6 resident per SM.
+// size (up to 64 registers), 5 / 6 = 256-thread blocks, 5 / 6 resident per SM;
+// kVariantRecords = variant 0 that also writes compact hit records.
+constexpr int kVariantRecords = 7;
+
+// Hit times: light speed in vacuum, and the group index used unless the
+// caller gives one (the paper gives none; 1.35 is a typical value for ice in
+// the blue, a reading).
+constexpr double kLightSpeedMperNs = 0.299792458;
+constexpr double kGroupIndexDefault = 1.35;
 cudaError_t launch_propagate(bool persistent, const IceDev& ice, const GeomDev& geom,
                              const WorkDev& work, const RunDev& run, int block_threads,
                              int grid_blocks, uint64_t n_photons_host, size_t smem,

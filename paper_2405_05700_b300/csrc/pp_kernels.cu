@@ -204,7 +204,8 @@ __global__ void k_finish(int64_t n_src, const int64_t* __restrict__ src_begin,
 }
 
 // ---- a2..a8: propagation ---------------------------------------------------
-template <bool kPersistent, int kMinBlocks>
+// kRecords (persistent only): also append a compact record per hit.
+template <bool kPersistent, int kMinBlocks, bool kRecords = false>
 __global__ void __launch_bounds__(kMinBlocks > 0 ? 256 : 1024, kMinBlocks > 0 ? kMinBlocks : 1)
 k_propagate(IceDev I, GeomDev G, WorkDev W, RunDev R, uint64_t n_plain) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -258,6 +259,7 @@ k_propagate(IceDev I, GeomDev G, WorkDev W, RunDev R, uint64_t n_plain) {
             identify(W, s, in_src, g, ph);
             const pp_source src = W.src[s];
             alive = birth(ph, src, I, R);
+            if (kRecords) ph.src = s;
             births += 1;
             if (!alive) atomicOr(W.err, kErrBadSource);
           }
@@ -271,6 +273,7 @@ k_propagate(IceDev I, GeomDev G, WorkDev W, RunDev R, uint64_t n_plain) {
         const int out = photon_step(ph, I, G, T, R, crossings, slow);
         if (out != kScattered) {
           tally(W, G.n_dom, ph, out, lt);
+          if (kRecords && out >= 0) record_hit(W, R, ph, out);
           steps += ph.n;
           alive = false;
         }
@@ -402,7 +405,8 @@ cudaError_t launch_expand(const pp_source* src, int64_t n_src, const int64_t* sr
 
 cudaError_t set_propagate_smem_limit(size_t smem) {
   const void* fns[] = {(const void*)k_propagate<true, 0>, (const void*)k_propagate<true, 5>,
-                       (const void*)k_propagate<true, 6>, (const void*)k_propagate<false, 0>};
+                       (const void*)k_propagate<true, 6>, (const void*)k_propagate<false, 0>,
+                       (const void*)k_propagate<true, 0, true>};
   cudaError_t e;
   for (const void* f : fns) {
     e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -421,6 +425,9 @@ cudaError_t propagate_occupancy(int block_threads, size_t smem, int variant, int
   if (variant == 6)
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_propagate<true, 6>, 256,
                                                          smem);
+  if (variant == kVariantRecords)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        blocks_per_sm, k_propagate<true, 0, true>, block_threads, smem);
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_propagate<true, 0>,
                                                        block_threads, smem);
 }
@@ -434,6 +441,8 @@ cudaError_t launch_propagate(bool persistent, const IceDev& ice, const GeomDev& 
       k_propagate<true, 5><<<grid_blocks, 256, smem, st>>>(ice, geom, work, run, 0);
     else if (variant == 6)
       k_propagate<true, 6><<<grid_blocks, 256, smem, st>>>(ice, geom, work, run, 0);
+    else if (variant == kVariantRecords)
+      k_propagate<true, 0, true><<<grid_blocks, block_threads, smem, st>>>(ice, geom, work, run, 0);
     else
       k_propagate<true, 0><<<grid_blocks, block_threads, smem, st>>>(ice, geom, work, run, 0);
   } else {

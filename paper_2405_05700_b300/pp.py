@@ -62,6 +62,8 @@ _SIGS = {
     "pp_propagate_batch_async": [_vp, _i32, _vp, _vp, _vp, _i64, _vp, _vp, _vp],
     "pp_propagate_plain_async": [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "pp_propagate_noalloc": [_vp, _u64, _vp, _i64, _vp, _vp, _vp],
+    "pp_propagate_records_async": [_vp, _i32, _vp, _vp, _vp, _i64, _vp, _vp, C.c_float, _vp, _u64,
+                                   _vp, _vp],
     "pp_propagate_range_async": [_vp, _u64, _vp, _i64, _u64, _u64, _i32, _vp, _vp, _vp],
     "pp_sync": [_vp, _vp],
     "pp_set_launch": [_vp, _i32, _i32, _i32],
@@ -209,6 +211,20 @@ def pp_propagate_range_async(ctx, event_id, d_src, n_src, photon_begin, photon_e
                              d_hits, d_counts, stream=None):
     return _call("pp_propagate_range_async", ctx, event_id, _ptr(d_src), n_src, photon_begin,
                  photon_end, 1 if accumulate else 0, _ptr(d_hits), _ptr(d_counts), _ptr(stream))
+
+
+# pp_hit: DOM index, source index, time (ns), weight
+HIT_DTYPE = np.dtype([("dom", "<u4"), ("source", "<u4"), ("time_ns", "<f4"), ("weight", "<f4")])
+
+
+def pp_propagate_records_async(ctx, n_events, d_event_ids, d_src_begin, d_src, n_src, d_hits,
+                               d_counts, group_index, d_records, max_records, d_n_records,
+                               stream=None):
+    """Batched propagation that also writes compact hit records (16 bytes each,
+    HIT_DTYPE) into d_records and their total number into d_n_records."""
+    return _call("pp_propagate_records_async", ctx, n_events, _ptr(d_event_ids),
+                 _ptr(d_src_begin), _ptr(d_src), n_src, _ptr(d_hits), _ptr(d_counts),
+                 group_index, _ptr(d_records), max_records, _ptr(d_n_records), _ptr(stream))
 
 
 PP_NOALLOC_MAX_SOURCES = 8192
