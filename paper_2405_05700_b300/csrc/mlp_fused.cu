@@ -3,16 +3,21 @@
 // leaving the SM.
 //
 // Per CTA (one per SM): two row halves of 128 pairs, each an M = 128 tcgen05
-// MMA with its FP32 accumulator (256 columns) in TMEM, so one weight chunk
-// feeds both halves.  The layer's input (features, then BF16 activations)
-// sits in shared memory as the MMA's A operand; the weights (W1 as one chunk,
-// then 8 chunks per hidden layer) stream from global memory (L2-resident,
-// shared by every CTA) through a ring of 16 KB chunks filled by bulk copies.
+// MMA chain with its FP32 accumulator (256 columns) in TMEM.  The halves run
+// in ping-pong: while the tensor core computes one half's layer, the other
+// half's epilogue converts its previous layer, so MMAs and epilogues overlap.
+// A layer's input (features, then BF16 activations) sits in shared memory as
+// the MMA's A operand; the weights (W1 as one chunk, then 8 chunks per hidden
+// layer) stream from global memory (L2-resident, shared by every CTA) through
+// a ring of 16 KB chunks filled by bulk copies, once per half.
 //
-//   warps 0-7 : epilogue (warp w: half w / 4, TMEM lanes 32 (w % 4) ..): features,
-//               bias + SiLU to BF16 back into shared memory, head
-//   warp 8    : producer of the weight ring
-//   warp 9    : MMA issue (one thread)
+//   warps 0-15 : epilogue.  Warp w serves half (w / 4) % 2, TMEM lanes
+//                32 (w % 4) .. + 31 (its 32 rows) and columns 128 (w / 8) .. + 127:
+//                features (column group 0), bias + SiLU to BF16 back into shared
+//                memory, the head (the two column groups' partial dot products
+//                meet in shared memory)
+//   warp 16    : producer of the weight ring
+//   warp 17    : MMA issue (one thread)
 //
 // Every wait is bounded; a wait that runs out raises the CTA's abort flag and
 // the device error flag, and every role then leaves its loop.
@@ -35,10 +40,14 @@ constexpr int kChunksPerLayer = kHid / kChunkK;
 constexpr int kChunkBytes = kHid * kChunkK * 2;
 constexpr int kStages = 5;
 constexpr int kHiddenGemms = kLayers - 1;  // layers 2..4
-constexpr int kChunksPerTile = 1 + kHiddenGemms * kChunksPerLayer;
+constexpr int kChunksPerLayerSet = 1 + kHiddenGemms * kChunksPerLayer;  // W1..W4
+constexpr int kChunksPerTile = 2 * kChunksPerLayerSet;                   // once per half
 static_assert(kIn == kChunkK, "W1 is one ring chunk");
-constexpr int kEpiThreads = 256;
+constexpr int kEpiWarps = 16;
+constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kThreads = kEpiThreads + 64;
+constexpr int kProducerWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1;
+constexpr int kColsPerWarp = kHid / 2;
 constexpr uint32_t kWaitTries = 1u << 22;
 
 // dynamic shared memory
@@ -73,7 +82,9 @@ __device__ __forceinline__ float silu_exact(float z) { return z / (1.0f + __expf
 template <bool kFromPairs, bool kExactSilu>
 __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], acc_full, in_ready, done;
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], acc_full[2], in_ready[2], done;
+  __shared__ __align__(8) uint64_t head_bar[8];  // per (half, lane quarter): partial z written
+  __shared__ float zpart[kRows];                 // column group 1's partial head sums
   __shared__ uint32_t tslot;
   __shared__ int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -86,9 +97,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
       tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], 1);
     }
-    tc::mbar_init(&acc_full, 1);
-    tc::mbar_init(&in_ready, kEpiThreads);
+    for (int h = 0; h < 2; ++h) {
+      tc::mbar_init(&acc_full[h], 1);
+      tc::mbar_init(&in_ready[h], kEpiThreads / 2);
+    }
     tc::mbar_init(&done, 1);
+    for (int i = 0; i < 8; ++i) tc::mbar_init(&head_bar[i], 32);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -103,13 +117,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
   tc::fence_after_sync();
   const uint32_t tmem = tslot;
 
-  if (warp == 8) {
+  if (warp == kProducerWarp) {
     // ---------------------------------------------------------- producer --
     if (lane == 0) {
       uint32_t it = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-        for (int j = 0; j < kChunksPerTile; ++j, ++it) {
+        for (int jt = 0; jt < kChunksPerTile; ++jt, ++it) {
+          // job order (layer, half); W1 is chunk 0, hidden layer l's chunk c is 1 + 8 (l - 1) + c
+          const int layer = jt < 2 ? 0 : 1 + (jt - 2) / (2 * kChunksPerLayer);
+          const int c = jt < 2 ? 0 : (jt - 2) % kChunksPerLayer;
+          const int j = layer == 0 ? 0 : 1 + (layer - 1) * kChunksPerLayer + c;
           const uint32_t s = it % kStages;
           if (it >= (uint32_t)kStages) {
             if (!tc::mbar_wait(&empty[s], ((it / kStages) - 1) & 1, kWaitTries) ||
@@ -134,22 +152,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
         tc::mbar_wait(&full[i % kStages], (i / kStages) & 1, kWaitTries);
       }
     }
-  } else if (warp == 9) {
+  } else if (warp == kMmaWarp) {
     // --------------------------------------------------------------- MMA --
     if (lane == 0) {
       const uint32_t idesc = tc::idesc_bf16(kHalf, kHid);
       const uint32_t sh = tc::smem_u32(smem + kOffH);
       const uint32_t ring = tc::smem_u32(smem + kOffRing);
-      uint32_t it = 0, in_phase = 0;
+      uint32_t it = 0, in_phase[2] = {0u, 0u};
       bool ok = true;
       for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-        for (int layer = 0; layer < kLayers && ok; ++layer) {
-          if (!tc::mbar_wait(&in_ready, in_phase & 1, kWaitTries) ||
+        // jobs (layer, half) in order: half h's layer l waits for its own
+        // epilogue of layer l - 1, which overlaps the other half's MMAs
+        for (int job = 0; job < 2 * kLayers && ok; ++job) {
+          const int layer = job >> 1, h = job & 1;
+          if (!tc::mbar_wait(&in_ready[h], in_phase[h] & 1, kWaitTries) ||
               *(volatile int*)&abort_flag) {
             ok = false;
             break;
           }
-          ++in_phase;
+          ++in_phase[h];
           tc::fence_after_sync();
           // layer 0: features (32 columns) x W1 (one chunk); then 8 chunks per layer
           const int chunks = layer == 0 ? 1 : kChunksPerLayer;
@@ -163,18 +184,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
             tc::fence_after_sync();
             const uint32_t b0 = ring + s * kChunkBytes;
 #pragma unroll
-            for (int h = 0; h < 2; ++h)
-#pragma unroll
-              for (int kk = 0; kk < kChunkK / 16; ++kk) {
-                const uint32_t k0 = c * kChunkK + kk * 16;
-                tc::mma_bf16(tmem + h * kHid,
-                             tc::smem_desc(sh + h * kHalfBytes + k0 * 16, 128, sbo_a),
-                             tc::smem_desc(b0 + kk * 256, 128, kChunkK * 16), idesc,
-                             (c > 0 || kk > 0) ? 1u : 0u);
-              }
+            for (int kk = 0; kk < kChunkK / 16; ++kk) {
+              const uint32_t k0 = c * kChunkK + kk * 16;
+              tc::mma_bf16(tmem + h * kHid,
+                           tc::smem_desc(sh + h * kHalfBytes + k0 * 16, 128, sbo_a),
+                           tc::smem_desc(b0 + kk * 256, 128, kChunkK * 16), idesc,
+                           (c > 0 || kk > 0) ? 1u : 0u);
+            }
             tc::mma_commit(&empty[s]);
           }
-          tc::mma_commit(&acc_full);
+          tc::mma_commit(&acc_full[h]);
         }
       }
       if (!ok) {
@@ -187,18 +206,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
     }
   } else {
     // ---------------------------------------------------------- epilogue --
-    const int h = warp >> 2, q = warp & 3;
+    const int q = warp & 3, h = (warp >> 2) & 1, cg = warp >> 3;
     const int r = q * 32 + lane;  // row within the half = TMEM lane
+    const int c_begin = cg * kColsPerWarp;
     unsigned char* sH = smem + kOffH + h * kHalfBytes;
     const float* par = reinterpret_cast<const float*>(smem + kOffPar);
-    const uint32_t tacc = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * kHid);
-    uint32_t acc_phase = 0;
+    const uint32_t tacc =
+        tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * kHid) + (uint32_t)c_begin;
+    uint64_t* hb = &head_bar[h * 4 + q];
+    uint32_t acc_phase = 0, head_phase = 0;
     bool ok = true;
     for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
       const int64_t row = t * kRows + h * kHalf + r;
       const bool valid = row < a.n;
       // features of this row as the first MMA's A operand (aliasing the activations)
-      {
+      if (cg == 0) {
         uint4 fv[kIn / 8];
 #pragma unroll
         for (int i = 0; i < kIn / 8; ++i) fv[i] = make_uint4(0, 0, 0, 0);
@@ -217,14 +239,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
 #pragma unroll
         for (int i = 0; i < kIn / 8; ++i)
           *reinterpret_cast<uint4*>(sH + tc::tile_off(r, 8 * i, kIn)) = fv[i];
+        tc::fence_smem_async();
       }
-      tc::fence_smem_async();
       tc::fence_before_sync();
-      tc::mbar_arrive(&in_ready);
-      float zh = 0.0f;  // head: w5 . h4
+      tc::mbar_arrive(&in_ready[h]);
+      float zh = 0.0f;  // head: this column group's part of w5 . h4
       for (int layer = 0; layer < kLayers; ++layer) {
         // warp-uniform outcome: the TMEM loads below are warp-collective
-        const bool got = tc::mbar_wait(&acc_full, acc_phase & 1, kWaitTries) &&
+        const bool got = tc::mbar_wait(&acc_full[h], acc_phase & 1, kWaitTries) &&
                          !*(volatile int*)&abort_flag;
         if (!__all_sync(0xffffffffu, got)) {
           ok = false;
@@ -233,12 +255,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
         ++acc_phase;
         __syncwarp();
         tc::fence_after_sync();
-        const float* bias = par + layer * kHid;
-        const float* w5 = par + kLayers * kHid;
-        for (int c0 = 0; c0 < kHid; c0 += 32) {
-          uint32_t raw[32];
-          tc::tmem_ld32_nowait(tacc + c0, raw);
-          tc::tmem_wait_ld();
+        const float* bias = par + layer * kHid + c_begin;
+        const float* w5 = par + kLayers * kHid + c_begin;
+        const bool last = layer == kLayers - 1;
+        // 32 columns: bias, SiLU, BF16; into shared memory (or the head)
+        auto consume = [&](const uint32_t (&raw)[32], int c0) {
           uint32_t packed[16];
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
@@ -248,10 +269,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
             const float y1 = kExactSilu ? silu_exact(z1) : silu_fast(z1);
             packed[j] = pack_bf16(y0, y1);
           }
-          if (layer < kLayers - 1) {
+          if (!last) {
 #pragma unroll
             for (int i = 0; i < 4; ++i)
-              *reinterpret_cast<uint4*>(sH + tc::tile_off(r, c0 + 8 * i, kHid)) =
+              *reinterpret_cast<uint4*>(sH + tc::tile_off(r, c_begin + c0 + 8 * i, kHid)) =
                   make_uint4(packed[4 * i], packed[4 * i + 1], packed[4 * i + 2],
                              packed[4 * i + 3]);
           } else {
@@ -262,15 +283,42 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
               zh = fmaf(__high2float(v), w5[c0 + 2 * j + 1], zh);
             }
           }
-        }
-        if (layer < kLayers - 1) {
+        };
+        // two register sets: the next TMEM load is in flight while one is converted
+        uint32_t ra[32], rb[32];
+        tc::tmem_ld32_nowait(tacc + 0, ra);
+        tc::tmem_wait_ld(ra);
+        tc::tmem_ld32_nowait(tacc + 32, rb);
+        consume(ra, 0);
+        tc::tmem_wait_ld(rb);
+        tc::tmem_ld32_nowait(tacc + 64, ra);
+        consume(rb, 32);
+        tc::tmem_wait_ld(ra);
+        tc::tmem_ld32_nowait(tacc + 96, rb);
+        consume(ra, 64);
+        tc::tmem_wait_ld(rb);
+        consume(rb, 96);
+        if (!last) {
           // activations written and accumulator read: the next layer may start
           tc::fence_smem_async();
           tc::fence_before_sync();
-          tc::mbar_arrive(&in_ready);
+          tc::mbar_arrive(&in_ready[h]);
         }
       }
       if (!ok) break;
+      // the head: column group 1 hands its partial sum to group 0
+      if (cg == 1) {
+        zpart[h * kHalf + r] = zh;
+        tc::mbar_arrive(hb);
+        continue;
+      }
+      const bool got = tc::mbar_wait(hb, head_phase & 1, kWaitTries);
+      ++head_phase;
+      if (!got) {
+        ok = false;
+        break;
+      }
+      zh += zpart[h * kHalf + r];
       if (valid) {
         const float z = zh + *a.b5;
         if (kFromPairs) {
@@ -321,7 +369,7 @@ __global__ void k_pack_weights(const __nv_bfloat16* w1, const __nv_bfloat16* w2,
 
 }  // namespace
 
-size_t packed_weight_bytes() { return (size_t)kChunksPerTile * kChunkBytes; }
+size_t packed_weight_bytes() { return (size_t)kChunksPerLayerSet * kChunkBytes; }
 
 cudaError_t launch_pack_weights(const __nv_bfloat16* const* w, unsigned char* out,
                                 cudaStream_t st) {
