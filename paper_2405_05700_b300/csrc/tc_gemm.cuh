@@ -68,19 +68,31 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
           smem_u32(bar)));
 }
 
-// Waits for the mbarrier phase `parity` to complete; gives up after
-// `max_tries` polls (returns false) so that a lost arrival cannot hang the GPU.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t max_tries) {
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Waits for the mbarrier phase `parity` to complete.  Each try suspends the
+// thread until the phase completes or a 0.1 ms hint runs out, so a waiter
+// resumes as soon as the phase flips; the wait gives up (returns false) after
+// `max_tries` tries or once `limit_ns` have passed on the global timer, so a
+// lost arrival cannot hang the GPU.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t max_tries,
+                                          uint64_t limit_ns = 2000000000ull) {
   const uint32_t a = smem_u32(bar);
+  uint64_t t0 = 0;
   for (uint32_t i = 0; i < max_tries; ++i) {
     uint32_t done;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
         " selp.b32 %0, 1, 0, p;\n}"
         : "=r"(done)
-        : "r"(a), "r"(parity));
+        : "r"(a), "r"(parity), "r"(100000u));
     if (done) return true;
-    if (i > 64) __nanosleep(64);
+    if (i == 0) t0 = globaltimer_ns();
+    else if (globaltimer_ns() - t0 > limit_ns) return false;
   }
   return false;
 }
