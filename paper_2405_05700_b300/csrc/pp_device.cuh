@@ -24,19 +24,22 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
       k.x += 0x9E3779B9u;
       k.y += 0xBB67AE85u;
     }
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-    const uint32_t lo0 = 0xD2511F53u * c.x;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
-    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    // one 32 x 32 -> 64-bit product each (high and low halves together)
+    const unsigned long long p0 = 0xD2511F53ull * c.x;
+    const unsigned long long p1 = 0xCD9E8D57ull * c.z;
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
     c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
   }
   return c;
 }
 
 // uint32 -> (0, 1): top 24 bits with the lowest forced to 1, times 2^-24
-// (exact in FP32).
+// (exact in FP32).  With j = x >> 9 that is (2j + 1) 2^-24, formed without an
+// int-to-float conversion as (1 + j 2^-23) - (1 - 2^-24): both operands and
+// the difference are exact in FP32, so the subtraction is exact.
 __device__ __forceinline__ float u01f(uint32_t x) {
-  return __uint2float_rn((x >> 8) | 1u) * 5.9604644775390625e-08f;
+  return __uint_as_float(0x3F800000u | (x >> 9)) - __uint_as_float(0x3F7FFFFFu);
 }
 
 // Hot-path arithmetic: hardware approximations (PTX sqrt.approx / MUFU
@@ -184,6 +187,13 @@ __device__ __forceinline__ float world_exit_within(const GeomDev& G, float px, f
   return inside ? PP_INF : world_exit(G, px, py, pz, dx, dy, dz);
 }
 
+// Radius of a ball about p that lies inside the world cylinder (less a 1 cm
+// margin for FP32 error); negative outside.
+__device__ __forceinline__ float world_inner(const GeomDev& G, float px, float py, float pz) {
+  const float rho = fast_sqrt(fmaf(px, px, py * py));
+  return fminf(G.R - rho, fminf(pz - G.zlo, G.zhi - pz)) - 0.01f;
+}
+
 // Sphere of radius r about c met on [p, p + S d]: entry distance, 0 when the
 // start is inside.  Uses r^2 - |m - (m.d) d|^2 for the discriminant (the
 // same quantity as (m.d)^2 - |m|^2 + r^2, with less cancellation).
@@ -260,17 +270,24 @@ __device__ __forceinline__ void test_string(const GeomDev& G, const Tables& T, i
 // Fast path: a step shorter (horizontally) than its cell's clearance cannot
 // reach any string.  Otherwise the cell's string list (steps up to `halo`
 // long) or every string is searched.
+// clear_out (optional) receives the clearance of the start point's cell: no
+// horizontal displacement shorter than it reaches a string.
 __device__ __forceinline__ int first_hit_grid(const GeomDev& G, const Tables& T, float px,
                                               float py, float pz, float dx, float dy, float dz,
-                                              float S, float& t_out, uint32_t& slow) {
+                                              float S, float& t_out, uint32_t& slow,
+                                              float* clear_out = nullptr) {
   t_out = PP_INF;
-  if (G.n_dom == 0) return -1;
+  if (G.n_dom == 0) {
+    if (clear_out) *clear_out = PP_INF;
+    return -1;
+  }
   const float dxy2 = fmaf(dx, dx, dy * dy);
   const float L2 = S * S * dxy2;  // squared horizontal length of the step
   const int ix = min(max(__float2int_rd((px - G.gx0) * G.inv_cell), 0), G.nx - 1);
   const int iy = min(max(__float2int_rd((py - G.gy0) * G.inv_cell), 0), G.ny - 1);
   const int cell = iy * G.nx + ix;
   const float clr = (float)T.clear[cell] * G.clear_unit;
+  if (clear_out) *clear_out = clr;
   if (L2 < clr * clr) return -1;
   slow += 1;
   const float Lxy = fast_sqrt(L2);
@@ -363,6 +380,11 @@ struct Photon {
   // segment, path length so far, emitting source
   float t_emit, path;
   int src;
+  // conservative budgets (negative: unknown): a ball of radius wb about the
+  // position lies inside the world; no horizontal move shorter than cb
+  // reaches a string.  They shrink by each step's length, so most steps
+  // skip the world-exit and cell-grid tests.
+  float wb, cb;
 };
 
 // a2: birth from Philox block 0 -- point on the emitting segment, direction
@@ -404,6 +426,8 @@ __device__ __forceinline__ bool birth(Photon& ph, const pp_source& s, const IceD
   }
   ph.tau_a = neg_log(u01f(x.w));
   ph.n = 0;
+  ph.wb = -1.0f;
+  ph.cb = -1.0f;
   const bool ok = s.type <= PP_SRC_CASCADE && isfinite(ph.px) && isfinite(ph.py) &&
                   isfinite(ph.pz) && nn > 0.0f && s.length >= 0.0f;
   ph.layer = ok ? layer_at(I, ph.pz, ph.dz) : 0;
@@ -422,10 +446,20 @@ __device__ __forceinline__ int photon_step(Photon& ph, const IceDev& I, const Ge
   float tau_a = ph.tau_a;
   bool absorb;
   const float S = walk(T.layer, I, ph.pz, ph.dz, layer, tau_s, tau_a, absorb, crossings);
-  const float tw = world_exit_within(G, ph.px, ph.py, ph.pz, ph.dx, ph.dy, ph.dz, S);
+  // world exit: +inf while the step provably stays inside (same decisions as
+  // the exact distance, see world_exit_within)
+  float tw = PP_INF;
+  if (!(S + 0.01f < ph.wb)) {
+    ph.wb = world_inner(G, ph.px, ph.py, ph.pz);
+    if (!(S + 0.01f < ph.wb)) tw = world_exit(G, ph.px, ph.py, ph.pz, ph.dx, ph.dy, ph.dz);
+  }
   const float St = fminf(S, tw);
-  float th;
-  const int k = first_hit_grid(G, T, ph.px, ph.py, ph.pz, ph.dx, ph.dy, ph.dz, St, th, slow);
+  // DOM test, skipped while the step's horizontal length is inside the budget
+  const float lxy = St * fast_sqrt(fmaf(ph.dx, ph.dx, ph.dy * ph.dy));
+  float th = PP_INF;
+  int k = -1;
+  if (!(lxy < ph.cb))
+    k = first_hit_grid(G, T, ph.px, ph.py, ph.pz, ph.dx, ph.dy, ph.dz, St, th, slow, &ph.cb);
   if (k >= 0 && th < tw) {
     ph.path += th;
     return k;
@@ -433,6 +467,8 @@ __device__ __forceinline__ int photon_step(Photon& ph, const IceDev& I, const Ge
   if (tw <= S) return kEscaped;
   if (absorb) return kAbsorbed;
   ph.path += S;
+  ph.wb -= S + 1e-4f;
+  ph.cb -= lxy + 1e-4f;
   ph.px = fmaf(S, ph.dx, ph.px);
   ph.py = fmaf(S, ph.dy, ph.py);
   ph.pz = fmaf(S, ph.dz, ph.pz);
