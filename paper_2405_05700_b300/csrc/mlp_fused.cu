@@ -54,7 +54,7 @@ constexpr uint32_t kWaitTries = 1u << 22;
 constexpr uint32_t kOffH = 0;                                  // 2 x [128][256] BF16 (features alias)
 constexpr uint32_t kHalfBytes = kHalf * kHid * 2;
 constexpr uint32_t kOffRing = kOffH + 2 * kHalfBytes;
-constexpr uint32_t kOffPar = kOffRing + kStages * kChunkBytes;  // biases [4][256], w5 [256] (FP32)
+constexpr uint32_t kOffPar = kOffRing + kStages * kChunkBytes;  // biases / 2 [4][256], w5 [256] (FP32)
 constexpr uint32_t kSmemBytes = kOffPar + (kLayers + 1) * kHid * 4;
 static_assert(kSmemBytes + 1024 <= 232448, "shared memory per CTA");
 
@@ -64,11 +64,8 @@ __device__ __forceinline__ float tanh_approx(float x) {
   return y;
 }
 
-// silu(z) = z sigmoid(z) = z (1 + tanh(z / 2)) / 2: one SFU operation.
-__device__ __forceinline__ float silu_fast(float z) {
-  const float h = 0.5f * z;
-  return fmaf(h, tanh_approx(h), h);
-}
+// silu(z) = z sigmoid(z) = h (1 + tanh h) with h = z / 2: one SFU operation.
+__device__ __forceinline__ float silu_half(float h) { return fmaf(h, tanh_approx(h), h); }
 
 __device__ __forceinline__ float softplus(float z) { return z > 20.0f ? z : log1pf(__expf(z)); }
 
@@ -107,9 +104,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   {
+    // halved biases: the epilogue forms z / 2 = acc / 2 + b / 2 in one FMA
     float* par = reinterpret_cast<float*>(smem + kOffPar);
     for (int i = threadIdx.x; i < kLayers * kHid; i += blockDim.x)
-      par[i] = a.bias[i / kHid][i % kHid];
+      par[i] = 0.5f * a.bias[i / kHid][i % kHid];
     for (int i = threadIdx.x; i < kHid; i += blockDim.x) par[kLayers * kHid + i] = a.w5[i];
   }
   tc::fence_before_sync();
@@ -255,19 +253,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
         ++acc_phase;
         __syncwarp();
         tc::fence_after_sync();
-        const float* bias = par + layer * kHid + c_begin;
+        const float* hbias = par + layer * kHid + c_begin;
         const float* w5 = par + kLayers * kHid + c_begin;
         const bool last = layer == kLayers - 1;
         // 32 columns: bias, SiLU, BF16; into shared memory (or the head)
         auto consume = [&](const uint32_t (&raw)[32], int c0) {
           uint32_t packed[16];
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const float z0 = __uint_as_float(raw[2 * j]) + bias[c0 + 2 * j];
-            const float z1 = __uint_as_float(raw[2 * j + 1]) + bias[c0 + 2 * j + 1];
-            const float y0 = kExactSilu ? silu_exact(z0) : silu_fast(z0);
-            const float y1 = kExactSilu ? silu_exact(z1) : silu_fast(z1);
-            packed[j] = pack_bf16(y0, y1);
+          for (int j4 = 0; j4 < 8; ++j4) {
+            const float4 hb = *reinterpret_cast<const float4*>(hbias + c0 + 4 * j4);
+            const float hz[4] = {fmaf(__uint_as_float(raw[4 * j4 + 0]), 0.5f, hb.x),
+                                 fmaf(__uint_as_float(raw[4 * j4 + 1]), 0.5f, hb.y),
+                                 fmaf(__uint_as_float(raw[4 * j4 + 2]), 0.5f, hb.z),
+                                 fmaf(__uint_as_float(raw[4 * j4 + 3]), 0.5f, hb.w)};
+            float y[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+              y[i] = kExactSilu ? silu_exact(hz[i] + hz[i]) : silu_half(hz[i]);
+            packed[2 * j4] = pack_bf16(y[0], y[1]);
+            packed[2 * j4 + 1] = pack_bf16(y[2], y[3]);
           }
           if (!last) {
 #pragma unroll
