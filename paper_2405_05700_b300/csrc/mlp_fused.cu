@@ -76,7 +76,10 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 
 __device__ __forceinline__ float silu_exact(float z) { return z / (1.0f + __expf(-z)); }
 
-template <bool kFromPairs, bool kExactSilu>
+// kTrain: rows mode for training -- also writes each layer's BF16
+// pre-activations and activations (the backward pass's inputs) to global
+// memory, row-major [n][256].
+template <bool kFromPairs, bool kExactSilu, bool kTrain = false>
 __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kStages], empty[kStages], acc_full[2], in_ready[2], done;
@@ -272,6 +275,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
               y[i] = kExactSilu ? silu_exact(hz[i] + hz[i]) : silu_half(hz[i]);
             packed[2 * j4] = pack_bf16(y[0], y[1]);
             packed[2 * j4 + 1] = pack_bf16(y[2], y[3]);
+            if (kTrain && valid) {
+              const size_t o = (size_t)row * kHid + c_begin + c0 + 4 * j4;
+              *reinterpret_cast<uint2*>(a.z_out[layer] + o) =
+                  make_uint2(pack_bf16(hz[0] + hz[0], hz[1] + hz[1]),
+                             pack_bf16(hz[2] + hz[2], hz[3] + hz[3]));
+              *reinterpret_cast<uint2*>(a.h_out[layer] + o) =
+                  make_uint2(packed[2 * j4], packed[2 * j4 + 1]);
+            }
           }
           if (!last) {
 #pragma unroll
@@ -330,7 +341,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
           const float lam = a.nph[s] * softplus(z);
           if (a.dom_sum) atomicAdd(a.dom_sum + d, (double)lam);
           if (a.lambda_out) a.lambda_out[(size_t)s * a.n_dom + d] = lam;
-        } else {
+        } else if (!kTrain) {
           a.lambda[row] = a.nph[row] * softplus(z);
         }
       }
@@ -382,13 +393,13 @@ cudaError_t launch_pack_weights(const __nv_bfloat16* const* w, unsigned char* ou
   return cudaGetLastError();
 }
 
-template <bool P, bool E>
+template <bool P, bool E, bool T = false>
 cudaError_t launch_variant(const FusedArgs& a, int g, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(k_mlp_fused<P, E>,
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_fused<P, E, T>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kSmemBytes);
   if (e != cudaSuccess) return e;
-  k_mlp_fused<P, E><<<g, kThreads, kSmemBytes, st>>>(a);
+  k_mlp_fused<P, E, T><<<g, kThreads, kSmemBytes, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -396,6 +407,7 @@ cudaError_t launch_mlp_fused(const FusedArgs& a, bool from_pairs, int grid, cuda
   if (a.n <= 0) return cudaSuccess;
   const int64_t tiles = (a.n + kRows - 1) / kRows;
   const int g = (int)(tiles < grid ? tiles : grid);
+  if (a.z_out[0]) return launch_variant<false, true, true>(a, g, st);  // training forward
   if (from_pairs)
     return a.exact_silu ? launch_variant<true, true>(a, g, st) : launch_variant<true, false>(a, g, st);
   return a.exact_silu ? launch_variant<false, true>(a, g, st) : launch_variant<false, false>(a, g, st);

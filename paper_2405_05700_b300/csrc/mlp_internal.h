@@ -14,7 +14,6 @@ namespace mlp {
 enum {
   kEpiStoreF32 = 0,      // Cf = acc
   kEpiAddF32 = 1,        // Cf += acc
-  kEpiBiasSiluBf16 = 2,  // z = acc + bias; Zb = bf16(z) (if set); Cb = bf16(silu(z))
   kEpiDsiluBf16 = 3,     // Cb = bf16(acc * silu'(Zin))
   kEpiAtomicF32 = 4,     // Cf += acc with atomics (split-K partial sums)
 };
@@ -28,9 +27,7 @@ struct GemmArgs {
   int swap_lbo_sbo;        // layout probe: exchange the descriptor strides
   float* Cf;
   __nv_bfloat16* Cb;
-  __nv_bfloat16* Zb;
   const __nv_bfloat16* Zin;
-  const float* bias;
   int* err;
 };
 
@@ -92,7 +89,11 @@ struct FusedArgs {
   double* dom_sum;               // pairs mode, may be null
   float* lambda_out;             // pairs mode [n_src][n_dom], may be null
   int n_dom;
-  float* lambda;                 // rows mode
+  float* lambda;                 // rows mode (inference)
+  // training forward (rows mode, exact SiLU, no lambda): each layer's BF16
+  // pre-activations and activations [n][256]; null for inference
+  __nv_bfloat16* z_out[kLayers];
+  __nv_bfloat16* h_out[kLayers];
   int* err;
 };
 

@@ -17,8 +17,6 @@ constexpr int kBM = 128;      // rows of A / C per CTA (the MMA's M)
 constexpr int kBK = 64;       // K staged per round
 constexpr uint32_t kWaitTries = 1u << 22;
 
-__device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
-
 __device__ __forceinline__ float silu_grad(float z) {
   const float s = 1.0f / (1.0f + __expf(-z));
   return s * (1.0f + z * (1.0f - s));
@@ -145,10 +143,6 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
           g.Cf[o] = v[j];
         } else if (EPI == kEpiAddF32) {
           g.Cf[o] += v[j];
-        } else if (EPI == kEpiBiasSiluBf16) {
-          const float z = v[j] + g.bias[col];
-          if (g.Zb) g.Zb[o] = __float2bfloat16_rn(z);
-          g.Cb[o] = __float2bfloat16_rn(silu(z));
         } else if (EPI == kEpiDsiluBf16) {
           g.Cb[o] = __float2bfloat16_rn(v[j] * silu_grad(__bfloat162float(g.Zin[o])));
         } else if (EPI == kEpiAtomicF32) {
@@ -181,7 +175,6 @@ cudaError_t launch_gemm(const GemmArgs& g, int epi, cudaStream_t st) {
   switch (epi) {
     PP_GEMM_CASE(kEpiStoreF32)
     PP_GEMM_CASE(kEpiAddF32)
-    PP_GEMM_CASE(kEpiBiasSiluBf16)
     PP_GEMM_CASE(kEpiDsiluBf16)
     PP_GEMM_CASE(kEpiAtomicF32)
     default:

@@ -110,18 +110,43 @@ int refresh_bf16(pp_mlp* m, cudaStream_t st) {
   return PP_OK;
 }
 
-// Hidden layers on n rows of features x0: h (and, when training, z) buffers.
-int forward_layers(pp_mlp* m, const __nv_bfloat16* x0, int n, __nv_bfloat16* const* h,
-                   __nv_bfloat16* const* z, cudaStream_t st) {
-  const __nv_bfloat16* in = x0;
+int ensure_packed(pp_mlp* m, cudaStream_t st) {
+  if (m->packed_version == m->weights_version) return PP_OK;
+  PP_MLP_CUDA(launch_pack_weights(m->wb, m->wpack, st));
+  m->packed_version = m->weights_version;
+  return PP_OK;
+}
+
+FusedArgs fused_args(pp_mlp* m) {
+  FusedArgs a{};
+  a.fg = m->fg;
+  a.wpack = m->wpack;
+  a.exact_silu = m->exact_silu;
+  for (int l = 0; l < kLayers; ++l) a.bias[l] = m->p + off_b(l);
+  a.w5 = m->p + kOffW5;
+  a.b5 = m->p + kOffB5;
+  a.n_dom = m->fg.n_dom;
+  a.err = m->err;
+  return a;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Training forward through the fused kernel: every layer's BF16
+// pre-activations m->z and activations m->h (exact SiLU, as the gradients
+// assume).
+int forward_train(pp_mlp* m, const __nv_bfloat16* x0, int n, cudaStream_t st) {
+  int rc;
+  if ((rc = ensure_packed(m, st))) return rc;
+  FusedArgs a = fused_args(m);
+  a.feat = x0;
+  a.n = n;
+  a.exact_silu = 1;
   for (int l = 0; l < kLayers; ++l) {
-    GemmArgs a = gemm(in, m->wb[l], n, kHid, l == 0 ? kIn : kHid, m->err);
-    a.bias = m->p + off_b(l);
-    a.Cb = h[l];
-    a.Zb = z ? z[l] : nullptr;
-    PP_MLP_CUDA(launch_gemm(a, kEpiBiasSiluBf16, st));
-    in = h[l];
+    a.z_out[l] = m->z[l];
+    a.h_out[l] = m->h[l];
   }
+  PP_MLP_CUDA(launch_mlp_fused(a, false, m->sms, st));
   return PP_OK;
 }
 
@@ -130,7 +155,7 @@ int forward_backward(pp_mlp* m, const __nv_bfloat16* x0, const float* nph, const
                      int n, cudaStream_t st) {
   int rc;
   PP_MLP_CUDA(cudaMemsetAsync(m->g, 0, sizeof(float) * kNParams, st));
-  if ((rc = forward_layers(m, x0, n, m->h, m->z, st))) return rc;
+  if ((rc = forward_train(m, x0, n, st))) return rc;
   PP_MLP_CUDA(launch_head_backward(m->h[3], m->z[3], m->p + kOffW5, m->p + kOffB5, nph, cnt, n,
                                    1.0f / (float)n, m->dza, m->g + kOffW5, m->g + kOffB5, m->loss,
                                    st));
@@ -160,28 +185,6 @@ int forward_backward(pp_mlp* m, const __nv_bfloat16* x0, const float* nph, const
   }
   return PP_OK;
 }
-
-int ensure_packed(pp_mlp* m, cudaStream_t st) {
-  if (m->packed_version == m->weights_version) return PP_OK;
-  PP_MLP_CUDA(launch_pack_weights(m->wb, m->wpack, st));
-  m->packed_version = m->weights_version;
-  return PP_OK;
-}
-
-FusedArgs fused_args(pp_mlp* m) {
-  FusedArgs a{};
-  a.fg = m->fg;
-  a.wpack = m->wpack;
-  a.exact_silu = m->exact_silu;
-  for (int l = 0; l < kLayers; ++l) a.bias[l] = m->p + off_b(l);
-  a.w5 = m->p + kOffW5;
-  a.b5 = m->p + kOffB5;
-  a.n_dom = m->fg.n_dom;
-  a.err = m->err;
-  return a;
-}
-
-bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 int check_batch(pp_mlp* m, int64_t n) {
   if (n < 16 || n > m->max_batch || n % 16)
