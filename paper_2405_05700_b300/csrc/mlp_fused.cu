@@ -357,6 +357,238 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
   if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
+__device__ __forceinline__ float silu_grad(float z) {
+  const float sg = 1.0f / (1.0f + __expf(-z));
+  return sg * (1.0f + z * (1.0f - sg));
+}
+
+// Backward pass of the hidden layers for training, fused like the forward:
+// per 256-row tile, dL/dz of the last hidden layer (from the head) becomes
+// the A operand; three MMA layers against the transposed weights W4^T, W3^T,
+// W2^T give dL/dz of layers 3, 2, 1:
+//   dz_{l-1} = bf16((dz_l . W_l) * silu'(z_{l-1}))
+// each written back into shared memory (the next A operand) and to global
+// memory (for the weight gradients).  Same warp roles, ping-pong and bounded
+// waits as k_mlp_fused; the weight image holds 8 chunks per transposed layer.
+constexpr int kBwdLayers = kLayers - 1;
+constexpr int kBwdChunksPerTile = 2 * kBwdLayers * kChunksPerLayer;
+
+__global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd(BwdArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], acc_full[2], in_ready[2], done;
+  __shared__ uint32_t tslot;
+  __shared__ int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t n_tiles = (a.n + kRows - 1) / kRows;
+  if (warp == 0) tc::tmem_alloc(&tslot, 512);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    for (int h = 0; h < 2; ++h) {
+      tc::mbar_init(&acc_full[h], 1);
+      tc::mbar_init(&in_ready[h], kEpiThreads / 2);
+    }
+    tc::mbar_init(&done, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tslot;
+
+  if (warp == kProducerWarp) {
+    if (lane == 0) {
+      uint32_t it = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        for (int jt = 0; jt < kBwdChunksPerTile; ++jt, ++it) {
+          // job order (layer step j, half); step j's chunk c is 8 j + c
+          const int j = jt / (2 * kChunksPerLayer), c = jt % kChunksPerLayer;
+          const uint32_t s = it % kStages;
+          if (it >= (uint32_t)kStages) {
+            if (!tc::mbar_wait(&empty[s], ((it / kStages) - 1) & 1, kWaitTries) ||
+                *(volatile int*)&abort_flag) {
+              ok = false;
+              break;
+            }
+          }
+          tc::mbar_arrive_expect_tx(&full[s], kChunkBytes);
+          tc::bulk_g2s(smem + kOffRing + s * kChunkBytes,
+                       a.wpack + (size_t)(j * kChunksPerLayer + c) * kChunkBytes, kChunkBytes,
+                       &full[s]);
+        }
+      }
+      if (!ok) {
+        atomicExch(&abort_flag, 1);
+        atomicOr(a.err, 1);
+      }
+      const uint32_t last = it < (uint32_t)kStages ? it : (uint32_t)kStages;
+      for (uint32_t q = 0; q < last; ++q) {
+        const uint32_t i = it - 1 - q;
+        tc::mbar_wait(&full[i % kStages], (i / kStages) & 1, kWaitTries);
+      }
+    }
+  } else if (warp == kMmaWarp) {
+    if (lane == 0) {
+      const uint32_t idesc = tc::idesc_bf16(kHalf, kHid);
+      const uint32_t sh = tc::smem_u32(smem + kOffH);
+      const uint32_t ring = tc::smem_u32(smem + kOffRing);
+      uint32_t it = 0, in_phase[2] = {0u, 0u};
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        for (int job = 0; job < 2 * kBwdLayers && ok; ++job) {
+          const int h = job & 1;
+          if (!tc::mbar_wait(&in_ready[h], in_phase[h] & 1, kWaitTries) ||
+              *(volatile int*)&abort_flag) {
+            ok = false;
+            break;
+          }
+          ++in_phase[h];
+          tc::fence_after_sync();
+          for (int c = 0; c < kChunksPerLayer; ++c, ++it) {
+            const uint32_t s = it % kStages;
+            if (!tc::mbar_wait(&full[s], (it / kStages) & 1, kWaitTries)) {
+              ok = false;
+              break;
+            }
+            tc::fence_after_sync();
+            const uint32_t b0 = ring + s * kChunkBytes;
+#pragma unroll
+            for (int kk = 0; kk < kChunkK / 16; ++kk) {
+              const uint32_t k0 = c * kChunkK + kk * 16;
+              tc::mma_bf16(tmem + h * kHid,
+                           tc::smem_desc(sh + h * kHalfBytes + k0 * 16, 128, kHid * 16),
+                           tc::smem_desc(b0 + kk * 256, 128, kChunkK * 16), idesc,
+                           (c > 0 || kk > 0) ? 1u : 0u);
+            }
+            tc::mma_commit(&empty[s]);
+          }
+          tc::mma_commit(&acc_full[h]);
+        }
+      }
+      if (!ok) {
+        atomicExch(&abort_flag, 1);
+        atomicOr(a.err, 1);
+      }
+      tc::mma_commit(&done);
+      tc::mbar_wait(&done, 0, kWaitTries);
+    }
+  } else {
+    const int q = warp & 3, h = (warp >> 2) & 1, cg = warp >> 3;
+    const int r = q * 32 + lane;
+    const int c_begin = cg * kColsPerWarp;
+    unsigned char* sH = smem + kOffH + h * kHalfBytes;
+    const uint32_t tacc =
+        tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * kHid) + (uint32_t)c_begin;
+    uint32_t acc_phase = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+      const int64_t row = t * kRows + h * kHalf + r;
+      const bool valid = row < a.n;
+      // dL/dz of the last hidden layer: this warp's 128 columns of the row
+      {
+        const __nv_bfloat16* src = a.dz[kBwdLayers] + (size_t)row * kHid + c_begin;
+#pragma unroll 4
+        for (int i = 0; i < kColsPerWarp / 8; ++i) {
+          const uint4 v = valid ? *reinterpret_cast<const uint4*>(src + 8 * i)
+                                : make_uint4(0, 0, 0, 0);
+          *reinterpret_cast<uint4*>(sH + tc::tile_off(r, c_begin + 8 * i, kHid)) = v;
+        }
+        tc::fence_smem_async();
+      }
+      tc::fence_before_sync();
+      tc::mbar_arrive(&in_ready[h]);
+      for (int j = 0; j < kBwdLayers; ++j) {
+        const int lo = kBwdLayers - 1 - j;  // layer whose dz this step produces
+        const bool got = tc::mbar_wait(&acc_full[h], acc_phase & 1, kWaitTries) &&
+                         !*(volatile int*)&abort_flag;
+        if (!__all_sync(0xffffffffu, got)) {
+          ok = false;
+          break;
+        }
+        ++acc_phase;
+        __syncwarp();
+        tc::fence_after_sync();
+        const __nv_bfloat16* zrow = a.z[lo] + (size_t)row * kHid + c_begin;
+        __nv_bfloat16* dzrow = a.dz[lo] + (size_t)row * kHid + c_begin;
+        const bool last = j == kBwdLayers - 1;
+        auto consume = [&](const uint32_t (&raw)[32], int c0) {
+          uint32_t packed[16];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            uint4 zv = make_uint4(0, 0, 0, 0);
+            if (valid) zv = *reinterpret_cast<const uint4*>(zrow + c0 + 8 * i);
+            const uint32_t zw[4] = {zv.x, zv.y, zv.z, zv.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const __nv_bfloat162 z2 = *reinterpret_cast<const __nv_bfloat162*>(&zw[k]);
+              const int e = 8 * i + 2 * k;
+              packed[4 * i + k] =
+                  pack_bf16(__uint_as_float(raw[e]) * silu_grad(__low2float(z2)),
+                            __uint_as_float(raw[e + 1]) * silu_grad(__high2float(z2)));
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const uint4 v = make_uint4(packed[4 * i], packed[4 * i + 1], packed[4 * i + 2],
+                                       packed[4 * i + 3]);
+            if (!last)
+              *reinterpret_cast<uint4*>(sH + tc::tile_off(r, c_begin + c0 + 8 * i, kHid)) = v;
+            if (valid) *reinterpret_cast<uint4*>(dzrow + c0 + 8 * i) = v;
+          }
+        };
+        uint32_t ra[32], rb[32];
+        tc::tmem_ld32_nowait(tacc + 0, ra);
+        tc::tmem_wait_ld(ra);
+        tc::tmem_ld32_nowait(tacc + 32, rb);
+        consume(ra, 0);
+        tc::tmem_wait_ld(rb);
+        tc::tmem_ld32_nowait(tacc + 64, ra);
+        consume(rb, 32);
+        tc::tmem_wait_ld(ra);
+        tc::tmem_ld32_nowait(tacc + 96, rb);
+        consume(ra, 64);
+        tc::tmem_wait_ld(rb);
+        consume(rb, 96);
+        if (!last) {
+          tc::fence_smem_async();
+          tc::fence_before_sync();
+          tc::mbar_arrive(&in_ready[h]);
+        }
+      }
+    }
+    if (!ok) {
+      atomicExch(&abort_flag, 1);
+      atomicOr(a.err, 1);
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+// The transposed hidden weights in the ring's chunk layout, for the backward
+// pass: step j uses W_l^T with l = 3 - j (0-based layers), chunk c holding
+// the outputs 32c .. 32c + 31 of W_l as K: element (in n, out k) of W_l^T at
+// tile_off(n, k - 32c, 32) of its 16 KB block.
+__global__ void k_pack_bwd(const __nv_bfloat16* w2, const __nv_bfloat16* w3,
+                           const __nv_bfloat16* w4, unsigned char* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // one element
+  if (i >= kBwdLayers * kHid * kHid) return;
+  const int j = i / (kHid * kHid);
+  const int rem = i % (kHid * kHid);
+  const int k = rem / kHid, n = rem % kHid;  // W_l[k][n]: output k, input n
+  const __nv_bfloat16* w = j == 0 ? w4 : (j == 1 ? w3 : w2);
+  const int c = k / kChunkK;
+  unsigned char* dst = out + (size_t)(j * kChunksPerLayer + c) * kChunkBytes +
+                       tc::tile_off(n, k - c * kChunkK, kChunkK);
+  *reinterpret_cast<__nv_bfloat16*>(dst) = w[rem];
+}
+
 // The weights in the ring's chunk layout: chunk 0 is W1 ([256][32]), then
 // each hidden layer (BF16 [256 out][256 in]) as 8 chunks of 32 inputs; every
 // chunk is one K-major 16 KB block, staged by one bulk copy.
@@ -400,6 +632,25 @@ cudaError_t launch_variant(const FusedArgs& a, int g, cudaStream_t st) {
                                        (int)kSmemBytes);
   if (e != cudaSuccess) return e;
   k_mlp_fused<P, E, T><<<g, kThreads, kSmemBytes, st>>>(a);
+  return cudaGetLastError();
+}
+
+size_t packed_bwd_bytes() { return (size_t)kBwdLayers * kChunksPerLayer * kChunkBytes; }
+
+cudaError_t launch_pack_bwd(const __nv_bfloat16* const* w, unsigned char* out, cudaStream_t st) {
+  const int n = kBwdLayers * kHid * kHid;
+  k_pack_bwd<<<(n + 255) / 256, 256, 0, st>>>(w[1], w[2], w[3], out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_bwd(const BwdArgs& a, int grid, cudaStream_t st) {
+  if (a.n <= 0) return cudaSuccess;
+  const int64_t tiles = (a.n + kRows - 1) / kRows;
+  const int g = (int)(tiles < grid ? tiles : grid);
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kSmemBytes);
+  if (e != cudaSuccess) return e;
+  k_mlp_bwd<<<g, kThreads, kSmemBytes, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -14,7 +14,6 @@ namespace mlp {
 enum {
   kEpiStoreF32 = 0,      // Cf = acc
   kEpiAddF32 = 1,        // Cf += acc
-  kEpiDsiluBf16 = 3,     // Cb = bf16(acc * silu'(Zin))
   kEpiAtomicF32 = 4,     // Cf += acc with atomics (split-K partial sums)
 };
 
@@ -26,8 +25,6 @@ struct GemmArgs {
   int k_split;             // K ranges run by separate CTAs (grid z); needs kEpiAtomicF32 if > 1
   int swap_lbo_sbo;        // layout probe: exchange the descriptor strides
   float* Cf;
-  __nv_bfloat16* Cb;
-  const __nv_bfloat16* Zin;
   int* err;
 };
 
@@ -102,6 +99,22 @@ cudaError_t launch_pack_weights(const __nv_bfloat16* const* w, unsigned char* ou
                                 cudaStream_t st);
 // grid: the CTA count cap (one CTA per SM runs at a time)
 cudaError_t launch_mlp_fused(const FusedArgs& a, bool from_pairs, int grid, cudaStream_t st);
+
+// Fused backward of the hidden layers (training): from dz[3] (dL/dz of the
+// last hidden layer, BF16 [n][256]) and the forward's pre-activations z[0..2],
+// writes dz[2], dz[1], dz[0].  wpack: the transposed hidden weights packed by
+// launch_pack_bwd.
+struct BwdArgs {
+  int64_t n;
+  const unsigned char* wpack;
+  const __nv_bfloat16* z[kLayers];
+  __nv_bfloat16* dz[kLayers];
+  int* err;
+};
+size_t packed_bwd_bytes();
+// w: the 4 BF16 weight matrices (w[1..3] used)
+cudaError_t launch_pack_bwd(const __nv_bfloat16* const* w, unsigned char* out, cudaStream_t st);
+cudaError_t launch_mlp_bwd(const BwdArgs& a, int grid, cudaStream_t st);
 
 cudaError_t launch_transpose(const __nv_bfloat16* in, int rows, int cols, __nv_bfloat16* out,
                              cudaStream_t st);

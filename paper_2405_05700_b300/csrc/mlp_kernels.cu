@@ -17,11 +17,6 @@ constexpr int kBM = 128;      // rows of A / C per CTA (the MMA's M)
 constexpr int kBK = 64;       // K staged per round
 constexpr uint32_t kWaitTries = 1u << 22;
 
-__device__ __forceinline__ float silu_grad(float z) {
-  const float s = 1.0f / (1.0f + __expf(-z));
-  return s * (1.0f + z * (1.0f - s));
-}
-
 __device__ __forceinline__ uint32_t pow2_cols(int n) {
   return n > 128 ? 256u : (n > 64 ? 128u : (n > 32 ? 64u : 32u));
 }
@@ -143,8 +138,6 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
           g.Cf[o] = v[j];
         } else if (EPI == kEpiAddF32) {
           g.Cf[o] += v[j];
-        } else if (EPI == kEpiDsiluBf16) {
-          g.Cb[o] = __float2bfloat16_rn(v[j] * silu_grad(__bfloat162float(g.Zin[o])));
         } else if (EPI == kEpiAtomicF32) {
           atomicAdd(g.Cf + o, v[j]);
         }
@@ -175,7 +168,6 @@ cudaError_t launch_gemm(const GemmArgs& g, int epi, cudaStream_t st) {
   switch (epi) {
     PP_GEMM_CASE(kEpiStoreF32)
     PP_GEMM_CASE(kEpiAddF32)
-    PP_GEMM_CASE(kEpiDsiluBf16)
     PP_GEMM_CASE(kEpiAtomicF32)
     default:
       return cudaErrorInvalidValue;

@@ -52,18 +52,20 @@ struct pp_mlp {
   // parameters
   float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
   __nv_bfloat16* wb[kLayers] = {};   // BF16 weights of the 4 GEMM layers
-  __nv_bfloat16* wtb[kLayers] = {};  // their transposes (layers 1..3 used)
   int64_t step = 0;
   // training activations [max_batch][256]
   __nv_bfloat16* z[kLayers] = {};
   __nv_bfloat16* h[kLayers] = {};
-  __nv_bfloat16 *dza = nullptr, *dzb = nullptr, *t1 = nullptr, *t2 = nullptr;
+  __nv_bfloat16* dz[kLayers] = {};  // dL/dz of each layer (pre-activation) [max_batch][256]
+  __nv_bfloat16 *t1 = nullptr, *t2 = nullptr;
   double* loss = nullptr;
   int* err = nullptr;
   // inference: hidden weights in the fused kernel's chunk layout (repacked
   // when the weights change), the pair list [max_rows]
   unsigned char* wpack = nullptr;
   int64_t weights_version = 0, packed_version = -1;
+  unsigned char* wpack_bwd = nullptr;  // transposed hidden weights for the backward kernel
+  int64_t packed_bwd_version = -1;
   int exact_silu = 0;
   float2* ice_cum = nullptr;
   int sms = 0;
@@ -100,13 +102,11 @@ GemmArgs gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, int M, int N, int 
   return a;
 }
 
-// BF16 copies and transposes of the weights from the FP32 masters.
+// BF16 copies of the weights from the FP32 masters.
 int refresh_bf16(pp_mlp* m, cudaStream_t st) {
   PP_MLP_CUDA(launch_to_bf16(m->p + kOffW1, (int64_t)kHid * kIn, m->wb[0], st));
-  for (int l = 1; l < kLayers; ++l) {
+  for (int l = 1; l < kLayers; ++l)
     PP_MLP_CUDA(launch_to_bf16(m->p + off_w(l), (int64_t)kHid * kHid, m->wb[l], st));
-    PP_MLP_CUDA(launch_transpose(m->wb[l], kHid, kHid, m->wtb[l], st));
-  }
   return PP_OK;
 }
 
@@ -157,31 +157,34 @@ int forward_backward(pp_mlp* m, const __nv_bfloat16* x0, const float* nph, const
   PP_MLP_CUDA(cudaMemsetAsync(m->g, 0, sizeof(float) * kNParams, st));
   if ((rc = forward_train(m, x0, n, st))) return rc;
   PP_MLP_CUDA(launch_head_backward(m->h[3], m->z[3], m->p + kOffW5, m->p + kOffB5, nph, cnt, n,
-                                   1.0f / (float)n, m->dza, m->g + kOffW5, m->g + kOffB5, m->loss,
-                                   st));
-  __nv_bfloat16* dz = m->dza;     // dL/dz of the current layer (pre-activation)
-  __nv_bfloat16* dzn = m->dzb;
+                                   1.0f / (float)n, m->dz[3], m->g + kOffW5, m->g + kOffB5,
+                                   m->loss, st));
+  // dz_{l-1} = (dz_l . W_l) * silu'(z_{l-1}) for l = 3, 2, 1: one fused kernel
+  if (m->packed_bwd_version != m->weights_version) {
+    PP_MLP_CUDA(launch_pack_bwd(m->wb, m->wpack_bwd, st));
+    m->packed_bwd_version = m->weights_version;
+  }
+  BwdArgs b{};
+  b.n = n;
+  b.wpack = m->wpack_bwd;
+  for (int l = 0; l < kLayers; ++l) {
+    b.z[l] = m->z[l];
+    b.dz[l] = m->dz[l];
+  }
+  b.err = m->err;
+  PP_MLP_CUDA(launch_mlp_bwd(b, m->sms, st));
+  // dW_l = dz_l^T . x_l (split over the batch, summed with atomics), db_l = sum dz_l
   const int ks = n >= 8192 ? 32 : (n >= 1024 ? 8 : 1);
   for (int l = kLayers - 1; l >= 0; --l) {
     const int in_w = l == 0 ? kIn : kHid;
     const __nv_bfloat16* x = l == 0 ? x0 : m->h[l - 1];
-    // dW_l = dz^T . x  (split over the batch, summed with atomics)
-    PP_MLP_CUDA(launch_transpose(dz, n, kHid, m->t1, st));
+    PP_MLP_CUDA(launch_transpose(m->dz[l], n, kHid, m->t1, st));
     PP_MLP_CUDA(launch_transpose(x, n, in_w, m->t2, st));
     GemmArgs a = gemm(m->t1, m->t2, kHid, in_w, n, m->err);
     a.k_split = ks;
     a.Cf = m->g + off_w(l);
     PP_MLP_CUDA(launch_gemm(a, kEpiAtomicF32, st));
-    PP_MLP_CUDA(launch_colsum(dz, n, kHid, m->g + off_b(l), st));
-    if (l == 0) break;
-    // dz_{l-1} = (dz . W_l) * silu'(z_{l-1})
-    GemmArgs b = gemm(dz, m->wtb[l], n, kHid, kHid, m->err);
-    b.Zin = m->z[l - 1];
-    b.Cb = dzn;
-    PP_MLP_CUDA(launch_gemm(b, kEpiDsiluBf16, st));
-    __nv_bfloat16* t = dz;
-    dz = dzn;
-    dzn = t;
+    PP_MLP_CUDA(launch_colsum(m->dz[l], n, kHid, m->g + off_b(l), st));
   }
   return PP_OK;
 }
@@ -241,21 +244,18 @@ int pp_mlp_create(pp_ctx* ctx, int32_t max_batch, int64_t max_rows, pp_mlp** out
   PP_A(dalloc(&m->m, kNParams));
   PP_A(dalloc(&m->v, kNParams));
   PP_A(dalloc(&m->wb[0], H * kIn));
-  for (int l = 1; l < kLayers; ++l) {
-    PP_A(dalloc(&m->wb[l], H * H));
-    PP_A(dalloc(&m->wtb[l], H * H));
-  }
+  for (int l = 1; l < kLayers; ++l) PP_A(dalloc(&m->wb[l], H * H));
   for (int l = 0; l < kLayers; ++l) {
     PP_A(dalloc(&m->z[l], B * H));
     PP_A(dalloc(&m->h[l], B * H));
+    PP_A(dalloc(&m->dz[l], B * H));
   }
-  PP_A(dalloc(&m->dza, B * H));
-  PP_A(dalloc(&m->dzb, B * H));
   PP_A(dalloc(&m->t1, B * H));
   PP_A(dalloc(&m->t2, B * H));
   PP_A(dalloc(&m->loss, 1));
   PP_A(dalloc(&m->err, 64));
   PP_A(dalloc(&m->wpack, packed_weight_bytes()));
+  PP_A(dalloc(&m->wpack_bwd, packed_bwd_bytes()));
   PP_A(dalloc(&m->ice_cum, (size_t)m->fg.L));
   m->fg.cum = m->ice_cum;
   PP_A(launch_ice_cum(m->fg, m->ice_cum, 0));
@@ -281,14 +281,14 @@ int pp_mlp_destroy(pp_mlp* m) {
   if (!m) return PP_OK;
   cudaSetDevice(m->view.device);
   cudaDeviceSynchronize();
-  void* bufs[] = {m->p,    m->g,   m->m,    m->v,  m->dza,   m->dzb, m->t1,
-                  m->t2,   m->loss, m->err, m->wpack, m->ps, m->pd,  m->count, m->ice_cum};
+  void* bufs[] = {m->p,   m->g,     m->m,         m->v,  m->t1, m->t2,    m->loss, m->err,
+                  m->wpack, m->wpack_bwd, m->ps, m->pd, m->count, m->ice_cum};
   for (void* b : bufs) cudaFree(b);
   for (int l = 0; l < kLayers; ++l) {
     cudaFree(m->wb[l]);
-    cudaFree(m->wtb[l]);
     cudaFree(m->z[l]);
     cudaFree(m->h[l]);
+    cudaFree(m->dz[l]);
   }
   if (m->ctx) ppk::attach_server(m->ctx, -1);
   delete m;
@@ -390,7 +390,6 @@ int pp_mlp_train_step(pp_mlp* m, const uint16_t* d_feat, const float* d_nph, con
     const int64_t ob = off_b(l);
     PP_MLP_CUDA(launch_adam(m->p + ob, m->g + ob, m->m + ob, m->v + ob, kHid, lr, b1, b2, 1e-8f,
                             bc1, bc2, nullptr, st));
-    PP_MLP_CUDA(launch_transpose(m->wb[l], kHid, kHid, m->wtb[l], st));
   }
   PP_MLP_CUDA(launch_adam(m->p + kOffW5, m->g + kOffW5, m->m + kOffW5, m->v + kOffW5, kHid + 1,
                           lr, b1, b2, 1e-8f, bc1, bc2, nullptr, st));
