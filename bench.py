@@ -59,7 +59,7 @@ LANES_PER_SM = 128        # 4 schedulers x 32 lanes issue one instruction per cl
 # launch of the 1000-event step (captured on its first 200 events, scaled by sources),
 # and one 4 194 304-row launch of the fused surrogate kernel.
 NCU_TRAFFIC_BYTES = 186e6
-SUR_NCU_TRAFFIC_BYTES = 301.6e6
+SUR_NCU_TRAFFIC_BYTES = 301.0e6
 
 
 def parse():

@@ -44,7 +44,7 @@ struct pp_ctx {
   // scratch
   DevBuf off, chunk, aux, bsum, meta, work, err, stats;
   // staging for host entry points
-  DevBuf s_src, s_begin, s_ids, s_hits, s_counts, s_misc1, s_misc2, s_misc3, s_misc4;
+  DevBuf s_src, s_begin, s_ids, s_hits, s_counts, s_misc1, s_misc2, s_misc3, s_misc4, s_bad;
   size_t smem_limit_set = 0;
 
   int block_threads = 256;
@@ -141,6 +141,25 @@ int check_sources(pp_ctx* ctx, const pp_source* src, int64_t n) {
       return fail(ctx, PP_EINVAL, "source " + std::to_string(i) +
                                       " has a non-finite field, a zero direction, a negative "
                                       "length or an unknown type");
+  return PP_OK;
+}
+
+// The same check on sources already copied to the device (one kernel and a
+// 8-byte read-back instead of a host loop over every source).
+int check_sources_device(pp_ctx* ctx, const pp_source* d_src, int64_t n, cudaStream_t st) {
+  if (n <= 0) return PP_OK;
+  int rc;
+  if ((rc = ensure(ctx, ctx->s_bad, sizeof(unsigned long long)))) return rc;
+  auto* bad = static_cast<unsigned long long*>(ctx->s_bad.p);
+  PP_CUDA(cudaMemsetAsync(bad, 0xFF, sizeof(unsigned long long), st));
+  PP_CUDA(launch_check_sources(d_src, n, bad, st));
+  unsigned long long first = 0;
+  PP_CUDA(cudaMemcpyAsync(&first, bad, sizeof(first), cudaMemcpyDeviceToHost, st));
+  PP_CUDA(cudaStreamSynchronize(st));
+  if (first != ~0ull)
+    return fail(ctx, PP_EINVAL, "source " + std::to_string(first) +
+                                    " has a non-finite field, a zero direction, a negative "
+                                    "length or an unknown type");
   return PP_OK;
 }
 
@@ -461,7 +480,7 @@ int batch_host(pp_ctx* ctx, bool plain, int32_t n_events, const uint64_t* ids,
     if (begin[e + 1] < begin[e]) return fail(ctx, PP_EINVAL, "src_begin decreases");
   const int64_t n_src = begin[n_events];
   if (n_src > 0 && !src) return fail(ctx, PP_EINVAL, "null source pointer");
-  if ((rc = check_sources(ctx, src, n_src))) return rc;
+  if (n_src > kMaxSources) return fail(ctx, PP_EINVAL, "more than 33554432 sources per call");
   const int n_dom = ctx->geom.n_dom;
   cudaStream_t st = ctx->stream;
   if ((rc = ensure(ctx, ctx->s_src, sizeof(pp_source) * (size_t)std::max<int64_t>(n_src, 1)))) return rc;
@@ -476,6 +495,7 @@ int batch_host(pp_ctx* ctx, bool plain, int32_t n_events, const uint64_t* ids,
   uint64_t* d_hits = static_cast<uint64_t*>(ctx->s_hits.p);
   uint64_t* d_counts = static_cast<uint64_t*>(ctx->s_counts.p);
   const pp_source* d_src = static_cast<const pp_source*>(ctx->s_src.p);
+  if ((rc = check_sources_device(ctx, d_src, n_src, st))) return rc;
   if (plain) {
     std::vector<uint64_t> ph(n_events, 0);
     for (int32_t e = 0; e < n_events; ++e)
@@ -609,7 +629,7 @@ int pp_destroy(pp_ctx* ctx) {
                     &ctx->chunk, &ctx->aux, &ctx->bsum, &ctx->meta, &ctx->work, &ctx->err,
                     &ctx->stats,
                     &ctx->s_src, &ctx->s_begin, &ctx->s_ids, &ctx->s_hits, &ctx->s_counts,
-                    &ctx->s_misc1, &ctx->s_misc2, &ctx->s_misc3, &ctx->s_misc4};
+                    &ctx->s_misc1, &ctx->s_misc2, &ctx->s_misc3, &ctx->s_misc4, &ctx->s_bad};
   drop_graphs(ctx);
   for (DevBuf* b : bufs) release(*b);
   for (auto& pr : ctx->pending) {

@@ -432,7 +432,7 @@ def test_edge_cases(tiny, pp):
     assert np.array_equal(h1, h[1]) and np.array_equal(c1, c[1])
     h0, c0 = tiny.propagate(5, W.make_sources(0))
     assert h0.sum() == 0 and c0.sum() == 0
-    # malformed input is refused on the host
+    # malformed input is refused before any propagation (PP_EINVAL)
     bad = W.point_source(np.nan, 0, 0, 10)
     with pytest.raises(pp.PPError) as ei:
         tiny.propagate(0, bad)
