@@ -52,9 +52,6 @@ OPS_PER_BIRTH = 180       # Philox block, 4 uniforms, source lookup, point, dire
                           # -ln u, starting layer
 LANES_PER_SM = 128        # 4 schedulers x 32 lanes issue one instruction per clock
 
-# DRAM bytes per launch of the persistent kernel from the committed ncu
-# summary of this workload (profiles/propagate_persistent_full.md); None until
-# a capture of the current kernel exists.
 # DRAM bytes per launch from ncu captures of the current kernels: the propagation
 # launch of the 1000-event step (captured on its first 200 events, scaled by sources),
 # and one 4 194 304-row launch of the fused surrogate kernel.
@@ -93,6 +90,23 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(x: float, device) -> float:
+    """The largest x over the ranks of the process group (x itself when there
+    is no group): the whole job is as slow as its slowest replica."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(world: int, photons_per_rank: int, steps: int, total_ms: float) -> float:
+    """Whole-job photons/s: every rank's photons over the slowest rank's time."""
+    return world * photons_per_rank * steps / (total_ms * 1e-3)
 
 
 def replica_batch(rank: int, n_events: int = 1000) -> W.Batch:
@@ -409,11 +423,7 @@ def run_ours(args):
     kern_ms, n_timed, _ = pp.pp_get_kernel_time(ctx)
     pp.pp_set_kernel_timing(ctx, False)
     steps_n, cross_n, births_n, slow_n = pp.pp_get_path_stats(ctx)
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dev)
 
     # validity: exact conservation on the last step
     hits = d_hits.cpu().numpy().astype(np.int64)
@@ -603,7 +613,7 @@ def run_ours(args):
            + OPS_PER_BIRTH * births_per_launch)
     kern_avg_ms = kern_ms / max(1, n_timed)
     achieved = ops / (kern_avg_ms * 1e-3) / 1e9
-    value = world * photons * args.steps / (total_ms * 1e-3)
+    value = aggregate_value(world, photons, args.steps, total_ms)
     plain_value = photons / (statistics.mean(plain_ms) * 1e-3) if plain_ms else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
