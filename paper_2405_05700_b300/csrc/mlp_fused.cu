@@ -48,6 +48,8 @@ constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kThreads = kEpiThreads + 64;
 constexpr int kProducerWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1;
 constexpr int kColsPerWarp = kHid / 2;
+// 18 warps: two of the four schedulers hold 5 warps, whose registers come from
+// that scheduler's 16K, so a thread gets at most 96 registers
 constexpr uint32_t kWaitTries = 1u << 22;
 
 // dynamic shared memory
@@ -77,8 +79,9 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 __device__ __forceinline__ float silu_exact(float z) { return z / (1.0f + __expf(-z)); }
 
 // kTrain: rows mode for training -- also writes each layer's BF16
-// pre-activations and activations (the backward pass's inputs) to global
-// memory, row-major [n][256].
+// pre-activations (row-major [n][256]) and activations (the first three
+// layers transposed, [256][n], as the weight-gradient GEMMs read them; the
+// last row-major, for the head) to global memory.
 template <bool kFromPairs, bool kExactSilu, bool kTrain = false>
 __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -262,6 +265,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
         // 32 columns: bias, SiLU, BF16; into shared memory (or the head)
         auto consume = [&](const uint32_t (&raw)[32], int c0) {
           uint32_t packed[16];
+          uint32_t zpk[4];
 #pragma unroll
           for (int j4 = 0; j4 < 8; ++j4) {
             const float4 hb = *reinterpret_cast<const float4*>(hbias + c0 + 4 * j4);
@@ -275,13 +279,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
               y[i] = kExactSilu ? silu_exact(hz[i] + hz[i]) : silu_half(hz[i]);
             packed[2 * j4] = pack_bf16(y[0], y[1]);
             packed[2 * j4 + 1] = pack_bf16(y[2], y[3]);
-            if (kTrain && valid) {
-              const size_t o = (size_t)row * kHid + c_begin + c0 + 4 * j4;
-              *reinterpret_cast<uint2*>(a.z_out[layer] + o) =
-                  make_uint2(pack_bf16(hz[0] + hz[0], hz[1] + hz[1]),
-                             pack_bf16(hz[2] + hz[2], hz[3] + hz[3]));
-              *reinterpret_cast<uint2*>(a.h_out[layer] + o) =
-                  make_uint2(packed[2 * j4], packed[2 * j4 + 1]);
+            if (kTrain) {
+              zpk[2 * (j4 & 1)] = pack_bf16(hz[0] + hz[0], hz[1] + hz[1]);
+              zpk[2 * (j4 & 1) + 1] = pack_bf16(hz[2] + hz[2], hz[3] + hz[3]);
+              if ((j4 & 1) && valid) {
+                const size_t o = (size_t)row * kHid + c_begin + c0 + 4 * (j4 - 1);
+                *reinterpret_cast<uint4*>(a.z_out[layer] + o) =
+                    make_uint4(zpk[0], zpk[1], zpk[2], zpk[3]);
+                if (last)
+                  *reinterpret_cast<uint4*>(a.h_out[layer] + o) = make_uint4(
+                      packed[2 * j4 - 2], packed[2 * j4 - 1], packed[2 * j4], packed[2 * j4 + 1]);
+              }
+            }
+          }
+          if (kTrain && !last && valid) {
+            // activations transposed ([256][n]): a warp stores 32 consecutive rows of a column
+            __nv_bfloat16* ht = a.h_out[layer] + (size_t)(c_begin + c0) * a.n + row;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(&packed[j]);
+              ht[(size_t)(2 * j) * a.n] = __low2bfloat16(v);
+              ht[(size_t)(2 * j + 1) * a.n] = __high2bfloat16(v);
             }
           }
           if (!last) {
@@ -367,8 +385,8 @@ __device__ __forceinline__ float silu_grad(float z) {
 // the A operand; three MMA layers against the transposed weights W4^T, W3^T,
 // W2^T give dL/dz of layers 3, 2, 1:
 //   dz_{l-1} = bf16((dz_l . W_l) * silu'(z_{l-1}))
-// each written back into shared memory (the next A operand) and to global
-// memory (for the weight gradients).  Same warp roles, ping-pong and bounded
+// each written back into shared memory (the next A operand) and, transposed
+// ([256][n], the weight-gradient GEMM's operand), to global memory.  Same warp roles, ping-pong and bounded
 // waits as k_mlp_fused; the weight image holds 8 chunks per transposed layer.
 constexpr int kBwdLayers = kLayers - 1;
 constexpr int kBwdChunksPerTile = 2 * kBwdLayers * kChunksPerLayer;
@@ -513,7 +531,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd(BwdArgs a) {
         __syncwarp();
         tc::fence_after_sync();
         const __nv_bfloat16* zrow = a.z[lo] + (size_t)row * kHid + c_begin;
-        __nv_bfloat16* dzrow = a.dz[lo] + (size_t)row * kHid + c_begin;
+        __nv_bfloat16* dzt = a.dz[lo];
         const bool last = j == kBwdLayers - 1;
         auto consume = [&](const uint32_t (&raw)[32], int c0) {
           uint32_t packed[16];
@@ -531,13 +549,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd(BwdArgs a) {
                             __uint_as_float(raw[e + 1]) * silu_grad(__high2float(z2)));
             }
           }
+          if (!last) {
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const uint4 v = make_uint4(packed[4 * i], packed[4 * i + 1], packed[4 * i + 2],
-                                       packed[4 * i + 3]);
-            if (!last)
-              *reinterpret_cast<uint4*>(sH + tc::tile_off(r, c_begin + c0 + 8 * i, kHid)) = v;
-            if (valid) *reinterpret_cast<uint4*>(dzrow + c0 + 8 * i) = v;
+            for (int i = 0; i < 4; ++i)
+              *reinterpret_cast<uint4*>(sH + tc::tile_off(r, c_begin + c0 + 8 * i, kHid)) =
+                  make_uint4(packed[4 * i], packed[4 * i + 1], packed[4 * i + 2],
+                             packed[4 * i + 3]);
+          }
+          if (valid) {
+            // dL/dz transposed ([256][n]): a warp stores 32 consecutive rows of a column
+            __nv_bfloat16* dt = dzt + (size_t)(c_begin + c0) * a.n + row;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(&packed[j]);
+              dt[(size_t)(2 * j) * a.n] = __low2bfloat16(v);
+              dt[(size_t)(2 * j + 1) * a.n] = __high2bfloat16(v);
+            }
           }
         };
         uint32_t ra[32], rb[32];

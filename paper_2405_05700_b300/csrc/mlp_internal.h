@@ -88,7 +88,8 @@ struct FusedArgs {
   int n_dom;
   float* lambda;                 // rows mode (inference)
   // training forward (rows mode, exact SiLU, no lambda): each layer's BF16
-  // pre-activations and activations [n][256]; null for inference
+  // pre-activations [n][256] and activations (layers 0-2 transposed [256][n],
+  // layer 3 [n][256]); null for inference
   __nv_bfloat16* z_out[kLayers];
   __nv_bfloat16* h_out[kLayers];
   int* err;
@@ -101,9 +102,9 @@ cudaError_t launch_pack_weights(const __nv_bfloat16* const* w, unsigned char* ou
 cudaError_t launch_mlp_fused(const FusedArgs& a, bool from_pairs, int grid, cudaStream_t st);
 
 // Fused backward of the hidden layers (training): from dz[3] (dL/dz of the
-// last hidden layer, BF16 [n][256]) and the forward's pre-activations z[0..2],
-// writes dz[2], dz[1], dz[0].  wpack: the transposed hidden weights packed by
-// launch_pack_bwd.
+// last hidden layer, BF16 [n][256]) and the forward's pre-activations z[0..2]
+// ([n][256]), writes dz[2], dz[1], dz[0] transposed ([256][n]).  wpack: the
+// transposed hidden weights packed by launch_pack_bwd.
 struct BwdArgs {
   int64_t n;
   const unsigned char* wpack;
@@ -118,6 +119,9 @@ cudaError_t launch_mlp_bwd(const BwdArgs& a, int grid, cudaStream_t st);
 
 cudaError_t launch_transpose(const __nv_bfloat16* in, int rows, int cols, __nv_bfloat16* out,
                              cudaStream_t st);
+// out[r] = sum_c in[r][c] (FP32) for a BF16 matrix [rows][cols]
+cudaError_t launch_rowsum(const __nv_bfloat16* in, int rows, int cols, float* out,
+                          cudaStream_t st);
 // out[c] = sum_r in[r][c] (FP32) for a BF16 matrix
 cudaError_t launch_colsum(const __nv_bfloat16* in, int rows, int cols, float* out,
                           cudaStream_t st);

@@ -321,6 +321,31 @@ __global__ void k_transpose(const __nv_bfloat16* in, int rows, int cols, __nv_bf
   }
 }
 
+__global__ void __launch_bounds__(256) k_rowsum(const __nv_bfloat16* in, int cols, float* out) {
+  __shared__ float part[8];
+  const __nv_bfloat16* r = in + (size_t)blockIdx.x * cols;
+  float acc = 0.0f;
+  for (int c = threadIdx.x * 8; c < cols; c += blockDim.x * 8) {
+    if (c + 8 <= cols) {
+      const uint4 v = *reinterpret_cast<const uint4*>(r + c);
+      const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&v);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc += __bfloat162float(e[j]);
+    } else {
+      for (int j = c; j < cols; ++j) acc += __bfloat162float(r[j]);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.0f;
+    for (int w = 0; w < 8; ++w) t += part[w];
+    out[blockIdx.x] += t;
+  }
+}
+
 __global__ void k_colsum(const __nv_bfloat16* in, int rows, int cols, float* out) {
   const int c = blockIdx.y * blockDim.x + threadIdx.x;
   if (c >= cols) return;
@@ -390,6 +415,13 @@ cudaError_t launch_transpose(const __nv_bfloat16* in, int rows, int cols, __nv_b
                              cudaStream_t st) {
   const dim3 grid(blocks_for(cols, 32), blocks_for(rows, 32));
   k_transpose<<<grid, dim3(32, 8), 0, st>>>(in, rows, cols, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rowsum(const __nv_bfloat16* in, int rows, int cols, float* out,
+                          cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  k_rowsum<<<rows, 256, 0, st>>>(in, cols, out);
   return cudaGetLastError();
 }
 

@@ -173,18 +173,26 @@ int forward_backward(pp_mlp* m, const __nv_bfloat16* x0, const float* nph, const
   }
   b.err = m->err;
   PP_MLP_CUDA(launch_mlp_bwd(b, m->sms, st));
-  // dW_l = dz_l^T . x_l (split over the batch, summed with atomics), db_l = sum dz_l
-  const int ks = n >= 8192 ? 32 : (n >= 1024 ? 8 : 1);
+  // dW_l = dz_l^T . x_l (split over the batch, summed with atomics), db_l = sum dz_l.
+  // The fused kernels left dz_0..2 and the activations h_0..2 transposed
+  // ([256][n]); dz_3 (row-major, from the head) and the features are transposed here.
+  const int ks = n >= 32768 ? 128 : (n >= 8192 ? 32 : (n >= 1024 ? 8 : 1));
   for (int l = kLayers - 1; l >= 0; --l) {
     const int in_w = l == 0 ? kIn : kHid;
-    const __nv_bfloat16* x = l == 0 ? x0 : m->h[l - 1];
-    PP_MLP_CUDA(launch_transpose(m->dz[l], n, kHid, m->t1, st));
-    PP_MLP_CUDA(launch_transpose(x, n, in_w, m->t2, st));
-    GemmArgs a = gemm(m->t1, m->t2, kHid, in_w, n, m->err);
+    const __nv_bfloat16* dzt = m->dz[l];
+    if (l == kLayers - 1) {
+      PP_MLP_CUDA(launch_transpose(m->dz[l], n, kHid, m->t1, st));
+      dzt = m->t1;
+      PP_MLP_CUDA(launch_colsum(m->dz[l], n, kHid, m->g + off_b(l), st));
+    } else {
+      PP_MLP_CUDA(launch_rowsum(dzt, kHid, n, m->g + off_b(l), st));
+    }
+    const __nv_bfloat16* xt = l > 0 ? m->h[l - 1] : m->t2;
+    if (l == 0) PP_MLP_CUDA(launch_transpose(x0, n, kIn, m->t2, st));
+    GemmArgs a = gemm(dzt, xt, kHid, in_w, n, m->err);
     a.k_split = ks;
     a.Cf = m->g + off_w(l);
     PP_MLP_CUDA(launch_gemm(a, kEpiAtomicF32, st));
-    PP_MLP_CUDA(launch_colsum(m->dz[l], n, kHid, m->g + off_b(l), st));
   }
   return PP_OK;
 }
