@@ -31,6 +31,7 @@ struct DevBuf {
 struct pp_ctx {
   pp_config cfg{};
   cudaStream_t stream = nullptr;
+  cudaStream_t copy_stream = nullptr;  // host path: uploads and downloads beside the kernels
   bool own_stream = false;
   int sm_count = 0;
   std::mutex mu;
@@ -152,7 +153,7 @@ int check_sources_device(pp_ctx* ctx, const pp_source* d_src, int64_t n, cudaStr
   if ((rc = ensure(ctx, ctx->s_bad, sizeof(unsigned long long)))) return rc;
   auto* bad = static_cast<unsigned long long*>(ctx->s_bad.p);
   PP_CUDA(cudaMemsetAsync(bad, 0xFF, sizeof(unsigned long long), st));
-  PP_CUDA(launch_check_sources(d_src, n, bad, st));
+  PP_CUDA(launch_check_sources(d_src, n, 0, bad, st));
   unsigned long long first = 0;
   PP_CUDA(cudaMemcpyAsync(&first, bad, sizeof(first), cudaMemcpyDeviceToHost, st));
   PP_CUDA(cudaStreamSynchronize(st));
@@ -467,6 +468,107 @@ int sync_and_check(pp_ctx* ctx, cudaStream_t st) {
   return PP_OK;
 }
 
+// Host batch, batched path, large inputs: the events are cut into 2 chunks
+// of about equal source counts; a copy stream uploads every chunk and
+// downloads each chunk's results once its propagation (on the context's
+// stream) is done, so transfers overlap the kernels.  The sources are
+// checked on the device; a malformed one fails the call with PP_EINVAL after
+// the work (the kernels skip malformed sources).
+int batch_host_pipelined(pp_ctx* ctx, int32_t n_events, const uint64_t* ids, const int64_t* begin,
+                         const pp_source* src, uint64_t* hits, uint64_t* counts) {
+  int rc;
+  const int64_t n_src = begin[n_events];
+  const int n_dom = ctx->geom.n_dom;
+  cudaStream_t st = ctx->stream;
+  if (!ctx->copy_stream) PP_CUDA(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+  cudaStream_t cs = ctx->copy_stream;
+  // chunks: event ranges of about n_src / kChunks sources each
+  std::vector<int32_t> cut{0};
+  constexpr int kChunks = 2;
+  for (int k = 1; k < kChunks; ++k) {
+    const int64_t target = n_src * k / kChunks;
+    int32_t e = cut.back();
+    while (e < n_events && begin[e] < target) ++e;
+    if (e > cut.back() && e < n_events) cut.push_back(e);
+  }
+  cut.push_back(n_events);
+  const int nc = (int)cut.size() - 1;
+  if ((rc = ensure(ctx, ctx->s_src, sizeof(pp_source) * (size_t)std::max<int64_t>(n_src, 1)))) return rc;
+  if ((rc = ensure(ctx, ctx->s_begin, sizeof(int64_t) * (size_t)(n_events + nc)))) return rc;
+  if ((rc = ensure(ctx, ctx->s_ids, sizeof(uint64_t) * (size_t)n_events))) return rc;
+  if ((rc = ensure(ctx, ctx->s_hits, sizeof(uint64_t) * (size_t)n_events * std::max(n_dom, 1)))) return rc;
+  if ((rc = ensure(ctx, ctx->s_counts, sizeof(uint64_t) * 4 * (size_t)n_events))) return rc;
+  if ((rc = ensure(ctx, ctx->s_bad, sizeof(unsigned long long)))) return rc;
+  auto* bad = static_cast<unsigned long long*>(ctx->s_bad.p);
+  auto* d_src = static_cast<pp_source*>(ctx->s_src.p);
+  auto* d_begin = static_cast<int64_t*>(ctx->s_begin.p);
+  auto* d_ids = static_cast<uint64_t*>(ctx->s_ids.p);
+  auto* d_hits = static_cast<uint64_t*>(ctx->s_hits.p);
+  auto* d_counts = static_cast<uint64_t*>(ctx->s_counts.p);
+  // each chunk's source offsets relative to its first source (kept until the end)
+  std::vector<int64_t> rel((size_t)(n_events + nc));
+  std::vector<cudaEvent_t> up(nc, nullptr), done(nc, nullptr);
+  auto release = [&]() {
+    for (auto& e : up) if (e) cudaEventDestroy(e);
+    for (auto& e : done) if (e) cudaEventDestroy(e);
+  };
+  auto step = [&]() -> int {
+    PP_CUDA(cudaMemsetAsync(bad, 0xFF, sizeof(unsigned long long), st));
+    for (int k = 0; k < nc; ++k) {
+      const int32_t e0 = cut[k], e1 = cut[k + 1];
+      const int64_t s0 = begin[e0], s1 = begin[e1];
+      int64_t* rk = rel.data() + e0 + k;
+      for (int32_t e = e0; e <= e1; ++e) rk[e - e0] = begin[e] - s0;
+      PP_CUDA(cudaEventCreateWithFlags(&up[k], cudaEventDisableTiming));
+      PP_CUDA(cudaEventCreateWithFlags(&done[k], cudaEventDisableTiming));
+      if (s1 > s0)
+        PP_CUDA(cudaMemcpyAsync(d_src + s0, src + s0, sizeof(pp_source) * (size_t)(s1 - s0),
+                                cudaMemcpyHostToDevice, cs));
+      PP_CUDA(cudaMemcpyAsync(d_begin + e0 + k, rk, sizeof(int64_t) * (size_t)(e1 - e0 + 1),
+                              cudaMemcpyHostToDevice, cs));
+      PP_CUDA(cudaMemcpyAsync(d_ids + e0, ids + e0, sizeof(uint64_t) * (size_t)(e1 - e0),
+                              cudaMemcpyHostToDevice, cs));
+      PP_CUDA(cudaEventRecord(up[k], cs));
+    }
+    for (int k = 0; k < nc; ++k) {
+      const int32_t e0 = cut[k], e1 = cut[k + 1];
+      const int64_t s0 = begin[e0], s1 = begin[e1];
+      PP_CUDA(cudaStreamWaitEvent(st, up[k], 0));
+      PP_CUDA(launch_check_sources(d_src + s0, s1 - s0, s0, bad, st));
+      int r = batch_async(ctx, e1 - e0, d_ids + e0, d_begin + e0 + k, d_src + s0, s1 - s0,
+                          d_hits + (size_t)e0 * n_dom, d_counts + (size_t)e0 * 4, st);
+      if (r) return r;
+      PP_CUDA(cudaEventRecord(done[k], st));
+      PP_CUDA(cudaStreamWaitEvent(cs, done[k], 0));
+      if (n_dom)
+        PP_CUDA(cudaMemcpyAsync(hits + (size_t)e0 * n_dom, d_hits + (size_t)e0 * n_dom,
+                                sizeof(uint64_t) * (size_t)(e1 - e0) * n_dom,
+                                cudaMemcpyDeviceToHost, cs));
+      PP_CUDA(cudaMemcpyAsync(counts + (size_t)e0 * 4, d_counts + (size_t)e0 * 4,
+                              sizeof(uint64_t) * 4 * (size_t)(e1 - e0), cudaMemcpyDeviceToHost, cs));
+    }
+    PP_CUDA(cudaStreamSynchronize(cs));
+    return PP_OK;
+  };
+  rc = step();
+  release();
+  if (rc) {
+    cudaStreamSynchronize(cs);
+    cudaStreamSynchronize(st);
+    return rc;
+  }
+  unsigned long long first = 0;
+  PP_CUDA(cudaMemcpy(&first, bad, sizeof(first), cudaMemcpyDeviceToHost));
+  if (first != ~0ull) {
+    PP_CUDA(cudaStreamSynchronize(st));
+    PP_CUDA(cudaMemset(ctx->err.p, 0, sizeof(int)));  // the kernels' flag for the same sources
+    return fail(ctx, PP_EINVAL, "source " + std::to_string(first) +
+                                    " has a non-finite field, a zero direction, a negative "
+                                    "length or an unknown type");
+  }
+  return sync_and_check(ctx, st);
+}
+
 // Host batch: stage inputs, run the given path, copy results back.
 int batch_host(pp_ctx* ctx, bool plain, int32_t n_events, const uint64_t* ids,
                const int64_t* begin, const pp_source* src, uint64_t* hits, uint64_t* counts) {
@@ -481,6 +583,8 @@ int batch_host(pp_ctx* ctx, bool plain, int32_t n_events, const uint64_t* ids,
   const int64_t n_src = begin[n_events];
   if (n_src > 0 && !src) return fail(ctx, PP_EINVAL, "null source pointer");
   if (n_src > kMaxSources) return fail(ctx, PP_EINVAL, "more than 33554432 sources per call");
+  if (!plain && n_src >= (1 << 18) && n_events >= 4)
+    return batch_host_pipelined(ctx, n_events, ids, begin, src, hits, counts);
   const int n_dom = ctx->geom.n_dom;
   cudaStream_t st = ctx->stream;
   if ((rc = ensure(ctx, ctx->s_src, sizeof(pp_source) * (size_t)std::max<int64_t>(n_src, 1)))) return rc;
@@ -638,6 +742,7 @@ int pp_destroy(pp_ctx* ctx) {
   }
   for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
   delete ctx;
   return PP_OK;
 }

@@ -150,9 +150,9 @@ cudaError_t launch_trace(const IceDev& ice, const GeomDev& geom, const WorkDev& 
                          int* outcome, int64_t* n_steps, float* birth, float* trace,
                          size_t smem, cudaStream_t st);
 
-// *first_bad = min(*first_bad, index of each malformed source)
-cudaError_t launch_check_sources(const pp_source* src, int64_t n, unsigned long long* first_bad,
-                                 cudaStream_t st);
+// *first_bad = min(*first_bad, base + index of each malformed source)
+cudaError_t launch_check_sources(const pp_source* src, int64_t n, int64_t base,
+                                 unsigned long long* first_bad, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n,
                           cudaStream_t st);
 

@@ -466,7 +466,7 @@ cudaError_t launch_trace(const IceDev& ice, const GeomDev& geom, const WorkDev& 
 
 // Host-API argument check on the device: the lowest index of a malformed
 // source (non-finite field, zero direction, negative length, unknown type).
-__global__ void k_check_sources(const pp_source* __restrict__ src, int64_t n,
+__global__ void k_check_sources(const pp_source* __restrict__ src, int64_t n, int64_t base,
                                 unsigned long long* first_bad) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -474,13 +474,13 @@ __global__ void k_check_sources(const pp_source* __restrict__ src, int64_t n,
   const bool ok = isfinite(s.x) && isfinite(s.y) && isfinite(s.z) && isfinite(s.dx) &&
                   isfinite(s.dy) && isfinite(s.dz) && isfinite(s.length) && s.length >= 0.0f &&
                   (s.dx != 0.0f || s.dy != 0.0f || s.dz != 0.0f) && s.type <= PP_SRC_CASCADE;
-  if (!ok) atomicMin(first_bad, (unsigned long long)i);
+  if (!ok) atomicMin(first_bad, (unsigned long long)(base + i));
 }
 
-cudaError_t launch_check_sources(const pp_source* src, int64_t n, unsigned long long* first_bad,
-                                 cudaStream_t st) {
+cudaError_t launch_check_sources(const pp_source* src, int64_t n, int64_t base,
+                                 unsigned long long* first_bad, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  k_check_sources<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, n, first_bad);
+  k_check_sources<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, n, base, first_bad);
   return cudaGetLastError();
 }
 

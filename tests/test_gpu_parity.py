@@ -479,3 +479,30 @@ def test_full_workload_conservation_and_sampled_photons(full, orc):
         n_diff += int(((out_g != out_o) | (ns_g != ns_o)).sum())
         n_tot += len(ids)
     assert n_diff <= max(2, 1e-3 * n_tot), (n_diff, n_tot)
+
+
+def test_host_batch_pipeline_equals_device_batch(pp, full):
+    """The host entry point cuts large batches into chunks whose uploads and
+    downloads overlap the kernels: results equal the device-pointer path bit
+    for bit, and a malformed source anywhere still fails the call."""
+    import torch
+    b = W.events_full(120, seed=9)
+    assert len(b.sources) >= 1 << 18 and b.n_events >= 4
+    h, c = full.propagate_batch(b)
+    src = np.ascontiguousarray(b.sources)
+    d_src = torch.from_numpy(src.view(np.uint8).copy()).cuda()
+    d_ids = torch.from_numpy(b.event_ids.astype(np.int64)).cuda()
+    d_beg = torch.from_numpy(b.src_begin.astype(np.int64)).cuda()
+    hd = torch.zeros((b.n_events, full.n_dom), dtype=torch.int64, device="cuda")
+    cd = torch.zeros((b.n_events, 4), dtype=torch.int64, device="cuda")
+    pp.pp_propagate_batch_async(full.ctx, b.n_events, d_ids, d_beg, d_src, len(src), hd, cd)
+    pp.pp_sync(full.ctx)
+    assert np.array_equal(h, hd.cpu().numpy().view(np.uint64).astype(h.dtype))
+    assert np.array_equal(c, cd.cpu().numpy().view(np.uint64).astype(c.dtype))
+    bad = W.Batch(b.event_ids.copy(), b.src_begin.copy(), b.sources.copy())
+    bad.sources["dx"][len(src) * 3 // 4], bad.sources["dy"][len(src) * 3 // 4] = np.nan, 0.0
+    with pytest.raises(pp.PPError) as ei:
+        full.propagate_batch(bad)
+    assert ei.value.code == pp.PP_EINVAL and str(len(src) * 3 // 4) in str(ei.value)
+    h2, c2 = full.propagate_batch(b)                 # the context stays usable
+    assert np.array_equal(h2, h) and np.array_equal(c2, c)
