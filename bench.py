@@ -249,7 +249,7 @@ SUR_FLOP_PER_PAIR = 2 * (32 * 256 + 3 * 256 * 256 + 256)   # the four GEMMs and 
 
 def surrogate_leg(args, prop, stream, dev):
     """The learned surrogate on the full grid: trained on pairs from the
-    propagator's own Monte Carlo, judged against independent Monte Carlo
+    propagator's own Monte Carlo, compared with independent Monte Carlo
     (chi2/ndf over DOMs), timed against Monte Carlo of the same sources; the
     operating point is the fastest one (surrogate alone, or with MC fallback
     for sources near a DOM) with chi2/ndf <= 1.2.  Then the dense inference

@@ -359,7 +359,7 @@ const char* pp_server_last_error(const pp_server* server);
 /* No counterpart in the paper's propagation step: an MLP that predicts the
  * expected number of photons a DOM receives from a light source, trained on
  * this library's own Monte Carlo hit counts, so that MC can be replaced where
- * the surrogate is accurate enough and kept as the fallback and judge
+ * the surrogate is accurate enough and kept as the fallback and as the reference
  * elsewhere.  Network: 32 inputs per (source, DOM) pair -- the ten named
  * (source position, source direction polar/azimuth angles, DOM position
  * relative to the source, effective scattering and absorption at the source's

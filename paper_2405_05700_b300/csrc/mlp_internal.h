@@ -1,5 +1,5 @@
-// Internal interface of the surrogate MLP kernels (mlp_kernels.cu) and its C
-// ABI (pp_mlp.cu).  Not part of the public ABI.
+// Internal interface of the surrogate MLP kernels (mlp_fused.cu,
+// mlp_kernels.cu) and its C ABI (pp_mlp.cu).  Not part of the public ABI.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -13,7 +13,6 @@ namespace mlp {
 // Epilogues of the tensor-core GEMM C = A . B^T (FP32 accumulators):
 enum {
   kEpiStoreF32 = 0,      // Cf = acc
-  kEpiAddF32 = 1,        // Cf += acc
   kEpiAtomicF32 = 4,     // Cf += acc with atomics (split-K partial sums)
 };
 

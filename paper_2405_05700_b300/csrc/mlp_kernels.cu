@@ -1,6 +1,8 @@
-// Kernels of the learned surrogate: a tensor-core GEMM with fused epilogues
-// (tcgen05, BF16 in, FP32 accumulate in TMEM) and the small element-wise and
-// reduction kernels of training and inference.
+// Kernels of the learned surrogate beside the fused ones (mlp_fused.cu): a
+// tensor-core GEMM (tcgen05, BF16 in, FP32 accumulate in TMEM; plain or
+// split-K atomic epilogue) for the weight gradients, the pair features and
+// pair search, the head's loss gradient, and the small element-wise and
+// reduction kernels of training.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -136,8 +138,6 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
         const size_t o = (size_t)row * g.ldc + col;
         if (EPI == kEpiStoreF32) {
           g.Cf[o] = v[j];
-        } else if (EPI == kEpiAddF32) {
-          g.Cf[o] += v[j];
         } else if (EPI == kEpiAtomicF32) {
           atomicAdd(g.Cf + o, v[j]);
         }
@@ -167,7 +167,6 @@ cudaError_t launch_gemm(const GemmArgs& g, int epi, cudaStream_t st) {
     break;
   switch (epi) {
     PP_GEMM_CASE(kEpiStoreF32)
-    PP_GEMM_CASE(kEpiAddF32)
     PP_GEMM_CASE(kEpiAtomicF32)
     default:
       return cudaErrorInvalidValue;

@@ -173,20 +173,6 @@ __device__ __forceinline__ float world_exit(const GeomDev& G, float px, float py
   return fminf(tz, tr);
 }
 
-// Exit distance when the step [0, S] may reach the world boundary, +inf when
-// it provably stays inside (then only "t_exit > S" matters and every decision
-// is the same as with the exact distance).  The 1 cm margin exceeds the FP32
-// error of both tests.
-__device__ __forceinline__ float world_exit_within(const GeomDev& G, float px, float py,
-                                                   float pz, float dx, float dy, float dz,
-                                                   float S) {
-  const float m = S + 0.01f;
-  const float rin = G.R - m;
-  const bool inside = rin > 0.0f && fmaf(px, px, py * py) < rin * rin && pz - m > G.zlo &&
-                      pz + m < G.zhi;
-  return inside ? PP_INF : world_exit(G, px, py, pz, dx, dy, dz);
-}
-
 // Radius of a ball about p that lies inside the world cylinder (less a 1 cm
 // margin for FP32 error); negative outside.
 __device__ __forceinline__ float world_inner(const GeomDev& G, float px, float py, float pz) {
@@ -446,8 +432,9 @@ __device__ __forceinline__ int photon_step(Photon& ph, const IceDev& I, const Ge
   float tau_a = ph.tau_a;
   bool absorb;
   const float S = walk(T.layer, I, ph.pz, ph.dz, layer, tau_s, tau_a, absorb, crossings);
-  // world exit: +inf while the step provably stays inside (same decisions as
-  // the exact distance, see world_exit_within)
+  // world exit: +inf while the step provably stays inside, which gives the
+  // same decisions as the exact distance (only "t_exit > S" matters then);
+  // the 1 cm margin exceeds the FP32 error of the test
   float tw = PP_INF;
   if (!(S + 0.01f < ph.wb)) {
     ph.wb = world_inner(G, ph.px, ph.py, ph.pz);

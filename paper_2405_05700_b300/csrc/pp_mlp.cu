@@ -1,8 +1,9 @@
 // The learned surrogate behind the C ABI: an MLP from (source, DOM) pair
 // features to the expected number of photons the DOM receives, trained on the
 // propagator's own hit counts.  BF16 weights and activations, FP32
-// accumulation on the tensor cores (tcgen05 GEMMs of mlp_kernels.cu), FP32
-// master weights and Adam state.
+// accumulation on the tensor cores (the fused tcgen05 kernels of mlp_fused.cu
+// for inference and the training forward / backward, the GEMM of
+// mlp_kernels.cu for the weight gradients), FP32 master weights and Adam state.
 //
 //   h1 = silu(W1 x + b1), h2..h4 = silu(Wi h + bi), z = w5 . h4 + b5,
 //   lambda = n_photons * softplus(z),  loss = mean(lambda - n ln lambda)

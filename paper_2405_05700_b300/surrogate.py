@@ -190,7 +190,7 @@ def evaluate(prop, mlp, n_sources, photons, seed=123, event_base=10_000_000,
     chi2 / ndf over DOMs expecting >= min_expected hits).  Hybrid, for each
     fallback radius: sources closer than the radius to a DOM go to MC (the
     same events, hence the same counts), the rest to the surrogate, each part
-    timed on its own; judged against an independent MC run of all sources
+    timed on its own; compared with an independent MC run of all sources
     (variance: the surrogate part's expectation + twice the MC part's
     counts).  Speedup = full MC time / surrogate (+ fallback MC) time."""
     import torch
@@ -225,7 +225,7 @@ def _evaluate(prop, mlp, n_sources, photons, seed, event_base, r_fallbacks, min_
     src = W.surrogate_sources(np.random.default_rng(seed), n_sources, photons)
     ids = np.arange(event_base, event_base + n_sources, dtype=np.int64)
     hits, mc_secs = mc_hits(prop, src, 0, event_ids=ids)
-    hits2, _ = mc_hits(prop, src, 0, event_ids=ids + 5_000_000)   # the judge
+    hits2, _ = mc_hits(prop, src, 0, event_ids=ids + 5_000_000)   # independent reference run
     ref = hits2.sum(0).astype(np.float64)
     lam = torch.zeros((n_sources, prop.n_dom), dtype=torch.float32, device="cuda")
     sur_dom, sur_secs = _sur_time(prop, mlp, src, photons, r_max, lam)
