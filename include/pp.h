@@ -380,60 +380,88 @@ const char* pp_server_last_error(const pp_server* server);
 #define PP_MLP_INPUTS 32
 typedef struct pp_mlp pp_mlp;
 
-/* max_batch: largest training batch (multiple of 16); max_rows: capacity of
- * the inference pair list (8 bytes per row). */
+/* Creates a surrogate on ctx (geometry and ice loaded; while it exists the
+ * context refuses new geometry or ice).
+ *   max_batch  largest training batch, a multiple of 16 (>= 16); training
+ *              buffers of ~6 KiB per row are allocated
+ *   max_rows   capacity of the inference pair list (8 bytes per row); a
+ *              pp_mlp_dom_sums pass holds at most this many pairs
+ * Parameters start at zero (use pp_mlp_set_params).
+ * Errors: PP_EINVAL, PP_ENOTLOADED, PP_ENOMEM. */
 int pp_mlp_create(pp_ctx* ctx, int32_t max_batch, int64_t max_rows, pp_mlp** out);
+
+/* Waits for the device and frees the surrogate.  NULL is accepted. */
 int pp_mlp_destroy(pp_mlp* mlp);
+
+/* Message for the last error raised on this surrogate (never NULL). */
 const char* pp_mlp_last_error(const pp_mlp* mlp);
 
-/* Host FP32 parameters in / out (n = PP_MLP_N_PARAMS); set also resets Adam. */
+/* Host FP32 parameters in / out, n = PP_MLP_N_PARAMS (layout above); set also
+ * resets the Adam moments and step.  Both synchronise.
+ * Errors: PP_EINVAL (null pointer, wrong n), PP_ECUDA, PP_EDEVICE. */
 int pp_mlp_set_params(pp_mlp* mlp, const float* params, int64_t n);
 int pp_mlp_get_params(pp_mlp* mlp, float* params, int64_t n);
 
-/* Device features of n pairs (source index, DOM index) into d_feat[n][32]
- * (BF16 bit patterns); sources as in pp_propagate (the point is the segment's
- * midpoint). */
+/* Features of n pairs into d_feat[n][32] (BF16 bit patterns, row-major):
+ *   d_src              sources as in pp_propagate (the point is the segment's midpoint)
+ *   d_pair_src[n], d_pair_dom[n]  indices into d_src and the loaded DOMs (caller-checked)
+ * Enqueued on `stream` (NULL: the context's stream).  Errors: PP_EINVAL, PP_ECUDA. */
 int pp_mlp_features(pp_mlp* mlp, const pp_source* d_src, const int32_t* d_pair_src,
                     const int32_t* d_pair_dom, int64_t n, uint16_t* d_feat, void* stream);
 
-/* d_lambda[i] = predicted photons on pair i given d_nph[i] photons emitted
- * (fused inference kernel; d_feat 16-byte aligned). */
+/* d_lambda[i] = predicted photons on pair i given d_nph[i] photons emitted,
+ * by the fused inference kernel (rows mode).  d_feat[n][32] BF16, 16-byte
+ * aligned.  Enqueued on `stream` (NULL: the context's stream); a device error
+ * (a bounded wait that ran out) is reported by pp_mlp_sync.
+ * Errors: PP_EINVAL (null or misaligned pointer), PP_ECUDA. */
 int pp_mlp_forward(pp_mlp* mlp, const uint16_t* d_feat, const float* d_nph, int64_t n,
                    float* d_lambda, void* stream);
 
-/* Forward and backward on one batch (n multiple of 16, <= max_batch) without
- * updating: h_grads[PP_MLP_N_PARAMS] receives d(loss)/d(params) and *h_loss
- * the mean loss.  Synchronous. */
+/* Forward and backward on one batch without updating: d_feat[n][32] (16-byte
+ * aligned), d_nph[n] photons, d_count[n] observed hits; n a multiple of 16 in
+ * [16, max_batch].  h_grads[PP_MLP_N_PARAMS] receives d(loss)/d(params) and
+ * *h_loss (may be NULL) the mean loss.  Synchronous, on the context's stream.
+ * Errors: PP_EINVAL, PP_ECUDA, PP_EDEVICE. */
 int pp_mlp_gradients(pp_mlp* mlp, const uint16_t* d_feat, const float* d_nph,
                      const float* d_count, int64_t n, float* h_grads, double* h_loss);
 
-/* One Adam step (beta 0.9 / 0.999, eps 1e-8) on a batch of pairs with counts. */
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, learning rate lr > 0) on a batch
+ * as for pp_mlp_gradients; the batch's mean loss is added to the running sum
+ * pp_mlp_loss returns.  Enqueued on `stream` (NULL: the context's stream).
+ * Errors: PP_EINVAL, PP_ECUDA (device errors: pp_mlp_sync / pp_mlp_loss). */
 int pp_mlp_train_step(pp_mlp* mlp, const uint16_t* d_feat, const float* d_nph,
                       const float* d_count, int64_t n, float lr, void* stream);
 
-/* Sum of the mean losses of the train steps since the last call (waits). */
+/* Sum of the mean losses of the train steps since the last call, then reset.
+ * Synchronous.  Errors: PP_EINVAL, PP_ECUDA, PP_EDEVICE. */
 int pp_mlp_loss(pp_mlp* mlp, double* loss);
 
 /* Dense inference over n_src sources x all DOMs: d_dom_sums[n_dom] (zeroed
  * here) receives sum over sources of lambda, and d_lambda[n_src][n_dom] (if not
- * NULL) every pair's lambda; d_nph_src[n_src] photons per source.  Pairs
- * farther apart than r_max (the distance range the network was trained on)
- * count zero. */
+ * NULL, zeroed here) every pair's lambda; d_nph_src[n_src] photons per source.
+ * Pairs farther apart than r_max (the distance range the network was trained
+ * on) count zero; the pairs within it are found on the device and evaluated
+ * by the fused kernel (pairs mode) in passes of at most max_rows pairs.  The
+ * call waits for each pass's pair count, so it returns once the last pass is
+ * enqueued on `stream` (NULL: the context's stream).
+ * Errors: PP_EINVAL (also: one source with more than max_rows pairs), PP_ECUDA. */
 int pp_mlp_dom_sums(pp_mlp* mlp, const pp_source* d_src, int64_t n_src, const float* d_nph_src,
                     float r_max, double* d_dom_sums, float* d_lambda, void* stream);
 
 /* The (source, DOM) pairs closer than r_max (segment midpoint to DOM centre),
  * in unspecified order: the first max_out go to d_pair_src / d_pair_dom, and
- * *h_count receives how many there are (may exceed max_out).  Synchronous. */
+ * *h_count receives how many there are (may exceed max_out).  Synchronous, on
+ * the context's stream.  Errors: PP_EINVAL, PP_ECUDA. */
 int pp_mlp_near_pairs(pp_mlp* mlp, const pp_source* d_src, int64_t n_src, float r_max,
                       int64_t max_out, int32_t* d_pair_src, int32_t* d_pair_dom,
                       uint64_t* h_count);
 
-/* SiLU of the inference kernel: 0 (default) one tanh.approx per unit, 1
- * z / (1 + exp(-z)) as in training. */
+/* SiLU of the inference kernel: 0 (default) z/2 (1 + tanh.approx(z/2)), one
+ * SFU operation per unit; 1: z / (1 + exp(-z)) as in training.  Errors: PP_EINVAL. */
 int pp_mlp_set_exact_silu(pp_mlp* mlp, int exact);
 
-/* Waits for the MLP's work and reports a device error flag. */
+/* Waits for the context's stream and reports (then clears) the surrogate's
+ * device error flag.  Errors: PP_EINVAL, PP_ECUDA, PP_EDEVICE. */
 int pp_mlp_sync(pp_mlp* mlp);
 
 /* ---- debug and parity entry points (host buffers) ------------------------ */

@@ -198,9 +198,10 @@ int forward_backward(pp_mlp* m, const __nv_bfloat16* x0, const float* nph, const
   return PP_OK;
 }
 
-int check_batch(pp_mlp* m, int64_t n) {
+int check_batch(pp_mlp* m, int64_t n, const void* d_feat) {
   if (n < 16 || n > m->max_batch || n % 16)
     return mfail(m, PP_EINVAL, "training batch must be a multiple of 16 in [16, max_batch]");
+  if (!aligned16(d_feat)) return mfail(m, PP_EINVAL, "features must be 16-byte aligned");
   return PP_OK;
 }
 
@@ -359,7 +360,7 @@ int pp_mlp_gradients(pp_mlp* m, const uint16_t* d_feat, const float* d_nph, cons
                      int64_t n, float* h_grads, double* h_loss) {
   if (!m || !d_feat || !d_nph || !d_count || !h_grads) return PP_EINVAL;
   int rc;
-  if ((rc = check_batch(m, n))) return rc;
+  if ((rc = check_batch(m, n, d_feat))) return rc;
   PP_MLP_CUDA(cudaSetDevice(m->view.device));
   cudaStream_t st = m->view.stream;
   PP_MLP_CUDA(cudaMemsetAsync(m->loss, 0, sizeof(double), st));
@@ -376,7 +377,7 @@ int pp_mlp_train_step(pp_mlp* m, const uint16_t* d_feat, const float* d_nph, con
                       int64_t n, float lr, void* stream) {
   if (!m || !d_feat || !d_nph || !d_count || !(lr > 0.0f)) return PP_EINVAL;
   int rc;
-  if ((rc = check_batch(m, n))) return rc;
+  if ((rc = check_batch(m, n, d_feat))) return rc;
   PP_MLP_CUDA(cudaSetDevice(m->view.device));
   cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : m->view.stream;
   if ((rc = forward_backward(m, reinterpret_cast<const __nv_bfloat16*>(d_feat), d_nph, d_count,
