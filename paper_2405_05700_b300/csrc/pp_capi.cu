@@ -468,8 +468,8 @@ int sync_and_check(pp_ctx* ctx, cudaStream_t st) {
   return PP_OK;
 }
 
-// Host batch, batched path, large inputs: the events are cut into 2 chunks
-// of about equal source counts; a copy stream uploads every chunk and
+// Host batch, batched path, large inputs: the events are cut into 3 chunks
+// (10 %, 80 %, 10 % of the sources); a copy stream uploads every chunk and
 // downloads each chunk's results once its propagation (on the context's
 // stream) is done, so transfers overlap the kernels.  The sources are
 // checked on the device; a malformed one fails the call with PP_EINVAL after
@@ -482,11 +482,13 @@ int batch_host_pipelined(pp_ctx* ctx, int32_t n_events, const uint64_t* ids, con
   cudaStream_t st = ctx->stream;
   if (!ctx->copy_stream) PP_CUDA(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
   cudaStream_t cs = ctx->copy_stream;
-  // chunks: event ranges of about n_src / kChunks sources each
+  // chunks: event ranges cut at 10 % and 90 % of the sources
   std::vector<int32_t> cut{0};
-  constexpr int kChunks = 2;
-  for (int k = 1; k < kChunks; ++k) {
-    const int64_t target = n_src * k / kChunks;
+  // a small first chunk (its upload is exposed), a small last one (its
+  // download is exposed), the bulk in between
+  const double edges[2] = {0.1, 0.9};
+  for (int k = 0; k < 2; ++k) {
+    const int64_t target = (int64_t)(edges[k] * (double)n_src);
     int32_t e = cut.back();
     while (e < n_events && begin[e] < target) ++e;
     if (e > cut.back() && e < n_events) cut.push_back(e);
