@@ -79,7 +79,7 @@ def parse():
                     help="leading events of the workload (profiling runs use fewer)")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--sur-train-sources", type=int, default=200_000)
-    ap.add_argument("--sur-epochs", type=int, default=16)
+    ap.add_argument("--sur-epochs", type=int, default=32)
     ap.add_argument("--sur-eval-sources", type=int, default=5000)
     ap.add_argument("--sur-dense-sources", type=int, default=1_000_000)
     return ap.parse_args()
