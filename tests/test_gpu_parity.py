@@ -506,3 +506,34 @@ def test_host_batch_pipeline_equals_device_batch(pp, full):
     assert ei.value.code == pp.PP_EINVAL and str(len(src) * 3 // 4) in str(ei.value)
     h2, c2 = full.propagate_batch(b)                 # the context stays usable
     assert np.array_equal(h2, h) and np.array_equal(c2, c)
+
+
+def test_sources_outside_the_world_and_the_ice_table(full, tiny, orc):
+    """Edge geometry: a source outside the world cylinder escapes at once
+    (every photon); on the tiny detector, whose world reaches beyond both ends
+    of its ice table, sources above and below the table (edge layers
+    extended) propagate like the oracle's photons, one by one, and every
+    photon is accounted for."""
+    R = float(full.world()[0])
+    out = W.point_source(R + 50.0, 0.0, 0.0, 20_000)
+    h, c = full.propagate(3, out)
+    assert int(h.sum()) == 0 and int(c[1]) == 20_000 and int(c[0]) == 0
+    geom, ice = W.geometry_tiny(), W.ice_tiny()
+    _, zlo, zhi = (float(v) for v in tiny.world())
+    z_top_table = 1950.0 - ice.depth_top
+    z_bot_table = 1950.0 - (ice.depth_top + ice.dz * len(ice.b_e))
+    assert zhi > z_top_table + 20.0 and zlo < z_bot_table - 20.0
+    src = np.concatenate([W.point_source(0.0, 0.0, z_top_table + 20.0, 5_000),
+                          W.point_source(10.0, 5.0, z_bot_table - 20.0, 5_000)])
+    h, c = tiny.propagate(4, src)
+    assert int(h.sum() + c[0] + c[1]) == 10_000
+    ids = np.arange(0, 10_000, 37, dtype=np.uint64)
+    out_g, ns_g, birth_g, tr_g = tiny.trace(4, src, ids, n_trace=10)
+    m = orc.Model(geom, ice, seed=0)
+    out_o, ns_o, birth_o, tr_o = orc.trace(m, 4, src, ids, n_trace=10)
+    assert np.allclose(birth_g, birth_o, atol=1e-3)
+    both = np.isfinite(tr_g) & np.isfinite(tr_o)
+    assert both.sum() > 0.9 * np.isfinite(tr_o).sum()
+    scale = np.maximum(np.abs(tr_o[both]), 1.0)
+    assert np.all(np.abs(tr_g[both] - tr_o[both]) <= 1e-4 * scale + 1e-4)
+    assert (out_g != out_o).mean() <= 2e-2

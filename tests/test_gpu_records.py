@@ -119,3 +119,18 @@ def test_records_overflow_and_bad_group_index(pp, tiny):
     with pytest.raises(pp.PPError) as ei:
         _run(pp, tiny, batch, group_index=0.5)
     assert ei.value.code == pp.PP_EINVAL
+
+
+def test_group_index_scales_path_time(pp, tiny):
+    """The same photons hit the same DOMs whatever the group index; each hit
+    time is (emission offset + n_g x path) / c, so for a point source (no
+    offset) the times scale with n_g exactly up to FP32 rounding."""
+    dom = W.geometry_tiny().xyz[30]
+    src = W.point_source(float(dom[0]) + 3.0, float(dom[1]), float(dom[2]), 200_000)
+    batch = W.single_event(src, 11)
+    h1, c1, r1, n1 = _run(pp, tiny, batch, group_index=1.30)
+    h2, c2, r2, n2 = _run(pp, tiny, batch, group_index=1.50)
+    assert np.array_equal(h1, h2) and np.array_equal(c1, c2) and n1 == n2 > 100
+    t1 = np.sort(r1["time_ns"].astype(np.float64))
+    t2 = np.sort(r2["time_ns"].astype(np.float64))
+    assert np.allclose(t2, t1 * (1.50 / 1.30), rtol=1e-5)

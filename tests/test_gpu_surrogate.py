@@ -262,3 +262,25 @@ def test_trained_surrogate_gains_over_monte_carlo(pp, prop):
     # MC fallback for sources near a DOM: no worse than the surrogate alone
     hyb = {h["r_fallback"]: h for h in trained["hybrid"]}
     assert hyb[10.0]["chi2_ndf"] <= hyb[0.0]["chi2_ndf"] * 1.1
+
+
+def test_features_outside_the_ice_table_match_oracle(pp, prop, mlp):
+    """Sources and DOMs beyond the ends of the ice table: point values take
+    the edge layer, line means extend the edge layers; device against oracle."""
+    import torch
+    from oracle import mlp as M
+    geom, ice = W.geometry_full(), W.ice_full()
+    rng = np.random.default_rng(21)
+    src, ps, pd = _training_like_pairs(rng, 200, geom, 2048)
+    z_top = 1950.0 - ice.depth_top
+    z_bot = 1950.0 - (ice.depth_top + ice.dz * len(ice.b_e))
+    src["z"][:100] = rng.uniform(z_top + 5.0, z_top + 200.0, 100)      # above the table
+    src["z"][100:] = rng.uniform(z_bot - 200.0, z_bot - 5.0, 100)      # below it
+    feat = torch.zeros((len(ps), pp.PP_MLP_INPUTS), dtype=torch.int16, device="cuda")
+    pp.pp_mlp_features(mlp.handle, _dev(src.view(np.uint8)), _dev(ps), _dev(pd), len(ps), feat)
+    pp.pp_mlp_sync(mlp.handle)
+    got = pp.bf16_value(feat.cpu().numpy().view(np.uint16)).astype(np.float64)
+    ref = M.bf16(M.features(src, ps, pd, geom.xyz, ice.b_e, ice.a, ice.depth_top, ice.dz))
+    step = np.abs(ref) * 2.0 ** -7 + 1e-30
+    assert np.mean(np.abs(got - ref) <= step * 1.01) > 0.999
+    assert np.mean(got == ref) > 0.98
