@@ -382,7 +382,7 @@ typedef struct pp_mlp pp_mlp;
 
 /* Creates a surrogate on ctx (geometry and ice loaded; while it exists the
  * context refuses new geometry or ice).
- *   max_batch  largest training batch, a multiple of 16 (>= 16); training
+ *   max_batch  largest training batch, a multiple of 64 (>= 64); training
  *              buffers of ~6 KiB per row are allocated
  *   max_rows   capacity of the inference pair list (8 bytes per row); a
  *              pp_mlp_dom_sums pass holds at most this many pairs
@@ -418,8 +418,8 @@ int pp_mlp_forward(pp_mlp* mlp, const uint16_t* d_feat, const float* d_nph, int6
                    float* d_lambda, void* stream);
 
 /* Forward and backward on one batch without updating: d_feat[n][32] (16-byte
- * aligned), d_nph[n] photons, d_count[n] observed hits; n a multiple of 16 in
- * [16, max_batch].  h_grads[PP_MLP_N_PARAMS] receives d(loss)/d(params) and
+ * aligned), d_nph[n] photons, d_count[n] observed hits; n a multiple of 64 in
+ * [64, max_batch].  h_grads[PP_MLP_N_PARAMS] receives d(loss)/d(params) and
  * *h_loss (may be NULL) the mean loss.  Synchronous, on the context's stream.
  * Errors: PP_EINVAL, PP_ECUDA, PP_EDEVICE. */
 int pp_mlp_gradients(pp_mlp* mlp, const uint16_t* d_feat, const float* d_nph,

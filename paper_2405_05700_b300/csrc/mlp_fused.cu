@@ -238,6 +238,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
 #pragma unroll
             for (int i = 0; i < kIn / 8; ++i)
               fv[i] = *reinterpret_cast<const uint4*>(a.feat + row * kIn + 8 * i);
+            if (kTrain) {  // the features K-tiled, the first layer's weight-gradient operand
+#pragma unroll
+              for (int i = 0; i < kIn / 8; ++i) {
+                const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&fv[i]);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                  *reinterpret_cast<__nv_bfloat16*>(
+                      a.x_t + kt_off((uint32_t)(8 * i + j), (uint32_t)row, kIn)) = e[j];
+              }
+            }
           }
         }
 #pragma unroll
@@ -293,13 +303,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
             }
           }
           if (kTrain && !last && valid) {
-            // activations transposed ([256][n]): a warp stores 32 consecutive rows of a column
-            __nv_bfloat16* ht = a.h_out[layer] + (size_t)(c_begin + c0) * a.n + row;
+            // activations K-tiled ([256][n]): a warp's 32 rows of one column
+            // land in four 16-byte runs
+            unsigned char* ht = reinterpret_cast<unsigned char*>(a.h_out[layer]);
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
               const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(&packed[j]);
-              ht[(size_t)(2 * j) * a.n] = __low2bfloat16(v);
-              ht[(size_t)(2 * j + 1) * a.n] = __high2bfloat16(v);
+              const uint32_t m = (uint32_t)(c_begin + c0 + 2 * j);
+              *reinterpret_cast<__nv_bfloat16*>(ht + kt_off(m, (uint32_t)row, kHid)) = __low2bfloat16(v);
+              *reinterpret_cast<__nv_bfloat16*>(ht + kt_off(m + 1, (uint32_t)row, kHid)) =
+                  __high2bfloat16(v);
             }
           }
           if (!last) {
@@ -514,6 +527,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd(BwdArgs a) {
           const uint4 v = valid ? *reinterpret_cast<const uint4*>(src + 8 * i)
                                 : make_uint4(0, 0, 0, 0);
           *reinterpret_cast<uint4*>(sH + tc::tile_off(r, c_begin + 8 * i, kHid)) = v;
+          if (valid) {  // and K-tiled, the last layer's weight-gradient operand
+            const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              *reinterpret_cast<__nv_bfloat16*>(
+                  a.dz3_t + kt_off((uint32_t)(c_begin + 8 * i + j), (uint32_t)row, kHid)) = e[j];
+          }
         }
         tc::fence_smem_async();
       }
@@ -557,13 +577,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd(BwdArgs a) {
                              packed[4 * i + 3]);
           }
           if (valid) {
-            // dL/dz transposed ([256][n]): a warp stores 32 consecutive rows of a column
-            __nv_bfloat16* dt = dzt + (size_t)(c_begin + c0) * a.n + row;
+            // dL/dz K-tiled ([256][n]), the weight-gradient kernel's A operand
+            unsigned char* dt = reinterpret_cast<unsigned char*>(dzt);
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
               const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(&packed[j]);
-              dt[(size_t)(2 * j) * a.n] = __low2bfloat16(v);
-              dt[(size_t)(2 * j + 1) * a.n] = __high2bfloat16(v);
+              const uint32_t m = (uint32_t)(c_begin + c0 + 2 * j);
+              *reinterpret_cast<__nv_bfloat16*>(dt + kt_off(m, (uint32_t)row, kHid)) = __low2bfloat16(v);
+              *reinterpret_cast<__nv_bfloat16*>(dt + kt_off(m + 1, (uint32_t)row, kHid)) =
+                  __high2bfloat16(v);
             }
           }
         };
@@ -614,6 +636,162 @@ __global__ void k_pack_bwd(const __nv_bfloat16* w2, const __nv_bfloat16* w3,
   unsigned char* dst = out + (size_t)(j * kChunksPerLayer + c) * kChunkBytes +
                        tc::tile_off(n, k - c * kChunkK, kChunkK);
   *reinterpret_cast<__nv_bfloat16*>(dst) = w[rem];
+}
+
+// Weight gradients of one layer: dw[256][nb] += sum over the batch of
+// dz^T . x, both operands K-tiled (one 64-row block of each is one bulk copy).
+// Persistent CTAs take blocks round-robin; the two 128-row halves of dw
+// accumulate in TMEM (2 nb columns) over the CTA's blocks, and each CTA
+// stores its partial sums (zeros when it had no block) to partial[CTA][256][nb];
+// k_reduce_dw adds them to dw.  Warps 0-3: TMEM
+// readout; warp 4: producer (3-stage ring); warp 5: MMA issue.  Bounded waits.
+constexpr int kDwStages = 3;
+constexpr int kDwThreads = 192;
+constexpr uint32_t kDwABytes = kHid * kKTile * 2;  // 32 KB
+constexpr uint32_t kDwStageBytes = 2 * kDwABytes;  // A and B (B <= 32 KB)
+
+__global__ void __launch_bounds__(kDwThreads, 1) k_dw(DwArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[kDwStages], empty[kDwStages], acc_done;
+  __shared__ uint32_t tslot;
+  __shared__ int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t n_blocks = a.n / kKTile;
+  const uint32_t b_bytes = (uint32_t)a.nb * kKTile * 2;
+  const uint32_t ncols = a.nb == kHid ? 512u : 64u;  // 2 nb, a power of two >= 32
+  if (warp == 0) tc::tmem_alloc(&tslot, ncols);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kDwStages; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    tc::mbar_init(&acc_done, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tslot;
+  const int64_t mine = blockIdx.x < n_blocks ? (n_blocks - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  if (warp == 4) {
+    if (lane == 0) {
+      uint32_t it = 0;
+      for (int64_t q = blockIdx.x; q < n_blocks; q += gridDim.x, ++it) {
+        const uint32_t s = it % kDwStages;
+        if (it >= (uint32_t)kDwStages &&
+            (!tc::mbar_wait(&empty[s], ((it / kDwStages) - 1) & 1, kWaitTries) ||
+             *(volatile int*)&abort_flag)) {
+          atomicExch(&abort_flag, 1);
+          atomicOr(a.err, 1);
+          break;
+        }
+        unsigned char* st = smem + s * kDwStageBytes;
+        tc::mbar_arrive_expect_tx(&full[s], kDwABytes + b_bytes);
+        tc::bulk_g2s(st, a.a + (size_t)q * kDwABytes, kDwABytes, &full[s]);
+        tc::bulk_g2s(st + kDwABytes, a.b + (size_t)q * b_bytes, b_bytes, &full[s]);
+      }
+      const uint32_t last = it < (uint32_t)kDwStages ? it : (uint32_t)kDwStages;
+      for (uint32_t q = 0; q < last; ++q) {
+        const uint32_t i = it - 1 - q;
+        tc::mbar_wait(&full[i % kDwStages], (i / kDwStages) & 1, kWaitTries);
+      }
+    }
+  } else if (warp == 5) {
+    if (lane == 0 && mine > 0) {
+      const uint32_t idesc = tc::idesc_bf16(kHalf, (uint32_t)a.nb);
+      const uint32_t base = tc::smem_u32(smem);
+      bool ok = true;
+      uint32_t it = 0;
+      for (int64_t q = blockIdx.x; q < n_blocks && ok; q += gridDim.x, ++it) {
+        const uint32_t s = it % kDwStages;
+        if (!tc::mbar_wait(&full[s], (it / kDwStages) & 1, kWaitTries) ||
+            *(volatile int*)&abort_flag) {
+          ok = false;
+          break;
+        }
+        tc::fence_after_sync();
+        const uint32_t sa = base + s * kDwStageBytes, sb = sa + kDwABytes;
+#pragma unroll
+        for (int mb = 0; mb < 2; ++mb)
+#pragma unroll
+          for (int kk = 0; kk < kKTile / 16; ++kk)
+            tc::mma_bf16(tmem + mb * a.nb,
+                         tc::smem_desc(sa + mb * (kHalf / 8) * (kKTile * 16) + kk * 256, 128,
+                                       kKTile * 16),
+                         tc::smem_desc(sb + kk * 256, 128, kKTile * 16), idesc,
+                         (it > 0 || kk > 0) ? 1u : 0u);
+        tc::mma_commit(&empty[s]);
+      }
+      if (!ok) {
+        atomicExch(&abort_flag, 1);
+        atomicOr(a.err, 1);
+      }
+      tc::mma_commit(&acc_done);
+    }
+  } else {
+    // warps 0-3: TMEM lanes 32 w .. + 31 = rows of each half of dw
+    float* part = a.partial + (size_t)blockIdx.x * kHid * a.nb;
+    const bool got = mine == 0 ||
+                     (tc::mbar_wait(&acc_done, 0, kWaitTries) && !*(volatile int*)&abort_flag);
+    if (__all_sync(0xffffffffu, got)) {
+      __syncwarp();
+      tc::fence_after_sync();
+      for (int mb = 0; mb < 2; ++mb) {
+        const int m = mb * kHalf + warp * 32 + lane;
+        for (int c0 = 0; c0 < a.nb; c0 += 32) {
+          float v[32];
+          if (mine > 0) {
+            tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(mb * a.nb + c0), v);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = 0.0f;
+          }
+          float4* dst = reinterpret_cast<float4*>(part + (size_t)m * a.nb + c0);
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        }
+      }
+    } else if (lane == 0) {
+      atomicOr(a.err, 1);
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tmem, ncols);
+}
+
+// dw[i] += sum over the CTAs of partial[c][i]
+__global__ void k_reduce_dw(const float* partial, int parts, int size, float* dw) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= size) return;
+  float acc = 0.0f;
+  for (int c = 0; c < parts; ++c) acc += partial[(size_t)c * size + i];
+  dw[i] += acc;
+}
+
+__global__ void __launch_bounds__(256) k_rowsum_kt(const unsigned char* in, int R, int64_t n,
+                                                    float* out) {
+  __shared__ float part[8];
+  const uint32_t r = blockIdx.x;
+  float acc = 0.0f;
+  for (int64_t g = threadIdx.x; g < n / 8; g += blockDim.x) {  // 8 consecutive batch rows
+    const uint4 v = *reinterpret_cast<const uint4*>(in + kt_off(r, (uint32_t)(g * 8), (uint32_t)R));
+    const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&v);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc += __bfloat162float(e[j]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.0f;
+    for (int w = 0; w < 8; ++w) t += part[w];
+    out[r] += t;
+  }
 }
 
 // The weights in the ring's chunk layout: chunk 0 is W1 ([256][32]), then
@@ -678,6 +856,30 @@ cudaError_t launch_mlp_bwd(const BwdArgs& a, int grid, cudaStream_t st) {
                                        (int)kSmemBytes);
   if (e != cudaSuccess) return e;
   k_mlp_bwd<<<g, kThreads, kSmemBytes, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dw(const DwArgs& a, int grid, cudaStream_t st) {
+  const int64_t blocks = a.n / kKTile;
+  if (blocks <= 0) return cudaSuccess;
+  if (grid > a.partial_cap) grid = a.partial_cap;
+  if (grid < 1 || (a.nb != kHid && a.nb != kIn) || a.n % kKTile) return cudaErrorInvalidValue;
+  const int g = (int)(blocks < grid ? blocks : grid);
+  const size_t smem = (size_t)kDwStages * kDwStageBytes;
+  cudaError_t e = cudaFuncSetAttribute(k_dw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_dw<<<g, kDwThreads, smem, st>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int size = kHid * a.nb;
+  k_reduce_dw<<<(size + 255) / 256, 256, 0, st>>>(a.partial, g, size, a.dw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rowsum_kt(const unsigned char* in, int R, int64_t n, float* out,
+                             cudaStream_t st) {
+  if (R <= 0 || n <= 0) return cudaSuccess;
+  k_rowsum_kt<<<R, 256, 0, st>>>(in, R, n, out);
   return cudaGetLastError();
 }
 

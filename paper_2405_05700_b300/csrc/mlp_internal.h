@@ -10,25 +10,19 @@
 
 namespace mlp {
 
-// Epilogues of the tensor-core GEMM C = A . B^T (FP32 accumulators):
-enum {
-  kEpiStoreF32 = 0,      // Cf = acc
-  kEpiAtomicF32 = 4,     // Cf += acc with atomics (split-K partial sums)
-};
-
+// Plain tensor-core GEMM C = A . B^T (FP32), the debug entry point's kernel.
 struct GemmArgs {
   const __nv_bfloat16* A;  // [M][lda], K contiguous
   const __nv_bfloat16* B;  // [N][ldb], K contiguous
   int M, N, K, lda, ldb, ldc;
   int bn;                  // N tile: multiple of 16, <= 256
-  int k_split;             // K ranges run by separate CTAs (grid z); needs kEpiAtomicF32 if > 1
   int swap_lbo_sbo;        // layout probe: exchange the descriptor strides
   float* Cf;
   int* err;
 };
 
 size_t gemm_smem_bytes(int bn);
-cudaError_t launch_gemm(const GemmArgs& g, int epi, cudaStream_t st);
+cudaError_t launch_gemm(const GemmArgs& g, cudaStream_t st);
 
 constexpr int kIn = 32;      // input features (10 named + 22 derived), the first MMA's K
 constexpr int kHid = 256;    // hidden width
@@ -87,10 +81,11 @@ struct FusedArgs {
   int n_dom;
   float* lambda;                 // rows mode (inference)
   // training forward (rows mode, exact SiLU, no lambda): each layer's BF16
-  // pre-activations [n][256] and activations (layers 0-2 transposed [256][n],
+  // pre-activations [n][256] and activations (layers 0-2 K-tiled [256][n],
   // layer 3 [n][256]); null for inference
   __nv_bfloat16* z_out[kLayers];
   __nv_bfloat16* h_out[kLayers];
+  unsigned char* x_t;            // training: the features K-tiled [32][n]
   int* err;
 };
 
@@ -102,13 +97,14 @@ cudaError_t launch_mlp_fused(const FusedArgs& a, bool from_pairs, int grid, cuda
 
 // Fused backward of the hidden layers (training): from dz[3] (dL/dz of the
 // last hidden layer, BF16 [n][256]) and the forward's pre-activations z[0..2]
-// ([n][256]), writes dz[2], dz[1], dz[0] transposed ([256][n]).  wpack: the
+// ([n][256]), writes dz[2], dz[1], dz[0] K-tiled ([256][n]).  wpack: the
 // transposed hidden weights packed by launch_pack_bwd.
 struct BwdArgs {
   int64_t n;
   const unsigned char* wpack;
   const __nv_bfloat16* z[kLayers];
   __nv_bfloat16* dz[kLayers];
+  unsigned char* dz3_t;          // dz[3] K-tiled [256][n], written while it is staged
   int* err;
 };
 size_t packed_bwd_bytes();
@@ -116,14 +112,33 @@ size_t packed_bwd_bytes();
 cudaError_t launch_pack_bwd(const __nv_bfloat16* const* w, unsigned char* out, cudaStream_t st);
 cudaError_t launch_mlp_bwd(const BwdArgs& a, int grid, cudaStream_t st);
 
-cudaError_t launch_transpose(const __nv_bfloat16* in, int rows, int cols, __nv_bfloat16* out,
+// K-tiled layout of a training matrix X[R][n] (R = 256 units or the 32
+// features; K = the n batch rows, a multiple of 64): blocks of 64 batch rows,
+// each the K-major core-matrix image of an MMA operand tile (R x 64 BF16), so
+// that one bulk copy stages it.  Byte offset of element (r, k):
+constexpr int kKTile = 64;
+__host__ __device__ constexpr size_t kt_off(uint32_t r, uint32_t k, uint32_t R) {
+  return (size_t)(k / kKTile) * ((size_t)R * kKTile * 2) + (size_t)(r >> 3) * (kKTile * 16) +
+         ((k % kKTile) >> 3) * 128u + (r & 7u) * 16u + (k & 7u) * 2u;
+}
+
+// out[r] += sum over the n batch rows of a K-tiled [R][n] matrix (FP32)
+cudaError_t launch_rowsum_kt(const unsigned char* in, int R, int64_t n, float* out,
                              cudaStream_t st);
-// out[r] = sum_c in[r][c] (FP32) for a BF16 matrix [rows][cols]
-cudaError_t launch_rowsum(const __nv_bfloat16* in, int rows, int cols, float* out,
-                          cudaStream_t st);
-// out[c] = sum_r in[r][c] (FP32) for a BF16 matrix
-cudaError_t launch_colsum(const __nv_bfloat16* in, int rows, int cols, float* out,
-                          cudaStream_t st);
+// Weight gradient dw[256][nb] += A . B^T over the batch: A = dL/dz^T (R = 256),
+// B = the layer's input^T (R = nb: 256 or 32), both K-tiled over n rows.
+struct DwArgs {
+  const unsigned char* a;
+  const unsigned char* b;
+  int64_t n;
+  int nb;
+  float* dw;
+  float* partial;  // [partial_cap][256][nb] FP32 scratch
+  int partial_cap;  // CTAs the scratch holds (the grid is capped to it)
+  int* err;
+};
+cudaError_t launch_dw(const DwArgs& a, int grid, cudaStream_t st);
+
 // Adam on n parameters; writes the BF16 copy of the weights it updates.
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr,
                         float b1, float b2, float eps, float bc1, float bc2, __nv_bfloat16* pb,

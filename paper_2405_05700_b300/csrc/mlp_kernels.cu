@@ -1,8 +1,8 @@
 // Kernels of the learned surrogate beside the fused ones (mlp_fused.cu): a
-// tensor-core GEMM (tcgen05, BF16 in, FP32 accumulate in TMEM; plain or
-// split-K atomic epilogue) for the weight gradients, the pair features and
-// pair search, the head's loss gradient, and the small element-wise and
-// reduction kernels of training.
+// plain tensor-core GEMM (tcgen05, BF16 in, FP32 accumulate in TMEM) behind
+// the debug entry point that checks the operand layout the fused kernels use,
+// the pair features and pair search, the head's loss gradient, the ice
+// profile's prefix sums, Adam and the BF16 weight copies.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -53,7 +53,6 @@ __device__ __forceinline__ void stage_tile(unsigned char* tile, const __nv_bfloa
 
 // Two operand stages: while the tensor core works on one, the threads stage
 // the next K slice into the other.
-template <int EPI>
 __global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ uint32_t tslot;
@@ -61,10 +60,7 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
   const int BN = g.bn;
   const int stage = (kBM + BN) * kBK * 2;
   const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
-  // split K: this CTA runs K range [kb, ke)
-  const int kc = g.k_split > 1 ? ((g.K + g.k_split * kBK - 1) / (g.k_split * kBK)) * kBK : g.K;
-  const int kb = blockIdx.z * kc;
-  const int ke = (kb + kc < g.K) ? kb + kc : g.K;
+  const int kb = 0, ke = g.K;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t ncols = pow2_cols(BN);
   if (warp == 0) tc::tmem_alloc(&tslot, ncols);
@@ -135,12 +131,7 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
       for (int j = 0; j < 32; ++j) {
         const int col = n0 + c0 + j;
         if (col >= g.N || c0 + j >= BN) continue;
-        const size_t o = (size_t)row * g.ldc + col;
-        if (EPI == kEpiStoreF32) {
-          g.Cf[o] = v[j];
-        } else if (EPI == kEpiAtomicF32) {
-          atomicAdd(g.Cf + o, v[j]);
-        }
+        g.Cf[(size_t)row * g.ldc + col] = v[j];
       }
     }
   }
@@ -153,26 +144,16 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
 
 size_t gemm_smem_bytes(int bn) { return 2 * (size_t)(kBM + bn) * kBK * 2 + 1024; }
 
-cudaError_t launch_gemm(const GemmArgs& g, int epi, cudaStream_t st) {
+cudaError_t launch_gemm(const GemmArgs& g, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0 || g.K <= 0) return cudaSuccess;
-  const dim3 grid((g.M + kBM - 1) / kBM, (g.N + g.bn - 1) / g.bn, g.k_split > 1 ? g.k_split : 1);
+  const dim3 grid((g.M + kBM - 1) / kBM, (g.N + g.bn - 1) / g.bn);
   const size_t smem = gemm_smem_bytes(g.bn);
   // at least 80 KB per CTA: at most two CTAs (2 x 256 TMEM columns) per SM
   const size_t smem_req = smem < 80 * 1024 ? 80 * 1024 : smem;
-  cudaError_t e = cudaSuccess;
-#define PP_GEMM_CASE(E)                                                                          \
-  case E:                                                                                        \
-    e = cudaFuncSetAttribute(k_gemm<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_req); \
-    if (e == cudaSuccess) k_gemm<E><<<grid, 128, smem_req, st>>>(g);                             \
-    break;
-  switch (epi) {
-    PP_GEMM_CASE(kEpiStoreF32)
-    PP_GEMM_CASE(kEpiAtomicF32)
-    default:
-      return cudaErrorInvalidValue;
-  }
-#undef PP_GEMM_CASE
+  cudaError_t e = cudaFuncSetAttribute(k_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_req);
   if (e != cudaSuccess) return e;
+  k_gemm<<<grid, 128, smem_req, st>>>(g);
   return cudaGetLastError();
 }
 
@@ -306,55 +287,6 @@ __global__ void k_near_pairs(FeatGeom fg, const pp_source* src, int64_t s0, int6
 }
 
 // ----------------------------------------------------------- utilities --
-__global__ void k_transpose(const __nv_bfloat16* in, int rows, int cols, __nv_bfloat16* out) {
-  __shared__ __nv_bfloat16 t[32][33];
-  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-    const int r = r0 + i, c = c0 + threadIdx.x;
-    if (r < rows && c < cols) t[i][threadIdx.x] = in[(size_t)r * cols + c];
-  }
-  __syncthreads();
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-    const int c = c0 + i, r = r0 + threadIdx.x;
-    if (r < rows && c < cols) out[(size_t)c * rows + r] = t[threadIdx.x][i];
-  }
-}
-
-__global__ void __launch_bounds__(256) k_rowsum(const __nv_bfloat16* in, int cols, float* out) {
-  __shared__ float part[8];
-  const __nv_bfloat16* r = in + (size_t)blockIdx.x * cols;
-  float acc = 0.0f;
-  for (int c = threadIdx.x * 8; c < cols; c += blockDim.x * 8) {
-    if (c + 8 <= cols) {
-      const uint4 v = *reinterpret_cast<const uint4*>(r + c);
-      const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&v);
-#pragma unroll
-      for (int j = 0; j < 8; ++j) acc += __bfloat162float(e[j]);
-    } else {
-      for (int j = c; j < cols; ++j) acc += __bfloat162float(r[j]);
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float t = 0.0f;
-    for (int w = 0; w < 8; ++w) t += part[w];
-    out[blockIdx.x] += t;
-  }
-}
-
-__global__ void k_colsum(const __nv_bfloat16* in, int rows, int cols, float* out) {
-  const int c = blockIdx.y * blockDim.x + threadIdx.x;
-  if (c >= cols) return;
-  const int per = (rows + gridDim.x - 1) / gridDim.x;
-  const int rb = blockIdx.x * per, re = min(rows, rb + per);
-  float acc = 0.0f;
-  for (int r = rb; r < re; ++r) acc += __bfloat162float(in[(size_t)r * cols + c]);
-  atomicAdd(out + c, acc);
-}
-
 __global__ void k_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1,
                        float b2, float eps, float bc1, float bc2, __nv_bfloat16* pb) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -407,27 +339,6 @@ cudaError_t launch_near_pairs(const FeatGeom& fg, const pp_source* src, int64_t 
   const int64_t n = ns * fg.n_dom;
   if (n <= 0) return cudaSuccess;
   k_near_pairs<<<blocks_for(n, 256), 256, 0, st>>>(fg, src, s0, ns, r_max, max_out, ps, pd, count);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_transpose(const __nv_bfloat16* in, int rows, int cols, __nv_bfloat16* out,
-                             cudaStream_t st) {
-  const dim3 grid(blocks_for(cols, 32), blocks_for(rows, 32));
-  k_transpose<<<grid, dim3(32, 8), 0, st>>>(in, rows, cols, out);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_rowsum(const __nv_bfloat16* in, int rows, int cols, float* out,
-                          cudaStream_t st) {
-  if (rows <= 0 || cols <= 0) return cudaSuccess;
-  k_rowsum<<<rows, 256, 0, st>>>(in, cols, out);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_colsum(const __nv_bfloat16* in, int rows, int cols, float* out,
-                          cudaStream_t st) {
-  const int parts = rows >= 4096 ? 128 : 1;
-  k_colsum<<<dim3(parts, blocks_for(cols, 256)), 256, 0, st>>>(in, rows, cols, out);
   return cudaGetLastError();
 }
 

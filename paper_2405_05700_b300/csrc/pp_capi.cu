@@ -1270,7 +1270,7 @@ int pp_debug_gemm(pp_ctx* ctx, const uint16_t* A, const uint16_t* B, int32_t M, 
   g.swap_lbo_sbo = swap_lbo_sbo;
   g.Cf = static_cast<float*>(ctx->s_misc3.p);
   g.err = static_cast<int*>(ctx->err.p);
-  PP_CUDA(mlp::launch_gemm(g, mlp::kEpiStoreF32, st));
+  PP_CUDA(mlp::launch_gemm(g, st));
   PP_CUDA(cudaMemcpyAsync(C, ctx->s_misc3.p, c, cudaMemcpyDeviceToHost, st));
   return sync_and_check(ctx, st);
 }

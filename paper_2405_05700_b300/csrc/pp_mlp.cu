@@ -66,6 +66,7 @@ struct pp_mlp {
   unsigned char* wpack = nullptr;
   int64_t weights_version = 0, packed_version = -1;
   unsigned char* wpack_bwd = nullptr;  // transposed hidden weights for the backward kernel
+  float* dw_part = nullptr;            // per-CTA weight-gradient partial sums
   int64_t packed_bwd_version = -1;
   int exact_silu = 0;
   float2* ice_cum = nullptr;
@@ -86,22 +87,6 @@ int mfail(pp_mlp* m, int code, const std::string& msg) {
     cudaError_t _e = (expr);                                                           \
     if (_e != cudaSuccess) return mfail(m, PP_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
   } while (0)
-
-GemmArgs gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, int M, int N, int K, int* err) {
-  GemmArgs a{};
-  a.A = A;
-  a.B = B;
-  a.M = M;
-  a.N = N;
-  a.K = K;
-  a.lda = K;
-  a.ldb = K;
-  a.ldc = N;
-  a.bn = N;
-  a.k_split = 1;
-  a.err = err;
-  return a;
-}
 
 // BF16 copies of the weights from the FP32 masters.
 int refresh_bf16(pp_mlp* m, cudaStream_t st) {
@@ -147,6 +132,7 @@ int forward_train(pp_mlp* m, const __nv_bfloat16* x0, int n, cudaStream_t st) {
     a.z_out[l] = m->z[l];
     a.h_out[l] = m->h[l];
   }
+  a.x_t = reinterpret_cast<unsigned char*>(m->t2);
   PP_MLP_CUDA(launch_mlp_fused(a, false, m->sms, st));
   return PP_OK;
 }
@@ -168,39 +154,36 @@ int forward_backward(pp_mlp* m, const __nv_bfloat16* x0, const float* nph, const
   BwdArgs b{};
   b.n = n;
   b.wpack = m->wpack_bwd;
+  b.dz3_t = reinterpret_cast<unsigned char*>(m->t1);
   for (int l = 0; l < kLayers; ++l) {
     b.z[l] = m->z[l];
     b.dz[l] = m->dz[l];
   }
   b.err = m->err;
   PP_MLP_CUDA(launch_mlp_bwd(b, m->sms, st));
-  // dW_l = dz_l^T . x_l (split over the batch, summed with atomics), db_l = sum dz_l.
-  // The fused kernels left dz_0..2 and the activations h_0..2 transposed
-  // ([256][n]); dz_3 (row-major, from the head) and the features are transposed here.
-  const int ks = n >= 32768 ? 128 : (n >= 8192 ? 32 : (n >= 1024 ? 8 : 1));
+  // dW_l = dz_l^T . x_l and db_l = sum dz_l over the batch, from K-tiled
+  // operands the fused kernels left: dz_0..3, the features and h_0..2
+  auto* dz3t = reinterpret_cast<unsigned char*>(m->t1);
+  auto* x0t = reinterpret_cast<unsigned char*>(m->t2);
   for (int l = kLayers - 1; l >= 0; --l) {
-    const int in_w = l == 0 ? kIn : kHid;
-    const __nv_bfloat16* dzt = m->dz[l];
-    if (l == kLayers - 1) {
-      PP_MLP_CUDA(launch_transpose(m->dz[l], n, kHid, m->t1, st));
-      dzt = m->t1;
-      PP_MLP_CUDA(launch_colsum(m->dz[l], n, kHid, m->g + off_b(l), st));
-    } else {
-      PP_MLP_CUDA(launch_rowsum(dzt, kHid, n, m->g + off_b(l), st));
-    }
-    const __nv_bfloat16* xt = l > 0 ? m->h[l - 1] : m->t2;
-    if (l == 0) PP_MLP_CUDA(launch_transpose(x0, n, kIn, m->t2, st));
-    GemmArgs a = gemm(dzt, xt, kHid, in_w, n, m->err);
-    a.k_split = ks;
-    a.Cf = m->g + off_w(l);
-    PP_MLP_CUDA(launch_gemm(a, kEpiAtomicF32, st));
+    DwArgs d{};
+    d.a = l == kLayers - 1 ? dz3t : reinterpret_cast<const unsigned char*>(m->dz[l]);
+    d.b = l == 0 ? x0t : reinterpret_cast<const unsigned char*>(m->h[l - 1]);
+    d.n = n;
+    d.nb = l == 0 ? kIn : kHid;
+    d.dw = m->g + off_w(l);
+    d.partial = m->dw_part;
+    d.partial_cap = m->sms;
+    d.err = m->err;
+    PP_MLP_CUDA(launch_rowsum_kt(d.a, kHid, n, m->g + off_b(l), st));
+    PP_MLP_CUDA(launch_dw(d, m->sms, st));
   }
   return PP_OK;
 }
 
 int check_batch(pp_mlp* m, int64_t n, const void* d_feat) {
-  if (n < 16 || n > m->max_batch || n % 16)
-    return mfail(m, PP_EINVAL, "training batch must be a multiple of 16 in [16, max_batch]");
+  if (n < kKTile || n > m->max_batch || n % kKTile)
+    return mfail(m, PP_EINVAL, "training batch must be a multiple of 64 in [64, max_batch]");
   if (!aligned16(d_feat)) return mfail(m, PP_EINVAL, "features must be 16-byte aligned");
   return PP_OK;
 }
@@ -221,7 +204,7 @@ int mlp_sync(pp_mlp* m, cudaStream_t st) {
 extern "C" {
 
 int pp_mlp_create(pp_ctx* ctx, int32_t max_batch, int64_t max_rows, pp_mlp** out) {
-  if (!ctx || !out || max_batch < 16 || max_batch % 16 || max_rows < 1) return PP_EINVAL;
+  if (!ctx || !out || max_batch < kKTile || max_batch % kKTile || max_rows < 1) return PP_EINVAL;
   *out = nullptr;
   pp_mlp* m = new pp_mlp();
   m->ctx = ctx;
@@ -249,6 +232,8 @@ int pp_mlp_create(pp_ctx* ctx, int32_t max_batch, int64_t max_rows, pp_mlp** out
   const size_t B = (size_t)max_batch, H = (size_t)kHid;
 #define PP_A(x) \
   if (e == cudaSuccess) e = (x)
+  PP_A(cudaDeviceGetAttribute(&m->sms, cudaDevAttrMultiProcessorCount, m->view.device));
+  if (e == cudaSuccess && m->sms < 1) e = cudaErrorInvalidDevice;
   PP_A(dalloc(&m->p, kNParams));
   PP_A(dalloc(&m->g, kNParams));
   PP_A(dalloc(&m->m, kNParams));
@@ -266,11 +251,11 @@ int pp_mlp_create(pp_ctx* ctx, int32_t max_batch, int64_t max_rows, pp_mlp** out
   PP_A(dalloc(&m->err, 64));
   PP_A(dalloc(&m->wpack, packed_weight_bytes()));
   PP_A(dalloc(&m->wpack_bwd, packed_bwd_bytes()));
+  PP_A(dalloc(&m->dw_part, (size_t)m->sms * kHid * kHid));
   PP_A(dalloc(&m->ice_cum, (size_t)m->fg.L));
   m->fg.cum = m->ice_cum;
   PP_A(launch_ice_cum(m->fg, m->ice_cum, 0));
   PP_A(cudaDeviceSynchronize());
-  PP_A(cudaDeviceGetAttribute(&m->sms, cudaDevAttrMultiProcessorCount, m->view.device));
   PP_A(dalloc(&m->ps, (size_t)max_rows));
   PP_A(dalloc(&m->pd, (size_t)max_rows));
   PP_A(dalloc(&m->count, 1));
@@ -292,7 +277,7 @@ int pp_mlp_destroy(pp_mlp* m) {
   cudaSetDevice(m->view.device);
   cudaDeviceSynchronize();
   void* bufs[] = {m->p,   m->g,     m->m,         m->v,  m->t1, m->t2,    m->loss, m->err,
-                  m->wpack, m->wpack_bwd, m->ps, m->pd, m->count, m->ice_cum};
+                  m->wpack, m->wpack_bwd, m->ps, m->pd, m->count, m->ice_cum, m->dw_part};
   for (void* b : bufs) cudaFree(b);
   for (int l = 0; l < kLayers; ++l) {
     cudaFree(m->wb[l]);
