@@ -51,6 +51,15 @@ OPS_PER_CROSSING = 14     # one more layer visited inside a step
 OPS_PER_BIRTH = 180       # Philox block, 4 uniforms, source lookup, point, direction,
                           # -ln u, starting layer
 LANES_PER_SM = 128        # 4 schedulers x 32 lanes issue one instruction per clock
+# The same counts split by pipe (integer / FP32 / special-function unit):
+#   step:     Philox 98, uniforms 9, layer index 4, cell index 8 integer; reciprocal of the
+#             direction's z (layer boundary), log, world-exit sqrt, HG reciprocal, sin theta
+#             sqrt, sin, cos, two rsqrt of the rotation = 9 SFU; the remaining 82 FP32
+#   crossing: 3 integer (next layer, its table row), 11 FP32
+#   birth:    Philox 98, uniforms 12, source lookup 20, starting layer 4 integer; sin, cos,
+#             rsqrt of the cone rotation and the log of -ln u = 4 SFU; the remaining 42 FP32
+FP32_OPS = {"step": 82, "crossing": 11, "birth": 42}
+SFU_OPS = {"step": 9, "crossing": 0, "birth": 4}
 
 # DRAM bytes per launch from ncu captures of the current kernels: the propagation
 # launch of the 1000-event step (captured on its first 200 events, scaled by sources),
@@ -607,6 +616,8 @@ def run_ours(args):
         pass
     props = torch.cuda.get_device_properties(dev)
     ck = clocks.summary()
+    pipes = pipe_utilisation(dev, kern_ms / max(1, n_timed), steps_per_launch,
+                             cross_per_launch, births_per_launch)
     sm_max = ck["sm_max_mhz"] or peaks.get("sm_max_mhz") or 2032.0
     peak_gops = props.multi_processor_count * LANES_PER_SM * sm_max * 1e6 / 1e9
     ops = (OPS_PER_STEP * steps_per_launch + OPS_PER_CROSSING * cross_per_launch
@@ -639,6 +650,7 @@ def run_ours(args):
                      "crossings_per_launch": cross_per_launch,
                      "string_search_frac": slow_n / max(1, steps_n)},
         "autotune": {"best": tuned[0], "best_ms": tuned[1]} if tuned else None,
+        "pipes": pipes,
         "steps_per_s": steps_per_launch / (kern_avg_ms * 1e-3),
         "records": records,
         "large_event": large,
@@ -655,6 +667,23 @@ def run_ours(args):
     prop.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def pipe_utilisation(dev, kernel_ms, steps, crossings, births):
+    """FP32 and SFU lane operations of the propagation launch per second,
+    against the device's measured FMA and lg2 rates (pp_measure_issue_rate,
+    run after the timed region)."""
+    from paper_2405_05700_b300 import pp
+    units = {"step": steps, "crossing": crossings, "birth": births}
+    fp32 = sum(FP32_OPS[k] * units[k] for k in units) / (kernel_ms * 1e-3) / 1e9
+    sfu = sum(SFU_OPS[k] * units[k] for k in units) / (kernel_ms * 1e-3) / 1e9
+    index = dev.index if dev.index is not None else 0
+    fma_rate, fma_ms = pp.pp_measure_issue_rate(index, pp.PP_ISSUE_FP32_FMA)
+    sfu_rate, sfu_ms = pp.pp_measure_issue_rate(index, pp.PP_ISSUE_SFU_LG2)
+    return {"fp32_gops": fp32, "fp32_peak_gops": fma_rate / 1e9, "fp32_frac": fp32 / (fma_rate / 1e9),
+            "sfu_gops": sfu, "sfu_peak_gops": sfu_rate / 1e9, "sfu_frac": sfu / (sfu_rate / 1e9),
+            "peak_basis": "measured: fmaf chains and lg2.approx chains on every SM "
+                          f"({fma_ms:.1f} ms, {sfu_ms:.1f} ms launches)"}
 
 
 def main():

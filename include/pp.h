@@ -449,9 +449,10 @@ int pp_mlp_dom_sums(pp_mlp* mlp, const pp_source* d_src, int64_t n_src, const fl
                     float r_max, double* d_dom_sums, float* d_lambda, void* stream);
 
 /* The (source, DOM) pairs closer than r_max (segment midpoint to DOM centre),
- * in unspecified order: the first max_out go to d_pair_src / d_pair_dom, and
+ * in (source, DOM) order: the first max_out go to d_pair_src / d_pair_dom, and
  * *h_count receives how many there are (may exceed max_out).  Synchronous, on
- * the context's stream.  Errors: PP_EINVAL, PP_ECUDA. */
+ * the context's stream; grows a scratch of 12 bytes per 2048 candidate pairs
+ * (n_src x DOMs) when needed.  Errors: PP_EINVAL, PP_ENOMEM, PP_ECUDA. */
 int pp_mlp_near_pairs(pp_mlp* mlp, const pp_source* d_src, int64_t n_src, float r_max,
                       int64_t max_out, int32_t* d_pair_src, int32_t* d_pair_dom,
                       uint64_t* h_count);
@@ -501,6 +502,23 @@ int pp_debug_gemm(pp_ctx* ctx, const uint16_t* A, const uint16_t* B, int32_t M, 
  *   dom[n]      out: DOM index or -1;  t[n] out: distance (inf when none) */
 int pp_debug_first_hit(pp_ctx* ctx, const float* seg, int64_t n, int32_t mode, int32_t* dom,
                        float* t);
+
+/* ---- measured issue rates ------------------------------------------------- */
+
+/* Measured lane-operation rate of one pipe of `device`, the denominator of the
+ * propagation kernel's FP32 and SFU utilisation.  A kernel that fills every SM
+ * runs independent chains of one instruction per thread, once to warm up and
+ * once timed with CUDA events:
+ *   PP_ISSUE_FP32_FMA  fmaf chains (one FMA = one lane operation)
+ *   PP_ISSUE_SFU_LG2   lg2.approx chains (the special-function unit)
+ *   lane_ops_per_s     out: lane operations per second over the whole device
+ *   ms                 out: duration of the timed launch (may be NULL)
+ * Takes about 0.1 s; allocates 4 bytes and its own stream.  The rate follows
+ * the SM clock of the moment.  Errors: PP_EINVAL (unknown kind, NULL output,
+ * bad device), PP_ENODEV, PP_ENOMEM, PP_ECUDA. */
+#define PP_ISSUE_FP32_FMA 0
+#define PP_ISSUE_SFU_LG2 1
+int pp_measure_issue_rate(int32_t device, int32_t kind, double* lane_ops_per_s, double* ms);
 
 #ifdef __cplusplus
 }

@@ -41,24 +41,35 @@ struct FeatGeom {
 // fg.cum from fg.layer (one thread; L is small).
 cudaError_t launch_ice_cum(const FeatGeom& fg, float2* cum, cudaStream_t st);
 
-// Features of pairs (source s, DOM d) as BF16 [n][16].
+// Features of pairs (source s, DOM d) as BF16 [n][32].
 cudaError_t launch_features(const FeatGeom& fg, const pp_source* src, const int32_t* pair_src,
                             const int32_t* pair_dom, int64_t n, __nv_bfloat16* feat,
                             cudaStream_t st);
 
 // Head with loss and gradients: Poisson NLL sum(lambda - n ln lambda) / n_total;
-// dZ4 = dL/dz * w5 * silu'(z4) (BF16), dw5 += sum dL/dz * h, db5 += sum dL/dz,
-// loss (double) += the batch's loss sum / n_total.
+// dZ4 = dL/dz * w5 * silu'(z4) (BF16); dw5b5[0..255] += sum dL/dz * h,
+// dw5b5[256] += sum dL/dz, loss (double) += the batch's loss sum / n_total.
+// Per-block partial sums go to part[ceil(n / 64)][257] and lpart[ceil(n / 64)]
+// (part_rows rows available) and are added in block order: deterministic.
 cudaError_t launch_head_backward(const __nv_bfloat16* h, const __nv_bfloat16* z4, const float* w5,
                                  const float* b5, const float* nph, const float* cnt, int64_t n,
-                                 float inv_n, __nv_bfloat16* dz4, float* dw5, float* db5,
-                                 double* loss, cudaStream_t st);
+                                 float inv_n, __nv_bfloat16* dz4, float* dw5b5, double* loss,
+                                 float* part, double* lpart, int64_t part_rows, cudaStream_t st);
+constexpr int kHeadPartCols = 257;  // W5 and b5
+constexpr int kHeadPartPairs = 64;  // pairs per partial-sum row
 
-// Pairs of sources [s0, s0+ns) x DOMs within r_max into (ps, pd); *count += all of them
-// (only the first max_out are written).
+// Pairs of sources [s0, s0+ns) x DOMs within r_max into (ps, pd) in any order;
+// *count += all of them (only the first max_out are written).
 cudaError_t launch_near_pairs(const FeatGeom& fg, const pp_source* src, int64_t s0, int64_t ns,
                               float r_max, int64_t max_out, int32_t* ps, int32_t* pd,
                               unsigned long long* count, cudaStream_t st);
+// The same for sources [0, ns) in (source, DOM) order; *count = all of them.
+// Scratch: bcount[nb], boff[nb] with nb = near_pairs_ordered_blocks(ns * n_dom).
+int64_t near_pairs_ordered_blocks(int64_t n_candidates);
+cudaError_t launch_near_pairs_ordered(const FeatGeom& fg, const pp_source* src, int64_t ns,
+                                      float r_max, int64_t max_out, int32_t* ps, int32_t* pd,
+                                      unsigned long long* count, uint32_t* bcount,
+                                      unsigned long long* boff, cudaStream_t st);
 // Fused inference (mlp_fused.cu): rows are either pairs (features computed
 // in the kernel; lambda summed per DOM and/or stored as [source][DOM]) or
 // precomputed BF16 feature rows (lambda per row).  All feature and pair

@@ -193,15 +193,22 @@ __device__ __forceinline__ float head_z(const __nv_bfloat16* hp, const float* w5
   return acc + b5;
 }
 
-constexpr int kHeadPairs = 64;  // pairs per block of the head backward
+constexpr int kHeadPairs = kHeadPartPairs;  // pairs per block of the head backward
+constexpr int kHeadCols = kHeadPartCols;    // W5 and b5: one partial-sum row per block
+static_assert(kHeadCols == kHid + 1, "W5 and b5");
 
+// Head backward on a block of kHeadPairs pairs: dz4, and the block's partial
+// sums of dL/dW5, dL/db5 (part[block][257]) and of the loss (lpart[block]).
+// Every sum runs in a fixed order, so the gradients do not depend on timing.
 __global__ void __launch_bounds__(256) k_head_bwd(const __nv_bfloat16* h, const __nv_bfloat16* z4,
                                                   const float* w5, const float* b5,
                                                   const float* nph, const float* cnt, int64_t n,
-                                                  float inv_n, __nv_bfloat16* dz4, float* dw5,
-                                                  float* db5, double* loss) {
+                                                  float inv_n, __nv_bfloat16* dz4, float* part,
+                                                  double* lpart) {
   __shared__ float s_g[kHeadPairs];
   __shared__ float s_w5[kHid];
+  __shared__ float s_gsum[8];
+  __shared__ double s_lsum[8];
   const int64_t p0 = (int64_t)blockIdx.x * kHeadPairs;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   s_w5[threadIdx.x] = w5[threadIdx.x];
@@ -225,6 +232,10 @@ __global__ void __launch_bounds__(256) k_head_bwd(const __nv_bfloat16* h, const 
       gsum += g;
     }
   }
+  if (lane == 0) {
+    s_gsum[warp] = gsum;
+    s_lsum[warp] = lsum;
+  }
   __syncthreads();
   const int j = threadIdx.x;
   float acc = 0.0f;
@@ -238,16 +249,85 @@ __global__ void __launch_bounds__(256) k_head_bwd(const __nv_bfloat16* h, const 
     const float sg = 1.0f / (1.0f + __expf(-zz));
     dz4[o] = __float2bfloat16_rn(g * s_w5[j] * sg * (1.0f + zz * (1.0f - sg)));
   }
-  atomicAdd(dw5 + j, acc);
-  if (lane == 0) {
-    if (gsum != 0.0f) atomicAdd(db5, gsum);
-    if (lsum != 0.0) atomicAdd(loss, lsum);
+  float* row = part + (size_t)blockIdx.x * kHeadCols;
+  row[j] = acc;
+  if (j == 0) {
+    float gs = 0.0f;
+    double ls = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      gs += s_gsum[w];
+      ls += s_lsum[w];
+    }
+    row[kHid] = gs;
+    lpart[blockIdx.x] = ls;
   }
 }
 
-// Pairs of sources [s0, s0 + ns) x all DOMs whose distance (segment midpoint
-// to DOM centre, as in the features) is at most r_max, appended in any order
-// (one atomic per warp); at most max_out are written, *count counts them all.
+// dW5, db5 (257 values) += the column sums of part[parts][257]; *loss += the
+// sum of lpart[parts].  Blocks 0..8 take 32 columns each: warp w sums rows
+// w, w + 8, ..., and the eight warp sums are added in warp order.  Block 9
+// sums the loss partials the same way (256 threads, then lanes and warps in a
+// fixed tree).  Every sum has a fixed order: the result does not depend on
+// timing.
+constexpr int kHeadReduceColBlocks = (kHeadCols + 31) / 32;
+
+__global__ void __launch_bounds__(256) k_head_reduce(const float* part, const double* lpart,
+                                                     int parts, float* dw5b5, double* loss) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (blockIdx.x < kHeadReduceColBlocks) {
+    __shared__ float ws[8][32];
+    const int col = blockIdx.x * 32 + lane;
+    float acc = 0.0f;
+    if (col < kHeadCols) {
+#pragma unroll 8
+      for (int c = warp; c < parts; c += 8) acc += part[(size_t)c * kHeadCols + col];
+    }
+    ws[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0 && col < kHeadCols) {
+      float t = 0.0f;
+      for (int w = 0; w < 8; ++w) t += ws[w][lane];
+      dw5b5[col] += t;
+    }
+  } else {
+    __shared__ double wl[8];
+    double acc = 0.0;
+    for (int c = threadIdx.x; c < parts; c += 256) acc += lpart[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) wl[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < 8; ++w) t += wl[w];
+      *loss += t;
+    }
+  }
+}
+
+// Is candidate i = (source s0 + i / n_dom, DOM i % n_dom) within r_max?  The
+// distance is from the segment's midpoint to the DOM centre, as in the features.
+__device__ __forceinline__ bool pair_near(const FeatGeom& fg, const pp_source* src, int64_t s0,
+                                          int64_t i, float r_max, int64_t& s, int& d) {
+  s = s0 + i / fg.n_dom;
+  d = (int)(i % fg.n_dom);
+  const pp_source q = src[s];
+  float dx = q.dx, dy = q.dy, dz = q.dz;
+  const float nn = sqrtf(dx * dx + dy * dy + dz * dz);
+  if (nn > 0.0f) {
+    dx /= nn;
+    dy /= nn;
+    dz /= nn;
+  }
+  const float h = 0.5f * q.length;
+  const float4 c = fg.dom[d];
+  const float ex = c.x - (q.x + h * dx), ey = c.y - (q.y + h * dy), ez = c.z - (q.z + h * dz);
+  return sqrtf(ex * ex + ey * ey + ez * ez) <= r_max;
+}
+
+// Pairs of sources [s0, s0 + ns) x all DOMs within r_max, appended in any
+// order (one atomic per warp); at most max_out are written, *count counts
+// them all.  The per-DOM sums of the inference do not depend on the order.
 __global__ void k_near_pairs(FeatGeom fg, const pp_source* src, int64_t s0, int64_t ns,
                              float r_max, int64_t max_out, int32_t* ps, int32_t* pd,
                              unsigned long long* count) {
@@ -255,22 +335,7 @@ __global__ void k_near_pairs(FeatGeom fg, const pp_source* src, int64_t s0, int6
   bool near = false;
   int64_t s = 0;
   int d = 0;
-  if (i < ns * fg.n_dom) {
-    s = s0 + i / fg.n_dom;
-    d = (int)(i % fg.n_dom);
-    const pp_source q = src[s];
-    float dx = q.dx, dy = q.dy, dz = q.dz;
-    const float nn = sqrtf(dx * dx + dy * dy + dz * dz);
-    if (nn > 0.0f) {
-      dx /= nn;
-      dy /= nn;
-      dz /= nn;
-    }
-    const float h = 0.5f * q.length;
-    const float4 c = fg.dom[d];
-    const float ex = c.x - (q.x + h * dx), ey = c.y - (q.y + h * dy), ez = c.z - (q.z + h * dz);
-    near = sqrtf(ex * ex + ey * ey + ez * ez) <= r_max;
-  }
+  if (i < ns * fg.n_dom) near = pair_near(fg, src, s0, i, r_max, s, d);
   const unsigned mask = __ballot_sync(0xffffffffu, near);
   if (!mask) return;
   const int lane = threadIdx.x & 31;
@@ -283,6 +348,107 @@ __global__ void k_near_pairs(FeatGeom fg, const pp_source* src, int64_t s0, int6
       ps[o] = (int32_t)s;
       pd[o] = d;
     }
+  }
+}
+
+// The same list in (source, DOM) order: a stable compaction in three passes.
+// A block covers kNearTile consecutive candidates, kNearItems per thread.
+constexpr int kNearThreads = 256;
+constexpr int kNearItems = 8;
+constexpr int kNearTile = kNearThreads * kNearItems;
+constexpr int kNearScanThreads = 1024;
+
+// Bit j of the result: candidate first + j is a pair within r_max.
+__device__ __forceinline__ uint32_t near_bits(const FeatGeom& fg, const pp_source* src, int64_t s0,
+                                              int64_t first, int64_t total, float r_max) {
+  uint32_t bits = 0;
+#pragma unroll
+  for (int j = 0; j < kNearItems; ++j) {
+    const int64_t i = first + j;
+    int64_t s;
+    int d;
+    if (i < total && pair_near(fg, src, s0, i, r_max, s, d)) bits |= 1u << j;
+  }
+  return bits;
+}
+
+// Exclusive prefix of v over the block's threads (256); *total = the sum.
+__device__ __forceinline__ uint32_t block_excl_256(uint32_t v, uint32_t* ws, uint32_t& total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[warp] = x;
+  __syncthreads();
+  uint32_t before = 0;
+  total = 0;
+  for (int w = 0; w < kNearThreads / 32; ++w) {
+    if (w < warp) before += ws[w];
+    total += ws[w];
+  }
+  return before + x - v;
+}
+
+__global__ void __launch_bounds__(kNearThreads) k_near_count(FeatGeom fg, const pp_source* src,
+                                                             int64_t s0, int64_t total,
+                                                             float r_max, uint32_t* bcount) {
+  __shared__ uint32_t ws[kNearThreads / 32];
+  const int64_t first = (int64_t)blockIdx.x * kNearTile + (int64_t)threadIdx.x * kNearItems;
+  const uint32_t c = __popc(near_bits(fg, src, s0, first, total, r_max));
+  uint32_t sum;
+  block_excl_256(c, ws, sum);
+  if (threadIdx.x == 0) bcount[blockIdx.x] = sum;
+}
+
+// One block: boff[b] = sum of bcount[0..b), *count = the sum of all.
+__global__ void __launch_bounds__(kNearScanThreads) k_near_scan(const uint32_t* bcount, int64_t nb,
+                                                                unsigned long long* boff,
+                                                                unsigned long long* count) {
+  __shared__ unsigned long long ws[kNearScanThreads];
+  const int t = threadIdx.x;
+  const int64_t seg = (nb + kNearScanThreads - 1) / kNearScanThreads;
+  const int64_t b0 = t * seg, b1 = b0 + seg < nb ? b0 + seg : nb;
+  unsigned long long mine = 0;
+  for (int64_t b = b0; b < b1; ++b) mine += bcount[b];
+  ws[t] = mine;
+  __syncthreads();
+  // Hillis-Steele inclusive scan over the 1024 segment sums
+  for (int o = 1; o < kNearScanThreads; o <<= 1) {
+    const unsigned long long y = t >= o ? ws[t - o] : 0ull;
+    __syncthreads();
+    ws[t] += y;
+    __syncthreads();
+  }
+  unsigned long long run = ws[t] - mine;
+  for (int64_t b = b0; b < b1; ++b) {
+    boff[b] = run;
+    run += bcount[b];
+  }
+  if (t == kNearScanThreads - 1) *count = ws[t];
+}
+
+__global__ void __launch_bounds__(kNearThreads) k_near_write(FeatGeom fg, const pp_source* src,
+                                                             int64_t s0, int64_t total,
+                                                             float r_max,
+                                                             const unsigned long long* boff,
+                                                             int64_t max_out, int32_t* ps,
+                                                             int32_t* pd) {
+  __shared__ uint32_t ws[kNearThreads / 32];
+  const int64_t first = (int64_t)blockIdx.x * kNearTile + (int64_t)threadIdx.x * kNearItems;
+  uint32_t bits = near_bits(fg, src, s0, first, total, r_max);
+  uint32_t sum;
+  unsigned long long o = boff[blockIdx.x] + block_excl_256(__popc(bits), ws, sum);
+  while (bits) {
+    const int j = __ffs(bits) - 1;
+    bits &= bits - 1;
+    if ((int64_t)o < max_out) {
+      ps[o] = (int32_t)(s0 + (first + j) / fg.n_dom);
+      pd[o] = (int32_t)((first + j) % fg.n_dom);
+    }
+    ++o;
   }
 }
 
@@ -325,11 +491,13 @@ cudaError_t launch_features(const FeatGeom& fg, const pp_source* src, const int3
 
 cudaError_t launch_head_backward(const __nv_bfloat16* h, const __nv_bfloat16* z4, const float* w5,
                                  const float* b5, const float* nph, const float* cnt, int64_t n,
-                                 float inv_n, __nv_bfloat16* dz4, float* dw5, float* db5,
-                                 double* loss, cudaStream_t st) {
+                                 float inv_n, __nv_bfloat16* dz4, float* dw5b5, double* loss,
+                                 float* part, double* lpart, int64_t part_rows, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  k_head_bwd<<<blocks_for(n, kHeadPairs), 256, 0, st>>>(h, z4, w5, b5, nph, cnt, n, inv_n, dz4,
-                                                        dw5, db5, loss);
+  const int64_t blocks = (n + kHeadPairs - 1) / kHeadPairs;
+  if (blocks > part_rows) return cudaErrorInvalidValue;
+  k_head_bwd<<<(unsigned)blocks, 256, 0, st>>>(h, z4, w5, b5, nph, cnt, n, inv_n, dz4, part, lpart);
+  k_head_reduce<<<kHeadReduceColBlocks + 1, 256, 0, st>>>(part, lpart, (int)blocks, dw5b5, loss);
   return cudaGetLastError();
 }
 
@@ -339,6 +507,24 @@ cudaError_t launch_near_pairs(const FeatGeom& fg, const pp_source* src, int64_t 
   const int64_t n = ns * fg.n_dom;
   if (n <= 0) return cudaSuccess;
   k_near_pairs<<<blocks_for(n, 256), 256, 0, st>>>(fg, src, s0, ns, r_max, max_out, ps, pd, count);
+  return cudaGetLastError();
+}
+
+int64_t near_pairs_ordered_blocks(int64_t n_candidates) {
+  return (n_candidates + kNearTile - 1) / kNearTile;
+}
+
+cudaError_t launch_near_pairs_ordered(const FeatGeom& fg, const pp_source* src, int64_t ns,
+                                      float r_max, int64_t max_out, int32_t* ps, int32_t* pd,
+                                      unsigned long long* count, uint32_t* bcount,
+                                      unsigned long long* boff, cudaStream_t st) {
+  const int64_t n = ns * fg.n_dom;
+  if (n <= 0) return cudaSuccess;
+  const int64_t nb = near_pairs_ordered_blocks(n);
+  if (nb > 0x7fffffff) return cudaErrorInvalidValue;
+  k_near_count<<<(unsigned)nb, kNearThreads, 0, st>>>(fg, src, 0, n, r_max, bcount);
+  k_near_scan<<<1, kNearScanThreads, 0, st>>>(bcount, nb, boff, count);
+  k_near_write<<<(unsigned)nb, kNearThreads, 0, st>>>(fg, src, 0, n, r_max, boff, max_out, ps, pd);
   return cudaGetLastError();
 }
 

@@ -67,12 +67,18 @@ struct pp_mlp {
   int64_t weights_version = 0, packed_version = -1;
   unsigned char* wpack_bwd = nullptr;  // transposed hidden weights for the backward kernel
   float* dw_part = nullptr;            // per-CTA weight-gradient partial sums
+  float* head_part = nullptr;          // head backward: per-block partial sums of dW5, db5
+  double* head_lpart = nullptr;        // and of the loss
   int64_t packed_bwd_version = -1;
   int exact_silu = 0;
   float2* ice_cum = nullptr;
   int sms = 0;
   int32_t *ps = nullptr, *pd = nullptr;
   unsigned long long* count = nullptr;
+  // ordered pair search: per-block counts and offsets (grown on demand)
+  uint32_t* near_bcount = nullptr;
+  unsigned long long* near_boff = nullptr;
+  int64_t near_cap = 0;
 };
 
 namespace {
@@ -143,9 +149,10 @@ int forward_backward(pp_mlp* m, const __nv_bfloat16* x0, const float* nph, const
   int rc;
   PP_MLP_CUDA(cudaMemsetAsync(m->g, 0, sizeof(float) * kNParams, st));
   if ((rc = forward_train(m, x0, n, st))) return rc;
+  static_assert(kOffB5 == kOffW5 + kHid, "W5 and b5 are adjacent");
   PP_MLP_CUDA(launch_head_backward(m->h[3], m->z[3], m->p + kOffW5, m->p + kOffB5, nph, cnt, n,
-                                   1.0f / (float)n, m->dz[3], m->g + kOffW5, m->g + kOffB5,
-                                   m->loss, st));
+                                   1.0f / (float)n, m->dz[3], m->g + kOffW5, m->loss, m->head_part,
+                                   m->head_lpart, m->max_batch / kHeadPartPairs, st));
   // dz_{l-1} = (dz_l . W_l) * silu'(z_{l-1}) for l = 3, 2, 1: one fused kernel
   if (m->packed_bwd_version != m->weights_version) {
     PP_MLP_CUDA(launch_pack_bwd(m->wb, m->wpack_bwd, st));
@@ -252,6 +259,8 @@ int pp_mlp_create(pp_ctx* ctx, int32_t max_batch, int64_t max_rows, pp_mlp** out
   PP_A(dalloc(&m->wpack, packed_weight_bytes()));
   PP_A(dalloc(&m->wpack_bwd, packed_bwd_bytes()));
   PP_A(dalloc(&m->dw_part, (size_t)m->sms * kHid * kHid));
+  PP_A(dalloc(&m->head_part, (B / kHeadPartPairs) * kHeadPartCols));
+  PP_A(dalloc(&m->head_lpart, B / kHeadPartPairs));
   PP_A(dalloc(&m->ice_cum, (size_t)m->fg.L));
   m->fg.cum = m->ice_cum;
   PP_A(launch_ice_cum(m->fg, m->ice_cum, 0));
@@ -277,7 +286,8 @@ int pp_mlp_destroy(pp_mlp* m) {
   cudaSetDevice(m->view.device);
   cudaDeviceSynchronize();
   void* bufs[] = {m->p,   m->g,     m->m,         m->v,  m->t1, m->t2,    m->loss, m->err,
-                  m->wpack, m->wpack_bwd, m->ps, m->pd, m->count, m->ice_cum, m->dw_part};
+                  m->wpack, m->wpack_bwd, m->ps, m->pd, m->count, m->ice_cum, m->dw_part,
+                  m->head_part, m->head_lpart, m->near_bcount, m->near_boff};
   for (void* b : bufs) cudaFree(b);
   for (int l = 0; l < kLayers; ++l) {
     cudaFree(m->wb[l]);
@@ -455,9 +465,24 @@ int pp_mlp_near_pairs(pp_mlp* m, const pp_source* d_src, int64_t n_src, float r_
     return PP_EINVAL;
   PP_MLP_CUDA(cudaSetDevice(m->view.device));
   cudaStream_t st = m->view.stream;
+  const int64_t nb = near_pairs_ordered_blocks(n_src * (int64_t)m->fg.n_dom);
+  if (nb > m->near_cap) {
+    PP_MLP_CUDA(cudaStreamSynchronize(st));
+    cudaFree(m->near_bcount);
+    cudaFree(m->near_boff);
+    m->near_bcount = nullptr;
+    m->near_boff = nullptr;
+    m->near_cap = 0;
+    if (dalloc(&m->near_bcount, (size_t)nb) != cudaSuccess ||
+        dalloc(&m->near_boff, (size_t)nb) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return mfail(m, PP_ENOMEM, "pair search scratch");
+    }
+    m->near_cap = nb;
+  }
   PP_MLP_CUDA(cudaMemsetAsync(m->count, 0, sizeof(unsigned long long), st));
-  PP_MLP_CUDA(launch_near_pairs(m->fg, d_src, 0, n_src, r_max, max_out, d_pair_src, d_pair_dom,
-                                m->count, st));
+  PP_MLP_CUDA(launch_near_pairs_ordered(m->fg, d_src, n_src, r_max, max_out, d_pair_src,
+                                        d_pair_dom, m->count, m->near_bcount, m->near_boff, st));
   unsigned long long c = 0;
   PP_MLP_CUDA(cudaMemcpyAsync(&c, m->count, sizeof(c), cudaMemcpyDeviceToHost, st));
   PP_MLP_CUDA(cudaStreamSynchronize(st));

@@ -98,6 +98,7 @@ _SIGS = {
     "pp_debug_first_hit": [_vp, _vp, _i64, _i32, _vp, _vp],
     "pp_debug_gemm": [_vp, _vp, _vp, _i32, _i32, _i32, _i32, _vp],
     "pp_debug_scatter": [_vp, _vp, _vp, _vp, _i64],
+    "pp_measure_issue_rate": [_i32, _i32, _vp, _vp],
 }
 EXPORTS = tuple(_SIGS) + ("pp_last_error", "pp_strerror", "pp_server_last_error",
                           "pp_mlp_last_error")
@@ -307,6 +308,18 @@ def pp_debug_scatter(ctx, dir, words, out, n):
 
 def pp_debug_gemm(ctx, A, B, M, N, K, swap_lbo_sbo, C):
     return _call("pp_debug_gemm", ctx, _ptr(A), _ptr(B), M, N, K, swap_lbo_sbo, _ptr(C))
+
+
+PP_ISSUE_FP32_FMA, PP_ISSUE_SFU_LG2 = 0, 1
+
+
+def pp_measure_issue_rate(device, kind):
+    """(lane operations per second, timed launch in ms) of one pipe."""
+    rate, ms = C.c_double(), C.c_double()
+    rc = _lib.pp_measure_issue_rate(device, kind, C.byref(rate), C.byref(ms))
+    if rc:
+        raise PPError(rc, f"pp_measure_issue_rate: {pp_strerror(rc)}")
+    return rate.value, ms.value
 
 
 def bf16_bits(x) -> np.ndarray:

@@ -70,3 +70,9 @@ def test_source_struct_layout_matches_workloads(lib):
 
 def test_oracle_library_loads(orc):
     assert orc.lib() is not None
+
+
+def test_issue_rate_probe_checks_its_arguments(lib):
+    rate = ctypes.c_double()
+    assert lib._lib.pp_measure_issue_rate(0, 7, ctypes.byref(rate), None) == lib.PP_EINVAL
+    assert lib._lib.pp_measure_issue_rate(0, lib.PP_ISSUE_FP32_FMA, None, None) == lib.PP_EINVAL

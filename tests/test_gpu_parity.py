@@ -537,3 +537,20 @@ def test_sources_outside_the_world_and_the_ice_table(full, tiny, orc):
     scale = np.maximum(np.abs(tr_o[both]), 1.0)
     assert np.all(np.abs(tr_g[both] - tr_o[both]) <= 1e-4 * scale + 1e-4)
     assert (out_g != out_o).mean() <= 2e-2
+
+
+def test_measured_issue_rates_are_physical(pp):
+    """The FMA probe reaches a large part of, and never exceeds, 128 lanes per
+    SM and clock at the maximum SM clock; the SFU runs far below it."""
+    import torch
+    props = torch.cuda.get_device_properties(0)
+    import subprocess
+    out = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits",
+                          "-i", "0"], capture_output=True, text=True)
+    max_mhz = float(out.stdout.split()[0]) if out.returncode == 0 and out.stdout.strip() else 2032.0
+    bound = props.multi_processor_count * 128 * max_mhz * 1e6
+    fma, fma_ms = pp.pp_measure_issue_rate(0, pp.PP_ISSUE_FP32_FMA)
+    sfu, sfu_ms = pp.pp_measure_issue_rate(0, pp.PP_ISSUE_SFU_LG2)
+    assert 0.3 * bound < fma <= 1.02 * bound, (fma, bound)
+    assert 0.01 * bound < sfu <= 0.5 * fma, (sfu, fma)
+    assert fma_ms > 1.0 and sfu_ms > 1.0

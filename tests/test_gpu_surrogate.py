@@ -172,6 +172,34 @@ def test_training_on_propagator_counts_lowers_loss(pp, prop, mlp):
     torch.cuda.synchronize()
 
 
+def test_training_is_bit_reproducible(pp, prop, mlp):
+    """Every gradient sum runs in a fixed order (no floating-point atomics), so
+    the same data, initial parameters and batch order give the same parameters
+    bit for bit, and so does one gradient evaluation repeated."""
+    import torch
+    from paper_2405_05700_b300 import surrogate
+    data = surrogate.make_training_set(prop, mlp, n_sources=200, photons=20_000, r_max=200.0,
+                                       seed=2)
+    n = 4096
+    grads = []
+    for _ in range(2):
+        mlp.set_params(pp.mlp_init_params(4))
+        g = np.zeros(pp.PP_MLP_N_PARAMS, np.float32)
+        loss = np.zeros(1)
+        pp.pp_mlp_gradients(mlp.handle, data.feat[:n].contiguous(), data.nph[:n].contiguous(),
+                            data.counts[:n].contiguous(), n, g, loss)
+        grads.append((g, loss[0]))
+    assert np.array_equal(grads[0][0], grads[1][0]) and grads[0][1] == grads[1][1]
+    runs = []
+    for _ in range(2):
+        mlp.set_params(pp.mlp_init_params(4))
+        losses = surrogate.train(mlp, data, epochs=2, batch=n, lr=2e-3, seed=5)
+        runs.append((mlp.get_params(), losses))
+    assert np.array_equal(runs[0][0], runs[1][0])
+    assert runs[0][1] == runs[1][1]
+    torch.cuda.synchronize()
+
+
 def test_near_pairs_match_brute_force(pp, prop, mlp):
     import torch
     geom = W.geometry_full()
@@ -184,8 +212,10 @@ def test_near_pairs_match_brute_force(pp, prop, mlp):
     ps = torch.zeros(n, dtype=torch.int32, device="cuda")
     pd = torch.zeros(n, dtype=torch.int32, device="cuda")
     assert pp.pp_mlp_near_pairs(mlp.handle, d_src, len(src), r_max, n, ps, pd) == n
-    got = set(zip(ps.cpu().numpy().tolist(), pd.cpu().numpy().tolist()))
-    assert len(got) == n                      # no pair twice
+    ps_h, pd_h = ps.cpu().numpy().astype(np.int64), pd.cpu().numpy().astype(np.int64)
+    key = ps_h * geom.n_dom + pd_h
+    assert np.all(np.diff(key) > 0)           # (source, DOM) order, no pair twice
+    got = set(zip(ps_h.tolist(), pd_h.tolist()))
     d = np.stack([src["dx"], src["dy"], src["dz"]], 1).astype(np.float64)
     d /= np.linalg.norm(d, axis=1, keepdims=True)
     mid = np.stack([src["x"], src["y"], src["z"]], 1) + 0.5 * src["length"][:, None] * d
@@ -193,8 +223,13 @@ def test_near_pairs_match_brute_force(pp, prop, mlp):
     inside = set(zip(*np.nonzero(r <= r_max - 1e-3)))
     border = set(zip(*np.nonzero(np.abs(r - r_max) < 1e-3)))
     assert inside <= got and got <= inside | border
-    # a short output buffer receives a prefix, the count stays the total
+    # a short output buffer receives the first pairs, the count stays the total
+    ps.zero_()
+    pd.zero_()
     assert pp.pp_mlp_near_pairs(mlp.handle, d_src, len(src), r_max, 10, ps, pd) == n
+    assert np.array_equal(ps.cpu().numpy()[:10], ps_h[:10])
+    assert np.array_equal(pd.cpu().numpy()[:10], pd_h[:10])
+    assert not ps.cpu().numpy()[10:].any()
 
 
 def test_dom_sums_match_oracle(pp, prop, mlp):
