@@ -48,6 +48,9 @@ constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kThreads = kEpiThreads + 64;
 constexpr int kProducerWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1;
 constexpr int kColsPerWarp = kHid / 2;
+// columns per TMEM load in the forward epilogue: 16 (two register sets of 16
+// leave the compiler room to overlap the conversions; 32 were 1.4 % slower)
+constexpr int kEpiCols = 16;
 // 18 warps: two of the four schedulers hold 5 warps, whose registers come from
 // that scheduler's 16K, so a thread gets at most 96 registers
 constexpr uint32_t kWaitTries = 1u << 22;
@@ -77,6 +80,8 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 }
 
 __device__ __forceinline__ float silu_exact(float z) { return z / (1.0f + __expf(-z)); }
+
+__device__ __forceinline__ void epi_ld(uint32_t taddr, uint32_t (&r)[16]) { tc::tmem_ld16_nowait(taddr, r); }
 
 // kTrain: rows mode for training -- also writes each layer's BF16
 // pre-activations (row-major [n][256]) and activations (the first three
@@ -272,12 +277,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
         const float* hbias = par + layer * kHid + c_begin;
         const float* w5 = par + kLayers * kHid + c_begin;
         const bool last = layer == kLayers - 1;
-        // 32 columns: bias, SiLU, BF16; into shared memory (or the head)
-        auto consume = [&](const uint32_t (&raw)[32], int c0) {
-          uint32_t packed[16];
+        // kEpiCols columns: bias, SiLU, BF16; into shared memory (or the head)
+        auto consume = [&](const uint32_t (&raw)[kEpiCols], int c0) {
+          uint32_t packed[kEpiCols / 2];
           uint32_t zpk[4];
 #pragma unroll
-          for (int j4 = 0; j4 < 8; ++j4) {
+          for (int j4 = 0; j4 < kEpiCols / 4; ++j4) {
             const float4 hb = *reinterpret_cast<const float4*>(hbias + c0 + 4 * j4);
             const float hz[4] = {fmaf(__uint_as_float(raw[4 * j4 + 0]), 0.5f, hb.x),
                                  fmaf(__uint_as_float(raw[4 * j4 + 1]), 0.5f, hb.y),
@@ -307,7 +312,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
             // land in four 16-byte runs
             unsigned char* ht = reinterpret_cast<unsigned char*>(a.h_out[layer]);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
+            for (int j = 0; j < kEpiCols / 2; ++j) {
               const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(&packed[j]);
               const uint32_t m = (uint32_t)(c_begin + c0 + 2 * j);
               *reinterpret_cast<__nv_bfloat16*>(ht + kt_off(m, (uint32_t)row, kHid)) = __low2bfloat16(v);
@@ -317,13 +322,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
           }
           if (!last) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < kEpiCols / 8; ++i)
               *reinterpret_cast<uint4*>(sH + tc::tile_off(r, c_begin + c0 + 8 * i, kHid)) =
                   make_uint4(packed[4 * i], packed[4 * i + 1], packed[4 * i + 2],
                              packed[4 * i + 3]);
           } else {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
+            for (int j = 0; j < kEpiCols / 2; ++j) {
               const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(&packed[j]);
               zh = fmaf(__low2float(v), w5[c0 + 2 * j], zh);
               zh = fmaf(__high2float(v), w5[c0 + 2 * j + 1], zh);
@@ -331,19 +336,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
           }
         };
         // two register sets: the next TMEM load is in flight while one is converted
-        uint32_t ra[32], rb[32];
-        tc::tmem_ld32_nowait(tacc + 0, ra);
+        uint32_t ra[kEpiCols], rb[kEpiCols];
+        epi_ld(tacc + 0, ra);
         tc::tmem_wait_ld(ra);
-        tc::tmem_ld32_nowait(tacc + 32, rb);
-        consume(ra, 0);
-        tc::tmem_wait_ld(rb);
-        tc::tmem_ld32_nowait(tacc + 64, ra);
-        consume(rb, 32);
-        tc::tmem_wait_ld(ra);
-        tc::tmem_ld32_nowait(tacc + 96, rb);
-        consume(ra, 64);
-        tc::tmem_wait_ld(rb);
-        consume(rb, 96);
+#pragma unroll
+        for (int c0 = 0; c0 < kColsPerWarp; c0 += 2 * kEpiCols) {
+          epi_ld(tacc + c0 + kEpiCols, rb);
+          consume(ra, c0);
+          tc::tmem_wait_ld(rb);
+          if (c0 + 2 * kEpiCols < kColsPerWarp) epi_ld(tacc + c0 + 2 * kEpiCols, ra);
+          consume(rb, c0 + kEpiCols);
+          if (c0 + 2 * kEpiCols < kColsPerWarp) tc::tmem_wait_ld(ra);
+        }
         if (!last) {
           // activations written and accumulator read: the next layer may start
           tc::fence_smem_async();
