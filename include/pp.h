@@ -432,6 +432,17 @@ int pp_mlp_gradients(pp_mlp* mlp, const uint16_t* d_feat, const float* d_nph,
 int pp_mlp_train_step(pp_mlp* mlp, const uint16_t* d_feat, const float* d_nph,
                       const float* d_count, int64_t n, float lr, void* stream);
 
+/* pp_mlp_train_step on chosen rows of a training set held on the device:
+ * d_feat[n_rows][32] (16-byte aligned), d_nph[n_rows], d_count[n_rows] and
+ * d_rows[n] (int64 row indices).  One kernel gathers the n rows into the
+ * context's batch buffers (an index outside [0, n_rows) raises the device error
+ * flag and takes row 0 instead), then the step runs as pp_mlp_train_step.
+ * Enqueued on `stream` (NULL: the context's stream).
+ * Errors: PP_EINVAL, PP_ECUDA (device errors: pp_mlp_sync / pp_mlp_loss). */
+int pp_mlp_train_step_rows(pp_mlp* mlp, const uint16_t* d_feat, const float* d_nph,
+                           const float* d_count, int64_t n_rows, const int64_t* d_rows, int64_t n,
+                           float lr, void* stream);
+
 /* Sum of the mean losses of the train steps since the last call, then reset.
  * Synchronous.  Errors: PP_EINVAL, PP_ECUDA, PP_EDEVICE. */
 int pp_mlp_loss(pp_mlp* mlp, double* loss);

@@ -58,6 +58,14 @@ cudaError_t launch_head_backward(const __nv_bfloat16* h, const __nv_bfloat16* z4
 constexpr int kHeadPartCols = 257;  // W5 and b5
 constexpr int kHeadPartPairs = 64;  // pairs per partial-sum row
 
+// out[i] = in[rows[i]] for features [.][32], photons and counts; a row outside
+// [0, n_rows) sets kGatherBadRow in *err and reads row 0.
+constexpr int kGatherBadRow = 4;
+cudaError_t launch_gather_rows(const __nv_bfloat16* feat, const float* nph, const float* cnt,
+                               int64_t n_rows, const int64_t* rows, int64_t n,
+                               __nv_bfloat16* feat_out, float* nph_out, float* cnt_out, int* err,
+                               cudaStream_t st);
+
 // Pairs of sources [s0, s0+ns) x DOMs within r_max into (ps, pd) in any order;
 // *count += all of them (only the first max_out are written).
 cudaError_t launch_near_pairs(const FeatGeom& fg, const pp_source* src, int64_t s0, int64_t ns,

@@ -452,6 +452,27 @@ __global__ void __launch_bounds__(kNearThreads) k_near_write(FeatGeom fg, const 
   }
 }
 
+// Training batch from chosen rows: out[i] = in[rows[i]] for the 64-byte
+// feature rows, photons and counts.  A row index outside [0, n_rows) raises
+// the error flag and reads row 0.
+__global__ void k_gather_rows(const uint4* feat, const float* nph, const float* cnt, int64_t n_rows,
+                              const int64_t* rows, int64_t n, uint4* feat_out, float* nph_out,
+                              float* cnt_out, int* err) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // one 16-byte part
+  if (t >= n * 4) return;
+  const int64_t i = t >> 2;
+  int64_t r = rows[i];
+  if (r < 0 || r >= n_rows) {
+    atomicOr(err, kGatherBadRow);
+    r = 0;
+  }
+  feat_out[t] = feat[r * 4 + (t & 3)];
+  if ((t & 3) == 0) {
+    nph_out[i] = nph[r];
+    cnt_out[i] = cnt[r];
+  }
+}
+
 // ----------------------------------------------------------- utilities --
 __global__ void k_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1,
                        float b2, float eps, float bc1, float bc2, __nv_bfloat16* pb) {
@@ -533,6 +554,18 @@ cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t n,
                         cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   k_adam<<<blocks_for(n, 256), 256, 0, st>>>(p, g, m, v, n, lr, b1, b2, eps, bc1, bc2, pb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rows(const __nv_bfloat16* feat, const float* nph, const float* cnt,
+                               int64_t n_rows, const int64_t* rows, int64_t n,
+                               __nv_bfloat16* feat_out, float* nph_out, float* cnt_out, int* err,
+                               cudaStream_t st) {
+  static_assert(kIn * 2 == 4 * 16, "a feature row is four 16-byte parts");
+  if (n <= 0) return cudaSuccess;
+  k_gather_rows<<<blocks_for(n * 4, 256), 256, 0, st>>>(
+      reinterpret_cast<const uint4*>(feat), nph, cnt, n_rows, rows, n,
+      reinterpret_cast<uint4*>(feat_out), nph_out, cnt_out, err);
   return cudaGetLastError();
 }
 

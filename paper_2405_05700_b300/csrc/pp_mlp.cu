@@ -67,6 +67,8 @@ struct pp_mlp {
   int64_t weights_version = 0, packed_version = -1;
   unsigned char* wpack_bwd = nullptr;  // transposed hidden weights for the backward kernel
   float* dw_part = nullptr;            // per-CTA weight-gradient partial sums
+  __nv_bfloat16* bfeat = nullptr;      // batch gathered from chosen training rows [max_batch][32]
+  float *bnph = nullptr, *bcnt = nullptr;
   float* head_part = nullptr;          // head backward: per-block partial sums of dW5, db5
   double* head_lpart = nullptr;        // and of the loss
   int64_t packed_bwd_version = -1;
@@ -195,12 +197,18 @@ int check_batch(pp_mlp* m, int64_t n, const void* d_feat) {
   return PP_OK;
 }
 
+// One Adam step on a batch already in device memory (features 16-byte aligned).
+int train_step(pp_mlp* m, const __nv_bfloat16* feat, const float* nph, const float* cnt,
+               int64_t n, float lr, cudaStream_t st);
+
 int mlp_sync(pp_mlp* m, cudaStream_t st) {
   PP_MLP_CUDA(cudaStreamSynchronize(st));
   int flag = 0;
   PP_MLP_CUDA(cudaMemcpy(&flag, m->err, sizeof(int), cudaMemcpyDeviceToHost));
   if (flag) {
     PP_MLP_CUDA(cudaMemset(m->err, 0, sizeof(int)));
+    if (flag & kGatherBadRow)
+      return mfail(m, PP_EDEVICE, "a training row index was outside the training set");
     return mfail(m, PP_EDEVICE, "a tensor-core wait ran out (device error flag)");
   }
   return PP_OK;
@@ -259,6 +267,9 @@ int pp_mlp_create(pp_ctx* ctx, int32_t max_batch, int64_t max_rows, pp_mlp** out
   PP_A(dalloc(&m->wpack, packed_weight_bytes()));
   PP_A(dalloc(&m->wpack_bwd, packed_bwd_bytes()));
   PP_A(dalloc(&m->dw_part, (size_t)m->sms * kHid * kHid));
+  PP_A(dalloc(&m->bfeat, B * kIn));
+  PP_A(dalloc(&m->bnph, B));
+  PP_A(dalloc(&m->bcnt, B));
   PP_A(dalloc(&m->head_part, (B / kHeadPartPairs) * kHeadPartCols));
   PP_A(dalloc(&m->head_lpart, B / kHeadPartPairs));
   PP_A(dalloc(&m->ice_cum, (size_t)m->fg.L));
@@ -287,7 +298,8 @@ int pp_mlp_destroy(pp_mlp* m) {
   cudaDeviceSynchronize();
   void* bufs[] = {m->p,   m->g,     m->m,         m->v,  m->t1, m->t2,    m->loss, m->err,
                   m->wpack, m->wpack_bwd, m->ps, m->pd, m->count, m->ice_cum, m->dw_part,
-                  m->head_part, m->head_lpart, m->near_bcount, m->near_boff};
+                  m->head_part, m->head_lpart, m->near_bcount, m->near_boff, m->bfeat,
+                  m->bnph, m->bcnt};
   for (void* b : bufs) cudaFree(b);
   for (int l = 0; l < kLayers; ++l) {
     cudaFree(m->wb[l]);
@@ -375,9 +387,31 @@ int pp_mlp_train_step(pp_mlp* m, const uint16_t* d_feat, const float* d_nph, con
   if ((rc = check_batch(m, n, d_feat))) return rc;
   PP_MLP_CUDA(cudaSetDevice(m->view.device));
   cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : m->view.stream;
-  if ((rc = forward_backward(m, reinterpret_cast<const __nv_bfloat16*>(d_feat), d_nph, d_count,
-                             (int)n, st)))
-    return rc;
+  return train_step(m, reinterpret_cast<const __nv_bfloat16*>(d_feat), d_nph, d_count, n, lr, st);
+}
+
+int pp_mlp_train_step_rows(pp_mlp* m, const uint16_t* d_feat, const float* d_nph,
+                           const float* d_count, int64_t n_rows, const int64_t* d_rows, int64_t n,
+                           float lr, void* stream) {
+  if (!m || !d_feat || !d_nph || !d_count || !d_rows || n_rows < 1 || !(lr > 0.0f))
+    return PP_EINVAL;
+  int rc;
+  if ((rc = check_batch(m, n, d_feat))) return rc;
+  PP_MLP_CUDA(cudaSetDevice(m->view.device));
+  cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : m->view.stream;
+  PP_MLP_CUDA(launch_gather_rows(reinterpret_cast<const __nv_bfloat16*>(d_feat), d_nph, d_count,
+                                 n_rows, d_rows, n, m->bfeat, m->bnph, m->bcnt, m->err, st));
+  return train_step(m, m->bfeat, m->bnph, m->bcnt, n, lr, st);
+}
+
+}  // extern "C"
+
+namespace {
+
+int train_step(pp_mlp* m, const __nv_bfloat16* feat, const float* nph, const float* cnt,
+               int64_t n, float lr, cudaStream_t st) {
+  int rc;
+  if ((rc = forward_backward(m, feat, nph, cnt, (int)n, st))) return rc;
   m->step += 1;
   m->weights_version += 1;
   const float b1 = 0.9f, b2 = 0.999f;
@@ -400,6 +434,10 @@ int pp_mlp_train_step(pp_mlp* m, const uint16_t* d_feat, const float* d_nph, con
                           lr, b1, b2, 1e-8f, bc1, bc2, nullptr, st));
   return PP_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 int pp_mlp_loss(pp_mlp* m, double* loss) {
   if (!m || !loss) return PP_EINVAL;

@@ -88,6 +88,7 @@ _SIGS = {
     "pp_mlp_forward": [_vp, _vp, _vp, _i64, _vp, _vp],
     "pp_mlp_gradients": [_vp, _vp, _vp, _vp, _i64, _vp, _vp],
     "pp_mlp_train_step": [_vp, _vp, _vp, _vp, _i64, C.c_float, _vp],
+    "pp_mlp_train_step_rows": [_vp, _vp, _vp, _vp, _i64, _vp, _i64, C.c_float, _vp],
     "pp_mlp_loss": [_vp, _vp],
     "pp_mlp_dom_sums": [_vp, _vp, _i64, _vp, C.c_float, _vp, _vp, _vp],
     "pp_mlp_sync": [_vp],
@@ -490,6 +491,11 @@ def pp_mlp_gradients(m, d_feat, d_nph, d_count, n, h_grads, h_loss):
 def pp_mlp_train_step(m, d_feat, d_nph, d_count, n, lr, stream=None):
     return _mcall("pp_mlp_train_step", m, _ptr(d_feat), _ptr(d_nph), _ptr(d_count), n, lr,
                   _ptr(stream))
+
+
+def pp_mlp_train_step_rows(m, d_feat, d_nph, d_count, n_rows, d_rows, n, lr, stream=None):
+    return _mcall("pp_mlp_train_step_rows", m, _ptr(d_feat), _ptr(d_nph), _ptr(d_count), n_rows,
+                  _ptr(d_rows), n, lr, _ptr(stream))
 
 
 def pp_mlp_loss(m):

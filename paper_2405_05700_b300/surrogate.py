@@ -170,10 +170,10 @@ def _train(mlp, data, epochs, batch, lr, lr_final_frac, seed, max_steps):
         for i in range(steps_per_epoch):
             if k >= total:
                 break
-            idx = perm[i * batch:(i + 1) * batch]
+            rows = perm[i * batch:(i + 1) * batch]
             rate = lr * (lr_final_frac + (1 - lr_final_frac) * 0.5 * (1 + math.cos(math.pi * k / max(1, total))))
-            pp.pp_mlp_train_step(mlp.handle, data.feat[idx].contiguous(), data.nph[idx].contiguous(),
-                                 data.counts[idx].contiguous(), batch, rate)
+            pp.pp_mlp_train_step_rows(mlp.handle, data.feat, data.nph, data.counts, data.n_pairs,
+                                      rows, batch, rate)
             k += 1
             done += 1
         losses.append(pp.pp_mlp_loss(mlp.handle) / max(1, done))

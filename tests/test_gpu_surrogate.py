@@ -200,6 +200,37 @@ def test_training_is_bit_reproducible(pp, prop, mlp):
     torch.cuda.synchronize()
 
 
+def test_train_step_on_chosen_rows_equals_step_on_gathered_batch(pp, prop, mlp):
+    """pp_mlp_train_step_rows gathers the rows in its own kernel: the same
+    parameters as a step on the batch gathered beforehand, bit for bit; a row
+    index outside the set is reported by the device flag."""
+    import torch
+    rng = np.random.default_rng(12)
+    n_rows, n = 10_000, 4096
+    x, nph, counts = _batch(rng, n_rows)
+    feat = _dev(pp.bf16_bits(x).view(np.int16))
+    d_nph, d_cnt = _dev(nph.astype(np.float32)), _dev(counts.astype(np.float32))
+    rows = torch.from_numpy(rng.choice(n_rows, n, replace=False).astype(np.int64)).cuda()
+    p0 = pp.mlp_init_params(13)
+    mlp.set_params(p0)
+    pp.pp_mlp_train_step(mlp.handle, feat[rows].contiguous(), d_nph[rows].contiguous(),
+                         d_cnt[rows].contiguous(), n, 1e-3)
+    a = mlp.get_params()
+    mlp.set_params(p0)
+    pp.pp_mlp_train_step_rows(mlp.handle, feat, d_nph, d_cnt, n_rows, rows, n, 1e-3)
+    b = mlp.get_params()
+    assert np.array_equal(a, b) and not np.array_equal(a, p0)
+    bad = rows.clone()
+    bad[7] = n_rows
+    mlp.set_params(p0)
+    pp.pp_mlp_train_step_rows(mlp.handle, feat, d_nph, d_cnt, n_rows, bad, n, 1e-3)
+    with pytest.raises(pp.PPError) as e:
+        pp.pp_mlp_sync(mlp.handle)
+    assert e.value.code == pp.PP_EDEVICE and "row index" in str(e.value)
+    pp.pp_mlp_sync(mlp.handle)   # the flag was cleared
+    torch.cuda.synchronize()
+
+
 def test_near_pairs_match_brute_force(pp, prop, mlp):
     import torch
     geom = W.geometry_full()
