@@ -91,6 +91,8 @@ def parse():
     ap.add_argument("--sur-epochs", type=int, default=32)
     ap.add_argument("--sur-eval-sources", type=int, default=5000)
     ap.add_argument("--sur-dense-sources", type=int, default=1_000_000)
+    ap.add_argument("--sur-activation", choices=["silu", "hswish"], default="silu",
+                    help="hidden-layer activation of the surrogate")
     return ap.parse_args()
 
 
@@ -267,7 +269,8 @@ def surrogate_leg(args, prop, stream, dev):
     import torch
     from paper_2405_05700_b300 import pp, surrogate as S
     mlp = pp.Mlp(prop, max_batch=65536, max_rows=1 << 22)
-    out = {}
+    mlp.set_activation(args.sur_activation)
+    out = {"activation": {"hswish": "hard-swish", "silu": "SiLU"}[args.sur_activation]}
     try:
         t = time.time()
         data = S.make_training_set(prop, mlp, n_sources=args.sur_train_sources, photons=50_000,

@@ -468,6 +468,17 @@ int pp_mlp_near_pairs(pp_mlp* mlp, const pp_source* d_src, int64_t n_src, float 
                       int64_t max_out, int32_t* d_pair_src, int32_t* d_pair_dom,
                       uint64_t* h_count);
 
+/* The hidden layers' activation (the network's definition, for training and
+ * inference alike; parameters are kept):
+ *   PP_MLP_ACT_SILU        silu(z) = z / (1 + exp(-z)) (default)
+ *   PP_MLP_ACT_HARD_SWISH  z * clamp(z / 6 + 1/2, 0, 1): no special-function
+ *                          operation (the SiLU's one per value caps inference
+ *                          at 16 values per SM and clock)
+ * Errors: PP_EINVAL. */
+#define PP_MLP_ACT_SILU 0
+#define PP_MLP_ACT_HARD_SWISH 1
+int pp_mlp_set_activation(pp_mlp* mlp, int32_t act);
+
 /* SiLU of the inference kernel: 0 (default) z/2 (1 + tanh.approx(z/2)), one
  * SFU operation per unit; 1: z / (1 + exp(-z)) as in training.  Errors: PP_EINVAL. */
 int pp_mlp_set_exact_silu(pp_mlp* mlp, int exact);

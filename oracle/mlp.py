@@ -6,9 +6,13 @@ not import the CUDA library.
 
 The network (the surrogate has no counterpart in the paper; its definition is
 the task's: BF16 weights, FP32 accumulation, Poisson mean output):
-    h1 = silu(W1 x + b1), h_l = silu(W_l h_{l-1} + b_l) (l = 2..4),
+    h1 = act(W1 x + b1), h_l = act(W_l h_{l-1} + b_l) (l = 2..4),
     z = w5 . h4 + b5,  lambda = n_photons * softplus(z),
-    loss = mean over pairs of (lambda - n ln lambda).
+    loss = mean over pairs of (lambda - n ln lambda),
+with act = silu(z) = z / (1 + exp(-z)), or hard-swish
+    hswish(z) = z * clamp(z / 6 + 1/2, 0, 1)
+(Howard et al., "Searching for MobileNetV3", 2019), whose derivative is taken
+as t + z / 6 inside (-3, 3) and t outside, t = clamp(z / 6 + 1/2, 0, 1).
 With rounding=True the values the device stores in BF16 are rounded to BF16
 at the same points (weights W1..W4, inputs, hidden activations, the stored
 pre-activations used by the backward pass, and the back-propagated dL/dz of
@@ -150,6 +154,18 @@ def _silu(z):
     return z / (1.0 + np.exp(-z))
 
 
+def hswish(z):
+    z = np.asarray(z, np.float64)
+    return z * np.clip(z / 6.0 + 0.5, 0.0, 1.0)
+
+
+def hswish_grad(z):
+    z = np.asarray(z, np.float64)
+    u = z / 6.0 + 0.5
+    t = np.clip(u, 0.0, 1.0)
+    return np.where((u > 0.0) & (u < 1.0), t + z / 6.0, t)
+
+
 def _silu_grad(z):
     s = 1.0 / (1.0 + np.exp(-z))
     return s * (1.0 + z * (1.0 - s))
@@ -159,8 +175,17 @@ def _softplus(z):
     return np.where(z > 20.0, z, np.log1p(np.exp(np.minimum(z, 20.0))))
 
 
-def forward(params, x, nph, rounding=True):
+def _act(act):
+    if act == "silu":
+        return _silu, _silu_grad
+    if act == "hswish":
+        return hswish, hswish_grad
+    raise ValueError(act)
+
+
+def forward(params, x, nph, rounding=True, act="silu"):
     """Returns lambda [n] and the cache the backward pass needs."""
+    f, _ = _act(act)
     P = unpack(params)
     rnd = bf16 if rounding else (lambda v: np.asarray(v, np.float64))
     h = rnd(x)
@@ -169,7 +194,7 @@ def forward(params, x, nph, rounding=True):
         W = rnd(P[f"W{l}"])
         z = h @ W.T + P[f"b{l}"]
         cache["z"].append(rnd(z))
-        h = rnd(_silu(z))
+        h = rnd(f(z))
         cache["h"].append(h)
     zf = h @ P["w5"] + P["b5"]
     lam = np.asarray(nph, np.float64) * _softplus(zf)
@@ -178,11 +203,12 @@ def forward(params, x, nph, rounding=True):
     return lam, cache
 
 
-def loss_and_grads(params, x, nph, counts, rounding=True):
+def loss_and_grads(params, x, nph, counts, rounding=True, act="silu"):
     """Mean Poisson NLL and its gradient with respect to every parameter."""
+    _, fgrad = _act(act)
     P = unpack(params)
     rnd = bf16 if rounding else (lambda v: np.asarray(v, np.float64))
-    lam, c = forward(params, x, nph, rounding)
+    lam, c = forward(params, x, nph, rounding, act)
     n = np.asarray(counts, np.float64)
     npairs = len(lam)
     lam_c = np.maximum(lam, 1e-300)
@@ -190,12 +216,12 @@ def loss_and_grads(params, x, nph, counts, rounding=True):
     sig = 1.0 / (1.0 + np.exp(-c["zf"]))
     g = np.asarray(nph, np.float64) * sig * (1.0 - n / lam_c) / npairs   # dL/dz
     G = {"w5": c["h"][3].T @ g, "b5": g.sum()}
-    dz = rnd(g[:, None] * P["w5"][None, :] * _silu_grad(c["z"][3]))
+    dz = rnd(g[:, None] * P["w5"][None, :] * fgrad(c["z"][3]))
     for l in (4, 3, 2, 1):
         x_in = c["h"][l - 2] if l > 1 else c["x"]
         G[f"W{l}"] = dz.T @ x_in
         G[f"b{l}"] = dz.sum(0)
         if l > 1:
             W = rnd(P[f"W{l}"])
-            dz = rnd((dz @ W) * _silu_grad(c["z"][l - 2]))
+            dz = rnd((dz @ W) * fgrad(c["z"][l - 2]))
     return loss, pack(G)

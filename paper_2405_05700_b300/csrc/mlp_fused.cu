@@ -87,7 +87,12 @@ __device__ __forceinline__ void epi_ld(uint32_t taddr, uint32_t (&r)[16]) { tc::
 // pre-activations (row-major [n][256]) and activations (the first three
 // layers transposed, [256][n], as the weight-gradient GEMMs read them; the
 // last row-major, for the head) to global memory.
-template <bool kFromPairs, bool kExactSilu, bool kTrain = false>
+// kMode: how the hidden-layer activation is evaluated
+//   kModeSiluFast   silu(z) = h (1 + tanh h), h = z / 2: one tanh.approx
+//   kModeSiluExact  z / (1 + exp(-z))
+//   kModeHardSwish  z * clamp(z / 6 + 1/2, 0, 1): FMA pipe only
+constexpr int kModeSiluFast = 0, kModeSiluExact = 1, kModeHardSwish = 2;
+template <bool kFromPairs, int kMode, bool kTrain = false>
 __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kStages], empty[kStages], acc_full[2], in_ready[2], done;
@@ -291,7 +296,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
             float y[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
-              y[i] = kExactSilu ? silu_exact(hz[i] + hz[i]) : silu_half(hz[i]);
+              if (kMode == kModeHardSwish)  // z t with t = sat(z / 6 + 1/2) = sat(h / 3 + 1/2)
+                y[i] = (hz[i] + hz[i]) * __saturatef(fmaf(hz[i], 1.0f / 3.0f, 0.5f));
+              else if (kMode == kModeSiluExact)
+                y[i] = silu_exact(hz[i] + hz[i]);
+              else
+                y[i] = silu_half(hz[i]);
             packed[2 * j4] = pack_bf16(y[0], y[1]);
             packed[2 * j4 + 1] = pack_bf16(y[2], y[3]);
             if (kTrain) {
@@ -392,10 +402,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
   if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
-__device__ __forceinline__ float silu_grad(float z) {
-  const float sg = 1.0f / (1.0f + __expf(-z));
-  return sg * (1.0f + z * (1.0f - sg));
-}
 
 // Backward pass of the hidden layers for training, fused like the forward:
 // per 256-row tile, dL/dz of the last hidden layer (from the head) becomes
@@ -569,8 +575,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd(BwdArgs a) {
               const __nv_bfloat162 z2 = *reinterpret_cast<const __nv_bfloat162*>(&zw[k]);
               const int e = 8 * i + 2 * k;
               packed[4 * i + k] =
-                  pack_bf16(__uint_as_float(raw[e]) * silu_grad(__low2float(z2)),
-                            __uint_as_float(raw[e + 1]) * silu_grad(__high2float(z2)));
+                  pack_bf16(__uint_as_float(raw[e]) * act_grad(a.act, __low2float(z2)),
+                            __uint_as_float(raw[e + 1]) * act_grad(a.act, __high2float(z2)));
             }
           }
           if (!last) {
@@ -834,7 +840,7 @@ cudaError_t launch_pack_weights(const __nv_bfloat16* const* w, unsigned char* ou
   return cudaGetLastError();
 }
 
-template <bool P, bool E, bool T = false>
+template <bool P, int E, bool T = false>
 cudaError_t launch_variant(const FusedArgs& a, int g, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(k_mlp_fused<P, E, T>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -891,10 +897,18 @@ cudaError_t launch_mlp_fused(const FusedArgs& a, bool from_pairs, int grid, cuda
   if (a.n <= 0) return cudaSuccess;
   const int64_t tiles = (a.n + kRows - 1) / kRows;
   const int g = (int)(tiles < grid ? tiles : grid);
-  if (a.z_out[0]) return launch_variant<false, true, true>(a, g, st);  // training forward
+  const bool hs = a.act == kActHardSwish;
+  if (a.z_out[0])  // training forward: the activation evaluated exactly
+    return hs ? launch_variant<false, kModeHardSwish, true>(a, g, st)
+              : launch_variant<false, kModeSiluExact, true>(a, g, st);
+  const int mode = hs ? kModeHardSwish : (a.exact_silu ? kModeSiluExact : kModeSiluFast);
   if (from_pairs)
-    return a.exact_silu ? launch_variant<true, true>(a, g, st) : launch_variant<true, false>(a, g, st);
-  return a.exact_silu ? launch_variant<false, true>(a, g, st) : launch_variant<false, false>(a, g, st);
+    return mode == kModeHardSwish   ? launch_variant<true, kModeHardSwish>(a, g, st)
+           : mode == kModeSiluExact ? launch_variant<true, kModeSiluExact>(a, g, st)
+                                    : launch_variant<true, kModeSiluFast>(a, g, st);
+  return mode == kModeHardSwish   ? launch_variant<false, kModeHardSwish>(a, g, st)
+         : mode == kModeSiluExact ? launch_variant<false, kModeSiluExact>(a, g, st)
+                                  : launch_variant<false, kModeSiluFast>(a, g, st);
 }
 
 }  // namespace mlp

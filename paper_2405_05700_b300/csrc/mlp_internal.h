@@ -41,6 +41,24 @@ struct FeatGeom {
 // fg.cum from fg.layer (one thread; L is small).
 cudaError_t launch_ice_cum(const FeatGeom& fg, float2* cum, cudaStream_t st);
 
+// Hidden-layer activations (the network's definition; the oracle states the same):
+//   kActSilu       silu(z) = z / (1 + exp(-z))
+//   kActHardSwish  hswish(z) = z * clamp(z / 6 + 1/2, 0, 1): no special-function
+//                  operation, the derivative t + z / 6 inside (-3, 3), t outside
+//                  (t = clamp(z / 6 + 1/2, 0, 1); at z = -3 and 3 the outer value)
+constexpr int kActSilu = 0;
+constexpr int kActHardSwish = 1;
+
+__device__ __forceinline__ float act_grad(int act, float z) {
+  if (act == kActHardSwish) {
+    const float u = fmaf(z, 1.0f / 6.0f, 0.5f);
+    const float t = __saturatef(u);
+    return (u > 0.0f && u < 1.0f) ? fmaf(z, 1.0f / 6.0f, t) : t;
+  }
+  const float sg = 1.0f / (1.0f + __expf(-z));
+  return sg * (1.0f + z * (1.0f - sg));
+}
+
 // Features of pairs (source s, DOM d) as BF16 [n][32].
 cudaError_t launch_features(const FeatGeom& fg, const pp_source* src, const int32_t* pair_src,
                             const int32_t* pair_dom, int64_t n, __nv_bfloat16* feat,
@@ -54,7 +72,8 @@ cudaError_t launch_features(const FeatGeom& fg, const pp_source* src, const int3
 cudaError_t launch_head_backward(const __nv_bfloat16* h, const __nv_bfloat16* z4, const float* w5,
                                  const float* b5, const float* nph, const float* cnt, int64_t n,
                                  float inv_n, __nv_bfloat16* dz4, float* dw5b5, double* loss,
-                                 float* part, double* lpart, int64_t part_rows, cudaStream_t st);
+                                 float* part, double* lpart, int64_t part_rows, int act,
+                                 cudaStream_t st);
 constexpr int kHeadPartCols = 257;  // W5 and b5
 constexpr int kHeadPartPairs = 64;  // pairs per partial-sum row
 
@@ -90,7 +109,8 @@ struct FusedArgs {
   const __nv_bfloat16* feat;     // rows mode: [n][kIn]
   int64_t n;
   const unsigned char* wpack;    // W1..W4 in the ring's chunk layout
-  int exact_silu;                // 1: z / (1 + exp(-z)); 0: one tanh.approx
+  int act;                       // kActSilu or kActHardSwish
+  int exact_silu;                // SiLU: 1: z / (1 + exp(-z)); 0: one tanh.approx
   const float* bias[kLayers];
   const float* w5;
   const float* b5;
@@ -120,6 +140,7 @@ cudaError_t launch_mlp_fused(const FusedArgs& a, bool from_pairs, int grid, cuda
 // transposed hidden weights packed by launch_pack_bwd.
 struct BwdArgs {
   int64_t n;
+  int act;                       // kActSilu or kActHardSwish
   const unsigned char* wpack;
   const __nv_bfloat16* z[kLayers];
   __nv_bfloat16* dz[kLayers];

@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(256) k_head_bwd(const __nv_bfloat16* h, const 
                                                   const float* w5, const float* b5,
                                                   const float* nph, const float* cnt, int64_t n,
                                                   float inv_n, __nv_bfloat16* dz4, float* part,
-                                                  double* lpart) {
+                                                  double* lpart, int act) {
   __shared__ float s_g[kHeadPairs];
   __shared__ float s_w5[kHid];
   __shared__ float s_gsum[8];
@@ -245,9 +245,7 @@ __global__ void __launch_bounds__(256) k_head_bwd(const __nv_bfloat16* h, const 
     const float g = s_g[q];
     const size_t o = (size_t)p * kHid + j;
     acc = fmaf(g, __bfloat162float(h[o]), acc);
-    const float zz = __bfloat162float(z4[o]);
-    const float sg = 1.0f / (1.0f + __expf(-zz));
-    dz4[o] = __float2bfloat16_rn(g * s_w5[j] * sg * (1.0f + zz * (1.0f - sg)));
+    dz4[o] = __float2bfloat16_rn(g * s_w5[j] * act_grad(act, __bfloat162float(z4[o])));
   }
   float* row = part + (size_t)blockIdx.x * kHeadCols;
   row[j] = acc;
@@ -513,11 +511,13 @@ cudaError_t launch_features(const FeatGeom& fg, const pp_source* src, const int3
 cudaError_t launch_head_backward(const __nv_bfloat16* h, const __nv_bfloat16* z4, const float* w5,
                                  const float* b5, const float* nph, const float* cnt, int64_t n,
                                  float inv_n, __nv_bfloat16* dz4, float* dw5b5, double* loss,
-                                 float* part, double* lpart, int64_t part_rows, cudaStream_t st) {
+                                 float* part, double* lpart, int64_t part_rows, int act,
+                                 cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int64_t blocks = (n + kHeadPairs - 1) / kHeadPairs;
   if (blocks > part_rows) return cudaErrorInvalidValue;
-  k_head_bwd<<<(unsigned)blocks, 256, 0, st>>>(h, z4, w5, b5, nph, cnt, n, inv_n, dz4, part, lpart);
+  k_head_bwd<<<(unsigned)blocks, 256, 0, st>>>(h, z4, w5, b5, nph, cnt, n, inv_n, dz4, part, lpart,
+                                               act);
   k_head_reduce<<<kHeadReduceColBlocks + 1, 256, 0, st>>>(part, lpart, (int)blocks, dw5b5, loss);
   return cudaGetLastError();
 }

@@ -73,6 +73,7 @@ struct pp_mlp {
   double* head_lpart = nullptr;        // and of the loss
   int64_t packed_bwd_version = -1;
   int exact_silu = 0;
+  int act = kActSilu;
   float2* ice_cum = nullptr;
   int sms = 0;
   int32_t *ps = nullptr, *pd = nullptr;
@@ -116,6 +117,7 @@ FusedArgs fused_args(pp_mlp* m) {
   a.fg = m->fg;
   a.wpack = m->wpack;
   a.exact_silu = m->exact_silu;
+  a.act = m->act;
   for (int l = 0; l < kLayers; ++l) a.bias[l] = m->p + off_b(l);
   a.w5 = m->p + kOffW5;
   a.b5 = m->p + kOffB5;
@@ -154,7 +156,7 @@ int forward_backward(pp_mlp* m, const __nv_bfloat16* x0, const float* nph, const
   static_assert(kOffB5 == kOffW5 + kHid, "W5 and b5 are adjacent");
   PP_MLP_CUDA(launch_head_backward(m->h[3], m->z[3], m->p + kOffW5, m->p + kOffB5, nph, cnt, n,
                                    1.0f / (float)n, m->dz[3], m->g + kOffW5, m->loss, m->head_part,
-                                   m->head_lpart, m->max_batch / kHeadPartPairs, st));
+                                   m->head_lpart, m->max_batch / kHeadPartPairs, m->act, st));
   // dz_{l-1} = (dz_l . W_l) * silu'(z_{l-1}) for l = 3, 2, 1: one fused kernel
   if (m->packed_bwd_version != m->weights_version) {
     PP_MLP_CUDA(launch_pack_bwd(m->wb, m->wpack_bwd, st));
@@ -162,6 +164,7 @@ int forward_backward(pp_mlp* m, const __nv_bfloat16* x0, const float* nph, const
   }
   BwdArgs b{};
   b.n = n;
+  b.act = m->act;
   b.wpack = m->wpack_bwd;
   b.dz3_t = reinterpret_cast<unsigned char*>(m->t1);
   for (int l = 0; l < kLayers; ++l) {
@@ -525,6 +528,13 @@ int pp_mlp_near_pairs(pp_mlp* m, const pp_source* d_src, int64_t n_src, float r_
   PP_MLP_CUDA(cudaMemcpyAsync(&c, m->count, sizeof(c), cudaMemcpyDeviceToHost, st));
   PP_MLP_CUDA(cudaStreamSynchronize(st));
   *h_count = c;
+  return PP_OK;
+}
+
+int pp_mlp_set_activation(pp_mlp* m, int32_t act) {
+  if (!m || (act != PP_MLP_ACT_SILU && act != PP_MLP_ACT_HARD_SWISH)) return PP_EINVAL;
+  static_assert(PP_MLP_ACT_SILU == kActSilu && PP_MLP_ACT_HARD_SWISH == kActHardSwish, "codes");
+  m->act = act;
   return PP_OK;
 }
 

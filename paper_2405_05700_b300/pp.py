@@ -93,6 +93,7 @@ _SIGS = {
     "pp_mlp_dom_sums": [_vp, _vp, _i64, _vp, C.c_float, _vp, _vp, _vp],
     "pp_mlp_sync": [_vp],
     "pp_mlp_set_exact_silu": [_vp, _i32],
+    "pp_mlp_set_activation": [_vp, _i32],
     "pp_mlp_near_pairs": [_vp, _vp, _i64, C.c_float, _i64, _vp, _vp, _vp],
     "pp_debug_philox": [_vp, _vp, _vp, _vp, _i64],
     "pp_debug_trace": [_vp, _u64, _vp, _i64, _vp, _i64, _i32, _vp, _vp, _vp, _vp],
@@ -521,6 +522,13 @@ def pp_mlp_sync(m):
     return _mcall("pp_mlp_sync", m)
 
 
+PP_MLP_ACT_SILU, PP_MLP_ACT_HARD_SWISH = 0, 1
+
+
+def pp_mlp_set_activation(m, act):
+    return _mcall("pp_mlp_set_activation", m, act)
+
+
 def pp_mlp_set_exact_silu(m, exact):
     return _mcall("pp_mlp_set_exact_silu", m, 1 if exact else 0)
 
@@ -556,6 +564,11 @@ class Mlp:
 
     def __exit__(self, *exc):
         self.close()
+
+    def set_activation(self, act):
+        """PP_MLP_ACT_SILU or PP_MLP_ACT_HARD_SWISH (or "silu" / "hswish")."""
+        codes = {"silu": PP_MLP_ACT_SILU, "hswish": PP_MLP_ACT_HARD_SWISH}
+        pp_mlp_set_activation(self.handle, codes.get(act, act))
 
     def set_params(self, p):
         p = np.ascontiguousarray(p, np.float32)

@@ -106,37 +106,42 @@ def _batch(rng, n):
     return x, nph, counts
 
 
-@pytest.mark.parametrize("n,exact", [(2048, 0), (77, 0), (80_077, 0), (80_077, 1)])
-def test_forward_matches_oracle(pp, mlp, n, exact):
+@pytest.mark.parametrize("n,exact,act", [(2048, 0, "silu"), (77, 0, "silu"), (80_077, 0, "silu"),
+                                         (80_077, 1, "silu"), (77, 0, "hswish"),
+                                         (80_077, 0, "hswish")])
+def test_forward_matches_oracle(pp, mlp, n, exact, act):
     """The fused inference kernel (rows mode) against the oracle network: one
     tile, a ragged single tile, and several tiles per CTA with a ragged end,
-    with the one-SFU SiLU (default) and the exact one.
+    with the one-SFU SiLU (default), the exact one, and hard-swish.
 
     Both sides round to BF16 at the same points, so almost every row agrees
-    to FP32 accumulation error; where the device's SiLU lands on the other
-    side of a BF16 rounding boundary, that one-ulp step (2^-8 relative)
+    to FP32 accumulation error; where the device's activation lands on the
+    other side of a BF16 rounding boundary, that one-ulp step (2^-8 relative)
     propagates through the later layers: rare, up to a few per cent."""
     import torch
     from oracle import mlp as M
     rng = np.random.default_rng(5 + n)
     x, nph, _ = _batch(rng, n)
     pp.pp_mlp_set_exact_silu(mlp.handle, exact)
+    mlp.set_activation(act)
     p = pp.mlp_init_params(7).astype(np.float64)
     p[-1] = -6.0
     mlp.set_params(p.astype(np.float32))
     p32 = p.astype(np.float32).astype(np.float64)
-    lam_ref, _ = M.forward(p32, x, nph, rounding=True)
+    lam_ref, _ = M.forward(p32, x, nph, rounding=True, act=act)
     feat = _dev(pp.bf16_bits(x).view(np.int16))
     lam = torch.zeros(len(x), dtype=torch.float32, device="cuda")
     pp.pp_mlp_forward(mlp.handle, feat, _dev(nph.astype(np.float32)), len(x), lam)
     pp.pp_mlp_sync(mlp.handle)
     pp.pp_mlp_set_exact_silu(mlp.handle, 0)
+    mlp.set_activation("silu")
     rel = np.abs(lam.cpu().numpy() - lam_ref) / lam_ref
     assert np.median(rel) < 1e-4, np.median(rel)
     assert np.quantile(rel, 0.99) < 2e-2 and rel.max() < 0.1, (np.quantile(rel, 0.99), rel.max())
 
 
-def test_gradients_match_oracle(pp, mlp):
+@pytest.mark.parametrize("act", ["silu", "hswish"])
+def test_gradients_match_oracle(pp, mlp, act):
     from oracle import mlp as M
     rng = np.random.default_rng(6)
     n = 4096
@@ -144,12 +149,14 @@ def test_gradients_match_oracle(pp, mlp):
     p = pp.mlp_init_params(9).astype(np.float64)
     p[-1] = -6.0
     mlp.set_params(p.astype(np.float32))
+    mlp.set_activation(act)
     p32 = p.astype(np.float32).astype(np.float64)
-    loss_ref, g_ref = M.loss_and_grads(p32, x, nph, counts, rounding=True)
+    loss_ref, g_ref = M.loss_and_grads(p32, x, nph, counts, rounding=True, act=act)
     g = np.zeros(pp.PP_MLP_N_PARAMS, np.float32)
     loss = np.zeros(1)
     pp.pp_mlp_gradients(mlp.handle, _dev(pp.bf16_bits(x).view(np.int16)),
                         _dev(nph.astype(np.float32)), _dev(counts.astype(np.float32)), n, g, loss)
+    mlp.set_activation("silu")
     assert abs(loss[0] - loss_ref) <= 1e-3 * abs(loss_ref)
     blocks = M.unpack(np.arange(M.N_PARAMS))
     for name, idx in blocks.items():
@@ -263,7 +270,8 @@ def test_near_pairs_match_brute_force(pp, prop, mlp):
     assert not ps.cpu().numpy()[10:].any()
 
 
-def test_dom_sums_match_oracle(pp, prop, mlp):
+@pytest.mark.parametrize("act", ["silu", "hswish"])
+def test_dom_sums_match_oracle(pp, prop, mlp, act):
     """Pairs mode of the fused kernel: lambda of every pair within r_max against
     the oracle network on the oracle's features (sampled), zero beyond r_max,
     and the per-DOM sums equal to the sums of the per-pair values."""
@@ -275,6 +283,7 @@ def test_dom_sums_match_oracle(pp, prop, mlp):
     p = pp.mlp_init_params(4).astype(np.float64)
     p[-1] = -6.0
     mlp.set_params(p.astype(np.float32))
+    mlp.set_activation(act)
     p32 = p.astype(np.float32).astype(np.float64)
     nph = rng.uniform(1e3, 1e5, len(src)).astype(np.float32)
     r_max = 250.0
@@ -283,6 +292,7 @@ def test_dom_sums_match_oracle(pp, prop, mlp):
     pp.pp_mlp_dom_sums(mlp.handle, _dev(src.view(np.uint8)), len(src), _dev(nph), r_max, sums, lam,
                        None)
     pp.pp_mlp_sync(mlp.handle)
+    mlp.set_activation("silu")
     lam = lam.cpu().numpy().astype(np.float64)
     sums = sums.cpu().numpy()
     d = np.stack([src["dx"], src["dy"], src["dz"]], 1).astype(np.float64)
@@ -297,7 +307,7 @@ def test_dom_sums_match_oracle(pp, prop, mlp):
     pick = rng.choice(len(s_i), 6000, replace=False)
     ps, pd = s_i[pick], d_i[pick]
     x = M.bf16(M.features(src, ps, pd, geom.xyz, ice.b_e, ice.a, ice.depth_top, ice.dz))
-    ref, _ = M.forward(p32, x, nph[ps].astype(np.float64), rounding=True)
+    ref, _ = M.forward(p32, x, nph[ps].astype(np.float64), rounding=True, act=act)
     rel = np.abs(lam[ps, pd] - ref) / ref
     # device features may sit one BF16 step from the oracle's (FP32 vs FP64)
     assert np.median(rel) < 3e-3 and np.quantile(rel, 0.99) < 3e-2, (np.median(rel), rel.max())

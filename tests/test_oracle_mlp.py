@@ -5,6 +5,7 @@ hand-computed pairs."""
 import math
 
 import numpy as np
+import pytest
 
 from oracle import mlp as M
 from paper_2405_05700_b300 import workloads as W
@@ -18,23 +19,54 @@ def _params(seed, scale=1.0):
     return M.pack(d)
 
 
-def test_gradients_match_finite_differences():
+@pytest.mark.parametrize("act", ["silu", "hswish"])
+def test_gradients_match_finite_differences(act):
+    """For hard-swish W1 is scaled up so that the pre-activations of every
+    layer spread over several units and each of its pieces (0, the quadratic,
+    the identity) is exercised; the fraction in each piece is checked."""
     rng = np.random.default_rng(3)
     n = 48
     x = rng.normal(0, 1, (n, M.IN))
     nph = rng.uniform(50, 500, n)
     counts = rng.poisson(3.0, n).astype(np.float64)
     p = _params(4)
-    loss, g = M.loss_and_grads(p, x, nph, counts, rounding=False)
+    if act == "hswish":
+        d = M.unpack(p)
+        d["W1"] = d["W1"] * 25.0
+        p = M.pack(d)
+        _, c = M.forward(p, x, nph, rounding=False, act=act)
+        for z in c["z"]:
+            assert (z < -3).mean() > 0.05 and (z > 3).mean() > 0.05
+            assert (np.abs(z) < 3).mean() > 0.05
+    loss, g = M.loss_and_grads(p, x, nph, counts, rounding=False, act=act)
     idx = np.concatenate([rng.choice(M.N_PARAMS - 1, 60, replace=False), [M.N_PARAMS - 1]])
     h = 1e-6
     for i in idx:
         e = np.zeros(M.N_PARAMS)
         e[i] = h
-        lp, _ = M.loss_and_grads(p + e, x, nph, counts, rounding=False)
-        lm, _ = M.loss_and_grads(p - e, x, nph, counts, rounding=False)
+        lp, _ = M.loss_and_grads(p + e, x, nph, counts, rounding=False, act=act)
+        lm, _ = M.loss_and_grads(p - e, x, nph, counts, rounding=False, act=act)
         fd = (lp - lm) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)) + 1e-7, (i, fd, g[i])
+
+
+def test_hard_swish_closed_form_values_and_slopes():
+    """The definition's three pieces: 0 below -3, z^2/6 + z/2 between, z above
+    (MobileNetV3's hard-swish), and its derivative z/3 + 1/2 inside, 0 and 1
+    outside; the value is continuous at -3 and 3."""
+    z = np.array([-10.0, -4.0, -3.0, -1.5, 0.0, 1.0, 2.5, 3.0, 4.0, 50.0])
+    want = np.where(z <= -3, 0.0, np.where(z >= 3, z, z * z / 6 + z / 2))
+    assert np.allclose(M.hswish(z), want, rtol=0, atol=1e-15)
+    assert M.hswish(1.0) == pytest.approx(2.0 / 3.0) and M.hswish(-1.5) == pytest.approx(-0.375)
+    slope = np.where(z <= -3, 0.0, np.where(z >= 3, 1.0, z / 3 + 0.5))
+    assert np.allclose(M.hswish_grad(z), slope, rtol=0, atol=1e-15)
+    # the derivative against central differences away from the kinks
+    zz = np.linspace(-6, 6, 241)
+    zz = zz[np.abs(np.abs(zz) - 3) > 1e-3]
+    fd = (M.hswish(zz + 1e-6) - M.hswish(zz - 1e-6)) / 2e-6
+    assert np.allclose(fd, M.hswish_grad(zz), atol=1e-6)
+    for a, b in ((-3 - 1e-9, -3 + 1e-9), (3 - 1e-9, 3 + 1e-9)):
+        assert abs(M.hswish(a) - M.hswish(b)) < 1e-8
 
 
 def test_bf16_rounding_definition():
