@@ -32,6 +32,7 @@ struct pp_ctx {
   pp_config cfg{};
   cudaStream_t stream = nullptr;
   cudaStream_t copy_stream = nullptr;  // host path: uploads and downloads beside the kernels
+  cudaStream_t stream2 = nullptr;      // host path: every other chunk's kernels (tails overlap)
   bool own_stream = false;
   int sm_count = 0;
   std::mutex mu;
@@ -44,6 +45,8 @@ struct pp_ctx {
   DevBuf dom, str, str_range, sdom_z, sdom_idx, clear, cell_off, cell_list, layers;
   // scratch
   DevBuf off, chunk, aux, bsum, meta, work, err, stats;
+  // a second set of the expansion's scratch, for chunks launched on stream2
+  DevBuf off2, chunk2, aux2, bsum2, meta2, work2;
   // staging for host entry points
   DevBuf s_src, s_begin, s_ids, s_hits, s_counts, s_misc1, s_misc2, s_misc3, s_misc4, s_bad;
   size_t smem_limit_set = 0;
@@ -93,8 +96,9 @@ int cuda_fail_ctx(pp_ctx* c, cudaError_t e, const char* where) { return cuda_fai
 int ensure(pp_ctx* ctx, DevBuf& b, size_t bytes) {
   if (bytes <= b.cap && b.p) return PP_OK;
   ctx->epoch += 1;  // captured graphs hold the old address
-  // the old buffer may still be read by queued work on the context's stream
+  // the old buffer may still be read by queued work on the context's streams
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess && ctx->stream2) e = cudaStreamSynchronize(ctx->stream2);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
   if (b.p) cudaFree(b.p);
   b.p = nullptr;
@@ -474,6 +478,16 @@ int sync_and_check(pp_ctx* ctx, cudaStream_t st) {
 // stream) is done, so transfers overlap the kernels.  The sources are
 // checked on the device; a malformed one fails the call with PP_EINVAL after
 // the work (the kernels skip malformed sources).
+// Exchanges the expansion scratch the launch helpers use with the second set.
+void swap_scratch(pp_ctx* ctx) {
+  std::swap(ctx->off, ctx->off2);
+  std::swap(ctx->chunk, ctx->chunk2);
+  std::swap(ctx->aux, ctx->aux2);
+  std::swap(ctx->bsum, ctx->bsum2);
+  std::swap(ctx->meta, ctx->meta2);
+  std::swap(ctx->work, ctx->work2);
+}
+
 int batch_host_pipelined(pp_ctx* ctx, int32_t n_events, const uint64_t* ids, const int64_t* begin,
                          const pp_source* src, uint64_t* hits, uint64_t* counts) {
   int rc;
@@ -481,14 +495,20 @@ int batch_host_pipelined(pp_ctx* ctx, int32_t n_events, const uint64_t* ids, con
   const int n_dom = ctx->geom.n_dom;
   cudaStream_t st = ctx->stream;
   if (!ctx->copy_stream) PP_CUDA(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+  if (!ctx->stream2) PP_CUDA(cudaStreamCreateWithFlags(&ctx->stream2, cudaStreamNonBlocking));
   cudaStream_t cs = ctx->copy_stream;
+  // chunks alternate between the two compute streams, each with its own
+  // expansion scratch, so that a chunk's kernels start while the previous
+  // chunk's last photons finish; a chunk waits only for its own upload and
+  // (same stream) for the chunk two before it, which used the same scratch
+  cudaStream_t cst[2] = {st, ctx->stream2};
   // chunks: event ranges cut at 10 % and 90 % of the sources
   std::vector<int32_t> cut{0};
   // a small first chunk (its upload is exposed), a small last one (its
   // download is exposed), the bulk in between
-  const double edges[2] = {0.1, 0.9};
-  for (int k = 0; k < 2; ++k) {
-    const int64_t target = (int64_t)(edges[k] * (double)n_src);
+  static constexpr double edges[] = {0.1, 0.9};
+  for (double edge : edges) {
+    const int64_t target = (int64_t)(edge * (double)n_src);
     int32_t e = cut.back();
     while (e < n_events && begin[e] < target) ++e;
     if (e > cut.back() && e < n_events) cut.push_back(e);
@@ -510,12 +530,20 @@ int batch_host_pipelined(pp_ctx* ctx, int32_t n_events, const uint64_t* ids, con
   // each chunk's source offsets relative to its first source (kept until the end)
   std::vector<int64_t> rel((size_t)(n_events + nc));
   std::vector<cudaEvent_t> up(nc, nullptr), done(nc, nullptr);
+  cudaEvent_t cleared = nullptr;
+  const bool keep_graphs = ctx->graphs;
+  ctx->graphs = false;  // captured graphs are keyed without the scratch set
   auto release = [&]() {
     for (auto& e : up) if (e) cudaEventDestroy(e);
     for (auto& e : done) if (e) cudaEventDestroy(e);
+    if (cleared) cudaEventDestroy(cleared);
+    ctx->graphs = keep_graphs;
   };
   auto step = [&]() -> int {
     PP_CUDA(cudaMemsetAsync(bad, 0xFF, sizeof(unsigned long long), st));
+    PP_CUDA(cudaEventCreateWithFlags(&cleared, cudaEventDisableTiming));
+    PP_CUDA(cudaEventRecord(cleared, st));
+    PP_CUDA(cudaStreamWaitEvent(ctx->stream2, cleared, 0));
     for (int k = 0; k < nc; ++k) {
       const int32_t e0 = cut[k], e1 = cut[k + 1];
       const int64_t s0 = begin[e0], s1 = begin[e1];
@@ -535,12 +563,15 @@ int batch_host_pipelined(pp_ctx* ctx, int32_t n_events, const uint64_t* ids, con
     for (int k = 0; k < nc; ++k) {
       const int32_t e0 = cut[k], e1 = cut[k + 1];
       const int64_t s0 = begin[e0], s1 = begin[e1];
-      PP_CUDA(cudaStreamWaitEvent(st, up[k], 0));
-      PP_CUDA(launch_check_sources(d_src + s0, s1 - s0, s0, bad, st));
+      cudaStream_t ks = cst[k & 1];
+      PP_CUDA(cudaStreamWaitEvent(ks, up[k], 0));
+      PP_CUDA(launch_check_sources(d_src + s0, s1 - s0, s0, bad, ks));
+      if (k & 1) swap_scratch(ctx);
       int r = batch_async(ctx, e1 - e0, d_ids + e0, d_begin + e0 + k, d_src + s0, s1 - s0,
-                          d_hits + (size_t)e0 * n_dom, d_counts + (size_t)e0 * 4, st);
+                          d_hits + (size_t)e0 * n_dom, d_counts + (size_t)e0 * 4, ks);
+      if (k & 1) swap_scratch(ctx);
       if (r) return r;
-      PP_CUDA(cudaEventRecord(done[k], st));
+      PP_CUDA(cudaEventRecord(done[k], ks));
       PP_CUDA(cudaStreamWaitEvent(cs, done[k], 0));
       if (n_dom)
         PP_CUDA(cudaMemcpyAsync(hits + (size_t)e0 * n_dom, d_hits + (size_t)e0 * n_dom,
@@ -556,9 +587,11 @@ int batch_host_pipelined(pp_ctx* ctx, int32_t n_events, const uint64_t* ids, con
   release();
   if (rc) {
     cudaStreamSynchronize(cs);
+    cudaStreamSynchronize(ctx->stream2);
     cudaStreamSynchronize(st);
     return rc;
   }
+  PP_CUDA(cudaStreamSynchronize(ctx->stream2));
   unsigned long long first = 0;
   PP_CUDA(cudaMemcpy(&first, bad, sizeof(first), cudaMemcpyDeviceToHost));
   if (first != ~0ull) {
@@ -733,7 +766,8 @@ int pp_destroy(pp_ctx* ctx) {
   DevBuf* bufs[] = {&ctx->dom, &ctx->str, &ctx->str_range, &ctx->sdom_z, &ctx->sdom_idx,
                     &ctx->clear, &ctx->cell_off, &ctx->cell_list, &ctx->layers, &ctx->off,
                     &ctx->chunk, &ctx->aux, &ctx->bsum, &ctx->meta, &ctx->work, &ctx->err,
-                    &ctx->stats,
+                    &ctx->stats, &ctx->off2, &ctx->chunk2, &ctx->aux2, &ctx->bsum2, &ctx->meta2,
+                    &ctx->work2,
                     &ctx->s_src, &ctx->s_begin, &ctx->s_ids, &ctx->s_hits, &ctx->s_counts,
                     &ctx->s_misc1, &ctx->s_misc2, &ctx->s_misc3, &ctx->s_misc4, &ctx->s_bad};
   drop_graphs(ctx);
@@ -745,6 +779,7 @@ int pp_destroy(pp_ctx* ctx) {
   for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  if (ctx->stream2) cudaStreamDestroy(ctx->stream2);
   delete ctx;
   return PP_OK;
 }
