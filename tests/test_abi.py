@@ -76,3 +76,14 @@ def test_issue_rate_probe_checks_its_arguments(lib):
     rate = ctypes.c_double()
     assert lib._lib.pp_measure_issue_rate(0, 7, ctypes.byref(rate), None) == lib.PP_EINVAL
     assert lib._lib.pp_measure_issue_rate(0, lib.PP_ISSUE_FP32_FMA, None, None) == lib.PP_EINVAL
+
+
+def test_surrogate_entry_points_refuse_null_handles(lib):
+    """Argument checks that happen before any device work."""
+    L = lib._lib
+    assert L.pp_mlp_set_activation(None, lib.PP_MLP_ACT_SILU) == lib.PP_EINVAL
+    assert L.pp_mlp_set_exact_silu(None, 0) == lib.PP_EINVAL
+    assert L.pp_mlp_train_step_rows(None, None, None, None, 10, None, 64, ctypes.c_float(1e-3),
+                                    None) == lib.PP_EINVAL
+    assert L.pp_mlp_near_pairs(None, None, 0, ctypes.c_float(1.0), 0, None, None, None) == lib.PP_EINVAL
+    assert lib.PP_MLP_ACT_SILU == 0 and lib.PP_MLP_ACT_HARD_SWISH == 1
