@@ -220,13 +220,25 @@ int pp_propagate_range_async(pp_ctx* ctx, uint64_t event_id, const pp_source* d_
  *   time_ns  emission offset along the segment at the speed of light plus
  *            the photon's path length at the group velocity c / group_index,
  *            from the segment's start point (sources carry no start time)
- *   weight   1: every geometric hit counts once (no acceptance model is given) */
+ *   weight   the probability that the hit makes a photoelectron (paper Sec. 2:
+ *            a function of the photon's position, direction, time and
+ *            wavelength, not given there): 1 by default, or the acceptance
+ *            polynomial set by pp_set_hit_acceptance.  Hits and counts are
+ *            geometric either way. */
 typedef struct pp_hit {
   uint32_t dom;
   uint32_t source;
   float time_ns;
   float weight;
 } pp_hit;
+
+/* Acceptance of the hit records: weight = clamp(sum_{i < n} coeffs[i] eta^i,
+ * 0, 1) with eta the z component of the photon's unit direction when it
+ * reaches the DOM (eta = 1: moving straight up, onto the bottom of the DOM).
+ * 0 <= n <= PP_MAX_ACCEPT_COEFFS, finite coefficients (host memory, copied);
+ * n = 0 restores weight 1.  Errors: PP_EINVAL. */
+#define PP_MAX_ACCEPT_COEFFS 8
+int pp_set_hit_acceptance(pp_ctx* ctx, const float* coeffs, int32_t n);
 
 /* pp_propagate_batch_async that also writes the hit records: the same hits
  * and counts, plus up to max_records records in d_records[max_records]

@@ -66,8 +66,8 @@ def lib():
             "orc_first_hit": ([P, vp, vp, vp, vp, vp, i64], None),
             "orc_propagate": ([P, i32, vp, vp, vp, vp, vp, vp, vp, vp], C.c_int),
             "orc_trace": ([P, C.c_uint64, i64, vp, vp, vp, vp, i64, i32, vp, vp, vp, vp, vp], C.c_int),
-            "orc_hit_records": ([P, C.c_uint64, i64, vp, vp, vp, d, i64, vp, vp, vp, vp, vp],
-                                C.c_int),
+            "orc_hit_records": ([P, C.c_uint64, i64, vp, vp, vp, d, C.c_int32, vp, i64, vp, vp,
+                                 vp, vp, vp, vp], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(_lib, name)
@@ -249,20 +249,26 @@ def trace(model: Model, event_id: int, sources, photon_ids, n_trace: int = 10,
 
 
 def hit_records(model: Model, event_id: int, sources, group_index: float = 1.35,
-                max_records: int = 1 << 22):
+                max_records: int = 1 << 22, acceptance=None):
     """Compact hit records of one event (single-threaded): dict of arrays
-    dom (u32), source (u32), time_ns (f64), photon (u64, per-event id)."""
+    dom (u32), source (u32), time_ns (f64), weight (f64), photon (u64,
+    per-event id).  acceptance: polynomial coefficients c_0.. in the z
+    component of the photon's direction at the DOM (weight = clamp to [0, 1]
+    of sum c_i eta^i); None gives weight 1."""
     f, typ, nph = _source_arrays(sources)
+    acc = np.ascontiguousarray([] if acceptance is None else acceptance, np.float64)
     dom = np.zeros(max_records, np.uint32)
     src = np.zeros(max_records, np.uint32)
     t = np.zeros(max_records)
+    w = np.zeros(max_records)
     ph = np.zeros(max_records, np.uint64)
     n = C.c_int64()
     rc = lib().orc_hit_records(model.pref(), int(event_id), f.shape[0], _ptr(f), _ptr(typ),
-                               _ptr(nph), float(group_index), max_records, _ptr(dom), _ptr(src),
-                               _ptr(t), _ptr(ph), C.addressof(n))
+                               _ptr(nph), float(group_index), int(acc.size),
+                               _ptr(acc) if acc.size else None, max_records, _ptr(dom),
+                               _ptr(src), _ptr(t), _ptr(w), _ptr(ph), C.addressof(n))
     if rc != 0:
         raise RuntimeError(f"orc_hit_records failed: {rc}")
     k = min(n.value, max_records)
-    return {"dom": dom[:k], "source": src[:k], "time_ns": t[:k], "photon": ph[:k],
-            "n": n.value}
+    return {"dom": dom[:k], "source": src[:k], "time_ns": t[:k], "weight": w[:k],
+            "photon": ph[:k], "n": n.value}

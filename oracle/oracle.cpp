@@ -445,7 +445,8 @@ double dom_margin(const Geom& G, const double p[3], const double d[3], double S)
 
 int simulate_photon(const Model& M, uint32_t event_lo, uint64_t pid, const Source& src,
                     PhotonStats* st, double* birth6, double* trace, int n_trace,
-                    double* margin = nullptr, double* emit_offset = nullptr) {
+                    double* margin = nullptr, double* emit_offset = nullptr,
+                    double* hit_dir = nullptr) {
   const uint32_t key[2] = {(uint32_t)M.seed, event_lo};
   uint32_t ctr[4] = {(uint32_t)pid, (uint32_t)(pid >> 32), 0u, 0u};
   uint32_t x[4];
@@ -494,6 +495,8 @@ int simulate_photon(const Model& M, uint32_t event_lo, uint64_t pid, const Sourc
     }
     if (k >= 0 && th < tw) {
       st->path += th;
+      if (hit_dir)
+        for (int q = 0; q < 3; ++q) hit_dir[q] = dir[q];
       return k;
     }
     if (tw <= w.S) {
@@ -684,13 +687,21 @@ int orc_propagate(const orc_params* P, int32_t n_events, const uint64_t* event_i
 // Compact hit records of one event (paper Sec. 4: the producing particle's
 // ID, the hit time and the weight), one per photon that ends on a DOM, in
 // photon order: DOM, source index, time = (emission offset along the segment
-// + group_index x path length) / c in ns, and the photon's id.  At most
-// max_records are written; *n_records receives the number of hits.
+// + group_index x path length) / c in ns, the weight and the photon's id.  The
+// weight is the probability that the hit makes a photoelectron (paper Sec. 2
+// names it a function of the photon's position, direction, time and
+// wavelength and gives none): here the caller's polynomial accept[0..n_accept)
+// in eta, the z component of the photon's direction at the DOM, clamped to
+// [0, 1]; 1 when n_accept = 0.  At most max_records are written (weight may
+// be NULL); *n_records receives the number of hits.
 int orc_hit_records(const orc_params* P, uint64_t event_id, int64_t n_src, const float* src_f,
                     const uint32_t* src_type, const uint64_t* src_n, double group_index,
-                    int64_t max_records, uint32_t* dom, uint32_t* source, double* time_ns,
-                    uint64_t* photon, int64_t* n_records) {
-  if (!P || n_src < 0 || max_records < 0 || !(group_index >= 1.0)) return -1;
+                    int32_t n_accept, const double* accept, int64_t max_records, uint32_t* dom,
+                    uint32_t* source, double* time_ns, double* weight, uint64_t* photon,
+                    int64_t* n_records) {
+  if (!P || n_src < 0 || max_records < 0 || !(group_index >= 1.0) || n_accept < 0 ||
+      (n_accept > 0 && !accept))
+    return -1;
   Model M;
   build_model(P, &M);
   const double c = 0.299792458;  // m / ns
@@ -701,16 +712,29 @@ int orc_hit_records(const orc_params* P, uint64_t event_id, int64_t n_src, const
     const Source src = read_source(src_f, src_type, s);
     for (uint64_t j = 0; j < src_n[s]; ++j) {
       const double path0 = ps.path;
-      double t_emit = 0.0;
+      double t_emit = 0.0, hd[3] = {0.0, 0.0, 0.0};
       const uint64_t pid = off[s] + j;
       const int out = simulate_photon(M, (uint32_t)event_id, pid, src, &ps, nullptr, nullptr, 0,
-                                      nullptr, &t_emit);
+                                      nullptr, &t_emit, hd);
       if (out < 0) continue;
       if (n < max_records) {
         dom[n] = (uint32_t)out;
         source[n] = (uint32_t)s;
         time_ns[n] = (t_emit + group_index * (ps.path - path0)) / c;
         photon[n] = pid;
+        // weight: the caller's acceptance polynomial in the z component of the
+        // photon's direction at the DOM, clamped to [0, 1]; 1 without one
+        double w = 1.0;
+        if (n_accept > 0) {
+          w = 0.0;
+          double eta_i = 1.0;
+          for (int32_t i = 0; i < n_accept; ++i) {
+            w += accept[i] * eta_i;
+            eta_i *= hd[2];
+          }
+          w = std::min(1.0, std::max(0.0, w));
+        }
+        if (weight) weight[n] = w;
       }
       ++n;
     }

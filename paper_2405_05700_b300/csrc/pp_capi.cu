@@ -51,6 +51,9 @@ struct pp_ctx {
   DevBuf s_src, s_begin, s_ids, s_hits, s_counts, s_misc1, s_misc2, s_misc3, s_misc4, s_bad;
   size_t smem_limit_set = 0;
 
+  int n_accept = 0;                    // hit-record acceptance polynomial
+  float accept[PP_MAX_ACCEPT_COEFFS] = {};
+
   int block_threads = 256;
   int blocks_per_sm = 0;  // 0: occupancy maximum
   int refill = 8;
@@ -211,6 +214,8 @@ RunDev run_params(const pp_ctx* ctx) {
   r.refill = ctx->refill;
   r.ns_per_m_emit = (float)(1.0 / kLightSpeedMperNs);
   r.ns_per_m_path = (float)(kGroupIndexDefault / kLightSpeedMperNs);
+  r.n_accept = ctx->n_accept;
+  for (int i = 0; i < PP_MAX_ACCEPT_COEFFS; ++i) r.accept[i] = ctx->accept[i];
   return r;
 }
 
@@ -1139,6 +1144,19 @@ int pp_set_graphs(pp_ctx* ctx, int32_t enable) {
   PP_CUDA(cudaSetDevice(ctx->cfg.device));
   ctx->graphs = enable != 0;
   if (!ctx->graphs) drop_graphs(ctx);
+  return PP_OK;
+}
+
+int pp_set_hit_acceptance(pp_ctx* ctx, const float* coeffs, int32_t n) {
+  if (!ctx) return PP_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (n < 0 || n > PP_MAX_ACCEPT_COEFFS || (n > 0 && !coeffs))
+    return fail(ctx, PP_EINVAL, "acceptance: 0 <= n <= 8 coefficients");
+  for (int32_t i = 0; i < n; ++i)
+    if (!std::isfinite(coeffs[i])) return fail(ctx, PP_EINVAL, "acceptance: non-finite coefficient");
+  ctx->n_accept = n;
+  for (int i = 0; i < PP_MAX_ACCEPT_COEFFS; ++i) ctx->accept[i] = i < n ? coeffs[i] : 0.0f;
+  ctx->epoch += 1;  // captured graphs hold the old run parameters
   return PP_OK;
 }
 

@@ -570,7 +570,14 @@ __device__ __forceinline__ void record_hit(const WorkDev& W, const RunDev& R, co
     h.dom = (uint32_t)dom;
     h.source = (uint32_t)ph.src;
     h.time_ns = fmaf(ph.path, R.ns_per_m_path, ph.t_emit * R.ns_per_m_emit);
-    h.weight = 1.0f;
+    // acceptance: the caller's polynomial in the direction's z (Horner), in [0, 1]
+    float w = 1.0f;
+    if (R.n_accept > 0) {
+      w = R.accept[R.n_accept - 1];
+      for (int i = R.n_accept - 2; i >= 0; --i) w = fmaf(w, ph.dz, R.accept[i]);
+      w = __saturatef(w);
+    }
+    h.weight = w;
     W.records[i] = h;
   }
 }

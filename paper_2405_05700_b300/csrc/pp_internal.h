@@ -104,6 +104,8 @@ struct RunDev {
   int refill;                 // persistent: refill once this many lanes are idle
   float ns_per_m_emit;        // hit time: emission offset along the segment at c (ns / m)
   float ns_per_m_path;        // hit time: photon path at the group velocity (ns / m)
+  int n_accept;               // hit records: acceptance polynomial in the direction's z
+  float accept[PP_MAX_ACCEPT_COEFFS];
 };
 
 // Shared-memory footprint of the tables the propagation kernels stage.

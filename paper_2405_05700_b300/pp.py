@@ -101,6 +101,7 @@ _SIGS = {
     "pp_debug_gemm": [_vp, _vp, _vp, _i32, _i32, _i32, _i32, _vp],
     "pp_debug_scatter": [_vp, _vp, _vp, _vp, _i64],
     "pp_measure_issue_rate": [_i32, _i32, _vp, _vp],
+    "pp_set_hit_acceptance": [_vp, _vp, _i32],
 }
 EXPORTS = tuple(_SIGS) + ("pp_last_error", "pp_strerror", "pp_server_last_error",
                           "pp_mlp_last_error")
@@ -310,6 +311,16 @@ def pp_debug_scatter(ctx, dir, words, out, n):
 
 def pp_debug_gemm(ctx, A, B, M, N, K, swap_lbo_sbo, C):
     return _call("pp_debug_gemm", ctx, _ptr(A), _ptr(B), M, N, K, swap_lbo_sbo, _ptr(C))
+
+
+PP_MAX_ACCEPT_COEFFS = 8
+
+
+def pp_set_hit_acceptance(ctx, coeffs):
+    """Hit-record weights: clamp(sum c_i eta^i, 0, 1), eta = the direction's z at
+    the DOM; an empty list restores weight 1."""
+    c = np.ascontiguousarray(coeffs if coeffs is not None else [], np.float32)
+    return _call("pp_set_hit_acceptance", ctx, _ptr(c) if c.size else None, int(c.size))
 
 
 PP_ISSUE_FP32_FMA, PP_ISSUE_SFU_LG2 = 0, 1

@@ -87,3 +87,8 @@ def test_surrogate_entry_points_refuse_null_handles(lib):
                                     None) == lib.PP_EINVAL
     assert L.pp_mlp_near_pairs(None, None, 0, ctypes.c_float(1.0), 0, None, None, None) == lib.PP_EINVAL
     assert lib.PP_MLP_ACT_SILU == 0 and lib.PP_MLP_ACT_HARD_SWISH == 1
+
+
+def test_hit_acceptance_is_checked_on_the_host(lib):
+    L = lib._lib
+    assert L.pp_set_hit_acceptance(None, None, 0) == lib.PP_EINVAL

@@ -9,6 +9,9 @@
 * A buffer smaller than the number of hits: the count is the full number,
   and each written record is one of the full run's records, bit for bit.
 * A group index outside [1, 10) is refused.
+* Acceptance weights: with a polynomial set, each record's weight equals the
+  oracle's for the same photon (matched by time within a (source, DOM)) to
+  1e-5; tallies are unchanged; an empty polynomial restores weight 1.
 """
 import numpy as np
 import pytest
@@ -134,3 +137,34 @@ def test_group_index_scales_path_time(pp, tiny):
     t1 = np.sort(r1["time_ns"].astype(np.float64))
     t2 = np.sort(r2["time_ns"].astype(np.float64))
     assert np.allclose(t2, t1 * (1.50 / 1.30), rtol=1e-5)
+
+
+def test_acceptance_weights_match_oracle(pp, tiny, orc):
+    geom, ice = W.geometry_tiny(), W.ice_tiny()
+    src = W.point_source(0.0, 0.0, 0.0, 200_000)
+    batch = W.single_event(src, 5)
+    acc = [0.3, 0.4, 0.2, 0.1]
+    h0, c0, r0, _ = _run(pp, tiny, batch)
+    try:
+        pp.pp_set_hit_acceptance(tiny.ctx, acc)
+        h, c, r, n = _run(pp, tiny, batch)
+    finally:
+        pp.pp_set_hit_acceptance(tiny.ctx, [])
+    assert np.array_equal(h, h0) and np.array_equal(c, c0)
+    assert np.all(r0["weight"] == 1.0) and (r["weight"] < 1.0).any()
+    assert np.all((r["weight"] >= 0.0) & (r["weight"] <= 1.0))
+    o = orc.hit_records(orc.Model(geom, ice, seed=0), 5, src, acceptance=acc)
+    compared, bad = 0, 0
+    for d in range(geom.n_dom):
+        g_sel, o_sel = r["dom"] == d, o["dom"] == d
+        if g_sel.sum() != o_sel.sum() or not g_sel.any():
+            continue
+        ig = np.argsort(r["time_ns"][g_sel])
+        io = np.argsort(o["time_ns"][o_sel])
+        wg = r["weight"][g_sel][ig].astype(np.float64)
+        wo = o["weight"][o_sel][io]
+        compared += len(wg)
+        bad += int(np.sum(np.abs(wg - wo) > 1e-5))
+    assert compared > 0.9 * n and bad <= 1e-3 * compared, (bad, compared)
+    _, _, r1, _ = _run(pp, tiny, batch)
+    assert np.all(r1["weight"] == 1.0)

@@ -9,6 +9,10 @@
   emission point to the sphere.
 * The records' DOM histogram equals the per-DOM hits of the propagation of
   the same event, exactly.
+* Acceptance weights: with a DOM straight below (above) a point source and no
+  scattering, every hitting photon moves down (up) within the DOM's small
+  cone, so each weight lies within the polynomial's range over that cone;
+  constant polynomials above 1 or below 0 clamp to 1 and 0.
 """
 import math
 
@@ -76,3 +80,25 @@ def test_record_histogram_equals_propagated_hits(orc):
     assert np.array_equal(np.bincount(rec["dom"], minlength=geom.n_dom), hits[0])
     assert set(np.unique(rec["source"])) <= {0, 1}
     assert np.all(rec["time_ns"] > 0)
+
+
+def test_acceptance_weights_follow_the_incidence_direction(orc):
+    d, r = 10.0, 1.0
+    ice = W.ice_homogeneous(0.0, 0.0, g=0.9, n_layers=1, depth_top=0.0)
+    acc = [0.25, 0.5, 0.25]                      # 0.25 (1 + eta)^2
+
+    def poly(eta):
+        return 0.25 * (1.0 + eta) ** 2
+
+    eta_min = math.sqrt(1 - r * r / (d * d))    # the cone's edge: |eta| >= cos of its half-angle
+    for zc, lo, hi in ((-d, poly(-1.0), poly(-eta_min)), (d, poly(eta_min), poly(1.0))):
+        m = orc.Model(_one_dom([0.0, 0.0, zc], r), ice, seed=3, world_margin=1000.0)
+        rec = orc.hit_records(m, 1, W.point_source(0, 0, 0, 200_000), acceptance=acc)
+        assert rec["n"] > 200
+        w = rec["weight"]
+        assert w.min() >= lo - 1e-12 and w.max() <= hi + 1e-12, (zc, w.min(), w.max(), lo, hi)
+    m = orc.Model(_one_dom([0.0, 0.0, -d], r), ice, seed=3, world_margin=1000.0)
+    src = W.point_source(0, 0, 0, 50_000)
+    assert np.all(orc.hit_records(m, 1, src)["weight"] == 1.0)
+    assert np.all(orc.hit_records(m, 1, src, acceptance=[2.0])["weight"] == 1.0)
+    assert np.all(orc.hit_records(m, 1, src, acceptance=[-0.5])["weight"] == 0.0)
