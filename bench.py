@@ -244,7 +244,8 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD, "events": batch.n_events,
-                       "photons_per_step": batch.total_photons(), "parallelism": "replicas"},
+                       "photons_per_step": batch.total_photons(),
+                       "parallelism": "replicas" if world > 1 else "single"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"each step: first {sample.n_events} events "
                                        f"({n} photons), {cores} threads"},
