@@ -40,10 +40,10 @@ __device__ __forceinline__ void pair_features(const FeatGeom& fg, const pp_sourc
   const float ex = c.x - px, ey = c.y - py, ez = c.z - pz;
   const float r = sqrtf(ex * ex + ey * ey + ez * ez);
   const float rr = fmaxf(r, 1e-3f);
-  const float cs = (dx * ex + dy * ey + dz * ez) / rr;
+  const float cs = __fdividef(dx * ex + dy * ey + dz * ez, rr);
   const float th = acosf(fminf(1.0f, fmaxf(-1.0f, cs)));
   const float delta = th - fg.theta_c;
-  const float rho = r * sinf(delta);
+  const float rho = r * __sinf(delta);
   // point values and line means of the layer profile
   const float us = (fg.z_top - pz) / fg.dz, ud = (fg.z_top - c.z) / fg.dz;
   const int is = feat_layer(fg, us), id = feat_layer(fg, ud);
@@ -58,40 +58,43 @@ __device__ __forceinline__ void pair_features(const FeatGeom& fg, const pp_sourc
     mb = ((cd.x - cs_.x) + fd * bd - fs * bs) / du;
     ma = ((cd.y - cs_.y) + fd * ad - fs * as) / du;
   }
-  const float pi = 3.14159265358979f;
+  // Every input is rounded to BF16 (8 significant bits), so the scalings use
+  // constant reciprocals and the exponentials, logarithm and sine the SFU
+  // forms (errors of order 1e-6 relative, far below one BF16 step).
+  const float inv_pi = 0.318309886183791f;
   float f[kIn];
-  f[0] = px / 500.0f;
-  f[1] = py / 500.0f;
-  f[2] = pz / 500.0f;
-  f[3] = acosf(fminf(1.0f, fmaxf(-1.0f, dz))) / pi;
-  f[4] = atan2f(dy, dx) / pi;
-  f[5] = ex / 100.0f;
-  f[6] = ey / 100.0f;
-  f[7] = ez / 100.0f;
+  f[0] = px * (1.0f / 500.0f);
+  f[1] = py * (1.0f / 500.0f);
+  f[2] = pz * (1.0f / 500.0f);
+  f[3] = acosf(fminf(1.0f, fmaxf(-1.0f, dz))) * inv_pi;
+  f[4] = atan2f(dy, dx) * inv_pi;
+  f[5] = ex * (1.0f / 100.0f);
+  f[6] = ey * (1.0f / 100.0f);
+  f[7] = ez * (1.0f / 100.0f);
   f[8] = bs * 10.0f;
   f[9] = as * 50.0f;
   f[10] = dx;
   f[11] = dy;
   f[12] = dz;
-  f[13] = r / 100.0f;
+  f[13] = r * (1.0f / 100.0f);
   f[14] = cs;
-  f[15] = log1pf(r) / 5.0f;
+  f[15] = __logf(1.0f + r) * (1.0f / 5.0f);
   f[16] = 2.0f * delta;
-  f[17] = rho / 10.0f;
-  f[18] = expf(-fabsf(rho) / 2.0f);
+  f[17] = rho * (1.0f / 10.0f);
+  f[18] = __expf(-0.5f * fabsf(rho));
   f[19] = bd * 10.0f;
   f[20] = ad * 50.0f;
   f[21] = mb * 10.0f;
   f[22] = ma * 50.0f;
   f[23] = r * ma;
-  f[24] = r * mb / 10.0f;
-  f[25] = expf(-r / 10.0f);
-  f[26] = expf(-r / 30.0f);
-  f[27] = expf(-r / 100.0f);
-  f[28] = c.z / 500.0f;
-  f[29] = ez / rr;
-  f[30] = 1.0f / (1.0f + r / 5.0f);
-  f[31] = r * sqrtf(fmaxf(0.0f, 1.0f - cs * cs)) / 100.0f;
+  f[24] = r * mb * (1.0f / 10.0f);
+  f[25] = __expf(r * (-1.0f / 10.0f));
+  f[26] = __expf(r * (-1.0f / 30.0f));
+  f[27] = __expf(r * (-1.0f / 100.0f));
+  f[28] = c.z * (1.0f / 500.0f);
+  f[29] = __fdividef(ez, rr);
+  f[30] = __fdividef(1.0f, fmaf(r, 1.0f / 5.0f, 1.0f));
+  f[31] = r * sqrtf(fmaxf(0.0f, 1.0f - cs * cs)) * (1.0f / 100.0f);
 #pragma unroll
   for (int i = 0; i < kIn; ++i) out[i] = __float2bfloat16_rn(f[i]);
 }
