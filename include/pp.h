@@ -525,10 +525,9 @@ int pp_debug_scatter(pp_ctx* ctx, const float* dir, const uint32_t* words, float
 
 /* The tensor-core GEMM of the surrogate on host data: C[M][N] = A[M][K] . B[N][K]^T
  * with A, B BF16 (raw 16-bit patterns, row-major) and C FP32.  16 <= N <= 256,
- * N and K multiples of 16.  swap_lbo_sbo = 1 exchanges the two strides of the
- * shared-memory operand descriptors (a layout probe; results are then wrong). */
+ * N and K multiples of 16. */
 int pp_debug_gemm(pp_ctx* ctx, const uint16_t* A, const uint16_t* B, int32_t M, int32_t N,
-                  int32_t K, int32_t swap_lbo_sbo, float* C);
+                  int32_t K, float* C);
 
 /* The device hit test on given segments: first DOM met on [p, p + S d].
  *   seg[n][7]   p (3), d (3, unit), S

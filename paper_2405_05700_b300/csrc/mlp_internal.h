@@ -16,7 +16,6 @@ struct GemmArgs {
   const __nv_bfloat16* B;  // [N][ldb], K contiguous
   int M, N, K, lda, ldb, ldc;
   int bn;                  // N tile: multiple of 16, <= 256
-  int swap_lbo_sbo;        // layout probe: exchange the descriptor strides
   float* Cf;
   int* err;
 };

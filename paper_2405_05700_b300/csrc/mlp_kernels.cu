@@ -76,8 +76,7 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
   const uint32_t idesc = tc::idesc_bf16(kBM, BN);
   // descriptor strides: K-direction core matrices 128 B apart, 8-row groups
   // kBK * 16 B apart (exchanged when probing the layout)
-  const uint32_t lbo = g.swap_lbo_sbo ? kBK * 16 : 128;
-  const uint32_t sbo = g.swap_lbo_sbo ? 128 : kBK * 16;
+  const uint32_t lbo = 128, sbo = kBK * 16;  // K-direction and row-direction core-matrix strides
   uint32_t phase[2] = {0u, 0u};
   bool pending[2] = {false, false};
   bool ok = true;

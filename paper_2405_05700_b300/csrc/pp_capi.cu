@@ -1296,7 +1296,7 @@ int pp_debug_scatter(pp_ctx* ctx, const float* dir, const uint32_t* words, float
 }
 
 int pp_debug_gemm(pp_ctx* ctx, const uint16_t* A, const uint16_t* B, int32_t M, int32_t N,
-                  int32_t K, int32_t swap_lbo_sbo, float* C) {
+                  int32_t K, float* C) {
   if (!ctx) return PP_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (!A || !B || !C || M < 1 || N < 16 || N > 256 || N % 16 || K < 16 || K % 16)
@@ -1320,7 +1320,6 @@ int pp_debug_gemm(pp_ctx* ctx, const uint16_t* A, const uint16_t* B, int32_t M, 
   g.ldb = K;
   g.ldc = N;
   g.bn = N;
-  g.swap_lbo_sbo = swap_lbo_sbo;
   g.Cf = static_cast<float*>(ctx->s_misc3.p);
   g.err = static_cast<int*>(ctx->err.p);
   PP_CUDA(mlp::launch_gemm(g, st));

@@ -98,7 +98,7 @@ _SIGS = {
     "pp_debug_philox": [_vp, _vp, _vp, _vp, _i64],
     "pp_debug_trace": [_vp, _u64, _vp, _i64, _vp, _i64, _i32, _vp, _vp, _vp, _vp],
     "pp_debug_first_hit": [_vp, _vp, _i64, _i32, _vp, _vp],
-    "pp_debug_gemm": [_vp, _vp, _vp, _i32, _i32, _i32, _i32, _vp],
+    "pp_debug_gemm": [_vp, _vp, _vp, _i32, _i32, _i32, _vp],
     "pp_debug_scatter": [_vp, _vp, _vp, _vp, _i64],
     "pp_measure_issue_rate": [_i32, _i32, _vp, _vp],
     "pp_set_hit_acceptance": [_vp, _vp, _i32],
@@ -309,8 +309,8 @@ def pp_debug_scatter(ctx, dir, words, out, n):
     return _call("pp_debug_scatter", ctx, _ptr(dir), _ptr(words), _ptr(out), n)
 
 
-def pp_debug_gemm(ctx, A, B, M, N, K, swap_lbo_sbo, C):
-    return _call("pp_debug_gemm", ctx, _ptr(A), _ptr(B), M, N, K, swap_lbo_sbo, _ptr(C))
+def pp_debug_gemm(ctx, A, B, M, N, K, C):
+    return _call("pp_debug_gemm", ctx, _ptr(A), _ptr(B), M, N, K, _ptr(C))
 
 
 PP_MAX_ACCEPT_COEFFS = 8

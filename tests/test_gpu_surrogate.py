@@ -58,7 +58,7 @@ def test_tensor_core_gemm(pp, prop, M, N, K):
     A = pp.bf16_bits(rng.normal(size=(M, K)))
     B = pp.bf16_bits(rng.normal(size=(N, K)))
     C = np.zeros((M, N), np.float32)
-    pp.pp_debug_gemm(prop.ctx, A, B, M, N, K, 0, C)
+    pp.pp_debug_gemm(prop.ctx, A, B, M, N, K, C)
     ref = pp.bf16_value(A).astype(np.float64) @ pp.bf16_value(B).astype(np.float64).T
     assert np.max(np.abs(C - ref)) <= 2e-6 * np.sqrt(K) * np.abs(ref).max() + 1e-6
 
