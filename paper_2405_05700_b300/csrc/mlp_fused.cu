@@ -563,10 +563,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd(BwdArgs a) {
         const __nv_bfloat16* zrow = a.z[lo] + (size_t)row * kHid + c_begin;
         __nv_bfloat16* dzt = a.dz[lo];
         const bool last = j == kBwdLayers - 1;
-        auto consume = [&](const uint32_t (&raw)[32], int c0) {
-          uint32_t packed[16];
+        auto consume = [&](const uint32_t (&raw)[kEpiCols], int c0) {
+          uint32_t packed[kEpiCols / 2];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
+          for (int i = 0; i < kEpiCols / 8; ++i) {
             uint4 zv = make_uint4(0, 0, 0, 0);
             if (valid) zv = *reinterpret_cast<const uint4*>(zrow + c0 + 8 * i);
             const uint32_t zw[4] = {zv.x, zv.y, zv.z, zv.w};
@@ -581,7 +581,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd(BwdArgs a) {
           }
           if (!last) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < kEpiCols / 8; ++i)
               *reinterpret_cast<uint4*>(sH + tc::tile_off(r, c_begin + c0 + 8 * i, kHid)) =
                   make_uint4(packed[4 * i], packed[4 * i + 1], packed[4 * i + 2],
                              packed[4 * i + 3]);
@@ -590,7 +590,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd(BwdArgs a) {
             // dL/dz K-tiled ([256][n]), the weight-gradient kernel's A operand
             unsigned char* dt = reinterpret_cast<unsigned char*>(dzt);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
+            for (int j = 0; j < kEpiCols / 2; ++j) {
               const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(&packed[j]);
               const uint32_t m = (uint32_t)(c_begin + c0 + 2 * j);
               *reinterpret_cast<__nv_bfloat16*>(dt + kt_off(m, (uint32_t)row, kHid)) = __low2bfloat16(v);
@@ -599,19 +599,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd(BwdArgs a) {
             }
           }
         };
-        uint32_t ra[32], rb[32];
-        tc::tmem_ld32_nowait(tacc + 0, ra);
+        // two register sets: the next TMEM load is in flight while one is converted
+        uint32_t ra[kEpiCols], rb[kEpiCols];
+        epi_ld(tacc + 0, ra);
         tc::tmem_wait_ld(ra);
-        tc::tmem_ld32_nowait(tacc + 32, rb);
-        consume(ra, 0);
-        tc::tmem_wait_ld(rb);
-        tc::tmem_ld32_nowait(tacc + 64, ra);
-        consume(rb, 32);
-        tc::tmem_wait_ld(ra);
-        tc::tmem_ld32_nowait(tacc + 96, rb);
-        consume(ra, 64);
-        tc::tmem_wait_ld(rb);
-        consume(rb, 96);
+#pragma unroll
+        for (int c0 = 0; c0 < kColsPerWarp; c0 += 2 * kEpiCols) {
+          epi_ld(tacc + c0 + kEpiCols, rb);
+          consume(ra, c0);
+          tc::tmem_wait_ld(rb);
+          if (c0 + 2 * kEpiCols < kColsPerWarp) epi_ld(tacc + c0 + 2 * kEpiCols, ra);
+          consume(rb, c0 + kEpiCols);
+          if (c0 + 2 * kEpiCols < kColsPerWarp) tc::tmem_wait_ld(ra);
+        }
         if (!last) {
           tc::fence_smem_async();
           tc::fence_before_sync();
