@@ -506,6 +506,19 @@ def test_host_batch_pipeline_equals_device_batch(pp, full):
     assert ei.value.code == pp.PP_EINVAL and str(len(src) * 3 // 4) in str(ei.value)
     h2, c2 = full.propagate_batch(b)                 # the context stays usable
     assert np.array_equal(h2, h) and np.array_equal(c2, c)
+    # with CUDA graphs on: the host path (two compute streams, two scratch
+    # sets) and the device path interleaved, each twice, all equal
+    pp.pp_set_graphs(full.ctx, True)
+    try:
+        for _ in range(2):
+            hg, cg = full.propagate_batch(b)
+            assert np.array_equal(hg, h) and np.array_equal(cg, c)
+            hd.zero_()
+            pp.pp_propagate_batch_async(full.ctx, b.n_events, d_ids, d_beg, d_src, len(src), hd, cd)
+            pp.pp_sync(full.ctx)
+            assert np.array_equal(h, hd.cpu().numpy().view(np.uint64).astype(h.dtype))
+    finally:
+        pp.pp_set_graphs(full.ctx, False)
 
 
 def test_sources_outside_the_world_and_the_ice_table(full, tiny, orc):
