@@ -303,23 +303,19 @@ __global__ void __launch_bounds__(256) k_head_reduce(const float* part, const do
 }
 
 // Is candidate i = (source s0 + i / n_dom, DOM i % n_dom) within r_max?  The
-// distance is from the segment's midpoint to the DOM centre, as in the features.
+// distance is from the segment's midpoint to the DOM centre, as in the
+// features; the test compares squares (no square root or division per pair).
 __device__ __forceinline__ bool pair_near(const FeatGeom& fg, const pp_source* src, int64_t s0,
                                           int64_t i, float r_max, int64_t& s, int& d) {
   s = s0 + i / fg.n_dom;
   d = (int)(i % fg.n_dom);
   const pp_source q = src[s];
-  float dx = q.dx, dy = q.dy, dz = q.dz;
-  const float nn = sqrtf(dx * dx + dy * dy + dz * dz);
-  if (nn > 0.0f) {
-    dx /= nn;
-    dy /= nn;
-    dz /= nn;
-  }
-  const float h = 0.5f * q.length;
+  const float nn = fmaf(q.dx, q.dx, fmaf(q.dy, q.dy, q.dz * q.dz));
+  const float h = nn > 0.0f ? 0.5f * q.length * rsqrtf(nn) : 0.0f;  // half length / |d|
   const float4 c = fg.dom[d];
-  const float ex = c.x - (q.x + h * dx), ey = c.y - (q.y + h * dy), ez = c.z - (q.z + h * dz);
-  return sqrtf(ex * ex + ey * ey + ez * ez) <= r_max;
+  const float ex = c.x - fmaf(h, q.dx, q.x), ey = c.y - fmaf(h, q.dy, q.y),
+              ez = c.z - fmaf(h, q.dz, q.z);
+  return fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= r_max * r_max;
 }
 
 // Pairs of sources [s0, s0 + ns) x all DOMs within r_max, appended in any
