@@ -26,8 +26,19 @@ __device__ __forceinline__ int feat_layer(const FeatGeom& fg, float u) {
 //   23 r x mean a, 24 r x mean b_e / 10, 25-27 exp(-r / 10, 30, 100 m),
 //   28 DOM z / 500 m, 29 e_z / max(r, 1 mm), 30 1 / (1 + r / 5 m),
 //   31 r sin(acos c) / 100 m.
-__device__ __forceinline__ void pair_features(const FeatGeom& fg, const pp_source& s, float4 c,
-                                              __nv_bfloat16* out) {
+// What the features take from the source alone (shared by all its pairs).
+struct __align__(16) SrcPrep {
+  float px, py, pz;  // segment midpoint
+  float dx, dy, dz;  // unit direction
+  float us;          // layer coordinate of the midpoint
+  float bs, as;      // effective scattering and absorption there
+  float f3, f4;      // polar angle / pi, azimuth / pi
+  int is;            // layer index of the midpoint
+};
+static_assert(sizeof(SrcPrep) == 48, "three 16-byte loads");
+
+__device__ __forceinline__ SrcPrep source_prep(const FeatGeom& fg, const pp_source& s) {
+  SrcPrep P;
   float dx = s.dx, dy = s.dy, dz = s.dz;
   const float nn = sqrtf(dx * dx + dy * dy + dz * dz);
   if (nn > 0.0f) {
@@ -36,7 +47,27 @@ __device__ __forceinline__ void pair_features(const FeatGeom& fg, const pp_sourc
     dz /= nn;
   }
   const float h = 0.5f * s.length;
-  const float px = s.x + h * dx, py = s.y + h * dy, pz = s.z + h * dz;
+  P.px = s.x + h * dx;
+  P.py = s.y + h * dy;
+  P.pz = s.z + h * dz;
+  P.dx = dx;
+  P.dy = dy;
+  P.dz = dz;
+  P.us = (fg.z_top - P.pz) / fg.dz;
+  P.is = feat_layer(fg, P.us);
+  const float4 Ls = fg.layer[P.is];
+  P.bs = Ls.x * fg.be_over_b;
+  P.as = Ls.y;
+  const float inv_pi = 0.318309886183791f;
+  P.f3 = acosf(fminf(1.0f, fmaxf(-1.0f, dz))) * inv_pi;
+  P.f4 = atan2f(dy, dx) * inv_pi;
+  return P;
+}
+
+// The pair's features from its source's part and the DOM centre c.
+__device__ __forceinline__ void pair_features(const FeatGeom& fg, const SrcPrep& P, float4 c,
+                                              __nv_bfloat16* out) {
+  const float px = P.px, py = P.py, pz = P.pz, dx = P.dx, dy = P.dy, dz = P.dz;
   const float ex = c.x - px, ey = c.y - py, ez = c.z - pz;
   const float r = sqrtf(ex * ex + ey * ey + ez * ez);
   const float rr = fmaxf(r, 1e-3f);
@@ -45,10 +76,10 @@ __device__ __forceinline__ void pair_features(const FeatGeom& fg, const pp_sourc
   const float delta = th - fg.theta_c;
   const float rho = r * __sinf(delta);
   // point values and line means of the layer profile
-  const float us = (fg.z_top - pz) / fg.dz, ud = (fg.z_top - c.z) / fg.dz;
-  const int is = feat_layer(fg, us), id = feat_layer(fg, ud);
-  const float4 Ls = fg.layer[is], Ld = fg.layer[id];
-  const float bs = Ls.x * fg.be_over_b, as = Ls.y;
+  const float us = P.us, ud = (fg.z_top - c.z) / fg.dz;
+  const int is = P.is, id = feat_layer(fg, ud);
+  const float4 Ld = fg.layer[id];
+  const float bs = P.bs, as = P.as;
   const float bd = Ld.x * fg.be_over_b, ad = Ld.y;
   float mb = bs, ma = as;
   if (is != id) {
@@ -61,13 +92,12 @@ __device__ __forceinline__ void pair_features(const FeatGeom& fg, const pp_sourc
   // Every input is rounded to BF16 (8 significant bits), so the scalings use
   // constant reciprocals and the exponentials, logarithm and sine the SFU
   // forms (errors of order 1e-6 relative, far below one BF16 step).
-  const float inv_pi = 0.318309886183791f;
   float f[kIn];
   f[0] = px * (1.0f / 500.0f);
   f[1] = py * (1.0f / 500.0f);
   f[2] = pz * (1.0f / 500.0f);
-  f[3] = acosf(fminf(1.0f, fmaxf(-1.0f, dz))) * inv_pi;
-  f[4] = atan2f(dy, dx) * inv_pi;
+  f[3] = P.f3;
+  f[4] = P.f4;
   f[5] = ex * (1.0f / 100.0f);
   f[6] = ey * (1.0f / 100.0f);
   f[7] = ez * (1.0f / 100.0f);
@@ -97,6 +127,11 @@ __device__ __forceinline__ void pair_features(const FeatGeom& fg, const pp_sourc
   f[31] = r * sqrtf(fmaxf(0.0f, 1.0f - cs * cs)) * (1.0f / 100.0f);
 #pragma unroll
   for (int i = 0; i < kIn; ++i) out[i] = __float2bfloat16_rn(f[i]);
+}
+
+__device__ __forceinline__ void pair_features(const FeatGeom& fg, const pp_source& s, float4 c,
+                                              __nv_bfloat16* out) {
+  pair_features(fg, source_prep(fg, s), c, out);
 }
 
 }  // namespace mlp

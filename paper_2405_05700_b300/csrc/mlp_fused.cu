@@ -241,7 +241,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
         if (valid) {
           if (kFromPairs) {
             __align__(16) __nv_bfloat16 fb[kIn];
-            pair_features(a.fg, a.src[a.ps[row]], a.fg.dom[a.pd[row]], fb);
+            const int sidx = a.ps[row];
+            if (a.sprep)
+              pair_features(a.fg, a.sprep[sidx - a.sprep_base], a.fg.dom[a.pd[row]], fb);
+            else
+              pair_features(a.fg, a.src[sidx], a.fg.dom[a.pd[row]], fb);
 #pragma unroll
             for (int i = 0; i < kIn / 8; ++i) fv[i] = *reinterpret_cast<const uint4*>(fb + 8 * i);
           } else {

@@ -58,6 +58,12 @@ __device__ __forceinline__ float act_grad(int act, float z) {
   return sg * (1.0f + z * (1.0f - sg));
 }
 
+struct SrcPrep;  // per-source part of the features (mlp_features.cuh)
+
+// The per-source part of the features of sources [s0, s0 + ns) into out[ns].
+cudaError_t launch_src_prep(const FeatGeom& fg, const pp_source* src, int64_t s0, int64_t ns,
+                            SrcPrep* out, cudaStream_t st);
+
 // Features of pairs (source s, DOM d) as BF16 [n][32].
 cudaError_t launch_features(const FeatGeom& fg, const pp_source* src, const int32_t* pair_src,
                             const int32_t* pair_dom, int64_t n, __nv_bfloat16* feat,
@@ -103,6 +109,8 @@ cudaError_t launch_near_pairs_ordered(const FeatGeom& fg, const pp_source* src, 
 struct FusedArgs {
   FeatGeom fg;
   const pp_source* src;          // pairs mode
+  const SrcPrep* sprep;          // pairs mode, optional: sprep[s - sprep_base] for source s
+  int64_t sprep_base;
   const int32_t* ps;
   const int32_t* pd;
   const __nv_bfloat16* feat;     // rows mode: [n][kIn]

@@ -466,6 +466,12 @@ __global__ void k_gather_rows(const uint4* feat, const float* nph, const float* 
   }
 }
 
+__global__ void k_src_prep(FeatGeom fg, const pp_source* src, int64_t s0, int64_t ns,
+                           SrcPrep* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ns) out[i] = source_prep(fg, src[s0 + i]);
+}
+
 // ----------------------------------------------------------- utilities --
 __global__ void k_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1,
                        float b2, float eps, float bc1, float bc2, __nv_bfloat16* pb) {
@@ -561,6 +567,13 @@ cudaError_t launch_gather_rows(const __nv_bfloat16* feat, const float* nph, cons
   k_gather_rows<<<blocks_for(n * 4, 256), 256, 0, st>>>(
       reinterpret_cast<const uint4*>(feat), nph, cnt, n_rows, rows, n,
       reinterpret_cast<uint4*>(feat_out), nph_out, cnt_out, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_src_prep(const FeatGeom& fg, const pp_source* src, int64_t s0, int64_t ns,
+                            SrcPrep* out, cudaStream_t st) {
+  if (ns <= 0) return cudaSuccess;
+  k_src_prep<<<blocks_for(ns, 256), 256, 0, st>>>(fg, src, s0, ns, out);
   return cudaGetLastError();
 }
 

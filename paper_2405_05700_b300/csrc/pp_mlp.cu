@@ -14,6 +14,7 @@
 #include <cstring>
 #include <string>
 
+#include "mlp_features.cuh"
 #include "mlp_internal.h"
 #include "pp.h"
 #include "pp_internal.h"
@@ -78,6 +79,8 @@ struct pp_mlp {
   int sms = 0;
   int32_t *ps = nullptr, *pd = nullptr;
   unsigned long long* count = nullptr;
+  SrcPrep* sprep = nullptr;            // per-source feature part of one dom_sums pass
+  int64_t sprep_cap = 0;
   // ordered pair search: per-block counts and offsets (grown on demand)
   uint32_t* near_bcount = nullptr;
   unsigned long long* near_boff = nullptr;
@@ -282,6 +285,8 @@ int pp_mlp_create(pp_ctx* ctx, int32_t max_batch, int64_t max_rows, pp_mlp** out
   PP_A(dalloc(&m->ps, (size_t)max_rows));
   PP_A(dalloc(&m->pd, (size_t)max_rows));
   PP_A(dalloc(&m->count, 1));
+  m->sprep_cap = m->fg.n_dom > 0 ? std::max<int64_t>(1, 8 * (max_rows / m->fg.n_dom)) : 1;
+  PP_A(dalloc(&m->sprep, (size_t)m->sprep_cap));
   PP_A(cudaMemset(m->loss, 0, sizeof(double)));
   PP_A(cudaMemset(m->err, 0, 64 * sizeof(int)));
   PP_A(cudaMemset(m->p, 0, sizeof(float) * kNParams));
@@ -302,7 +307,7 @@ int pp_mlp_destroy(pp_mlp* m) {
   void* bufs[] = {m->p,   m->g,     m->m,         m->v,  m->t1, m->t2,    m->loss, m->err,
                   m->wpack, m->wpack_bwd, m->ps, m->pd, m->count, m->ice_cum, m->dw_part,
                   m->head_part, m->head_lpart, m->near_bcount, m->near_boff, m->bfeat,
-                  m->bnph, m->bcnt};
+                  m->bnph, m->bcnt, m->sprep};
   for (void* b : bufs) cudaFree(b);
   for (int l = 0; l < kLayers; ++l) {
     cudaFree(m->wb[l]);
@@ -485,6 +490,11 @@ int pp_mlp_dom_sums(pp_mlp* m, const pp_source* d_src, int64_t n_src, const floa
     if (cnt > 0) {
       FusedArgs a = fused_args(m);
       a.src = d_src;
+      if (ns <= m->sprep_cap) {  // the sources' part of the features, once per source
+        PP_MLP_CUDA(launch_src_prep(m->fg, d_src, s0, ns, m->sprep, st));
+        a.sprep = m->sprep;
+        a.sprep_base = s0;
+      }
       a.ps = m->ps;
       a.pd = m->pd;
       a.n = (int64_t)cnt;
