@@ -64,69 +64,81 @@ __device__ __forceinline__ SrcPrep source_prep(const FeatGeom& fg, const pp_sour
   return P;
 }
 
-// The pair's features from its source's part and the DOM centre c.
-__device__ __forceinline__ void pair_features(const FeatGeom& fg, const SrcPrep& P, float4 c,
-                                              __nv_bfloat16* out) {
+// Features kPart * 16 .. + 15 of the pair from its source's part and the DOM
+// centre c (two halves, so that two threads can share a row's work).
+template <int kPart>
+__device__ __forceinline__ void pair_features_half(const FeatGeom& fg, const SrcPrep& P, float4 c,
+                                                   __nv_bfloat16* out) {
   const float px = P.px, py = P.py, pz = P.pz, dx = P.dx, dy = P.dy, dz = P.dz;
   const float ex = c.x - px, ey = c.y - py, ez = c.z - pz;
   const float r = sqrtf(ex * ex + ey * ey + ez * ez);
   const float rr = fmaxf(r, 1e-3f);
   const float cs = __fdividef(dx * ex + dy * ey + dz * ez, rr);
-  const float th = acosf(fminf(1.0f, fmaxf(-1.0f, cs)));
-  const float delta = th - fg.theta_c;
-  const float rho = r * __sinf(delta);
-  // point values and line means of the layer profile
-  const float us = P.us, ud = (fg.z_top - c.z) / fg.dz;
-  const int is = P.is, id = feat_layer(fg, ud);
-  const float4 Ld = fg.layer[id];
-  const float bs = P.bs, as = P.as;
-  const float bd = Ld.x * fg.be_over_b, ad = Ld.y;
-  float mb = bs, ma = as;
-  if (is != id) {
-    const float2 cs_ = fg.cum[is], cd = fg.cum[id];
-    const float fs = us - (float)is, fd = ud - (float)id;
-    const float du = ud - us;
-    mb = ((cd.x - cs_.x) + fd * bd - fs * bs) / du;
-    ma = ((cd.y - cs_.y) + fd * ad - fs * as) / du;
-  }
   // Every input is rounded to BF16 (8 significant bits), so the scalings use
   // constant reciprocals and the exponentials, logarithm and sine the SFU
   // forms (errors of order 1e-6 relative, far below one BF16 step).
-  float f[kIn];
-  f[0] = px * (1.0f / 500.0f);
-  f[1] = py * (1.0f / 500.0f);
-  f[2] = pz * (1.0f / 500.0f);
-  f[3] = P.f3;
-  f[4] = P.f4;
-  f[5] = ex * (1.0f / 100.0f);
-  f[6] = ey * (1.0f / 100.0f);
-  f[7] = ez * (1.0f / 100.0f);
-  f[8] = bs * 10.0f;
-  f[9] = as * 50.0f;
-  f[10] = dx;
-  f[11] = dy;
-  f[12] = dz;
-  f[13] = r * (1.0f / 100.0f);
-  f[14] = cs;
-  f[15] = __logf(1.0f + r) * (1.0f / 5.0f);
-  f[16] = 2.0f * delta;
-  f[17] = rho * (1.0f / 10.0f);
-  f[18] = __expf(-0.5f * fabsf(rho));
-  f[19] = bd * 10.0f;
-  f[20] = ad * 50.0f;
-  f[21] = mb * 10.0f;
-  f[22] = ma * 50.0f;
-  f[23] = r * ma;
-  f[24] = r * mb * (1.0f / 10.0f);
-  f[25] = __expf(r * (-1.0f / 10.0f));
-  f[26] = __expf(r * (-1.0f / 30.0f));
-  f[27] = __expf(r * (-1.0f / 100.0f));
-  f[28] = c.z * (1.0f / 500.0f);
-  f[29] = __fdividef(ez, rr);
-  f[30] = __fdividef(1.0f, fmaf(r, 1.0f / 5.0f, 1.0f));
-  f[31] = r * sqrtf(fmaxf(0.0f, 1.0f - cs * cs)) * (1.0f / 100.0f);
+  float f[kIn / 2];
+  if (kPart == 0) {
+    f[0] = px * (1.0f / 500.0f);
+    f[1] = py * (1.0f / 500.0f);
+    f[2] = pz * (1.0f / 500.0f);
+    f[3] = P.f3;
+    f[4] = P.f4;
+    f[5] = ex * (1.0f / 100.0f);
+    f[6] = ey * (1.0f / 100.0f);
+    f[7] = ez * (1.0f / 100.0f);
+    f[8] = P.bs * 10.0f;
+    f[9] = P.as * 50.0f;
+    f[10] = dx;
+    f[11] = dy;
+    f[12] = dz;
+    f[13] = r * (1.0f / 100.0f);
+    f[14] = cs;
+    f[15] = __logf(1.0f + r) * (1.0f / 5.0f);
+  } else {
+    const float th = acosf(fminf(1.0f, fmaxf(-1.0f, cs)));
+    const float delta = th - fg.theta_c;
+    const float rho = r * __sinf(delta);
+    // point values and line means of the layer profile
+    const float us = P.us, ud = (fg.z_top - c.z) / fg.dz;
+    const int is = P.is, id = feat_layer(fg, ud);
+    const float4 Ld = fg.layer[id];
+    const float bs = P.bs, as = P.as;
+    const float bd = Ld.x * fg.be_over_b, ad = Ld.y;
+    float mb = bs, ma = as;
+    if (is != id) {
+      const float2 cs_ = fg.cum[is], cd = fg.cum[id];
+      const float fs = us - (float)is, fd = ud - (float)id;
+      const float du = ud - us;
+      mb = ((cd.x - cs_.x) + fd * bd - fs * bs) / du;
+      ma = ((cd.y - cs_.y) + fd * ad - fs * as) / du;
+    }
+    f[0] = 2.0f * delta;
+    f[1] = rho * (1.0f / 10.0f);
+    f[2] = __expf(-0.5f * fabsf(rho));
+    f[3] = bd * 10.0f;
+    f[4] = ad * 50.0f;
+    f[5] = mb * 10.0f;
+    f[6] = ma * 50.0f;
+    f[7] = r * ma;
+    f[8] = r * mb * (1.0f / 10.0f);
+    f[9] = __expf(r * (-1.0f / 10.0f));
+    f[10] = __expf(r * (-1.0f / 30.0f));
+    f[11] = __expf(r * (-1.0f / 100.0f));
+    f[12] = c.z * (1.0f / 500.0f);
+    f[13] = __fdividef(ez, rr);
+    f[14] = __fdividef(1.0f, fmaf(r, 1.0f / 5.0f, 1.0f));
+    f[15] = r * sqrtf(fmaxf(0.0f, 1.0f - cs * cs)) * (1.0f / 100.0f);
+  }
 #pragma unroll
-  for (int i = 0; i < kIn; ++i) out[i] = __float2bfloat16_rn(f[i]);
+  for (int i = 0; i < kIn / 2; ++i) out[i] = __float2bfloat16_rn(f[i]);
+}
+
+// All 32 features of the pair.
+__device__ __forceinline__ void pair_features(const FeatGeom& fg, const SrcPrep& P, float4 c,
+                                              __nv_bfloat16* out) {
+  pair_features_half<0>(fg, P, c, out);
+  pair_features_half<1>(fg, P, c, out + kIn / 2);
 }
 
 __device__ __forceinline__ void pair_features(const FeatGeom& fg, const pp_source& s, float4 c,

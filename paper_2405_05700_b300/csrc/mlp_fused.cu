@@ -234,33 +234,43 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
       const int64_t row = t * kRows + h * kHalf + r;
       const bool valid = row < a.n;
       // features of this row as the first MMA's A operand (aliasing the activations)
-      if (cg == 0) {
+      if (kFromPairs) {
+        // pairs: column group g computes features 16 g .. 16 g + 15 of the row
+        uint4 fv[kIn / 16];
+#pragma unroll
+        for (int i = 0; i < kIn / 16; ++i) fv[i] = make_uint4(0, 0, 0, 0);
+        if (valid) {
+          __align__(16) __nv_bfloat16 fb[kIn / 2];
+          const int sidx = a.ps[row];
+          const SrcPrep P = a.sprep ? a.sprep[sidx - a.sprep_base] : source_prep(a.fg, a.src[sidx]);
+          const float4 c = a.fg.dom[a.pd[row]];
+          if (cg == 0)
+            pair_features_half<0>(a.fg, P, c, fb);
+          else
+            pair_features_half<1>(a.fg, P, c, fb);
+#pragma unroll
+          for (int i = 0; i < kIn / 16; ++i) fv[i] = *reinterpret_cast<const uint4*>(fb + 8 * i);
+        }
+#pragma unroll
+        for (int i = 0; i < kIn / 16; ++i)
+          *reinterpret_cast<uint4*>(sH + tc::tile_off(r, cg * (kIn / 2) + 8 * i, kIn)) = fv[i];
+        tc::fence_smem_async();
+      } else if (cg == 0) {
         uint4 fv[kIn / 8];
 #pragma unroll
         for (int i = 0; i < kIn / 8; ++i) fv[i] = make_uint4(0, 0, 0, 0);
         if (valid) {
-          if (kFromPairs) {
-            __align__(16) __nv_bfloat16 fb[kIn];
-            const int sidx = a.ps[row];
-            if (a.sprep)
-              pair_features(a.fg, a.sprep[sidx - a.sprep_base], a.fg.dom[a.pd[row]], fb);
-            else
-              pair_features(a.fg, a.src[sidx], a.fg.dom[a.pd[row]], fb);
 #pragma unroll
-            for (int i = 0; i < kIn / 8; ++i) fv[i] = *reinterpret_cast<const uint4*>(fb + 8 * i);
-          } else {
+          for (int i = 0; i < kIn / 8; ++i)
+            fv[i] = *reinterpret_cast<const uint4*>(a.feat + row * kIn + 8 * i);
+          if (kTrain) {  // the features K-tiled, the first layer's weight-gradient operand
 #pragma unroll
-            for (int i = 0; i < kIn / 8; ++i)
-              fv[i] = *reinterpret_cast<const uint4*>(a.feat + row * kIn + 8 * i);
-            if (kTrain) {  // the features K-tiled, the first layer's weight-gradient operand
+            for (int i = 0; i < kIn / 8; ++i) {
+              const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&fv[i]);
 #pragma unroll
-              for (int i = 0; i < kIn / 8; ++i) {
-                const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&fv[i]);
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-                  *reinterpret_cast<__nv_bfloat16*>(
-                      a.x_t + kt_off((uint32_t)(8 * i + j), (uint32_t)row, kIn)) = e[j];
-              }
+              for (int j = 0; j < 8; ++j)
+                *reinterpret_cast<__nv_bfloat16*>(
+                    a.x_t + kt_off((uint32_t)(8 * i + j), (uint32_t)row, kIn)) = e[j];
             }
           }
         }
