@@ -536,6 +536,17 @@ int pp_debug_gemm(pp_ctx* ctx, const uint16_t* A, const uint16_t* B, int32_t M, 
 int pp_debug_first_hit(pp_ctx* ctx, const float* seg, int64_t n, int32_t mode, int32_t* dom,
                        float* t);
 
+/* The bounded wait every tensor-core kernel uses for its mbarriers, on one
+ * that no arrival completes: it gives up after limit_ns (1e3 .. 1e9) on the
+ * global timer and the kernel reports that, so a lost arrival becomes an error
+ * status on the host rather than a hung GPU (the kernels then raise their
+ * device error flag: PP_EDEVICE from pp_mlp_sync).  One block on `device`.
+ *   timed_out  out: 1 if the wait gave up (always, here), 0 if it completed
+ *   waited_ns  out: time spent in the wait
+ * Errors: PP_EINVAL, PP_ENODEV, PP_ENOMEM, PP_ECUDA. */
+int pp_debug_wait_timeout(int32_t device, uint64_t limit_ns, int32_t* timed_out,
+                          uint64_t* waited_ns);
+
 /* ---- measured issue rates ------------------------------------------------- */
 
 /* Measured lane-operation rate of one pipe of `device`, the denominator of the

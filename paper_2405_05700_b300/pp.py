@@ -102,6 +102,7 @@ _SIGS = {
     "pp_debug_scatter": [_vp, _vp, _vp, _vp, _i64],
     "pp_measure_issue_rate": [_i32, _i32, _vp, _vp],
     "pp_set_hit_acceptance": [_vp, _vp, _i32],
+    "pp_debug_wait_timeout": [_i32, _u64, _vp, _vp],
 }
 EXPORTS = tuple(_SIGS) + ("pp_last_error", "pp_strerror", "pp_server_last_error",
                           "pp_mlp_last_error")
@@ -321,6 +322,15 @@ def pp_set_hit_acceptance(ctx, coeffs):
     the DOM; an empty list restores weight 1."""
     c = np.ascontiguousarray(coeffs if coeffs is not None else [], np.float32)
     return _call("pp_set_hit_acceptance", ctx, _ptr(c) if c.size else None, int(c.size))
+
+
+def pp_debug_wait_timeout(device, limit_ns):
+    """(timed_out, waited_ns) of a bounded mbarrier wait that nothing completes."""
+    flag, ns = C.c_int32(), C.c_uint64()
+    rc = _lib.pp_debug_wait_timeout(device, limit_ns, C.byref(flag), C.byref(ns))
+    if rc:
+        raise PPError(rc, f"pp_debug_wait_timeout: {pp_strerror(rc)}")
+    return flag.value, ns.value
 
 
 PP_ISSUE_FP32_FMA, PP_ISSUE_SFU_LG2 = 0, 1

@@ -92,3 +92,11 @@ def test_surrogate_entry_points_refuse_null_handles(lib):
 def test_hit_acceptance_is_checked_on_the_host(lib):
     L = lib._lib
     assert L.pp_set_hit_acceptance(None, None, 0) == lib.PP_EINVAL
+
+
+def test_wait_probe_checks_its_arguments(lib):
+    flag, ns = ctypes.c_int32(), ctypes.c_uint64()
+    assert lib._lib.pp_debug_wait_timeout(0, 10, ctypes.byref(flag), ctypes.byref(ns)) == lib.PP_EINVAL
+    assert lib._lib.pp_debug_wait_timeout(0, 10 ** 10, ctypes.byref(flag),
+                                          ctypes.byref(ns)) == lib.PP_EINVAL
+    assert lib._lib.pp_debug_wait_timeout(0, 10 ** 6, None, None) == lib.PP_EINVAL

@@ -567,3 +567,15 @@ def test_measured_issue_rates_are_physical(pp):
     assert 0.3 * bound < fma <= 1.02 * bound, (fma, bound)
     assert 0.01 * bound < sfu <= 0.5 * fma, (sfu, fma)
     assert fma_ms > 1.0 and sfu_ms > 1.0
+
+
+def test_bounded_wait_gives_up_and_reports(pp, tiny):
+    """Failure detection without a fault: the kernels' bounded mbarrier wait on
+    a barrier that nothing completes gives up at its limit and the kernel
+    reports it; the device stays usable."""
+    for limit_ns in (2_000_000, 20_000_000):
+        timed_out, waited = pp.pp_debug_wait_timeout(0, limit_ns)
+        assert timed_out == 1
+        assert limit_ns <= waited < limit_ns + 200_000_000, (limit_ns, waited)
+    h, c = tiny.propagate(1, W.point_source(0, 0, 0, 10_000))
+    assert int(h.sum() + c[0] + c[1]) == 10_000
