@@ -15,6 +15,7 @@
 
 #include "pp.h"
 #include "pp_internal.h"
+#include "pp_nvtx.h"
 #include "mlp_internal.h"
 
 using namespace ppk;
@@ -281,6 +282,7 @@ int take_event(pp_ctx* ctx, cudaEvent_t* ev) {
 // Launches the propagation kernel, bracketed by timing events when enabled.
 int timed_propagate(pp_ctx* ctx, bool persistent, const WorkDev& w, const RunDev& run, int grid,
                     uint64_t n_photons, size_t smem, cudaStream_t st, int variant = -1) {
+  NvtxRange range("pp.propagate");
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int rc;
   if (ctx->timing) {
@@ -300,6 +302,7 @@ int timed_propagate(pp_ctx* ctx, bool persistent, const WorkDev& w, const RunDev
 
 int expand(pp_ctx* ctx, const pp_source* d_src, int64_t n_src, const int64_t* d_begin,
            const uint64_t* d_ids, int n_events, bool with_events, cudaStream_t st) {
+  NvtxRange range("pp.expand");
   PP_CUDA(launch_expand(d_src, n_src, d_begin, d_ids, n_events, expand_bufs(ctx, with_events), st));
   ctx->kernels_launched += (n_src <= kSmallMax) ? 1 : 4;
   return PP_OK;
@@ -317,6 +320,7 @@ struct RecordsOut {
 int batch_async(pp_ctx* ctx, int32_t n_events, const uint64_t* d_ids, const int64_t* d_begin,
                 const pp_source* d_src, int64_t n_src, uint64_t* d_hits, uint64_t* d_counts,
                 cudaStream_t st, const RecordsOut* rec = nullptr) {
+  NvtxRange range("pp.batch");
   int rc;
   if ((rc = check_loaded(ctx))) return rc;
   if (n_events < 0 || n_src < 0 || n_src > kMaxSources)
@@ -426,6 +430,7 @@ int range_async(pp_ctx* ctx, uint64_t event_id, const pp_source* d_src, int64_t 
 int plain_async(pp_ctx* ctx, int32_t n_events, const uint64_t* h_ids, const int64_t* h_begin,
                 const uint64_t* h_photons, const pp_source* d_src, uint64_t* d_hits,
                 uint64_t* d_counts, cudaStream_t st) {
+  NvtxRange range("pp.plain");
   int rc;
   if ((rc = check_loaded(ctx))) return rc;
   if (n_events < 0) return fail(ctx, PP_EINVAL, "n_events < 0");
@@ -495,6 +500,7 @@ void swap_scratch(pp_ctx* ctx) {
 
 int batch_host_pipelined(pp_ctx* ctx, int32_t n_events, const uint64_t* ids, const int64_t* begin,
                          const pp_source* src, uint64_t* hits, uint64_t* counts) {
+  NvtxRange range("pp.host_pipeline");
   int rc;
   const int64_t n_src = begin[n_events];
   const int n_dom = ctx->geom.n_dom;
@@ -612,6 +618,7 @@ int batch_host_pipelined(pp_ctx* ctx, int32_t n_events, const uint64_t* ids, con
 // Host batch: stage inputs, run the given path, copy results back.
 int batch_host(pp_ctx* ctx, bool plain, int32_t n_events, const uint64_t* ids,
                const int64_t* begin, const pp_source* src, uint64_t* hits, uint64_t* counts) {
+  NvtxRange range("pp.host_batch");
   int rc;
   if ((rc = check_loaded(ctx))) return rc;
   if (n_events < 0 || (n_events > 0 && (!ids || !begin || !hits || !counts)))

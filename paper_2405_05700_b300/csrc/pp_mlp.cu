@@ -16,6 +16,7 @@
 
 #include "mlp_features.cuh"
 #include "mlp_internal.h"
+#include "pp_nvtx.h"
 #include "pp.h"
 #include "pp_internal.h"
 
@@ -356,6 +357,7 @@ int pp_mlp_features(pp_mlp* m, const pp_source* d_src, const int32_t* d_pair_src
 
 int pp_mlp_forward(pp_mlp* m, const uint16_t* d_feat, const float* d_nph, int64_t n,
                    float* d_lambda, void* stream) {
+  ppk::NvtxRange range("pp.mlp.forward");
   if (!m || n < 0 || (n > 0 && (!d_feat || !d_nph || !d_lambda))) return PP_EINVAL;
   if (n > 0 && !aligned16(d_feat)) return mfail(m, PP_EINVAL, "features must be 16-byte aligned");
   PP_MLP_CUDA(cudaSetDevice(m->view.device));
@@ -418,6 +420,7 @@ namespace {
 
 int train_step(pp_mlp* m, const __nv_bfloat16* feat, const float* nph, const float* cnt,
                int64_t n, float lr, cudaStream_t st) {
+  ppk::NvtxRange range("pp.mlp.train_step");
   int rc;
   if ((rc = forward_backward(m, feat, nph, cnt, (int)n, st))) return rc;
   m->step += 1;
@@ -458,6 +461,7 @@ int pp_mlp_loss(pp_mlp* m, double* loss) {
 
 int pp_mlp_dom_sums(pp_mlp* m, const pp_source* d_src, int64_t n_src, const float* d_nph_src,
                     float r_max, double* d_dom_sums, float* d_lambda, void* stream) {
+  ppk::NvtxRange range("pp.mlp.dom_sums");
   if (!m || n_src < 0 || (n_src > 0 && (!d_src || !d_nph_src)) || (!d_dom_sums && !d_lambda) ||
       !(r_max > 0.0f))
     return PP_EINVAL;

@@ -33,6 +33,7 @@
 
 #include "pp.h"
 #include "pp_internal.h"
+#include "pp_nvtx.h"
 
 using Clock = std::chrono::steady_clock;
 
@@ -230,6 +231,7 @@ cudaError_t launch_slot(pp_server* s, int si) {
       w.single_event_lo = 0;
       w.g_begin = 0;
       w.g_end = ~0ull;
+      ppk::NvtxRange range("pp.server_batch");
       e = ppk::launch_propagate(true, s->view.ice, s->view.geom, w, s->view.run,
                                 s->view.block_threads, s->view.grid_blocks, 0, s->view.smem, st,
                                 s->view.variant);
