@@ -65,7 +65,7 @@ SFU_OPS = {"step": 9, "crossing": 0, "birth": 4}
 # launch of the 1000-event step (captured on its first 200 events, scaled by sources),
 # and one 4 194 304-row launch of the fused surrogate kernel.
 NCU_TRAFFIC_BYTES = 186e6
-SUR_NCU_TRAFFIC_BYTES = 301.1e6
+SUR_NCU_TRAFFIC_BYTES = 301.0e6
 
 
 def parse():
