@@ -168,3 +168,10 @@ def test_acceptance_weights_match_oracle(pp, tiny, orc):
     assert compared > 0.9 * n and bad <= 1e-3 * compared, (bad, compared)
     _, _, r1, _ = _run(pp, tiny, batch)
     assert np.all(r1["weight"] == 1.0)
+    # at most PP_MAX_ACCEPT_COEFFS finite coefficients
+    for bad in ([0.1] * (pp.PP_MAX_ACCEPT_COEFFS + 1), [0.5, float("nan")]):
+        with pytest.raises(pp.PPError) as e:
+            pp.pp_set_hit_acceptance(tiny.ctx, bad)
+        assert e.value.code == pp.PP_EINVAL
+    pp.pp_set_hit_acceptance(tiny.ctx, [1.0] * pp.PP_MAX_ACCEPT_COEFFS)
+    pp.pp_set_hit_acceptance(tiny.ctx, [])

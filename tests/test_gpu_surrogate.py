@@ -268,6 +268,12 @@ def test_near_pairs_match_brute_force(pp, prop, mlp):
     assert np.array_equal(ps.cpu().numpy()[:10], ps_h[:10])
     assert np.array_equal(pd.cpu().numpy()[:10], pd_h[:10])
     assert not ps.cpu().numpy()[10:].any()
+    # no sources, and a radius no pair is within: no pairs
+    assert pp.pp_mlp_near_pairs(mlp.handle, d_src, 0, r_max, 0, None, None) == 0
+    far = src.copy()
+    far["z"] = 5000.0
+    assert pp.pp_mlp_near_pairs(mlp.handle, _dev(far.view(np.uint8)), len(far), r_max, 0, None,
+                                None) == 0
 
 
 @pytest.mark.parametrize("act", ["silu", "hswish"])
