@@ -43,7 +43,7 @@ WORKLOAD = ("batched MC, full grid: 86x60 = 5160 DOMs, 171 ice layers (smooth + 
             "1000 power-law muon-bundle events, Cherenkov 41 deg from 1 m segments")
 
 # Algorithmic ALU work per unit (FP32 + INT32 lane operations of the method as
-# stated in the oracle, an FMA counted once; derivation in the design notes):
+# the oracle states it, an FMA counted once; each count below lists its parts):
 OPS_PER_STEP = 210        # Philox block (98), 3 uniforms (12), -ln u (2), first layer
                           # visit (14), world exit (17), cell test (19), resolve (4),
                           # move (3), HG (6), sin theta (5), sincos (3), rotation (28)

@@ -185,13 +185,17 @@ int pp_propagate_plain_async(pp_ctx* ctx, int32_t n_events, const uint64_t* h_ev
  *   d_src[n_src]  device sources of the event, 0 <= n_src <= PP_NOALLOC_MAX_SOURCES
  *                 (more: PP_EINVAL with a message, nothing enqueued)
  *   d_hits[n_dom], d_counts[4]  device outputs, overwritten (as pp_propagate)
- *   stream        CUDA stream (NULL: the context's stream); returns once enqueued,
- *                 device errors are reported by pp_sync
- * The first call on a device looks up the array's device address (set-up, once
- * per device), so make that first call before any stream capture.  Every call
- * shares the one array and the work counter in it is cleared by each call:
- * calls whose GPU work overlaps in time (different streams, or several
- * contexts on one device) race and must be serialised by the caller. */
+ *   stream        CUDA stream (NULL: the context's stream); returns once enqueued.
+ *                 Device errors (a malformed source) are latched in the context
+ *                 and returned by pp_sync(ctx, stream) with this same stream,
+ *                 which orders the check after this call's kernels.
+ * The array's device address is looked up when a context is created on the
+ * device (pp_create, with the device current; a context created after a device
+ * reset looks it up afresh), so calls need no set-up of their own.  Every
+ * call shares the one array and the work
+ * counter in it is cleared by each call: calls whose GPU work overlaps in time
+ * (different streams, or several contexts on one device) race and must be
+ * serialised by the caller.  A call launches two kernels (counted by pp_get_kernel_time). */
 #define PP_NOALLOC_MAX_SOURCES 8192
 int pp_propagate_noalloc(pp_ctx* ctx, uint64_t event_id, const pp_source* d_src, int64_t n_src,
                          uint64_t* d_hits, uint64_t* d_counts, void* stream);
@@ -300,6 +304,11 @@ int pp_set_graphs(pp_ctx* ctx, int32_t enable);
  * since the previous pp_get_kernel_time; then it resets them. */
 int pp_set_kernel_timing(pp_ctx* ctx, int32_t enable);
 int pp_get_kernel_time(pp_ctx* ctx, double* total_ms, uint64_t* n_timed, uint64_t* n_kernels);
+
+/* Device memory held by the context's own buffers (tables, scratch, staging;
+ * not the surrogate's or a server's), in bytes, and the number of device
+ * allocations the context has made since pp_create.  Either pointer may be NULL. */
+int pp_get_memory(pp_ctx* ctx, uint64_t* device_bytes, uint64_t* n_allocations);
 
 /* Totals counted by the persistent kernel since the previous call (waits for
  * the device, then resets them): out4 = {steps, layer crossings, photons born,
@@ -413,6 +422,20 @@ const char* pp_mlp_last_error(const pp_mlp* mlp);
  * Errors: PP_EINVAL (null pointer, wrong n), PP_ECUDA, PP_EDEVICE. */
 int pp_mlp_set_params(pp_mlp* mlp, const float* params, int64_t n);
 int pp_mlp_get_params(pp_mlp* mlp, float* params, int64_t n);
+
+/* The whole training state, for checkpoint and resume: the FP32 parameters,
+ * Adam's first and second moment estimates m and v (Kingma & Ba, "Adam: A
+ * Method for Stochastic Optimization", 2015, Algorithm 1), each a host array
+ * of n = PP_MLP_N_PARAMS values in the parameter layout above, and the number
+ * of Adam steps taken (the next step's bias corrections use step + 1).  get
+ * copies out, set copies in (and refreshes the BF16 weight copies).  The moments
+ * may be NULL in set (then they start at zero) and in get (not copied); step
+ * may be NULL in get.  Both synchronise.
+ * Errors: PP_EINVAL (null params, wrong n, step < 0, non-finite values or
+ * negative v), PP_ECUDA, PP_EDEVICE. */
+int pp_mlp_get_state(pp_mlp* mlp, float* params, float* m, float* v, int64_t n, int64_t* step);
+int pp_mlp_set_state(pp_mlp* mlp, const float* params, const float* m, const float* v, int64_t n,
+                     int64_t step);
 
 /* Features of n pairs into d_feat[n][32] (BF16 bit patterns, row-major):
  *   d_src              sources as in pp_propagate (the point is the segment's midpoint)

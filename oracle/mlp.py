@@ -18,6 +18,7 @@ at the same points (weights W1..W4, inputs, hidden activations, the stored
 pre-activations used by the backward pass, and the back-propagated dL/dz of
 each layer); everything else is float64.  With rounding=False it is the plain
 float64 network, which the finite-difference pin checks.
+The optimizer is Adam (adam_step).
 """
 from __future__ import annotations
 
@@ -201,6 +202,23 @@ def forward(params, x, nph, rounding=True, act="silu"):
     cache["zf"] = zf
     cache["lam"] = lam
     return lam, cache
+
+
+def adam_step(p, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba, "Adam: A Method for Stochastic
+    Optimization", ICLR 2015, Algorithm 1), float64, elementwise.
+
+    t is the number of the step being taken (1 for the first).  The moments
+    are exponential moving averages of the gradient and of its square; the
+    bias-corrected averages m_hat = m / (1 - b1^t), v_hat = v / (1 - b2^t)
+    set the step -lr * m_hat / (sqrt(v_hat) + eps).  Returns (p, m, v) after
+    the step; the inputs are not modified."""
+    p, g, m, v = (np.asarray(a, np.float64) for a in (p, g, m, v))
+    m_new = b1 * m + (1.0 - b1) * g
+    v_new = b2 * v + (1.0 - b2) * g * g
+    m_hat = m_new / (1.0 - b1 ** t)
+    v_hat = v_new / (1.0 - b2 ** t)
+    return p - lr * m_hat / (np.sqrt(v_hat) + eps), m_new, v_new
 
 
 def loss_and_grads(params, x, nph, counts, rounding=True, act="silu"):

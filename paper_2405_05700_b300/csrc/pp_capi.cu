@@ -75,6 +75,8 @@ struct pp_ctx {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
   std::vector<cudaEvent_t> event_pool;
   uint64_t kernels_launched = 0;
+  // device memory the context holds (its DevBufs) and its cudaMalloc calls
+  uint64_t device_bytes = 0, n_allocations = 0;
 };
 
 namespace {
@@ -105,10 +107,12 @@ int ensure(pp_ctx* ctx, DevBuf& b, size_t bytes) {
   if (e == cudaSuccess && ctx->stream2) e = cudaStreamSynchronize(ctx->stream2);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
   if (b.p) cudaFree(b.p);
+  ctx->device_bytes -= b.cap;
   b.p = nullptr;
   b.cap = 0;
   size_t nb = std::max<size_t>(bytes, 256);
   nb = (nb + 255) & ~(size_t)255;
+  ctx->n_allocations += 1;
   e = cudaMalloc(&b.p, nb);
   if (e != cudaSuccess) {
     b.p = nullptr;
@@ -117,6 +121,7 @@ int ensure(pp_ctx* ctx, DevBuf& b, size_t bytes) {
                                      " bytes failed: " + cudaGetErrorString(e));
   }
   b.cap = nb;
+  ctx->device_bytes += nb;
   return PP_OK;
 }
 
@@ -675,11 +680,14 @@ int LaunchView::cuda_fail(cudaError_t e, const char* where) const {
 
 void attach_server(pp_ctx* ctx, int delta) { ctx->servers += delta; }
 
+void count_launches(pp_ctx* ctx, int n) { ctx->kernels_launched += (uint64_t)n; }
+
 int with_launch_view(pp_ctx* ctx, const std::function<int(const LaunchView&)>& fn) {
   std::lock_guard<std::mutex> lk(ctx->mu);
   int rc;
   if ((rc = check_loaded(ctx))) return rc;
-  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  DeviceScope dev_scope(ctx->cfg.device);
+  PP_CUDA(dev_scope.status());
   LaunchView v;
   v.ctx = ctx;
   v.device = ctx->cfg.device;
@@ -747,7 +755,8 @@ int pp_create(const pp_config* cfg, pp_ctx** out) {
   if (cfg->device < 0 || cfg->device >= ndev) return PP_ENODEV;
   pp_ctx* ctx = new pp_ctx();
   ctx->cfg = *cfg;
-  cudaError_t e = cudaSetDevice(cfg->device);
+  ppk::DeviceScope dev_scope(cfg->device);
+  cudaError_t e = dev_scope.status();
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, cfg->device);
   if (e == cudaSuccess) {
     if (cfg->stream) {
@@ -757,6 +766,7 @@ int pp_create(const pp_config* cfg, pp_ctx** out) {
       ctx->own_stream = (e == cudaSuccess);
     }
   }
+  if (e == cudaSuccess) e = ppk::noalloc_setup(cfg->device);
   if (e == cudaSuccess && ensure(ctx, ctx->err, sizeof(int)) == PP_OK &&
       ensure(ctx, ctx->stats, 4 * sizeof(uint64_t)) == PP_OK) {
     e = cudaMemset(ctx->err.p, 0, sizeof(int));
@@ -773,7 +783,7 @@ int pp_create(const pp_config* cfg, pp_ctx** out) {
 
 int pp_destroy(pp_ctx* ctx) {
   if (!ctx) return PP_OK;
-  cudaSetDevice(ctx->cfg.device);
+  ppk::DeviceScope dev_scope(ctx->cfg.device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   DevBuf* bufs[] = {&ctx->dom, &ctx->str, &ctx->str_range, &ctx->sdom_z, &ctx->sdom_idx,
                     &ctx->clear, &ctx->cell_off, &ctx->cell_list, &ctx->layers, &ctx->off,
@@ -806,7 +816,8 @@ int pp_load_geometry(pp_ctx* ctx, const float* xyz, const int32_t* string_id, in
     return fail(ctx, PP_EINVAL, "need 0 <= n_dom <= 65535, xyz, dom_radius > 0");
   for (int64_t i = 0; i < 3 * (int64_t)n_dom; ++i)
     if (!std::isfinite(xyz[i])) return fail(ctx, PP_EINVAL, "non-finite DOM coordinate");
-  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  DeviceScope dev_scope(ctx->cfg.device);
+  PP_CUDA(dev_scope.status());
   const double r = dom_radius;
   const double M = ctx->cfg.world_margin_m;
   const double eps = 2e-3;  // slack for FP32 rounding in the culling tests
@@ -944,7 +955,8 @@ int pp_load_ice(pp_ctx* ctx, const float* b_e, const float* a, int32_t n_layers,
   for (int i = 0; i < n_layers; ++i)
     if (!(b_e[i] >= 0.f) || !(a[i] >= 0.f) || !std::isfinite(b_e[i]) || !std::isfinite(a[i]))
       return fail(ctx, PP_EINVAL, "coefficients must be finite and >= 0");
-  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  DeviceScope dev_scope(ctx->cfg.device);
+  PP_CUDA(dev_scope.status());
   const double gd = g;
   std::vector<float4> lay(n_layers);
   const float inf = INFINITY;
@@ -976,7 +988,8 @@ int pp_propagate(pp_ctx* ctx, uint64_t event_id, const pp_source* src, int64_t n
   if (!ctx) return PP_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (n_src < 0) return fail(ctx, PP_EINVAL, "n_src < 0");
-  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  DeviceScope dev_scope(ctx->cfg.device);
+  PP_CUDA(dev_scope.status());
   const int64_t begin[2] = {0, n_src};
   return batch_host(ctx, true, 1, &event_id, begin, src, hits, counts);
 }
@@ -986,7 +999,8 @@ int pp_propagate_batch(pp_ctx* ctx, int32_t n_events, const uint64_t* event_ids,
                        uint64_t* counts) {
   if (!ctx) return PP_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
-  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  DeviceScope dev_scope(ctx->cfg.device);
+  PP_CUDA(dev_scope.status());
   return batch_host(ctx, false, n_events, event_ids, src_begin, src, hits, counts);
 }
 
@@ -995,7 +1009,8 @@ int pp_propagate_batch_async(pp_ctx* ctx, int32_t n_events, const uint64_t* d_ev
                              uint64_t* d_hits, uint64_t* d_counts, void* stream) {
   if (!ctx) return PP_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
-  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  DeviceScope dev_scope(ctx->cfg.device);
+  PP_CUDA(dev_scope.status());
   return batch_async(ctx, n_events, d_event_ids, d_src_begin, d_src, n_src, d_hits, d_counts,
                      pick_stream(ctx, stream));
 }
@@ -1007,7 +1022,8 @@ int pp_propagate_records_async(pp_ctx* ctx, int32_t n_events, const uint64_t* d_
                                void* stream) {
   if (!ctx) return PP_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
-  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  DeviceScope dev_scope(ctx->cfg.device);
+  PP_CUDA(dev_scope.status());
   const RecordsOut rec{d_records, max_records, d_n_records,
                        group_index > 0.0f ? group_index : (float)kGroupIndexDefault};
   return batch_async(ctx, n_events, d_event_ids, d_src_begin, d_src, n_src, d_hits, d_counts,
@@ -1020,7 +1036,8 @@ int pp_propagate_plain_async(pp_ctx* ctx, int32_t n_events, const uint64_t* h_ev
                              void* stream) {
   if (!ctx) return PP_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
-  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  DeviceScope dev_scope(ctx->cfg.device);
+  PP_CUDA(dev_scope.status());
   return plain_async(ctx, n_events, h_event_ids, h_src_begin, h_event_photons, d_src, d_hits,
                      d_counts, pick_stream(ctx, stream));
 }
@@ -1031,7 +1048,8 @@ int pp_propagate_range_async(pp_ctx* ctx, uint64_t event_id, const pp_source* d_
                              void* stream) {
   if (!ctx) return PP_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
-  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  DeviceScope dev_scope(ctx->cfg.device);
+  PP_CUDA(dev_scope.status());
   return range_async(ctx, event_id, d_src, n_src, photon_begin, photon_end, accumulate != 0,
                      d_hits, d_counts, pick_stream(ctx, stream));
 }
@@ -1039,7 +1057,8 @@ int pp_propagate_range_async(pp_ctx* ctx, uint64_t event_id, const pp_source* d_
 int pp_sync(pp_ctx* ctx, void* stream) {
   if (!ctx) return PP_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
-  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  DeviceScope dev_scope(ctx->cfg.device);
+  PP_CUDA(dev_scope.status());
   return sync_and_check(ctx, pick_stream(ctx, stream));
 }
 
@@ -1069,7 +1088,8 @@ int pp_get_launch(const pp_ctx* ctx_c, int32_t* block_threads, int32_t* blocks_p
   if (grid) {
     *grid = 0;
     if (ctx->geom_loaded && ctx->ice_loaded) {
-      PP_CUDA(cudaSetDevice(ctx->cfg.device));
+      DeviceScope dev_scope(ctx->cfg.device);
+  PP_CUDA(dev_scope.status());
       size_t smem;
       int rc = prepare_smem(ctx, &smem);
       if (!rc) rc = grid_blocks(ctx, smem, grid);
@@ -1085,7 +1105,8 @@ int pp_autotune_batch(pp_ctx* ctx, int32_t n_events, const uint64_t* d_event_ids
                       int32_t* best3, float* best_ms) {
   if (!ctx) return PP_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
-  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  DeviceScope dev_scope(ctx->cfg.device);
+  PP_CUDA(dev_scope.status());
   if (repeats < 1) repeats = 1;
   cudaStream_t st = pick_stream(ctx, stream);
   struct Cand {
@@ -1148,7 +1169,8 @@ int pp_autotune_batch(pp_ctx* ctx, int32_t n_events, const uint64_t* d_event_ids
 int pp_set_graphs(pp_ctx* ctx, int32_t enable) {
   if (!ctx) return PP_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
-  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  DeviceScope dev_scope(ctx->cfg.device);
+  PP_CUDA(dev_scope.status());
   ctx->graphs = enable != 0;
   if (!ctx->graphs) drop_graphs(ctx);
   return PP_OK;
@@ -1167,6 +1189,14 @@ int pp_set_hit_acceptance(pp_ctx* ctx, const float* coeffs, int32_t n) {
   return PP_OK;
 }
 
+int pp_get_memory(pp_ctx* ctx, uint64_t* device_bytes, uint64_t* n_allocations) {
+  if (!ctx) return PP_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (device_bytes) *device_bytes = ctx->device_bytes;
+  if (n_allocations) *n_allocations = ctx->n_allocations;
+  return PP_OK;
+}
+
 int pp_set_kernel_timing(pp_ctx* ctx, int32_t enable) {
   if (!ctx) return PP_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
@@ -1177,7 +1207,8 @@ int pp_set_kernel_timing(pp_ctx* ctx, int32_t enable) {
 int pp_get_kernel_time(pp_ctx* ctx, double* total_ms, uint64_t* n_timed, uint64_t* n_kernels) {
   if (!ctx) return PP_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
-  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  DeviceScope dev_scope(ctx->cfg.device);
+  PP_CUDA(dev_scope.status());
   double sum = 0.0;
   const uint64_t n = ctx->pending.size();
   for (auto& pr : ctx->pending) {
@@ -1199,7 +1230,8 @@ int pp_get_kernel_time(pp_ctx* ctx, double* total_ms, uint64_t* n_timed, uint64_
 int pp_get_path_stats(pp_ctx* ctx, uint64_t* out4) {
   if (!ctx || !out4) return PP_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
-  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  DeviceScope dev_scope(ctx->cfg.device);
+  PP_CUDA(dev_scope.status());
   PP_CUDA(cudaStreamSynchronize(ctx->stream));
   PP_CUDA(cudaDeviceSynchronize());
   PP_CUDA(cudaMemcpy(out4, ctx->stats.p, 4 * sizeof(uint64_t), cudaMemcpyDeviceToHost));
@@ -1222,7 +1254,8 @@ int pp_debug_philox(pp_ctx* ctx, const uint32_t* ctr, const uint32_t* key, uint3
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (n < 0 || (n > 0 && (!ctr || !key || !out))) return fail(ctx, PP_EINVAL, "bad arguments");
   if (n == 0) return PP_OK;
-  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  DeviceScope dev_scope(ctx->cfg.device);
+  PP_CUDA(dev_scope.status());
   int rc;
   if ((rc = ensure(ctx, ctx->s_misc1, 16 * (size_t)n))) return rc;
   if ((rc = ensure(ctx, ctx->s_misc2, 8 * (size_t)n))) return rc;
@@ -1249,7 +1282,8 @@ int pp_debug_trace(pp_ctx* ctx, uint64_t event_id, const pp_source* src, int64_t
     return fail(ctx, PP_EINVAL, "bad arguments");
   if ((rc = check_sources(ctx, src, n_src))) return rc;
   if (n == 0) return PP_OK;
-  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  DeviceScope dev_scope(ctx->cfg.device);
+  PP_CUDA(dev_scope.status());
   cudaStream_t st = ctx->stream;
   if ((rc = ensure(ctx, ctx->s_src, sizeof(pp_source) * n_src))) return rc;
   if ((rc = ensure(ctx, ctx->s_misc1, 8 * (size_t)n))) return rc;
@@ -1286,7 +1320,8 @@ int pp_debug_scatter(pp_ctx* ctx, const float* dir, const uint32_t* words, float
   if (!ctx->ice_loaded) return fail(ctx, PP_ENOTLOADED, "load ice first");
   if (n < 0 || (n > 0 && (!dir || !words || !out))) return fail(ctx, PP_EINVAL, "bad arguments");
   if (n == 0) return PP_OK;
-  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  DeviceScope dev_scope(ctx->cfg.device);
+  PP_CUDA(dev_scope.status());
   cudaStream_t st = ctx->stream;
   int rc;
   if ((rc = ensure(ctx, ctx->s_misc1, 12 * (size_t)n))) return rc;
@@ -1308,7 +1343,8 @@ int pp_debug_gemm(pp_ctx* ctx, const uint16_t* A, const uint16_t* B, int32_t M, 
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (!A || !B || !C || M < 1 || N < 16 || N > 256 || N % 16 || K < 16 || K % 16)
     return fail(ctx, PP_EINVAL, "need M >= 1, 16 <= N <= 256 (multiple of 16), K multiple of 16");
-  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  DeviceScope dev_scope(ctx->cfg.device);
+  PP_CUDA(dev_scope.status());
   cudaStream_t st = ctx->stream;
   int rc;
   const size_t a = 2 * (size_t)M * K, b = 2 * (size_t)N * K, c = 4 * (size_t)M * N;
@@ -1343,7 +1379,8 @@ int pp_debug_first_hit(pp_ctx* ctx, const float* seg, int64_t n, int32_t mode, i
   if (n < 0 || (n > 0 && (!seg || !dom || !t)) || (mode != 0 && mode != 1))
     return fail(ctx, PP_EINVAL, "bad arguments");
   if (n == 0) return PP_OK;
-  PP_CUDA(cudaSetDevice(ctx->cfg.device));
+  DeviceScope dev_scope(ctx->cfg.device);
+  PP_CUDA(dev_scope.status());
   cudaStream_t st = ctx->stream;
   if ((rc = ensure(ctx, ctx->s_misc1, 28 * (size_t)n))) return rc;
   if ((rc = ensure(ctx, ctx->s_misc2, 4 * (size_t)n))) return rc;

@@ -11,6 +11,32 @@
 
 namespace ppk {
 
+// Makes `device` current for the enclosing scope and gives the calling
+// thread back its own current device on exit: an entry point never leaves a
+// host thread that drives another GPU switched to this library's device.
+class DeviceScope {
+ public:
+  explicit DeviceScope(int device) {
+    if (cudaGetDevice(&prev_) != cudaSuccess) {
+      (void)cudaGetLastError();
+      prev_ = -1;
+    }
+    status_ = (prev_ == device) ? cudaSuccess : cudaSetDevice(device);
+    restore_ = status_ == cudaSuccess && prev_ >= 0 && prev_ != device;
+  }
+  ~DeviceScope() {
+    if (restore_) cudaSetDevice(prev_);
+  }
+  DeviceScope(const DeviceScope&) = delete;
+  DeviceScope& operator=(const DeviceScope&) = delete;
+  cudaError_t status() const { return status_; }
+
+ private:
+  int prev_ = -1;
+  bool restore_ = false;
+  cudaError_t status_ = cudaSuccess;
+};
+
 constexpr int kMaxLayers = 4096;
 constexpr int kMaxStrings = 4096;
 constexpr int kMaxCells = 32768;         // u8 clearance grid staged in shared memory
@@ -191,5 +217,15 @@ int with_launch_view(pp_ctx* ctx, const std::function<int(const LaunchView&)>& f
 // Servers that hold a LaunchView of the context (its table pointers): while
 // any is attached the context refuses to load new geometry or ice.
 void attach_server(pp_ctx* ctx, int delta);
+
+// Adds n to the context's count of launched kernels (pp_stats); the caller
+// holds the context's lock (inside with_launch_view).
+void count_launches(pp_ctx* ctx, int n);
+
+// pp_noalloc.cu: looks up the device address of the no-allocation entry
+// point's static scratch array on `device` (which must be current) and keeps
+// it for that device, replacing an earlier one.  Called by pp_create, so a
+// context created after a device reset never sees a stale address.
+cudaError_t noalloc_setup(int device);
 
 }  // namespace ppk

@@ -250,7 +250,8 @@ int pp_mlp_create(pp_ctx* ctx, int32_t max_batch, int64_t max_rows, pp_mlp** out
   m->fg.dz = m->view.ice.dz;
   m->fg.be_over_b = m->view.scatter_effective ? 1.0f - g : 1.0f;
   m->fg.theta_c = std::acos(m->view.run.cos_cherenkov);
-  cudaError_t e = cudaSetDevice(m->view.device);
+  ppk::DeviceScope dev_scope(m->view.device);
+  cudaError_t e = dev_scope.status();
   const size_t B = (size_t)max_batch, H = (size_t)kHid;
 #define PP_A(x) \
   if (e == cudaSuccess) e = (x)
@@ -303,7 +304,7 @@ int pp_mlp_create(pp_ctx* ctx, int32_t max_batch, int64_t max_rows, pp_mlp** out
 
 int pp_mlp_destroy(pp_mlp* m) {
   if (!m) return PP_OK;
-  cudaSetDevice(m->view.device);
+  ppk::DeviceScope dev_scope(m->view.device);
   cudaDeviceSynchronize();
   void* bufs[] = {m->p,   m->g,     m->m,         m->v,  m->t1, m->t2,    m->loss, m->err,
                   m->wpack, m->wpack_bwd, m->ps, m->pd, m->count, m->ice_cum, m->dw_part,
@@ -326,7 +327,8 @@ const char* pp_mlp_last_error(const pp_mlp* m) { return m ? m->last_error.c_str(
 int pp_mlp_set_params(pp_mlp* m, const float* params, int64_t n) {
   if (!m || !params || n != kNParams) return PP_EINVAL;
   cudaStream_t st = m->view.stream;
-  PP_MLP_CUDA(cudaSetDevice(m->view.device));
+  ppk::DeviceScope dev_scope(m->view.device);
+  PP_MLP_CUDA(dev_scope.status());
   PP_MLP_CUDA(cudaMemcpyAsync(m->p, params, sizeof(float) * kNParams, cudaMemcpyHostToDevice, st));
   PP_MLP_CUDA(cudaMemsetAsync(m->m, 0, sizeof(float) * kNParams, st));
   PP_MLP_CUDA(cudaMemsetAsync(m->v, 0, sizeof(float) * kNParams, st));
@@ -339,16 +341,57 @@ int pp_mlp_set_params(pp_mlp* m, const float* params, int64_t n) {
 
 int pp_mlp_get_params(pp_mlp* m, float* params, int64_t n) {
   if (!m || !params || n != kNParams) return PP_EINVAL;
-  PP_MLP_CUDA(cudaSetDevice(m->view.device));
+  ppk::DeviceScope dev_scope(m->view.device);
+  PP_MLP_CUDA(dev_scope.status());
   PP_MLP_CUDA(cudaStreamSynchronize(m->view.stream));
   PP_MLP_CUDA(cudaMemcpy(params, m->p, sizeof(float) * kNParams, cudaMemcpyDeviceToHost));
   return PP_OK;
 }
 
+int pp_mlp_get_state(pp_mlp* m, float* params, float* m1, float* v1, int64_t n, int64_t* step) {
+  if (!m || !params || n != kNParams) return PP_EINVAL;
+  ppk::DeviceScope dev_scope(m->view.device);
+  PP_MLP_CUDA(dev_scope.status());
+  PP_MLP_CUDA(cudaStreamSynchronize(m->view.stream));
+  PP_MLP_CUDA(cudaMemcpy(params, m->p, sizeof(float) * kNParams, cudaMemcpyDeviceToHost));
+  if (m1) PP_MLP_CUDA(cudaMemcpy(m1, m->m, sizeof(float) * kNParams, cudaMemcpyDeviceToHost));
+  if (v1) PP_MLP_CUDA(cudaMemcpy(v1, m->v, sizeof(float) * kNParams, cudaMemcpyDeviceToHost));
+  if (step) *step = m->step;
+  return PP_OK;
+}
+
+int pp_mlp_set_state(pp_mlp* m, const float* params, const float* m1, const float* v1, int64_t n,
+                     int64_t step) {
+  if (!m || !params || n != kNParams || step < 0) return PP_EINVAL;
+  for (int64_t i = 0; i < kNParams; ++i) {
+    if (!std::isfinite(params[i]) || (m1 && !std::isfinite(m1[i])) ||
+        (v1 && !(std::isfinite(v1[i]) && v1[i] >= 0.0f)))
+      return mfail(m, PP_EINVAL, "non-finite parameter or moment, or negative second moment");
+  }
+  cudaStream_t st = m->view.stream;
+  ppk::DeviceScope dev_scope(m->view.device);
+  PP_MLP_CUDA(dev_scope.status());
+  PP_MLP_CUDA(cudaMemcpyAsync(m->p, params, sizeof(float) * kNParams, cudaMemcpyHostToDevice, st));
+  if (m1)
+    PP_MLP_CUDA(cudaMemcpyAsync(m->m, m1, sizeof(float) * kNParams, cudaMemcpyHostToDevice, st));
+  else
+    PP_MLP_CUDA(cudaMemsetAsync(m->m, 0, sizeof(float) * kNParams, st));
+  if (v1)
+    PP_MLP_CUDA(cudaMemcpyAsync(m->v, v1, sizeof(float) * kNParams, cudaMemcpyHostToDevice, st));
+  else
+    PP_MLP_CUDA(cudaMemsetAsync(m->v, 0, sizeof(float) * kNParams, st));
+  m->step = step;
+  m->weights_version += 1;
+  int rc = refresh_bf16(m, st);
+  if (rc) return rc;
+  return mlp_sync(m, st);
+}
+
 int pp_mlp_features(pp_mlp* m, const pp_source* d_src, const int32_t* d_pair_src,
                     const int32_t* d_pair_dom, int64_t n, uint16_t* d_feat, void* stream) {
   if (!m || n < 0 || (n > 0 && (!d_src || !d_pair_src || !d_pair_dom || !d_feat))) return PP_EINVAL;
-  PP_MLP_CUDA(cudaSetDevice(m->view.device));
+  ppk::DeviceScope dev_scope(m->view.device);
+  PP_MLP_CUDA(dev_scope.status());
   cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : m->view.stream;
   PP_MLP_CUDA(launch_features(m->fg, d_src, d_pair_src, d_pair_dom, n,
                               reinterpret_cast<__nv_bfloat16*>(d_feat), st));
@@ -360,7 +403,8 @@ int pp_mlp_forward(pp_mlp* m, const uint16_t* d_feat, const float* d_nph, int64_
   ppk::NvtxRange range("pp.mlp.forward");
   if (!m || n < 0 || (n > 0 && (!d_feat || !d_nph || !d_lambda))) return PP_EINVAL;
   if (n > 0 && !aligned16(d_feat)) return mfail(m, PP_EINVAL, "features must be 16-byte aligned");
-  PP_MLP_CUDA(cudaSetDevice(m->view.device));
+  ppk::DeviceScope dev_scope(m->view.device);
+  PP_MLP_CUDA(dev_scope.status());
   cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : m->view.stream;
   int rc;
   if ((rc = ensure_packed(m, st))) return rc;
@@ -378,7 +422,8 @@ int pp_mlp_gradients(pp_mlp* m, const uint16_t* d_feat, const float* d_nph, cons
   if (!m || !d_feat || !d_nph || !d_count || !h_grads) return PP_EINVAL;
   int rc;
   if ((rc = check_batch(m, n, d_feat))) return rc;
-  PP_MLP_CUDA(cudaSetDevice(m->view.device));
+  ppk::DeviceScope dev_scope(m->view.device);
+  PP_MLP_CUDA(dev_scope.status());
   cudaStream_t st = m->view.stream;
   PP_MLP_CUDA(cudaMemsetAsync(m->loss, 0, sizeof(double), st));
   if ((rc = forward_backward(m, reinterpret_cast<const __nv_bfloat16*>(d_feat), d_nph, d_count,
@@ -395,7 +440,8 @@ int pp_mlp_train_step(pp_mlp* m, const uint16_t* d_feat, const float* d_nph, con
   if (!m || !d_feat || !d_nph || !d_count || !(lr > 0.0f)) return PP_EINVAL;
   int rc;
   if ((rc = check_batch(m, n, d_feat))) return rc;
-  PP_MLP_CUDA(cudaSetDevice(m->view.device));
+  ppk::DeviceScope dev_scope(m->view.device);
+  PP_MLP_CUDA(dev_scope.status());
   cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : m->view.stream;
   return train_step(m, reinterpret_cast<const __nv_bfloat16*>(d_feat), d_nph, d_count, n, lr, st);
 }
@@ -407,7 +453,8 @@ int pp_mlp_train_step_rows(pp_mlp* m, const uint16_t* d_feat, const float* d_nph
     return PP_EINVAL;
   int rc;
   if ((rc = check_batch(m, n, d_feat))) return rc;
-  PP_MLP_CUDA(cudaSetDevice(m->view.device));
+  ppk::DeviceScope dev_scope(m->view.device);
+  PP_MLP_CUDA(dev_scope.status());
   cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : m->view.stream;
   PP_MLP_CUDA(launch_gather_rows(reinterpret_cast<const __nv_bfloat16*>(d_feat), d_nph, d_count,
                                  n_rows, d_rows, n, m->bfeat, m->bnph, m->bcnt, m->err, st));
@@ -465,7 +512,8 @@ int pp_mlp_dom_sums(pp_mlp* m, const pp_source* d_src, int64_t n_src, const floa
   if (!m || n_src < 0 || (n_src > 0 && (!d_src || !d_nph_src)) || (!d_dom_sums && !d_lambda) ||
       !(r_max > 0.0f))
     return PP_EINVAL;
-  PP_MLP_CUDA(cudaSetDevice(m->view.device));
+  ppk::DeviceScope dev_scope(m->view.device);
+  PP_MLP_CUDA(dev_scope.status());
   cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : m->view.stream;
   const int n_dom = m->fg.n_dom;
   if (d_dom_sums) PP_MLP_CUDA(cudaMemsetAsync(d_dom_sums, 0, sizeof(double) * n_dom, st));
@@ -518,7 +566,8 @@ int pp_mlp_near_pairs(pp_mlp* m, const pp_source* d_src, int64_t n_src, float r_
   if (!m || n_src < 0 || (n_src > 0 && !d_src) || !h_count || max_out < 0 || !(r_max > 0.0f) ||
       (max_out > 0 && (!d_pair_src || !d_pair_dom)))
     return PP_EINVAL;
-  PP_MLP_CUDA(cudaSetDevice(m->view.device));
+  ppk::DeviceScope dev_scope(m->view.device);
+  PP_MLP_CUDA(dev_scope.status());
   cudaStream_t st = m->view.stream;
   const int64_t nb = near_pairs_ordered_blocks(n_src * (int64_t)m->fg.n_dom);
   if (nb > m->near_cap) {

@@ -7,7 +7,8 @@
 // that loads this library holds the array until the process exits.  In host
 // code the array's name is only a stand-in for the symbol, not a device
 // address: the address the kernels get comes from cudaGetSymbolAddress, taken
-// once per device with that device current (on the first call there).
+// with the device current when a context is created on it (pp_create calls
+// noalloc_setup), and again by the first call on a device that has none.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -36,21 +37,38 @@ constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 void* g_scratch_addr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device (set-up once).
+cudaError_t lookup(int device) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return e;
+  g_scratch_addr[device] = p;
+  return cudaSuccess;
+}
+
+// Device address of the scratch array on `device` (current): the one the
+// last set-up found there, else looked up now.
 cudaError_t scratch_address(int device, unsigned char** out) {
   if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lk(g_setup_mu);
   if (!g_scratch_addr[device]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    const cudaError_t e = lookup(device);
     if (e != cudaSuccess) return e;
-    g_scratch_addr[device] = p;
   }
   *out = static_cast<unsigned char*>(g_scratch_addr[device]);
   return cudaSuccess;
 }
 
 }  // namespace
+
+namespace ppk {
+
+cudaError_t noalloc_setup(int device) {
+  if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_setup_mu);
+  return lookup(device);
+}
+
+}  // namespace ppk
 
 extern "C" int pp_propagate_noalloc(pp_ctx* ctx, uint64_t event_id, const pp_source* d_src,
                                     int64_t n_src, uint64_t* d_hits, uint64_t* d_counts,
@@ -63,9 +81,8 @@ extern "C" int pp_propagate_noalloc(pp_ctx* ctx, uint64_t event_id, const pp_sou
                                "pp_propagate_batch_async");
     if (!d_hits || !d_counts || (n_src > 0 && !d_src))
       return v.fail(PP_EINVAL, "null device pointer");
-    cudaError_t e = cudaSetDevice(v.device);
-    unsigned char* base = nullptr;
-    if (e == cudaSuccess) e = scratch_address(v.device, &base);
+    unsigned char* base = nullptr;  // with_launch_view made v.device current
+    cudaError_t e = scratch_address(v.device, &base);
     if (e != cudaSuccess) return v.cuda_fail(e, "cudaGetSymbolAddress(noalloc scratch)");
     cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : v.stream;
     if (v.geom.n_dom)
@@ -83,6 +100,7 @@ extern "C" int pp_propagate_noalloc(pp_ctx* ctx, uint64_t event_id, const pp_sou
     e = cudaMemsetAsync(work, 0, sizeof(uint64_t), st);  // the counter starts at 0 each call
     if (e == cudaSuccess) e = ppk::launch_expand(d_src, n_src, nullptr, nullptr, 1, b, st);
     if (e != cudaSuccess) return v.cuda_fail(e, "noalloc expansion");
+    ppk::count_launches(v.ctx, 1);
     ppk::WorkDev w{};
     w.src = d_src;
     w.off = b.off;
@@ -101,6 +119,7 @@ extern "C" int pp_propagate_noalloc(pp_ctx* ctx, uint64_t event_id, const pp_sou
     e = ppk::launch_propagate(true, v.ice, v.geom, w, v.run, v.block_threads, v.grid_blocks, 0,
                               v.smem, st, v.variant);
     if (e != cudaSuccess) return v.cuda_fail(e, "noalloc propagation");
+    ppk::count_launches(v.ctx, 1);
     return PP_OK;
   });
 }

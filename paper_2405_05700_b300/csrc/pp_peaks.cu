@@ -10,6 +10,7 @@
 #include <stdint.h>
 
 #include "pp.h"
+#include "pp_internal.h"
 
 namespace {
 
@@ -66,7 +67,8 @@ extern "C" int pp_measure_issue_rate(int32_t device, int32_t kind, double* lane_
   int n_dev = 0;
   if (cudaGetDeviceCount(&n_dev) != cudaSuccess || n_dev == 0) return PP_ENODEV;
   if (device < 0 || device >= n_dev) return PP_EINVAL;
-  if (cudaSetDevice(device) != cudaSuccess) return PP_ECUDA;
+  ppk::DeviceScope dev_scope(device);
+  if (dev_scope.status() != cudaSuccess) return PP_ECUDA;
   int sms = 0, max_threads = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
       cudaDeviceGetAttribute(&max_threads, cudaDevAttrMaxThreadsPerMultiProcessor, device) !=

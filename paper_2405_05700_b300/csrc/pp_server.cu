@@ -381,7 +381,7 @@ int pp_server_create(pp_ctx* ctx, const pp_server_config* cfg, pp_server** out) 
     delete s;
     return rc;
   }
-  cudaSetDevice(s->view.device);
+  ppk::DeviceScope dev_scope(s->view.device);
   s->slots.resize(cfg->slots);
   for (Slot& sl : s->slots) {
     if (alloc_slot(sl, cfg->max_batch_sources, cfg->max_batch_requests, s->view.geom.n_dom) !=
@@ -406,7 +406,7 @@ int pp_server_destroy(pp_server* s) {
   }
   s->cv_sched.notify_all();
   if (s->sched.joinable()) s->sched.join();
-  cudaSetDevice(s->view.device);
+  ppk::DeviceScope dev_scope(s->view.device);
   for (Slot& sl : s->slots) {
     if (sl.stream) cudaStreamSynchronize(sl.stream);
     free_slot(sl);

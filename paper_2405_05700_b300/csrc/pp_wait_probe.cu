@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "pp.h"
+#include "pp_internal.h"
 #include "tc_gemm.cuh"
 
 namespace {
@@ -33,7 +34,8 @@ extern "C" int pp_debug_wait_timeout(int32_t device, uint64_t limit_ns, int32_t*
   int n_dev = 0;
   if (cudaGetDeviceCount(&n_dev) != cudaSuccess || n_dev == 0) return PP_ENODEV;
   if (device < 0 || device >= n_dev) return PP_EINVAL;
-  if (cudaSetDevice(device) != cudaSuccess) return PP_ECUDA;
+  ppk::DeviceScope dev_scope(device);
+  if (dev_scope.status() != cudaSuccess) return PP_ECUDA;
   int* d_flag = nullptr;
   unsigned long long* d_ns = nullptr;
   if (cudaMalloc(&d_flag, sizeof(int)) != cudaSuccess) return PP_ENOMEM;

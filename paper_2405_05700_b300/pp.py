@@ -73,6 +73,7 @@ _SIGS = {
     "pp_set_kernel_timing": [_vp, _i32],
     "pp_set_graphs": [_vp, _i32],
     "pp_get_path_stats": [_vp, _vp],
+    "pp_get_memory": [_vp, _vp, _vp],
     "pp_get_kernel_time": [_vp, _vp, _vp, _vp],
     "pp_server_config_default": [_vp],
     "pp_server_create": [_vp, _vp, _vp],
@@ -84,6 +85,8 @@ _SIGS = {
     "pp_mlp_destroy": [_vp],
     "pp_mlp_set_params": [_vp, _vp, _i64],
     "pp_mlp_get_params": [_vp, _vp, _i64],
+    "pp_mlp_get_state": [_vp, _vp, _vp, _vp, _i64, _vp],
+    "pp_mlp_set_state": [_vp, _vp, _vp, _vp, _i64, _i64],
     "pp_mlp_features": [_vp, _vp, _vp, _vp, _i64, _vp, _vp],
     "pp_mlp_forward": [_vp, _vp, _vp, _i64, _vp, _vp],
     "pp_mlp_gradients": [_vp, _vp, _vp, _vp, _i64, _vp, _vp],
@@ -286,6 +289,13 @@ def pp_get_kernel_time(ctx):
     ms, nt, nk = C.c_double(), C.c_uint64(), C.c_uint64()
     _call("pp_get_kernel_time", ctx, C.addressof(ms), C.addressof(nt), C.addressof(nk))
     return ms.value, nt.value, nk.value
+
+
+def pp_get_memory(ctx):
+    """(device bytes held by the context's buffers, device allocations made)."""
+    b, n = C.c_uint64(0), C.c_uint64(0)
+    _call("pp_get_memory", ctx, C.addressof(b), C.addressof(n))
+    return b.value, n.value
 
 
 def pp_get_path_stats(ctx):
@@ -494,6 +504,17 @@ def pp_mlp_set_params(m, params, n):
 
 def pp_mlp_get_params(m, params, n):
     return _mcall("pp_mlp_get_params", m, _ptr(params), n)
+
+
+def pp_mlp_get_state(m, params, m1, v1, n):
+    """Returns the Adam step count; fills params (and m1, v1 unless None)."""
+    step = C.c_int64(0)
+    _mcall("pp_mlp_get_state", m, _ptr(params), _ptr(m1), _ptr(v1), n, C.addressof(step))
+    return step.value
+
+
+def pp_mlp_set_state(m, params, m1, v1, n, step):
+    return _mcall("pp_mlp_set_state", m, _ptr(params), _ptr(m1), _ptr(v1), n, step)
 
 
 def pp_mlp_features(m, d_src, d_pair_src, d_pair_dom, n, d_feat, stream=None):

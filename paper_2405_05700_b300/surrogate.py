@@ -7,7 +7,8 @@ kernels.
 
 * make_training_set: sources propagated by Monte Carlo, one event per source;
   every (source, DOM) pair within r_max becomes a training pair with its hit
-  count (pairs farther out carry no light worth learning: see DESIGN notes).
+  count (pairs farther out carry no light worth learning: beyond 250 m the
+  Monte Carlo light of the full detector is ~3e-4 of the total).
 * train: Adam steps over shuffled batches, cosine learning-rate decay.
 * evaluate: per-DOM expected hits of fresh sources from the surrogate against
   Monte Carlo hit counts (Pearson chi2 over DOMs expecting >= 5 hits), the

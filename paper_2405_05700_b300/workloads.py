@@ -9,9 +9,9 @@ step (Sec. 1 and Sec. 2): 5160 DOMs between 1450 m and 2450 m depth, ice in
 10 m layers with per-layer scattering and absorption, light sources handed on
 as photon-emitting steps (Sec. 4), primaries generated on a cylinder slightly
 larger than the instrumented volume (Sec. 4).  The paper prints no workload
-numbers for the propagator itself; the concrete recipes below are the readings
-written down in the design notes (coordinate convention, hex string layout,
-ice profiles, muon-bundle recipe).
+numbers for the propagator itself; the concrete recipes below are readings
+of it, each stated in the docstring of the function that builds it
+(coordinate convention, hex string layout, ice profiles, muon-bundle recipe).
 
 Coordinates: right-handed, metres, z up, ``z = Z0_DEPTH - depth`` with
 ``Z0_DEPTH = 1950``.

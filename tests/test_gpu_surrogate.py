@@ -6,6 +6,8 @@
 * Forward lambda and every parameter's gradient against the oracle network,
   which rounds to BF16 where the device does; the oracle's features are fed
   to both, so the comparison isolates the network.
+* One whole training step (gradients and Adam) against the oracle's
+  loss_and_grads + adam_step; the training state round trip.
 * Training on the propagator's own hit counts lowers the Poisson loss.
 """
 import numpy as np
@@ -164,6 +166,98 @@ def test_gradients_match_oracle(pp, mlp, act):
         a, b = g[idx].astype(np.float64), g_ref[idx]
         err = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
         assert err < 2e-2, (name, err)
+
+
+@pytest.mark.parametrize("act", ["silu", "hswish"])
+def test_full_training_step_matches_oracle(pp, mlp, act):
+    """One pp_mlp_train_step (fused forward, backward, weight and bias
+    gradients, head, Adam) against the oracle's loss_and_grads + adam_step,
+    from a mid-training optimizer state (step 9, non-zero moments) so that the
+    update depends smoothly on the gradient (from zero moments the first Adam
+    step is lr times the gradient's sign, which BF16 can flip for tiny
+    components).
+
+    Tolerances follow from the gradient parity above (relative L2 < 2e-2 per
+    block): the new first moment carries (1 - b1) = 0.1 of the gradient's
+    error, the second moment (1 - b2) = 0.001 of it squared, and the update
+    m_hat / (sqrt(v_hat) + eps) the first moment's; FP32 arithmetic adds
+    ~1e-7.  After the step the BF16 weight copies must be the new parameters:
+    a forward pass equals the oracle network at the device's new parameters."""
+    import torch
+    from oracle import mlp as M
+    rng = np.random.default_rng(21)
+    n, lr, step0 = 4096, 2e-3, 9
+    x, nph, counts = _batch(rng, n)
+    p0 = pp.mlp_init_params(17).astype(np.float64)
+    p0[-1] = -6.0
+    p0 = p0.astype(np.float32)
+    p32 = p0.astype(np.float64)
+    mlp.set_activation(act)
+    loss_ref, g_ref = M.loss_and_grads(p32, x, nph, counts, rounding=True, act=act)
+    blocks = {k: np.asarray(v).ravel().astype(np.int64)
+              for k, v in M.unpack(np.arange(M.N_PARAMS)).items()}
+    m0 = np.zeros(M.N_PARAMS, np.float32)
+    v0 = np.zeros(M.N_PARAMS, np.float32)
+    for idx in blocks.values():
+        rms = float(np.sqrt(np.mean(g_ref[idx] ** 2))) + 1e-30
+        m0[idx] = rng.normal(0.0, rms, len(idx))
+        v0[idx] = (rms * rng.uniform(1.0, 3.0, len(idx))) ** 2
+    pp.pp_mlp_set_state(mlp.handle, p0, m0, v0, M.N_PARAMS, step0)
+    pp.pp_mlp_loss(mlp.handle)                           # clear the running loss
+    feat = _dev(pp.bf16_bits(x).view(np.int16))
+    d_nph = _dev(nph.astype(np.float32))
+    pp.pp_mlp_train_step(mlp.handle, feat, d_nph, _dev(counts.astype(np.float32)), n, lr)
+    loss = pp.pp_mlp_loss(mlp.handle)
+    p1 = np.zeros(M.N_PARAMS, np.float32)
+    m1 = np.zeros(M.N_PARAMS, np.float32)
+    v1 = np.zeros(M.N_PARAMS, np.float32)
+    step1 = pp.pp_mlp_get_state(mlp.handle, p1, m1, v1, M.N_PARAMS)
+    assert step1 == step0 + 1
+    assert abs(loss - loss_ref) <= 1e-3 * abs(loss_ref), (loss, loss_ref)
+    p_ref, m_ref, v_ref = M.adam_step(p32, g_ref, m0.astype(np.float64), v0.astype(np.float64),
+                                      step0 + 1, lr)
+
+    def rel(a, b, idx):
+        b = b[idx]
+        return np.linalg.norm(a[idx].astype(np.float64) - b) / max(np.linalg.norm(b), 1e-30)
+
+    for name, idx in blocks.items():
+        assert rel(m1, m_ref, idx) < 5e-3, (name, "m", rel(m1, m_ref, idx))
+        assert rel(v1, v_ref, idx) < 1e-4, (name, "v", rel(v1, v_ref, idx))
+        d_gpu = p1.astype(np.float64) - p32
+        assert rel(d_gpu, p_ref - p32, idx) < 5e-3, (name, "update", rel(d_gpu, p_ref - p32, idx))
+    # the BF16 copies the next forward pass uses are the new parameters
+    lam_ref, _ = M.forward(p1.astype(np.float64), x, nph, rounding=True, act=act)
+    lam = torch.zeros(n, dtype=torch.float32, device="cuda")
+    pp.pp_mlp_forward(mlp.handle, feat, d_nph, n, lam)
+    pp.pp_mlp_sync(mlp.handle)
+    mlp.set_activation("silu")
+    r = np.abs(lam.cpu().numpy() - lam_ref) / lam_ref
+    assert np.median(r) < 1e-4 and np.quantile(r, 0.99) < 2e-2, (np.median(r), np.quantile(r, 0.99))
+    torch.cuda.synchronize()
+
+
+def test_training_state_round_trip(pp, mlp):
+    """set_state / get_state carry the parameters, both moments and the step
+    count bit for bit; NULL moments start at zero; bad arguments are refused."""
+    from oracle import mlp as M
+    rng = np.random.default_rng(22)
+    p = rng.normal(0, 0.1, M.N_PARAMS).astype(np.float32)
+    m = rng.normal(0, 1e-3, M.N_PARAMS).astype(np.float32)
+    v = rng.uniform(0, 1e-6, M.N_PARAMS).astype(np.float32)
+    pp.pp_mlp_set_state(mlp.handle, p, m, v, M.N_PARAMS, 123)
+    a, b, c = (np.zeros(M.N_PARAMS, np.float32) for _ in range(3))
+    assert pp.pp_mlp_get_state(mlp.handle, a, b, c, M.N_PARAMS) == 123
+    assert np.array_equal(a, p) and np.array_equal(b, m) and np.array_equal(c, v)
+    pp.pp_mlp_set_state(mlp.handle, p, None, None, M.N_PARAMS, 0)
+    assert pp.pp_mlp_get_state(mlp.handle, a, b, c, M.N_PARAMS) == 0
+    assert not b.any() and not c.any()
+    bad = v.copy()
+    bad[5] = -1.0
+    for args in ((p, m, bad, M.N_PARAMS, 1), (p, m, v, M.N_PARAMS - 1, 1), (p, m, v, M.N_PARAMS, -1)):
+        with pytest.raises(pp.PPError) as e:
+            pp.pp_mlp_set_state(mlp.handle, *args)
+        assert e.value.code == pp.PP_EINVAL
 
 
 def test_training_on_propagator_counts_lowers_loss(pp, prop, mlp):

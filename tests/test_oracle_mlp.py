@@ -137,3 +137,125 @@ def test_path_mean_against_numerical_integration():
     # inside one layer: that layer's value; a homogeneous profile: its value
     assert np.allclose(M.path_mean(v, np.array([3.2]), np.array([3.9])), v[3])
     assert np.allclose(M.path_mean(np.full(5, 0.07), u1, u2), 0.07)
+
+
+# ---- the network's definition, pinned against an independent float64 torch
+# model built from the same parameters (torch.nn layers, torch's softplus and
+# Poisson NLL, autograd), not against the oracle's own formulas ------------------
+
+def _torch_net(params, act):
+    import torch
+    P = M.unpack(params)
+    layers = []
+    for l, (n_in, n_out) in enumerate(((M.IN, M.HID), (M.HID, M.HID), (M.HID, M.HID),
+                                       (M.HID, M.HID)), start=1):
+        lin = torch.nn.Linear(n_in, n_out, dtype=torch.float64)
+        with torch.no_grad():
+            lin.weight.copy_(torch.from_numpy(P[f"W{l}"]))
+            lin.bias.copy_(torch.from_numpy(P[f"b{l}"]))
+        layers += [lin, torch.nn.SiLU() if act == "silu" else torch.nn.Hardswish()]
+    head = torch.nn.Linear(M.HID, 1, dtype=torch.float64)
+    with torch.no_grad():
+        head.weight.copy_(torch.from_numpy(P["w5"][None, :]))
+        head.bias.fill_(float(P["b5"]))
+    return torch.nn.Sequential(*layers, head)
+
+
+def _torch_grads_in_oracle_layout(net):
+    lin = [m for m in net if hasattr(m, "weight")]
+    d = {}
+    for l in (1, 2, 3, 4):
+        d[f"W{l}"] = lin[l - 1].weight.grad.numpy()
+        d[f"b{l}"] = lin[l - 1].bias.grad.numpy()
+    d["w5"] = lin[4].weight.grad.numpy()[0]
+    d["b5"] = float(lin[4].bias.grad.numpy()[0])
+    return M.pack(d)
+
+
+@pytest.mark.parametrize("act", ["silu", "hswish"])
+def test_network_loss_and_gradients_match_torch(act):
+    import torch
+    rng = np.random.default_rng(11)
+    n = 96
+    x = rng.normal(0, 1, (n, M.IN))
+    nph = rng.uniform(50, 500, n)
+    counts = rng.poisson(3.0, n).astype(np.float64)
+    counts[:8] = 0.0                                    # the n = 0 term of the loss
+    p = _params(12, scale=3.0 if act == "hswish" else 1.0)
+    net = _torch_net(p, act)
+    xt = torch.from_numpy(x)
+    lam_t = torch.from_numpy(nph) * torch.nn.functional.softplus(net(xt)[:, 0])
+    # Poisson NLL with log input: exp(log lam) - n log lam = lam - n ln lam
+    loss_t = torch.nn.functional.poisson_nll_loss(torch.log(lam_t), torch.from_numpy(counts),
+                                                  log_input=True, full=False, reduction="mean")
+    loss_t.backward()
+    lam, _ = M.forward(p, x, nph, rounding=False, act=act)
+    loss, g = M.loss_and_grads(p, x, nph, counts, rounding=False, act=act)
+    assert np.allclose(lam, lam_t.detach().numpy(), rtol=1e-12, atol=0)
+    assert loss == pytest.approx(float(loss_t), rel=1e-12)
+    gt = _torch_grads_in_oracle_layout(net)
+    scale = np.abs(gt).max()
+    assert np.abs(g - gt).max() <= 1e-10 * scale
+
+
+def test_rounded_forward_matches_torch_with_bf16_casts():
+    """rounding=True: inputs, weights and hidden activations pass through BF16
+    (torch's own float64 -> bfloat16 cast, round to nearest even)."""
+    import torch
+    rng = np.random.default_rng(13)
+    x = rng.normal(0, 1, (64, M.IN))
+    nph = rng.uniform(50, 500, 64)
+    p = _params(14)
+    P = M.unpack(p)
+
+    def r(t):
+        return t.to(torch.bfloat16).to(torch.float64)
+
+    h = r(torch.from_numpy(x))
+    for l in (1, 2, 3, 4):
+        h = r(torch.nn.functional.silu(h @ r(torch.from_numpy(P[f"W{l}"])).T +
+                                       torch.from_numpy(P[f"b{l}"])))
+    lam_t = torch.from_numpy(nph) * torch.nn.functional.softplus(h @ torch.from_numpy(P["w5"]) +
+                                                                 float(P["b5"]))
+    lam, _ = M.forward(p, x, nph, rounding=True)
+    assert np.allclose(lam, lam_t.numpy(), rtol=1e-12, atol=0)
+
+
+# ---- Adam -----------------------------------------------------------------------
+
+def test_adam_matches_torch_optimizer_over_several_steps():
+    import torch
+    rng = np.random.default_rng(15)
+    n, lr = 1000, 3e-3
+    p = rng.normal(0, 1, n)
+    w = torch.nn.Parameter(torch.from_numpy(p.copy()))
+    opt = torch.optim.Adam([w], lr=lr, betas=(0.9, 0.999), eps=1e-8)
+    m = np.zeros(n)
+    v = np.zeros(n)
+    for t in range(1, 8):
+        g = rng.normal(0, 10.0 ** rng.uniform(-4, 1), n)
+        w.grad = torch.from_numpy(g.copy())
+        opt.step()
+        p, m, v = M.adam_step(p, g, m, v, t, lr)
+        st = opt.state[w]
+        # torch forms the averages as m + (1 - b1)(g - m) (another rounding
+        # order): compare at the averages' own scale
+        assert np.abs(m - st["exp_avg"].numpy()).max() <= 1e-14 * np.abs(m).max()
+        assert np.abs(v - st["exp_avg_sq"].numpy()).max() <= 1e-14 * np.abs(v).max()
+        assert np.allclose(p, w.detach().numpy(), rtol=0, atol=1e-12)
+
+
+def test_adam_first_step_and_scale_invariance():
+    """From zero moments the bias corrections give m_hat = g and v_hat = g^2,
+    so the first step is -lr g / (|g| + eps); with eps = 0 a step does not
+    change when the gradient and the moments are scaled by c and c^2."""
+    rng = np.random.default_rng(16)
+    g = rng.normal(0, 1, 500) * 10.0 ** rng.uniform(-6, 2, 500)
+    p0 = rng.normal(0, 1, 500)
+    p1, m1, v1 = M.adam_step(p0, g, np.zeros(500), np.zeros(500), 1, 0.01)
+    assert np.allclose(p1 - p0, -0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=0)
+    assert np.allclose(m1, 0.1 * g, rtol=1e-15) and np.allclose(v1, 0.001 * g * g, rtol=1e-15)
+    m0, v0 = rng.normal(0, 1, 500), rng.uniform(0.5, 2, 500)
+    a = M.adam_step(p0, g, m0, v0, 5, 0.01, eps=0.0)[0]
+    b = M.adam_step(p0, 7.0 * g, 7.0 * m0, 49.0 * v0, 5, 0.01, eps=0.0)[0]
+    assert np.allclose(a, b, rtol=0, atol=1e-13)

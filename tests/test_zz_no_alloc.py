@@ -4,7 +4,8 @@ array instead of cudaMalloc-grown context buffers).
 
 Checked through the C ABI against the allocating entry point pp_propagate on
 the same events, on two calls in a row (the second call reuses the array the
-first one left behind), and for the size limit.  The comparison is exact, as
+first one left behind), for a warm call on a caller-owned stream that must
+allocate nothing, and for the size limit.  The comparison is exact, as
 in the other tally tests: both paths draw the same Philox streams and count
 with integer atomics.  Kept in a file of its own, collected last.
 """
@@ -44,6 +45,37 @@ def test_noalloc_matches_allocating_entry_point_twice_in_a_row():
             assert np.array_equal(got_h, want_h), call
             assert np.array_equal(got_c, want_c), call
             assert int(got_h.sum() + got_c[0] + got_c[1]) == int(src["n_photons"].sum())
+
+        # a warm call on a caller-owned stream allocates nothing: the context's
+        # device bytes and allocation count and the device's free memory are
+        # unchanged across it; it launches its two kernels; its result and the
+        # error check (pp_sync on that same stream) are ordered on that stream;
+        # the caller's current device is left as it was
+        e = events[-1]
+        src = np.ascontiguousarray(batch.event(e))
+        ev_id = int(batch.event_ids[e]) + 100
+        want_h, want_c = prop.propagate(ev_id, src)
+        d_src = torch.from_numpy(src.view(np.uint8).copy()).to(dev)
+        d_hits = torch.full((geom.n_dom,), -1, dtype=torch.int64, device=dev)
+        d_counts = torch.full((4,), -1, dtype=torch.int64, device=dev)
+        user = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        pp.pp_set_kernel_timing(prop.ctx, False)
+        pp.pp_get_kernel_time(prop.ctx)                      # reset the launch count
+        mem0 = pp.pp_get_memory(prop.ctx)
+        free0 = torch.cuda.mem_get_info()[0]
+        device0 = torch.cuda.current_device()
+        pp.pp_propagate_noalloc(prop.ctx, ev_id, d_src, len(src), d_hits, d_counts,
+                                user.cuda_stream)
+        pp.pp_sync(prop.ctx, user.cuda_stream)
+        assert torch.cuda.mem_get_info()[0] == free0
+        assert pp.pp_get_memory(prop.ctx) == mem0
+        assert pp.pp_get_kernel_time(prop.ctx)[2] == 2
+        assert torch.cuda.current_device() == device0
+        with torch.cuda.stream(user):
+            got_h = d_hits.cpu().numpy().astype(np.uint64)
+            got_c = d_counts.cpu().numpy().astype(np.uint64)
+        assert np.array_equal(got_h, want_h) and np.array_equal(got_c, want_c)
 
         # more sources than the static array holds: refused, nothing enqueued
         big = np.ascontiguousarray(np.concatenate([batch.sources, batch.sources]))
