@@ -639,7 +639,7 @@ def run_ours(args):
                    "l2": "flushed (256 MB write) between steps, outside the timed events",
                    "timed_launch": "CUDA-graph replay of the captured step",
                    "launch": dict(zip(("block_threads", "blocks_per_sm", "refill_threshold",
-                                       "grid_blocks"), prop.get_launch()))},
+                                       "photons_per_lane", "grid_blocks"), prop.get_launch()))},
         "plain": {"value": plain_value, "unit": UNIT,
                   "ms_per_step": statistics.mean(plain_ms) if plain_ms else None,
                   "same_hits_as_batched": plain_same},

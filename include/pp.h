@@ -264,27 +264,38 @@ int pp_sync(pp_ctx* ctx, void* stream);
 /* Launch settings of the persistent kernel (the autotuner's knobs).
  *   block_threads     128, 256, 512 or 1024 (0: keep)
  *   blocks_per_sm     >= 1 (0: as many as fit)
- *   refill_threshold  1..32: a warp claims new photons once at least this
- *                     many of its lanes are idle (0: keep) */
+ *   refill_threshold  1..32: a warp gives its idle lanes new photons once at
+ *                     least this many of them are idle (0: keep)
+ *   photons_per_lane  1: idle lanes are given photons born on the spot, by
+ *                     those lanes alone; 2: each warp also keeps up to 48
+ *                     photons born ahead in shared memory (2.3 KiB per warp,
+ *                     2.6 KiB in the hit-records variant), topped up 32 at a
+ *                     time by all of its lanes together, and idle lanes take
+ *                     the next of those (0: keep)
+ * Defaults: 1024, 0, 2, 2.  Results never depend on these settings (every
+ * photon draws its own random numbers and the tallies are integers).
+ * Errors: PP_EINVAL. */
 int pp_set_launch(pp_ctx* ctx, int32_t block_threads, int32_t blocks_per_sm,
-                  int32_t refill_threshold);
+                  int32_t refill_threshold, int32_t photons_per_lane);
 
 /* Autotuner: times the batched path on the given device-resident batch (as
  * pp_propagate_batch_async) for a fixed set of launch settings -- block size
  * 128..1024, 4 to 6 resident 256-thread blocks per SM (register-capped kernel
- * variants), refill thresholds 1..32 -- each once untimed and `repeats` times
- * timed with CUDA events on `stream`, keeps the fastest, and reports it in
- * best3 = {block_threads, blocks_per_sm, refill_threshold} and best_ms (both
- * may be NULL).  Results do not depend on the settings (the outputs of the
- * last run are valid).  Errors: as pp_propagate_batch_async. */
+ * variants), refill thresholds 1..32, one or two photons per lane -- each once
+ * untimed and `repeats` times timed with CUDA events on `stream`, keeps the
+ * fastest, and reports it in best4 = {block_threads, blocks_per_sm,
+ * refill_threshold, photons_per_lane} and best_ms (both may be NULL).  Results
+ * do not depend on the settings (the outputs of the last run are valid).
+ * Errors: as pp_propagate_batch_async. */
 int pp_autotune_batch(pp_ctx* ctx, int32_t n_events, const uint64_t* d_event_ids,
                       const int64_t* d_src_begin, const pp_source* d_src, int64_t n_src,
                       uint64_t* d_hits, uint64_t* d_counts, void* stream, int32_t repeats,
-                      int32_t* best3, float* best_ms);
+                      int32_t* best4, float* best_ms);
 
-/* Reads back the launch settings in use (any pointer may be NULL). */
+/* Reads back the launch settings in use and the persistent grid they give
+ * (any pointer may be NULL). */
 int pp_get_launch(const pp_ctx* ctx, int32_t* block_threads, int32_t* blocks_per_sm,
-                  int32_t* refill_threshold, int32_t* grid_blocks);
+                  int32_t* refill_threshold, int32_t* photons_per_lane, int32_t* grid_blocks);
 
 /* CUDA graphs for pp_propagate_batch_async.  While enabled, the first call with
  * a given shape (event and source counts, device pointers, stream, launch

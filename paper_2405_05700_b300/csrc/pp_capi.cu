@@ -55,9 +55,13 @@ struct pp_ctx {
   int n_accept = 0;                    // hit-record acceptance polynomial
   float accept[PP_MAX_ACCEPT_COEFFS] = {};
 
-  int block_threads = 256;
+  // defaults: the fastest setting measured on the full-detector batch
+  // (1024-thread blocks, one per SM; reserved photons handed out once two
+  // lanes are idle)
+  int block_threads = 1024;
   int blocks_per_sm = 0;  // 0: occupancy maximum
-  int refill = 8;
+  int refill = 2;
+  int lane_photons = 2;   // 2: the persistent kernel keeps a per-warp photon reserve
 
   // CUDA graphs of the batched path, keyed by everything a capture bakes in
   struct GraphEntry {
@@ -183,21 +187,41 @@ int check_loaded(pp_ctx* ctx) {
   return PP_OK;
 }
 
-int prepare_smem(pp_ctx* ctx, size_t* smem) {
-  *smem = tables_smem_bytes(ctx->ice, ctx->geom);
-  if (*smem > ctx->smem_limit_set || ctx->smem_limit_set == 0) {
-    cudaError_t e = set_propagate_smem_limit(std::max<size_t>(*smem, 48 * 1024));
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute");
-    ctx->smem_limit_set = std::max<size_t>(*smem, 48 * 1024);
-  }
-  return PP_OK;
+// Register-capped kernel variant for the launch settings (see launch_propagate),
+// with the photon reserve when two photons per lane are asked for.
+// One photon per lane: 256-thread blocks at 5 or 6 per SM use kernels capped at
+// 48 / 40 registers.  Two photons per lane: 256-thread blocks at 3 per SM use
+// a kernel allowed 80 registers (the reserve's birth pass holds a second
+// photon's state beside the lane's own).
+int kernel_variant(const pp_ctx* ctx, bool records = false) {
+  const bool reserve = ctx->lane_photons == 2;
+  int v = 0;
+  if (records) v = kVariantRecords;
+  else if (ctx->block_threads == 256 && !reserve &&
+           (ctx->blocks_per_sm == 5 || ctx->blocks_per_sm == 6))
+    v = ctx->blocks_per_sm;
+  else if (ctx->block_threads == 256 && reserve && ctx->blocks_per_sm == 3)
+    v = 3;
+  return reserve ? v + kVariantReserve : v;
 }
 
-// Register-capped kernel variant for the launch settings (see launch_propagate).
-int kernel_variant(const pp_ctx* ctx) {
-  if (ctx->block_threads == 256 && (ctx->blocks_per_sm == 5 || ctx->blocks_per_sm == 6))
-    return ctx->blocks_per_sm;
-  return 0;
+// Dynamic shared memory of a launch of `variant` (0 for the kernels without a
+// reserve): the staged tables, plus the photon reserve of reserve variants;
+// raises the kernels' limit when needed.
+int prepare_smem(pp_ctx* ctx, size_t* smem, int variant) {
+  *smem = tables_smem_bytes(ctx->ice, ctx->geom);
+  if (variant >= kVariantReserve) {
+    const int base = variant - kVariantReserve;
+    const int bt = (base == 3 || base == 5 || base == 6) ? 256 : ctx->block_threads;
+    *smem += reserve_smem_bytes(bt, base == kVariantRecords);
+  }
+  if (*smem > ctx->smem_limit_set || ctx->smem_limit_set == 0) {
+    const size_t lim = std::max<size_t>(*smem, 48 * 1024);
+    cudaError_t e = set_propagate_smem_limit(lim);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute");
+    ctx->smem_limit_set = lim;
+  }
+  return PP_OK;
 }
 
 int grid_blocks(pp_ctx* ctx, size_t smem, int* out, int variant = -1) {
@@ -338,12 +362,12 @@ int batch_async(pp_ctx* ctx, int32_t n_events, const uint64_t* d_ids, const int6
     return fail(ctx, PP_EINVAL, "hit records: need a count pointer, a buffer for capacity > 0 "
                                 "and 1 <= group_index < 10");
   const size_t hb = sizeof(uint64_t) * (size_t)n_events * ctx->geom.n_dom;
-  const int variant = rec ? kVariantRecords : kernel_variant(ctx);
+  const int variant = kernel_variant(ctx, rec != nullptr);
   size_t smem = 0;
   int grid = 0;
   if (n_src > 0) {
     if ((rc = ensure_scratch(ctx, n_src, true))) return rc;
-    if ((rc = prepare_smem(ctx, &smem))) return rc;
+    if ((rc = prepare_smem(ctx, &smem, variant))) return rc;
     if ((rc = grid_blocks(ctx, smem, &grid, variant))) return rc;
   }
   auto enqueue = [&]() -> int {
@@ -369,7 +393,8 @@ int batch_async(pp_ctx* ctx, int32_t n_events, const uint64_t* d_ids, const int6
   const uint64_t key[12] = {(uint64_t)n_events, (uint64_t)n_src, (uint64_t)d_ids, (uint64_t)d_begin,
                             (uint64_t)d_src, (uint64_t)d_hits, (uint64_t)d_counts, (uint64_t)st,
                             ctx->epoch, (uint64_t)ctx->block_threads,
-                            (uint64_t)ctx->blocks_per_sm, (uint64_t)ctx->refill};
+                            (uint64_t)ctx->blocks_per_sm,
+                            (uint64_t)ctx->refill | (uint64_t)ctx->lane_photons << 32};
   for (const auto& g : ctx->graph_cache) {
     if (std::memcmp(g.key, key, sizeof(key)) == 0) {
       PP_CUDA(cudaGraphLaunch(g.exec, st));
@@ -419,7 +444,7 @@ int range_async(pp_ctx* ctx, uint64_t event_id, const pp_source* d_src, int64_t 
   if (n_src == 0 || g1 == g0) return PP_OK;
   if ((rc = ensure_scratch(ctx, n_src, false))) return rc;
   size_t smem;
-  if ((rc = prepare_smem(ctx, &smem))) return rc;
+  if ((rc = prepare_smem(ctx, &smem, kernel_variant(ctx)))) return rc;
   int grid;
   if ((rc = grid_blocks(ctx, smem, &grid))) return rc;
   PP_CUDA(cudaMemsetAsync(ctx->work.p, 0, sizeof(uint64_t), st));
@@ -455,7 +480,7 @@ int plain_async(pp_ctx* ctx, int32_t n_events, const uint64_t* h_ids, const int6
   PP_CUDA(cudaMemsetAsync(d_counts, 0, sizeof(uint64_t) * 4 * (size_t)n_events, st));
   if ((rc = ensure_scratch(ctx, std::max<int64_t>(max_src, 1), false))) return rc;
   size_t smem;
-  if ((rc = prepare_smem(ctx, &smem))) return rc;
+  if ((rc = prepare_smem(ctx, &smem, 0))) return rc;
   const RunDev run = run_params(ctx);
   for (int32_t e = 0; e < n_events; ++e) {
     const int64_t n = h_begin[e + 1] - h_begin[e];
@@ -698,7 +723,7 @@ int with_launch_view(pp_ctx* ctx, const std::function<int(const LaunchView&)>& f
   v.block_threads = ctx->block_threads;
   v.variant = kernel_variant(ctx);
   v.scatter_effective = ctx->cfg.scatter_coeff_is_effective;
-  if ((rc = prepare_smem(ctx, &v.smem))) return rc;
+  if ((rc = prepare_smem(ctx, &v.smem, v.variant))) return rc;
   if ((rc = grid_blocks(ctx, v.smem, &v.grid_blocks))) return rc;
   v.err = static_cast<int*>(ctx->err.p);
   v.stats = static_cast<unsigned long long*>(ctx->stats.p);
@@ -1063,7 +1088,7 @@ int pp_sync(pp_ctx* ctx, void* stream) {
 }
 
 int pp_set_launch(pp_ctx* ctx, int32_t block_threads, int32_t blocks_per_sm,
-                  int32_t refill_threshold) {
+                  int32_t refill_threshold, int32_t photons_per_lane) {
   if (!ctx) return PP_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (block_threads != 0 && block_threads != 128 && block_threads != 256 && block_threads != 512 &&
@@ -1071,27 +1096,31 @@ int pp_set_launch(pp_ctx* ctx, int32_t block_threads, int32_t blocks_per_sm,
     return fail(ctx, PP_EINVAL, "block_threads must be 128, 256, 512 or 1024");
   if (blocks_per_sm < 0 || refill_threshold < 0 || refill_threshold > 32)
     return fail(ctx, PP_EINVAL, "blocks_per_sm >= 0 and 0 <= refill_threshold <= 32");
+  if (photons_per_lane < 0 || photons_per_lane > 2)
+    return fail(ctx, PP_EINVAL, "photons_per_lane must be 0 (keep), 1 or 2");
   if (block_threads) ctx->block_threads = block_threads;
   ctx->blocks_per_sm = blocks_per_sm;
   if (refill_threshold) ctx->refill = refill_threshold;
+  if (photons_per_lane) ctx->lane_photons = photons_per_lane;
   return PP_OK;
 }
 
 int pp_get_launch(const pp_ctx* ctx_c, int32_t* block_threads, int32_t* blocks_per_sm,
-                  int32_t* refill_threshold, int32_t* grid) {
+                  int32_t* refill_threshold, int32_t* photons_per_lane, int32_t* grid) {
   pp_ctx* ctx = const_cast<pp_ctx*>(ctx_c);
   if (!ctx) return PP_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (block_threads) *block_threads = ctx->block_threads;
   if (blocks_per_sm) *blocks_per_sm = ctx->blocks_per_sm;
   if (refill_threshold) *refill_threshold = ctx->refill;
+  if (photons_per_lane) *photons_per_lane = ctx->lane_photons;
   if (grid) {
     *grid = 0;
     if (ctx->geom_loaded && ctx->ice_loaded) {
       DeviceScope dev_scope(ctx->cfg.device);
-  PP_CUDA(dev_scope.status());
+      PP_CUDA(dev_scope.status());
       size_t smem;
-      int rc = prepare_smem(ctx, &smem);
+      int rc = prepare_smem(ctx, &smem, kernel_variant(ctx));
       if (!rc) rc = grid_blocks(ctx, smem, grid);
       if (rc) return rc;
     }
@@ -1102,7 +1131,7 @@ int pp_get_launch(const pp_ctx* ctx_c, int32_t* block_threads, int32_t* blocks_p
 int pp_autotune_batch(pp_ctx* ctx, int32_t n_events, const uint64_t* d_event_ids,
                       const int64_t* d_src_begin, const pp_source* d_src, int64_t n_src,
                       uint64_t* d_hits, uint64_t* d_counts, void* stream, int32_t repeats,
-                      int32_t* best3, float* best_ms) {
+                      int32_t* best4, float* best_ms) {
   if (!ctx) return PP_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
   DeviceScope dev_scope(ctx->cfg.device);
@@ -1110,13 +1139,21 @@ int pp_autotune_batch(pp_ctx* ctx, int32_t n_events, const uint64_t* d_event_ids
   if (repeats < 1) repeats = 1;
   cudaStream_t st = pick_stream(ctx, stream);
   struct Cand {
-    int bt, bps, refill;
+    int bt, bps, refill, lane_photons;
   };
+  // one photon per lane: refill thresholds around the measured optimum (8);
+  // two photons per lane: reserved photons are cheap to hand out, so small
+  // thresholds; the reserve's shared memory limits 256-thread blocks to 3-4
+  // per SM, so larger blocks (tables staged once for more warps) are tried
   static const Cand cands[] = {
-      {256, 0, 1},  {256, 0, 2},  {256, 0, 4},  {256, 0, 8},  {256, 0, 16}, {256, 0, 32},
-      {256, 5, 4},  {256, 5, 8},  {256, 5, 16}, {256, 6, 4},  {256, 6, 8},  {256, 6, 16},
-      {128, 0, 4},  {128, 0, 8},  {128, 0, 16}, {512, 0, 8},  {512, 0, 16}, {1024, 0, 16}};
-  const int keep_bt = ctx->block_threads, keep_bps = ctx->blocks_per_sm, keep_r = ctx->refill;
+      {256, 0, 1, 1},  {256, 0, 2, 1},  {256, 0, 4, 1},  {256, 0, 8, 1},  {256, 0, 16, 1},
+      {256, 0, 32, 1}, {256, 5, 4, 1},  {256, 5, 8, 1},  {256, 5, 16, 1}, {256, 6, 4, 1},
+      {256, 6, 8, 1},  {256, 6, 16, 1}, {128, 0, 4, 1},  {128, 0, 8, 1},  {128, 0, 16, 1},
+      {512, 0, 8, 1},  {512, 0, 16, 1}, {1024, 0, 16, 1},
+      {256, 0, 1, 2},  {256, 0, 2, 2},  {256, 0, 4, 2},  {256, 3, 1, 2},  {256, 3, 2, 2},
+      {256, 3, 4, 2},  {512, 0, 1, 2},  {512, 0, 2, 2},  {512, 0, 4, 2},  {1024, 0, 1, 2},
+      {1024, 0, 2, 2}, {1024, 0, 4, 2}};
+  const Cand keep{ctx->block_threads, ctx->blocks_per_sm, ctx->refill, ctx->lane_photons};
   const bool keep_timing = ctx->timing, keep_graphs = ctx->graphs;
   ctx->timing = false;
   ctx->graphs = false;
@@ -1124,12 +1161,13 @@ int pp_autotune_batch(pp_ctx* ctx, int32_t n_events, const uint64_t* d_event_ids
   PP_CUDA(cudaEventCreate(&e0));
   PP_CUDA(cudaEventCreate(&e1));
   float best = 3.4e38f;
-  Cand win{keep_bt, keep_bps, keep_r};
+  Cand win = keep;
   int rc = PP_OK;
   for (const Cand& c : cands) {
     ctx->block_threads = c.bt;
     ctx->blocks_per_sm = c.bps;
     ctx->refill = c.refill;
+    ctx->lane_photons = c.lane_photons;
     // warm-up launch, then the timed ones
     rc = batch_async(ctx, n_events, d_event_ids, d_src_begin, d_src, n_src, d_hits, d_counts, st);
     if (rc) break;
@@ -1153,14 +1191,17 @@ int pp_autotune_batch(pp_ctx* ctx, int32_t n_events, const uint64_t* d_event_ids
   cudaEventDestroy(e1);
   ctx->timing = keep_timing;
   ctx->graphs = keep_graphs;
-  ctx->block_threads = rc ? keep_bt : win.bt;
-  ctx->blocks_per_sm = rc ? keep_bps : win.bps;
-  ctx->refill = rc ? keep_r : win.refill;
+  const Cand& use = rc ? keep : win;
+  ctx->block_threads = use.bt;
+  ctx->blocks_per_sm = use.bps;
+  ctx->refill = use.refill;
+  ctx->lane_photons = use.lane_photons;
   if (rc) return rc;
-  if (best3) {
-    best3[0] = win.bt;
-    best3[1] = win.bps;
-    best3[2] = win.refill;
+  if (best4) {
+    best4[0] = win.bt;
+    best4[1] = win.bps;
+    best4[2] = win.refill;
+    best4[3] = win.lane_photons;
   }
   if (best_ms) *best_ms = best;
   return PP_OK;
@@ -1292,7 +1333,7 @@ int pp_debug_trace(pp_ctx* ctx, uint64_t event_id, const pp_source* src, int64_t
   if ((rc = ensure(ctx, ctx->s_misc4, 12 * (size_t)n * std::max(n_trace, 1)))) return rc;
   if ((rc = ensure_scratch(ctx, n_src, false))) return rc;
   size_t smem;
-  if ((rc = prepare_smem(ctx, &smem))) return rc;
+  if ((rc = prepare_smem(ctx, &smem, 0))) return rc;
   PP_CUDA(cudaMemcpyAsync(ctx->s_src.p, src, sizeof(pp_source) * n_src, cudaMemcpyHostToDevice, st));
   PP_CUDA(cudaMemcpyAsync(ctx->s_misc1.p, photon_ids, 8 * n, cudaMemcpyHostToDevice, st));
   const pp_source* d_src = static_cast<const pp_source*>(ctx->s_src.p);
@@ -1386,7 +1427,7 @@ int pp_debug_first_hit(pp_ctx* ctx, const float* seg, int64_t n, int32_t mode, i
   if ((rc = ensure(ctx, ctx->s_misc2, 4 * (size_t)n))) return rc;
   if ((rc = ensure(ctx, ctx->s_misc3, 4 * (size_t)n))) return rc;
   size_t smem;
-  if ((rc = prepare_smem(ctx, &smem))) return rc;
+  if ((rc = prepare_smem(ctx, &smem, 0))) return rc;
   PP_CUDA(cudaMemcpyAsync(ctx->s_misc1.p, seg, 28 * n, cudaMemcpyHostToDevice, st));
   PP_CUDA(launch_first_hit(ctx->geom, ctx->ice, static_cast<float*>(ctx->s_misc1.p), n, mode,
                            static_cast<int*>(ctx->s_misc2.p), static_cast<float*>(ctx->s_misc3.p),

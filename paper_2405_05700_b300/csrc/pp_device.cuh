@@ -254,9 +254,14 @@ __device__ __forceinline__ void test_string(const GeomDev& G, const Tables& T, i
 
 // First DOM met on [p, p + S d] (smallest t, ties to the lowest index).
 // Fast path: a step shorter (horizontally) than its cell's clearance cannot
-// reach any string.  Otherwise the cell's string list (steps up to `halo`
-// long) or every string is searched.
-// clear_out (optional) receives the clearance of the start point's cell: no
+// reach any string.  Next, the clearance of the start point itself: strings
+// missing from the cell's list lie more than `halo` beyond their cylinders'
+// radius from every point of the cell, so the point's clearance is at least
+// min(halo, distance to each listed string's cylinder), less a 1 cm margin
+// for FP32 rounding; a step shorter than that cannot reach a string either.
+// Otherwise the cell's string list (steps up to `halo` long) or every string
+// is searched.
+// clear_out (optional) receives the larger of the two clearances: no
 // horizontal displacement shorter than it reaches a string.
 __device__ __forceinline__ int first_hit_grid(const GeomDev& G, const Tables& T, float px,
                                               float py, float pz, float dx, float dy, float dz,
@@ -272,7 +277,19 @@ __device__ __forceinline__ int first_hit_grid(const GeomDev& G, const Tables& T,
   const int ix = min(max(__float2int_rd((px - G.gx0) * G.inv_cell), 0), G.nx - 1);
   const int iy = min(max(__float2int_rd((py - G.gy0) * G.inv_cell), 0), G.ny - 1);
   const int cell = iy * G.nx + ix;
-  const float clr = (float)T.clear[cell] * G.clear_unit;
+  float clr = (float)T.clear[cell] * G.clear_unit;
+  if (L2 < clr * clr) {
+    if (clear_out) *clear_out = clr;
+    return -1;
+  }
+  const uint32_t b = __ldg(G.cell_off + cell), e = __ldg(G.cell_off + cell + 1);
+  float pc = G.halo;
+  for (uint32_t j = b; j < e; ++j) {
+    const float4 st = T.str[__ldg(G.cell_list + j)];
+    const float ox = px - st.x, oy = py - st.y;
+    pc = fminf(pc, fast_sqrt(fmaf(ox, ox, oy * oy)) - st.z);
+  }
+  clr = fmaxf(clr, pc - 0.01f);
   if (clear_out) *clear_out = clr;
   if (L2 < clr * clr) return -1;
   slow += 1;
@@ -280,7 +297,6 @@ __device__ __forceinline__ int first_hit_grid(const GeomDev& G, const Tables& T,
   int best = -1;
   float bt = PP_INF;
   if (Lxy <= G.halo) {
-    const uint32_t b = __ldg(G.cell_off + cell), e = __ldg(G.cell_off + cell + 1);
     for (uint32_t j = b; j < e; ++j)
       test_string(G, T, (int)__ldg(G.cell_list + j), px, py, pz, dx, dy, dz, S, dxy2, best, bt);
   } else {

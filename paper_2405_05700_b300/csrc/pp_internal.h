@@ -127,15 +127,34 @@ struct RunDev {
   uint32_t seed_lo;
   uint32_t max_steps;
   float cos_cherenkov, sin_cherenkov;
-  int refill;                 // persistent: refill once this many lanes are idle
+  int refill;                 // persistent: refill once this many lanes are idle (with the
+                              // reserve: take reserved photons once this many are idle)
   float ns_per_m_emit;        // hit time: emission offset along the segment at c (ns / m)
   float ns_per_m_path;        // hit time: photon path at the group velocity (ns / m)
   int n_accept;               // hit records: acceptance polynomial in the direction's z
   float accept[PP_MAX_ACCEPT_COEFFS];
 };
 
-// Shared-memory footprint of the tables the propagation kernels stage.
+// Shared-memory footprint of the tables the propagation kernels stage
+// (layers float4, strings float4 + int2, u8 clearance cells; 16-byte multiple).
+__host__ __device__ inline size_t tables_bytes(int n_layers, int n_str, int n_cells) {
+  const size_t b = (size_t)n_layers * 16 + (size_t)n_str * 24 + (size_t)n_cells;
+  return (b + 15) & ~(size_t)15;
+}
 size_t tables_smem_bytes(const IceDev& ice, const GeomDev& geom);
+
+// Photon reserve of the persistent kernel (two photons per lane): each warp
+// keeps up to kReserveCap born photons in shared memory, kReserveWords 32-bit
+// words each (position, direction, tau_a, layer, id words, event slot; the
+// records variant adds the emission offset and the source index), laid out
+// word-major so that consecutive slots fall in consecutive banks.
+constexpr int kReserveCap = 48;
+constexpr int kReserveWords = 12;
+constexpr int kReserveWordsRecords = 14;
+inline size_t reserve_smem_bytes(int block_threads, bool records) {
+  return (size_t)(block_threads / 32) * kReserveCap *
+         (records ? kReserveWordsRecords : kReserveWords) * 4;
+}
 
 // Scratch needed by the expansion for n_src sources.
 struct ExpandBufs {
@@ -157,8 +176,12 @@ cudaError_t launch_expand(const pp_source* src, int64_t n_src, const int64_t* sr
 //   persistent = true : grid_blocks persistent blocks with warp refill
 // variant selects the register budget of the persistent kernel: 0 = any block
 // size (up to 64 registers), 5 / 6 = 256-thread blocks, 5 / 6 resident per SM;
-// kVariantRecords = variant 0 that also writes compact hit records.
+// kVariantRecords = variant 0 that also writes compact hit records;
+// + kVariantReserve: the same kernel with a per-warp photon reserve (two
+// photons per lane: births of whole warps into shared memory, idle lanes
+// take the next reserved photon).
 constexpr int kVariantRecords = 7;
+constexpr int kVariantReserve = 16;
 
 // Hit times: light speed in vacuum, and the group index used unless the
 // caller gives one (the paper gives none; 1.35 is a typical value for ice in

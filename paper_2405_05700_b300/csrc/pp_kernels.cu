@@ -204,15 +204,214 @@ __global__ void k_finish(int64_t n_src, const int64_t* __restrict__ src_begin,
 }
 
 // ---- a2..a8: propagation ---------------------------------------------------
+__device__ __forceinline__ void flush_path_stats(const WorkDev& W, uint64_t steps,
+                                                 uint32_t crossings, uint32_t births,
+                                                 uint32_t slow) {
+  if (!W.stats) return;
+  unsigned long long v0 = steps, v1 = crossings, v2 = births, v3 = slow;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v0 += __shfl_down_sync(kFull, v0, o);
+    v1 += __shfl_down_sync(kFull, v1, o);
+    v2 += __shfl_down_sync(kFull, v2, o);
+    v3 += __shfl_down_sync(kFull, v3, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(W.stats + 0, v0);
+    atomicAdd(W.stats + 1, v1);
+    atomicAdd(W.stats + 2, v2);
+    atomicAdd(W.stats + 3, v3);
+  }
+}
+
+// a8 with a photon reserve: the warp keeps up to kReserveCap born photons in
+// shared memory.  Whenever the reserve holds no more than kReserveCap - 32,
+// the warp claims 32 photon indices with one atomic and all 32 lanes give
+// birth together (one converged pass, instead of a pass for the few lanes
+// that happen to be idle); idle lanes take the next reserved photons once
+// `refill` of them are idle (or the work is exhausted).  Only which lane runs
+// which photon changes: every photon still draws its own Philox streams.
+// Values the reserve loop needs only at a top-up or a hand-out are re-read
+// there instead of being kept in registers across the photon step (whose
+// register budget is what limits the kernel): special registers and the
+// expansion's totals, read with volatile asm so that the compiler does not
+// hoist them out of the loop.
+extern __shared__ __align__(16) unsigned char dyn_smem[];
+
+__device__ __forceinline__ unsigned tid_x() {
+  unsigned t;
+  asm volatile("mov.u32 %0, %%tid.x;" : "=r"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned lanes_below() {
+  unsigned m;
+  asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ uint64_t ld_u64_volatile(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.global.nc.u64 %0, [%1];" : "=l"(v) : "l"(p));
+  return v;
+}
+
+// The warp's reserve ring and the lane's parking slot, after the tables.
+template <bool kRecords>
+__device__ __forceinline__ uint32_t* reserve_ring(const IceDev& I, const GeomDev& G) {
+  constexpr int RW = kRecords ? kReserveWordsRecords : kReserveWords;
+  uint32_t* rings = reinterpret_cast<uint32_t*>(dyn_smem + tables_bytes(I.L, G.n_str, G.nx * G.ny));
+  return rings + (tid_x() >> 5) * (kReserveCap * RW);
+}
+
+// One top-up of the warp's reserve: claim 32 photon indices with one atomic,
+// give birth to them on all 32 lanes, append the well-formed ones to the ring
+// after its rcount live slots from rhead.  Returns the new rcount; sets
+// `exhausted` once the claim reaches the end of the work.  Kept out of line:
+// it runs once per ~40 steps of the warp, and as a call its temporaries do
+// not compete for registers with the photon step.
+template <bool kRecords>
+__device__ __noinline__ int topup(const IceDev& I, const GeomDev& G, const WorkDev& W,
+                                  const RunDev& R, int rhead, int rcount, bool& exhausted) {
+  constexpr int CAP = kReserveCap;
+  const uint64_t total = ld_u64_volatile(W.meta + 0);
+  const uint32_t k = (uint32_t)ld_u64_volatile(W.meta + 1);
+  const uint64_t end = total < W.g_end ? total : W.g_end;
+  const unsigned lane = tid_x() & 31;
+  unsigned long long base = 0;
+  if (lane == 0) base = W.g_begin + atomicAdd(W.work, 32ull);
+  base = __shfl_sync(kFull, base, 0);
+  if (base + 32 >= end) exhausted = true;
+  if (base < end) {
+    uint64_t in_src = 0;
+    const int s = locate_claim(W, k, base, lane, end, in_src);
+    const uint64_t g = base + lane;
+    bool ok = false;
+    Photon q;
+    if (g < end) {
+      identify(W, s, in_src, g, q);
+      ok = birth(q, W.src[s], I, R);
+      if (!ok) atomicOr(W.err, kErrBadSource);
+    }
+    const unsigned okm = __ballot_sync(kFull, ok);
+    if (W.stats && lane == 0) {
+      const uint64_t left = end - base;
+      atomicAdd(W.stats + 2, (unsigned long long)(left < 32 ? left : 32));
+    }
+    if (ok) {
+      uint32_t* ring = reserve_ring<kRecords>(I, G);
+      float* ringf = reinterpret_cast<float*>(ring);
+      int slot = rhead + rcount + __popc(okm & lanes_below());
+      if (slot >= CAP) slot -= CAP;
+      ringf[0 * CAP + slot] = q.px;
+      ringf[1 * CAP + slot] = q.py;
+      ringf[2 * CAP + slot] = q.pz;
+      ringf[3 * CAP + slot] = q.dx;
+      ringf[4 * CAP + slot] = q.dy;
+      ringf[5 * CAP + slot] = q.dz;
+      ringf[6 * CAP + slot] = q.tau_a;
+      ring[7 * CAP + slot] = (uint32_t)q.layer;
+      ring[8 * CAP + slot] = q.pid_lo;
+      ring[9 * CAP + slot] = q.pid_hi;
+      ring[10 * CAP + slot] = q.ev_lo;
+      ring[11 * CAP + slot] = (uint32_t)q.ev;
+      if (kRecords) {
+        ringf[12 * CAP + slot] = q.t_emit;
+        ring[13 * CAP + slot] = (uint32_t)s;
+      }
+    }
+    rcount += __popc(okm);
+  }
+  return rcount;
+}
+
+template <bool kRecords>
+__device__ __forceinline__ void run_with_reserve(const IceDev& I, const GeomDev& G,
+                                                 const WorkDev& W, const RunDev& R,
+                                                 const Tables& T) {
+  constexpr int CAP = kReserveCap;
+  bool alive = false, exhausted = false;
+  int rhead = 0, rcount = 0;  // warp-uniform ring state
+  // path statistics: births are added per warp at each top-up; steps per lane
+  // fit 32 bits (a launch gives a lane far fewer than 2^32 steps)
+  uint32_t crossings = 0, slow = 0, steps = 0;
+  LaneTally lt;
+  Photon ph;
+  for (;;) {
+    if (!exhausted && rcount <= CAP - 32) {
+      __syncwarp();  // earlier reads of the slots about to be refilled are done
+      rcount = topup<kRecords>(I, G, W, R, rhead, rcount, exhausted);
+      __syncwarp();  // the new slots are visible to every lane of the warp
+    }
+    const unsigned idle = __ballot_sync(kFull, !alive);
+    const int n_idle = __popc(idle);
+    if (rcount > 0 && n_idle > 0 && (n_idle >= R.refill || exhausted)) {
+      const int n = min(n_idle, rcount);
+      const int rank = __popc(idle & lanes_below());
+      if (!alive && rank < n) {
+        const uint32_t* ring = reserve_ring<kRecords>(I, G);
+        const float* ringf = reinterpret_cast<const float*>(ring);
+        int slot = rhead + rank;
+        if (slot >= CAP) slot -= CAP;
+        ph.px = ringf[0 * CAP + slot];
+        ph.py = ringf[1 * CAP + slot];
+        ph.pz = ringf[2 * CAP + slot];
+        ph.dx = ringf[3 * CAP + slot];
+        ph.dy = ringf[4 * CAP + slot];
+        ph.dz = ringf[5 * CAP + slot];
+        ph.tau_a = ringf[6 * CAP + slot];
+        ph.layer = (int)ring[7 * CAP + slot];
+        ph.pid_lo = ring[8 * CAP + slot];
+        ph.pid_hi = ring[9 * CAP + slot];
+        ph.ev_lo = ring[10 * CAP + slot];
+        ph.ev = (int)ring[11 * CAP + slot];
+        if (kRecords) {
+          ph.t_emit = ringf[12 * CAP + slot];
+          ph.src = (int)ring[13 * CAP + slot];
+        }
+        ph.path = 0.0f;
+        ph.n = 0;
+        ph.wb = -1.0f;
+        ph.cb = -1.0f;
+        alive = true;
+      }
+      rhead += n;
+      if (rhead >= CAP) rhead -= CAP;
+      rcount -= n;
+    }
+    if (__ballot_sync(kFull, alive) == 0) {
+      if (exhausted && rcount == 0) break;
+      continue;
+    }
+    if (alive) {
+      const int out = photon_step(ph, I, G, T, R, crossings, slow);
+      if (out != kScattered) {
+        tally(W, G.n_dom, ph, out, lt);
+        if (kRecords && out >= 0) record_hit(W, R, ph, out);
+        steps += ph.n;
+        alive = false;
+      }
+    }
+  }
+  flush(W, lt);
+  flush_path_stats(W, steps, crossings, 0, slow);
+}
+
 // kRecords (persistent only): also append a compact record per hit.
-template <bool kPersistent, int kMinBlocks, bool kRecords = false>
+// kReserve (persistent only): the photon reserve above.
+template <bool kPersistent, int kMinBlocks, bool kRecords = false, bool kReserve = false>
 __global__ void __launch_bounds__(kMinBlocks > 0 ? 256 : 1024, kMinBlocks > 0 ? kMinBlocks : 1)
-k_propagate(IceDev I, GeomDev G, WorkDev W, RunDev R, uint64_t n_plain) {
+k_propagate(const __grid_constant__ IceDev I, const __grid_constant__ GeomDev G,
+            const __grid_constant__ WorkDev W, const __grid_constant__ RunDev R, uint64_t n_plain) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Tables T = stage_tables(smem, I, G);
   __syncthreads();
   const uint64_t total = __ldg(W.meta + 0);
   const uint32_t k = (uint32_t)__ldg(W.meta + 1);
+  if (kPersistent && kReserve) {
+    run_with_reserve<kRecords>(I, G, W, R, T);
+    return;
+  }
   Photon ph;
   if (!kPersistent) {
     const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -280,22 +479,7 @@ k_propagate(IceDev I, GeomDev G, WorkDev W, RunDev R, uint64_t n_plain) {
       }
     }
     flush(W, lt);
-    if (W.stats) {
-      unsigned long long v0 = steps, v1 = crossings, v2 = births, v3 = slow;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        v0 += __shfl_down_sync(kFull, v0, o);
-        v1 += __shfl_down_sync(kFull, v1, o);
-        v2 += __shfl_down_sync(kFull, v2, o);
-        v3 += __shfl_down_sync(kFull, v3, o);
-      }
-      if (lane == 0) {
-        atomicAdd(W.stats + 0, v0);
-        atomicAdd(W.stats + 1, v1);
-        atomicAdd(W.stats + 2, v2);
-        atomicAdd(W.stats + 3, v3);
-      }
-    }
+    flush_path_stats(W, steps, crossings, births, slow);
   }
 }
 
@@ -383,8 +567,7 @@ __global__ void k_first_hit(GeomDev G, IceDev I, const float* seg, int64_t n, in
 }  // namespace
 
 size_t tables_smem_bytes(const IceDev& ice, const GeomDev& geom) {
-  const size_t b = (size_t)ice.L * 16 + (size_t)geom.n_str * 24 + (size_t)geom.nx * geom.ny;
-  return (b + 15) & ~(size_t)15;
+  return tables_bytes(ice.L, geom.n_str, geom.nx * geom.ny);
 }
 
 cudaError_t launch_expand(const pp_source* src, int64_t n_src, const int64_t* src_begin,
@@ -406,7 +589,12 @@ cudaError_t launch_expand(const pp_source* src, int64_t n_src, const int64_t* sr
 cudaError_t set_propagate_smem_limit(size_t smem) {
   const void* fns[] = {(const void*)k_propagate<true, 0>, (const void*)k_propagate<true, 5>,
                        (const void*)k_propagate<true, 6>, (const void*)k_propagate<false, 0>,
-                       (const void*)k_propagate<true, 0, true>};
+                       (const void*)k_propagate<true, 0, true>,
+                       (const void*)k_propagate<true, 0, false, true>,
+                       (const void*)k_propagate<true, 5, false, true>,
+                       (const void*)k_propagate<true, 6, false, true>,
+                       (const void*)k_propagate<true, 3, false, true>,
+                       (const void*)k_propagate<true, 0, true, true>};
   cudaError_t e;
   for (const void* f : fns) {
     e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -418,18 +606,32 @@ cudaError_t set_propagate_smem_limit(size_t smem) {
                               (int)smem);
 }
 
+// The kernel instance of a variant (register budget, records, reserve).
+const void* propagate_fn(int variant) {
+  switch (variant) {
+    case 5: return (const void*)k_propagate<true, 5>;
+    case 6: return (const void*)k_propagate<true, 6>;
+    case kVariantRecords: return (const void*)k_propagate<true, 0, true>;
+    case kVariantReserve: return (const void*)k_propagate<true, 0, false, true>;
+    case kVariantReserve + 5: return (const void*)k_propagate<true, 5, false, true>;
+    case kVariantReserve + 6: return (const void*)k_propagate<true, 6, false, true>;
+    case kVariantReserve + 3: return (const void*)k_propagate<true, 3, false, true>;
+    case kVariantReserve + kVariantRecords: return (const void*)k_propagate<true, 0, true, true>;
+    default: return (const void*)k_propagate<true, 0>;
+  }
+}
+
+// Register-capped variants (minimum blocks per SM in their launch bounds) run
+// 256-thread blocks.
+int variant_threads(int variant, int block_threads) {
+  const int base = variant % kVariantReserve;
+  return (base == 3 || base == 5 || base == 6) ? 256 : block_threads;
+}
+
 cudaError_t propagate_occupancy(int block_threads, size_t smem, int variant, int* blocks_per_sm) {
-  if (variant == 5)
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_propagate<true, 5>, 256,
-                                                         smem);
-  if (variant == 6)
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_propagate<true, 6>, 256,
-                                                         smem);
-  if (variant == kVariantRecords)
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        blocks_per_sm, k_propagate<true, 0, true>, block_threads, smem);
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_propagate<true, 0>,
-                                                       block_threads, smem);
+  const int bt = variant_threads(variant, block_threads);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, propagate_fn(variant), bt,
+                                                       smem);
 }
 
 cudaError_t launch_propagate(bool persistent, const IceDev& ice, const GeomDev& geom,
@@ -437,20 +639,14 @@ cudaError_t launch_propagate(bool persistent, const IceDev& ice, const GeomDev& 
                              int grid_blocks, uint64_t n_photons_host, size_t smem,
                              cudaStream_t st, int variant) {
   if (persistent) {
-    if (variant == 5)
-      k_propagate<true, 5><<<grid_blocks, 256, smem, st>>>(ice, geom, work, run, 0);
-    else if (variant == 6)
-      k_propagate<true, 6><<<grid_blocks, 256, smem, st>>>(ice, geom, work, run, 0);
-    else if (variant == kVariantRecords)
-      k_propagate<true, 0, true><<<grid_blocks, block_threads, smem, st>>>(ice, geom, work, run, 0);
-    else
-      k_propagate<true, 0><<<grid_blocks, block_threads, smem, st>>>(ice, geom, work, run, 0);
-  } else {
-    if (n_photons_host == 0) return cudaSuccess;
-    const uint64_t nb = (n_photons_host + block_threads - 1) / block_threads;
-    k_propagate<false, 0><<<(unsigned)nb, block_threads, smem, st>>>(ice, geom, work, run,
-                                                                      n_photons_host);
+    const int bt = variant_threads(variant, block_threads);
+    void* args[] = {(void*)&ice, (void*)&geom, (void*)&work, (void*)&run, (void*)&n_photons_host};
+    return cudaLaunchKernel(propagate_fn(variant), dim3(grid_blocks), dim3(bt), args, smem, st);
   }
+  if (n_photons_host == 0) return cudaSuccess;
+  const uint64_t nb = (n_photons_host + block_threads - 1) / block_threads;
+  k_propagate<false, 0><<<(unsigned)nb, block_threads, smem, st>>>(ice, geom, work, run,
+                                                                    n_photons_host);
   return cudaGetLastError();
 }
 

@@ -66,9 +66,9 @@ _SIGS = {
                                    _vp, _vp],
     "pp_propagate_range_async": [_vp, _u64, _vp, _i64, _u64, _u64, _i32, _vp, _vp, _vp],
     "pp_sync": [_vp, _vp],
-    "pp_set_launch": [_vp, _i32, _i32, _i32],
+    "pp_set_launch": [_vp, _i32, _i32, _i32, _i32],
     "pp_autotune_batch": [_vp, _i32, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _i32, _vp, _vp],
-    "pp_get_launch": [_vp, _vp, _vp, _vp, _vp],
+    "pp_get_launch": [_vp, _vp, _vp, _vp, _vp, _vp],
     "pp_get_world": [_vp, _vp],
     "pp_set_kernel_timing": [_vp, _i32],
     "pp_set_graphs": [_vp, _i32],
@@ -249,14 +249,15 @@ def pp_sync(ctx, stream=None):
     return _call("pp_sync", ctx, _ptr(stream))
 
 
-def pp_set_launch(ctx, block_threads=0, blocks_per_sm=0, refill_threshold=0):
-    return _call("pp_set_launch", ctx, block_threads, blocks_per_sm, refill_threshold)
+def pp_set_launch(ctx, block_threads=0, blocks_per_sm=0, refill_threshold=0, photons_per_lane=0):
+    return _call("pp_set_launch", ctx, block_threads, blocks_per_sm, refill_threshold,
+                 photons_per_lane)
 
 
 def pp_autotune_batch(ctx, n_events, d_event_ids, d_src_begin, d_src, n_src, d_hits, d_counts,
                       stream=None, repeats=2):
-    """-> ((block_threads, blocks_per_sm, refill_threshold), best_ms)"""
-    best = (C.c_int32 * 3)()
+    """-> ((block_threads, blocks_per_sm, refill_threshold, photons_per_lane), best_ms)"""
+    best = (C.c_int32 * 4)()
     ms = C.c_float()
     _call("pp_autotune_batch", ctx, n_events, _ptr(d_event_ids), _ptr(d_src_begin), _ptr(d_src),
           n_src, _ptr(d_hits), _ptr(d_counts), _ptr(stream), repeats, C.addressof(best),
@@ -265,7 +266,8 @@ def pp_autotune_batch(ctx, n_events, d_event_ids, d_src_begin, d_src, n_src, d_h
 
 
 def pp_get_launch(ctx):
-    v = [C.c_int32() for _ in range(4)]
+    """-> (block_threads, blocks_per_sm, refill_threshold, photons_per_lane, grid_blocks)"""
+    v = [C.c_int32() for _ in range(5)]
     _call("pp_get_launch", ctx, *[C.addressof(x) for x in v])
     return tuple(x.value for x in v)
 
@@ -693,8 +695,8 @@ class Propagator:
         pp_propagate_batch(self.ctx, E, ids, beg, s if s.size else None, hits, counts)
         return hits, counts
 
-    def set_launch(self, block_threads=0, blocks_per_sm=0, refill_threshold=0):
-        pp_set_launch(self.ctx, block_threads, blocks_per_sm, refill_threshold)
+    def set_launch(self, block_threads=0, blocks_per_sm=0, refill_threshold=0, photons_per_lane=0):
+        pp_set_launch(self.ctx, block_threads, blocks_per_sm, refill_threshold, photons_per_lane)
 
     def get_launch(self):
         return pp_get_launch(self.ctx)
