@@ -50,7 +50,6 @@ struct pp_ctx {
   DevBuf off2, chunk2, aux2, bsum2, meta2, work2;
   // staging for host entry points
   DevBuf s_src, s_begin, s_ids, s_hits, s_counts, s_misc1, s_misc2, s_misc3, s_misc4, s_bad;
-  size_t smem_limit_set = 0;
 
   int n_accept = 0;                    // hit-record acceptance polynomial
   float accept[PP_MAX_ACCEPT_COEFFS] = {};
@@ -215,12 +214,9 @@ int prepare_smem(pp_ctx* ctx, size_t* smem, int variant) {
     const int bt = (base == 3 || base == 5 || base == 6) ? 256 : ctx->block_threads;
     *smem += reserve_smem_bytes(bt, base == kVariantRecords);
   }
-  if (*smem > ctx->smem_limit_set || ctx->smem_limit_set == 0) {
-    const size_t lim = std::max<size_t>(*smem, 48 * 1024);
-    cudaError_t e = set_propagate_smem_limit(lim);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute");
-    ctx->smem_limit_set = lim;
-  }
+  // raises the kernels' limit (process-wide, never lowered) when needed
+  const cudaError_t e = set_propagate_smem_limit(std::max<size_t>(*smem, 48 * 1024));
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute");
   return PP_OK;
 }
 

@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "pp_device.cuh"
 #include "pp_internal.h"
 
@@ -586,7 +588,21 @@ cudaError_t launch_expand(const pp_source* src, int64_t n_src, const int64_t* sr
   return cudaGetLastError();
 }
 
+// The dynamic shared-memory limit is an attribute of each kernel, shared by
+// every context on the device: it is only ever raised, so that one context
+// cannot lower it under another's launches.
+namespace {
+std::mutex g_smem_mu;
+size_t g_smem_limit[64] = {};
+}  // namespace
+
 cudaError_t set_propagate_smem_limit(size_t smem) {
+  int dev = 0;
+  cudaError_t e0 = cudaGetDevice(&dev);
+  if (e0 != cudaSuccess) return e0;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_smem_mu);
+  if (smem <= g_smem_limit[dev]) return cudaSuccess;
   const void* fns[] = {(const void*)k_propagate<true, 0>, (const void*)k_propagate<true, 5>,
                        (const void*)k_propagate<true, 6>, (const void*)k_propagate<false, 0>,
                        (const void*)k_propagate<true, 0, true>,
@@ -602,8 +618,9 @@ cudaError_t set_propagate_smem_limit(size_t smem) {
   }
   e = cudaFuncSetAttribute(k_trace, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_first_hit, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem);
+  e = cudaFuncSetAttribute(k_first_hit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) g_smem_limit[dev] = smem;
+  return e;
 }
 
 // The kernel instance of a variant (register budget, records, reserve).
