@@ -334,30 +334,44 @@ int pp_get_world(const pp_ctx* ctx, float* out3);
  * in blocks to one photon server, which aggregates steps from many events and
  * clients to keep the GPU busy; several client instances share one memory
  * budget.  A pp_server runs that server on a context: any number of host
- * threads submit bunches (pp_submit) and collect their results (pp_collect);
- * one scheduler thread admits bunches in arrival order under a fixed budget and
- * runs them in batches as soon as one of `slots` batch slots is free
- * (continuous batching: bunches that arrive while others run join the next
- * batch, and the slots' kernels overlap on the device).  A bunch's result is
- * the same alone and in any mix. */
+ * threads submit bunches (pp_submit) and collect their results (pp_collect).
+ * Admitted bunches live in a request ring in device memory; a persistent
+ * serving kernel claims photons from the ring 32 at a time while requests keep
+ * arriving (continuous batching on the device: a bunch admitted while others
+ * run is taken by the running kernel, next to them), and raises a flag in
+ * host-mapped memory when a bunch's last photon is tallied.  A scheduler
+ * thread admits bunches in arrival order while the ring, the device arenas and
+ * the budget allow, copies finished bunches' outputs back, and relaunches the
+ * kernel, which leaves after idle_exit_us without work and stops taking
+ * photons max_launch_ms after its launch.  A bunch's result is the same alone
+ * and in any mix. */
 typedef struct pp_server pp_server; /* opaque */
 
 typedef struct pp_server_config {
-  uint64_t budget_bytes;        /* admission budget (default 8 GiB): a bunch is charged
-                                   photon_state_bytes per photon + 68 B per source +
-                                   8 B per DOM + 64 B while admitted and not finished */
-  uint64_t photon_state_bytes;  /* bytes charged per photon (default 32) */
-  int32_t slots;                /* batches in flight at once, 1..16 (default 3) */
-  int32_t max_batch_requests;   /* bunches per batch (default 512) */
-  int64_t max_batch_sources;    /* sources per batch, also per bunch (default 1 << 20) */
+  uint64_t budget_bytes;  /* admission cap (default 8 GiB) on the device bytes the
+                             admitted bunches occupy: per bunch 40 B per source
+                             (arena), 8 B per source + 8 (photon prefix), 4 B per
+                             photon chunk + 4 (chunk table), 8 B per DOM + 32
+                             (output slot) and 64 B (ring entry).  Photon state
+                             lives in registers and shared memory, so no bytes
+                             are charged per photon. */
+  int64_t arena_sources;  /* device source-arena capacity, also the most sources of
+                             one bunch (default 4 194 304) */
+  int32_t ring_requests;  /* request-ring slots = bunches admitted at once; a power
+                             of two, 1..65536 (default 256) */
+  int32_t idle_exit_us;   /* the serving kernel leaves after this long with nothing
+                             to claim (default 1000) */
+  int32_t max_launch_ms;  /* and stops claiming this long after its launch; the
+                             scheduler relaunches it (default 200) */
 } pp_server_config;
 
 /* Fills *cfg with the defaults above. */
 int pp_server_config_default(pp_server_config* cfg);
 
 /* Starts a server on ctx (geometry and ice loaded; while the server exists the
- * context refuses new geometry or ice).  Allocates `slots` sets of device
- * buffers and pinned staging sized by the batch limits.
+ * context refuses new geometry or ice).  Allocates the ring, the arenas (52 B
+ * per arena source), the output slots (8 B per DOM per ring slot) and pinned
+ * host mirrors of the same size, and starts the scheduler thread.
  * Errors: PP_EINVAL, PP_ENOTLOADED, PP_ENOMEM. */
 int pp_server_create(pp_ctx* ctx, const pp_server_config* cfg, pp_server** out);
 
@@ -365,27 +379,30 @@ int pp_server_create(pp_ctx* ctx, const pp_server_config* cfg, pp_server** out);
  * server; results not yet collected are discarded. */
 int pp_server_destroy(pp_server* server);
 
+/* Message for the last error the server met (never NULL). */
+const char* pp_server_last_error(const pp_server* server);
+
 /* Thread-safe.  Copies n_src host sources of one bunch (event id as for
  * pp_propagate) and queues it; *ticket_out identifies it.
- * Errors: PP_EINVAL (bad source, too many sources), PP_EBUDGET (the bunch alone
- * costs more than the whole budget). */
+ * A bunch with no photons is complete at once (zero outputs).
+ * Errors: PP_EINVAL (bad source, 2^35 photons or more), PP_EBUDGET (the bunch
+ * alone occupies more than the whole budget, or has more sources than the
+ * arena), PP_ECUDA (the server failed earlier). */
 int pp_submit(pp_server* server, uint64_t event_id, const pp_source* src, int64_t n_src,
               uint64_t* ticket_out);
 
 /* Thread-safe.  Waits up to timeout_ms (< 0: no limit) for the bunch's result
  * and copies it to hits[n_dom] and counts[4] (either may be NULL); the ticket
  * is then released.  Errors: PP_EINVAL (unknown ticket), PP_ETIMEDOUT (not done
- * yet; the ticket stays valid), PP_EDEVICE / PP_ECUDA (the batch failed). */
+ * yet; the ticket stays valid), PP_EDEVICE / PP_ECUDA (the bunch failed). */
 int pp_collect(pp_server* server, uint64_t ticket, uint64_t* hits, uint64_t* counts,
                int32_t timeout_ms);
 
 /* out8 = {bunches done, photons done, p50 latency ms, p99 latency ms,
- * photons/s from first submit to last completion, mean bunches per batch,
- * batches, peak admitted bytes}; latency = submit to result ready. */
+ * photons/s from first submit to last completion, serving-kernel launches,
+ * peak admitted bytes (device bytes occupied by admitted bunches), device
+ * bytes the server allocated}; latency = submit to result ready. */
 int pp_server_stats(pp_server* server, double* out8);
-
-/* Message for the last scheduler error (never NULL). */
-const char* pp_server_last_error(const pp_server* server);
 
 /* ---- learned surrogate -------------------------------------------------- */
 /* No counterpart in the paper's propagation step: an MLP that predicts the

@@ -484,14 +484,25 @@ __device__ __forceinline__ int photon_step(Photon& ph, const IceDev& I, const Ge
   return kScattered;
 }
 
+// Loads of the work description's read-only arrays.  kCg: through L2 only
+// (ld.global.cg), for memory the host may have rewritten while the kernel
+// runs (the serving arenas, reused by later requests), where a line left in
+// an SM's L1 could be stale; otherwise the read-only path.
+template <bool kCg, class T>
+__device__ __forceinline__ T ld_work(const T* p) {
+  if (kCg) return __ldcg(p);
+  return __ldg(p);
+}
+
 // Source containing batch photon index g: the last s with off[s] <= g, found
 // inside the range the photon-chunk table gives for g's chunk.
+template <bool kCg = false>
 __device__ __forceinline__ int find_source(const WorkDev& W, uint32_t chunk_log2, uint64_t g) {
   const uint64_t c = g >> chunk_log2;
-  int lo = (int)__ldg(W.chunk_src + c), hi = (int)__ldg(W.chunk_src + c + 1);
+  int lo = (int)ld_work<kCg>(W.chunk_src + c), hi = (int)ld_work<kCg>(W.chunk_src + c + 1);
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (__ldg(W.off + mid) <= g) lo = mid;
+    if (ld_work<kCg>(W.off + mid) <= g) lo = mid;
     else hi = mid - 1;
   }
   return lo;
@@ -529,14 +540,15 @@ __device__ __forceinline__ int locate(const WorkDev& W, uint32_t chunk_log2, uin
 // 5-step shuffle search for how many of them lie at or below its photon.
 // Returns the lane's source; in_src receives the photon's index inside it.
 // Must be called by all 32 lanes; `rank` only matters for lanes that use it.
+template <bool kCg = false>
 __device__ __forceinline__ int locate_claim(const WorkDev& W, uint32_t chunk_log2, uint64_t g0,
                                             uint32_t rank, uint64_t total, uint64_t& in_src) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const int s0 = find_source(W, chunk_log2, g0);
-  const uint64_t off0 = __ldg(W.off + s0);
+  const int s0 = find_source<kCg>(W, chunk_log2, g0);
+  const uint64_t off0 = ld_work<kCg>(W.off + s0);
   const int sj = s0 + 1 + lane;
-  const uint64_t bj = (sj <= W.n_src) ? __ldg(W.off + sj) : ~0ull;
+  const uint64_t bj = (sj <= W.n_src) ? ld_work<kCg>(W.off + sj) : ~0ull;
   const uint64_t dj = bj - g0;  // > 0: boundary after source s0 + lane, relative to g0
   const uint32_t kj = dj > 0xffffffffull ? 0xffffffffu : (uint32_t)dj;
   int pos = 0;
@@ -553,8 +565,8 @@ __device__ __forceinline__ int locate_claim(const WorkDev& W, uint32_t chunk_log
       in_src = 0;
       return s0;
     }
-    const int s = find_source(W, chunk_log2, g);
-    in_src = g - __ldg(W.off + s);
+    const int s = find_source<kCg>(W, chunk_log2, g);
+    in_src = g - ld_work<kCg>(W.off + s);
     return s;
   }
   in_src = (pos == 0) ? (g0 - off0) + rank : (uint64_t)(rank - kprev);

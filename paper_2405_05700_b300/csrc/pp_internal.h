@@ -237,6 +237,57 @@ struct LaunchView {
 
 int with_launch_view(pp_ctx* ctx, const std::function<int(const LaunchView&)>& fn);
 
+// ---- serving: the device-resident request ring ------------------------------
+// One admitted request (a bunch of sources of one event) in the ring the
+// serving kernel pulls photons from; request q lives in slot q % cap.  The
+// host fills a slot in two copies before it publishes the request: first
+// everything but `claimed` (done = 0), then `claimed` = (q mod 2^28) << 36,
+// which arms the slot.  Warps claim photons by adding 32 to `claimed`: the
+// high bits say which request the claim went to, the low bits where it
+// starts.  A claim is kept only if the slot's seq matches its high bits and
+// it starts below the total, so a warp still looking at a slot's previous
+// request can never take photons twice.
+struct ServeReq {
+  unsigned long long claimed;  // (request number mod 2^28) << 36 | photons claimed
+  unsigned long long done;     // photons tallied so far
+  uint64_t total;              // photons of the request (0 < total < 2^35)
+  uint64_t src_off;            // its first source in the source arena
+  uint64_t off_off;            // its photon prefix (n_src + 1 entries) in the prefix arena
+  uint64_t chunk_off;          // its photon-chunk table in the chunk arena
+  uint32_t n_src, chunk_log2;  // as the batch expansion's meta
+  uint32_t event_lo;           // event id, low word (the Philox key word)
+  uint32_t seq;                // request number (low word)
+};
+static_assert(sizeof(ServeReq) == 64, "request entry layout");
+
+constexpr int kServeOffsetBits = 36;
+constexpr int kServeSeqBits = 28;
+constexpr uint64_t kServeMaxPhotons = 1ull << 35;  // headroom above a total for late claims
+constexpr int kServeMaxRequests = 1 << 16;         // ring capacity limit (a power of two)
+
+struct ServeDev {
+  ServeReq* req;                     // [cap] (cap a power of two)
+  int cap;
+  const unsigned long long* tail;    // requests published (written by host copies)
+  unsigned long long* head;          // oldest request that may have unclaimed photons
+  const pp_source* src;              // source arena
+  const uint64_t* off;               // prefix arena
+  const uint32_t* chunk;             // chunk arena
+  unsigned long long* hits;          // [cap][n_dom]
+  unsigned long long* counts;        // [cap][4] absorbed, escaped, truncated, steps
+  volatile uint32_t* done_flag;      // host-mapped [cap]: seq + 1 once tallied
+  int* err;
+  uint64_t idle_ns;                  // a warp leaves after this long with nothing to do
+  uint64_t max_ns;                   // and stops taking new photons this long after launch
+};
+
+// The serving kernel: persistent blocks (1024 threads, photon reserve) that
+// take photons from published requests until idle.
+cudaError_t launch_serve(const IceDev& ice, const GeomDev& geom, const ServeDev& sv,
+                         const RunDev& run, int grid_blocks, size_t smem, cudaStream_t st);
+cudaError_t serve_occupancy(size_t smem, int* blocks_per_sm);
+constexpr int kServeThreads = 1024;
+
 // Servers that hold a LaunchView of the context (its table pointers): while
 // any is attached the context refuses to load new geometry or ice.
 void attach_server(pp_ctx* ctx, int delta);

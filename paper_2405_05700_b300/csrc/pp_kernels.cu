@@ -258,12 +258,62 @@ __device__ __forceinline__ uint64_t ld_u64_volatile(const uint64_t* p) {
   return v;
 }
 
-// The warp's reserve ring and the lane's parking slot, after the tables.
+// The warp's reserve ring, after the tables.
 template <bool kRecords>
 __device__ __forceinline__ uint32_t* reserve_ring(const IceDev& I, const GeomDev& G) {
   constexpr int RW = kRecords ? kReserveWordsRecords : kReserveWords;
   uint32_t* rings = reinterpret_cast<uint32_t*>(dyn_smem + tables_bytes(I.L, G.n_str, G.nx * G.ny));
   return rings + (tid_x() >> 5) * (kReserveCap * RW);
+}
+
+// A born photon into ring slot `slot` / the photon of a slot out of the ring
+// (word-major: word j of slot i at ring[j * kReserveCap + i]).
+template <bool kRecords>
+__device__ __forceinline__ void ring_put(uint32_t* ring, int slot, const Photon& q, int src) {
+  constexpr int CAP = kReserveCap;
+  float* ringf = reinterpret_cast<float*>(ring);
+  ringf[0 * CAP + slot] = q.px;
+  ringf[1 * CAP + slot] = q.py;
+  ringf[2 * CAP + slot] = q.pz;
+  ringf[3 * CAP + slot] = q.dx;
+  ringf[4 * CAP + slot] = q.dy;
+  ringf[5 * CAP + slot] = q.dz;
+  ringf[6 * CAP + slot] = q.tau_a;
+  ring[7 * CAP + slot] = (uint32_t)q.layer;
+  ring[8 * CAP + slot] = q.pid_lo;
+  ring[9 * CAP + slot] = q.pid_hi;
+  ring[10 * CAP + slot] = q.ev_lo;
+  ring[11 * CAP + slot] = (uint32_t)q.ev;
+  if (kRecords) {
+    ringf[12 * CAP + slot] = q.t_emit;
+    ring[13 * CAP + slot] = (uint32_t)src;
+  }
+}
+
+template <bool kRecords>
+__device__ __forceinline__ void ring_take(const uint32_t* ring, int slot, Photon& ph) {
+  constexpr int CAP = kReserveCap;
+  const float* ringf = reinterpret_cast<const float*>(ring);
+  ph.px = ringf[0 * CAP + slot];
+  ph.py = ringf[1 * CAP + slot];
+  ph.pz = ringf[2 * CAP + slot];
+  ph.dx = ringf[3 * CAP + slot];
+  ph.dy = ringf[4 * CAP + slot];
+  ph.dz = ringf[5 * CAP + slot];
+  ph.tau_a = ringf[6 * CAP + slot];
+  ph.layer = (int)ring[7 * CAP + slot];
+  ph.pid_lo = ring[8 * CAP + slot];
+  ph.pid_hi = ring[9 * CAP + slot];
+  ph.ev_lo = ring[10 * CAP + slot];
+  ph.ev = (int)ring[11 * CAP + slot];
+  if (kRecords) {
+    ph.t_emit = ringf[12 * CAP + slot];
+    ph.src = (int)ring[13 * CAP + slot];
+  }
+  ph.path = 0.0f;
+  ph.n = 0;
+  ph.wb = -1.0f;
+  ph.cb = -1.0f;
 }
 
 // One top-up of the warp's reserve: claim 32 photon indices with one atomic,
@@ -301,26 +351,9 @@ __device__ __noinline__ int topup(const IceDev& I, const GeomDev& G, const WorkD
       atomicAdd(W.stats + 2, (unsigned long long)(left < 32 ? left : 32));
     }
     if (ok) {
-      uint32_t* ring = reserve_ring<kRecords>(I, G);
-      float* ringf = reinterpret_cast<float*>(ring);
       int slot = rhead + rcount + __popc(okm & lanes_below());
       if (slot >= CAP) slot -= CAP;
-      ringf[0 * CAP + slot] = q.px;
-      ringf[1 * CAP + slot] = q.py;
-      ringf[2 * CAP + slot] = q.pz;
-      ringf[3 * CAP + slot] = q.dx;
-      ringf[4 * CAP + slot] = q.dy;
-      ringf[5 * CAP + slot] = q.dz;
-      ringf[6 * CAP + slot] = q.tau_a;
-      ring[7 * CAP + slot] = (uint32_t)q.layer;
-      ring[8 * CAP + slot] = q.pid_lo;
-      ring[9 * CAP + slot] = q.pid_hi;
-      ring[10 * CAP + slot] = q.ev_lo;
-      ring[11 * CAP + slot] = (uint32_t)q.ev;
-      if (kRecords) {
-        ringf[12 * CAP + slot] = q.t_emit;
-        ring[13 * CAP + slot] = (uint32_t)s;
-      }
+      ring_put<kRecords>(reserve_ring<kRecords>(I, G), slot, q, s);
     }
     rcount += __popc(okm);
   }
@@ -351,30 +384,9 @@ __device__ __forceinline__ void run_with_reserve(const IceDev& I, const GeomDev&
       const int n = min(n_idle, rcount);
       const int rank = __popc(idle & lanes_below());
       if (!alive && rank < n) {
-        const uint32_t* ring = reserve_ring<kRecords>(I, G);
-        const float* ringf = reinterpret_cast<const float*>(ring);
         int slot = rhead + rank;
         if (slot >= CAP) slot -= CAP;
-        ph.px = ringf[0 * CAP + slot];
-        ph.py = ringf[1 * CAP + slot];
-        ph.pz = ringf[2 * CAP + slot];
-        ph.dx = ringf[3 * CAP + slot];
-        ph.dy = ringf[4 * CAP + slot];
-        ph.dz = ringf[5 * CAP + slot];
-        ph.tau_a = ringf[6 * CAP + slot];
-        ph.layer = (int)ring[7 * CAP + slot];
-        ph.pid_lo = ring[8 * CAP + slot];
-        ph.pid_hi = ring[9 * CAP + slot];
-        ph.ev_lo = ring[10 * CAP + slot];
-        ph.ev = (int)ring[11 * CAP + slot];
-        if (kRecords) {
-          ph.t_emit = ringf[12 * CAP + slot];
-          ph.src = (int)ring[13 * CAP + slot];
-        }
-        ph.path = 0.0f;
-        ph.n = 0;
-        ph.wb = -1.0f;
-        ph.cb = -1.0f;
+        ring_take<kRecords>(reserve_ring<kRecords>(I, G), slot, ph);
         alive = true;
       }
       rhead += n;
@@ -483,6 +495,239 @@ k_propagate(const __grid_constant__ IceDev I, const __grid_constant__ GeomDev G,
     flush(W, lt);
     flush_path_stats(W, steps, crossings, births, slow);
   }
+}
+
+// ---- serving: photons pulled from the device request ring -------------------
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Per-lane tallies of the request the lane last worked on (as LaneTally),
+// plus the number of its photons tallied.  The flush adds them to the
+// request's counters and that number to its done count, after a fence that
+// makes the lane's hit atomics visible first; the flush that brings done to
+// the request's total raises the request's host-visible flag.
+struct ServeTally {
+  int slot = -1;
+  uint32_t absorbed = 0, escaped = 0, truncated = 0, photons = 0;
+  unsigned long long steps = 0;
+};
+
+__device__ __forceinline__ void serve_done(const ServeDev& S, int slot, unsigned long long n) {
+  __threadfence();
+  ServeReq* r = S.req + slot;
+  const unsigned long long before = atomicAdd(&r->done, n);
+  if (before + n == __ldcg(&r->total)) {
+    __threadfence_system();
+    S.done_flag[slot] = __ldcg(&r->seq) + 1u;
+  }
+}
+
+__device__ __noinline__ void serve_flush(const ServeDev& S, ServeTally& t) {
+  if (t.slot >= 0 && t.photons) {
+    unsigned long long* cnt = S.counts + (size_t)t.slot * 4;
+    if (t.absorbed) atomicAdd(cnt + 0, (unsigned long long)t.absorbed);
+    if (t.escaped) atomicAdd(cnt + 1, (unsigned long long)t.escaped);
+    if (t.truncated) atomicAdd(cnt + 2, (unsigned long long)t.truncated);
+    if (t.steps) atomicAdd(cnt + 3, t.steps);
+    serve_done(S, t.slot, t.photons);
+  }
+  t = ServeTally();
+}
+
+__device__ __forceinline__ void serve_tally(const ServeDev& S, int n_dom, const Photon& ph,
+                                            int out, ServeTally& t) {
+  if (ph.ev != t.slot) {
+    serve_flush(S, t);
+    t.slot = ph.ev;
+  }
+  if (out >= 0) {
+    atomicAdd(S.hits + (size_t)ph.ev * n_dom + out, 1ull);
+  } else if (out == kEscaped) {
+    t.escaped += 1;
+  } else {
+    t.absorbed += 1;
+    if (out == kTruncated) t.truncated += 1;
+  }
+  t.photons += 1;
+  t.steps += ph.n;
+}
+
+// One top-up of the warp's reserve from the request ring: lane 0 claims up to
+// 32 photons of the oldest request with unclaimed photons (one atomic add to
+// its slot's claim word; moving the shared head past a request whose photons
+// are all claimed), all lanes give birth to them and append them to the ring.
+// The photon's event slot is the request's ring slot, so that its tallies go
+// to that request's outputs.  `got` is false when no published request has
+// unclaimed photons.
+__device__ __noinline__ int serve_topup(const IceDev& I, const GeomDev& G, const ServeDev& S,
+                                        const RunDev& R, int rhead, int rcount, bool& got) {
+  constexpr int CAP = kReserveCap;
+  constexpr unsigned long long kOffMask = (1ull << kServeOffsetBits) - 1ull;
+  constexpr unsigned kSeqMask = (1u << kServeSeqBits) - 1u;
+  const unsigned lane = tid_x() & 31;
+  unsigned long long o = 0, tot = 0, src_off = 0, off_off = 0, chunk_off = 0;
+  unsigned n_src = 0, k = 0, ev_lo = 0, slot_req = 0;
+  int ok_claim = 0;
+  if (lane == 0) {
+    for (int tries = 0; tries < 64; ++tries) {
+      const unsigned long long h = ld_relaxed(S.head);
+      if (h >= ld_relaxed(S.tail)) break;  // every published photon is claimed
+      slot_req = (unsigned)(h & (unsigned long long)(S.cap - 1));
+      ServeReq* r = S.req + slot_req;
+      const unsigned long long c = atomicAdd(&r->claimed, 32ull);
+      const unsigned seq_c = (unsigned)(c >> kServeOffsetBits);
+      o = c & kOffMask;
+      // the slot's entry was written by host copies: read it through L2,
+      // after the claim (and the seq after the total: if the slot was
+      // rewritten meanwhile, the seq no longer matches the claim's)
+      __threadfence();
+      tot = __ldcg(&r->total);
+      __threadfence();
+      const unsigned sq = __ldcg(&r->seq) & kSeqMask;
+      if (sq != seq_c) continue;  // a claim on the slot's previous request: nothing taken
+      if (o >= tot) {             // every photon of this request is claimed
+        atomicCAS(S.head, h, h + 1);
+        continue;
+      }
+      src_off = __ldcg(&r->src_off);
+      off_off = __ldcg(&r->off_off);
+      chunk_off = __ldcg(&r->chunk_off);
+      n_src = __ldcg(&r->n_src);
+      k = __ldcg(&r->chunk_log2);
+      ev_lo = __ldcg(&r->event_lo);
+      ok_claim = 1;
+      break;
+    }
+  }
+  got = __shfl_sync(kFull, ok_claim, 0) != 0;
+  if (!got) return rcount;
+  o = __shfl_sync(kFull, o, 0);
+  tot = __shfl_sync(kFull, tot, 0);
+  if (tot - o > 32ull) tot = o + 32ull;  // this claim's photons end here
+  slot_req = __shfl_sync(kFull, slot_req, 0);
+  WorkDev Wv{};
+  Wv.src = S.src + __shfl_sync(kFull, src_off, 0);
+  Wv.off = S.off + __shfl_sync(kFull, off_off, 0);
+  Wv.chunk_src = S.chunk + __shfl_sync(kFull, chunk_off, 0);
+  Wv.aux = nullptr;
+  Wv.n_src = (int)__shfl_sync(kFull, n_src, 0);
+  Wv.single_event_lo = __shfl_sync(kFull, ev_lo, 0);
+  k = __shfl_sync(kFull, k, 0);
+  uint64_t in_src = 0;
+  const int s = locate_claim<true>(Wv, k, o, lane, tot, in_src);
+  const uint64_t g = o + lane;
+  bool ok = false;
+  Photon q;
+  if (g < tot) {
+    identify(Wv, s, in_src, g, q);
+    q.ev = (int)slot_req;
+    // the source record, also through L2 (the arena range may have held
+    // another request's sources)
+    pp_source src;
+    const uint2* sp = reinterpret_cast<const uint2*>(Wv.src + s);
+    uint2* dp = reinterpret_cast<uint2*>(&src);
+#pragma unroll
+    for (int w = 0; w < (int)(sizeof(pp_source) / sizeof(uint2)); ++w) dp[w] = __ldcg(sp + w);
+    ok = birth(q, src, I, R);
+    if (!ok) {  // a malformed source (the host checks them): raise the error, count it done
+      atomicOr(S.err, kErrBadSource);
+      serve_done(S, (int)slot_req, 1);
+    }
+  }
+  const unsigned okm = __ballot_sync(kFull, ok);
+  if (ok) {
+    int slot = rhead + rcount + __popc(okm & lanes_below());
+    if (slot >= CAP) slot -= CAP;
+    ring_put<false>(reserve_ring<false>(I, G), slot, q, s);
+  }
+  return rcount + __popc(okm);
+}
+
+// The serving kernel: the reserve loop of the batched kernel, fed from the
+// request ring.  A warp keeps taking photons while requests are published;
+// once it has nothing in flight and nothing to claim it polls (sleeping a few
+// microseconds between looks) and leaves after idle_ns; it stops claiming
+// max_ns after the launch and leaves once its photons are done.  Every wait is
+// bounded by the global timer; the host relaunches the kernel while published
+// requests are unfinished.
+__global__ void __launch_bounds__(kServeThreads, 1)
+k_serve(const __grid_constant__ IceDev I, const __grid_constant__ GeomDev G,
+        const __grid_constant__ ServeDev S, const __grid_constant__ RunDev R) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Tables T = stage_tables(smem, I, G);
+  __syncthreads();
+  constexpr int CAP = kReserveCap;
+  const uint64_t t0 = __shfl_sync(kFull, global_ns(), 0);
+  uint64_t idle_since = 0;
+  bool alive = false, claiming = true, idle = false;
+  int rhead = 0, rcount = 0;
+  uint32_t crossings = 0, slow = 0;
+  ServeTally st;
+  Photon ph;
+  for (;;) {
+    bool got = false;
+    if (claiming && rcount <= CAP - 32) {
+      __syncwarp();
+      rcount = serve_topup(I, G, S, R, rhead, rcount, got);
+      __syncwarp();
+      const uint64_t now = __shfl_sync(kFull, global_ns(), 0);
+      if (now - t0 > S.max_ns) claiming = false;
+      if (got) idle = false;
+    }
+    const unsigned idle_lanes = __ballot_sync(kFull, !alive);
+    const int n_idle = __popc(idle_lanes);
+    if (rcount > 0 && n_idle > 0 && (n_idle >= R.refill || !got)) {
+      const int n = min(n_idle, rcount);
+      const int rank = __popc(idle_lanes & lanes_below());
+      if (!alive && rank < n) {
+        int slot = rhead + rank;
+        if (slot >= CAP) slot -= CAP;
+        ring_take<false>(reserve_ring<false>(I, G), slot, ph);
+        alive = true;
+      }
+      rhead += n;
+      if (rhead >= CAP) rhead -= CAP;
+      rcount -= n;
+    }
+    // a lane left without a photon hands in its tallies, so that the request
+    // it worked on completes as soon as its last photon is done
+    if (!alive && st.slot >= 0) serve_flush(S, st);
+    if (__ballot_sync(kFull, alive) == 0) {
+      if (rcount > 0) continue;
+      if (!claiming) break;
+      const uint64_t now = __shfl_sync(kFull, global_ns(), 0);
+      if (!idle) {
+        idle = true;
+        idle_since = now;
+      }
+      if (now - idle_since > S.idle_ns) break;
+      __nanosleep(4000);
+      continue;
+    }
+    if (alive) {
+      const int out = photon_step(ph, I, G, T, R, crossings, slow);
+      if (out != kScattered) {
+        serve_tally(S, G.n_dom, ph, out, st);
+        alive = false;
+      }
+    }
+  }
+  serve_flush(S, st);
 }
 
 // ---- debug kernels ---------------------------------------------------------
@@ -664,6 +909,19 @@ cudaError_t launch_propagate(bool persistent, const IceDev& ice, const GeomDev& 
   const uint64_t nb = (n_photons_host + block_threads - 1) / block_threads;
   k_propagate<false, 0><<<(unsigned)nb, block_threads, smem, st>>>(ice, geom, work, run,
                                                                     n_photons_host);
+  return cudaGetLastError();
+}
+
+cudaError_t serve_occupancy(size_t smem, int* blocks_per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_serve, kServeThreads, smem);
+}
+
+cudaError_t launch_serve(const IceDev& ice, const GeomDev& geom, const ServeDev& sv,
+                         const RunDev& run, int grid_blocks, size_t smem, cudaStream_t st) {
+  k_serve<<<grid_blocks, kServeThreads, smem, st>>>(ice, geom, sv, run);
   return cudaGetLastError();
 }
 

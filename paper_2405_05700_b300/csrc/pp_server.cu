@@ -1,22 +1,35 @@
-// Serving loop: many host client threads submit photon bunches; one scheduler
-// thread admits them under a fixed budget and runs them in continuous batches.
+// Serving loop: many host client threads submit photon bunches; the bunches
+// are admitted into a request ring in device memory, and a persistent serving
+// kernel pulls photons from the ring while requests keep arriving.
 //
 // Paper Sec. 4: the propagation clients queue photon-emitting steps and send
 // them, in blocks, to a photon server that aggregates steps from many events
 // and clients to keep the GPU busy; several client instances share one server
 // and one memory budget.  Here:
-//   * pp_submit copies a bunch's sources and queues it (thread-safe);
-//   * the scheduler forms a batch from queued bunches, in arrival order, as
-//     soon as a batch slot is free and the admission budget allows, so bunches
-//     that arrive while others run join the next batch (continuous batching);
-//   * each slot owns its device buffers, pinned staging and stream; with
-//     several slots in flight, one batch's kernels start while the previous
-//     batch's are still finishing;
-//   * completion is signalled by a host function queued on the slot's stream
-//     (it only posts the slot to the scheduler; no CUDA call inside);
-//   * pp_collect waits (bounded) for one bunch's result.
-// Results depend only on (seed, event id, sources): a bunch's result is the
-// same alone and in any mix.
+//   * pp_submit (any client thread) checks a bunch, computes its photon prefix
+//     and photon-chunk table on the host, and queues it for admission;
+//   * the scheduler thread admits queued bunches in arrival order while a
+//     ring slot, arena space and the budget allow: it copies the sources,
+//     prefix and chunk table into device arenas, clears the slot's outputs,
+//     writes the ring entry and finally the ring's tail (the doorbell), all as
+//     copies on one stream, so the device sees a request only once its data is
+//     in place;
+//   * the serving kernel (k_serve) claims up to 32 photons at a time from the
+//     oldest request with unclaimed photons (an atomic add to its ring
+//     slot's claim word), runs them with the batched
+//     kernel's per-warp photon reserve, tallies them into the request's
+//     outputs and raises the request's host-mapped done flag when its last
+//     photon is tallied.  Requests that arrive while it runs are taken by the
+//     running kernel (continuous batching on the device); it leaves when idle,
+//     or after a time limit, and the scheduler relaunches it while published
+//     requests are unfinished;
+//   * the scheduler copies a finished request's outputs back and wakes its
+//     collector.
+// Admission charges the device bytes a request actually occupies while
+// admitted (its sources, prefix and chunk table in the arenas, its output
+// slot and ring entry): photon state lives in registers and in shared memory,
+// never in device memory.  Results depend only on (seed, event id, sources):
+// a bunch's result is the same alone and in any mix.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -25,6 +38,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -39,40 +53,65 @@ using Clock = std::chrono::steady_clock;
 
 namespace {
 
+constexpr int kQueued = 1, kPublished = 2, kCopying = 3;
+
 struct Request {
-  uint64_t ticket = 0, event_id = 0, n_photons = 0, cost = 0;
+  uint64_t ticket = 0, event_id = 0, n_photons = 0, bytes = 0;
   std::vector<pp_source> src;
+  std::vector<uint64_t> off;     // photon prefix over the sources (n_src + 1)
+  std::vector<uint32_t> chunk;   // photon-chunk -> first source (n_chunks + 1)
+  uint32_t chunk_log2 = 0;
   Clock::time_point t_submit, t_done;
-  int status = 1;  // 1 pending, 0 done, < 0 error
+  int status = kQueued;          // kQueued, kPublished, kCopying, 0 done, < 0 error
+  uint64_t seq = 0;
+  int slot = -1;
+  uint64_t src_at = 0, off_at = 0, chunk_at = 0;
   std::vector<uint64_t> hits;
   uint64_t counts[4] = {0, 0, 0, 0};
 };
 
-struct Slot {
-  cudaStream_t stream = nullptr;
-  bool busy = false;
-  // device
-  pp_source* d_src = nullptr;
-  int64_t* d_begin = nullptr;
-  uint64_t* d_ids = nullptr;
-  uint64_t* d_hits = nullptr;
-  uint64_t* d_counts = nullptr;
-  uint64_t* d_off = nullptr;
-  uint32_t* d_chunk = nullptr;
-  ppk::SrcAux* d_aux = nullptr;
-  uint64_t* d_bsum = nullptr;
-  uint64_t* d_meta = nullptr;
-  unsigned long long* d_work = nullptr;
-  int* d_err = nullptr;
-  // pinned host
-  pp_source* h_src = nullptr;
-  int64_t* h_begin = nullptr;
-  uint64_t* h_ids = nullptr;
-  uint64_t* h_hits = nullptr;
-  uint64_t* h_counts = nullptr;
-  int* h_err = nullptr;
-  std::vector<Request*> reqs;
-  uint64_t cost = 0;
+// First-fit allocator of ranges [0, cap) with coalescing of freed ranges.
+class RangeAlloc {
+ public:
+  void reset(uint64_t cap) {
+    free_.clear();
+    if (cap) free_[0] = cap;
+  }
+  bool take(uint64_t n, uint64_t* at) {
+    if (n == 0) {
+      *at = 0;
+      return true;
+    }
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= n) {
+        *at = it->first;
+        const uint64_t rest = it->second - n, start = it->first + n;
+        free_.erase(it);
+        if (rest) free_[start] = rest;
+        return true;
+      }
+    }
+    return false;
+  }
+  void give(uint64_t at, uint64_t n) {
+    if (n == 0) return;
+    auto next = free_.lower_bound(at);
+    if (next != free_.end() && at + n == next->first) {
+      n += next->second;
+      next = free_.erase(next);
+    }
+    if (next != free_.begin()) {
+      auto prev = std::prev(next);
+      if (prev->first + prev->second == at) {
+        prev->second += n;
+        return;
+      }
+    }
+    free_[at] = n;
+  }
+
+ private:
+  std::map<uint64_t, uint64_t> free_;
 };
 
 }  // namespace
@@ -81,45 +120,57 @@ struct pp_server {
   pp_ctx* ctx = nullptr;
   ppk::LaunchView view{};
   pp_server_config cfg{};
-  std::vector<Slot> slots;
+  int cap = 0;                 // ring slots (a power of two)
+  int grid = 0;                // serving kernel blocks
+  size_t smem = 0;
+  // device
+  ppk::ServeReq* d_req = nullptr;
+  unsigned long long* d_tail = nullptr;
+  unsigned long long* d_head = nullptr;
+  pp_source* d_src = nullptr;
+  uint64_t* d_off = nullptr;
+  uint32_t* d_chunk = nullptr;
+  uint64_t* d_hits = nullptr;
+  uint64_t* d_counts = nullptr;
+  int* d_err = nullptr;
+  uint64_t device_bytes = 0;
+  // pinned host: staging mirrors of the arenas and the ring, result landing
+  // areas, the host-mapped done flags
+  pp_source* h_src = nullptr;
+  uint64_t* h_off = nullptr;
+  uint32_t* h_chunk = nullptr;
+  ppk::ServeReq* h_req = nullptr;
+  unsigned long long* h_tail = nullptr;  // [cap]: the tail value each publication writes
+  unsigned long long* h_arm = nullptr;   // [cap]: the claim word that arms each slot
+  uint64_t* h_zero = nullptr;            // n_dom + 4 zeros
+  uint64_t* h_hits = nullptr;
+  uint64_t* h_counts = nullptr;
+  int* h_err = nullptr;                  // [cap]
+  volatile uint32_t* h_flag = nullptr;   // [cap], device-mapped
+  uint32_t* d_flag = nullptr;            // its device address
+  cudaStream_t s_pub = nullptr, s_down = nullptr, s_kern = nullptr;
+  cudaEvent_t kern_done = nullptr;
+  std::vector<cudaEvent_t> copied;       // [cap]
+  bool kernel_running = false;
+  // host state
   std::mutex mu;
   std::condition_variable cv_sched, cv_done;
   std::deque<Request*> pending;
+  std::vector<Request*> by_slot;         // [cap]: the admitted request in each slot
   std::unordered_map<uint64_t, Request*> by_ticket;
-  std::deque<int> completed;
-  uint64_t next_ticket = 1, in_flight_cost = 0, queued_cost = 0;
-  bool stop = false;
+  RangeAlloc a_src, a_off, a_chunk;
+  uint64_t next_ticket = 1, next_seq = 0, admitted_bytes = 0, published = 0;
+  bool stop = false, broken = false;
   std::thread sched;
   std::string last_error = "no error";
   // statistics
   std::vector<double> latency_ms;
-  uint64_t done_requests = 0, done_photons = 0, batches = 0, batch_requests = 0;
-  uint64_t peak_cost = 0;
+  uint64_t done_requests = 0, done_photons = 0, launches = 0, peak_bytes = 0;
   Clock::time_point t_first_submit, t_last_done;
   bool any_submit = false;
 };
 
 namespace {
-
-struct HostFnArg {
-  pp_server* s;
-  int slot;
-};
-
-void CUDART_CB on_slot_done(void* p) {
-  HostFnArg* a = static_cast<HostFnArg*>(p);
-  {
-    std::lock_guard<std::mutex> lk(a->s->mu);
-    a->s->completed.push_back(a->slot);
-  }
-  a->s->cv_sched.notify_all();
-  delete a;
-}
-
-uint64_t request_cost(const pp_server* s, uint64_t n_photons, int64_t n_src) {
-  return n_photons * s->cfg.photon_state_bytes + (uint64_t)n_src * 68ull +
-         (uint64_t)s->view.geom.n_dom * 8ull + 64ull;
-}
 
 bool source_ok(const pp_source& s) {
   return std::isfinite(s.x) && std::isfinite(s.y) && std::isfinite(s.z) && std::isfinite(s.dx) &&
@@ -127,223 +178,370 @@ bool source_ok(const pp_source& s) {
          (s.dx != 0.f || s.dy != 0.f || s.dz != 0.f) && s.type <= PP_SRC_CASCADE;
 }
 
-void free_slot(Slot& sl) {
-  cudaFree(sl.d_src);
-  cudaFree(sl.d_begin);
-  cudaFree(sl.d_ids);
-  cudaFree(sl.d_hits);
-  cudaFree(sl.d_counts);
-  cudaFree(sl.d_off);
-  cudaFree(sl.d_chunk);
-  cudaFree(sl.d_aux);
-  cudaFree(sl.d_bsum);
-  cudaFree(sl.d_meta);
-  cudaFree(sl.d_work);
-  cudaFree(sl.d_err);
-  cudaFreeHost(sl.h_src);
-  cudaFreeHost(sl.h_begin);
-  cudaFreeHost(sl.h_ids);
-  cudaFreeHost(sl.h_hits);
-  cudaFreeHost(sl.h_counts);
-  cudaFreeHost(sl.h_err);
-  if (sl.stream) cudaStreamDestroy(sl.stream);
-  sl = Slot();
+// a1 for one request, on the host: the exclusive photon prefix over its
+// sources and the table of 2^k-photon chunks (k the smallest with at most
+// n_src + 1 chunks) -> the last source starting at or before the chunk's
+// first photon, as the device expansion builds them for a batch.
+void expand_on_host(Request* r) {
+  const size_t n = r->src.size();
+  r->off.resize(n + 1);
+  uint64_t acc = 0;
+  for (size_t i = 0; i < n; ++i) {
+    r->off[i] = acc;
+    acc += r->src[i].n_photons;
+  }
+  r->off[n] = acc;
+  r->n_photons = acc;
+  uint32_t k = 0;
+  const uint64_t cap = std::max<uint64_t>(n, 1);
+  while ((acc >> k) > cap) ++k;
+  r->chunk_log2 = k;
+  const uint64_t n_chunks = (acc + (1ull << k) - 1) >> k;
+  r->chunk.resize(n_chunks + 1);
+  size_t s = 0;
+  for (uint64_t c = 0; c <= n_chunks; ++c) {
+    const uint64_t g = c << k;
+    while (s + 1 < n && r->off[s + 1] <= g) ++s;
+    r->chunk[c] = (uint32_t)s;
+  }
 }
 
-cudaError_t alloc_slot(Slot& sl, int64_t max_src, int max_req, int n_dom) {
-  const int64_t nb = (max_src + ppk::kScanTile - 1) / ppk::kScanTile;
-  const size_t hits = sizeof(uint64_t) * (size_t)max_req * std::max(n_dom, 1);
-  cudaError_t e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
-#define PP_SLOT(x) \
-  if (e == cudaSuccess) e = (x)
-  PP_SLOT(cudaMalloc(&sl.d_src, sizeof(pp_source) * max_src));
-  PP_SLOT(cudaMalloc(&sl.d_begin, sizeof(int64_t) * (max_req + 1)));
-  PP_SLOT(cudaMalloc(&sl.d_ids, sizeof(uint64_t) * max_req));
-  PP_SLOT(cudaMalloc(&sl.d_hits, hits));
-  PP_SLOT(cudaMalloc(&sl.d_counts, sizeof(uint64_t) * 4 * max_req));
-  PP_SLOT(cudaMalloc(&sl.d_off, sizeof(uint64_t) * (max_src + 1)));
-  PP_SLOT(cudaMalloc(&sl.d_chunk, sizeof(uint32_t) * (max_src + 2)));
-  PP_SLOT(cudaMalloc(&sl.d_aux, sizeof(ppk::SrcAux) * max_src));
-  PP_SLOT(cudaMalloc(&sl.d_bsum, sizeof(uint64_t) * std::max<int64_t>(nb, 1)));
-  PP_SLOT(cudaMalloc(&sl.d_meta, 256));
-  PP_SLOT(cudaMalloc(&sl.d_work, 256));
-  PP_SLOT(cudaMalloc(&sl.d_err, 256));
-  PP_SLOT(cudaMallocHost(&sl.h_src, sizeof(pp_source) * max_src));
-  PP_SLOT(cudaMallocHost(&sl.h_begin, sizeof(int64_t) * (max_req + 1)));
-  PP_SLOT(cudaMallocHost(&sl.h_ids, sizeof(uint64_t) * max_req));
-  PP_SLOT(cudaMallocHost(&sl.h_hits, hits));
-  PP_SLOT(cudaMallocHost(&sl.h_counts, sizeof(uint64_t) * 4 * max_req));
-  PP_SLOT(cudaMallocHost(&sl.h_err, sizeof(int)));
-#undef PP_SLOT
-  if (e == cudaSuccess) e = cudaMemset(sl.d_err, 0, 256);
+// Device bytes a request occupies while admitted: its sources, prefix and
+// chunk table in the arenas, its output slot and its ring entry.
+uint64_t request_bytes(const pp_server* s, const Request* r) {
+  return sizeof(pp_source) * r->src.size() + sizeof(uint64_t) * r->off.size() +
+         sizeof(uint32_t) * r->chunk.size() +
+         sizeof(uint64_t) * ((uint64_t)s->view.geom.n_dom + 4) + sizeof(ppk::ServeReq);
+}
+
+void free_server_memory(pp_server* s) {
+  void* dev[] = {s->d_req, s->d_tail, s->d_head, s->d_src, s->d_off, s->d_chunk,
+                 s->d_hits, s->d_counts, s->d_err};
+  for (void* p : dev) cudaFree(p);
+  void* host[] = {s->h_src, s->h_off, s->h_chunk, s->h_req, s->h_tail, s->h_arm, s->h_zero,
+                  s->h_hits, s->h_counts, s->h_err, (void*)s->h_flag};
+  for (void* p : host) cudaFreeHost(p);
+  for (cudaEvent_t e : s->copied) cudaEventDestroy(e);
+  if (s->kern_done) cudaEventDestroy(s->kern_done);
+  if (s->s_pub) cudaStreamDestroy(s->s_pub);
+  if (s->s_down) cudaStreamDestroy(s->s_down);
+  if (s->s_kern) cudaStreamDestroy(s->s_kern);
+}
+
+template <class T>
+cudaError_t dev_alloc(pp_server* s, T** p, size_t n) {
+  const size_t b = sizeof(T) * std::max<size_t>(n, 1);
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), b);
+  if (e == cudaSuccess) s->device_bytes += b;
   return e;
 }
 
-// Stages a formed batch into the slot and enqueues copies, kernels and the
-// completion host function on its stream.  Runs without the server lock (the
-// slot and its requests belong to this thread until completion).
-cudaError_t launch_slot(pp_server* s, int si) {
-  Slot& sl = s->slots[si];
-  const int n = (int)sl.reqs.size();
-  int64_t n_src = 0;
-  sl.h_begin[0] = 0;
-  for (int i = 0; i < n; ++i) {
-    Request* r = sl.reqs[i];
-    std::memcpy(sl.h_src + n_src, r->src.data(), sizeof(pp_source) * r->src.size());
-    n_src += (int64_t)r->src.size();
-    sl.h_begin[i + 1] = n_src;
-    sl.h_ids[i] = r->event_id;
+cudaError_t alloc_server_memory(pp_server* s) {
+  const size_t S = (size_t)s->cfg.arena_sources, R = (size_t)s->cap;
+  const size_t n_dom = (size_t)std::max(s->view.geom.n_dom, 1);
+  cudaError_t e = cudaSuccess;
+#define PP_A(x) \
+  if (e == cudaSuccess) e = (x)
+  PP_A(dev_alloc(s, &s->d_req, R));
+  PP_A(dev_alloc(s, &s->d_tail, 1));
+  PP_A(dev_alloc(s, &s->d_head, 1));
+  PP_A(dev_alloc(s, &s->d_src, S));
+  PP_A(dev_alloc(s, &s->d_off, S + R));
+  PP_A(dev_alloc(s, &s->d_chunk, S + 2 * R));
+  PP_A(dev_alloc(s, &s->d_hits, R * n_dom));
+  PP_A(dev_alloc(s, &s->d_counts, R * 4));
+  PP_A(dev_alloc(s, &s->d_err, 1));
+  PP_A(cudaMallocHost(&s->h_src, sizeof(pp_source) * std::max<size_t>(S, 1)));
+  PP_A(cudaMallocHost(&s->h_off, sizeof(uint64_t) * (S + R)));
+  PP_A(cudaMallocHost(&s->h_chunk, sizeof(uint32_t) * (S + 2 * R)));
+  PP_A(cudaMallocHost(&s->h_req, sizeof(ppk::ServeReq) * R));
+  PP_A(cudaMallocHost(&s->h_tail, sizeof(unsigned long long) * R));
+  PP_A(cudaMallocHost(&s->h_arm, sizeof(unsigned long long) * R));
+  PP_A(cudaMallocHost(&s->h_zero, sizeof(uint64_t) * (n_dom + 4)));
+  PP_A(cudaMallocHost(&s->h_hits, sizeof(uint64_t) * R * n_dom));
+  PP_A(cudaMallocHost(&s->h_counts, sizeof(uint64_t) * R * 4));
+  PP_A(cudaMallocHost(&s->h_err, sizeof(int) * R));
+  void* flag = nullptr;
+  PP_A(cudaHostAlloc(&flag, sizeof(uint32_t) * R, cudaHostAllocMapped));
+  if (e == cudaSuccess) {
+    s->h_flag = static_cast<volatile uint32_t*>(flag);
+    e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->d_flag), flag, 0);
   }
+  PP_A(cudaStreamCreateWithFlags(&s->s_pub, cudaStreamNonBlocking));
+  PP_A(cudaStreamCreateWithFlags(&s->s_down, cudaStreamNonBlocking));
+  PP_A(cudaStreamCreateWithFlags(&s->s_kern, cudaStreamNonBlocking));
+  PP_A(cudaEventCreateWithFlags(&s->kern_done, cudaEventDisableTiming));
+  s->copied.assign(R, nullptr);
+  for (size_t i = 0; i < R && e == cudaSuccess; ++i)
+    e = cudaEventCreateWithFlags(&s->copied[i], cudaEventDisableTiming);
+#undef PP_A
+  if (e != cudaSuccess) return e;
+  std::memset(s->h_zero, 0, sizeof(uint64_t) * (n_dom + 4));
+  for (size_t i = 0; i < R; ++i) s->h_flag[i] = 0;
+  // the ring starts empty (tail and head 0) with every slot disarmed (a
+  // claim word whose request number matches no slot's seq), no error
+  ppk::ServeReq* init = s->h_req;
+  for (size_t i = 0; i < R; ++i) {
+    std::memset(&init[i], 0, sizeof(ppk::ServeReq));
+    init[i].claimed = (((1ull << ppk::kServeSeqBits) - 1) << ppk::kServeOffsetBits) |
+                      ppk::kServeMaxPhotons;
+    init[i].seq = ~0u;
+  }
+  e = cudaMemcpyAsync(s->d_req, init, sizeof(ppk::ServeReq) * R, cudaMemcpyHostToDevice, s->s_pub);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_tail, 0, sizeof(unsigned long long), s->s_pub);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_head, 0, sizeof(unsigned long long), s->s_pub);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_err, 0, sizeof(int), s->s_pub);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->s_pub);
+  s->a_src.reset(S);
+  s->a_off.reset(S + R);
+  s->a_chunk.reset(S + 2 * R);
+  return e;
+}
+
+// Admits the oldest queued request if a ring slot, arena space and the budget
+// allow (server lock held).  Its data go to the device as copies on the
+// publication stream, the ring entry and the tail last.  Returns false when
+// the request has to wait.
+bool admit_front(pp_server* s) {
+  Request* r = s->pending.front();
+  const int slot = (int)(s->next_seq & (uint64_t)(s->cap - 1));
+  if (s->by_slot[slot]) return false;  // the slot's previous request is not collected back yet
+  if (s->admitted_bytes + r->bytes > s->cfg.budget_bytes) return false;
+  uint64_t a = 0, b = 0, c = 0;
+  if (!s->a_src.take(r->src.size(), &a)) return false;
+  if (!s->a_off.take(r->off.size(), &b)) {
+    s->a_src.give(a, r->src.size());
+    return false;
+  }
+  if (!s->a_chunk.take(r->chunk.size(), &c)) {
+    s->a_src.give(a, r->src.size());
+    s->a_off.give(b, r->off.size());
+    return false;
+  }
+  s->pending.pop_front();
+  r->src_at = a;
+  r->off_at = b;
+  r->chunk_at = c;
+  r->slot = slot;
+  r->seq = s->next_seq++;
+  s->by_slot[slot] = r;
+  s->admitted_bytes += r->bytes;
+  s->peak_bytes = std::max(s->peak_bytes, s->admitted_bytes);
   const int n_dom = s->view.geom.n_dom;
-  cudaStream_t st = sl.stream;
-  cudaError_t e = cudaMemsetAsync(sl.d_err, 0, sizeof(int), st);
+  // stage into the pinned mirrors (the ranges are this request's alone)
+  std::memcpy(s->h_src + a, r->src.data(), sizeof(pp_source) * r->src.size());
+  std::memcpy(s->h_off + b, r->off.data(), sizeof(uint64_t) * r->off.size());
+  std::memcpy(s->h_chunk + c, r->chunk.data(), sizeof(uint32_t) * r->chunk.size());
+  ppk::ServeReq& q = s->h_req[slot];
+  q.claimed = 0;  // not copied: the arming copy below writes it
+  q.done = 0;
+  q.total = r->n_photons;
+  q.src_off = a;
+  q.off_off = b;
+  q.chunk_off = c;
+  q.n_src = (uint32_t)r->src.size();
+  q.chunk_log2 = r->chunk_log2;
+  q.event_lo = (uint32_t)r->event_id;
+  q.seq = (uint32_t)r->seq;
+  s->h_arm[slot] = (r->seq & ((1ull << ppk::kServeSeqBits) - 1)) << ppk::kServeOffsetBits;
+  s->h_tail[slot] = r->seq + 1;
+  s->h_flag[slot] = 0;
+  cudaStream_t st = s->s_pub;
+  cudaError_t e = cudaMemcpyAsync(s->d_src + a, s->h_src + a, sizeof(pp_source) * r->src.size(),
+                                  cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(sl.d_src, sl.h_src, sizeof(pp_source) * n_src, cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(s->d_off + b, s->h_off + b, sizeof(uint64_t) * r->off.size(),
+                        cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(sl.d_begin, sl.h_begin, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(sl.d_ids, sl.h_ids, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(s->d_chunk + c, s->h_chunk + c, sizeof(uint32_t) * r->chunk.size(),
+                        cudaMemcpyHostToDevice, st);
+  // outputs cleared by copies of zeros (copy engine, no kernel: the serving
+  // kernel may be holding every SM)
   if (e == cudaSuccess && n_dom)
-    e = cudaMemsetAsync(sl.d_hits, 0, sizeof(uint64_t) * (size_t)n * n_dom, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(sl.d_counts, 0, sizeof(uint64_t) * 4 * n, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(sl.d_work, 0, sizeof(uint64_t), st);
-  if (e == cudaSuccess && n_src > 0) {
-    ppk::ExpandBufs b;
-    b.off = sl.d_off;
-    b.chunk_src = sl.d_chunk;
-    b.aux = sl.d_aux;
-    b.bsum = sl.d_bsum;
-    b.meta = sl.d_meta;
-    e = ppk::launch_expand(sl.d_src, n_src, sl.d_begin, sl.d_ids, n, b, st);
-    if (e == cudaSuccess) {
-      ppk::WorkDev w{};
-      w.src = sl.d_src;
-      w.off = sl.d_off;
-      w.chunk_src = sl.d_chunk;
-      w.aux = sl.d_aux;
-      w.meta = sl.d_meta;
-      w.work = sl.d_work;
-      w.hits = reinterpret_cast<unsigned long long*>(sl.d_hits);
-      w.counts = reinterpret_cast<unsigned long long*>(sl.d_counts);
-      w.err = sl.d_err;
-      w.stats = nullptr;
-      w.n_src = (int)n_src;
-      w.single_event_lo = 0;
-      w.g_begin = 0;
-      w.g_end = ~0ull;
-      ppk::NvtxRange range("pp.server_batch");
-      e = ppk::launch_propagate(true, s->view.ice, s->view.geom, w, s->view.run,
-                                s->view.block_threads, s->view.grid_blocks, 0, s->view.smem, st,
-                                s->view.variant);
+    e = cudaMemcpyAsync(s->d_hits + (size_t)slot * n_dom, s->h_zero, sizeof(uint64_t) * n_dom,
+                        cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->d_counts + (size_t)slot * 4, s->h_zero, sizeof(uint64_t) * 4,
+                        cudaMemcpyHostToDevice, st);
+  // the entry without its claim word, then the claim word (arming the slot
+  // only once the rest is in place: a warp still adding to the slot's
+  // previous claim word finds the new seq and takes nothing)
+  constexpr size_t kWord = sizeof(unsigned long long);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(reinterpret_cast<char*>(s->d_req + slot) + kWord,
+                        reinterpret_cast<const char*>(&q) + kWord,
+                        sizeof(ppk::ServeReq) - kWord, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&s->d_req[slot].claimed, s->h_arm + slot, kWord, cudaMemcpyHostToDevice,
+                        st);
+  // the doorbell: requests are published in order, so the tail only grows
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->d_tail, s->h_tail + slot, sizeof(unsigned long long),
+                        cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) {
+    // a publication cut short would leave a hole in the ring's order: the
+    // server stops taking work and fails what it holds
+    s->last_error = std::string("publication: ") + cudaGetErrorString(e);
+    s->broken = true;
+    r->status = PP_ECUDA;
+    return true;
+  }
+  r->status = kPublished;
+  s->published += 1;
+  return true;
+}
+
+// Releases a finished request's slot, arena ranges and budget (lock held).
+void release(pp_server* s, Request* r) {
+  s->a_src.give(r->src_at, r->src.size());
+  s->a_off.give(r->off_at, r->off.size());
+  s->a_chunk.give(r->chunk_at, r->chunk.size());
+  s->admitted_bytes -= r->bytes;
+  s->by_slot[r->slot] = nullptr;
+  r->src.clear();
+  r->src.shrink_to_fit();
+  r->off.clear();
+  r->off.shrink_to_fit();
+  r->chunk.clear();
+  r->chunk.shrink_to_fit();
+}
+
+// One pass over the admitted requests (lock held): a raised done flag starts
+// the copy of the request's outputs; a finished copy completes the request.
+// Returns true when a request completed.
+bool poll_admitted(pp_server* s) {
+  const int n_dom = s->view.geom.n_dom;
+  bool any = false;
+  for (int slot = 0; slot < s->cap; ++slot) {
+    Request* r = s->by_slot[slot];
+    if (!r) continue;
+    if (r->status == kPublished && s->h_flag[slot] == (uint32_t)(r->seq + 1)) {
+      cudaStream_t st = s->s_down;
+      cudaError_t e = cudaSuccess;
+      if (n_dom)
+        e = cudaMemcpyAsync(s->h_hits + (size_t)slot * n_dom, s->d_hits + (size_t)slot * n_dom,
+                            sizeof(uint64_t) * n_dom, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->h_counts + (size_t)slot * 4, s->d_counts + (size_t)slot * 4,
+                            sizeof(uint64_t) * 4, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->h_err + slot, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaEventRecord(s->copied[slot], st);
+      if (e != cudaSuccess) {
+        s->last_error = std::string("result copy: ") + cudaGetErrorString(e);
+        r->status = PP_ECUDA;
+      } else {
+        r->status = kCopying;
+        continue;
+      }
+    }
+    if (r->status == kCopying) {
+      const cudaError_t q = cudaEventQuery(s->copied[slot]);
+      if (q == cudaErrorNotReady) continue;
+      if (q != cudaSuccess) {
+        s->last_error = std::string("result copy: ") + cudaGetErrorString(q);
+        r->status = PP_ECUDA;
+      } else {
+        r->hits.assign(s->h_hits + (size_t)slot * n_dom, s->h_hits + (size_t)(slot + 1) * n_dom);
+        std::memcpy(r->counts, s->h_counts + (size_t)slot * 4, sizeof(r->counts));
+        r->status = s->h_err[slot] ? PP_EDEVICE : PP_OK;
+      }
+    }
+    if (r->status == kPublished && s->broken) r->status = PP_ECUDA;
+    if (r->status <= 0) {  // done or failed
+      r->t_done = Clock::now();
+      if (r->status == PP_OK) {
+        s->latency_ms.push_back(
+            std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
+        s->done_requests += 1;
+        s->done_photons += r->n_photons;
+        s->t_last_done = r->t_done;
+      }
+      release(s, r);
+      any = true;
     }
   }
-  if (e == cudaSuccess && n_dom)
-    e = cudaMemcpyAsync(sl.h_hits, sl.d_hits, sizeof(uint64_t) * (size_t)n * n_dom,
-                        cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(sl.h_counts, sl.d_counts, sizeof(uint64_t) * 4 * n, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(sl.h_err, sl.d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaLaunchHostFunc(st, on_slot_done, new HostFnArg{s, si});
+  return any;
+}
+
+bool unfinished_published(const pp_server* s) {
+  for (int slot = 0; slot < s->cap; ++slot) {
+    const Request* r = s->by_slot[slot];
+    if (r && r->status == kPublished) return true;
+  }
+  return false;
+}
+
+cudaError_t launch_kernel(pp_server* s) {
+  ppk::ServeDev sv{};
+  sv.req = s->d_req;
+  sv.cap = s->cap;
+  sv.tail = s->d_tail;
+  sv.head = s->d_head;
+  sv.src = s->d_src;
+  sv.off = s->d_off;
+  sv.chunk = s->d_chunk;
+  sv.hits = reinterpret_cast<unsigned long long*>(s->d_hits);
+  sv.counts = reinterpret_cast<unsigned long long*>(s->d_counts);
+  sv.done_flag = s->d_flag;
+  sv.err = s->d_err;
+  sv.idle_ns = (uint64_t)s->cfg.idle_exit_us * 1000ull;
+  sv.max_ns = (uint64_t)s->cfg.max_launch_ms * 1000000ull;
+  ppk::NvtxRange range("pp.server_kernel");
+  cudaError_t e = ppk::launch_serve(s->view.ice, s->view.geom, sv, s->view.run, s->grid, s->smem,
+                                    s->s_kern);
+  if (e == cudaSuccess) e = cudaEventRecord(s->kern_done, s->s_kern);
+  if (e == cudaSuccess) {
+    s->kernel_running = true;
+    s->launches += 1;
+  }
   return e;
-}
-
-// Results of a completed slot into its requests (server lock held).
-void finalize_slot(pp_server* s, int si) {
-  Slot& sl = s->slots[si];
-  const int n_dom = s->view.geom.n_dom;
-  const int err = *sl.h_err;
-  const Clock::time_point now = Clock::now();
-  for (size_t i = 0; i < sl.reqs.size(); ++i) {
-    Request* r = sl.reqs[i];
-    r->hits.assign(sl.h_hits + i * n_dom, sl.h_hits + (i + 1) * n_dom);
-    std::memcpy(r->counts, sl.h_counts + 4 * i, sizeof(r->counts));
-    r->status = err ? PP_EDEVICE : PP_OK;
-    r->t_done = now;
-    s->latency_ms.push_back(std::chrono::duration<double, std::milli>(now - r->t_submit).count());
-    s->done_requests += 1;
-    s->done_photons += r->n_photons;
-    r->src.clear();
-    r->src.shrink_to_fit();
-  }
-  s->t_last_done = now;
-  s->in_flight_cost -= sl.cost;
-  sl.cost = 0;
-  sl.reqs.clear();
-  sl.busy = false;
-}
-
-void fail_slot(pp_server* s, int si, int code) {
-  Slot& sl = s->slots[si];
-  for (Request* r : sl.reqs) {
-    r->status = code;
-    r->t_done = Clock::now();
-  }
-  s->in_flight_cost -= sl.cost;
-  sl.cost = 0;
-  sl.reqs.clear();
-  sl.busy = false;
 }
 
 void scheduler(pp_server* s) {
-  cudaSetDevice(s->view.device);
+  cudaSetDevice(s->view.device);  // this library-owned thread works on the server's device
   std::unique_lock<std::mutex> lk(s->mu);
   for (;;) {
-    auto can_launch = [&]() {
-      if (s->pending.empty()) return false;
-      for (const Slot& sl : s->slots)
-        if (!sl.busy) return s->in_flight_cost + s->pending.front()->cost <= s->cfg.budget_bytes;
-      return false;
-    };
-    auto drained = [&]() {
-      if (!s->stop || !s->pending.empty()) return false;
-      for (const Slot& sl : s->slots)
-        if (sl.busy) return false;
-      return true;
-    };
-    s->cv_sched.wait(lk, [&]() { return !s->completed.empty() || can_launch() || drained(); });
-    bool any_done = false;
-    while (!s->completed.empty()) {
-      const int si = s->completed.front();
-      s->completed.pop_front();
-      finalize_slot(s, si);
-      any_done = true;
-    }
-    if (any_done) s->cv_done.notify_all();
-    if (drained()) break;
-    // launch into every free slot while queued work fits the budget
-    for (int si = 0; si < (int)s->slots.size(); ++si) {
-      Slot& sl = s->slots[si];
-      if (sl.busy || s->pending.empty()) continue;
-      int64_t n_src = 0;
+    bool woke = false;
+    if (poll_admitted(s)) woke = true;
+    if (s->broken) {
       while (!s->pending.empty()) {
-        Request* r = s->pending.front();
-        if ((int)sl.reqs.size() >= s->cfg.max_batch_requests) break;
-        if (n_src + (int64_t)r->src.size() > s->cfg.max_batch_sources) break;
-        if (s->in_flight_cost + sl.cost + r->cost > s->cfg.budget_bytes) break;
+        s->pending.front()->status = PP_ECUDA;
         s->pending.pop_front();
-        s->queued_cost -= r->cost;
-        sl.reqs.push_back(r);
-        sl.cost += r->cost;
-        n_src += (int64_t)r->src.size();
-      }
-      if (sl.reqs.empty()) break;  // the budget is full: wait for a completion
-      sl.busy = true;
-      s->in_flight_cost += sl.cost;
-      s->peak_cost = std::max(s->peak_cost, s->in_flight_cost);
-      s->batches += 1;
-      s->batch_requests += sl.reqs.size();
-      lk.unlock();
-      const cudaError_t e = launch_slot(s, si);
-      lk.lock();
-      if (e != cudaSuccess) {
-        s->last_error = std::string("batch launch: ") + cudaGetErrorString(e);
-        fail_slot(s, si, PP_ECUDA);
-        s->cv_done.notify_all();
+        woke = true;
       }
     }
+    while (!s->broken && !s->pending.empty() && admit_front(s)) {
+    }
+    if (s->kernel_running) {
+      const cudaError_t q = cudaEventQuery(s->kern_done);
+      if (q != cudaErrorNotReady) {
+        s->kernel_running = false;
+        if (q != cudaSuccess) {
+          s->last_error = std::string("serving kernel: ") + cudaGetErrorString(q);
+          s->broken = true;
+        }
+      }
+    }
+    if (!s->kernel_running && !s->broken && unfinished_published(s)) {
+      const cudaError_t e = launch_kernel(s);
+      if (e != cudaSuccess) {
+        s->last_error = std::string("serving kernel launch: ") + cudaGetErrorString(e);
+        s->broken = true;
+      }
+    }
+    if (woke) s->cv_done.notify_all();
+    bool holding = s->kernel_running || !s->pending.empty();
+    for (int slot = 0; slot < s->cap && !holding; ++slot) holding = s->by_slot[slot] != nullptr;
+    if (s->stop && !holding) break;
+    // while work is in flight, look again after a short wait (the device
+    // raises done flags in host memory; nothing signals this thread); else
+    // sleep until a submission or the stop
+    if (holding)
+      s->cv_sched.wait_for(lk, std::chrono::microseconds(40));
+    else
+      s->cv_sched.wait(lk, [&]() { return s->stop || !s->pending.empty(); });
   }
-  // fail anything left (only reachable on stop with nothing pending)
   s->cv_done.notify_all();
 }
 
@@ -355,23 +553,25 @@ int pp_server_config_default(pp_server_config* cfg) {
   if (!cfg) return PP_EINVAL;
   std::memset(cfg, 0, sizeof(*cfg));
   cfg->budget_bytes = 8ull << 30;
-  cfg->photon_state_bytes = 32;
-  cfg->slots = 3;
-  cfg->max_batch_requests = 512;
-  cfg->max_batch_sources = 1 << 20;
+  cfg->arena_sources = 1 << 22;
+  cfg->ring_requests = 256;
+  cfg->idle_exit_us = 1000;
+  cfg->max_launch_ms = 200;
   return PP_OK;
 }
 
 int pp_server_create(pp_ctx* ctx, const pp_server_config* cfg, pp_server** out) {
   if (!ctx || !cfg || !out) return PP_EINVAL;
   *out = nullptr;
-  if (cfg->slots < 1 || cfg->slots > 16 || cfg->max_batch_requests < 1 ||
-      cfg->max_batch_sources < 1 || cfg->max_batch_sources > ppk::kMaxSources ||
-      cfg->budget_bytes == 0)
+  const int R = cfg->ring_requests;
+  if (R < 1 || R > ppk::kServeMaxRequests || (R & (R - 1)) != 0 || cfg->arena_sources < 1 ||
+      cfg->arena_sources > ppk::kMaxSources || cfg->budget_bytes == 0 || cfg->idle_exit_us < 0 ||
+      cfg->max_launch_ms < 1)
     return PP_EINVAL;
   pp_server* s = new pp_server();
   s->ctx = ctx;
   s->cfg = *cfg;
+  s->cap = R;
   const int rc = ppk::with_launch_view(ctx, [&](const ppk::LaunchView& v) {
     s->view = v;
     ppk::attach_server(ctx, +1);  // the context refuses new tables while attached
@@ -382,16 +582,23 @@ int pp_server_create(pp_ctx* ctx, const pp_server_config* cfg, pp_server** out) 
     return rc;
   }
   ppk::DeviceScope dev_scope(s->view.device);
-  s->slots.resize(cfg->slots);
-  for (Slot& sl : s->slots) {
-    if (alloc_slot(sl, cfg->max_batch_sources, cfg->max_batch_requests, s->view.geom.n_dom) !=
-        cudaSuccess) {
-      (void)cudaGetLastError();
-      for (Slot& x : s->slots) free_slot(x);
-      ppk::attach_server(ctx, -1);
-      delete s;
-      return PP_ENOMEM;
-    }
+  // the serving kernel: 1024-thread blocks holding the tables and the warps'
+  // photon reserves, as many as fit on each SM
+  s->smem = ppk::tables_smem_bytes(s->view.ice, s->view.geom) +
+            ppk::reserve_smem_bytes(ppk::kServeThreads, false);
+  int occ = 0, sms = 0;
+  cudaError_t e = ppk::serve_occupancy(s->smem, &occ);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->view.device);
+  if (e == cudaSuccess && occ < 1) e = cudaErrorInvalidConfiguration;
+  s->grid = occ * sms;
+  s->by_slot.assign(R, nullptr);
+  if (e == cudaSuccess) e = alloc_server_memory(s);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    free_server_memory(s);
+    ppk::attach_server(ctx, -1);
+    delete s;
+    return PP_ENOMEM;
   }
   s->sched = std::thread(scheduler, s);
   *out = s;
@@ -407,10 +614,10 @@ int pp_server_destroy(pp_server* s) {
   s->cv_sched.notify_all();
   if (s->sched.joinable()) s->sched.join();
   ppk::DeviceScope dev_scope(s->view.device);
-  for (Slot& sl : s->slots) {
-    if (sl.stream) cudaStreamSynchronize(sl.stream);
-    free_slot(sl);
-  }
+  if (s->s_kern) cudaStreamSynchronize(s->s_kern);
+  if (s->s_pub) cudaStreamSynchronize(s->s_pub);
+  if (s->s_down) cudaStreamSynchronize(s->s_down);
+  free_server_memory(s);
   for (auto& kv : s->by_ticket) delete kv.second;
   ppk::attach_server(s->ctx, -1);
   delete s;
@@ -424,30 +631,44 @@ const char* pp_server_last_error(const pp_server* s) {
 int pp_submit(pp_server* s, uint64_t event_id, const pp_source* src, int64_t n_src,
               uint64_t* ticket_out) {
   if (!s || !ticket_out || n_src < 0 || (n_src > 0 && !src)) return PP_EINVAL;
-  if (n_src > s->cfg.max_batch_sources) return PP_EINVAL;
-  uint64_t n_photons = 0;
-  for (int64_t i = 0; i < n_src; ++i) {
+  for (int64_t i = 0; i < n_src; ++i)
     if (!source_ok(src[i])) return PP_EINVAL;
-    n_photons += src[i].n_photons;
-  }
-  const uint64_t cost = request_cost(s, n_photons, n_src);
-  if (cost > s->cfg.budget_bytes) return PP_EBUDGET;
   Request* r = new Request();
   r->event_id = event_id;
-  r->n_photons = n_photons;
-  r->cost = cost;
   r->src.assign(src, src + n_src);
+  expand_on_host(r);
+  if (r->n_photons >= ppk::kServeMaxPhotons) {  // room in the claim word's photon field
+    delete r;
+    return PP_EINVAL;
+  }
+  r->bytes = request_bytes(s, r);
+  if (r->bytes > s->cfg.budget_bytes || n_src > s->cfg.arena_sources) {
+    delete r;
+    return PP_EBUDGET;
+  }
   r->t_submit = Clock::now();
+  if (r->n_photons == 0) {  // nothing to propagate: its result is all zeros at once
+    r->hits.assign((size_t)s->view.geom.n_dom, 0);
+    r->status = PP_OK;
+    r->t_done = r->t_submit;
+    r->src.clear();
+    r->off.clear();
+    r->chunk.clear();
+  }
   {
     std::lock_guard<std::mutex> lk(s->mu);
-    if (s->stop) {
+    if (s->stop || s->broken) {
       delete r;
-      return PP_EINVAL;
+      return s->broken ? PP_ECUDA : PP_EINVAL;
     }
     r->ticket = s->next_ticket++;
     s->by_ticket[r->ticket] = r;
-    s->pending.push_back(r);
-    s->queued_cost += cost;
+    if (r->status == kQueued) {
+      s->pending.push_back(r);
+    } else {
+      s->latency_ms.push_back(0.0);
+      s->done_requests += 1;
+    }
     if (!s->any_submit) {
       s->any_submit = true;
       s->t_first_submit = r->t_submit;
@@ -465,7 +686,7 @@ int pp_collect(pp_server* s, uint64_t ticket, uint64_t* hits, uint64_t* counts,
   auto it = s->by_ticket.find(ticket);
   if (it == s->by_ticket.end()) return PP_EINVAL;
   Request* r = it->second;
-  auto ready = [&]() { return r->status != 1; };
+  auto ready = [&]() { return r->status <= 0; };
   if (timeout_ms < 0) {
     s->cv_done.wait(lk, ready);
   } else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready)) {
@@ -498,9 +719,9 @@ int pp_server_stats(pp_server* s, double* out8) {
   out8[2] = q(0.50);
   out8[3] = q(0.99);
   out8[4] = span > 0 ? (double)s->done_photons / span : 0.0;
-  out8[5] = s->batches ? (double)s->batch_requests / (double)s->batches : 0.0;
-  out8[6] = (double)s->batches;
-  out8[7] = (double)s->peak_cost;
+  out8[5] = (double)s->launches;
+  out8[6] = (double)s->peak_bytes;
+  out8[7] = (double)s->device_bytes;
   return PP_OK;
 }
 

@@ -376,9 +376,9 @@ def pp_debug_first_hit(ctx, seg, n, mode, dom, t):
 # ---- serving loop ------------------------------------------------------------
 
 class pp_server_config(C.Structure):
-    _fields_ = [("budget_bytes", C.c_uint64), ("photon_state_bytes", C.c_uint64),
-                ("slots", C.c_int32), ("max_batch_requests", C.c_int32),
-                ("max_batch_sources", C.c_int64)]
+    _fields_ = [("budget_bytes", C.c_uint64), ("arena_sources", C.c_int64),
+                ("ring_requests", C.c_int32), ("idle_exit_us", C.c_int32),
+                ("max_launch_ms", C.c_int32)]
 
 
 def pp_server_config_default() -> pp_server_config:
@@ -410,7 +410,7 @@ def pp_submit(server, event_id, src, n_src):
     t = C.c_uint64()
     rc = _lib.pp_submit(server, event_id, _ptr(src), n_src, C.byref(t))
     if rc:
-        raise PPError(rc, f"pp_submit: {pp_strerror(rc)}")
+        raise PPError(rc, f"pp_submit: {pp_strerror(rc)}: {pp_server_last_error(server)}")
     return t.value
 
 
@@ -424,21 +424,20 @@ def pp_server_stats(server):
     rc = _lib.pp_server_stats(server, _ptr(out))
     if rc:
         raise PPError(rc, "pp_server_stats")
-    keys = ("bunches", "photons", "p50_ms", "p99_ms", "photons_per_s", "bunches_per_batch",
-            "batches", "peak_admitted_bytes")
+    keys = ("bunches", "photons", "p50_ms", "p99_ms", "photons_per_s", "kernel_launches",
+            "peak_admitted_bytes", "device_bytes")
     return dict(zip(keys, out.tolist()))
 
 
 class Server:
     """A serving loop on a Propagator's context (same calls, numpy inputs)."""
 
-    def __init__(self, prop, budget_bytes=None, slots=None, max_batch_requests=None,
-                 max_batch_sources=None, photon_state_bytes=None):
+    def __init__(self, prop, budget_bytes=None, arena_sources=None, ring_requests=None,
+                 idle_exit_us=None, max_launch_ms=None):
         cfg = pp_server_config_default()
-        for k, v in (("budget_bytes", budget_bytes), ("slots", slots),
-                     ("max_batch_requests", max_batch_requests),
-                     ("max_batch_sources", max_batch_sources),
-                     ("photon_state_bytes", photon_state_bytes)):
+        for k, v in (("budget_bytes", budget_bytes), ("arena_sources", arena_sources),
+                     ("ring_requests", ring_requests), ("idle_exit_us", idle_exit_us),
+                     ("max_launch_ms", max_launch_ms)):
             if v is not None:
                 setattr(cfg, k, v)
         self.prop = prop
