@@ -60,11 +60,19 @@ LANES_PER_SM = 128        # 4 schedulers x 32 lanes issue one instruction per cl
 #             rsqrt of the cone rotation and the log of -ln u = 4 SFU; the remaining 42 FP32
 FP32_OPS = {"step": 82, "crossing": 11, "birth": 42}
 SFU_OPS = {"step": 9, "crossing": 0, "birth": 4}
+# The kernel skips the world-exit (17) and cell (19) tests on steps that stay
+# inside their conservative budgets.  Per step it re-measures the world budget
+# on 5.94 % of steps (8 ops: distance to the cylinder), takes the exact world
+# exit on 0.63 %, the clearance-cell lookup on 5.86 % and the point clearance
+# on 0.37 % (12 ops): rates counted by an instrumented build of the current
+# kernel on the 1000-event batch.  The work the kernel executes per step is so
+OPS_PER_STEP_EXECUTED = (OPS_PER_STEP - 17 - 19 + 0.0594 * 8 + 0.0063 * 17 + 0.0586 * 19
+                         + 0.0037 * 12)
 
 # DRAM bytes per launch from ncu captures of the current kernels: the propagation
 # launch of the 1000-event step (captured on its first 200 events, scaled by sources),
 # and one 4 194 304-row launch of the fused surrogate kernel.
-NCU_TRAFFIC_BYTES = 186e6
+NCU_TRAFFIC_BYTES = 192e6
 SUR_NCU_TRAFFIC_BYTES = 301.0e6
 
 
@@ -82,8 +90,7 @@ def parse():
     ap.add_argument("--serve-bunches", type=int, default=30)
     ap.add_argument("--large-photons", type=int, default=10_000_000_000)
     ap.add_argument("--large-chunk", type=int, default=1_000_000_000)
-    ap.add_argument("--cpu-sample-photons", type=int, default=10_000_000)
-    ap.add_argument("--ref-sample-photons", type=int, default=500_000)
+    ap.add_argument("--cpu-sample-photons", type=int, default=5_000_000)
     ap.add_argument("--events", type=int, default=1000,
                     help="leading events of the workload (profiling runs use fewer)")
     ap.add_argument("--no-surrogate", action="store_true")
@@ -206,22 +213,44 @@ def cpu_sample(batch: W.Batch, photons: int) -> W.Batch:
     return batch.select(range(min(n, batch.n_events)))
 
 
-def run_oracle_sample(sample: W.Batch):
+def run_oracle_sample(sample: W.Batch, n_threads: int = 0):
     import oracle
-    m = oracle.Model(W.geometry_full(), W.ice_full(), seed=0)
+    m = oracle.Model(W.geometry_full(), W.ice_full(), seed=0, n_threads=n_threads)
     t0 = time.perf_counter()
     hits, counts, _ = oracle.propagate(m, sample)
     dt = time.perf_counter() - t0
     return dt, hits, counts
 
 
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def cpu_baseline(batch: W.Batch, photons: int):
+    """The oracle on the leading events of the batch (about `photons` photons)
+    with all host threads, and on the leading events up to 1/16 of that with
+    one thread (the same event order, so the single-thread sample is a prefix
+    of the threaded one)."""
     sample = cpu_sample(batch, photons)
     dt, _, _ = run_oracle_sample(sample)
     n = sample.total_photons()
+    small = cpu_sample(batch, max(1, photons // 16))
+    dt1, _, _ = run_oracle_sample(small, n_threads=1)
+    n1 = small.total_photons()
     return {"value": n / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "cpu_model": cpu_model(),
             "sample": f"first {sample.n_events} of the 1000 events ({n} photons), "
-                      f"double precision, {os.cpu_count()} threads, {dt:.1f} s"}
+                      f"double precision, {os.cpu_count()} threads, {dt:.1f} s",
+            "single_thread": {"value": n1 / dt1, "unit": UNIT,
+                              "sample": f"first {small.n_events} events ({n1} photons), "
+                                        f"1 thread, {dt1:.1f} s"}}
 
 
 # ---------------------------------------------------------- reference arm --
@@ -231,7 +260,7 @@ def run_reference(args):
     if rank != 0:
         return
     batch = replica_batch(0, args.events)
-    sample = cpu_sample(batch, args.ref_sample_photons)
+    sample = cpu_sample(batch, args.cpu_sample_photons)   # the cpu_baseline leg's sample
     n = sample.total_photons()
     for _ in range(args.warmup):
         run_oracle_sample(sample)
@@ -247,6 +276,7 @@ def run_reference(args):
                        "photons_per_step": batch.total_photons(),
                        "parallelism": "replicas" if world > 1 else "single"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "cpu_model": cpu_model(),
                              "sample": f"each step: first {sample.n_events} events "
                                        f"({n} photons), {cores} threads"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -642,6 +672,9 @@ def run_ours(args):
            + OPS_PER_BIRTH * births_per_launch)
     kern_avg_ms = kern_ms / max(1, n_timed)
     achieved = ops / (kern_avg_ms * 1e-3) / 1e9
+    ops_executed = ops - (OPS_PER_STEP - OPS_PER_STEP_EXECUTED) * steps_per_launch
+    achieved_executed = ops_executed / (kern_avg_ms * 1e-3) / 1e9
+    fma_gops = pipes["fp32_peak_gops"]
     value = aggregate_value(world, photons, args.steps, total_ms)
     plain_value = photons / (statistics.mean(plain_ms) * 1e-3) if plain_ms else None
     line = {
@@ -666,7 +699,13 @@ def run_ours(args):
                      "kernel": "k_propagate<persistent>", "kernel_ms": kern_avg_ms,
                      "steps_per_launch": steps_per_launch,
                      "crossings_per_launch": cross_per_launch,
-                     "string_search_frac": slow_n / max(1, steps_n)},
+                     "string_search_frac": slow_n / max(1, steps_n),
+                     "frac_vs_measured_fma_rate": achieved / fma_gops,
+                     "executed": {"achieved": achieved_executed,
+                                  "frac": achieved_executed / peak_gops,
+                                  "ops_per_step": OPS_PER_STEP_EXECUTED,
+                                  "note": "counting only the world-exit and cell tests the "
+                                          "kernel runs (rates of an instrumented build)"}},
         "autotune": {"best": tuned[0], "best_ms": tuned[1]} if tuned else None,
         "pipes": pipes,
         "steps_per_s": steps_per_launch / (kern_avg_ms * 1e-3),

@@ -67,7 +67,6 @@ typedef struct pp_config {
   uint32_t max_steps;                 /* step cap per photon; reaching it counts as absorbed
                                          and as truncated (default 100000) */
   uint64_t seed;                      /* Philox key word 0 (low 32 bits used) */
-  uint64_t photon_budget_bytes;       /* admission budget for queued requests (0: none) */
   float world_margin_m;               /* world cylinder = DOM extent + margin (default 100) */
   float depth_of_z0_m;                /* depth of the z = 0 plane (default 1950) */
   int32_t scatter_coeff_is_effective; /* 1 (default): b_e is the effective coefficient and the

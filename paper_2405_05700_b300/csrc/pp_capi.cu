@@ -315,8 +315,12 @@ int timed_propagate(pp_ctx* ctx, bool persistent, const WorkDev& w, const RunDev
     PP_CUDA(cudaEventRecord(e0, st));
   }
   if (variant < 0) variant = persistent ? kernel_variant(ctx) : 0;
-  PP_CUDA(launch_propagate(persistent, ctx->ice, ctx->geom, w, run, ctx->block_threads, grid,
-                           n_photons, smem, st, variant));
+  // the plain path (one thread per photon, one launch per event) keeps its
+  // own block size: the persistent kernel's 1024-thread blocks leave long
+  // tails of idle threads there
+  PP_CUDA(launch_propagate(persistent, ctx->ice, ctx->geom, w, run,
+                           persistent ? ctx->block_threads : kPlainThreads, grid, n_photons, smem,
+                           st, variant));
   ctx->kernels_launched += 1;
   if (ctx->timing) {
     PP_CUDA(cudaEventRecord(e1, st));
@@ -755,7 +759,6 @@ int pp_config_default(pp_config* cfg) {
   cfg->device = 0;
   cfg->max_steps = 100000;
   cfg->seed = 0;
-  cfg->photon_budget_bytes = 0;
   cfg->world_margin_m = 100.0f;
   cfg->depth_of_z0_m = 1950.0f;
   cfg->scatter_coeff_is_effective = 1;

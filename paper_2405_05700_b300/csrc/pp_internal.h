@@ -181,6 +181,7 @@ cudaError_t launch_expand(const pp_source* src, int64_t n_src, const int64_t* sr
 // photons per lane: births of whole warps into shared memory, idle lanes
 // take the next reserved photon).
 constexpr int kVariantRecords = 7;
+constexpr int kPlainThreads = 256;  // block size of the plain (one thread per photon) path
 constexpr int kVariantReserve = 16;
 
 // Hit times: light speed in vacuum, and the group index used unless the

@@ -28,7 +28,7 @@ PP_OUT_ABSORBED, PP_OUT_ESCAPED, PP_OUT_TRUNCATED = -1, -2, -3
 class pp_config(C.Structure):
     _fields_ = [
         ("device", C.c_int32), ("max_steps", C.c_uint32), ("seed", C.c_uint64),
-        ("photon_budget_bytes", C.c_uint64), ("world_margin_m", C.c_float),
+        ("world_margin_m", C.c_float),
         ("depth_of_z0_m", C.c_float), ("scatter_coeff_is_effective", C.c_int32),
         ("reserved", C.c_int32), ("stream", C.c_void_p),
     ]

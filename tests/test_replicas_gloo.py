@@ -37,7 +37,7 @@ def _worker(rank, world, port, q):
         slowest = bench.max_over_ranks(100.0 + 7.0 * rank, "cpu")
         value = bench.aggregate_value(world, b.total_photons(), 3, slowest)
         # the reference arm: only rank 0 runs the oracle
-        args = argparse.Namespace(events=2, ref_sample_photons=1000, warmup=0, steps=1, gpus=world)
+        args = argparse.Namespace(events=2, cpu_sample_photons=1000, warmup=0, steps=1, gpus=world)
         ref_ran = rank == 0
         if rank != 0:
             assert bench.run_reference(args) is None
