@@ -359,7 +359,11 @@ def surrogate_leg(args, prop, stream, dev):
                         "pairs_within_r_max": pairs, "r_max_m": 250.0, "ms": d_ms,
                         "sources_per_s": nd / (d_ms * 1e-3),
                         "pairs_per_s": pairs / (d_ms * 1e-3),
-                        "mc_equivalent_photons_per_s": nd * 1e6 / (d_ms * 1e-3)}
+                        "pair_fraction_evaluated": pairs / (nd * prop.n_dom),
+                        "mc_equivalent_photons_per_s": nd * 1e6 / (d_ms * 1e-3),
+                        "note": "only pairs within 250 m are evaluated (farther pairs carry "
+                                "~3e-4 of the MC light); the MC-equivalent rate counts the "
+                                "1e6 photons of each source"}
         peaks = {}
         try:
             peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))

@@ -239,6 +239,34 @@ def _evaluate(prop, mlp, n_sources, photons, seed, event_base, r_fallbacks, min_
     res = {"sources": n_sources, "photons_per_source": photons, "mc_seconds": mc_secs,
            "surrogate_seconds": sur_secs, "speedup": mc_secs / sur_secs if sur_secs > 0 else None}
     res["chi2_ndf"], res["ndf"] = chi2((hits.sum(0) - sur_dom) ** 2, sur_dom)
+    # per (source, DOM) pair, where errors of opposite sign cannot cancel as
+    # they can in per-DOM sums: Pearson chi2 over pairs expecting >= min_expected
+    # hits, the Poisson deviance per pair over every pair the surrogate
+    # evaluates (expectation below 1 for pairs with few expected hits), and the
+    # ratio of all MC hits to all expected hits
+    n_pair = hits.astype(np.float64)
+    use = lam >= min_expected
+    modelled = lam > 0
+    dev = 2.0 * (np.where(n_pair > 0, n_pair * np.log(np.maximum(n_pair, 1e-300) /
+                                                     np.maximum(lam, 1e-300)), 0.0)
+                 - (n_pair - lam))
+    res["per_pair"] = {
+        "chi2_ndf": float(((n_pair - lam) ** 2 / np.where(use, lam, 1.0))[use].sum())
+                    / max(1, int(use.sum())),
+        "ndf": int(use.sum()), "min_expected": min_expected,
+        "deviance_per_pair": float(dev[modelled].sum()) / max(1, int(modelled.sum())),
+        "pairs": int(modelled.sum()),
+        "hits_over_expected": float(n_pair[modelled].sum() / max(lam[modelled].sum(), 1e-300))}
+    # MC time grows with the photons per source, the surrogate's does not:
+    # the speedup at a tenth of the photons as well
+    src10 = src.copy()
+    src10["n_photons"] = max(1, photons // 10)
+    _, mc10 = mc_hits(prop, src10, 0, event_ids=ids + 7_000_000)
+    res["speedup_by_photons"] = [
+        {"photons_per_source": photons, "mc_seconds": mc_secs,
+         "speedup": mc_secs / sur_secs if sur_secs > 0 else None},
+        {"photons_per_source": int(src10["n_photons"][0]), "mc_seconds": mc10,
+         "speedup": mc10 / sur_secs if sur_secs > 0 else None}]
     d_src = _device_sources(src)
     res["hybrid"] = []
     for r_fb in r_fallbacks:
