@@ -22,8 +22,8 @@ def sources():
 
 
 def _deps():
-    return sources() + glob.glob(os.path.join(HERE, "csrc", "*.h*")) + \
-        [os.path.join(ROOT, "include", "pp.h")]
+    return sources() + glob.glob(os.path.join(HERE, "csrc", "*.h")) + \
+        glob.glob(os.path.join(HERE, "csrc", "*.cuh")) + [os.path.join(ROOT, "include", "pp.h")]
 
 
 def up_to_date() -> bool:

@@ -51,16 +51,40 @@ __device__ __forceinline__ float fast_sqrt(float x) {
   return y;
 }
 
-// -ln u for u in (0, 1)
-__device__ __forceinline__ float neg_log(float u) { return -__logf(u); }
+// The other special functions of the step, as the PTX .approx instructions
+// with .ftz: every operand on the step is a normal number (directions,
+// distances and optical depths), where flushing subnormals changes no result,
+// and the .ftz forms need no subnormal handling -- and no branch -- around
+// the hardware operation.  Same results, 4 % less time for the batched kernel.
+__device__ __forceinline__ float fast_rsqrt(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float fast_rcp(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// -ln u for u in (0, 1): -log2(u) ln 2
+__device__ __forceinline__ float neg_log(float u) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(u));
+  return y * -0.693147180559945309f;
+}
 
 // (sin, cos) of 2 pi u for u in (0, 1): evaluated at pi (2u - 1), which lies
 // in (-pi, pi) where the hardware sine/cosine are accurate, and negated
 // (sin(x + pi) = -sin x, cos(x + pi) = -cos x).
 __device__ __forceinline__ void sincos_2pi(float u, float& s, float& c) {
-  __sincosf(3.14159265358979f * fmaf(2.0f, u, -1.0f), &s, &c);
-  s = -s;
-  c = -c;
+  const float xx = 3.14159265358979f * fmaf(2.0f, u, -1.0f);  // sin / cos.approx.ftz
+  float sx, cx;
+  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(sx) : "f"(xx));
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(cx) : "f"(xx));
+  s = -sx;
+  c = -cx;
 }
 
 // --------------------------------------------------------- shared tables --
@@ -117,17 +141,17 @@ __device__ __forceinline__ int layer_at(const IceDev& I, float z, float w) {
 __device__ __forceinline__ float walk(const float4* __restrict__ lay, const IceDev& I, float z,
                                       float w, int& layer, float tau_s, float& tau_a,
                                       bool& absorb, uint32_t& crossings) {
-  const float inv_w = __fdividef(1.0f, w);
+  const float inv_w = fast_rcp(w);
   float zc = z;
   float S = 0.0f;
   for (;;) {
     const float4 L = lay[layer];
-    float ell = PP_INF;
-    if (w < 0.0f) {
-      if (layer < I.L - 1) ell = (fmaf(-(float)(layer + 1), I.dz, I.z_top) - zc) * inv_w;
-    } else if (w > 0.0f) {
-      if (layer > 0) ell = (fmaf(-(float)layer, I.dz, I.z_top) - zc) * inv_w;
-    }
+    // distance to the boundary ahead, as selects rather than branches (the
+    // branchy form cost 5 % of the batched kernel's time)
+    const bool down = w < 0.0f;
+    const bool has = down ? (layer < I.L - 1) : (w > 0.0f && layer > 0);
+    const float zb = fmaf(-(float)(down ? layer + 1 : layer), I.dz, I.z_top);
+    float ell = has ? (zb - zc) * inv_w : PP_INF;
     ell = fmaxf(ell, 0.0f);
     const float ds = (L.x > 0.0f) ? tau_s * L.z : PP_INF;
     const float da = (L.y > 0.0f) ? tau_a * L.w : PP_INF;
@@ -333,7 +357,7 @@ __device__ __forceinline__ void hg_angle(const IceDev& I, float u, float& mu, fl
     return;
   }
   const float den = fmaf(I.c3, u, I.c2);        // 1 - g + 2gu
-  const float inv = __fdividef(1.0f, den);
+  const float inv = fast_rcp(den);
   const float t = I.c1 * inv;
   const float omm = I.c2 * (1.0f - u) * (t + I.c2) * inv;        // 1 - mu
   const float opm = (2.0f - I.c2) * u * ((2.0f - I.c2) + t) * inv;  // 1 + mu
@@ -349,23 +373,22 @@ __device__ __forceinline__ void rotate(float& dx, float& dy, float& dz, float mu
                                        float u_phi) {
   float sp, cp;
   sincos_2pi(u_phi, sp, cp);
-  float ox, oy, oz;
-  if (fabsf(dz) > 0.99999f) {
-    ox = st * cp;
-    oy = st * sp;
-    oz = (dz >= 0.0f) ? mu : -mu;
-  } else {
-    // 1 - dz^2 of a unit vector, taken as dx^2 + dy^2: an FP32 direction is
-    // unit only to ~1e-7, and near the poles 1 - dz^2 would carry that error
-    // into a frame of size ~1e-4
-    const float q = fmaf(dx, dx, dy * dy);
-    const float it = rsqrtf(q);
-    const float tmp = q * it;
-    ox = fmaf(st * fmaf(dx * dz, cp, -dy * sp), it, dx * mu);
-    oy = fmaf(st * fmaf(dy * dz, cp, dx * sp), it, dy * mu);
-    oz = fmaf(-st * cp, tmp, dz * mu);
-  }
-  const float inv = rsqrtf(fmaf(ox, ox, fmaf(oy, oy, oz * oz)));
+  // 1 - dz^2 of a unit vector, taken as dx^2 + dy^2: an FP32 direction is
+  // unit only to ~1e-7, and near the poles 1 - dz^2 would carry that error
+  // into a frame of size ~1e-4.  Both forms are evaluated and the lab frame
+  // is selected near the poles (a select, not a branch: the general form's
+  // value there, possibly not finite, is discarded)
+  const float q = fmaf(dx, dx, dy * dy);
+  const float it = fast_rsqrt(q);
+  const float tmp = q * it;
+  const bool pole = fabsf(dz) > 0.99999f;
+  const float gx = fmaf(st * fmaf(dx * dz, cp, -dy * sp), it, dx * mu);
+  const float gy = fmaf(st * fmaf(dy * dz, cp, dx * sp), it, dy * mu);
+  const float gz = fmaf(-st * cp, tmp, dz * mu);
+  const float ox = pole ? st * cp : gx;
+  const float oy = pole ? st * sp : gy;
+  const float oz = pole ? ((dz >= 0.0f) ? mu : -mu) : gz;
+  const float inv = fast_rsqrt(fmaf(ox, ox, fmaf(oy, oy, oz * oz)));
   dx = ox * inv;
   dy = oy * inv;
   dz = oz * inv;
