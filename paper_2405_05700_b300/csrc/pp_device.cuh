@@ -169,13 +169,8 @@ __device__ __forceinline__ float walk(const float4* __restrict__ lay, const IceD
     crossings += 1;
     tau_s = fmaxf(0.0f, fmaf(-L.x, ell, tau_s));
     tau_a = fmaxf(0.0f, fmaf(-L.y, ell, tau_a));
-    if (w < 0.0f) {
-      zc = fmaf(-(float)(layer + 1), I.dz, I.z_top);
-      layer += 1;
-    } else {
-      zc = fmaf(-(float)layer, I.dz, I.z_top);
-      layer -= 1;
-    }
+    zc = zb;  // the boundary crossed
+    layer += down ? 1 : -1;
   }
 }
 
