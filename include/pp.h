@@ -341,9 +341,9 @@ int pp_get_world(const pp_ctx* ctx, float* out3);
  * host-mapped memory when a bunch's last photon is tallied.  A scheduler
  * thread admits bunches in arrival order while the ring, the device arenas and
  * the budget allow, copies finished bunches' outputs back, and relaunches the
- * kernel, which leaves after idle_exit_us without work and stops taking
- * photons max_launch_ms after its launch.  A bunch's result is the same alone
- * and in any mix. */
+ * kernel.  A launch ends as a whole: idle_exit_us after the server last held
+ * unfinished work, or max_launch_ms after it started.  A bunch's result is the
+ * same alone and in any mix. */
 typedef struct pp_server pp_server; /* opaque */
 
 typedef struct pp_server_config {
@@ -358,9 +358,10 @@ typedef struct pp_server_config {
                              one bunch (default 4 194 304) */
   int32_t ring_requests;  /* request-ring slots = bunches admitted at once; a power
                              of two, 1..65536 (default 256) */
-  int32_t idle_exit_us;   /* the serving kernel leaves after this long with nothing
-                             to claim (default 1000) */
-  int32_t max_launch_ms;  /* and stops claiming this long after its launch; the
+  int32_t idle_exit_us;   /* a serving-kernel launch ends once its warps have been
+                             idle this long while the server holds no unfinished
+                             bunch (default 1000) */
+  int32_t max_launch_ms;  /* and stops claiming this long after it started; the
                              scheduler relaunches it (default 200) */
 } pp_server_config;
 

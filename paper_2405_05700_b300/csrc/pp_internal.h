@@ -278,8 +278,13 @@ struct ServeDev {
   unsigned long long* counts;        // [cap][4] absorbed, escaped, truncated, steps
   volatile uint32_t* done_flag;      // host-mapped [cap]: seq + 1 once tallied
   int* err;
-  uint64_t idle_ns;                  // a warp leaves after this long with nothing to do
-  uint64_t max_ns;                   // and stops taking new photons this long after launch
+  const int* may_leave;              // 1 while the host holds no unfinished request
+                                     // (written by host copies)
+  int* closing;                      // set by the warp that ends the launch; cleared by
+                                     // the host before each launch
+  uint64_t idle_ns;                  // an idle warp closes the launch after this long, once
+                                     // may_leave is set
+  uint64_t max_ns;                   // the launch closes this long after its start
 };
 
 // The serving kernel: persistent blocks (1024 threads, photon reserve) that

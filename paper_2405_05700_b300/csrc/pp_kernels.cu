@@ -510,6 +510,12 @@ __device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long lon
   return v;
 }
 
+__device__ __forceinline__ int ld_relaxed_int(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 // Per-lane tallies of the request the lane last worked on (as LaneTally),
 // plus the number of its photons tallied.  The flush adds them to the
 // request's counters and that number to its done count, after a fence that
@@ -655,10 +661,13 @@ __device__ __noinline__ int serve_topup(const IceDev& I, const GeomDev& G, const
 // The serving kernel: the reserve loop of the batched kernel, fed from the
 // request ring.  A warp keeps taking photons while requests are published;
 // once it has nothing in flight and nothing to claim it polls (sleeping a few
-// microseconds between looks) and leaves after idle_ns; it stops claiming
-// max_ns after the launch and leaves once its photons are done.  Every wait is
-// bounded by the global timer; the host relaunches the kernel while published
-// requests are unfinished.
+// microseconds between looks).  A launch ends as a whole: a warp that has
+// been idle for idle_ns while the host holds no unfinished request
+// (may_leave), or any warp max_ns after the launch, closes it (`closing`);
+// then no warp claims again and every warp leaves once its photons are done.
+// (Warps leaving one by one would leave the next request to the few still
+// running.)  Every wait is bounded by the global timer; the host relaunches
+// the kernel while published requests are unfinished.
 __global__ void __launch_bounds__(kServeThreads, 1)
 k_serve(const __grid_constant__ IceDev I, const __grid_constant__ GeomDev G,
         const __grid_constant__ ServeDev S, const __grid_constant__ RunDev R) {
@@ -676,12 +685,20 @@ k_serve(const __grid_constant__ IceDev I, const __grid_constant__ GeomDev G,
   for (;;) {
     bool got = false;
     if (claiming && rcount <= CAP - 32) {
-      __syncwarp();
-      rcount = serve_topup(I, G, S, R, rhead, rcount, got);
-      __syncwarp();
-      const uint64_t now = __shfl_sync(kFull, global_ns(), 0);
-      if (now - t0 > S.max_ns) claiming = false;
-      if (got) idle = false;
+      // once any warp has closed the launch, no warp claims any more
+      if (__shfl_sync(kFull, ld_relaxed_int(S.closing), 0)) {
+        claiming = false;
+      } else {
+        __syncwarp();
+        rcount = serve_topup(I, G, S, R, rhead, rcount, got);
+        __syncwarp();
+        const uint64_t now = __shfl_sync(kFull, global_ns(), 0);
+        if (now - t0 > S.max_ns) {
+          claiming = false;
+          if ((threadIdx.x & 31) == 0) atomicExch(S.closing, 1);
+        }
+        if (got) idle = false;
+      }
     }
     const unsigned idle_lanes = __ballot_sync(kFull, !alive);
     const int n_idle = __popc(idle_lanes);
@@ -709,7 +726,13 @@ k_serve(const __grid_constant__ IceDev I, const __grid_constant__ GeomDev G,
         idle = true;
         idle_since = now;
       }
-      if (now - idle_since > S.idle_ns) break;
+      const int leave = __shfl_sync(kFull, ld_relaxed_int(S.may_leave), 0);
+      if (leave && now - idle_since > S.idle_ns) {
+        // the host holds nothing unfinished: close the whole launch (every
+        // warp leaves, so that the next request finds a full launch)
+        if ((threadIdx.x & 31) == 0) atomicExch(S.closing, 1);
+        break;
+      }
       __nanosleep(4000);
       continue;
     }

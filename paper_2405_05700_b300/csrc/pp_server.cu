@@ -127,6 +127,8 @@ struct pp_server {
   ppk::ServeReq* d_req = nullptr;
   unsigned long long* d_tail = nullptr;
   unsigned long long* d_head = nullptr;
+  int* d_may_leave = nullptr;           // 1: the kernel's idle warps may close the launch
+  int* d_closing = nullptr;             // the launch is closing (cleared before each launch)
   pp_source* d_src = nullptr;
   uint64_t* d_off = nullptr;
   uint32_t* d_chunk = nullptr;
@@ -143,6 +145,7 @@ struct pp_server {
   unsigned long long* h_tail = nullptr;  // [cap]: the tail value each publication writes
   unsigned long long* h_arm = nullptr;   // [cap]: the claim word that arms each slot
   uint64_t* h_zero = nullptr;            // n_dom + 4 zeros
+  int* h_one = nullptr;                  // a pinned 1 (the may-leave flag's value)
   uint64_t* h_hits = nullptr;
   uint64_t* h_counts = nullptr;
   int* h_err = nullptr;                  // [cap]
@@ -152,6 +155,7 @@ struct pp_server {
   cudaEvent_t kern_done = nullptr;
   std::vector<cudaEvent_t> copied;       // [cap]
   bool kernel_running = false;
+  bool may_leave = false;                // the last value written to d_may_leave
   // host state
   std::mutex mu;
   std::condition_variable cv_sched, cv_done;
@@ -215,10 +219,10 @@ uint64_t request_bytes(const pp_server* s, const Request* r) {
 }
 
 void free_server_memory(pp_server* s) {
-  void* dev[] = {s->d_req, s->d_tail, s->d_head, s->d_src, s->d_off, s->d_chunk,
+  void* dev[] = {s->d_req, s->d_tail, s->d_head, s->d_may_leave, s->d_closing, s->d_src, s->d_off, s->d_chunk,
                  s->d_hits, s->d_counts, s->d_err};
   for (void* p : dev) cudaFree(p);
-  void* host[] = {s->h_src, s->h_off, s->h_chunk, s->h_req, s->h_tail, s->h_arm, s->h_zero,
+  void* host[] = {s->h_src, s->h_off, s->h_chunk, s->h_req, s->h_tail, s->h_arm, s->h_zero, s->h_one,
                   s->h_hits, s->h_counts, s->h_err, (void*)s->h_flag};
   for (void* p : host) cudaFreeHost(p);
   for (cudaEvent_t e : s->copied) cudaEventDestroy(e);
@@ -245,6 +249,8 @@ cudaError_t alloc_server_memory(pp_server* s) {
   PP_A(dev_alloc(s, &s->d_req, R));
   PP_A(dev_alloc(s, &s->d_tail, 1));
   PP_A(dev_alloc(s, &s->d_head, 1));
+  PP_A(dev_alloc(s, &s->d_may_leave, 1));
+  PP_A(dev_alloc(s, &s->d_closing, 1));
   PP_A(dev_alloc(s, &s->d_src, S));
   PP_A(dev_alloc(s, &s->d_off, S + R));
   PP_A(dev_alloc(s, &s->d_chunk, S + 2 * R));
@@ -258,6 +264,7 @@ cudaError_t alloc_server_memory(pp_server* s) {
   PP_A(cudaMallocHost(&s->h_tail, sizeof(unsigned long long) * R));
   PP_A(cudaMallocHost(&s->h_arm, sizeof(unsigned long long) * R));
   PP_A(cudaMallocHost(&s->h_zero, sizeof(uint64_t) * (n_dom + 4)));
+  PP_A(cudaMallocHost(&s->h_one, sizeof(int)));
   PP_A(cudaMallocHost(&s->h_hits, sizeof(uint64_t) * R * n_dom));
   PP_A(cudaMallocHost(&s->h_counts, sizeof(uint64_t) * R * 4));
   PP_A(cudaMallocHost(&s->h_err, sizeof(int) * R));
@@ -277,6 +284,7 @@ cudaError_t alloc_server_memory(pp_server* s) {
 #undef PP_A
   if (e != cudaSuccess) return e;
   std::memset(s->h_zero, 0, sizeof(uint64_t) * (n_dom + 4));
+  *s->h_one = 1;
   for (size_t i = 0; i < R; ++i) s->h_flag[i] = 0;
   // the ring starts empty (tail and head 0) with every slot disarmed (a
   // claim word whose request number matches no slot's seq), no error
@@ -290,6 +298,7 @@ cudaError_t alloc_server_memory(pp_server* s) {
   e = cudaMemcpyAsync(s->d_req, init, sizeof(ppk::ServeReq) * R, cudaMemcpyHostToDevice, s->s_pub);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_tail, 0, sizeof(unsigned long long), s->s_pub);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_head, 0, sizeof(unsigned long long), s->s_pub);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_may_leave, 0, sizeof(int), s->s_pub);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_err, 0, sizeof(int), s->s_pub);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->s_pub);
   s->a_src.reset(S);
@@ -374,6 +383,11 @@ bool admit_front(pp_server* s) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&s->d_req[slot].claimed, s->h_arm + slot, kWord, cudaMemcpyHostToDevice,
                         st);
+  // work in flight: the kernel's idle warps must stay
+  if (e == cudaSuccess && s->may_leave) {
+    e = cudaMemcpyAsync(s->d_may_leave, s->h_zero, sizeof(int), cudaMemcpyHostToDevice, st);
+    s->may_leave = false;
+  }
   // the doorbell: requests are published in order, so the tail only grows
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(s->d_tail, s->h_tail + slot, sizeof(unsigned long long),
@@ -485,10 +499,15 @@ cudaError_t launch_kernel(pp_server* s) {
   sv.counts = reinterpret_cast<unsigned long long*>(s->d_counts);
   sv.done_flag = s->d_flag;
   sv.err = s->d_err;
+  sv.may_leave = s->d_may_leave;
+  sv.closing = s->d_closing;
   sv.idle_ns = (uint64_t)s->cfg.idle_exit_us * 1000ull;
   sv.max_ns = (uint64_t)s->cfg.max_launch_ms * 1000000ull;
   ppk::NvtxRange range("pp.server_kernel");
-  cudaError_t e = ppk::launch_serve(s->view.ice, s->view.geom, sv, s->view.run, s->grid, s->smem,
+  // a fresh launch is open (a copy of zero: the previous launch has ended)
+  cudaError_t e = cudaMemcpyAsync(s->d_closing, s->h_zero, sizeof(int), cudaMemcpyHostToDevice,
+                                  s->s_kern);
+  if (e == cudaSuccess) e = ppk::launch_serve(s->view.ice, s->view.geom, sv, s->view.run, s->grid, s->smem,
                                     s->s_kern);
   if (e == cudaSuccess) e = cudaEventRecord(s->kern_done, s->s_kern);
   if (e == cudaSuccess) {
@@ -522,6 +541,16 @@ void scheduler(pp_server* s) {
           s->broken = true;
         }
       }
+    }
+    // nothing left on the device: the kernel's idle warps may leave
+    if (!s->may_leave && !s->broken && !unfinished_published(s) && s->pending.empty()) {
+      const cudaError_t e = cudaMemcpyAsync(s->d_may_leave, s->h_one, sizeof(int),
+                                            cudaMemcpyHostToDevice, s->s_pub);
+      if (e != cudaSuccess) {
+        s->last_error = std::string("serving flag: ") + cudaGetErrorString(e);
+        s->broken = true;
+      }
+      s->may_leave = true;
     }
     if (!s->kernel_running && !s->broken && unfinished_published(s)) {
       const cudaError_t e = launch_kernel(s);
