@@ -178,3 +178,23 @@ def test_collect_timeout_unknown_ticket_and_bad_input(pp, prop):
     # config checks: the ring size must be a power of two
     with pytest.raises(pp.PPError):
         pp.Server(prop, ring_requests=6)
+
+
+def test_a_large_bunch_after_small_ones_gets_the_whole_kernel(pp, prop):
+    """Small bunches one at a time leave most warps idle between them; a
+    large bunch that follows must still run on the whole serving kernel (a
+    launch ends as a whole, never warp by warp).  2e6 photons of the tiny
+    point-source kind take ~5 ms on the whole kernel; on the few warps a
+    warp-by-warp exit used to leave, up to the 200 ms launch limit."""
+    import time
+    with pp.Server(prop) as server:
+        for k in range(6):
+            t = server.submit(100 + k, W.point_source(0.0, 0.0, 0.0, 10_000))
+            assert server.collect(t, timeout_ms=60_000)[0] == pp.PP_OK
+        src = W.point_source(0.0, 0.0, 0.0, 2_000_000)
+        t0 = time.perf_counter()
+        t = server.submit(200, src)
+        rc, h, c = server.collect(t, timeout_ms=60_000)
+        ms = (time.perf_counter() - t0) * 1e3
+    assert rc == pp.PP_OK and int(h.sum() + c[0] + c[1]) == 2_000_000
+    assert ms < 60.0, ms
