@@ -13,6 +13,7 @@ while new bunches keep arriving.
 * pp_collect honours its timeout; unknown tickets and bad sources are refused;
   a bunch without photons is complete at once; the context refuses new tables
   while a server is attached.
+* A large bunch after a run of small ones gets the whole serving kernel.
 """
 import threading
 import time
@@ -186,7 +187,6 @@ def test_a_large_bunch_after_small_ones_gets_the_whole_kernel(pp, prop):
     launch ends as a whole, never warp by warp).  2e6 photons of the tiny
     point-source kind take ~5 ms on the whole kernel; on the few warps a
     warp-by-warp exit used to leave, up to the 200 ms launch limit."""
-    import time
     with pp.Server(prop) as server:
         for k in range(6):
             t = server.submit(100 + k, W.point_source(0.0, 0.0, 0.0, 10_000))
