@@ -23,9 +23,9 @@
  *     pp_destroy().
  *   - Results depend only on (seed, event id, the event's sources, geometry,
  *     ice, settings): never on batching, launch shape or timing.  Random
- *     numbers are Philox4x32-10 keyed by (seed, event id) with counter
- *     (photon id, step), and tallies are integer atomics, so hits + absorbed
- *     + escaped equals the number of emitted photons exactly.
+ *     numbers are Philox4x32-10 keyed by the 64-bit seed with counter
+ *     (photon id, step, event id), and tallies are integer atomics, so hits
+ *     + absorbed + escaped equals the number of emitted photons exactly.
  *   - Calls on one context are serialised by the library (a mutex).
  *
  * Coordinates: metres, right-handed, z up; depth = depth_of_z0_m - z.
@@ -66,7 +66,7 @@ typedef struct pp_config {
   int32_t device;                     /* CUDA device ordinal */
   uint32_t max_steps;                 /* step cap per photon; reaching it counts as absorbed
                                          and as truncated (default 100000) */
-  uint64_t seed;                      /* Philox key word 0 (low 32 bits used) */
+  uint64_t seed;                      /* Philox key (low word, high word) */
   float world_margin_m;               /* world cylinder = DOM extent + margin (default 100) */
   float depth_of_z0_m;                /* depth of the z = 0 plane (default 1950) */
   int32_t scatter_coeff_is_effective; /* 1 (default): b_e is the effective coefficient and the
@@ -142,7 +142,7 @@ int pp_propagate(pp_ctx* ctx, uint64_t event_id, const pp_source* src, int64_t n
 /* Many events in one persistent launch (cross-event batching, paper Sec. 4:
  * the photon server aggregates steps from many events and clients).  Host
  * buffers.
- *   event_ids[n_events]       event ids (the Philox key's second word, low 32 bits)
+ *   event_ids[n_events]       event ids (the Philox counter's fourth word, low 32 bits)
  *   src_begin[n_events + 1]   event e owns src[src_begin[e] .. src_begin[e+1]),
  *                             non-decreasing, src_begin[0] = 0
  *   src[src_begin[n_events]]  all sources

@@ -15,9 +15,9 @@
 // independent ("embarrassingly parallel", Sec. 2).  Everything numeric beyond
 // that skeleton is a stated reading:
 //   * random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11,
-//     "Parallel Random Numbers: As Easy as 1, 2, 3"), key (seed, event),
-//     counter (photon id lo, photon id hi, block, 0); block 0 = birth,
-//     block n >= 1 = step n;
+//     "Parallel Random Numbers: As Easy as 1, 2, 3"), key (seed lo, seed hi),
+//     counter (photon id lo, photon id hi, block, event id lo); block 0 =
+//     birth, block n >= 1 = step n;
 //   * u = ((x >> 8) | 1) * 2^-24, exact in binary32 and binary64, in (0, 1);
 //   * step lengths: exponential in optical depth, the scattering coefficient
 //     b = b_e / (1 - g) (b_e is the effective coefficient), absorption
@@ -447,8 +447,8 @@ int simulate_photon(const Model& M, uint32_t event_lo, uint64_t pid, const Sourc
                     PhotonStats* st, double* birth6, double* trace, int n_trace,
                     double* margin = nullptr, double* emit_offset = nullptr,
                     double* hit_dir = nullptr) {
-  const uint32_t key[2] = {(uint32_t)M.seed, event_lo};
-  uint32_t ctr[4] = {(uint32_t)pid, (uint32_t)(pid >> 32), 0u, 0u};
+  const uint32_t key[2] = {(uint32_t)M.seed, (uint32_t)(M.seed >> 32)};
+  uint32_t ctr[4] = {(uint32_t)pid, (uint32_t)(pid >> 32), 0u, event_lo};
   uint32_t x[4];
   // Birth (block 0): point along the emitting segment, direction, and the
   // absorption optical depth the photon carries.

@@ -233,7 +233,10 @@ int grid_blocks(pp_ctx* ctx, size_t smem, int* out, int variant = -1) {
 
 RunDev run_params(const pp_ctx* ctx) {
   RunDev r;
-  r.seed_lo = (uint32_t)ctx->cfg.seed;
+  for (uint32_t i = 0; i < 10; ++i) {
+    r.key_x[i] = (uint32_t)ctx->cfg.seed + 0x9E3779B9u * i;
+    r.key_y[i] = (uint32_t)(ctx->cfg.seed >> 32) + 0xBB67AE85u * i;
+  }
   r.max_steps = ctx->cfg.max_steps;
   r.cos_cherenkov = (float)std::cos(41.0 * 3.14159265358979323846 / 180.0);
   r.sin_cherenkov = (float)std::sin(41.0 * 3.14159265358979323846 / 180.0);

@@ -16,7 +16,17 @@ namespace ppk {
 // ---------------------------------------------------------------- Philox --
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 products
 // on counter words 0 and 2, the high halves xor-ed into the other words with
-// the key, the key bumped by the Weyl constants between rounds.
+// the round's key, the key bumped by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox_round(uint4 c, uint32_t kx, uint32_t ky) {
+  // one 32 x 32 -> 64-bit product each (high and low halves together)
+  const unsigned long long p0 = 0xD2511F53ull * c.x;
+  const unsigned long long p1 = 0xCD9E8D57ull * c.z;
+  return make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ kx, (uint32_t)p1,
+                    (uint32_t)(p0 >> 32) ^ c.w ^ ky, (uint32_t)p0);
+}
+
+// Any counter and key (the generator as such, for its check against the
+// oracle).
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
@@ -24,13 +34,19 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
       k.x += 0x9E3779B9u;
       k.y += 0xBB67AE85u;
     }
-    // one 32 x 32 -> 64-bit product each (high and low halves together)
-    const unsigned long long p0 = 0xD2511F53ull * c.x;
-    const unsigned long long p1 = 0xCD9E8D57ull * c.z;
-    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
-    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
-    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    c = philox_round(c, k.x, k.y);
   }
+  return c;
+}
+
+// The photons' streams: key (seed lo, seed hi) with its schedule from the
+// run's parameters, counter (photon id lo, photon id hi, block, event id lo).
+// Block 0 is the birth, block n >= 1 step n.
+__device__ __forceinline__ uint4 photon_block(const RunDev& R, uint32_t pid_lo, uint32_t pid_hi,
+                                              uint32_t block, uint32_t ev_lo) {
+  uint4 c = make_uint4(pid_lo, pid_hi, block, ev_lo);
+#pragma unroll
+  for (int r = 0; r < 10; ++r) c = philox_round(c, R.key_x[r], R.key_y[r]);
   return c;
 }
 
@@ -138,17 +154,64 @@ __device__ __forceinline__ int layer_at(const IceDev& I, float z, float w) {
 // with the local scattering coefficient and the photon's remaining tau_a with
 // the local absorption coefficient, crossing layer boundaries as it goes; it
 // ends at the scatter point or the absorption point (tie: absorption).
+//
+// Layers are 10 m and steps ~2 m, so a step crosses at most one boundary in
+// all but ~0.5 % of its crossings; but some lane of a warp crosses in ~90 %
+// of the warp's steps, and a loop pass for those few lanes cost the whole
+// warp.  So the current layer and the next one are evaluated together,
+// without branches (the next as if the boundary were crossed; its value is
+// discarded when it is not), and only a step that leaves the next layer as
+// well continues in the loop.  Each quantity is formed by the same operations
+// as in a layer-by-layer loop, so the results are those of the loop.
 __device__ __forceinline__ float walk(const float4* __restrict__ lay, const IceDev& I, float z,
                                       float w, int& layer, float tau_s, float& tau_a,
                                       bool& absorb, uint32_t& crossings) {
   const float inv_w = fast_rcp(w);
-  float zc = z;
-  float S = 0.0f;
+  const bool down = w < 0.0f;
+  // layer 1: the current one; the boundary ahead (none at the table's edge,
+  // or when level)
+  const float4 L1 = lay[layer];
+  const int l2 = layer + (down ? 1 : -1);
+  const bool has1 = down ? (layer < I.L - 1) : (w > 0.0f && layer > 0);
+  const float4 L2 = lay[has1 ? l2 : layer];
+  const float zb1 = fmaf(-(float)(down ? layer + 1 : layer), I.dz, I.z_top);
+  const float ell1 = fmaxf(has1 ? (zb1 - z) * inv_w : PP_INF, 0.0f);
+  const float ds1 = (L1.x > 0.0f) ? tau_s * L1.z : PP_INF;
+  const float da1 = (L1.y > 0.0f) ? tau_a * L1.w : PP_INF;
+  const bool ab1 = da1 <= ds1 && da1 <= ell1;
+  const bool cross1 = !ab1 && !(ds1 <= ell1);
+  // layer 2: what remains of the depths after crossing layer 1
+  const float ts2 = fmaxf(0.0f, fmaf(-L1.x, ell1, tau_s));
+  const float ta2 = fmaxf(0.0f, fmaf(-L1.y, ell1, tau_a));
+  const bool has2 = down ? (l2 < I.L - 1) : (w > 0.0f && l2 > 0);
+  const float zb2 = fmaf(-(float)(down ? l2 + 1 : l2), I.dz, I.z_top);
+  const float ell2 = fmaxf(has2 ? (zb2 - zb1) * inv_w : PP_INF, 0.0f);
+  const float ds2 = (L2.x > 0.0f) ? ts2 * L2.z : PP_INF;
+  const float da2 = (L2.y > 0.0f) ? ta2 * L2.w : PP_INF;
+  const bool ab2 = da2 <= ds2 && da2 <= ell2;
+  const bool cross2 = !ab2 && !(ds2 <= ell2);
+  if (!(cross1 && cross2)) {
+    absorb = cross1 ? ab2 : ab1;
+    const float d1 = ab1 ? da1 : ds1;
+    const float d2 = ab2 ? da2 : ds2;
+    const float taf1 = ab1 ? 0.0f : fmaxf(0.0f, fmaf(-L1.y, ds1, tau_a));
+    const float taf2 = ab2 ? 0.0f : fmaxf(0.0f, fmaf(-L2.y, ds2, ta2));
+    tau_a = cross1 ? taf2 : taf1;
+    crossings += cross1 ? 1u : 0u;
+    layer = cross1 ? l2 : layer;
+    return cross1 ? ell1 + d2 : d1;
+  }
+  // rare: beyond the second layer, one layer per pass.  (Written out again
+  // rather than shared with the two layers above: that form compiled to a
+  // 0.5 % slower kernel.)
+  crossings += 2;
+  float S = ell1 + ell2;
+  tau_s = fmaxf(0.0f, fmaf(-L2.x, ell2, ts2));
+  tau_a = fmaxf(0.0f, fmaf(-L2.y, ell2, ta2));
+  float zc = zb2;
+  layer = l2 + (down ? 1 : -1);
   for (;;) {
     const float4 L = lay[layer];
-    // distance to the boundary ahead, as selects rather than branches (the
-    // branchy form cost 5 % of the batched kernel's time)
-    const bool down = w < 0.0f;
     const bool has = down ? (layer < I.L - 1) : (w > 0.0f && layer > 0);
     const float zb = fmaf(-(float)(down ? layer + 1 : layer), I.dz, I.z_top);
     float ell = has ? (zb - zc) * inv_w : PP_INF;
@@ -400,11 +463,10 @@ struct Photon {
   // segment, path length so far, emitting source
   float t_emit, path;
   int src;
-  // conservative budgets (negative: unknown): a ball of radius wb about the
-  // position lies inside the world; no horizontal move shorter than cb
-  // reaches a string.  They shrink by each step's length, so most steps
-  // skip the world-exit and cell-grid tests.
-  float wb, cb;
+  // conservative budget (negative: unknown): no horizontal move shorter than
+  // cb reaches a string.  It shrinks by each step's horizontal length, so
+  // most steps skip the cell-grid test.
+  float cb;
 };
 
 // a2: birth from Philox block 0 -- point on the emitting segment, direction
@@ -412,8 +474,7 @@ struct Photon {
 // optical depth the photon carries.  Returns false for a malformed source.
 __device__ __forceinline__ bool birth(Photon& ph, const pp_source& s, const IceDev& I,
                                       const RunDev& R) {
-  const uint4 x = philox4x32_10(make_uint4(ph.pid_lo, ph.pid_hi, 0u, 0u),
-                                make_uint2(R.seed_lo, ph.ev_lo));
+  const uint4 x = photon_block(R, ph.pid_lo, ph.pid_hi, 0u, ph.ev_lo);
   float sdx = s.dx, sdy = s.dy, sdz = s.dz;
   const float nn = fmaf(sdx, sdx, fmaf(sdy, sdy, sdz * sdz));
   if (nn > 0.0f) {
@@ -446,7 +507,6 @@ __device__ __forceinline__ bool birth(Photon& ph, const pp_source& s, const IceD
   }
   ph.tau_a = neg_log(u01f(x.w));
   ph.n = 0;
-  ph.wb = -1.0f;
   ph.cb = -1.0f;
   const bool ok = s.type <= PP_SRC_CASCADE && isfinite(ph.px) && isfinite(ph.py) &&
                   isfinite(ph.pz) && nn > 0.0f && s.length >= 0.0f;
@@ -459,21 +519,22 @@ __device__ __forceinline__ int photon_step(Photon& ph, const IceDev& I, const Ge
                                            const Tables& T, const RunDev& R,
                                            uint32_t& crossings, uint32_t& slow) {
   ph.n += 1;
-  const uint4 x = philox4x32_10(make_uint4(ph.pid_lo, ph.pid_hi, ph.n, 0u),
-                                make_uint2(R.seed_lo, ph.ev_lo));
+  const uint4 x = photon_block(R, ph.pid_lo, ph.pid_hi, ph.n, ph.ev_lo);
   const float tau_s = neg_log(u01f(x.x));
   int layer = ph.layer;
   float tau_a = ph.tau_a;
   bool absorb;
   const float S = walk(T.layer, I, ph.pz, ph.dz, layer, tau_s, tau_a, absorb, crossings);
-  // world exit: +inf while the step provably stays inside, which gives the
-  // same decisions as the exact distance (only "t_exit > S" matters then);
-  // the 1 cm margin exceeds the FP32 error of the test
+  // world exit: +inf while the step provably stays inside (shorter than the
+  // radius of a ball about the start that lies in the world), which gives
+  // the same decisions as the exact distance (only "t_exit > S" matters
+  // then); the 1 cm margin exceeds the FP32 error of the test.  The ball is
+  // measured on every step: a few converged instructions cost less than a
+  // budget carried across steps, whose re-measures some lane of the warp
+  // needed in most steps
   float tw = PP_INF;
-  if (!(S + 0.01f < ph.wb)) {
-    ph.wb = world_inner(G, ph.px, ph.py, ph.pz);
-    if (!(S + 0.01f < ph.wb)) tw = world_exit(G, ph.px, ph.py, ph.pz, ph.dx, ph.dy, ph.dz);
-  }
+  if (!(S + 0.01f < world_inner(G, ph.px, ph.py, ph.pz)))
+    tw = world_exit(G, ph.px, ph.py, ph.pz, ph.dx, ph.dy, ph.dz);
   const float St = fminf(S, tw);
   // DOM test, skipped while the step's horizontal length is inside the budget
   const float lxy = St * fast_sqrt(fmaf(ph.dx, ph.dx, ph.dy * ph.dy));
@@ -488,7 +549,6 @@ __device__ __forceinline__ int photon_step(Photon& ph, const IceDev& I, const Ge
   if (tw <= S) return kEscaped;
   if (absorb) return kAbsorbed;
   ph.path += S;
-  ph.wb -= S + 1e-4f;
   ph.cb -= lxy + 1e-4f;
   ph.px = fmaf(S, ph.dx, ph.px);
   ph.py = fmaf(S, ph.dy, ph.py);

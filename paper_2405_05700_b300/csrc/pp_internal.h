@@ -124,7 +124,11 @@ struct WorkDev {
 };
 
 struct RunDev {
-  uint32_t seed_lo;
+  // Philox key schedule of the run: round r's key words (seed lo + r W0,
+  // seed hi + r W1), precomputed on the host.  The key is the same for every
+  // photon (the event id sits in the counter), so the rounds read their keys
+  // as kernel-parameter constants instead of bumping a per-lane key.
+  uint32_t key_x[10], key_y[10];
   uint32_t max_steps;
   float cos_cherenkov, sin_cherenkov;
   int refill;                 // persistent: refill once this many lanes are idle (with the

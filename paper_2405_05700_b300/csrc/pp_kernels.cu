@@ -312,7 +312,6 @@ __device__ __forceinline__ void ring_take(const uint32_t* ring, int slot, Photon
   }
   ph.path = 0.0f;
   ph.n = 0;
-  ph.wb = -1.0f;
   ph.cb = -1.0f;
 }
 
