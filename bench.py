@@ -60,13 +60,14 @@ LANES_PER_SM = 128        # 4 schedulers x 32 lanes issue one instruction per cl
 #             rsqrt of the cone rotation and the log of -ln u = 4 SFU; the remaining 42 FP32
 FP32_OPS = {"step": 82, "crossing": 11, "birth": 42}
 SFU_OPS = {"step": 9, "crossing": 0, "birth": 4}
-# The kernel skips the world-exit (17) and cell (19) tests on steps that stay
-# inside their conservative budgets.  Per step it re-measures the world budget
-# on 5.94 % of steps (8 ops: distance to the cylinder), takes the exact world
-# exit on 0.63 %, the clearance-cell lookup on 5.86 % and the point clearance
-# on 0.37 % (12 ops): rates counted by an instrumented build of the current
-# kernel on the 1000-event batch.  The work the kernel executes per step is so
-OPS_PER_STEP_EXECUTED = (OPS_PER_STEP - 17 - 19 + 0.0594 * 8 + 0.0063 * 17 + 0.0586 * 19
+# The kernel measures the distance to the world cylinder on every step (8 of the
+# world exit's 17 ops) and takes the exact world exit only on the 0.63 % of steps
+# that may leave; it skips the cell test (19) on steps that stay inside their
+# conservative horizontal budget: the clearance-cell lookup runs on 5.86 % of
+# steps and the point clearance on 0.37 % (12 ops): rates counted by an
+# instrumented build of the kernel on the 1000-event batch.  The work the kernel
+# executes per step is so
+OPS_PER_STEP_EXECUTED = (OPS_PER_STEP - 17 - 19 + 8 + 0.0063 * 17 + 0.0586 * 19
                          + 0.0037 * 12)
 
 # DRAM bytes per launch from ncu captures of the current kernels: the propagation
