@@ -4,8 +4,8 @@ gradients, written out plainly in numpy float64.
 TEST INFRASTRUCTURE ONLY (imported by tests/ and bench.py's checks); it does
 not import the CUDA library.
 
-The network (the surrogate has no counterpart in the paper; its definition is
-the task's: BF16 weights, FP32 accumulation, Poisson mean output):
+The network (the surrogate has no counterpart in the paper; it is a BF16
+multilayer perceptron with FP32 accumulation whose output is a Poisson mean):
     h1 = act(W1 x + b1), h_l = act(W_l h_{l-1} + b_l) (l = 2..4),
     z = w5 . h4 + b5,  lambda = n_photons * softplus(z),
     loss = mean over pairs of (lambda - n ln lambda),
