@@ -183,11 +183,25 @@ def _trace_both(prop, orc, geom, ice, batch_sources, ids, seed=0, event_id=0):
            (out_o, ns_o, birth_o, tr_o, mg_o)
 
 
-def _check_trajectories(g, o, max_flip_frac):
+def _grazing(birth, tr, i, j, limit=1e-3):
+    """Whether one of photon i's first j + 1 segments (birth -> scatter points)
+    runs within |w| < limit of horizontal in the oracle's trajectory."""
+    pts = np.vstack([birth[i, :3], tr[i, : j + 1]])
+    seg = np.diff(pts, axis=0)
+    ln = np.linalg.norm(seg, axis=1)
+    ok = ln > 0
+    return bool(np.any(np.abs(seg[ok, 2]) < limit * ln[ok]))
+
+
+def _check_trajectories(g, o, max_flip_frac, grazing_ok=False):
     """Births and the first 10 scatter points agree to 1e-4 * max(|p|, 1 m);
     photons whose first-10 history differs are rarer than max_flip_frac and
     each differs at a step whose decision (in the oracle) was within 1e-3 m of
-    flipping; whole-life outcomes differ for at most 1e-3 of the photons."""
+    flipping -- or, with grazing_ok, after a nearly horizontal segment
+    (|w| < 1e-3): a layer boundary's distance is (z_b - z) / w, so the FP32
+    position's rounding (~ulp(z)) reaches it magnified by 1 / |w|, and over
+    thin layers such crossings are common.  Whole-life outcomes differ for at
+    most 1e-3 of the photons."""
     out_g, ns_g, birth_g, tr_g = g
     out_o, ns_o, birth_o, tr_o, mg_o = o
     n = len(out_g)
@@ -203,7 +217,8 @@ def _check_trajectories(g, o, max_flip_frac):
     assert len(off) <= max(1, max_flip_frac * n), (len(off), n)
     for i in off:
         j = int(np.argmax(~agree[i]))          # first scatter index that differs
-        assert mg_o[i, j] < 1e-3, (i, j, mg_o[i, j], out_g[i], out_o[i], ns_g[i], ns_o[i])
+        assert mg_o[i, j] < 1e-3 or (grazing_ok and _grazing(birth_o, tr_o, i, j)), \
+            (i, j, mg_o[i, j], out_g[i], out_o[i], ns_g[i], ns_o[i])
     diff = (out_g != out_o) | (ns_g != ns_o)
     assert diff.sum() <= max(2, 1e-3 * n), (diff.sum(), n)
     return len(off), int(diff.sum())
@@ -225,6 +240,28 @@ def test_trajectories_cherenkov_bundle(full, orc):
     g, o = _trace_both(full, orc, W.geometry_full(), W.ice_full(), src, ids,
                        event_id=int(b.event_ids[e]))
     _check_trajectories(g, o, 1e-4)
+
+
+def test_trajectories_thin_layers(pp, orc):
+    """Layers of 1.5 m with independent coefficients: a step (mean 2 m at
+    b = 0.5 / m) often crosses two or more boundaries, so the walk's branch-free
+    two-layer part and its loop beyond the second layer both run on many
+    steps.  Same-stream trajectories against the oracle."""
+    rng = np.random.default_rng(77)
+    n_layers = 800
+    ice = W.Ice(rng.uniform(0.02, 0.1, n_layers).astype(np.float32),
+                rng.uniform(0.005, 0.02, n_layers).astype(np.float32), 1350.0, 1.5, 0.9)
+    geom = W.geometry_tiny()
+    b = W.sources_tiny()
+    ids = np.arange(50_000, dtype=np.uint64)
+    with pp.Propagator(geom, ice, seed=3) as prop:
+        g, o = _trace_both(prop, orc, geom, ice, b.sources, ids, seed=3)
+        pp.pp_get_path_stats(prop.ctx)
+        hb, cb = prop.propagate_batch(b)
+        steps, crossings, _, _ = pp.pp_get_path_stats(prop.ctx)
+    _check_trajectories(g, o, 1e-4, grazing_ok=True)
+    assert int(hb.sum() + cb[:, 0].sum() + cb[:, 1].sum()) == b.total_photons()
+    assert crossings > 0.5 * steps, (crossings, steps)   # many steps cross 2+ boundaries
 
 
 def test_photon_ids_beyond_32_bits(tiny, orc):
