@@ -69,8 +69,8 @@ __device__ __forceinline__ float tanh_approx(float x) {
   return y;
 }
 
-// silu(z) = z sigmoid(z) = h (1 + tanh h) with h = z / 2: one SFU operation.
-__device__ __forceinline__ float silu_half(float h) { return fmaf(h, tanh_approx(h), h); }
+// silu(z) = z sigmoid(z) = h (1 + tanh h) with h = z / 2: one SFU operation
+// (the epilogue evaluates h tanh h + h with ffma2, two columns at a time).
 
 __device__ __forceinline__ float softplus(float z) { return z > 20.0f ? z : log1pf(__expf(z)); }
 
@@ -80,6 +80,22 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 }
 
 __device__ __forceinline__ float silu_exact(float z) { return z / (1.0f + __expf(-z)); }
+
+// Two FP32 fused multiply-adds in one instruction (PTX fma.rn.f32x2, sm_100 and
+// later): d.x = a.x b.x + c.x, d.y = a.y b.y + c.y, each rounded to nearest as
+// fmaf is, so the results are those of two fmaf calls.  The epilogue issues
+// half as many FMA instructions, which leaves more issue slots on its
+// schedulers to the producer and MMA threads of the weight ring.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  unsigned long long ra, rb, rc, rd;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(rc) : "f"(c.x), "f"(c.y));
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(rd) : "l"(ra), "l"(rb), "l"(rc));
+  float2 d;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
+  return d;
+}
 
 __device__ __forceinline__ void epi_ld(uint32_t taddr, uint32_t (&r)[16]) { tc::tmem_ld16_nowait(taddr, r); }
 
@@ -303,19 +319,31 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
 #pragma unroll
           for (int j4 = 0; j4 < kEpiCols / 4; ++j4) {
             const float4 hb = *reinterpret_cast<const float4*>(hbias + c0 + 4 * j4);
-            const float hz[4] = {fmaf(__uint_as_float(raw[4 * j4 + 0]), 0.5f, hb.x),
-                                 fmaf(__uint_as_float(raw[4 * j4 + 1]), 0.5f, hb.y),
-                                 fmaf(__uint_as_float(raw[4 * j4 + 2]), 0.5f, hb.z),
-                                 fmaf(__uint_as_float(raw[4 * j4 + 3]), 0.5f, hb.w)};
+            // z / 2 = acc / 2 + b / 2, two columns per instruction
+            const float2 h01 = ffma2(make_float2(__uint_as_float(raw[4 * j4 + 0]),
+                                                 __uint_as_float(raw[4 * j4 + 1])),
+                                     make_float2(0.5f, 0.5f), make_float2(hb.x, hb.y));
+            const float2 h23 = ffma2(make_float2(__uint_as_float(raw[4 * j4 + 2]),
+                                                 __uint_as_float(raw[4 * j4 + 3])),
+                                     make_float2(0.5f, 0.5f), make_float2(hb.z, hb.w));
+            const float hz[4] = {h01.x, h01.y, h23.x, h23.y};
             float y[4];
+            if (kMode == kModeSiluFast) {
+              // silu(2h) = h (1 + tanh h) = h tanh h + h, two columns per FMA
+              const float2 y01 = ffma2(h01, make_float2(tanh_approx(h01.x), tanh_approx(h01.y)), h01);
+              const float2 y23 = ffma2(h23, make_float2(tanh_approx(h23.x), tanh_approx(h23.y)), h23);
+              y[0] = y01.x;
+              y[1] = y01.y;
+              y[2] = y23.x;
+              y[3] = y23.y;
+            } else {
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
-              if (kMode == kModeHardSwish)  // z t with t = sat(z / 6 + 1/2) = sat(h / 3 + 1/2)
-                y[i] = (hz[i] + hz[i]) * __saturatef(fmaf(hz[i], 1.0f / 3.0f, 0.5f));
-              else if (kMode == kModeSiluExact)
-                y[i] = silu_exact(hz[i] + hz[i]);
-              else
-                y[i] = silu_half(hz[i]);
+              for (int i = 0; i < 4; ++i)
+                if (kMode == kModeHardSwish)  // z t with t = sat(z / 6 + 1/2) = sat(h / 3 + 1/2)
+                  y[i] = (hz[i] + hz[i]) * __saturatef(fmaf(hz[i], 1.0f / 3.0f, 0.5f));
+                else
+                  y[i] = silu_exact(hz[i] + hz[i]);
+            }
             packed[2 * j4] = pack_bf16(y[0], y[1]);
             packed[2 * j4 + 1] = pack_bf16(y[2], y[3]);
             if (kTrain) {

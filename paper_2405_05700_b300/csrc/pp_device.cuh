@@ -50,6 +50,36 @@ __device__ __forceinline__ uint4 photon_block(const RunDev& R, uint32_t pid_lo, 
   return c;
 }
 
+// Two FP32 operations in one instruction (PTX mul.rn.f32x2 / fma.rn.f32x2,
+// sm_100 and later), each lane-half rounded to nearest exactly as FMUL / FFMA
+// is: the pairs below give the results of the scalar code, in half the
+// instructions, on a kernel bound by instruction issue.
+__device__ __forceinline__ unsigned long long pack_f2(float a, float b) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+
+__device__ __forceinline__ float2 unpack_f2(unsigned long long r) {
+  float2 d;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(r));
+  return d;
+}
+
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;"
+      : "=l"(d)
+      : "l"(pack_f2(a.x, a.y)), "l"(pack_f2(b.x, b.y)), "l"(pack_f2(c.x, c.y)));
+  return unpack_f2(d);
+}
+
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pack_f2(a.x, a.y)), "l"(pack_f2(b.x, b.y)));
+  return unpack_f2(d);
+}
+
 // uint32 -> (0, 1): top 24 bits with the lowest forced to 1, times 2^-24
 // (exact in FP32).  With j = x >> 9 that is (2j + 1) 2^-24, formed without an
 // int-to-float conversion as (1 + j 2^-23) - (1 - 2^-24): both operands and
@@ -176,18 +206,22 @@ __device__ __forceinline__ float walk(const float4* __restrict__ lay, const IceD
   const float4 L2 = lay[has1 ? l2 : layer];
   const float zb1 = fmaf(-(float)(down ? layer + 1 : layer), I.dz, I.z_top);
   const float ell1 = fmaxf(has1 ? (zb1 - z) * inv_w : PP_INF, 0.0f);
-  const float ds1 = (L1.x > 0.0f) ? tau_s * L1.z : PP_INF;
-  const float da1 = (L1.y > 0.0f) ? tau_a * L1.w : PP_INF;
+  const float2 q1 = mul2(make_float2(tau_s, tau_a), make_float2(L1.z, L1.w));
+  const float ds1 = (L1.x > 0.0f) ? q1.x : PP_INF;
+  const float da1 = (L1.y > 0.0f) ? q1.y : PP_INF;
   const bool ab1 = da1 <= ds1 && da1 <= ell1;
   const bool cross1 = !ab1 && !(ds1 <= ell1);
   // layer 2: what remains of the depths after crossing layer 1
-  const float ts2 = fmaxf(0.0f, fmaf(-L1.x, ell1, tau_s));
-  const float ta2 = fmaxf(0.0f, fmaf(-L1.y, ell1, tau_a));
+  const float2 r2 = fma2(make_float2(-L1.x, -L1.y), make_float2(ell1, ell1),
+                         make_float2(tau_s, tau_a));
+  const float ts2 = fmaxf(0.0f, r2.x);
+  const float ta2 = fmaxf(0.0f, r2.y);
   const bool has2 = down ? (l2 < I.L - 1) : (w > 0.0f && l2 > 0);
   const float zb2 = fmaf(-(float)(down ? l2 + 1 : l2), I.dz, I.z_top);
   const float ell2 = fmaxf(has2 ? (zb2 - zb1) * inv_w : PP_INF, 0.0f);
-  const float ds2 = (L2.x > 0.0f) ? ts2 * L2.z : PP_INF;
-  const float da2 = (L2.y > 0.0f) ? ta2 * L2.w : PP_INF;
+  const float2 q2 = mul2(make_float2(ts2, ta2), make_float2(L2.z, L2.w));
+  const float ds2 = (L2.x > 0.0f) ? q2.x : PP_INF;
+  const float da2 = (L2.y > 0.0f) ? q2.y : PP_INF;
   const bool ab2 = da2 <= ds2 && da2 <= ell2;
   const bool cross2 = !ab2 && !(ds2 <= ell2);
   if (!(cross1 && cross2)) {
@@ -417,8 +451,12 @@ __device__ __forceinline__ void hg_angle(const IceDev& I, float u, float& mu, fl
   const float den = fmaf(I.c3, u, I.c2);        // 1 - g + 2gu
   const float inv = fast_rcp(den);
   const float t = I.c1 * inv;
-  const float omm = I.c2 * (1.0f - u) * (t + I.c2) * inv;        // 1 - mu
-  const float opm = (2.0f - I.c2) * u * ((2.0f - I.c2) + t) * inv;  // 1 + mu
+  // (1 - mu, 1 + mu) = (c2 (1 - u) (t + c2) inv, (2 - c2) u ((2 - c2) + t) inv),
+  // the products taken left to right
+  const float2 p1 = mul2(make_float2(I.c2, 2.0f - I.c2), make_float2(1.0f - u, u));
+  const float2 p2 = mul2(p1, make_float2(t + I.c2, (2.0f - I.c2) + t));
+  const float2 p3 = mul2(p2, make_float2(inv, inv));
+  const float omm = p3.x, opm = p3.y;
   // both forms are positive (1 - g, 1 - u, t, u and 1 - g + 2gu are), so mu
   // lies in [-1, 1] and (1 - mu)(1 + mu) >= 0 without clamps
   mu = (omm < opm) ? 1.0f - omm : opm - 1.0f;
@@ -445,8 +483,14 @@ __device__ __forceinline__ void rotate(float& dx, float& dy, float& dz, float mu
   const float it = fast_rsqrt(q);
   const float tmp = q * it;
   const bool pole = fabsf(dz) > 0.99999f;
-  const float gx = fmaf(st * fmaf(dx * dz, cp, -dy * sp), it, dx * mu);
-  const float gy = fmaf(st * fmaf(dy * dz, cp, dx * sp), it, dy * mu);
+  // g_xy = st (d_xy d_z cos phi + (-d_y, d_x) sin phi) / sqrt(q) + d_xy mu, in pairs
+  const float2 a2 = mul2(make_float2(dx, dy), make_float2(dz, dz));
+  const float2 b2 = mul2(make_float2(-dy, dx), make_float2(sp, sp));
+  const float2 c2 = fma2(a2, make_float2(cp, cp), b2);
+  const float2 e2 = mul2(make_float2(st, st), c2);
+  const float2 m2 = mul2(make_float2(dx, dy), make_float2(mu, mu));
+  const float2 g2 = fma2(e2, make_float2(it, it), m2);
+  const float gx = g2.x, gy = g2.y;
   const float gz = fmaf(-st * cp, tmp, dz * mu);
   const float ox = pole ? st * cp : gx;
   const float oy = pole ? st * sp : gy;
