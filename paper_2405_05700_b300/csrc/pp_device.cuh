@@ -207,9 +207,11 @@ __device__ __forceinline__ float walk(const float4* __restrict__ lay, const IceD
   const float zb1 = fmaf(-(float)(down ? layer + 1 : layer), I.dz, I.z_top);
   const float ell1 = fmaxf(has1 ? (zb1 - z) * inv_w : PP_INF, 0.0f);
   const float2 q1 = mul2(make_float2(tau_s, tau_a), make_float2(L1.z, L1.w));
-  const float ds1 = (L1.x > 0.0f) ? q1.x : PP_INF;
-  const float da1 = (L1.y > 0.0f) ? q1.y : PP_INF;
-  const bool ab1 = da1 <= ds1 && da1 <= ell1;
+  // the layer table holds 1/b = inf (1/a = inf) for a layer without scattering
+  // (absorption); tau * inf is inf, or NaN for tau = 0, which fminf maps to inf
+  const float ds1 = fminf(q1.x, PP_INF);
+  const float da1 = fminf(q1.y, PP_INF);
+  const bool ab1 = da1 <= fminf(ds1, ell1);
   const bool cross1 = !ab1 && !(ds1 <= ell1);
   // layer 2: what remains of the depths after crossing layer 1
   const float2 r2 = fma2(make_float2(-L1.x, -L1.y), make_float2(ell1, ell1),
@@ -220,9 +222,9 @@ __device__ __forceinline__ float walk(const float4* __restrict__ lay, const IceD
   const float zb2 = fmaf(-(float)(down ? l2 + 1 : l2), I.dz, I.z_top);
   const float ell2 = fmaxf(has2 ? (zb2 - zb1) * inv_w : PP_INF, 0.0f);
   const float2 q2 = mul2(make_float2(ts2, ta2), make_float2(L2.z, L2.w));
-  const float ds2 = (L2.x > 0.0f) ? q2.x : PP_INF;
-  const float da2 = (L2.y > 0.0f) ? q2.y : PP_INF;
-  const bool ab2 = da2 <= ds2 && da2 <= ell2;
+  const float ds2 = fminf(q2.x, PP_INF);
+  const float da2 = fminf(q2.y, PP_INF);
+  const bool ab2 = da2 <= fminf(ds2, ell2);
   const bool cross2 = !ab2 && !(ds2 <= ell2);
   if (!(cross1 && cross2)) {
     absorb = cross1 ? ab2 : ab1;
@@ -491,7 +493,8 @@ __device__ __forceinline__ void rotate(float& dx, float& dy, float& dz, float mu
   const float2 m2 = mul2(make_float2(dx, dy), make_float2(mu, mu));
   const float2 g2 = fma2(e2, make_float2(it, it), m2);
   const float gx = g2.x, gy = g2.y;
-  const float gz = fmaf(-st * cp, tmp, dz * mu);
+  const float2 zz2 = mul2(make_float2(-st, dz), make_float2(cp, mu));
+  const float gz = fmaf(zz2.x, tmp, zz2.y);
   const float ox = pole ? st * cp : gx;
   const float oy = pole ? st * sp : gy;
   dx = ox;
