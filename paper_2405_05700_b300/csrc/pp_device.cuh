@@ -183,7 +183,9 @@ __device__ __forceinline__ int layer_at(const IceDev& I, float z, float w) {
 // distance to the next scatter is a Monte Carlo draw.  The step consumes tau_s
 // with the local scattering coefficient and the photon's remaining tau_a with
 // the local absorption coefficient, crossing layer boundaries as it goes; it
-// ends at the scatter point or the absorption point (tie: absorption).
+// ends at the scatter point or the absorption point (tie: absorption).  On
+// return tau_a holds what is left after a scatter; after an absorption its
+// value is unspecified (the photon ends there).
 //
 // Layers are 10 m and steps ~2 m, so a step crosses at most one boundary in
 // all but ~0.5 % of its crossings; but some lane of a warp crosses in ~90 %
@@ -230,8 +232,9 @@ __device__ __forceinline__ float walk(const float4* __restrict__ lay, const IceD
     absorb = cross1 ? ab2 : ab1;
     const float d1 = ab1 ? da1 : ds1;
     const float d2 = ab2 ? da2 : ds2;
-    const float taf1 = ab1 ? 0.0f : fmaxf(0.0f, fmaf(-L1.y, ds1, tau_a));
-    const float taf2 = ab2 ? 0.0f : fmaxf(0.0f, fmaf(-L2.y, ds2, ta2));
+    // tau_a after a scatter (an absorbed photon's tau_a is never read again)
+    const float taf1 = fmaxf(0.0f, fmaf(-L1.y, ds1, tau_a));
+    const float taf2 = fmaxf(0.0f, fmaf(-L2.y, ds2, ta2));
     tau_a = cross1 ? taf2 : taf1;
     crossings += cross1 ? 1u : 0u;
     layer = cross1 ? l2 : layer;
