@@ -446,13 +446,11 @@ __device__ __forceinline__ int first_hit_brute(const GeomDev& G, float px, float
 // the algebraically equal, cancellation-free forms
 //   1 - mu = (1-g)(1-u)(t + 1 - g) / (1 - g + 2gu)
 //   1 + mu = (1+g) u (1 + g + t) / (1 - g + 2gu)
-// (1 - u is exact in FP32), and sin(theta) = sqrt((1 - mu)(1 + mu)).
+// (1 - u is exact in FP32), and sin(theta) = sqrt((1 - mu)(1 + mu)).  The
+// same forms cover g = 0 (isotropic): t = 1, 1 - mu = 2(1 - u), 1 + mu = 2u,
+// so no branch is taken on g (a uniform branch on the step cost 1 % of the
+// batched kernel's time).
 __device__ __forceinline__ void hg_angle(const IceDev& I, float u, float& mu, float& st) {
-  if (I.g == 0.0f) {
-    mu = fmaf(2.0f, u, -1.0f);
-    st = 2.0f * fast_sqrt(u * (1.0f - u));
-    return;
-  }
   const float den = fmaf(I.c3, u, I.c2);        // 1 - g + 2gu
   const float inv = fast_rcp(den);
   const float t = I.c1 * inv;
