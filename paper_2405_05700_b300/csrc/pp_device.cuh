@@ -384,15 +384,13 @@ __device__ __forceinline__ void test_string(const GeomDev& G, const Tables& T, i
 // is searched.
 // clear_out (optional) receives the larger of the two clearances: no
 // horizontal displacement shorter than it reaches a string.
+// A detector without DOMs needs no special case: its grid has no strings,
+// the full clearance everywhere and empty cell lists.
 __device__ __forceinline__ int first_hit_grid(const GeomDev& G, const Tables& T, float px,
                                               float py, float pz, float dx, float dy, float dz,
                                               float S, float& t_out, uint32_t& slow,
                                               float* clear_out = nullptr) {
   t_out = PP_INF;
-  if (G.n_dom == 0) {
-    if (clear_out) *clear_out = PP_INF;
-    return -1;
-  }
   const float dxy2 = fmaf(dx, dx, dy * dy);
   const float L2 = S * S * dxy2;  // squared horizontal length of the step
   const int ix = min(max(__float2int_rd((px - G.gx0) * G.inv_cell), 0), G.nx - 1);
