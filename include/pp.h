@@ -475,7 +475,10 @@ int pp_mlp_features(pp_mlp* mlp, const pp_source* d_src, const int32_t* d_pair_s
 /* d_lambda[i] = predicted photons on pair i given d_nph[i] photons emitted,
  * by the fused inference kernel (rows mode).  d_feat[n][32] BF16, 16-byte
  * aligned.  Enqueued on `stream` (NULL: the context's stream); a device error
- * (a bounded wait that ran out) is reported by pp_mlp_sync.
+ * (a bounded wait that ran out) is reported by pp_mlp_sync.  The first
+ * inference call after the weights change (pp_mlp_set_params, set_state, a
+ * train step) reads the hidden biases back to the host, for the kernel's
+ * launch parameters, and so waits for `stream` once.
  * Errors: PP_EINVAL (null or misaligned pointer), PP_ECUDA. */
 int pp_mlp_forward(pp_mlp* mlp, const uint16_t* d_feat, const float* d_nph, int64_t n,
                    float* d_lambda, void* stream);
@@ -516,7 +519,8 @@ int pp_mlp_loss(pp_mlp* mlp, double* loss);
  * Pairs farther apart than r_max (the distance range the network was trained
  * on) count zero; the pairs within it are found on the device and evaluated
  * by the fused kernel (pairs mode) in passes of at most max_rows pairs.  The
- * call waits for each pass's pair count, so it returns once the last pass is
+ * call waits for each pass's pair count (and, after the weights change, for
+ * the biases, as pp_mlp_forward does), so it returns once the last pass is
  * enqueued on `stream` (NULL: the context's stream).
  * Errors: PP_EINVAL (also: one source with more than max_rows pairs), PP_ECUDA. */
 int pp_mlp_dom_sums(pp_mlp* mlp, const pp_source* d_src, int64_t n_src, const float* d_nph_src,

@@ -9,11 +9,14 @@
 // A layer's input (features, then BF16 activations) sits in shared memory as
 // the MMA's A operand; the weights (W1 as one 16 KB chunk, then 4 chunks of
 // 32 KB per hidden layer) stream from global memory (L2-resident, shared by
-// every CTA) through a 2-stage ring filled by bulk copies, once per half.
+// every CTA) through a 3-stage ring filled by bulk copies, once per half.
 // Each chunk costs a fixed round trip (its MMAs' commit frees the stage, the
 // producer's copy refills it), so the ring holds few large chunks: 32 KB
-// chunks run the kernel 13 % faster than 16 KB ones in 5 stages, and 8 KB
-// ones in 10 stages are 65 % slower.
+// chunks in 2 stages run the kernel 13 % faster than 16 KB ones in 5 stages
+// (8 KB ones in 10 stages are 65 % slower), and a third 32 KB stage another
+// 7 %.  The third stage takes the shared memory of the halved biases, which
+// inference passes as a launch parameter (read through the constant cache;
+// the training forward keeps them in shared memory and two stages).
 //
 //   warps 0-15 : epilogue.  Warp w serves half (w / 4) % 2, TMEM lanes
 //                32 (w % 4) .. + 31 (its 32 rows) and columns 128 (w / 8) .. + 127:
@@ -43,7 +46,10 @@ constexpr int kHalf = 128;                 // rows per MMA
 constexpr int kChunkK = 64;                // K per weight chunk of a hidden layer
 constexpr int kChunksPerLayer = kHid / kChunkK;
 constexpr int kChunkBytes = kHid * kChunkK * 2;
-constexpr int kStages = 2;
+// weight-ring stages: three 32 KB chunks in flight for inference and for the
+// backward pass; two for the training forward, whose halved biases take
+// shared memory (inference reads them from its launch parameter)
+constexpr int kStagesMax = 3;
 constexpr int kW1Bytes = kHid * kIn * 2;   // W1: one chunk of K = kIn
 constexpr int kHiddenGemms = kLayers - 1;  // layers 2..4
 constexpr int kChunksPerLayerSet = 1 + kHiddenGemms * kChunksPerLayer;  // W1..W4
@@ -65,9 +71,22 @@ constexpr uint32_t kWaitTries = 1u << 22;
 constexpr uint32_t kOffH = 0;                                  // 2 x [128][256] BF16 (features alias)
 constexpr uint32_t kHalfBytes = kHalf * kHid * 2;
 constexpr uint32_t kOffRing = kOffH + 2 * kHalfBytes;
-constexpr uint32_t kOffPar = kOffRing + kStages * kChunkBytes;  // biases / 2 [4][256], w5 [256] (FP32)
-constexpr uint32_t kSmemBytes = kOffPar + (kLayers + 1) * kHid * 4;
-static_assert(kSmemBytes + 1024 <= 232448, "shared memory per CTA");
+template <bool kTrain>
+struct FwdLayout {
+  static constexpr int kStages = kTrain ? 2 : kStagesMax;
+  // FP32 parameters after the ring: training: biases / 2 [4][256], then w5
+  // [256]; inference: w5 only
+  static constexpr uint32_t kOffPar = kOffRing + kStages * kChunkBytes;
+  static constexpr uint32_t kW5 = kTrain ? kLayers * kHid : 0;  // w5's offset in floats
+  static constexpr uint32_t kSmemBytes = kOffPar + (kW5 + kHid) * 4;
+};
+// 2 KB of static shared memory (barriers, the head's partial sums) besides
+static_assert(FwdLayout<false>::kSmemBytes + 2048 <= 232448 &&
+                  FwdLayout<true>::kSmemBytes + 2048 <= 232448,
+              "shared memory per CTA");
+constexpr int kBwdStages = kStagesMax;
+constexpr uint32_t kBwdSmemBytes = kOffRing + kBwdStages * kChunkBytes;
+static_assert(kBwdSmemBytes + 1024 <= 232448, "shared memory per CTA");
 
 __device__ __forceinline__ float tanh_approx(float x) {
   float y;
@@ -115,7 +134,10 @@ __device__ __forceinline__ void epi_ld(uint32_t taddr, uint32_t (&r)[16]) { tc::
 //   kModeHardSwish  z * clamp(z / 6 + 1/2, 0, 1): FMA pipe only
 constexpr int kModeSiluFast = 0, kModeSiluExact = 1, kModeHardSwish = 2;
 template <bool kFromPairs, int kMode, bool kTrain = false>
-__global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
+__global__ void __launch_bounds__(kThreads, 1)
+    k_mlp_fused(FusedArgs a, const __grid_constant__ HalfBias hbias_par) {
+  using L = FwdLayout<kTrain>;
+  constexpr int kStages = L::kStages;
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kStages], empty[kStages], acc_full[2], in_ready[2], done;
   __shared__ __align__(8) uint64_t head_bar[8];  // per (half, lane quarter): partial z written
@@ -143,10 +165,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
   }
   {
     // halved biases: the epilogue forms z / 2 = acc / 2 + b / 2 in one FMA
-    float* par = reinterpret_cast<float*>(smem + kOffPar);
-    for (int i = threadIdx.x; i < kLayers * kHid; i += blockDim.x)
-      par[i] = 0.5f * a.bias[i / kHid][i % kHid];
-    for (int i = threadIdx.x; i < kHid; i += blockDim.x) par[kLayers * kHid + i] = a.w5[i];
+    // (inference: hbias_par holds them already)
+    float* par = reinterpret_cast<float*>(smem + L::kOffPar);
+    if (kTrain)
+      for (int i = threadIdx.x; i < kLayers * kHid; i += blockDim.x)
+        par[i] = 0.5f * a.bias[i / kHid][i % kHid];
+    for (int i = threadIdx.x; i < kHid; i += blockDim.x) par[L::kW5 + i] = a.w5[i];
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -253,7 +277,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
     const int r = q * 32 + lane;  // row within the half = TMEM lane
     const int c_begin = cg * kColsPerWarp;
     unsigned char* sH = smem + kOffH + h * kHalfBytes;
-    const float* par = reinterpret_cast<const float*>(smem + kOffPar);
+    const float* par = reinterpret_cast<const float*>(smem + L::kOffPar);
     const uint32_t tacc =
         tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * kHid) + (uint32_t)c_begin;
     uint64_t* hb = &head_bar[h * 4 + q];
@@ -322,8 +346,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fused(FusedArgs a) {
         ++acc_phase;
         __syncwarp();
         tc::fence_after_sync();
-        const float* hbias = par + layer * kHid + c_begin;
-        const float* w5 = par + kLayers * kHid + c_begin;
+        // the same biases for the warp's 32 rows: a broadcast from the constant
+        // cache (inference) or shared memory (training)
+        const float* hbias = (kTrain ? par : hbias_par.v) + layer * kHid + c_begin;
+        const float* w5 = par + L::kW5 + c_begin;
         constexpr bool last = decltype(last_tag)::value;
         // kEpiCols columns: bias, SiLU, BF16; into shared memory (or the head)
         auto consume = [&](const uint32_t (&raw)[kEpiCols], int c0) {
@@ -475,6 +501,7 @@ constexpr int kBwdLayers = kLayers - 1;
 constexpr int kBwdChunksPerTile = 2 * kBwdLayers * kChunksPerLayer;
 
 __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd(BwdArgs a) {
+  constexpr int kStages = kBwdStages;
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kStages], empty[kStages], acc_full[2], in_ready[2], done;
   __shared__ uint32_t tslot;
@@ -903,12 +930,12 @@ cudaError_t launch_pack_weights(const __nv_bfloat16* const* w, unsigned char* ou
 }
 
 template <bool P, int E, bool T = false>
-cudaError_t launch_variant(const FusedArgs& a, int g, cudaStream_t st) {
+cudaError_t launch_variant(const FusedArgs& a, const HalfBias& hb, int g, cudaStream_t st) {
+  constexpr uint32_t bytes = FwdLayout<T>::kSmemBytes;
   cudaError_t e = cudaFuncSetAttribute(k_mlp_fused<P, E, T>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kSmemBytes);
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  k_mlp_fused<P, E, T><<<g, kThreads, kSmemBytes, st>>>(a);
+  k_mlp_fused<P, E, T><<<g, kThreads, bytes, st>>>(a, hb);
   return cudaGetLastError();
 }
 
@@ -925,9 +952,9 @@ cudaError_t launch_mlp_bwd(const BwdArgs& a, int grid, cudaStream_t st) {
   const int64_t tiles = (a.n + kRows - 1) / kRows;
   const int g = (int)(tiles < grid ? tiles : grid);
   cudaError_t e = cudaFuncSetAttribute(k_mlp_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kSmemBytes);
+                                       (int)kBwdSmemBytes);
   if (e != cudaSuccess) return e;
-  k_mlp_bwd<<<g, kThreads, kSmemBytes, st>>>(a);
+  k_mlp_bwd<<<g, kThreads, kBwdSmemBytes, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -955,22 +982,25 @@ cudaError_t launch_rowsum_kt(const unsigned char* in, int R, int64_t n, float* o
   return cudaGetLastError();
 }
 
-cudaError_t launch_mlp_fused(const FusedArgs& a, bool from_pairs, int grid, cudaStream_t st) {
+cudaError_t launch_mlp_fused(const FusedArgs& a, const HalfBias* hb, bool from_pairs, int grid,
+                             cudaStream_t st) {
   if (a.n <= 0) return cudaSuccess;
   const int64_t tiles = (a.n + kRows - 1) / kRows;
   const int g = (int)(tiles < grid ? tiles : grid);
   const bool hs = a.act == kActHardSwish;
+  static const HalfBias unused{};  // the training forward reads a.bias
   if (a.z_out[0])  // training forward: the activation evaluated exactly
-    return hs ? launch_variant<false, kModeHardSwish, true>(a, g, st)
-              : launch_variant<false, kModeSiluExact, true>(a, g, st);
+    return hs ? launch_variant<false, kModeHardSwish, true>(a, unused, g, st)
+              : launch_variant<false, kModeSiluExact, true>(a, unused, g, st);
+  if (!hb) return cudaErrorInvalidValue;
   const int mode = hs ? kModeHardSwish : (a.exact_silu ? kModeSiluExact : kModeSiluFast);
   if (from_pairs)
-    return mode == kModeHardSwish   ? launch_variant<true, kModeHardSwish>(a, g, st)
-           : mode == kModeSiluExact ? launch_variant<true, kModeSiluExact>(a, g, st)
-                                    : launch_variant<true, kModeSiluFast>(a, g, st);
-  return mode == kModeHardSwish   ? launch_variant<false, kModeHardSwish>(a, g, st)
-         : mode == kModeSiluExact ? launch_variant<false, kModeSiluExact>(a, g, st)
-                                  : launch_variant<false, kModeSiluFast>(a, g, st);
+    return mode == kModeHardSwish   ? launch_variant<true, kModeHardSwish>(a, *hb, g, st)
+           : mode == kModeSiluExact ? launch_variant<true, kModeSiluExact>(a, *hb, g, st)
+                                    : launch_variant<true, kModeSiluFast>(a, *hb, g, st);
+  return mode == kModeHardSwish   ? launch_variant<false, kModeHardSwish>(a, *hb, g, st)
+         : mode == kModeSiluExact ? launch_variant<false, kModeSiluExact>(a, *hb, g, st)
+                                  : launch_variant<false, kModeSiluFast>(a, *hb, g, st);
 }
 
 }  // namespace mlp

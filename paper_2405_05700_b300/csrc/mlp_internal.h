@@ -138,8 +138,19 @@ struct FusedArgs {
 size_t packed_weight_bytes();
 cudaError_t launch_pack_weights(const __nv_bfloat16* const* w, unsigned char* out,
                                 cudaStream_t st);
-// grid: the CTA count cap (one CTA per SM runs at a time)
-cudaError_t launch_mlp_fused(const FusedArgs& a, bool from_pairs, int grid, cudaStream_t st);
+// The hidden layers' biases halved (b / 2, layer-major [4][256]).  Inference
+// passes them to the fused kernel as a launch parameter: its epilogue reads
+// them from the constant cache, which leaves the shared memory they would
+// take to a third stage of the weight ring.
+struct HalfBias {
+  float v[kLayers * kHid];
+};
+
+// grid: the CTA count cap (one CTA per SM runs at a time).  hb: the halved
+// biases of a.bias, required for inference; the training forward (a.z_out
+// set) reads a.bias itself and ignores hb.
+cudaError_t launch_mlp_fused(const FusedArgs& a, const HalfBias* hb, bool from_pairs, int grid,
+                             cudaStream_t st);
 
 // Fused backward of the hidden layers (training): from dz[3] (dL/dz of the
 // last hidden layer, BF16 [n][256]) and the forward's pre-activations z[0..2]

@@ -67,6 +67,10 @@ struct pp_mlp {
   // when the weights change), the pair list [max_rows]
   unsigned char* wpack = nullptr;
   int64_t weights_version = 0, packed_version = -1;
+  // inference: the hidden biases / 2, the fused kernel's launch parameter
+  // (read back from the FP32 masters when the weights change)
+  HalfBias hbias{};
+  int64_t hbias_version = -1;
   unsigned char* wpack_bwd = nullptr;  // transposed hidden weights for the backward kernel
   float* dw_part = nullptr;            // per-CTA weight-gradient partial sums
   __nv_bfloat16* bfeat = nullptr;      // batch gathered from chosen training rows [max_batch][32]
@@ -116,6 +120,21 @@ int ensure_packed(pp_mlp* m, cudaStream_t st) {
   return PP_OK;
 }
 
+// The halved biases for an inference launch.  After the weights change (set,
+// restored or trained) they are read back once, so that call waits for the
+// stream's earlier work.
+int ensure_hbias(pp_mlp* m, cudaStream_t st) {
+  if (m->hbias_version == m->weights_version) return PP_OK;
+  HalfBias raw;
+  for (int l = 0; l < kLayers; ++l)
+    PP_MLP_CUDA(cudaMemcpyAsync(raw.v + l * kHid, m->p + off_b(l), sizeof(float) * kHid,
+                                cudaMemcpyDeviceToHost, st));
+  PP_MLP_CUDA(cudaStreamSynchronize(st));
+  for (int i = 0; i < kLayers * kHid; ++i) m->hbias.v[i] = 0.5f * raw.v[i];
+  m->hbias_version = m->weights_version;
+  return PP_OK;
+}
+
 FusedArgs fused_args(pp_mlp* m) {
   FusedArgs a{};
   a.fg = m->fg;
@@ -147,7 +166,7 @@ int forward_train(pp_mlp* m, const __nv_bfloat16* x0, int n, cudaStream_t st) {
     a.h_out[l] = m->h[l];
   }
   a.x_t = reinterpret_cast<unsigned char*>(m->t2);
-  PP_MLP_CUDA(launch_mlp_fused(a, false, m->sms, st));
+  PP_MLP_CUDA(launch_mlp_fused(a, nullptr, false, m->sms, st));
   return PP_OK;
 }
 
@@ -407,13 +426,13 @@ int pp_mlp_forward(pp_mlp* m, const uint16_t* d_feat, const float* d_nph, int64_
   PP_MLP_CUDA(dev_scope.status());
   cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : m->view.stream;
   int rc;
-  if ((rc = ensure_packed(m, st))) return rc;
+  if ((rc = ensure_packed(m, st)) || (rc = ensure_hbias(m, st))) return rc;
   FusedArgs a = fused_args(m);
   a.feat = reinterpret_cast<const __nv_bfloat16*>(d_feat);
   a.n = n;
   a.nph = d_nph;
   a.lambda = d_lambda;
-  PP_MLP_CUDA(launch_mlp_fused(a, false, m->sms, st));
+  PP_MLP_CUDA(launch_mlp_fused(a, &m->hbias, false, m->sms, st));
   return PP_OK;
 }
 
@@ -521,7 +540,7 @@ int pp_mlp_dom_sums(pp_mlp* m, const pp_source* d_src, int64_t n_src, const floa
     PP_MLP_CUDA(cudaMemsetAsync(d_lambda, 0, sizeof(float) * (size_t)n_src * n_dom, st));
   if (n_dom == 0 || n_src == 0) return PP_OK;
   int rc;
-  if ((rc = ensure_packed(m, st))) return rc;
+  if ((rc = ensure_packed(m, st)) || (rc = ensure_hbias(m, st))) return rc;
   // pairs within r_max only: the network is evaluated on a compacted list
   int64_t per = 8 * (m->max_rows / n_dom);
   if (per < 1) per = 1;
@@ -553,7 +572,7 @@ int pp_mlp_dom_sums(pp_mlp* m, const pp_source* d_src, int64_t n_src, const floa
       a.nph = d_nph_src;
       a.dom_sum = d_dom_sums;
       a.lambda_out = d_lambda;
-      PP_MLP_CUDA(launch_mlp_fused(a, true, m->sms, st));
+      PP_MLP_CUDA(launch_mlp_fused(a, &m->hbias, true, m->sms, st));
     }
     s0 += ns;
   }

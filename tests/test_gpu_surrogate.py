@@ -142,6 +142,55 @@ def test_forward_matches_oracle(pp, mlp, n, exact, act):
     assert np.quantile(rel, 0.99) < 2e-2 and rel.max() < 0.1, (np.quantile(rel, 0.99), rel.max())
 
 
+def test_forward_follows_changed_biases(pp, mlp):
+    """Inference takes the hidden biases as launch parameters, read back from
+    the device parameters whenever they change: a forward pass after
+    set_params with new biases (and after a train step) equals the oracle
+    network at the new parameters, not the old ones."""
+    import torch
+    from oracle import mlp as M
+    rng = np.random.default_rng(44)
+    n = 2048
+    x, nph, counts = _batch(rng, n)
+    feat = _dev(pp.bf16_bits(x).view(np.int16))
+    d_nph = _dev(nph.astype(np.float32))
+    lam = torch.zeros(n, dtype=torch.float32, device="cuda")
+    pa = pp.mlp_init_params(3).astype(np.float32)
+    pa[-1] = -6.0
+    pb = pa.copy()
+    for k, idx in M.unpack(np.arange(M.N_PARAMS)).items():
+        if k in ("b1", "b2", "b3", "b4"):
+            i = np.asarray(idx).ravel().astype(np.int64)
+            pb[i] += rng.normal(0.0, 0.3, len(i)).astype(np.float32)
+
+    def check(p):
+        pp.pp_mlp_forward(mlp.handle, feat, d_nph, n, lam)
+        pp.pp_mlp_sync(mlp.handle)
+        ref, _ = M.forward(p.astype(np.float64), x, nph, rounding=True)
+        got = lam.cpu().numpy()
+        # rows whose softplus underflows FP32 (z < -87: lambda / photons < 1e-37)
+        # are 0 on the device; compare them absolutely
+        tiny = ref < 1e-30 * nph
+        assert np.all(got[tiny] <= 1e-30 * nph[tiny])
+        r = np.abs(got[~tiny] - ref[~tiny]) / ref[~tiny]
+        assert np.median(r) < 1e-4 and np.quantile(r, 0.99) < 2e-2, (np.median(r), np.quantile(r, 0.99))
+        return got.copy()
+
+    mlp.set_params(pa)
+    la = check(pa)
+    mlp.set_params(pb)
+    lb = check(pb)
+    assert np.median(np.abs(lb - la) / la) > 1e-2
+    pp.pp_mlp_train_step(mlp.handle, feat, d_nph, _dev(counts.astype(np.float32)), n, 1e-3)
+    pp.pp_mlp_loss(mlp.handle)
+    p1 = np.zeros(M.N_PARAMS, np.float32)
+    pp.pp_mlp_get_params(mlp.handle, p1, M.N_PARAMS)
+    l1 = check(p1)
+    # the step moved the outputs by far more than the parity tolerance
+    assert np.median(np.abs(l1 - lb) / lb) > 1e-3
+    torch.cuda.synchronize()
+
+
 @pytest.mark.parametrize("act", ["silu", "hswish"])
 def test_gradients_match_oracle(pp, mlp, act):
     from oracle import mlp as M
