@@ -283,57 +283,72 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* hb = &head_bar[h * 4 + q];
     uint32_t acc_phase = 0, head_phase = 0;
     bool ok = true;
+    // The features of a tile's rows are the first MMA's A operand (aliasing
+    // the activations).  Each thread gathers its row's part into registers
+    // (pairs: column group g computes features 16 g .. 16 g + 15; rows: column
+    // group 0 loads all 32) and stores them once the half's shared memory is
+    // free.  For the next tile that happens while the last layer's MMAs run:
+    // the gather's loads or arithmetic overlap them, the store follows the
+    // last accumulator's arrival (its MMAs no longer read the activations),
+    // and the half's next first-layer MMA may start as soon as the last
+    // layer's accumulator has been read (a fifth of the tile's time went to
+    // the feature gather between tiles before).
+    constexpr int kFeatVecs = kFromPairs ? kIn / 16 : kIn / 8;
+    uint4 fv[kFeatVecs];
+    auto gather_features = [&](int64_t tt) {
+      const int64_t frow = tt * kRows + h * kHalf + r;
+#pragma unroll
+      for (int i = 0; i < kFeatVecs; ++i) fv[i] = make_uint4(0, 0, 0, 0);
+      if (frow >= a.n) return;
+      if (kFromPairs) {
+        __align__(16) __nv_bfloat16 fb[kIn / 2];
+        const int sidx = a.ps[frow];
+        const SrcPrep P = a.sprep ? a.sprep[sidx - a.sprep_base] : source_prep(a.fg, a.src[sidx]);
+        const float4 c = a.fg.dom[a.pd[frow]];
+        if (cg == 0)
+          pair_features_half<0>(a.fg, P, c, fb);
+        else
+          pair_features_half<1>(a.fg, P, c, fb);
+#pragma unroll
+        for (int i = 0; i < kFeatVecs; ++i) fv[i] = *reinterpret_cast<const uint4*>(fb + 8 * i);
+      } else if (cg == 0) {
+#pragma unroll
+        for (int i = 0; i < kFeatVecs; ++i)
+          fv[i] = *reinterpret_cast<const uint4*>(a.feat + frow * kIn + 8 * i);
+        if (kTrain) {  // the features K-tiled, the first layer's weight-gradient operand
+#pragma unroll
+          for (int i = 0; i < kFeatVecs; ++i) {
+            const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&fv[i]);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              *reinterpret_cast<__nv_bfloat16*>(
+                  a.x_t + kt_off((uint32_t)(8 * i + j), (uint32_t)frow, kIn)) = e[j];
+          }
+        }
+      }
+    };
+    auto store_features = [&]() {
+      if (kFromPairs) {
+#pragma unroll
+        for (int i = 0; i < kFeatVecs; ++i)
+          *reinterpret_cast<uint4*>(sH + tc::tile_off(r, cg * (kIn / 2) + 8 * i, kIn)) = fv[i];
+      } else if (cg == 0) {
+#pragma unroll
+        for (int i = 0; i < kFeatVecs; ++i)
+          *reinterpret_cast<uint4*>(sH + tc::tile_off(r, 8 * i, kIn)) = fv[i];
+      }
+    };
+    if ((int64_t)blockIdx.x < n_tiles) {
+      gather_features(blockIdx.x);
+      store_features();
+      tc::fence_smem_async();
+      tc::fence_before_sync();
+      tc::mbar_arrive(&in_ready[h]);
+    }
     for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
       const int64_t row = t * kRows + h * kHalf + r;
       const bool valid = row < a.n;
-      // features of this row as the first MMA's A operand (aliasing the activations)
-      if (kFromPairs) {
-        // pairs: column group g computes features 16 g .. 16 g + 15 of the row
-        uint4 fv[kIn / 16];
-#pragma unroll
-        for (int i = 0; i < kIn / 16; ++i) fv[i] = make_uint4(0, 0, 0, 0);
-        if (valid) {
-          __align__(16) __nv_bfloat16 fb[kIn / 2];
-          const int sidx = a.ps[row];
-          const SrcPrep P = a.sprep ? a.sprep[sidx - a.sprep_base] : source_prep(a.fg, a.src[sidx]);
-          const float4 c = a.fg.dom[a.pd[row]];
-          if (cg == 0)
-            pair_features_half<0>(a.fg, P, c, fb);
-          else
-            pair_features_half<1>(a.fg, P, c, fb);
-#pragma unroll
-          for (int i = 0; i < kIn / 16; ++i) fv[i] = *reinterpret_cast<const uint4*>(fb + 8 * i);
-        }
-#pragma unroll
-        for (int i = 0; i < kIn / 16; ++i)
-          *reinterpret_cast<uint4*>(sH + tc::tile_off(r, cg * (kIn / 2) + 8 * i, kIn)) = fv[i];
-        tc::fence_smem_async();
-      } else if (cg == 0) {
-        uint4 fv[kIn / 8];
-#pragma unroll
-        for (int i = 0; i < kIn / 8; ++i) fv[i] = make_uint4(0, 0, 0, 0);
-        if (valid) {
-#pragma unroll
-          for (int i = 0; i < kIn / 8; ++i)
-            fv[i] = *reinterpret_cast<const uint4*>(a.feat + row * kIn + 8 * i);
-          if (kTrain) {  // the features K-tiled, the first layer's weight-gradient operand
-#pragma unroll
-            for (int i = 0; i < kIn / 8; ++i) {
-              const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&fv[i]);
-#pragma unroll
-              for (int j = 0; j < 8; ++j)
-                *reinterpret_cast<__nv_bfloat16*>(
-                    a.x_t + kt_off((uint32_t)(8 * i + j), (uint32_t)row, kIn)) = e[j];
-            }
-          }
-        }
-#pragma unroll
-        for (int i = 0; i < kIn / 8; ++i)
-          *reinterpret_cast<uint4*>(sH + tc::tile_off(r, 8 * i, kIn)) = fv[i];
-        tc::fence_smem_async();
-      }
-      tc::fence_before_sync();
-      tc::mbar_arrive(&in_ready[h]);
+      const bool has_next = t + gridDim.x < n_tiles;
       float zh = 0.0f;  // head: this column group's part of w5 . h4
       // one layer's epilogue; whether it is the last layer (the head, no
       // activations stored) is a compile-time argument, so the column loop
@@ -346,11 +361,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         ++acc_phase;
         __syncwarp();
         tc::fence_after_sync();
+        constexpr bool last = decltype(last_tag)::value;
+        // the last layer's MMAs have read the activations: the next tile's features
+        if (last && has_next) store_features();
         // the same biases for the warp's 32 rows: a broadcast from the constant
         // cache (inference) or shared memory (training)
         const float* hbias = (kTrain ? par : hbias_par.v) + layer * kHid + c_begin;
         const float* w5 = par + L::kW5 + c_begin;
-        constexpr bool last = decltype(last_tag)::value;
         // kEpiCols columns: bias, SiLU, BF16; into shared memory (or the head)
         auto consume = [&](const uint32_t (&raw)[kEpiCols], int c0) {
           uint32_t packed[kEpiCols / 2];
@@ -439,16 +456,18 @@ __global__ void __launch_bounds__(kThreads, 1)
           consume(rb, c0 + kEpiCols);
           if (c0 + 2 * kEpiCols < kColsPerWarp) tc::tmem_wait_ld(ra);
         }
-        if (!last) {
-          // activations written and accumulator read: the next layer may start
+        if (!last || has_next) {
+          // activations (or the next tile's features) written and the
+          // accumulator read: the half's next MMA may start
           tc::fence_smem_async();
           tc::fence_before_sync();
           tc::mbar_arrive(&in_ready[h]);
         }
-              return true;
+        return true;
       };
       bool lok = true;
       for (int layer = 0; layer < kLayers - 1 && lok; ++layer) lok = run_layer(layer, std::false_type{});
+      if (lok && has_next) gather_features(t + gridDim.x);
       if (lok) lok = run_layer(kLayers - 1, std::true_type{});
       if (!lok) ok = false;
       if (!ok) break;
