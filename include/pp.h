@@ -518,10 +518,12 @@ int pp_mlp_loss(pp_mlp* mlp, double* loss);
  * NULL, zeroed here) every pair's lambda; d_nph_src[n_src] photons per source.
  * Pairs farther apart than r_max (the distance range the network was trained
  * on) count zero; the pairs within it are found on the device and evaluated
- * by the fused kernel (pairs mode) in passes of at most max_rows pairs.  The
- * call waits for each pass's pair count (and, after the weights change, for
- * the biases, as pp_mlp_forward does), so it returns once the last pass is
- * enqueued on `stream` (NULL: the context's stream).
+ * by the fused kernel (pairs mode) in passes of at most max_rows pairs.  When
+ * n_src x DOMs <= max_rows the call is one pass and returns once it is
+ * enqueued on `stream` (NULL: the context's stream); otherwise it enqueues
+ * every pass, then waits for the passes' pair counts, and if some pass found
+ * more pairs than max_rows it starts over with fewer sources per pass (after
+ * the weights change it also waits for the biases, as pp_mlp_forward does).
  * Errors: PP_EINVAL (also: one source with more than max_rows pairs), PP_ECUDA. */
 int pp_mlp_dom_sums(pp_mlp* mlp, const pp_source* d_src, int64_t n_src, const float* d_nph_src,
                     float r_max, double* d_dom_sums, float* d_lambda, void* stream);

@@ -145,7 +145,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ uint32_t tslot;
   __shared__ int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t n_tiles = (a.n + kRows - 1) / kRows;
+  // rows: a.n, or the pair search's count in device memory capped at a.n
+  // (read here, so that the host need not wait for it)
+  const int64_t n_rows = a.n_dev ? (int64_t)min((unsigned long long)a.n, *a.n_dev) : a.n;
+  const int64_t n_tiles = (n_rows + kRows - 1) / kRows;
 
   // setup: TMEM (512 columns: both accumulators), barriers, resident parameters
   if (warp == 0) tc::tmem_alloc(&tslot, 512);
@@ -299,7 +302,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t frow = tt * kRows + h * kHalf + r;
 #pragma unroll
       for (int i = 0; i < kFeatVecs; ++i) fv[i] = make_uint4(0, 0, 0, 0);
-      if (frow >= a.n) return;
+      if (frow >= n_rows) return;
       if (kFromPairs) {
         __align__(16) __nv_bfloat16 fb[kIn / 2];
         const int sidx = a.ps[frow];
@@ -347,7 +350,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
       const int64_t row = t * kRows + h * kHalf + r;
-      const bool valid = row < a.n;
+      const bool valid = row < n_rows;
       const bool has_next = t + gridDim.x < n_tiles;
       float zh = 0.0f;  // head: this column group's part of w5 . h4
       // one layer's epilogue; whether it is the last layer (the head, no

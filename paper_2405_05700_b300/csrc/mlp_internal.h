@@ -113,6 +113,8 @@ struct FusedArgs {
   int64_t sprep_base;
   const int32_t* ps;
   const int32_t* pd;
+  // pairs mode, optional: the row count in device memory (used up to n)
+  const unsigned long long* n_dev;
   const __nv_bfloat16* feat;     // rows mode: [n][kIn]
   int64_t n;
   const unsigned char* wpack;    // W1..W4 in the ring's chunk layout

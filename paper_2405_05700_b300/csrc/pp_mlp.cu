@@ -12,7 +12,9 @@
 
 #include <cmath>
 #include <cstring>
+#include <algorithm>
 #include <string>
+#include <vector>
 
 #include "mlp_features.cuh"
 #include "mlp_internal.h"
@@ -87,6 +89,9 @@ struct pp_mlp {
   SrcPrep* sprep = nullptr;            // per-source feature part of one dom_sums pass
   int64_t sprep_cap = 0;
   // ordered pair search: per-block counts and offsets (grown on demand)
+  // dom_sums: each pass's pair count (grown on demand)
+  unsigned long long* pass_count = nullptr;
+  int64_t pass_cap = 0;
   uint32_t* near_bcount = nullptr;
   unsigned long long* near_boff = nullptr;
   int64_t near_cap = 0;
@@ -327,7 +332,7 @@ int pp_mlp_destroy(pp_mlp* m) {
   cudaDeviceSynchronize();
   void* bufs[] = {m->p,   m->g,     m->m,         m->v,  m->t1, m->t2,    m->loss, m->err,
                   m->wpack, m->wpack_bwd, m->ps, m->pd, m->count, m->ice_cum, m->dw_part,
-                  m->head_part, m->head_lpart, m->near_bcount, m->near_boff, m->bfeat,
+                  m->head_part, m->head_lpart, m->pass_count, m->near_bcount, m->near_boff, m->bfeat,
                   m->bnph, m->bcnt, m->sprep};
   for (void* b : bufs) cudaFree(b);
   for (int l = 0; l < kLayers; ++l) {
@@ -541,9 +546,66 @@ int pp_mlp_dom_sums(pp_mlp* m, const pp_source* d_src, int64_t n_src, const floa
   if (n_dom == 0 || n_src == 0) return PP_OK;
   int rc;
   if ((rc = ensure_packed(m, st)) || (rc = ensure_hbias(m, st))) return rc;
-  // pairs within r_max only: the network is evaluated on a compacted list
+  // pairs within r_max only: the network is evaluated on a compacted list,
+  // per passes of `per` sources (8 times the pairs the buffers hold on average)
   int64_t per = 8 * (m->max_rows / n_dom);
   if (per < 1) per = 1;
+  // every pair of the call fits the buffers: one pass, no count to check, no wait
+  const bool fits = n_src <= m->max_rows / n_dom;
+  if (fits) per = n_src;
+  // one pass: the pair search over sources s0 .. s0 + ns, then the network on
+  // its pairs -- n of them, or (n_dev set) as many as the search counted
+  auto run_pass = [&](int64_t s0, int64_t ns, int64_t n, const unsigned long long* n_dev) -> int {
+    FusedArgs a = fused_args(m);
+    a.src = d_src;
+    if (ns <= m->sprep_cap) {  // the sources' part of the features, once per source
+      PP_MLP_CUDA(launch_src_prep(m->fg, d_src, s0, ns, m->sprep, st));
+      a.sprep = m->sprep;
+      a.sprep_base = s0;
+    }
+    a.ps = m->ps;
+    a.pd = m->pd;
+    a.n = n;
+    a.n_dev = n_dev;
+    a.nph = d_nph_src;
+    a.dom_sum = d_dom_sums;
+    a.lambda_out = d_lambda;
+    PP_MLP_CUDA(launch_mlp_fused(a, &m->hbias, true, m->sms, st));
+    return PP_OK;
+  };
+  // First every pass is enqueued at once, the network reading its row count
+  // from the search's count in device memory; the host waits once, at the
+  // end, for the passes' counts.  Only if some pass found more pairs than the
+  // buffers hold does the call start over, pass by pass, waiting for each
+  // count and passing fewer sources at a time where needed.
+  const int64_t n_pass = (n_src + per - 1) / per;
+  if (n_pass > m->pass_cap) {
+    cudaFree(m->pass_count);
+    m->pass_count = nullptr;
+    m->pass_cap = 0;
+    PP_MLP_CUDA(dalloc(&m->pass_count, (size_t)n_pass));
+    m->pass_cap = n_pass;
+  }
+  for (int64_t k = 0; k < n_pass; ++k) {
+    const int64_t s0 = k * per, ns = std::min(per, n_src - s0);
+    PP_MLP_CUDA(cudaMemsetAsync(m->count, 0, sizeof(unsigned long long), st));
+    PP_MLP_CUDA(launch_near_pairs(m->fg, d_src, s0, ns, r_max, m->max_rows, m->ps, m->pd,
+                                  m->count, st));
+    PP_MLP_CUDA(cudaMemcpyAsync(m->pass_count + k, m->count, sizeof(unsigned long long),
+                                cudaMemcpyDeviceToDevice, st));
+    if ((rc = run_pass(s0, ns, m->max_rows, m->count))) return rc;
+  }
+  if (fits) return PP_OK;
+  std::vector<unsigned long long> counts((size_t)n_pass);
+  PP_MLP_CUDA(cudaMemcpyAsync(counts.data(), m->pass_count, sizeof(unsigned long long) * n_pass,
+                              cudaMemcpyDeviceToHost, st));
+  PP_MLP_CUDA(cudaStreamSynchronize(st));
+  bool overflow = false;
+  for (unsigned long long c : counts) overflow |= (int64_t)c > m->max_rows;
+  if (!overflow) return PP_OK;
+  if (d_dom_sums) PP_MLP_CUDA(cudaMemsetAsync(d_dom_sums, 0, sizeof(double) * n_dom, st));
+  if (d_lambda)
+    PP_MLP_CUDA(cudaMemsetAsync(d_lambda, 0, sizeof(float) * (size_t)n_src * n_dom, st));
   for (int64_t s0 = 0; s0 < n_src;) {
     int64_t ns = (n_src - s0) < per ? (n_src - s0) : per;
     unsigned long long cnt = 0;
@@ -558,22 +620,7 @@ int pp_mlp_dom_sums(pp_mlp* m, const pp_source* d_src, int64_t n_src, const floa
     }
     if ((int64_t)cnt > m->max_rows)
       return mfail(m, PP_EINVAL, "one source has more pairs within r_max than max_rows");
-    if (cnt > 0) {
-      FusedArgs a = fused_args(m);
-      a.src = d_src;
-      if (ns <= m->sprep_cap) {  // the sources' part of the features, once per source
-        PP_MLP_CUDA(launch_src_prep(m->fg, d_src, s0, ns, m->sprep, st));
-        a.sprep = m->sprep;
-        a.sprep_base = s0;
-      }
-      a.ps = m->ps;
-      a.pd = m->pd;
-      a.n = (int64_t)cnt;
-      a.nph = d_nph_src;
-      a.dom_sum = d_dom_sums;
-      a.lambda_out = d_lambda;
-      PP_MLP_CUDA(launch_mlp_fused(a, &m->hbias, true, m->sms, st));
-    }
+    if (cnt > 0 && (rc = run_pass(s0, ns, (int64_t)cnt, nullptr))) return rc;
     s0 += ns;
   }
   return PP_OK;

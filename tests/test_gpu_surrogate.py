@@ -462,6 +462,40 @@ def test_dom_sums_match_oracle(pp, prop, mlp, act):
     assert np.median(rel) < 3e-3 and np.quantile(rel, 0.99) < 3e-2, (np.median(rel), rel.max())
 
 
+def test_dom_sums_with_more_pairs_than_the_buffers(pp, prop, mlp):
+    """Every pass of pp_mlp_dom_sums is first enqueued at once, each taking its
+    row count from device memory; when a pass finds more pairs than the
+    buffers hold (here: 60 sources x 5160 DOMs within r_max, against buffers of
+    65 536 pairs), the call starts over with fewer sources per pass.  The
+    result must be that of the network on every pair, counted once."""
+    import torch
+    from oracle import mlp as M
+    geom, ice = W.geometry_full(), W.ice_full()
+    rng = np.random.default_rng(31)
+    src, _, _ = _training_like_pairs(rng, 60, geom)
+    p = pp.mlp_init_params(6).astype(np.float64)
+    p[-1] = -6.0
+    mlp.set_params(p.astype(np.float32))
+    nph = rng.uniform(1e3, 1e5, len(src)).astype(np.float32)
+    sums = torch.zeros(geom.n_dom, dtype=torch.float64, device="cuda")
+    lam = torch.zeros((len(src), geom.n_dom), dtype=torch.float32, device="cuda")
+    pp.pp_mlp_dom_sums(mlp.handle, _dev(src.view(np.uint8)), len(src), _dev(nph), 1e5, sums, lam,
+                       None)
+    pp.pp_mlp_sync(mlp.handle)
+    lam = lam.cpu().numpy().astype(np.float64)
+    sums = sums.cpu().numpy()
+    assert len(src) * geom.n_dom > 65536
+    assert np.all(lam > 0.0)
+    assert np.allclose(sums, lam.sum(0), rtol=1e-5, atol=1e-9)
+    ps = rng.integers(0, len(src), 3000)
+    pd = rng.integers(0, geom.n_dom, 3000)
+    x = M.bf16(M.features(src, ps, pd, geom.xyz, ice.b_e, ice.a, ice.depth_top, ice.dz))
+    ref, _ = M.forward(p.astype(np.float32).astype(np.float64), x, nph[ps].astype(np.float64),
+                       rounding=True)
+    rel = np.abs(lam[ps, pd] - ref) / ref
+    assert np.median(rel) < 3e-3 and np.quantile(rel, 0.99) < 3e-2, (np.median(rel), rel.max())
+
+
 def test_trained_surrogate_gains_over_monte_carlo(pp, prop):
     """What the trained network gains over the method without it: on fresh
     sources its per-DOM expectation is far closer to Monte Carlo counts than
