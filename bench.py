@@ -82,7 +82,7 @@ OPS_PER_BIRTH_EXECUTED = OPS_PER_BIRTH - 18
 # launch of the 1000-event step (captured on its first 200 events, scaled by sources),
 # and one 4 194 304-row launch of the fused surrogate kernel.
 NCU_TRAFFIC_BYTES = 191e6
-SUR_NCU_TRAFFIC_BYTES = 301.1e6
+SUR_NCU_TRAFFIC_BYTES = 301.8e6
 
 
 def parse():
