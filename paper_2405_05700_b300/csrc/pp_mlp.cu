@@ -547,7 +547,8 @@ int pp_mlp_dom_sums(pp_mlp* m, const pp_source* d_src, int64_t n_src, const floa
   int rc;
   if ((rc = ensure_packed(m, st)) || (rc = ensure_hbias(m, st))) return rc;
   // pairs within r_max only: the network is evaluated on a compacted list,
-  // per passes of `per` sources (8 times the pairs the buffers hold on average)
+  // in passes of `per` sources, whose candidate pairs (sources x DOMs) are 8
+  // times what the buffers hold: at most an eighth are expected within r_max
   int64_t per = 8 * (m->max_rows / n_dom);
   if (per < 1) per = 1;
   // every pair of the call fits the buffers: one pass, no count to check, no wait
