@@ -462,17 +462,20 @@ def test_dom_sums_match_oracle(pp, prop, mlp, act):
     assert np.median(rel) < 3e-3 and np.quantile(rel, 0.99) < 3e-2, (np.median(rel), rel.max())
 
 
-def test_dom_sums_with_more_pairs_than_the_buffers(pp, prop, mlp):
-    """Every pass of pp_mlp_dom_sums is first enqueued at once, each taking its
-    row count from device memory; when a pass finds more pairs than the
-    buffers hold (here: 60 sources x 5160 DOMs within r_max, against buffers of
-    65 536 pairs), the call starts over with fewer sources per pass.  The
-    result must be that of the network on every pair, counted once."""
+@pytest.mark.parametrize("n_src", [10, 60])
+def test_dom_sums_pass_paths(pp, prop, mlp, n_src):
+    """The two ways pp_mlp_dom_sums runs, with every pair within r_max and
+    buffers of 65 536 pairs.  10 sources x 5160 DOMs fit the buffers: one pass,
+    no wait.  60 sources do not: the passes are first enqueued at once, each
+    taking its row count from device memory; a pass that found more pairs than
+    the buffers hold makes the call start over with fewer sources per pass.
+    Either way the result must be that of the network on every pair, counted
+    once."""
     import torch
     from oracle import mlp as M
     geom, ice = W.geometry_full(), W.ice_full()
     rng = np.random.default_rng(31)
-    src, _, _ = _training_like_pairs(rng, 60, geom)
+    src, _, _ = _training_like_pairs(rng, n_src, geom)
     p = pp.mlp_init_params(6).astype(np.float64)
     p[-1] = -6.0
     mlp.set_params(p.astype(np.float32))
@@ -484,7 +487,7 @@ def test_dom_sums_with_more_pairs_than_the_buffers(pp, prop, mlp):
     pp.pp_mlp_sync(mlp.handle)
     lam = lam.cpu().numpy().astype(np.float64)
     sums = sums.cpu().numpy()
-    assert len(src) * geom.n_dom > 65536
+    assert (len(src) * geom.n_dom > 65536) == (n_src == 60)
     assert np.all(lam > 0.0)
     assert np.allclose(sums, lam.sum(0), rtol=1e-5, atol=1e-9)
     ps = rng.integers(0, len(src), 3000)
